@@ -1,0 +1,156 @@
+"""Seeded synthetic inputs for the periodic 3D PFC solver.
+
+This module only draws random numbers and samples closed-form initial fields
+at cell centres; it holds none of the scheme's arithmetic.  Both the CUDA path
+and the CPU oracle are fed from here.
+
+Every generator returns a C-contiguous float64 numpy array of shape (n, n, n)
+indexed [k, j, i] (z, y, x); cell (i, j, k) has centre ((i+1/2)h, (j+1/2)h,
+(k+1/2)h) with h = L/n.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+DEFAULT_SEED = 1234
+
+
+def cell_centres(n: int, L: float):
+    """Cell-centre coordinates (z, y, x) as broadcastable 1-D arrays."""
+    h = L / n
+    c = (np.arange(n) + 0.5) * h
+    return c[:, None, None], c[None, :, None], c[None, None, :]
+
+
+def uniform_noise(n: int, mean: float, amp: float, seed: int = DEFAULT_SEED):
+    """phi = mean + amp * U(-1, 1) per cell (the small random-start case:
+    n = 16, L = 32, eps = 0.025, mean = amp = 0.07)."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(mean + amp * rng.uniform(-1.0, 1.0, (n, n, n)))
+
+
+def smooth_mode(n: int, L: float, amp: float = 0.1):
+    """phi = amp sin(2 pi x/L) cos(2 pi y/L) sin(2 pi z/L) (the smooth
+    convergence-sweep workload on L = 32)."""
+    z, y, x = cell_centres(n, L)
+    k = 2.0 * math.pi / L
+    return np.ascontiguousarray(
+        amp * np.sin(k * x) * np.cos(k * y) * np.sin(k * z))
+
+
+def cosine_bump(n: int, L: float = 3.2, mean: float = 0.2, amp: float = 0.05):
+    """phi = mean + amp cos(2 pi x/L) cos(2 pi y/L) cos(2 pi z/L) on [0, L]^3
+    (the initial data of the paper's accuracy and multigrid-complexity tests,
+    Section 6.1)."""
+    z, y, x = cell_centres(n, L)
+    k = 2.0 * math.pi / L
+    return np.ascontiguousarray(
+        mean + amp * np.cos(k * x) * np.cos(k * y) * np.cos(k * z))
+
+
+def uniform_01_start(n: int, mean: float = 0.2, amp: float = 0.005,
+                     seed: int = DEFAULT_SEED):
+    """phi = mean + amp * U[0, 1] per cell (Section 6.2 polycrystal start)."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(mean + amp * rng.uniform(0.0, 1.0, (n, n, n)))
+
+
+def _random_rotation(rng):
+    """Uniform random rotation matrix from a normalised Gaussian quaternion."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+# The six {110} wave vectors of a one-mode BCC density field, |q| = 1.
+BCC_Q = np.array([[1, 1, 0], [1, -1, 0], [1, 0, 1],
+                  [1, 0, -1], [0, 1, 1], [0, 1, -1]], dtype=float) / math.sqrt(2)
+
+
+def polycrystal_seeds(n: int, L: float | None = None, n_seeds: int = 6,
+                      liquid: float = -0.25, noise: float = 0.01,
+                      crystal_amp: float = 0.3, radius_cells: float = 10.0,
+                      seed: int = DEFAULT_SEED):
+    """Liquid phi = liquid + noise * N(0,1) with ``n_seeds`` spherical seeds
+    (radius ``radius_cells`` * h, uniform random centres, periodic distance),
+    each adding a one-mode BCC field crystal_amp * sum_q cos(q . R (r - c))
+    with a random rotation R per seed.  Default L = n * pi / 4 (h = pi/4)."""
+    if L is None:
+        L = n * math.pi / 4.0
+    h = L / n
+    rng = np.random.default_rng(seed)
+    phi = liquid + noise * rng.normal(size=(n, n, n))
+    z, y, x = cell_centres(n, L)
+    X = np.broadcast_to(x, (n, n, n))
+    Y = np.broadcast_to(y, (n, n, n))
+    Z = np.broadcast_to(z, (n, n, n))
+    radius = radius_cells * h
+    for _ in range(n_seeds):
+        centre = rng.uniform(0.0, L, 3)
+        R = _random_rotation(rng)
+        # periodic displacement from the centre
+        dx = (X - centre[0] + 0.5 * L) % L - 0.5 * L
+        dy = (Y - centre[1] + 0.5 * L) % L - 0.5 * L
+        dz = (Z - centre[2] + 0.5 * L) % L - 0.5 * L
+        inside = dx * dx + dy * dy + dz * dz <= radius * radius
+        qs = BCC_Q @ R.T
+        field = sum(np.cos(q[0] * dx + q[1] * dy + q[2] * dz) for q in qs)
+        phi = np.where(inside, phi + crystal_amp * field, phi)
+    return np.ascontiguousarray(phi)
+
+
+@dataclass(frozen=True)
+class Workload:
+    """One named workload: grid, model parameters and the initial field."""
+    name: str
+    n: int
+    L: float
+    eps: float
+    dt: float
+    steps: int
+    tol: float
+
+    @property
+    def h(self) -> float:
+        return self.L / self.n
+
+    def phi0(self, seed: int = DEFAULT_SEED):
+        if self.name.startswith("random16"):
+            return uniform_noise(self.n, 0.07, 0.07, seed)
+        if self.name.startswith("smooth"):
+            return smooth_mode(self.n, self.L)
+        if self.name.startswith("polycrystal"):
+            return polycrystal_seeds(self.n, self.L, seed=seed)
+        if self.name.startswith("cosine"):
+            return cosine_bump(self.n, self.L)
+        raise KeyError(self.name)
+
+
+def random16():
+    """16^3, L = 32, eps = 0.025, phi0 = 0.07 + 0.07 U(-1,1), dt = 0.01,
+    10 steps, tolerance 1e-10."""
+    return Workload("random16", 16, 32.0, 0.025, 0.01, 10, 1e-10)
+
+
+def smooth_sweep(n: int, dt: float = 0.0125, tol: float = 1e-9):
+    """Smooth mode on L = 32, eps = 0.025, to T = 1 (steps = 1/dt)."""
+    return Workload(f"smooth{n}", n, 32.0, 0.025, dt, int(round(1.0 / dt)), tol)
+
+
+def polycrystal(n: int = 256, steps: int = 2000, tol: float = 1e-9):
+    """Polycrystal growth: h = pi/4, eps = 0.25, dt = 0.1."""
+    return Workload(f"polycrystal{n}", n, n * math.pi / 4.0, 0.25, 0.1, steps, tol)
+
+
+def cosine_table(n: int, dt: float = 1e-3, steps: int = 10, tol: float = 1e-8):
+    """Section 6.1 multigrid-complexity setting: [0, 3.2]^3, eps = 0.025."""
+    return Workload(f"cosine{n}", n, 3.2, 0.025, dt, steps, tol)

@@ -1,0 +1,315 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics,
+independent of the oracle's own code paths (no GPU needed).
+
+Each test names the passage or identity it checks.  A plausible slip in the
+oracle (a dropped term, a wrong sign, a transposed operand, a wrong index)
+fails at least one of them:
+
+* Laplacian: Fourier symbol of Delta_h (Section 4.1, symbol of D_x) and a
+  brute-force 7-point loop (Section 2).
+* Summation by parts, Lemma 2.1; the inequality of Lemma 2.2.
+* Discrete energy Eq. 2.1 on a single Fourier mode in closed form.
+* Cramer's rule against LAPACK.
+* Transfers: mass and constants preserved, linear functions reproduced.
+* The scheme without the cubic term against its Fourier closed form.
+* A constant state as an exact solution of Eq. 1.10.
+* Exact energy law of the scheme (derived from Eq. 1.10 with Lemma 2.1) and
+  mass conservation.
+* FAS (Algorithm 1) against a dense Newton solve of N(u) = S.
+* Second-order time accuracy (Theorem 3.4) on a refinement in tau.
+* Multigrid iteration counts of Table 2.
+"""
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pfc_oracle as O
+from paper_1611_06288_gb300 import workloads as W
+
+RNG = np.random.default_rng(20240611)
+
+
+def rand_field(m, scale=1.0):
+    return scale * RNG.standard_normal((m, m, m))
+
+
+# --------------------------------------------------------------------------
+# Section 2 operators
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,L", [(8, 32.0), (12, 3.2), (16, 10.0)])
+def test_laplacian_fourier_symbol(m, L):
+    """Delta_h cos(2 pi r.x/L) = lam cos(...), lam = -(4/h^2) sum sin^2(pi r_d/m)."""
+    h = L / m
+    z, y, x = W.cell_centres(m, L)
+    for r in [(1, 0, 0), (0, 2, 1), (3, 1, 2), (m // 2, 1, 0)]:
+        theta = 2 * math.pi * (r[0] * x + r[1] * y + r[2] * z) / L
+        v = np.cos(theta)
+        lam = -(4.0 / h ** 2) * sum(math.sin(math.pi * rd / m) ** 2 for rd in r)
+        np.testing.assert_allclose(O.lap(v, h), lam * v, atol=1e-12 * abs(lam) + 1e-13)
+
+
+def test_laplacian_brute_force_loop():
+    """7-point formula of Section 2 evaluated cell by cell with explicit wrap."""
+    m, h = 5, 0.7
+    v = rand_field(m)
+    out = np.empty_like(v)
+    for k in range(m):
+        for j in range(m):
+            for i in range(m):
+                s = (v[k, j, (i + 1) % m] + v[k, j, (i - 1) % m]
+                     + v[k, (j + 1) % m, i] + v[k, (j - 1) % m, i]
+                     + v[(k + 1) % m, j, i] + v[(k - 1) % m, j, i])
+                out[k, j, i] = (s - 6.0 * v[k, j, i]) / h ** 2
+    np.testing.assert_allclose(O.lap(v, h), out, rtol=1e-13, atol=1e-13)
+
+
+def grad_ip(f, g, h):
+    return sum(O.face_ip(O.op_D(f, ax, h), O.op_D(g, ax, h), ax, h) for ax in O.AXES)
+
+
+def test_summation_by_parts_lemma_2_1():
+    """(f, D g) = -(grad f, grad g); (f, D^2 g) = (D f, D g);
+    (f, D^3 g) = -(grad D f, grad D g), D = Delta_h (Lemma 2.1)."""
+    m, h = 10, 0.3
+    f, g = rand_field(m), rand_field(m)
+    L1, L2 = O.lap(g, h), O.lap(O.lap(g, h), h)
+    L3 = O.lap(L2, h)
+    s = max(abs(O.ip2(f, L3, h)), 1.0)
+    assert O.ip2(f, L1, h) == pytest.approx(-grad_ip(f, g, h), rel=1e-12)
+    assert O.ip2(f, L2, h) == pytest.approx(O.ip2(O.lap(f, h), O.lap(g, h), h), rel=1e-12)
+    assert O.ip2(f, L3, h) == pytest.approx(
+        -grad_ip(O.lap(f, h), O.lap(g, h), h), rel=1e-11, abs=1e-12 * s)
+
+
+def test_lemma_2_2_inequality():
+    """||D phi||^2 <= ||phi||^2/(3 a^2) + (2a/3) ||grad D phi||^2 for all a > 0."""
+    m, h = 8, 0.5
+    for _ in range(5):
+        phi = rand_field(m)
+        lhs = O.norm2(O.lap(phi, h), h) ** 2
+        for a in (0.01, 0.1, 0.5, 1.0, 3.0, 20.0):
+            rhs = (O.norm2(phi, h) ** 2 / (3 * a * a)
+                   + 2 * a / 3 * O.grad_norm2_sq(O.lap(phi, h), h))
+            assert lhs <= rhs * (1 + 1e-12)
+
+
+def test_energy_single_mode_closed_form():
+    """F_h (Eq. 2.1) of phi = c0 + A cos(kx)cos(ky)cos(kz), k = 2 pi r/L.
+
+    On the grid the mean of cos^2 is 1/2 and of cos^4 is 3/8 per axis (for
+    4r not a multiple of m), and the Laplacian acts by its symbol lam."""
+    m, L, r = 16, 20.0, 1
+    h = L / m
+    A = 0.3
+    z, y, x = W.cell_centres(m, L)
+    k = 2 * math.pi * r / L
+    phi = A * np.cos(k * x) * np.cos(k * y) * np.cos(k * z)
+    lam = -(4.0 / h ** 2) * 3 * math.sin(math.pi * r / m) ** 2
+    vol = L ** 3
+    eps = 0.3
+    l2 = A * A * vol / 8.0
+    l4 = A ** 4 * vol * (3.0 / 8.0) ** 3
+    grad = -lam * l2
+    lap2 = lam * lam * l2
+    F = 0.25 * l4 + 0.5 * (1 - eps) * l2 - grad + 0.5 * lap2
+    assert O.energy(phi, h, eps) == pytest.approx(F, rel=1e-12)
+    assert O.mass(phi + 0.5, h) == pytest.approx(0.5 * vol, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Pointwise solve and transfers
+# --------------------------------------------------------------------------
+
+def test_cramer_matches_lapack():
+    n = 50
+    A = RNG.standard_normal((n, 3, 3)) + 3 * np.eye(3)
+    rhs = RNG.standard_normal((n, 3))
+    x = O.cramer3([[A[:, i, j] for j in range(3)] for i in range(3)],
+                  [rhs[:, i] for i in range(3)])
+    ref = np.linalg.solve(A, rhs[..., None])[..., 0]
+    np.testing.assert_allclose(np.stack(x, 1), ref, rtol=1e-11, atol=1e-12)
+
+
+def test_transfers():
+    m, L = 8, 4.0
+    v = rand_field(m)
+    # 8-cell average preserves the integral and constants
+    assert O.restrict(v).sum() * 8 == pytest.approx(v.sum(), rel=1e-13)
+    np.testing.assert_allclose(O.restrict(np.full((m,) * 3, 1.7)), 1.7, rtol=1e-15)
+    # a field linear in x (away from the periodic wrap) is averaged to the
+    # value at the coarse centre and interpolated exactly by trilinear P
+    z, y, x = W.cell_centres(m, L)
+    lin = np.broadcast_to(2.0 * x + 0.5, (m, m, m)).copy()
+    zc, yc, xc = W.cell_centres(m // 2, L)
+    np.testing.assert_allclose(O.restrict(lin)[0, 0, :], 2.0 * xc.ravel() + 0.5, rtol=1e-14)
+    fine = O.prolong(np.broadcast_to(2.0 * xc + 0.5, (m // 2,) * 3).copy())
+    np.testing.assert_allclose(fine[:, :, 1:-1], lin[:, :, 1:-1], rtol=1e-14)
+    # rows of P sum to one; piecewise-constant P copies values
+    np.testing.assert_allclose(O.prolong(np.ones((4, 4, 4))), 1.0, rtol=1e-15)
+    c = rand_field(4)
+    np.testing.assert_array_equal(O.restrict(O.prolong(c, "constant")), c)
+
+
+# --------------------------------------------------------------------------
+# The scheme: closed forms and the exact discrete laws
+# --------------------------------------------------------------------------
+
+def test_constant_state_is_exact():
+    """phi^{k-1} = phi^k = c0 gives phi^{k+1} = c0, mu = c0^3 + (1-eps) c0,
+    omega = 0 (Eqs. 5.1-5.3 with Delta_h c0 = 0)."""
+    m, h, eps, tau = 8, 1.5, 0.2, 0.05
+    c0 = 0.37
+    b = np.full((m,) * 3, c0)
+    prm = O.Params(eps=eps, tau=tau)
+    S = O.source_S(b, b, h, prm)
+    u = [b.copy(), np.full_like(b, c0 ** 3 + (1 - eps) * c0), np.zeros_like(b)]
+    assert O.rms(O.residual(S, u, b, h, prm)) < 1e-15
+
+
+@pytest.mark.parametrize("m,L", [(8, 12.0), (16, 32.0)])
+def test_linear_scheme_fourier_closed_form(m, L):
+    """Without the cubic term the step is diagonal in Fourier space; the FAS
+    solve (Algorithm 1) must reproduce the closed form."""
+    h = L / m
+    eps, tau = 0.1, 0.05
+    b = rand_field(m, 0.1)
+    c = b + rand_field(m, 0.01)
+    prm = O.Params(eps=eps, tau=tau, cubic=False, coarsest=2)
+    a_ref = O.linear_step_fft(b, c, h, eps, tau)
+    res = O.solve_step(b, c, [b, 0 * b, 0 * b], h, prm, tol=1e-14, max_cycles=60)
+    assert res.history[-1] <= 1e-13
+    np.testing.assert_allclose(res.u[0], a_ref, rtol=0, atol=1e-12 * np.abs(a_ref).max())
+    # the dense Newton solve agrees too
+    if m == 8:
+        u, _ = O.newton_dense(O.source_S(b, c, h, prm), [b, 0 * b, 0 * b], b, h, prm)
+        np.testing.assert_allclose(u[0], a_ref, atol=1e-12 * np.abs(a_ref).max())
+
+
+def energy_law_terms(a, b, c, mu, h, eps, tau):
+    """F~(a,b) - F~(b,c) and its prediction -tau||grad mu||^2 - 1/2||grad(a-2b+c)||^2."""
+    lhs = O.modified_energy(a, b, h, eps) - O.modified_energy(b, c, h, eps)
+    rhs = -tau * O.grad_norm2_sq(mu, h) - 0.5 * O.grad_norm2_sq(a - 2 * b + c, h)
+    return lhs, rhs
+
+
+def test_energy_law_and_mass_random16():
+    """Exact discrete energy law and mass conservation over several steps of
+    the 16^3 random start (L = 32, eps = 0.025, dt = 0.01)."""
+    wl = W.random16()
+    prm = O.Params(eps=wl.eps, tau=wl.dt)
+    phi0 = wl.phi0()
+    m0 = O.mass(phi0, wl.h)
+    checks = []
+
+    def cb(k, a, b, c, mu, om, res):
+        lhs, rhs = energy_law_terms(a, b, c, mu, wl.h, wl.eps, wl.dt)
+        checks.append((lhs, rhs, O.mass(a, wl.h), res.history[-1]))
+
+    O.run(phi0, 5, wl.h, prm, tol=1e-13, callback=cb)
+    for lhs, rhs, m, r in checks:
+        assert r <= 1e-13
+        assert lhs < 0
+        assert lhs == pytest.approx(rhs, rel=1e-8, abs=1e-9)
+        assert m == pytest.approx(m0, rel=1e-12)
+
+
+def test_energy_law_start_step_cosine():
+    """The same law on the first step (phi^{-1} = phi^0) of the Section 6.1
+    initial data at 16^3, a strongly evolving case."""
+    wl = W.cosine_table(16)
+    prm = O.Params(eps=wl.eps, tau=wl.dt, linearization="picard")
+    b = wl.phi0()
+    res = O.solve_step(b, b, [b, 0 * b, 0 * b], wl.h, prm, tol=1e-13)
+    a, mu = res.u[0], res.u[1]
+    lhs, rhs = energy_law_terms(a, b, b, mu, wl.h, wl.eps, wl.dt)
+    assert lhs == pytest.approx(rhs, rel=1e-8)
+    assert O.mass(a, wl.h) == pytest.approx(O.mass(b, wl.h), rel=1e-13)
+
+
+def test_fas_matches_dense_newton_8():
+    """Algorithm 1 reaches the unique solution of N(u) = S (Prop. 3.1) that a
+    dense Newton solve finds, at 8^3 with the cubic term active."""
+    m, L = 8, 16.0
+    h = L / m
+    eps, tau = 0.1, 0.05
+    b = 0.2 + rand_field(m, 0.1)
+    c = b + rand_field(m, 0.01)
+    for lin in ("newton", "picard"):
+        prm = O.Params(eps=eps, tau=tau, linearization=lin, coarsest=2)
+        S = O.source_S(b, c, h, prm)
+        ref, its = O.newton_dense(S, [b, 0 * b, 0 * b], b, h, prm)
+        assert O.rms(O.residual(S, ref, b, h, prm)) < 1e-13
+        res = O.solve_step(b, c, [b, 0 * b, 0 * b], h, prm, tol=1e-13)
+        for x, y in zip(res.u, ref):
+            np.testing.assert_allclose(x, y, atol=1e-11 * (1 + np.abs(y).max()))
+
+
+def test_exact_solution_is_smoother_fixed_point():
+    """One red-black sweep leaves the exact solution of N(u) = S unchanged
+    (both pointwise linearisations, Section 5)."""
+    m, L = 8, 16.0
+    h = L / m
+    b = 0.2 + rand_field(m, 0.1)
+    c = b + rand_field(m, 0.01)
+    for lin in ("newton", "picard"):
+        prm = O.Params(eps=0.1, tau=0.05, linearization=lin)
+        S = O.source_S(b, c, h, prm)
+        ref, _ = O.newton_dense(S, [b, 0 * b, 0 * b], b, h, prm)
+        out = O.smooth(ref, S, b, h, prm, 1)
+        for x, y in zip(out, ref):
+            np.testing.assert_allclose(x, y, atol=1e-12 * (1 + np.abs(y).max()))
+
+
+def test_smoother_reduces_residual():
+    """Several sweeps from a rough guess reduce the residual (Section 5 smoother)."""
+    wl = W.random16()
+    prm = O.Params(eps=wl.eps, tau=wl.dt)
+    b = wl.phi0()
+    S = O.source_S(b, b, wl.h, prm)
+    u = [b, 0 * b, 0 * b]
+    r0 = O.rms(O.residual(S, u, b, wl.h, prm))
+    u = O.smooth(u, S, b, wl.h, prm, 3)
+    assert O.rms(O.residual(S, u, b, wl.h, prm)) < 0.1 * r0
+
+
+# --------------------------------------------------------------------------
+# Theorem 3.4 (second order in time) and Table 2 (multigrid complexity)
+# --------------------------------------------------------------------------
+
+def test_second_order_in_time():
+    """Cauchy differences at T = 0.4 for tau, tau/2, tau/4, tau/8 on the 16^3
+    random start shrink by about 4 per halving (Theorem 3.4)."""
+    wl = W.random16()
+    phi0 = wl.phi0()
+    T = 0.4
+    sols = []
+    for tau in (0.1, 0.05, 0.025, 0.0125):
+        prm = O.Params(eps=wl.eps, tau=tau)
+        a, *_ = O.run(phi0, int(round(T / tau)), wl.h, prm, tol=1e-13)
+        sols.append(a)
+    d = [O.norm2(sols[i] - sols[i + 1], wl.h) for i in range(3)]
+    rates = [math.log2(d[i] / d[i + 1]) for i in range(2)]
+    assert all(1.8 < r < 2.3 for r in rates), (d, rates)
+
+
+def test_table2_vcycle_counts(golden_dir):
+    """V-cycles to tol 1e-8 at step 10 (Table 2, Section 6.1) with the paper's
+    Picard smoother, at 16^3 and 32^3: V(2,2) within +-2 of the printed
+    counts, and V(1,1) needs more cycles than V(2,2)."""
+    gold = json.load(open(os.path.join(golden_dir, "table2_vcycles.json")))
+    for idx, n in enumerate((16, 32)):
+        wl = W.cosine_table(n)
+        counts = {}
+        for nu in (1, 2):
+            prm = O.Params(eps=wl.eps, tau=wl.dt, nu1=nu, nu2=nu,
+                           linearization="picard", coarsest=2)
+            *_, cycles = O.run(wl.phi0(), 10, wl.h, prm, tol=wl.tol)
+            counts[nu] = cycles[-1]
+        assert abs(counts[2] - gold["cycles"]["2,2"][idx]) <= 2, counts
+        assert counts[1] > counts[2]
+        assert abs(counts[1] - gold["cycles"]["1,1"][idx]) <= 3, counts
