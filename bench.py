@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the PFC time step (second-order convex splitting, FAS /
+defect-correction multigrid) on GB300.
+
+Workload: 128^3 cells, L = 32, eps = 0.025, phi0 = 0.1 sin(2 pi x/L)
+cos(2 pi y/L) sin(2 pi z/L), dt = 0.0125, residual tolerance 1e-9 (RMS of the
+three FP64 components).  A "step" is one full time step: source, multigrid
+cycles until the FP64 residual is below the tolerance, and the energy/mass
+diagnostics.  The headline value is the mixed-precision path (FP64 defect
+correction around FP32 multigrid); the plain FP64 FAS path is timed beside it.
+
+Prints one JSON line (rank 0).  Under torchrun every rank advances its own
+replica (no collective on the data path; weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "steps/s at 128^3 (mixed vs FP64 GPU, residual 1e-9); % HBM roof per V-cycle"
+UNIT = "steps/s"
+WORKLOAD = {"workload": "smooth-mode 128^3", "n": 128, "L": 32.0, "eps": 0.025,
+            "dt": 0.0125, "tol": 1e-9, "phi0": "0.1 sin(2pi x/L) cos(2pi y/L) sin(2pi z/L)"}
+
+# Algorithmic bytes per cell of one counted launch, and launches per timed
+# group, for each kernel class (minimum traffic: every field touched once).
+KERNEL_BYTES = {
+    "defect": (64.0, 2),          # read phi,mu,om,b,S2,S3 (48) write r32 x3, q32 (16)
+    "lin_smooth": (20.0, 1),      # per colour pass: half of read d (12) + r,q (16) + write d (12)
+    "lin_restrict": (29.5, 1),    # read d,r,q (28) + write coarse r (12/8)
+    "lin_prolong": (25.5, 1),     # read+write d (24) + coarse d (12/8)
+    "correct": (60.0, 1),         # read u (24) d (12) write u (24)
+    "smooth": (40.0, 1),          # per colour pass: half of (u 24 + S2,S3 16 + b 8 + phi 8 + write u 24)
+    "residual_norm": (48.0, 2),   # read u, b, S2, S3
+    "residual_restrict": (57.0, 1),
+    "prolong": (57.0, 2),
+    "source": (32.0, 1),
+    "restrict": (9.0, 1),
+    "coarse_source": (80.0, 1),
+    "coarse_solve": (0.0, 1),
+    "lin_coarse": (0.0, 1),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--inner-cycles", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.idx)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step_time(n: int):
+    """Time one full oracle time step of the workload (start rule, tol 1e-9)."""
+    from oracle import pfc_oracle as O
+    from paper_1611_06288_gb300 import workloads as W
+    wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
+    phi0 = wl.phi0()
+    prm = O.Params(eps=wl.eps, tau=wl.dt)
+    t0 = time.perf_counter()
+    res = O.solve_step(phi0, phi0, [phi0, 0 * phi0, 0 * phi0], wl.h, prm, wl.tol)
+    O.energy(res.u[0], wl.h, wl.eps)
+    O.mass(res.u[0], wl.h)
+    return time.perf_counter() - t0, res.cycles
+
+
+def cpu_threads() -> int:
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        return max([i.get("num_threads", 1) for i in info] or [1])
+    except Exception:
+        return 1
+
+
+def run_reference(args):
+    """The oracle (numpy FP64, host cores) on the same workload and metric."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n = args.n
+    # One full step is ~15-20 s at 128^3: the bounded sample of each bench
+    # step is one oracle time step; steps/warmup are capped to keep the run
+    # within a few minutes.
+    warm = min(args.warmup, 1)
+    steps = min(args.steps, 3)
+    for _ in range(warm):
+        oracle_step_time(n)
+    times, cycles = [], []
+    for _ in range(steps):
+        t, c = oracle_step_time(n)
+        times.append(t)
+        cycles.append(c)
+    tot = sum(times)
+    value = steps / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": steps, "warmup": warm, "ms_per_step": 1e3 * tot / steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(WORKLOAD, n=n, l2="inputs > L2 not applicable (CPU)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                         "sample": f"{steps} full oracle time steps at {n}^3 from phi0 "
+                                   f"(start rule), V-cycles {cycles}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1611_06288_gb300 import binding as B
+    from paper_1611_06288_gb300 import workloads as W
+    from paper_1611_06288_gb300.solver import PFCSolver
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        tdist.init_process_group("nccl", device_id=dev)
+    B.lib()  # fails loudly if libpfc.so is missing
+
+    n = args.n
+    wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
+    phi0 = wl.phi0()
+    cells = n ** 3
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if ws > 1:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def time_steps(s, k, profile_classes=None, diag=True):
+        """k timed steps, L2 flushed (untimed) before each; returns total ms."""
+        st = s.stream
+        total = 0.0
+        cycles = []
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            stats = s.step(1)
+            if diag:
+                s.diagnostics()
+            e1.record(st)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+            cycles.append(stats.cycles_last)
+        return total, cycles
+
+    # ---- mixed path (headline) --------------------------------------------
+    s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="mixed",
+                  inner_cycles=args.inner_cycles)
+    for _ in range(args.warmup):
+        s.step(1)
+        s.diagnostics()
+    # one profiled step (all classes) to find the dominant kernel
+    s.profile(None)
+    time_steps(s, 2)
+    prof = s.profile_read()
+    (dom_cls, dom_lvl), (dom_n, dom_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    s.profile([dom_cls])
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = s.launches
+    ms_total, cycles = time_steps(s, args.steps)
+    launches = s.launches - launches0
+    barrier()
+    clk = clocks.stop()
+    dom_launches, dom_time = B.pfc_profile_read(s.ctx, B.KERNEL_CLASSES.index(dom_cls), dom_lvl)
+    s.profile([])
+
+    t_local = ms_total / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if ws > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    t_max = float(t.item())
+    value = ws * args.steps / t_max
+
+    # roofline of the dominant kernel
+    peaks, peak_src = measured_peaks()
+    m = n >> dom_lvl
+    per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
+    launch_bytes = per_cell * m ** 3 * per_group
+    groups = dom_launches / per_group
+    achieved = launch_bytes * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": f"{dom_cls} (level {dom_lvl}, {m}^3)",
+                "ms_per_launch": dom_time / max(groups, 1),
+                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"}
+
+    # ---- plain FP64 FAS path, same workload and tolerance -----------------
+    s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="fp64")
+    for _ in range(min(args.warmup, 2)):
+        s64.step(1)
+        s64.diagnostics()
+    ms64, cyc64 = time_steps(s64, args.fp64_steps)
+    fp64 = {"value": args.fp64_steps / (ms64 / 1e3), "unit": UNIT, "steps": args.fp64_steps,
+            "cycles_per_step": cyc64}
+    s64.close()
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    pin_a = torch.from_numpy(phi0.copy()).pin_memory()
+    pin_b = torch.from_numpy(phi0.copy()).pin_memory()
+    pin_out = torch.empty_like(pin_a).pin_memory()
+    se = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="mixed",
+                   inner_cycles=args.inner_cycles)
+    e2e_steps = max(1, min(args.steps, 10))
+
+    def host_step():
+        B.pfc_set_state(se.ctx, pin_a, pin_b)     # H2D of phi^k, phi^{k-1}
+        B.pfc_step(se.ctx, 1)
+        B.pfc_get_phi(se.ctx, pin_out)            # D2H of phi^{k+1}
+        B.pfc_diagnostics(se.ctx)                 # D2H of the diagnostics (blocking)
+        pin_b.copy_(pin_a)
+        pin_a.copy_(pin_out)
+
+    host_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        host_step()
+    e2e_t = time.perf_counter() - t0
+    e2e = {"value": e2e_steps / e2e_t, "unit": UNIT, "h2d_bytes_per_step": 2 * cells * 8,
+           "d2h_bytes_per_step": cells * 8 + 6 * 8}
+    se.close()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_cpu, cyc_cpu = oracle_step_time(n)
+        cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"1 full oracle time step at {n}^3 from phi0 (start rule), "
+                         f"{cyc_cpu} V-cycles"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD["workload"], "n": n, "L": wl.L, "eps": wl.eps,
+                       "dt": wl.dt, "tol": wl.tol, "precision": "mixed",
+                       "inner_cycles": args.inner_cycles,
+                       "parallelism": f"replicas x{ws}",
+                       "l2": "flushed (256 MiB write) before every timed step"},
+            "cycles_per_step": cycles,
+            "dof_updates_per_s": value * cells,
+            "fp64": fp64,
+            "mixed_over_fp64": value / ws / fp64["value"],
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "kernel_profile_ms": {f"{k[0]}@{n >> k[1]}": round(v[1], 4)
+                                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        }
+        if cpu is not None:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    s.close()
+    if ws > 1:
+        tdist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,295 @@
+/*
+ * pfc.h - C ABI of libpfc, the GB300 (sm_103a) solver for the second-order
+ * convex-splitting finite-difference scheme of the periodic 3D phase field
+ * crystal (PFC) equation, each time step solved by a nonlinear FAS multigrid
+ * V-cycle (Dong, Feng, Wang, Wise, Zhang, arXiv:1611.06288).
+ *
+ * Model (Section 3, Eq. 1.10, in the split form of Section 5, Eqs. 5.1-5.10,
+ * mobility M = 1): given phi^k = b and phi^{k-1} = c on the periodic
+ * cell-centred grid of n^3 cells, h = L/n, find u = (phi^{k+1}, mu, omega) with
+ *   N1 = phi - tau Lap_h mu                                    = S1 = b
+ *   N2 = mu - (phi+b)(phi^2+b^2)/4 - (1-eps)/2 phi - Lap_h omega
+ *                                      = S2 = (1-eps)/2 b + 3 Lap_h b - Lap_h c
+ *   N3 = omega - Lap_h phi / 2                                 = S3 = Lap_h b / 2
+ * where Lap_h is the 7-point Laplacian of Section 2.
+ *
+ * Conventions for every entry point:
+ *  - A "field" is n*n*n doubles (or floats where stated), x fastest: cell
+ *    (i, j, k) is element i + n*(j + n*k).  Fields must not overlap unless
+ *    stated.
+ *  - Pointers named d_* are device pointers on the current CUDA device.
+ *    Pointers named any_* may be device or host memory (copied with
+ *    cudaMemcpyDefault; pinned host memory keeps the copy asynchronous).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; calls return before it completes
+ *    unless stated as blocking.
+ *  - The library never frees caller memory.  It allocates no device memory:
+ *    the caller passes a workspace of pfc_workspace_bytes() bytes.  The only
+ *    host allocation is the context itself and a small pinned readback slot.
+ *  - Return value: PFC_OK (0) or a negative PFC_E* code; nothing is printed
+ *    and nothing aborts.  pfc_strerror() gives a message.
+ */
+#ifndef PFC_H
+#define PFC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFC_OK       0
+#define PFC_EINVAL  -1  /* bad argument (null pointer, eps >= 1, tau <= 0 ...) */
+#define PFC_ESIZE   -2  /* n not coarsenable to an even coarsest size, or workspace too small */
+#define PFC_ENOCONV -3  /* max_cycles reached before the residual tolerance */
+#define PFC_ENAN    -4  /* residual became NaN or Inf */
+#define PFC_ECUDA   -5  /* a CUDA runtime call failed */
+
+#define PFC_FP64  0     /* FAS V-cycles entirely in FP64 (Algorithm 1) */
+#define PFC_MIXED 1     /* FP64 defect correction around FP32 multigrid */
+
+#define PFC_NEWTON 0    /* pointwise Newton linearisation of the cubic term */
+#define PFC_PICARD 1    /* the paper's local Picard linearisation (Section 5) */
+
+typedef struct pfc_ctx pfc_ctx;   /* opaque; owns no device memory */
+
+typedef struct pfc_params {
+  int    n;            /* cells per side (cube only, Section 2); n >= 4, even */
+  double L;            /* side of the periodic box; h = L / n */
+  double eps;          /* model epsilon, 0 <= eps < 1 */
+  double dt;           /* time step tau > 0 */
+  int    nu1, nu2;     /* pre/post smoothing sweeps (Algorithm 1); >= 0 */
+  double tol;          /* absolute tolerance on the FP64 fine-grid residual,
+                          RMS over the three components */
+  int    max_cycles;   /* V-cycles (or defect corrections) per step */
+  int    precision;    /* PFC_FP64 or PFC_MIXED */
+  int    smoother;     /* PFC_NEWTON or PFC_PICARD (FP64 path) */
+  int    coarsest;     /* coarsen while the level size is even and larger
+                          than this; the last level is solved by sweeping to
+                          convergence.  >= 2 */
+  int    inner_cycles; /* PFC_MIXED: FP32 V-cycles per FP64 defect correction */
+} pfc_params;
+
+typedef struct pfc_step_stats {
+  int    steps;        /* steps completed by the call */
+  int    cycles_last;  /* V-cycles (FP64) or corrections (mixed) in the last step */
+  int    cycles_total; /* summed over the call */
+  double residual;     /* final RMS residual of the last step */
+  double residual0;    /* RMS residual of the initial guess of the last step */
+} pfc_step_stats;
+
+/* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
+ * FP64, coarsest 2, inner_cycles 1.  n, L, eps, dt are set to 0. */
+void pfc_default_params(pfc_params* p);
+
+/* Bytes of device workspace pfc_init needs for *p (0 if *p is invalid). */
+size_t pfc_workspace_bytes(const pfc_params* p);
+
+/* Create a solver context.
+ * d_workspace: >= pfc_workspace_bytes(p) bytes of device memory, 256-byte
+ *   aligned, owned by the caller and kept alive until pfc_destroy.
+ * any_phi0: phi^0 (a field).  any_phi1: phi^1, or NULL to start with the
+ *   rule phi^{-1} := phi^0 (the first step then uses c = b).
+ * Copies the initial fields into the workspace and returns after they are
+ * enqueued on `stream`.  Errors: PFC_EINVAL, PFC_ESIZE, PFC_ECUDA. */
+int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
+             size_t workspace_bytes, const double* any_phi0,
+             const double* any_phi1, void* stream);
+
+/* Advance nsteps time steps of Eq. 1.10.  Each step forms S (Eqs. 5.8-5.10)
+ * and runs V-cycles until the RMS residual <= tol.  Blocking: reads the
+ * residual back once per cycle.  On PFC_ENOCONV / PFC_ENAN the state holds
+ * the last iterate of the failing step (not advanced).  stats may be NULL. */
+int pfc_step(pfc_ctx* ctx, int nsteps, pfc_step_stats* stats);
+
+/* Replace the state by (phi^k, phi^{k-1}) = (any_phi, any_phi_prev);
+ * any_phi_prev NULL means phi^{k-1} := phi^k.  mu and omega are kept as warm
+ * starts.  Enqueued on the context stream. */
+int pfc_set_state(pfc_ctx* ctx, const double* any_phi, const double* any_phi_prev);
+
+/* Copy phi^k (the newest level) / mu^{k-1/2} / omega^{k-1/2} to any_dst.
+ * Enqueued on the context stream (synchronise before reading host memory). */
+int pfc_get_phi(pfc_ctx* ctx, double* any_dst);
+int pfc_get_mu(pfc_ctx* ctx, double* any_dst);
+int pfc_get_omega(pfc_ctx* ctx, double* any_dst);
+
+/* Discrete energy F_h(phi^k) (Eq. 2.1) and the modified energy
+ * F_h(phi^k) + 1/2 ||grad_h(phi^k - phi^{k-1})||^2 (Prop. 3.1); either
+ * output may be NULL.  Blocking.  Deterministic (fixed summation order). */
+int pfc_energy(pfc_ctx* ctx, double* F, double* F_modified);
+
+/* Mass (phi^k, 1)_2 = h^3 sum phi^k (Section 2).  Blocking, deterministic. */
+int pfc_mass(pfc_ctx* ctx, double* mass);
+
+/* All diagnostics of phi^k in one pass (blocking, deterministic):
+ * out[0] = F_h(phi^k), out[1] = modified energy, out[2] = mass,
+ * out[3] = ||grad_h phi^k||^2. */
+int pfc_diagnostics(pfc_ctx* ctx, double out[4]);
+
+/* Steps taken since pfc_init (counting phi^1 when it was given). */
+int pfc_step_index(const pfc_ctx* ctx);
+
+/* Kernel launches enqueued by pfc_step / pfc_energy / pfc_mass /
+ * pfc_diagnostics since pfc_init (a host-side counter). */
+long long pfc_launch_count(const pfc_ctx* ctx);
+
+void pfc_destroy(pfc_ctx* ctx);
+const char* pfc_strerror(int code);
+
+/* Detail of the last PFC_ECUDA returned on this host thread ("" if none). */
+const char* pfc_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * Kernel timing (tracing).  When enabled for a set of kernel classes, every
+ * launch of those classes made by pfc_step is bracketed by CUDA events on the
+ * context stream and its device time is accumulated per (class, level);
+ * level 0 is the finest grid.  Timing adds two event records per bracketed
+ * launch group and nothing else.
+ * --------------------------------------------------------------------- */
+#define PFC_K_SOURCE            0   /* S2, S3 (Eqs. 5.9-5.10) */
+#define PFC_K_RESTRICT          1   /* 8-cell average of phi^k or q per level */
+#define PFC_K_SMOOTH            2   /* FP64 red-black half-sweeps */
+#define PFC_K_RESIDUAL_RESTRICT 3   /* FP64 residual + restriction */
+#define PFC_K_COARSE_SOURCE     4   /* FAS coarse right-hand side */
+#define PFC_K_PROLONG           5   /* FP64 correction e = v - w, u += P e */
+#define PFC_K_COARSE_SOLVE      6   /* FP64 coarsest-level solve */
+#define PFC_K_RESIDUAL_NORM     7   /* FP64 residual norm (convergence test) */
+#define PFC_K_DEFECT            8   /* mixed: FP64 residual -> FP32, q */
+#define PFC_K_LIN_SMOOTH        9   /* mixed: FP32 red-black half-sweeps */
+#define PFC_K_LIN_RESTRICT     10   /* mixed: FP32 residual + restriction */
+#define PFC_K_LIN_PROLONG      11   /* mixed: FP32 d += P d_c */
+#define PFC_K_LIN_COARSE       12   /* mixed: FP32 coarsest-level solve */
+#define PFC_K_CORRECT          13   /* mixed: u += d in FP64 */
+#define PFC_K_COUNT            14
+#define PFC_PROFILE_LEVELS     24
+
+/* Enable timing for the classes whose bit (1 << PFC_K_*) is set in mask
+ * (0 disables) and clear the accumulators.  Creates CUDA events on first use. */
+int pfc_profile_enable(pfc_ctx* ctx, unsigned mask);
+
+/* Accumulated kernel launches and device milliseconds of one class on one
+ * level since pfc_profile_enable.  Synchronises the context stream. */
+int pfc_profile_read(pfc_ctx* ctx, int kclass, int level, long long* launches,
+                     double* ms);
+
+/* ------------------------------------------------------------------------
+ * Primitive operations: one per stage of the V-cycle, on caller device
+ * buffers, enqueued on `stream`.  n is the level size (cells per side), h its
+ * spacing.  They exist so that every stage can be checked on its own; the
+ * solver above calls the same kernels.
+ * --------------------------------------------------------------------- */
+
+/* S2 = (1-eps)/2 b + 3 Lap_h b - Lap_h c and S3 = Lap_h b / 2
+ * (Eqs. 5.9-5.10); S1 is b itself (Eq. 5.8). */
+int pfc_op_source(int n, double h, double eps, const double* d_b,
+                  const double* d_c, double* d_S2, double* d_S3, void* stream);
+
+/* `sweeps` red-black nonlinear Gauss-Seidel sweeps on u = (phi, mu, om) in
+ * place (Section 5): red cells ((i+j+k) even) first, each solving the
+ * pointwise 3x3 system with its neighbours fixed; `smoother` selects the
+ * Newton or the paper's Picard linearisation.  n even. */
+int pfc_op_smooth(int n, double h, double eps, double tau, int smoother,
+                  int sweeps, double* d_phi, double* d_mu, double* d_om,
+                  const double* d_S1, const double* d_S2, const double* d_S3,
+                  const double* d_b, void* stream);
+
+/* r = S - N(u) (Algorithm 1 "Residual"), full fine-grid fields. */
+int pfc_op_residual(int n, double h, double eps, double tau,
+                    const double* d_phi, const double* d_mu, const double* d_om,
+                    const double* d_S1, const double* d_S2, const double* d_S3,
+                    const double* d_b, double* d_r1, double* d_r2, double* d_r3,
+                    void* stream);
+
+/* Fused residual + restriction (Algorithm 1 "Residual", "Coarsening"): for
+ * every coarse cell, the 8-cell averages of r = S - N(u) and of u are written
+ * to d_rc* and d_uc* (fields of (n/2)^3).  n even. */
+int pfc_op_residual_restrict(int n, double h, double eps, double tau,
+                             const double* d_phi, const double* d_mu,
+                             const double* d_om, const double* d_S1,
+                             const double* d_S2, const double* d_S3,
+                             const double* d_b, double* d_rc1, double* d_rc2,
+                             double* d_rc3, double* d_uc1, double* d_uc2,
+                             double* d_uc3, void* stream);
+
+/* 8-cell average of one field onto the grid of size n/2. */
+int pfc_op_restrict(int n, const double* d_fine, double* d_coarse, void* stream);
+
+/* FAS coarse source S_c = N_c(u_c) + r_c on a level of size n, spacing h,
+ * with b_c the restricted phi^k (in place over d_r*: on return d_r* hold
+ * S_c).  Algorithm 1 "Solve"/"Recursion" right-hand side. */
+int pfc_op_coarse_source(int n, double h, double eps, double tau,
+                         const double* d_uc1, const double* d_uc2,
+                         const double* d_uc3, const double* d_bc,
+                         double* d_r1, double* d_r2, double* d_r3, void* stream);
+
+/* Correction u += P(v_c - w_c) for the three components (Algorithm 1
+ * "Correction"): P is trilinear cell-centred interpolation from the level of
+ * size n/2; v_c the coarse solution, w_c the restricted u it started from. */
+int pfc_op_prolong_correct(int n, const double* d_vc1, const double* d_vc2,
+                           const double* d_vc3, const double* d_wc1,
+                           const double* d_wc2, const double* d_wc3,
+                           double* d_u1, double* d_u2, double* d_u3,
+                           void* stream);
+
+/* Coarsest-level solve of N(u) = S by red-black sweeps until the largest
+ * change is below 1e-15 (relative) or max_sweeps; one thread block.  n even,
+ * n <= 16. */
+int pfc_op_coarse_solve(int n, double h, double eps, double tau, int smoother,
+                        int max_sweeps, double* d_phi, double* d_mu,
+                        double* d_om, const double* d_S1, const double* d_S2,
+                        const double* d_S3, const double* d_b, void* stream);
+
+/* Diagnostics of one field pair (Section 2 norms, Eq. 2.1), blocking:
+ * out[0] = F_h(a), out[1] = F_h(a) + 1/2 ||grad_h(a - b)||^2, out[2] = mass
+ * h^3 sum a, out[3] = ||grad_h a||^2.  d_scratch: pfc_reduce_scratch_bytes(n)
+ * bytes of device memory. */
+size_t pfc_reduce_scratch_bytes(int n);
+int pfc_op_diagnostics(int n, double h, double eps, const double* d_a,
+                       const double* d_b, void* d_scratch, double* out,
+                       void* stream);
+
+/* RMS residual sqrt(sum_c sum r_c^2 / (3 n^3)) of u (blocking). */
+int pfc_op_residual_norm(int n, double h, double eps, double tau,
+                         const double* d_phi, const double* d_mu,
+                         const double* d_om, const double* d_S1,
+                         const double* d_S2, const double* d_S3,
+                         const double* d_b, void* d_scratch, double* out,
+                         void* stream);
+
+/* ------------------------------------------------------------------------
+ * Primitive operations of the mixed-precision path (PFC_MIXED).  The outer
+ * loop is an FP64 defect correction: r = S - N(u) in FP64, then an FP32
+ * multigrid solve of J d = r, with J the Jacobian of N at u (Eqs. 5.4-5.6
+ * differentiated in phi: only the cubic term's coefficient
+ * q = f'(phi) + (1-eps)/2, f(a) = (a+b)(a^2+b^2)/4, depends on u), then
+ * u += d.  The paper has no mixed-precision form; this is a solver strategy
+ * whose fixed point is the FP64 solution of N(u) = S.
+ * --------------------------------------------------------------------- */
+
+/* FP64 residual r = S - N(u) stored as floats in d_r1..3, the coefficient
+ * q = f'(phi) + (1-eps)/2 as floats in d_q, and *out = RMS of the FP64
+ * residual (blocking).  d_scratch: pfc_reduce_scratch_bytes(n) bytes. */
+int pfc_op_defect(int n, double h, double eps, double tau, const double* d_phi,
+                  const double* d_mu, const double* d_om, const double* d_S1,
+                  const double* d_S2, const double* d_S3, const double* d_b,
+                  float* d_r1, float* d_r2, float* d_r3, float* d_q,
+                  void* d_scratch, double* out, void* stream);
+
+/* `sweeps` red-black Gauss-Seidel sweeps in FP32 on J d = r with q frozen
+ * (the same pointwise 3x3 system as pfc_op_smooth with q given).  zero_init
+ * != 0 declares d = 0 on entry (d need not be initialised).  n even. */
+int pfc_op_lin_smooth(int n, double h, double eps, double tau, int sweeps,
+                      int zero_init, float* d_d1, float* d_d2, float* d_d3,
+                      const float* d_r1, const float* d_r2, const float* d_r3,
+                      const float* d_q, void* stream);
+
+/* u += d (FP64 += FP32) for the three components. */
+int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
+                   const float* d_d1, const float* d_d2, const float* d_d3,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFC_H */

@@ -310,6 +310,49 @@ def smooth(u, S, b, h, prm: Params, sweeps):
 
 
 # --------------------------------------------------------------------------
+# Linearisation of N at u (used by the mixed-precision defect correction)
+# --------------------------------------------------------------------------
+
+def jacobian_coefficient(phi, b, prm: Params):
+    """q = f'(phi) + (1-eps)/2: the only u-dependent entry of dN/du."""
+    q = np.full_like(phi, 0.5 * (1.0 - prm.eps))
+    if prm.cubic:
+        q = q + cubic_fprime(phi, b)
+    return q
+
+
+def jacobian_apply(d, q, h, prm: Params):
+    """J d for J = dN/du of Eqs. 5.4-5.6 with the coefficient field q."""
+    dp, dm, dw = d
+    j1 = dp - prm.tau * div_M_grad(dm, h, prm.mob)
+    j2 = dm - q * dp - lap(dw, h)
+    j3 = dw - 0.5 * lap(dp, h)
+    return [j1, j2, j3]
+
+
+def linear_smooth(d, r, q, h, prm: Params, sweeps):
+    """Red-black Gauss-Seidel on J d = r: the Section 5 pointwise 3x3 system
+    with q held fixed and no cubic right-hand-side term."""
+    dp, dm, dw = (x.copy() for x in d)
+    r1, r2, r3 = r
+    colour = colour_mask(dp.shape[0])
+    g = 1.0 / (h * h)
+    kap = prm.tau * g * face_mobility_sums(dp.shape, prm.mob)
+    for _ in range(sweeps):
+        for col in (0, 1):
+            sel = colour == col
+            st1 = r1 + prm.tau * g * neighbour_sum(dm)
+            st2 = r2 + g * neighbour_sum(dw)
+            st3 = r3 + 0.5 * g * neighbour_sum(dp)
+            A = [[1.0, kap, 0.0], [-q, 1.0, 6.0 * g], [3.0 * g, 0.0, 1.0]]
+            x1, x2, x3 = cramer3(A, (st1, st2, st3))
+            dp = np.where(sel, x1, dp)
+            dm = np.where(sel, x2, dm)
+            dw = np.where(sel, x3, dw)
+    return [dp, dm, dw]
+
+
+# --------------------------------------------------------------------------
 # Transfers between levels
 # --------------------------------------------------------------------------
 

@@ -1,0 +1,313 @@
+"""ctypes binding of libpfc (include/pfc.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and takes
+torch tensors (device pointers) or plain numbers; every step of the solver runs
+in the CUDA library.  Loading fails loudly if libpfc.so is missing: there is no
+CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpfc.so")
+
+PFC_OK, PFC_EINVAL, PFC_ESIZE, PFC_ENOCONV, PFC_ENAN, PFC_ECUDA = 0, -1, -2, -3, -4, -5
+PFC_FP64, PFC_MIXED = 0, 1
+PFC_NEWTON, PFC_PICARD = 0, 1
+
+
+class PFCError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        self.code = code
+        msg = f"{what}: {strerror(code)} ({code})"
+        if detail:
+            msg += f" [{detail}]"
+        super().__init__(msg)
+
+
+class pfc_params(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("L", ctypes.c_double), ("eps", ctypes.c_double),
+                ("dt", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
+                ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("coarsest", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+
+
+class pfc_step_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("cycles_last", ctypes.c_int),
+                ("cycles_total", ctypes.c_int), ("residual", ctypes.c_double),
+                ("residual0", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "pfc_default_params": (None, [ctypes.POINTER(pfc_params)]),
+    "pfc_workspace_bytes": (_SZ, [ctypes.POINTER(pfc_params)]),
+    "pfc_init": (_I, [ctypes.POINTER(_P), ctypes.POINTER(pfc_params), _P, _SZ, _P, _P, _P]),
+    "pfc_step": (_I, [_P, _I, ctypes.POINTER(pfc_step_stats)]),
+    "pfc_set_state": (_I, [_P, _P, _P]),
+    "pfc_get_phi": (_I, [_P, _P]),
+    "pfc_get_mu": (_I, [_P, _P]),
+    "pfc_get_omega": (_I, [_P, _P]),
+    "pfc_energy": (_I, [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)]),
+    "pfc_mass": (_I, [_P, ctypes.POINTER(_D)]),
+    "pfc_step_index": (_I, [_P]),
+    "pfc_diagnostics": (_I, [_P, ctypes.POINTER(_D)]),
+    "pfc_launch_count": (ctypes.c_longlong, [_P]),
+    "pfc_destroy": (None, [_P]),
+    "pfc_strerror": (ctypes.c_char_p, [_I]),
+    "pfc_last_error": (ctypes.c_char_p, []),
+    "pfc_op_source": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
+    "pfc_op_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
+    "pfc_op_residual": (_I, [_I, _D, _D, _D] + [_P] * 10 + [_P]),
+    "pfc_op_residual_restrict": (_I, [_I, _D, _D, _D] + [_P] * 13 + [_P]),
+    "pfc_op_restrict": (_I, [_I, _P, _P, _P]),
+    "pfc_op_coarse_source": (_I, [_I, _D, _D, _D] + [_P] * 7 + [_P]),
+    "pfc_op_prolong_correct": (_I, [_I] + [_P] * 9 + [_P]),
+    "pfc_op_coarse_solve": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
+    "pfc_reduce_scratch_bytes": (_SZ, [_I]),
+    "pfc_op_diagnostics": (_I, [_I, _D, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
+    "pfc_op_residual_norm": (_I, [_I, _D, _D, _D] + [_P] * 8 + [ctypes.POINTER(_D), _P]),
+    "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
+    "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
+    "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
+    "pfc_profile_enable": (_I, [_P, ctypes.c_uint]),
+    "pfc_profile_read": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_longlong),
+                              ctypes.POINTER(_D)]),
+}
+
+# kernel classes of pfc_profile_enable / pfc_profile_read
+KERNEL_CLASSES = ["source", "restrict", "smooth", "residual_restrict", "coarse_source",
+                  "prolong", "coarse_solve", "residual_norm", "defect", "lin_smooth",
+                  "lin_restrict", "lin_prolong", "lin_coarse", "correct"]
+PROFILE_LEVELS = 24
+
+_lib = None
+
+
+def lib():
+    """Load libpfc.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise PFCError(PFC_EINVAL, "load libpfc.so",
+                           f"{LIB_PATH} missing: run `python -m paper_1611_06288_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return lib().pfc_strerror(code).decode()
+    except Exception:  # library not loadable: still format the error
+        return "error"
+
+
+def check(rc: int, what: str) -> None:
+    if rc != PFC_OK:
+        detail = lib().pfc_last_error().decode() if rc == PFC_ECUDA else ""
+        raise PFCError(rc, what, detail)
+
+
+def ptr(t) -> int | None:
+    """Device (or host) address of a tensor, None for None."""
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def stream_of(t=None):
+    """cudaStream_t of torch's current stream on the tensor's device."""
+    import torch
+    dev = t.device if t is not None else torch.device("cuda")
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# Solver context
+# ---------------------------------------------------------------------------
+
+def pfc_default_params() -> pfc_params:
+    p = pfc_params()
+    lib().pfc_default_params(ctypes.byref(p))
+    return p
+
+
+def pfc_workspace_bytes(p: pfc_params) -> int:
+    return int(lib().pfc_workspace_bytes(ctypes.byref(p)))
+
+
+def pfc_init(p: pfc_params, workspace, phi0, phi1=None, stream=None) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    rc = lib().pfc_init(ctypes.byref(ctx), ctypes.byref(p), ptr(workspace),
+                        workspace.numel() * workspace.element_size(), ptr(phi0),
+                        ptr(phi1), stream)
+    check(rc, "pfc_init")
+    return ctx
+
+
+def pfc_step(ctx, nsteps: int = 1) -> pfc_step_stats:
+    st = pfc_step_stats()
+    check(lib().pfc_step(ctx, nsteps, ctypes.byref(st)), "pfc_step")
+    return st
+
+
+def pfc_set_state(ctx, phi, phi_prev=None) -> None:
+    check(lib().pfc_set_state(ctx, ptr(phi), ptr(phi_prev)), "pfc_set_state")
+
+
+def pfc_get_phi(ctx, dst) -> None:
+    check(lib().pfc_get_phi(ctx, ptr(dst)), "pfc_get_phi")
+
+
+def pfc_get_mu(ctx, dst) -> None:
+    check(lib().pfc_get_mu(ctx, ptr(dst)), "pfc_get_mu")
+
+
+def pfc_get_omega(ctx, dst) -> None:
+    check(lib().pfc_get_omega(ctx, ptr(dst)), "pfc_get_omega")
+
+
+def pfc_energy(ctx) -> tuple[float, float]:
+    F, Fm = ctypes.c_double(), ctypes.c_double()
+    check(lib().pfc_energy(ctx, ctypes.byref(F), ctypes.byref(Fm)), "pfc_energy")
+    return F.value, Fm.value
+
+
+def pfc_mass(ctx) -> float:
+    m = ctypes.c_double()
+    check(lib().pfc_mass(ctx, ctypes.byref(m)), "pfc_mass")
+    return m.value
+
+
+def pfc_step_index(ctx) -> int:
+    return int(lib().pfc_step_index(ctx))
+
+
+def pfc_diagnostics(ctx) -> list[float]:
+    out = (ctypes.c_double * 4)()
+    check(lib().pfc_diagnostics(ctx, out), "pfc_diagnostics")
+    return list(out)
+
+
+def pfc_launch_count(ctx) -> int:
+    return int(lib().pfc_launch_count(ctx))
+
+
+def pfc_destroy(ctx) -> None:
+    lib().pfc_destroy(ctx)
+
+
+def pfc_profile_enable(ctx, mask: int) -> None:
+    check(lib().pfc_profile_enable(ctx, mask), "pfc_profile_enable")
+
+
+def pfc_profile_read(ctx, kclass: int, level: int) -> tuple[int, float]:
+    n, ms = ctypes.c_longlong(), ctypes.c_double()
+    check(lib().pfc_profile_read(ctx, kclass, level, ctypes.byref(n), ctypes.byref(ms)),
+          "pfc_profile_read")
+    return n.value, ms.value
+
+
+# ---------------------------------------------------------------------------
+# Primitive operations (tensors in, results written into tensors)
+# ---------------------------------------------------------------------------
+
+def pfc_op_source(n, h, eps, b, c, S2, S3, stream=None):
+    check(lib().pfc_op_source(n, h, eps, ptr(b), ptr(c), ptr(S2), ptr(S3), stream),
+          "pfc_op_source")
+
+
+def pfc_op_smooth(n, h, eps, tau, smoother, sweeps, phi, mu, om, S1, S2, S3, b, stream=None):
+    check(lib().pfc_op_smooth(n, h, eps, tau, smoother, sweeps, ptr(phi), ptr(mu), ptr(om),
+                              ptr(S1), ptr(S2), ptr(S3), ptr(b), stream), "pfc_op_smooth")
+
+
+def pfc_op_residual(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, r1, r2, r3, stream=None):
+    check(lib().pfc_op_residual(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1), ptr(S2),
+                                ptr(S3), ptr(b), ptr(r1), ptr(r2), ptr(r3), stream),
+          "pfc_op_residual")
+
+
+def pfc_op_residual_restrict(n, h, eps, tau, phi, mu, om, S1, S2, S3, b,
+                             rc1, rc2, rc3, uc1, uc2, uc3, stream=None):
+    check(lib().pfc_op_residual_restrict(
+        n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1), ptr(S2), ptr(S3), ptr(b),
+        ptr(rc1), ptr(rc2), ptr(rc3), ptr(uc1), ptr(uc2), ptr(uc3), stream),
+        "pfc_op_residual_restrict")
+
+
+def pfc_op_restrict(n, fine, coarse, stream=None):
+    check(lib().pfc_op_restrict(n, ptr(fine), ptr(coarse), stream), "pfc_op_restrict")
+
+
+def pfc_op_coarse_source(n, h, eps, tau, uc1, uc2, uc3, bc, r1, r2, r3, stream=None):
+    check(lib().pfc_op_coarse_source(n, h, eps, tau, ptr(uc1), ptr(uc2), ptr(uc3), ptr(bc),
+                                     ptr(r1), ptr(r2), ptr(r3), stream),
+          "pfc_op_coarse_source")
+
+
+def pfc_op_prolong_correct(n, vc1, vc2, vc3, wc1, wc2, wc3, u1, u2, u3, stream=None):
+    check(lib().pfc_op_prolong_correct(n, ptr(vc1), ptr(vc2), ptr(vc3), ptr(wc1), ptr(wc2),
+                                       ptr(wc3), ptr(u1), ptr(u2), ptr(u3), stream),
+          "pfc_op_prolong_correct")
+
+
+def pfc_op_coarse_solve(n, h, eps, tau, smoother, max_sweeps, phi, mu, om, S1, S2, S3, b,
+                        stream=None):
+    check(lib().pfc_op_coarse_solve(n, h, eps, tau, smoother, max_sweeps, ptr(phi), ptr(mu),
+                                    ptr(om), ptr(S1), ptr(S2), ptr(S3), ptr(b), stream),
+          "pfc_op_coarse_solve")
+
+
+def pfc_reduce_scratch_bytes(n) -> int:
+    return int(lib().pfc_reduce_scratch_bytes(n))
+
+
+def pfc_op_diagnostics(n, h, eps, a, b, scratch, stream=None):
+    out = (ctypes.c_double * 4)()
+    check(lib().pfc_op_diagnostics(n, h, eps, ptr(a), ptr(b), ptr(scratch), out, stream),
+          "pfc_op_diagnostics")
+    return list(out)
+
+
+def pfc_op_residual_norm(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, scratch, stream=None):
+    out = ctypes.c_double()
+    check(lib().pfc_op_residual_norm(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1),
+                                     ptr(S2), ptr(S3), ptr(b), ptr(scratch),
+                                     ctypes.byref(out), stream), "pfc_op_residual_norm")
+    return out.value
+
+
+def pfc_op_defect(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, scratch,
+                  stream=None):
+    out = ctypes.c_double()
+    check(lib().pfc_op_defect(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1), ptr(S2),
+                              ptr(S3), ptr(b), ptr(r1), ptr(r2), ptr(r3), ptr(q),
+                              ptr(scratch), ctypes.byref(out), stream), "pfc_op_defect")
+    return out.value
+
+
+def pfc_op_lin_smooth(n, h, eps, tau, sweeps, zero_init, d1, d2, d3, r1, r2, r3, q,
+                      stream=None):
+    check(lib().pfc_op_lin_smooth(n, h, eps, tau, sweeps, int(bool(zero_init)), ptr(d1),
+                                  ptr(d2), ptr(d3), ptr(r1), ptr(r2), ptr(r3), ptr(q),
+                                  stream), "pfc_op_lin_smooth")
+
+
+def pfc_op_correct(n, u1, u2, u3, d1, d2, d3, stream=None):
+    check(lib().pfc_op_correct(n, ptr(u1), ptr(u2), ptr(u3), ptr(d1), ptr(d2), ptr(d3),
+                               stream), "pfc_op_correct")

@@ -1,0 +1,681 @@
+// C ABI of libpfc (include/pfc.h): the solver context, the workspace carving,
+// the FAS V-cycle driver of Algorithm 1 and the primitive operations.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "pfc_internal.h"
+#include "pfc_mixed.h"
+
+namespace pfc {
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* what) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+  return PFC_ECUDA;
+}
+
+#define PFC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);  \
+  } while (0)
+
+// Enqueue `call` bracketed by the profiler's events for (cls, level).
+#define PFC_TIMED(pr, cls, level, nlaunch, st, call) \
+  do {                                                \
+    prof_begin(pr, cls, st);                          \
+    PFC_CUDA(call);                                   \
+    prof_end(pr, cls, level, nlaunch, st);            \
+  } while (0)
+
+constexpr int kMaxLevels = 24;
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Level sizes: halve while the size is even and larger than `coarsest`.
+int level_sizes(const pfc_params* p, int* sizes) {
+  int n = p->n, nl = 0;
+  sizes[nl++] = n;
+  while (n % 2 == 0 && n > p->coarsest && nl < kMaxLevels) {
+    n /= 2;
+    sizes[nl++] = n;
+  }
+  return nl;
+}
+
+int validate(const pfc_params* p) {
+  if (!p) return PFC_EINVAL;
+  if (p->n < 4 || (p->n & 1)) return PFC_ESIZE;
+  if (!(p->L > 0) || !(p->eps >= 0 && p->eps < 1) || !(p->dt > 0)) return PFC_EINVAL;
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return PFC_EINVAL;
+  if (!(p->tol > 0) || p->max_cycles < 1 || p->coarsest < 2) return PFC_EINVAL;
+  if (p->precision != PFC_FP64 && p->precision != PFC_MIXED) return PFC_EINVAL;
+  if (p->smoother != PFC_NEWTON && p->smoother != PFC_PICARD) return PFC_EINVAL;
+  if (p->precision == PFC_MIXED && p->inner_cycles < 1) return PFC_EINVAL;
+  int sizes[kMaxLevels];
+  const int nl = level_sizes(p, sizes);
+  const int nc = sizes[nl - 1];
+  if (nc % 2 != 0 || nc > 16 || nl < 2) return PFC_ESIZE;
+  return PFC_OK;
+}
+
+struct Carver {
+  char* base;
+  size_t off;
+  template <class T>
+  T* take(size_t count) {
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += align_up(count * sizeof(T));
+    return p;
+  }
+};
+
+}  // namespace
+
+struct Level64 {
+  int n;
+  Lvl L;
+  double *u[3], *w[3], *S[3], *b;   // level 0 uses only the ring/context fields
+};
+
+}  // namespace pfc
+
+struct pfc_ctx {
+  pfc_params p;
+  cudaStream_t st;
+  int nl;
+  int sizes[pfc::kMaxLevels];
+  pfc::Level64 lev[pfc::kMaxLevels];
+  double* ring[3];   // phi^{k-1}, phi^k, phi^{k+1} rotate through these
+  int ic, ib, ia;
+  double *mu, *om, *S2, *S3;
+  double* partials;  // reduction partial sums
+  double* dout;      // 8 device doubles of reduction results
+  double* hout;      // 8 pinned host doubles
+  pfc::MixedBufs mx; // FP32 hierarchy of the mixed path
+  int step;
+  pfc::Prof prof;    // optional event timing of launches
+};
+
+namespace pfc {
+namespace {
+
+size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
+  Carver cv{base, 0};
+  const int64_t n3 = (int64_t)p->n * p->n * p->n;
+  int sizes[kMaxLevels];
+  const int nl = level_sizes(p, sizes);
+  for (int r = 0; r < 3; ++r) {
+    double* f = cv.take<double>(n3);
+    if (c) c->ring[r] = f;
+  }
+  double* mu = cv.take<double>(n3);
+  double* om = cv.take<double>(n3);
+  double* S2 = cv.take<double>(n3);
+  double* S3 = cv.take<double>(n3);
+  if (c) {
+    c->mu = mu;
+    c->om = om;
+    c->S2 = S2;
+    c->S3 = S3;
+    c->nl = nl;
+    for (int l = 0; l < nl; ++l) c->sizes[l] = sizes[l];
+  }
+  for (int l = 1; l < nl; ++l) {
+    const int64_t m3 = (int64_t)sizes[l] * sizes[l] * sizes[l];
+    Level64 lv;
+    for (int q = 0; q < 3; ++q) lv.u[q] = cv.take<double>(m3);
+    for (int q = 0; q < 3; ++q) lv.w[q] = cv.take<double>(m3);
+    for (int q = 0; q < 3; ++q) lv.S[q] = cv.take<double>(m3);
+    lv.b = cv.take<double>(m3);
+    if (c) c->lev[l] = lv;
+  }
+  double* partials = cv.take<double>((size_t)kReduceBlocks * kReduceComps);
+  double* dout = cv.take<double>(kReduceComps);
+  if (c) {
+    c->partials = partials;
+    c->dout = dout;
+  }
+  if (p->precision == PFC_MIXED) {
+    MixedBufs mx;
+    mixed_carve(&mx, p->n, nl, sizes, [&](size_t count) { return cv.take<float>(count); });
+    if (c) c->mx = mx;
+  }
+  return cv.off;
+}
+
+// Views of level 0 for the current ring position.
+void level0(pfc_ctx* c, Level64* lv) {
+  lv->n = c->p.n;
+  lv->L = c->lev[0].L;
+  lv->u[0] = c->ring[c->ia];
+  lv->u[1] = c->mu;
+  lv->u[2] = c->om;
+  lv->S[0] = c->ring[c->ib];
+  lv->S[1] = c->S2;
+  lv->S[2] = c->S3;
+  lv->b = c->ring[c->ib];
+}
+
+int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
+  const int lin = c->p.smoother;
+  cudaStream_t st = c->st;
+  Prof* pr = &c->prof;
+  if (l == c->nl - 1) {
+    PFC_TIMED(pr, PFC_K_COARSE_SOLVE, l, 1, st,
+              launch_coarse_solve(lv.L, lin, 200, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
+                                  lv.S[1], lv.S[2], lv.b, st));
+    return PFC_OK;
+  }
+  Level64& cl = c->lev[l + 1];
+  if (c->p.nu1 > 0)
+    PFC_TIMED(pr, PFC_K_SMOOTH, l, 2 * c->p.nu1, st,
+              launch_smooth(lv.L, lin, c->p.nu1, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
+                            lv.S[1], lv.S[2], lv.b, st));
+  PFC_TIMED(pr, PFC_K_RESIDUAL_RESTRICT, l, 1, st,
+            launch_residual_restrict(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
+                                     lv.S[2], lv.b, cl.S[0], cl.S[1], cl.S[2], cl.u[0],
+                                     cl.u[1], cl.u[2], cl.w[0], cl.w[1], cl.w[2], st));
+  PFC_TIMED(pr, PFC_K_COARSE_SOURCE, l + 1, 1, st,
+            launch_coarse_source(cl.L, cl.u[0], cl.u[1], cl.u[2], cl.b, cl.S[0], cl.S[1],
+                                 cl.S[2], st));
+  int rc = vcycle64(c, l + 1, cl);
+  if (rc) return rc;
+  prof_begin(pr, PFC_K_PROLONG, st);
+  PFC_CUDA(launch_coarse_diff(cl.n, cl.u[0], cl.u[1], cl.u[2], cl.w[0], cl.w[1], cl.w[2],
+                              st));
+  PFC_CUDA(launch_prolong_add(lv.n, cl.w[0], cl.w[1], cl.w[2], lv.u[0], lv.u[1], lv.u[2],
+                              st));
+  prof_end(pr, PFC_K_PROLONG, l, 2, st);
+  if (c->p.nu2 > 0)
+    PFC_TIMED(pr, PFC_K_SMOOTH, l, 2 * c->p.nu2, st,
+              launch_smooth(lv.L, lin, c->p.nu2, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
+                            lv.S[1], lv.S[2], lv.b, st));
+  return PFC_OK;
+}
+
+// RMS residual of the level-0 iterate; blocking readback.
+int residual_rms(pfc_ctx* c, const Level64& lv, double* rms) {
+  cudaStream_t st = c->st;
+  PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
+            launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
+                                  lv.S[2], lv.b, c->partials, c->dout, st));
+  PFC_CUDA(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  prof_harvest(&c->prof);
+  const double n3 = (double)c->p.n * c->p.n * c->p.n;
+  *rms = sqrt(c->hout[0] / (3.0 * n3));
+  return PFC_OK;
+}
+
+int step_once(pfc_ctx* c, pfc_step_stats* stats) {
+  Level64 lv;
+  level0(c, &lv);
+  const double* cprev = c->ring[c->ic];
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  Prof* pr = &c->prof;
+  PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
+            launch_source(lv.L, lv.b, cprev, c->S2, c->S3, c->st));
+  // phi^k on every level (inside the coarse cubic terms of the FAS path)
+  if (c->p.precision == PFC_FP64) {
+    const double* fine = lv.b;
+    for (int l = 1; l < c->nl; ++l) {
+      PFC_TIMED(pr, PFC_K_RESTRICT, l - 1, 1, c->st,
+                launch_restrict(c->sizes[l - 1], fine, c->lev[l].b, c->st));
+      fine = c->lev[l].b;
+    }
+  }
+  PFC_CUDA(cudaMemcpyAsync(lv.u[0], lv.b, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                           c->st));
+  int rc = PFC_OK;
+  int cycles = 0;
+  double res0 = 0, res = 0;
+  if (c->p.precision == PFC_MIXED) {
+    rc = mixed_solve(c->mx, lv.L, c->p, c->nl, c->sizes, lv.u, lv.S, lv.b, c->partials,
+                     c->dout, c->hout, c->st, pr, &cycles, &res0, &res);
+    if (rc == PFC_ECUDA) snprintf(g_last_error, sizeof(g_last_error), "mixed path CUDA error");
+  } else {
+    rc = residual_rms(c, lv, &res);
+    if (rc) return rc;
+    res0 = res;
+    while (!(res <= c->p.tol)) {
+      if (!isfinite(res)) { rc = PFC_ENAN; break; }
+      if (cycles >= c->p.max_cycles) { rc = PFC_ENOCONV; break; }
+      rc = vcycle64(c, 0, lv);
+      if (rc) return rc;
+      ++cycles;
+      rc = residual_rms(c, lv, &res);
+      if (rc) return rc;
+    }
+  }
+  if (stats) {
+    stats->cycles_last = cycles;
+    stats->cycles_total += cycles;
+    stats->residual = res;
+    stats->residual0 = res0;
+  }
+  if (rc == PFC_ENAN) {
+    cudaMemsetAsync(c->mu, 0, n3 * sizeof(double), c->st);
+    cudaMemsetAsync(c->om, 0, n3 * sizeof(double), c->st);
+  }
+  if (rc) return rc;
+  const int old_c = c->ic;
+  c->ic = c->ib;
+  c->ib = c->ia;
+  c->ia = old_c;
+  c->step += 1;
+  if (stats) stats->steps += 1;
+  return PFC_OK;
+}
+
+}  // namespace
+
+void prof_begin(Prof* pr, int cls, cudaStream_t st) {
+  if (!pr || !((pr->mask >> cls) & 1u)) return;
+  if (pr->pending == Prof::kPool) {
+    cudaEventSynchronize(pr->ev[2 * Prof::kPool - 1]);
+    prof_harvest(pr);
+  }
+  cudaEventRecord(pr->ev[2 * pr->pending], st);
+}
+
+void prof_end(Prof* pr, int cls, int level, int nlaunch, cudaStream_t st) {
+  if (!pr) return;
+  pr->launches += nlaunch;
+  if (!((pr->mask >> cls) & 1u)) return;
+  const int i = pr->pending;
+  cudaEventRecord(pr->ev[2 * i + 1], st);
+  pr->cls[i] = cls;
+  pr->lev[i] = level < PFC_PROFILE_LEVELS ? level : PFC_PROFILE_LEVELS - 1;
+  pr->nlaunch[i] = nlaunch;
+  pr->pending = i + 1;
+}
+
+void prof_harvest(Prof* pr) {
+  if (!pr) return;
+  for (int i = 0; i < pr->pending; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pr->ev[2 * i], pr->ev[2 * i + 1]) == cudaSuccess) {
+      pr->ms[pr->cls[i]][pr->lev[i]] += t;
+      pr->cnt[pr->cls[i]][pr->lev[i]] += pr->nlaunch[i];
+    }
+  }
+  pr->pending = 0;
+}
+
+}  // namespace pfc
+
+using namespace pfc;
+
+extern "C" {
+
+void pfc_default_params(pfc_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->nu1 = 2;
+  p->nu2 = 2;
+  p->tol = 1e-9;
+  p->max_cycles = 50;
+  p->precision = PFC_FP64;
+  p->smoother = PFC_NEWTON;
+  p->coarsest = 2;
+  p->inner_cycles = 1;
+}
+
+size_t pfc_workspace_bytes(const pfc_params* p) {
+  if (validate(p) != PFC_OK) return 0;
+  return carve(nullptr, p, nullptr);
+}
+
+const char* pfc_last_error(void) { return g_last_error; }
+
+int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
+             size_t workspace_bytes, const double* any_phi0, const double* any_phi1,
+             void* stream) {
+  if (!out || !d_workspace || !any_phi0) return PFC_EINVAL;
+  *out = nullptr;
+  int v = validate(p);
+  if (v) return v;
+  if (((uintptr_t)d_workspace) % kAlign) return PFC_EINVAL;
+  cudaPointerAttributes attr;
+  cudaError_t e = cudaPointerGetAttributes(&attr, d_workspace);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(workspace)");
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return PFC_EINVAL;
+  const size_t need = carve(nullptr, p, nullptr);
+  if (workspace_bytes < need) return PFC_ESIZE;
+  pfc_ctx* c = (pfc_ctx*)calloc(1, sizeof(pfc_ctx));
+  if (!c) return PFC_EINVAL;
+  c->p = *p;
+  c->st = (cudaStream_t)stream;
+  carve(c, p, (char*)d_workspace);
+  double h = p->L / p->n;
+  for (int l = 0; l < c->nl; ++l) {
+    c->lev[l].n = c->sizes[l];
+    c->lev[l].L = make_lvl(c->sizes[l], h, p->eps, p->dt);
+    h *= 2.0;
+  }
+  e = cudaHostAlloc((void**)&c->hout, kReduceComps * sizeof(double), cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    free(c);
+    return cuda_fail(e, "cudaHostAlloc");
+  }
+  c->ic = 0;
+  c->ib = 1;
+  c->ia = 2;
+  const size_t bytes = (size_t)p->n * p->n * p->n * sizeof(double);
+  int rc = pfc_set_state(c, any_phi1 ? any_phi1 : any_phi0, any_phi1 ? any_phi0 : nullptr);
+  if (rc == PFC_OK) {
+    e = cudaMemsetAsync(c->mu, 0, bytes, c->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->om, 0, bytes, c->st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemsetAsync");
+  }
+  if (rc) {
+    pfc_destroy(c);
+    return rc;
+  }
+  c->step = any_phi1 ? 1 : 0;
+  *out = c;
+  return PFC_OK;
+}
+
+int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev) {
+  if (!c || !any_phi) return PFC_EINVAL;
+  const size_t bytes = (size_t)c->p.n * c->p.n * c->p.n * sizeof(double);
+  PFC_CUDA(cudaMemcpyAsync(c->ring[c->ib], any_phi, bytes, cudaMemcpyDefault, c->st));
+  PFC_CUDA(cudaMemcpyAsync(c->ring[c->ic], any_phi_prev ? any_phi_prev : any_phi, bytes,
+                           cudaMemcpyDefault, c->st));
+  return PFC_OK;
+}
+
+int pfc_step(pfc_ctx* c, int nsteps, pfc_step_stats* stats) {
+  if (!c || nsteps < 0) return PFC_EINVAL;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = step_once(c, stats);
+    if (rc) return rc;
+  }
+  return PFC_OK;
+}
+
+static int copy_field(pfc_ctx* c, const double* src, double* dst) {
+  if (!c || !dst) return PFC_EINVAL;
+  const size_t bytes = (size_t)c->p.n * c->p.n * c->p.n * sizeof(double);
+  PFC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->st));
+  return PFC_OK;
+}
+
+int pfc_get_phi(pfc_ctx* c, double* any_dst) {
+  return c ? copy_field(c, c->ring[c->ib], any_dst) : PFC_EINVAL;
+}
+int pfc_get_mu(pfc_ctx* c, double* any_dst) {
+  return c ? copy_field(c, c->mu, any_dst) : PFC_EINVAL;
+}
+int pfc_get_omega(pfc_ctx* c, double* any_dst) {
+  return c ? copy_field(c, c->om, any_dst) : PFC_EINVAL;
+}
+
+static int diagnostics(int n, double h, double eps, const double* a, const double* b,
+                       double* partials, double* dout, double* hout, cudaStream_t st,
+                       double* res) {
+  PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
+  PFC_CUDA(cudaMemcpyAsync(hout, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  const double h3 = h * h * h;
+  const double F = 0.25 * h3 * hout[0] + 0.5 * (1.0 - eps) * h3 * hout[1] - h * hout[2] +
+                   0.5 * hout[3] / h;
+  res[0] = F;
+  res[1] = F + 0.5 * h * hout[4];
+  res[2] = h3 * hout[5];
+  res[3] = h * hout[2];
+  return PFC_OK;
+}
+
+int pfc_diagnostics(pfc_ctx* c, double out[4]) {
+  if (!c || !out) return PFC_EINVAL;
+  c->prof.launches += 2;
+  return diagnostics(c->p.n, c->p.L / c->p.n, c->p.eps, c->ring[c->ib], c->ring[c->ic],
+                     c->partials, c->dout, c->hout, c->st, out);
+}
+
+int pfc_energy(pfc_ctx* c, double* F, double* F_modified) {
+  double r[4];
+  int rc = pfc_diagnostics(c, r);
+  if (rc) return rc;
+  if (F) *F = r[0];
+  if (F_modified) *F_modified = r[1];
+  return PFC_OK;
+}
+
+int pfc_mass(pfc_ctx* c, double* mass) {
+  if (!mass) return PFC_EINVAL;
+  double r[4];
+  int rc = pfc_diagnostics(c, r);
+  if (rc) return rc;
+  *mass = r[2];
+  return PFC_OK;
+}
+
+long long pfc_launch_count(const pfc_ctx* c) { return c ? c->prof.launches : -1; }
+
+int pfc_step_index(const pfc_ctx* c) { return c ? c->step : -1; }
+
+int pfc_profile_enable(pfc_ctx* c, unsigned mask) {
+  if (!c) return PFC_EINVAL;
+  Prof& pr = c->prof;
+  PFC_CUDA(cudaStreamSynchronize(c->st));
+  prof_harvest(&pr);
+  if (mask && !pr.created) {
+    for (int i = 0; i < 2 * Prof::kPool; ++i) PFC_CUDA(cudaEventCreate(&pr.ev[i]));
+    pr.created = true;
+  }
+  pr.mask = mask;
+  memset(pr.ms, 0, sizeof(pr.ms));
+  memset(pr.cnt, 0, sizeof(pr.cnt));
+  return PFC_OK;
+}
+
+int pfc_profile_read(pfc_ctx* c, int kclass, int level, long long* launches, double* ms) {
+  if (!c || kclass < 0 || kclass >= PFC_K_COUNT || level < 0 || level >= PFC_PROFILE_LEVELS)
+    return PFC_EINVAL;
+  PFC_CUDA(cudaStreamSynchronize(c->st));
+  prof_harvest(&c->prof);
+  if (launches) *launches = c->prof.cnt[kclass][level];
+  if (ms) *ms = c->prof.ms[kclass][level];
+  return PFC_OK;
+}
+
+void pfc_destroy(pfc_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  if (c->hout) cudaFreeHost(c->hout);
+  if (c->prof.created)
+    for (int i = 0; i < 2 * Prof::kPool; ++i) cudaEventDestroy(c->prof.ev[i]);
+  free(c);
+}
+
+const char* pfc_strerror(int code) {
+  switch (code) {
+    case PFC_OK: return "ok";
+    case PFC_EINVAL: return "invalid argument";
+    case PFC_ESIZE: return "grid size not supported or workspace too small";
+    case PFC_ENOCONV: return "multigrid did not reach the tolerance within max_cycles";
+    case PFC_ENAN: return "residual is NaN or Inf";
+    case PFC_ECUDA: return "CUDA runtime error";
+    default: return "unknown error";
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Primitive operations
+// ---------------------------------------------------------------------------
+
+int pfc_op_source(int n, double h, double eps, const double* b, const double* c,
+                  double* S2, double* S3, void* stream) {
+  if (n < 2 || !b || !c || !S2 || !S3 || !(h > 0)) return PFC_EINVAL;
+  PFC_CUDA(launch_source(make_lvl(n, h, eps, 0.0), b, c, S2, S3, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_smooth(int n, double h, double eps, double tau, int smoother, int sweeps,
+                  double* phi, double* mu, double* om, const double* S1, const double* S2,
+                  const double* S3, const double* b, void* stream) {
+  if (n < 2 || (n & 1) || sweeps < 0 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b)
+    return PFC_EINVAL;
+  if (smoother != PFC_NEWTON && smoother != PFC_PICARD) return PFC_EINVAL;
+  PFC_CUDA(launch_smooth(make_lvl(n, h, eps, tau), smoother, sweeps, phi, mu, om, S1, S2,
+                         S3, b, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_residual(int n, double h, double eps, double tau, const double* phi,
+                    const double* mu, const double* om, const double* S1, const double* S2,
+                    const double* S3, const double* b, double* r1, double* r2, double* r3,
+                    void* stream) {
+  if (n < 2 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 || !r2 || !r3)
+    return PFC_EINVAL;
+  PFC_CUDA(launch_residual(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b, r1, r2, r3,
+                           (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_residual_restrict(int n, double h, double eps, double tau, const double* phi,
+                             const double* mu, const double* om, const double* S1,
+                             const double* S2, const double* S3, const double* b,
+                             double* rc1, double* rc2, double* rc3, double* uc1,
+                             double* uc2, double* uc3, void* stream) {
+  if (n < 2 || (n & 1) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !rc1 || !rc2 ||
+      !rc3 || !uc1 || !uc2 || !uc3)
+    return PFC_EINVAL;
+  PFC_CUDA(launch_residual_restrict(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b,
+                                    rc1, rc2, rc3, uc1, uc2, uc3, nullptr, nullptr,
+                                    nullptr, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_restrict(int n, const double* fine, double* coarse, void* stream) {
+  if (n < 2 || (n & 1) || !fine || !coarse) return PFC_EINVAL;
+  PFC_CUDA(launch_restrict(n, fine, coarse, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_coarse_source(int n, double h, double eps, double tau, const double* uc1,
+                         const double* uc2, const double* uc3, const double* bc,
+                         double* r1, double* r2, double* r3, void* stream) {
+  if (n < 1 || !uc1 || !uc2 || !uc3 || !bc || !r1 || !r2 || !r3) return PFC_EINVAL;
+  PFC_CUDA(launch_coarse_source(make_lvl(n, h, eps, tau), uc1, uc2, uc3, bc, r1, r2, r3,
+                                (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_prolong_correct(int n, const double* vc1, const double* vc2, const double* vc3,
+                           const double* wc1, const double* wc2, const double* wc3,
+                           double* u1, double* u2, double* u3, void* stream) {
+  if (n < 2 || (n & 1) || !vc1 || !vc2 || !vc3 || !wc1 || !wc2 || !wc3 || !u1 || !u2 || !u3)
+    return PFC_EINVAL;
+  // e = v - w is formed in place over w, then interpolated and added.
+  cudaStream_t st = (cudaStream_t)stream;
+  PFC_CUDA(launch_coarse_diff(n / 2, vc1, vc2, vc3, (double*)wc1, (double*)wc2,
+                              (double*)wc3, st));
+  PFC_CUDA(launch_prolong_add(n, wc1, wc2, wc3, u1, u2, u3, st));
+  return PFC_OK;
+}
+
+int pfc_op_coarse_solve(int n, double h, double eps, double tau, int smoother,
+                        int max_sweeps, double* phi, double* mu, double* om,
+                        const double* S1, const double* S2, const double* S3,
+                        const double* b, void* stream) {
+  if (n < 2 || (n & 1) || n > 16 || max_sweeps < 1 || !phi || !mu || !om || !S1 || !S2 ||
+      !S3 || !b)
+    return PFC_EINVAL;
+  if (smoother != PFC_NEWTON && smoother != PFC_PICARD) return PFC_EINVAL;
+  PFC_CUDA(launch_coarse_solve(make_lvl(n, h, eps, tau), smoother, max_sweeps, phi, mu, om,
+                               S1, S2, S3, b, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+size_t pfc_reduce_scratch_bytes(int n) {
+  (void)n;
+  return ((size_t)kReduceBlocks * kReduceComps + kReduceComps) * sizeof(double);
+}
+
+int pfc_op_diagnostics(int n, double h, double eps, const double* a, const double* b,
+                       void* scratch, double* out, void* stream) {
+  if (n < 2 || !a || !b || !scratch || !out || !(h > 0)) return PFC_EINVAL;
+  double* partials = (double*)scratch;
+  double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
+  double hout[8];
+  cudaStream_t st = (cudaStream_t)stream;
+  PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
+  PFC_CUDA(cudaMemcpyAsync(hout, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  const double h3 = h * h * h;
+  const double F = 0.25 * h3 * hout[0] + 0.5 * (1.0 - eps) * h3 * hout[1] - h * hout[2] +
+                   0.5 * hout[3] / h;
+  out[0] = F;
+  out[1] = F + 0.5 * h * hout[4];
+  out[2] = h3 * hout[5];
+  out[3] = h * hout[2];
+  return PFC_OK;
+}
+
+int pfc_op_residual_norm(int n, double h, double eps, double tau, const double* phi,
+                         const double* mu, const double* om, const double* S1,
+                         const double* S2, const double* S3, const double* b,
+                         void* scratch, double* out, void* stream) {
+  if (n < 2 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !scratch || !out)
+    return PFC_EINVAL;
+  double* partials = (double*)scratch;
+  double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
+  double hv = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  PFC_CUDA(launch_residual_norm2(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b,
+                                 partials, dout, st));
+  PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  *out = sqrt(hv / (3.0 * (double)n * n * n));
+  return PFC_OK;
+}
+
+int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
+                  const double* mu, const double* om, const double* S1, const double* S2,
+                  const double* S3, const double* b, float* r1, float* r2, float* r3,
+                  float* q, void* scratch, double* out, void* stream) {
+  if (n < 2 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 || !r2 || !r3 || !q ||
+      !scratch || !out)
+    return PFC_EINVAL;
+  double* partials = (double*)scratch;
+  double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
+  double hv = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  PFC_CUDA(launch_residual64_to32(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b, r1,
+                                  r2, r3, q, partials, dout, st));
+  PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  *out = sqrt(hv / (3.0 * (double)n * n * n));
+  return PFC_OK;
+}
+
+int pfc_op_lin_smooth(int n, double h, double eps, double tau, int sweeps, int zero_init,
+                      float* d1, float* d2, float* d3, const float* r1, const float* r2,
+                      const float* r3, const float* q, void* stream) {
+  if (n < 2 || (n & 1) || sweeps < 0 || !d1 || !d2 || !d3 || !r1 || !r2 || !r3 || !q)
+    return PFC_EINVAL;
+  PFC_CUDA(launch_lin_smooth32(make_lvl(n, h, eps, tau), sweeps, zero_init != 0, d1, d2, d3,
+                               r1, r2, r3, q, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_correct(int n, double* u1, double* u2, double* u3, const float* d1,
+                   const float* d2, const float* d3, void* stream) {
+  if (n < 1 || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;
+  PFC_CUDA(launch_correct64(n, u1, u2, u3, d1, d2, d3, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,177 @@
+// Device-side building blocks of the PFC multigrid kernels: level constants,
+// periodic 7-point stencil addressing, the pointwise 3x3 solve of the
+// red-black smoother (Section 5) and the residual r = S - N(u) of Eqs. 5.4-5.10.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pfc.h"
+
+namespace pfc {
+
+// Constants of one multigrid level (spacing h, shared eps and tau).
+struct Lvl {
+  int n;        // cells per side
+  double g;     // 1/h^2
+  double tg;    // tau/h^2
+  double kap;   // 6 tau/h^2   (tau/h^2 times the six unit face mobilities)
+  double g6;    // 6/h^2
+  double g3;    // 3/h^2
+  double gh;    // 1/(2 h^2)
+  double Q0;    // 18/h^4      (the 6/h^2 * 3/h^2 coupling of rows 2 and 3)
+  double c1;    // (1 - eps)/2
+};
+
+inline Lvl make_lvl(int n, double h, double eps, double tau) {
+  Lvl L;
+  double g = 1.0 / (h * h);
+  L.n = n;
+  L.g = g;
+  L.tg = tau * g;
+  L.kap = 6.0 * tau * g;
+  L.g6 = 6.0 * g;
+  L.g3 = 3.0 * g;
+  L.gh = 0.5 * g;
+  L.Q0 = 18.0 * g * g;
+  L.c1 = 0.5 * (1.0 - eps);
+  return L;
+}
+
+// Linear indices of a cell and its six periodic face neighbours.
+struct Stencil {
+  int64_t c, xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Stencil stencil_at(int i, int j, int k, int n) {
+  const int im = (i == 0) ? n - 1 : i - 1, ip = (i + 1 == n) ? 0 : i + 1;
+  const int jm = (j == 0) ? n - 1 : j - 1, jp = (j + 1 == n) ? 0 : j + 1;
+  const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+  const int64_t nn = (int64_t)n * n;
+  const int64_t row = (int64_t)j * n + (int64_t)k * nn;
+  Stencil s;
+  s.c = row + i;
+  s.xm = row + im;
+  s.xp = row + ip;
+  s.ym = (int64_t)jm * n + (int64_t)k * nn + i;
+  s.yp = (int64_t)jp * n + (int64_t)k * nn + i;
+  s.zm = (int64_t)j * n + (int64_t)km * nn + i;
+  s.zp = (int64_t)j * n + (int64_t)kp * nn + i;
+  return s;
+}
+
+template <class T>
+__device__ __forceinline__ T nbsum(const T* __restrict__ v, const Stencil& s) {
+  return ((__ldg(v + s.xm) + __ldg(v + s.xp)) + (__ldg(v + s.ym) + __ldg(v + s.yp))) +
+         (__ldg(v + s.zm) + __ldg(v + s.zp));
+}
+
+// Neighbour sum through plain (coherent) loads, for arrays written earlier in
+// the same kernel by other threads of the block.
+template <class T>
+__device__ __forceinline__ T nbsum_coherent(const T* v, const Stencil& s) {
+  return ((v[s.xm] + v[s.xp]) + (v[s.ym] + v[s.yp])) + (v[s.zm] + v[s.zp]);
+}
+
+// Cubic term f(a) = (a+b)(a^2+b^2)/4 of Eq. 5.2 and its derivative in a.
+__device__ __forceinline__ double cubic_f(double a, double b) {
+  return 0.25 * (a + b) * fma(a, a, b * b);
+}
+__device__ __forceinline__ double cubic_fp(double a, double b) {
+  return fma(0.75 * a, a, fma(0.5 * a, b, 0.25 * b * b));
+}
+
+// Pointwise solve of the smoother's 3x3 system (Section 5)
+//   [ 1      kap   0   ] [phi]   [st1 = S1 + tau/h^2 sum mu_nb   ]
+//   [ -q     1     6g  ] [mu ] = [st2 = S2 + extra + g sum om_nb ]
+//   [ 3g     0     1   ] [om ]   [st3 = S3 + g/2 sum phi_nb      ]
+// by eliminating phi and om: mu = (st2 - 6g st3 + (q + 18 g^2) st1) / det,
+// det = 1 + kap (q + 18 g^2) >= 1 because q > 0.  The Newton variant uses
+// q = f'(phi_n) + (1-eps)/2, extra = f(phi_n) - f'(phi_n) phi_n; the paper's
+// Picard variant q = (phi_n^2 + b^2)/4 + (1-eps)/2, extra = (phi_n^2+b^2) b/4.
+template <int LIN>
+__device__ __forceinline__ void point_solve(const Lvl& L, double sphi, double smu,
+                                            double som, double phin, double b,
+                                            double s1, double s2, double s3,
+                                            double& phi, double& mu, double& om) {
+  const double st1 = fma(L.tg, smu, s1);
+  const double st3 = fma(L.gh, sphi, s3);
+  double q, extra;
+  if (LIN == PFC_NEWTON) {
+    const double fp = cubic_fp(phin, b);
+    q = fp + L.c1;
+    extra = fma(-fp, phin, cubic_f(phin, b));
+  } else {
+    const double p = 0.25 * fma(phin, phin, b * b);
+    q = p + L.c1;
+    extra = p * b;
+  }
+  const double st2 = fma(L.g, som, s2 + extra);
+  const double Q = q + L.Q0;
+  const double det = fma(L.kap, Q, 1.0);
+  mu = fma(Q, st1, fma(-L.g6, st3, st2)) / det;
+  phi = fma(-L.kap, mu, st1);
+  om = fma(-L.g3, phi, st3);
+}
+
+// r = S - N(u) at one cell (Eqs. 5.4-5.6 with M = 1).
+__device__ __forceinline__ void residual_at(const Lvl& L, const Stencil& s,
+                                            const double* __restrict__ phi,
+                                            const double* __restrict__ mu,
+                                            const double* __restrict__ om,
+                                            const double* __restrict__ S1,
+                                            const double* __restrict__ S2,
+                                            const double* __restrict__ S3,
+                                            const double* __restrict__ b,
+                                            double& r1, double& r2, double& r3) {
+  const double p = __ldg(phi + s.c), m = __ldg(mu + s.c), w = __ldg(om + s.c);
+  const double bb = __ldg(b + s.c);
+  const double lmu = fma(-6.0, m, nbsum(mu, s));
+  const double lom = fma(-6.0, w, nbsum(om, s));
+  const double lphi = fma(-6.0, p, nbsum(phi, s));
+  // N1 = phi - tau Lap mu ; N2 = mu - f - c1 phi - Lap om ; N3 = om - Lap phi / 2
+  r1 = __ldg(S1 + s.c) - fma(-L.tg, lmu, p);
+  r2 = __ldg(S2 + s.c) - (fma(-L.c1, p, m - cubic_f(p, bb)) - L.g * lom);
+  r3 = __ldg(S3 + s.c) - fma(-L.gh, lphi, w);
+}
+
+// N(u) at one cell (no source), coherent loads.
+__device__ __forceinline__ void operator_at(const Lvl& L, const Stencil& s,
+                                            const double* phi, const double* mu,
+                                            const double* om, const double* b,
+                                            double& n1, double& n2, double& n3) {
+  const double p = phi[s.c], m = mu[s.c], w = om[s.c], bb = b[s.c];
+  const double lmu = fma(-6.0, m, nbsum_coherent(mu, s));
+  const double lom = fma(-6.0, w, nbsum_coherent(om, s));
+  const double lphi = fma(-6.0, p, nbsum_coherent(phi, s));
+  n1 = fma(-L.tg, lmu, p);
+  n2 = fma(-L.c1, p, m - cubic_f(p, bb)) - L.g * lom;
+  n3 = fma(-L.gh, lphi, w);
+}
+
+// Block-wide sum of NV doubles into thread 0 (fixed order: deterministic).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* 32*NV */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    double x = v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) smem[c * 32 + wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      double x = (lane < nw) ? smem[c * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+      v[c] = x;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace pfc

@@ -1,0 +1,475 @@
+// FP64 kernels of one FAS V-cycle (Algorithm 1) for the split PFC system
+// (Eqs. 5.4-5.10, M = 1) and the Section 2 diagnostics.
+//
+// Layout: every field is n^3 doubles, x fastest (cell (i,j,k) at i + n(j + nk)),
+// one array per component (phi, mu, omega), so warps load contiguous x-runs.
+#include "pfc_internal.h"
+
+namespace pfc {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t work, int threads = kThreads) {
+  return (unsigned)((work + threads - 1) / threads);
+}
+
+__device__ __forceinline__ void cell_of(int64_t t, int n, int& i, int& j, int& k) {
+  i = (int)(t % n);
+  const int64_t r = t / n;
+  j = (int)(r % n);
+  k = (int)(r / n);
+}
+
+// ---------------------------------------------------------------------------
+// a1: source S2 = (1-eps)/2 b + 3 Lap b - Lap c, S3 = Lap b / 2 (Eqs. 5.9-5.10)
+// ---------------------------------------------------------------------------
+__global__ void k_source(Lvl L, const double* __restrict__ b, const double* __restrict__ c,
+                         double* __restrict__ S2, double* __restrict__ S3) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  const double bb = __ldg(b + s.c);
+  const double lb = L.g * fma(-6.0, bb, nbsum(b, s));
+  const double lc = L.g * fma(-6.0, __ldg(c + s.c), nbsum(c, s));
+  S2[s.c] = fma(3.0, lb, fma(L.c1, bb, -lc));
+  S3[s.c] = 0.5 * lb;
+}
+
+// ---------------------------------------------------------------------------
+// a2/a7: one colour of the red-black nonlinear Gauss-Seidel sweep (Section 5).
+// Thread t owns the t-th cell of the colour: i = 2p + ((j+k+colour) & 1).
+// Its six neighbours have the other colour and are not written here.
+// ---------------------------------------------------------------------------
+template <int LIN>
+__global__ void k_smooth_colour(Lvl L, int colour, double* phi, double* mu, double* om,
+                                const double* __restrict__ S1,
+                                const double* __restrict__ S2,
+                                const double* __restrict__ S3,
+                                const double* __restrict__ b) {
+  const int n = L.n, half = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)half * n * n) return;
+  const int p = (int)(t % half);
+  const int64_t r = t / half;
+  const int j = (int)(r % n), k = (int)(r / n);
+  const int i = 2 * p + ((j + k + colour) & 1);
+  const Stencil s = stencil_at(i, j, k, n);
+  double np, nm, nw;
+  point_solve<LIN>(L, nbsum(phi, s), nbsum(mu, s), nbsum(om, s), phi[s.c], __ldg(b + s.c),
+                   __ldg(S1 + s.c), __ldg(S2 + s.c), __ldg(S3 + s.c), np, nm, nw);
+  phi[s.c] = np;
+  mu[s.c] = nm;
+  om[s.c] = nw;
+}
+
+// ---------------------------------------------------------------------------
+// a3: residual r = S - N(u), full fields (used by the primitive op)
+// ---------------------------------------------------------------------------
+__global__ void k_residual(Lvl L, const double* __restrict__ phi,
+                           const double* __restrict__ mu, const double* __restrict__ om,
+                           const double* __restrict__ S1, const double* __restrict__ S2,
+                           const double* __restrict__ S3, const double* __restrict__ b,
+                           double* __restrict__ r1, double* __restrict__ r2,
+                           double* __restrict__ r3) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  double a, c, d;
+  residual_at(L, s, phi, mu, om, S1, S2, S3, b, a, c, d);
+  r1[s.c] = a;
+  r2[s.c] = c;
+  r3[s.c] = d;
+}
+
+// ---------------------------------------------------------------------------
+// a3: fused residual + 8-cell restriction of r and u; one thread per coarse
+// cell.  Optionally also stores the restricted u a second time (wc), which the
+// correction step needs after the coarse level has overwritten uc.
+// ---------------------------------------------------------------------------
+__global__ void k_residual_restrict(Lvl L, const double* __restrict__ phi,
+                                    const double* __restrict__ mu,
+                                    const double* __restrict__ om,
+                                    const double* __restrict__ S1,
+                                    const double* __restrict__ S2,
+                                    const double* __restrict__ S3,
+                                    const double* __restrict__ b, double* __restrict__ rc1,
+                                    double* __restrict__ rc2, double* __restrict__ rc3,
+                                    double* __restrict__ uc1, double* __restrict__ uc2,
+                                    double* __restrict__ uc3, double* __restrict__ wc1,
+                                    double* __restrict__ wc2, double* __restrict__ wc3) {
+  const int n = L.n, nc = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nc * nc * nc) return;
+  int I, J, K;
+  cell_of(t, nc, I, J, K);
+  double a1 = 0, a2 = 0, a3 = 0, v1 = 0, v2 = 0, v3 = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+    const Stencil s = stencil_at(i, j, k, n);
+    double x, y, z;
+    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
+    a1 += x;
+    a2 += y;
+    a3 += z;
+    v1 += __ldg(phi + s.c);
+    v2 += __ldg(mu + s.c);
+    v3 += __ldg(om + s.c);
+  }
+  rc1[t] = 0.125 * a1;
+  rc2[t] = 0.125 * a2;
+  rc3[t] = 0.125 * a3;
+  uc1[t] = 0.125 * v1;
+  uc2[t] = 0.125 * v2;
+  uc3[t] = 0.125 * v3;
+  if (wc1) {
+    wc1[t] = 0.125 * v1;
+    wc2[t] = 0.125 * v2;
+    wc3[t] = 0.125 * v3;
+  }
+}
+
+__global__ void k_restrict(int n, const double* __restrict__ f, double* __restrict__ c) {
+  const int nc = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nc * nc * nc) return;
+  int I, J, K;
+  cell_of(t, nc, I, J, K);
+  double acc = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t i = 2 * I + (q & 1), j = 2 * J + ((q >> 1) & 1), k = 2 * K + (q >> 2);
+    acc += __ldg(f + i + n * (j + (int64_t)n * k));
+  }
+  c[t] = 0.125 * acc;
+}
+
+// ---------------------------------------------------------------------------
+// a4: FAS coarse source S_c = N_c(u_c) + r_c, in place over r_c
+// ---------------------------------------------------------------------------
+__global__ void k_coarse_source(Lvl L, const double* __restrict__ u1,
+                                const double* __restrict__ u2,
+                                const double* __restrict__ u3,
+                                const double* __restrict__ bc, double* r1, double* r2,
+                                double* r3) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  double x, y, z;
+  operator_at(L, s, u1, u2, u3, bc, x, y, z);
+  r1[s.c] += x;
+  r2[s.c] += y;
+  r3[s.c] += z;
+}
+
+__global__ void k_coarse_diff(int64_t cells, const double* __restrict__ v1,
+                              const double* __restrict__ v2,
+                              const double* __restrict__ v3, double* w1, double* w2,
+                              double* w3) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  w1[t] = v1[t] - w1[t];
+  w2[t] = v2[t] - w2[t];
+  w3[t] = v3[t] - w3[t];
+}
+
+// ---------------------------------------------------------------------------
+// a6: u += P e, P trilinear cell-centred: fine cell 2I+a takes 3/4 of coarse I
+// and 1/4 of coarse I+(a ? 1 : -1) per axis, i.e. weights 27, 9, 3, 1 (/64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double interp8(const double* __restrict__ e, int64_t o000,
+                                          int64_t o100, int64_t o010, int64_t o001,
+                                          int64_t o110, int64_t o101, int64_t o011,
+                                          int64_t o111) {
+  const double g2 = (__ldg(e + o100) + __ldg(e + o010)) + __ldg(e + o001);
+  const double g3 = (__ldg(e + o110) + __ldg(e + o101)) + __ldg(e + o011);
+  double acc = fma(3.0, g3, __ldg(e + o111));
+  acc = fma(9.0, g2, acc);
+  acc = fma(27.0, __ldg(e + o000), acc);
+  return acc;
+}
+
+__global__ void k_prolong_add(int n, const double* __restrict__ e1,
+                              const double* __restrict__ e2,
+                              const double* __restrict__ e3, double* __restrict__ u1,
+                              double* __restrict__ u2, double* __restrict__ u3) {
+  const int nc = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  int I2 = (i & 1) ? I + 1 : I - 1;
+  int J2 = (j & 1) ? J + 1 : J - 1;
+  int K2 = (k & 1) ? K + 1 : K - 1;
+  I2 = (I2 + nc) % nc;
+  J2 = (J2 + nc) % nc;
+  K2 = (K2 + nc) % nc;
+  const int64_t nn = (int64_t)nc * nc;
+  const int64_t zK = K * nn, zK2 = K2 * nn, yJ = (int64_t)J * nc, yJ2 = (int64_t)J2 * nc;
+  const int64_t o000 = I + yJ + zK, o100 = I2 + yJ + zK, o010 = I + yJ2 + zK,
+                o001 = I + yJ + zK2, o110 = I2 + yJ2 + zK, o101 = I2 + yJ + zK2,
+                o011 = I + yJ2 + zK2, o111 = I2 + yJ2 + zK2;
+  const double w = 1.0 / 64.0;
+  u1[t] = fma(w, interp8(e1, o000, o100, o010, o001, o110, o101, o011, o111), u1[t]);
+  u2[t] = fma(w, interp8(e2, o000, o100, o010, o001, o110, o101, o011, o111), u2[t]);
+  u3[t] = fma(w, interp8(e3, o000, o100, o010, o001, o110, o101, o011, o111), u3[t]);
+}
+
+// ---------------------------------------------------------------------------
+// a5: coarsest level: red-black sweeps in one thread block until the largest
+// relative change falls below 1e-14 or max_sweeps.  Neighbours are read with
+// coherent loads because this block wrote them in the previous half-sweep.
+// ---------------------------------------------------------------------------
+template <int LIN>
+__global__ void k_coarse_solve(Lvl L, int max_sweeps, double* phi, double* mu, double* om,
+                               const double* S1, const double* S2, const double* S3,
+                               const double* b) {
+  __shared__ double red[32];
+  __shared__ int done;
+  const int n = L.n, half = n >> 1;
+  const int cells = half * n * n;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double change = 0.0;
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        const int p = t % half, r = t / half;
+        const int j = r % n, k = r / n;
+        const int i = 2 * p + ((j + k + colour) & 1);
+        const Stencil s = stencil_at(i, j, k, n);
+        const double op = phi[s.c], om_ = mu[s.c], ow = om[s.c];
+        double np, nm, nw;
+        point_solve<LIN>(L, nbsum_coherent(phi, s), nbsum_coherent(mu, s),
+                         nbsum_coherent(om, s), op, b[s.c], S1[s.c], S2[s.c], S3[s.c],
+                         np, nm, nw);
+        phi[s.c] = np;
+        mu[s.c] = nm;
+        om[s.c] = nw;
+        change = fmax(change, fabs(np - op) / (1.0 + fabs(np)));
+        change = fmax(change, fabs(nm - om_) / (1.0 + fabs(nm)));
+        change = fmax(change, fabs(nw - ow) / (1.0 + fabs(nw)));
+      }
+      __syncthreads();
+    }
+    // block max of the change
+    for (int o = 16; o > 0; o >>= 1) change = fmax(change, __shfl_down_sync(0xffffffffu, change, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = change;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = fmax(m, red[w]);
+      done = (m < 1e-14);
+    }
+    __syncthreads();
+    if (done) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions (deterministic: fixed grid, fixed per-thread order, fixed tree)
+// ---------------------------------------------------------------------------
+__global__ void k_residual_norm2(Lvl L, const double* __restrict__ phi,
+                                 const double* __restrict__ mu,
+                                 const double* __restrict__ om,
+                                 const double* __restrict__ S1,
+                                 const double* __restrict__ S2,
+                                 const double* __restrict__ S3,
+                                 const double* __restrict__ b, double* partials) {
+  __shared__ double sm[32];
+  const int n = L.n;
+  const int64_t cells = (int64_t)n * n * n;
+  double acc[1] = {0.0};
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(t, n, i, j, k);
+    const Stencil s = stencil_at(i, j, k, n);
+    double x, y, z;
+    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
+    acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
+  }
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+template <int NV>
+__global__ void k_reduce_final(const double* __restrict__ partials, int nparts,
+                               double* out) {
+  __shared__ double sm[32 * NV];
+  double acc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] += partials[(int64_t)p * NV + c];
+  }
+  block_sum<NV>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) out[c] = acc[c];
+  }
+}
+
+// Raw per-cell sums for F_h (Eq. 2.1), the modified energy and the mass.
+__global__ void k_diagnostics(int n, const double* __restrict__ a,
+                              const double* __restrict__ b, double* partials) {
+  __shared__ double sm[32 * 6];
+  const int64_t cells = (int64_t)n * n * n;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(t, n, i, j, k);
+    const Stencil s = stencil_at(i, j, k, n);
+    const double x = __ldg(a + s.c);
+    const double dx = __ldg(a + s.xp) - x, dy = __ldg(a + s.yp) - x,
+                 dz = __ldg(a + s.zp) - x;
+    const double lap = fma(-6.0, x, nbsum(a, s));
+    const double y = x - __ldg(b + s.c);
+    const double ex = (__ldg(a + s.xp) - __ldg(b + s.xp)) - y;
+    const double ey = (__ldg(a + s.yp) - __ldg(b + s.yp)) - y;
+    const double ez = (__ldg(a + s.zp) - __ldg(b + s.zp)) - y;
+    const double x2 = x * x;
+    acc[0] = fma(x2, x2, acc[0]);
+    acc[1] += x2;
+    acc[2] = fma(dx, dx, fma(dy, dy, fma(dz, dz, acc[2])));
+    acc[3] = fma(lap, lap, acc[3]);
+    acc[4] = fma(ex, ex, fma(ey, ey, fma(ez, ez, acc[4])));
+    acc[5] += x;
+  }
+  block_sum<6>(acc, sm);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 6; ++c) partials[(int64_t)blockIdx.x * 6 + c] = acc[c];
+  }
+}
+
+inline int reduce_blocks(int64_t cells) {
+  const int64_t nb = (cells + kReduceThreads - 1) / kReduceThreads;
+  return (int)(nb < kReduceBlocks ? nb : kReduceBlocks);
+}
+
+}  // namespace
+
+cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double* S2,
+                          double* S3, cudaStream_t st) {
+  const int64_t cells = (int64_t)L.n * L.n * L.n;
+  k_source<<<grid_for(cells), kThreads, 0, st>>>(L, b, c, S2, S3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_smooth(const Lvl& L, int lin, int sweeps, double* phi, double* mu,
+                          double* om, const double* S1, const double* S2,
+                          const double* S3, const double* b, cudaStream_t st) {
+  const int64_t work = (int64_t)(L.n / 2) * L.n * L.n;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour) {
+      if (lin == PFC_NEWTON)
+        k_smooth_colour<PFC_NEWTON><<<grid_for(work), kThreads, 0, st>>>(
+            L, colour, phi, mu, om, S1, S2, S3, b);
+      else
+        k_smooth_colour<PFC_PICARD><<<grid_for(work), kThreads, 0, st>>>(
+            L, colour, phi, mu, om, S1, S2, S3, b);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const Lvl& L, const double* phi, const double* mu,
+                            const double* om, const double* S1, const double* S2,
+                            const double* S3, const double* b, double* r1, double* r2,
+                            double* r3, cudaStream_t st) {
+  const int64_t cells = (int64_t)L.n * L.n * L.n;
+  k_residual<<<grid_for(cells), kThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1, r2,
+                                                  r3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_restrict(const Lvl& L, const double* phi, const double* mu,
+                                     const double* om, const double* S1,
+                                     const double* S2, const double* S3, const double* b,
+                                     double* rc1, double* rc2, double* rc3, double* uc1,
+                                     double* uc2, double* uc3, double* wc1, double* wc2,
+                                     double* wc3, cudaStream_t st) {
+  const int nc = L.n / 2;
+  const int64_t work = (int64_t)nc * nc * nc;
+  k_residual_restrict<<<grid_for(work), kThreads, 0, st>>>(
+      L, phi, mu, om, S1, S2, S3, b, rc1, rc2, rc3, uc1, uc2, uc3, wc1, wc2, wc3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(int n, const double* fine, double* coarse, cudaStream_t st) {
+  const int nc = n / 2;
+  const int64_t work = (int64_t)nc * nc * nc;
+  k_restrict<<<grid_for(work), kThreads, 0, st>>>(n, fine, coarse);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_source(const Lvl& Lc, const double* uc1, const double* uc2,
+                                 const double* uc3, const double* bc, double* r1,
+                                 double* r2, double* r3, cudaStream_t st) {
+  const int64_t cells = (int64_t)Lc.n * Lc.n * Lc.n;
+  k_coarse_source<<<grid_for(cells), kThreads, 0, st>>>(Lc, uc1, uc2, uc3, bc, r1, r2, r3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_diff(int nc, const double* v1, const double* v2,
+                               const double* v3, double* w1, double* w2, double* w3,
+                               cudaStream_t st) {
+  const int64_t cells = (int64_t)nc * nc * nc;
+  k_coarse_diff<<<grid_for(cells), kThreads, 0, st>>>(cells, v1, v2, v3, w1, w2, w3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int n, const double* e1, const double* e2,
+                               const double* e3, double* u1, double* u2, double* u3,
+                               cudaStream_t st) {
+  const int64_t cells = (int64_t)n * n * n;
+  k_prolong_add<<<grid_for(cells), kThreads, 0, st>>>(n, e1, e2, e3, u1, u2, u3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve(const Lvl& L, int lin, int max_sweeps, double* phi,
+                                double* mu, double* om, const double* S1,
+                                const double* S2, const double* S3, const double* b,
+                                cudaStream_t st) {
+  const int work = (L.n / 2) * L.n * L.n;
+  int threads = ((work + 31) / 32) * 32;
+  if (threads > 1024) threads = 1024;
+  if (lin == PFC_NEWTON)
+    k_coarse_solve<PFC_NEWTON><<<1, threads, 0, st>>>(L, max_sweeps, phi, mu, om, S1, S2,
+                                                       S3, b);
+  else
+    k_coarse_solve<PFC_PICARD><<<1, threads, 0, st>>>(L, max_sweeps, phi, mu, om, S1, S2,
+                                                       S3, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double* mu,
+                                  const double* om, const double* S1, const double* S2,
+                                  const double* S3, const double* b, double* partials,
+                                  double* out, cudaStream_t st) {
+  const int nb = reduce_blocks((int64_t)L.n * L.n * L.n);
+  k_residual_norm2<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, partials);
+  k_reduce_final<1><<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,
+                               double* out, cudaStream_t st) {
+  const int nb = reduce_blocks((int64_t)n * n * n);
+  k_diagnostics<<<nb, kReduceThreads, 0, st>>>(n, a, b, partials);
+  k_reduce_final<6><<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+}  // namespace pfc

@@ -1,0 +1,79 @@
+// Host-side launchers shared by the C ABI (pfc_api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pfc.h"
+#include "pfc_device.cuh"
+
+namespace pfc {
+
+// Largest number of partial sums a reduction writes (one per block).
+constexpr int kReduceBlocks = 1216;   // 8 * 152 SMs
+constexpr int kReduceThreads = 256;
+constexpr int kReduceComps = 8;       // doubles per block partial
+
+// Event timing of kernel launches per (class, level); see pfc_profile_enable.
+struct Prof {
+  static constexpr int kPool = 1024;
+  unsigned mask = 0;
+  bool created = false;
+  int pending = 0;
+  cudaEvent_t ev[2 * kPool];
+  int cls[kPool], lev[kPool], nlaunch[kPool];
+  double ms[PFC_K_COUNT][PFC_PROFILE_LEVELS];
+  long long cnt[PFC_K_COUNT][PFC_PROFILE_LEVELS];
+  long long launches = 0;   // every kernel launch of the context, timed or not
+};
+// No-ops unless pr is non-null and the class is enabled.
+void prof_begin(Prof* pr, int cls, cudaStream_t st);
+void prof_end(Prof* pr, int cls, int level, int nlaunch, cudaStream_t st);
+// Accumulate the completed brackets (call after the stream has synchronised).
+void prof_harvest(Prof* pr);
+
+// FP64 kernels (pfc_fp64.cu).  All enqueue on `st` and return the launch error.
+cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double* S2,
+                          double* S3, cudaStream_t st);
+cudaError_t launch_smooth(const Lvl& L, int lin, int sweeps, double* phi, double* mu,
+                          double* om, const double* S1, const double* S2,
+                          const double* S3, const double* b, cudaStream_t st);
+cudaError_t launch_residual(const Lvl& L, const double* phi, const double* mu,
+                            const double* om, const double* S1, const double* S2,
+                            const double* S3, const double* b, double* r1, double* r2,
+                            double* r3, cudaStream_t st);
+cudaError_t launch_residual_restrict(const Lvl& L, const double* phi, const double* mu,
+                                     const double* om, const double* S1,
+                                     const double* S2, const double* S3, const double* b,
+                                     double* rc1, double* rc2, double* rc3, double* uc1,
+                                     double* uc2, double* uc3, double* wc1, double* wc2,
+                                     double* wc3, cudaStream_t st);
+cudaError_t launch_restrict(int n, const double* fine, double* coarse, cudaStream_t st);
+cudaError_t launch_coarse_source(const Lvl& Lc, const double* uc1, const double* uc2,
+                                 const double* uc3, const double* bc, double* r1,
+                                 double* r2, double* r3, cudaStream_t st);
+// e_c = v_c - w_c in place over w_c (three coarse fields of size nc^3).
+cudaError_t launch_coarse_diff(int nc, const double* v1, const double* v2,
+                               const double* v3, double* w1, double* w2, double* w3,
+                               cudaStream_t st);
+// u += P e_c for a fine level of size n (e_c on n/2).
+cudaError_t launch_prolong_add(int n, const double* e1, const double* e2,
+                               const double* e3, double* u1, double* u2, double* u3,
+                               cudaStream_t st);
+cudaError_t launch_coarse_solve(const Lvl& L, int lin, int max_sweeps, double* phi,
+                                double* mu, double* om, const double* S1,
+                                const double* S2, const double* S3, const double* b,
+                                cudaStream_t st);
+// Sum over cells of r1^2 + r2^2 + r3^2 -> partials (one per block), then the
+// fixed-order final sum into out[0] (device).
+cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double* mu,
+                                  const double* om, const double* S1, const double* S2,
+                                  const double* S3, const double* b, double* partials,
+                                  double* out, cudaStream_t st);
+// out[0..5] = sum a^4, sum a^2, sum |D a|^2 (faces), sum (Lap a)^2 (times h^4
+// removed: raw stencil sums), sum |D(a-b)|^2, sum a.  Raw sums; the host scales.
+cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,
+                               double* out, cudaStream_t st);
+
+}  // namespace pfc

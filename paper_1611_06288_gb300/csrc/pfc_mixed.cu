@@ -1,0 +1,462 @@
+// Mixed-precision defect correction: FP64 residual and Jacobian coefficient,
+// FP32 linear multigrid for the correction (see pfc_mixed.h).
+#include <math.h>
+
+#include "pfc_internal.h"
+#include "pfc_mixed.h"
+
+namespace pfc {
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned grid_for(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
+
+// FP32 constants of one level of the linearised system.
+struct LvlF {
+  int n;
+  float g, tg, kap, g6, g3, gh, Q0;
+};
+
+inline LvlF to_f32(const Lvl& L) {
+  LvlF f;
+  f.n = L.n;
+  f.g = (float)L.g;
+  f.tg = (float)L.tg;
+  f.kap = (float)L.kap;
+  f.g6 = (float)L.g6;
+  f.g3 = (float)L.g3;
+  f.gh = (float)L.gh;
+  f.Q0 = (float)L.Q0;
+  return f;
+}
+
+__device__ __forceinline__ void cell_of(int64_t t, int n, int& i, int& j, int& k) {
+  i = (int)(t % n);
+  const int64_t r = t / n;
+  j = (int)(r % n);
+  k = (int)(r / n);
+}
+
+// FP64 residual r = S - N(u) -> FP32 copy, q = f'(phi) + (1-eps)/2 -> FP32,
+// and per-block partial sums of |r|^2 in FP64.
+__global__ void k_residual64_to32(Lvl L, const double* __restrict__ phi,
+                                  const double* __restrict__ mu,
+                                  const double* __restrict__ om,
+                                  const double* __restrict__ S1,
+                                  const double* __restrict__ S2,
+                                  const double* __restrict__ S3,
+                                  const double* __restrict__ b, float* __restrict__ r1,
+                                  float* __restrict__ r2, float* __restrict__ r3,
+                                  float* __restrict__ q, double* partials) {
+  __shared__ double sm[32];
+  const int n = L.n;
+  const int64_t cells = (int64_t)n * n * n;
+  double acc[1] = {0.0};
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, k;
+    cell_of(t, n, i, j, k);
+    const Stencil s = stencil_at(i, j, k, n);
+    double x, y, z;
+    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
+    acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
+    r1[t] = (float)x;
+    r2[t] = (float)y;
+    r3[t] = (float)z;
+    q[t] = (float)(cubic_fp(__ldg(phi + t), __ldg(b + t)) + L.c1);
+  }
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+__global__ void k_reduce1(const double* __restrict__ partials, int nparts, double* out) {
+  __shared__ double sm[32];
+  double acc[1] = {0.0};
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) acc[0] += partials[p];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) out[0] = acc[0];
+}
+
+__global__ void k_restrict32(int n, const float* __restrict__ f, float* __restrict__ c) {
+  const int nc = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nc * nc * nc) return;
+  int I, J, K;
+  cell_of(t, nc, I, J, K);
+  float acc = 0.f;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int64_t i = 2 * I + (s & 1), j = 2 * J + ((s >> 1) & 1), k = 2 * K + (s >> 2);
+    acc += __ldg(f + i + n * (j + (int64_t)n * k));
+  }
+  c[t] = 0.125f * acc;
+}
+
+// Pointwise solve of the linearised 3x3 system (q frozen):
+//   [ 1   kap  0  ] [dp]   [r1 + tau/h^2 sum d_mu]
+//   [ -q  1    6g ] [dm] = [r2 + g sum d_om      ]
+//   [ 3g  0    1  ] [dw]   [r3 + g/2 sum d_phi   ]
+__device__ __forceinline__ void lin_point(const LvlF& L, float sp, float sm_, float sw,
+                                          float q, float r1, float r2, float r3,
+                                          float& dp, float& dm, float& dw) {
+  const float st1 = fmaf(L.tg, sm_, r1);
+  const float st2 = fmaf(L.g, sw, r2);
+  const float st3 = fmaf(L.gh, sp, r3);
+  const float Q = q + L.Q0;
+  const float det = fmaf(L.kap, Q, 1.0f);
+  dm = fmaf(Q, st1, fmaf(-L.g6, st3, st2)) / det;
+  dp = fmaf(-L.kap, dm, st1);
+  dw = fmaf(-L.g3, dp, st3);
+}
+
+// One colour of a linear red-black sweep.  ZERO: the correction is known to
+// be zero everywhere before this half-sweep (first red pass from d = 0), so no
+// neighbour is read.
+template <bool ZERO>
+__global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* d3,
+                               const float* __restrict__ r1, const float* __restrict__ r2,
+                               const float* __restrict__ r3, const float* __restrict__ q) {
+  const int n = L.n, half = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)half * n * n) return;
+  const int p = (int)(t % half);
+  const int64_t r = t / half;
+  const int j = (int)(r % n), k = (int)(r / n);
+  const int i = 2 * p + ((j + k + colour) & 1);
+  const Stencil s = stencil_at(i, j, k, n);
+  float sp = 0.f, sm_ = 0.f, sw = 0.f;
+  if (!ZERO) {
+    sp = nbsum(d1, s);
+    sm_ = nbsum(d2, s);
+    sw = nbsum(d3, s);
+  }
+  float dp, dm, dw;
+  lin_point(L, sp, sm_, sw, __ldg(q + s.c), __ldg(r1 + s.c), __ldg(r2 + s.c),
+            __ldg(r3 + s.c), dp, dm, dw);
+  d1[s.c] = dp;
+  d2[s.c] = dm;
+  d3[s.c] = dw;
+}
+
+// rho = r - J d at the 8 children of each coarse cell, averaged.
+__global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
+                                          const float* __restrict__ d2,
+                                          const float* __restrict__ d3,
+                                          const float* __restrict__ r1,
+                                          const float* __restrict__ r2,
+                                          const float* __restrict__ r3,
+                                          const float* __restrict__ q,
+                                          float* __restrict__ c1, float* __restrict__ c2,
+                                          float* __restrict__ c3) {
+  const int n = L.n, nc = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)nc * nc * nc) return;
+  int I, J, K;
+  cell_of(t, nc, I, J, K);
+  float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
+    const Stencil s = stencil_at(i, j, k, n);
+    const float p = __ldg(d1 + s.c), m = __ldg(d2 + s.c), w = __ldg(d3 + s.c);
+    const float lm = fmaf(-6.f, m, nbsum(d2, s));
+    const float lw = fmaf(-6.f, w, nbsum(d3, s));
+    const float lp = fmaf(-6.f, p, nbsum(d1, s));
+    a1 += __ldg(r1 + s.c) - fmaf(-L.tg, lm, p);
+    a2 += __ldg(r2 + s.c) - (fmaf(-__ldg(q + s.c), p, m) - L.g * lw);
+    a3 += __ldg(r3 + s.c) - fmaf(-L.gh, lp, w);
+  }
+  c1[t] = 0.125f * a1;
+  c2[t] = 0.125f * a2;
+  c3[t] = 0.125f * a3;
+}
+
+__device__ __forceinline__ float interp8f(const float* __restrict__ e, int64_t o000,
+                                          int64_t o100, int64_t o010, int64_t o001,
+                                          int64_t o110, int64_t o101, int64_t o011,
+                                          int64_t o111) {
+  const float g2 = (__ldg(e + o100) + __ldg(e + o010)) + __ldg(e + o001);
+  const float g3 = (__ldg(e + o110) + __ldg(e + o101)) + __ldg(e + o011);
+  float acc = fmaf(3.f, g3, __ldg(e + o111));
+  acc = fmaf(9.f, g2, acc);
+  return fmaf(27.f, __ldg(e + o000), acc);
+}
+
+// d += P e (trilinear, weights 27, 9, 3, 1 over 64).
+__global__ void k_prolong_add32(int n, const float* __restrict__ e1,
+                                const float* __restrict__ e2, const float* __restrict__ e3,
+                                float* __restrict__ d1, float* __restrict__ d2,
+                                float* __restrict__ d3) {
+  const int nc = n >> 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
+  const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
+  const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
+  const int64_t nn = (int64_t)nc * nc;
+  const int64_t zK = K * nn, zK2 = K2 * nn, yJ = (int64_t)J * nc, yJ2 = (int64_t)J2 * nc;
+  const int64_t o000 = I + yJ + zK, o100 = I2 + yJ + zK, o010 = I + yJ2 + zK,
+                o001 = I + yJ + zK2, o110 = I2 + yJ2 + zK, o101 = I2 + yJ + zK2,
+                o011 = I + yJ2 + zK2, o111 = I2 + yJ2 + zK2;
+  const float w = 1.0f / 64.0f;
+  d1[t] = fmaf(w, interp8f(e1, o000, o100, o010, o001, o110, o101, o011, o111), d1[t]);
+  d2[t] = fmaf(w, interp8f(e2, o000, o100, o010, o001, o110, o101, o011, o111), d2[t]);
+  d3[t] = fmaf(w, interp8f(e3, o000, o100, o010, o001, o110, o101, o011, o111), d3[t]);
+}
+
+// Coarsest level of the linear problem: start from zero, red-black sweeps in
+// one block until the largest change is below 1e-7 of the largest value or
+// max_sweeps.
+__global__ void k_lin_coarse_solve32(LvlF L, int max_sweeps, float* d1, float* d2,
+                                     float* d3, const float* r1, const float* r2,
+                                     const float* r3, const float* q) {
+  __shared__ float red[2][32];
+  __shared__ int done;
+  const int n = L.n, half = n >> 1;
+  const int cells = n * n * n, ccells = half * n * n;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+    d1[t] = 0.f;
+    d2[t] = 0.f;
+    d3[t] = 0.f;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float change = 0.f, size = 0.f;
+    for (int colour = 0; colour < 2; ++colour) {
+      for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
+        const int p = t % half, r = t / half;
+        const int j = r % n, k = r / n;
+        const int i = 2 * p + ((j + k + colour) & 1);
+        const Stencil s = stencil_at(i, j, k, n);
+        float dp, dm, dw;
+        lin_point(L, nbsum_coherent(d1, s), nbsum_coherent(d2, s), nbsum_coherent(d3, s),
+                  q[s.c], r1[s.c], r2[s.c], r3[s.c], dp, dm, dw);
+        change = fmaxf(change, fmaxf(fabsf(dp - d1[s.c]),
+                                     fmaxf(fabsf(dm - d2[s.c]), fabsf(dw - d3[s.c]))));
+        size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+        d1[s.c] = dp;
+        d2[s.c] = dm;
+        d3[s.c] = dw;
+      }
+      __syncthreads();
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      change = fmaxf(change, __shfl_down_sync(0xffffffffu, change, o));
+      size = fmaxf(size, __shfl_down_sync(0xffffffffu, size, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = change;
+      red[1][threadIdx.x >> 5] = size;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float c = 0.f, z = 0.f;
+      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) {
+        c = fmaxf(c, red[0][w]);
+        z = fmaxf(z, red[1][w]);
+      }
+      done = (c <= 1e-7f * z);
+    }
+    __syncthreads();
+    if (done) break;
+  }
+}
+
+__global__ void k_correct64(int64_t cells, double* __restrict__ u1, double* __restrict__ u2,
+                            double* __restrict__ u3, const float* __restrict__ d1,
+                            const float* __restrict__ d2, const float* __restrict__ d3) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells) return;
+  u1[t] += (double)__ldg(d1 + t);
+  u2[t] += (double)__ldg(d2 + t);
+  u3[t] += (double)__ldg(d3 + t);
+}
+
+inline int nblocks_reduce(int64_t cells) {
+  const int64_t nb = (cells + kReduceThreads - 1) / kReduceThreads;
+  return (int)(nb < kReduceBlocks ? nb : kReduceBlocks);
+}
+
+struct Ctx32 {
+  MixedBufs* mx;
+  const pfc_params* p;
+  int nl;
+  LvlF L[kMaxLevelsMixed];
+  cudaStream_t st;
+  Prof* pr;
+};
+
+cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
+  const LvlF& L = c.L[l];
+  const int64_t work = (int64_t)(L.n / 2) * L.n * L.n;
+  float* const* d = c.mx->d[l];
+  float* const* r = c.mx->r[l];
+  const float* q = c.mx->q[l];
+  if (sweeps <= 0) return cudaSuccess;
+  prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
+  for (int s = 0; s < sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour) {
+      if (zero_init && s == 0 && colour == 0)
+        k_lin_smooth32<true><<<grid_for(work), kThreads, 0, c.st>>>(L, colour, d[0], d[1],
+                                                                    d[2], r[0], r[1], r[2], q);
+      else
+        k_lin_smooth32<false><<<grid_for(work), kThreads, 0, c.st>>>(
+            L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
+    }
+  }
+  prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps, c.st);
+  return cudaGetLastError();
+}
+
+cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
+  MixedBufs& mx = *c.mx;
+  const LvlF& L = c.L[l];
+  if (l == c.nl - 1) {
+    const int work = (L.n / 2) * L.n * L.n;
+    int threads = ((work + 31) / 32) * 32;
+    if (threads > 1024) threads = 1024;
+    prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
+    k_lin_coarse_solve32<<<1, threads, 0, c.st>>>(L, 200, mx.d[l][0], mx.d[l][1],
+                                                  mx.d[l][2], mx.r[l][0], mx.r[l][1],
+                                                  mx.r[l][2], mx.q[l]);
+    prof_end(c.pr, PFC_K_LIN_COARSE, l, 1, c.st);
+    return cudaGetLastError();
+  }
+  cudaError_t e;
+  if (c.p->nu1 > 0) {
+    e = smooth32(c, l, c.p->nu1, zero_init);
+  } else {
+    e = cudaSuccess;
+    if (zero_init) {
+      const size_t bytes = (size_t)L.n * L.n * L.n * sizeof(float);
+      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+        e = cudaMemsetAsync(mx.d[l][q], 0, bytes, c.st);
+    }
+  }
+  if (e != cudaSuccess) return e;
+  const int nc = L.n / 2;
+  prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
+  k_lin_residual_restrict32<<<grid_for((int64_t)nc * nc * nc), kThreads, 0, c.st>>>(
+      L, mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l],
+      mx.r[l + 1][0], mx.r[l + 1][1], mx.r[l + 1][2]);
+  prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
+  prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
+  k_prolong_add32<<<grid_for((int64_t)L.n * L.n * L.n), kThreads, 0, c.st>>>(
+      L.n, mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
+      mx.d[l][2]);
+  prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return smooth32(c, l, c.p->nu2, false);
+}
+
+}  // namespace
+
+cudaError_t launch_residual64_to32(const Lvl& L, const double* phi, const double* mu,
+                                   const double* om, const double* S1, const double* S2,
+                                   const double* S3, const double* b, float* r1, float* r2,
+                                   float* r3, float* q, double* partials, double* out,
+                                   cudaStream_t st) {
+  const int nb = nblocks_reduce((int64_t)L.n * L.n * L.n);
+  k_residual64_to32<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1, r2,
+                                                   r3, q, partials);
+  k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
+                                float* d2, float* d3, const float* r1, const float* r2,
+                                const float* r3, const float* q, cudaStream_t st) {
+  MixedBufs mx;
+  mx.d[0][0] = d1;
+  mx.d[0][1] = d2;
+  mx.d[0][2] = d3;
+  mx.r[0][0] = (float*)r1;
+  mx.r[0][1] = (float*)r2;
+  mx.r[0][2] = (float*)r3;
+  mx.q[0] = (float*)q;
+  Ctx32 c;
+  c.mx = &mx;
+  c.p = nullptr;
+  c.nl = 1;
+  c.L[0] = to_f32(L);
+  c.st = st;
+  c.pr = nullptr;
+  return smooth32(c, 0, sweeps, zero_init);
+}
+
+cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
+                             const float* d2, const float* d3, cudaStream_t st) {
+  const int64_t cells = (int64_t)n * n * n;
+  k_correct64<<<grid_for(cells), kThreads, 0, st>>>(cells, u1, u2, u3, d1, d2, d3);
+  return cudaGetLastError();
+}
+
+int mixed_solve(MixedBufs& mx, const Lvl& L0, const pfc_params& p, int nl,
+                const int* sizes, double* const u[3], double* const S[3], const double* b,
+                double* partials, double* dout, double* hout, cudaStream_t st,
+                Prof* pr, int* outer, double* res0, double* res) {
+  Ctx32 c;
+  c.mx = &mx;
+  c.p = &p;
+  c.nl = nl;
+  c.st = st;
+  c.pr = pr;
+  {
+    double h = p.L / p.n;
+    for (int l = 0; l < nl; ++l) {
+      c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
+      h *= 2.0;
+    }
+  }
+  const double n3 = (double)p.n * p.n * p.n;
+  auto fp64_residual = [&](double* r) -> int {
+    prof_begin(pr, PFC_K_DEFECT, st);
+    cudaError_t e = launch_residual64_to32(L0, u[0], u[1], u[2], S[0], S[1], S[2], b,
+                                           mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0],
+                                           partials, dout, st);
+    prof_end(pr, PFC_K_DEFECT, 0, 2, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hout, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return PFC_ECUDA;
+    prof_harvest(pr);
+    *r = sqrt(hout[0] / (3.0 * n3));
+    return PFC_OK;
+  };
+  int rc = fp64_residual(res);
+  if (rc) return rc;
+  *res0 = *res;
+  *outer = 0;
+  while (!(*res <= p.tol)) {
+    if (!isfinite(*res)) return PFC_ENAN;
+    if (*outer >= p.max_cycles) return PFC_ENOCONV;
+    cudaError_t e = cudaSuccess;
+    for (int l = 1; l < nl && e == cudaSuccess; ++l) {
+      prof_begin(pr, PFC_K_RESTRICT, st);
+      k_restrict32<<<grid_for((int64_t)sizes[l] * sizes[l] * sizes[l]), kThreads, 0, st>>>(
+          sizes[l - 1], mx.q[l - 1], mx.q[l]);
+      prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
+      e = cudaGetLastError();
+    }
+    for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic)
+      e = vcycle32(c, 0, ic == 0);
+    if (e == cudaSuccess) {
+      prof_begin(pr, PFC_K_CORRECT, st);
+      e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st);
+      prof_end(pr, PFC_K_CORRECT, 0, 1, st);
+    }
+    if (e != cudaSuccess) return PFC_ECUDA;
+    *outer += 1;
+    rc = fp64_residual(res);
+    if (rc) return rc;
+  }
+  return PFC_OK;
+}
+
+}  // namespace pfc

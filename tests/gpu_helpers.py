@@ -1,0 +1,28 @@
+"""Shared helpers of the GPU tests: numpy <-> CUDA tensors and tolerances."""
+
+import numpy as np
+import torch
+
+
+def dev(x, dtype=torch.float64):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda", dtype=dtype)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().double().cpu().numpy()
+
+
+def empty(n, dtype=torch.float64):
+    return torch.empty((n, n, n), dtype=dtype, device="cuda")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_close_field(got, ref, rtol, what=""):
+    """max |got - ref| <= rtol * max(|ref|, 1): element by element."""
+    scale = max(float(np.abs(ref).max()), 1.0)
+    err = float(np.abs(got - ref).max())
+    assert err <= rtol * scale, f"{what}: max err {err:.3e} > {rtol:.1e} * {scale:.3e}"

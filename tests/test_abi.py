@@ -1,0 +1,74 @@
+"""The C ABI library builds, loads and exports every entry point declared in
+include/pfc.h; host-only entry points behave as documented (no GPU needed, no
+compute call is made)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1611_06288_gb300 import binding as B
+from paper_1611_06288_gb300 import build as BLD
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libpfc():
+    BLD.build()
+    return B.lib()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(pfc_\w+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(libpfc):
+    names = declared_symbols()
+    assert "pfc_init" in names and "pfc_step" in names
+    missing = [n for n in names if not hasattr(libpfc, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_symbol():
+    assert set(declared_symbols()) == set(B._SIGS), (
+        set(declared_symbols()) ^ set(B._SIGS))
+
+
+def test_default_params_and_workspace(libpfc):
+    p = B.pfc_default_params()
+    assert (p.nu1, p.nu2, p.smoother, p.precision, p.coarsest) == (2, 2, 0, 0, 2)
+    assert B.pfc_workspace_bytes(p) == 0          # n, L, dt unset -> invalid
+    p.n, p.L, p.eps, p.dt = 16, 32.0, 0.025, 0.01
+    n16 = B.pfc_workspace_bytes(p)
+    # 7 fine FP64 fields + 10 per coarse level (8, 4, 2) + reduction buffers
+    fields = 7 * 16 ** 3 + 10 * (8 ** 3 + 4 ** 3 + 2 ** 3)
+    assert fields * 8 <= n16 <= fields * 8 + 200_000
+    p.precision = B.PFC_MIXED
+    assert B.pfc_workspace_bytes(p) > n16
+    p.n = 6                                   # 6 -> 3: odd coarsest level
+    assert B.pfc_workspace_bytes(p) == 0
+    p.n, p.coarsest = 12, 6                   # 12 -> 6: accepted
+    assert B.pfc_workspace_bytes(p) > 0
+
+
+def test_validation_errors_without_gpu(libpfc):
+    p = B.pfc_default_params()
+    p.n, p.L, p.eps, p.dt = 16, 32.0, 0.025, 0.01
+    ctx = ctypes.c_void_p()
+    # null workspace / phi0 are rejected before any CUDA call
+    assert libpfc.pfc_init(ctypes.byref(ctx), ctypes.byref(p), None, 0, None, None, None) \
+        == B.PFC_EINVAL
+    p.eps = 1.0
+    assert B.pfc_workspace_bytes(p) == 0
+    assert libpfc.pfc_step(None, 1, None) == B.PFC_EINVAL
+    assert libpfc.pfc_op_smooth(5, 1.0, 0.1, 0.1, 0, 1, *([None] * 7), None) == B.PFC_EINVAL
+    for code in (0, -1, -2, -3, -4, -5):
+        assert B.strerror(code)

@@ -1,0 +1,200 @@
+"""Parity of every CUDA stage of the V-cycle with the CPU oracle, through the
+C ABI, element by element, on seeded inputs.  Sizes span several thread
+blocks with a ragged tail (12^3 = 1728 cells = 6.75 blocks of 256) and the
+smallest levels (2^3, 4^3)."""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import assert_close_field, dev, empty, host
+from oracle import pfc_oracle as O
+from paper_1611_06288_gb300 import binding as B
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [2, 4, 12, 32]
+EPS, TAU = 0.1, 0.05
+# FP64 stages differ from the oracle only by rounding order and FMA
+# contraction: a few ulps of the largest term.  The Laplacian amplifies by
+# up to 12/h^2 relative to the field, hence the h-dependent scale.
+FP64_RTOL = 1e-12
+
+
+def case(n, seed=0):
+    rng = np.random.default_rng(1000 + n + seed)
+    L = 0.8 * n
+    h = L / n
+    b = 0.2 + 0.1 * rng.standard_normal((n, n, n))
+    c = b + 0.01 * rng.standard_normal((n, n, n))
+    u = [b + 0.02 * rng.standard_normal((n, n, n)), rng.standard_normal((n, n, n)),
+         rng.standard_normal((n, n, n))]
+    return h, b, c, u
+
+
+def prm(lin="newton"):
+    return O.Params(eps=EPS, tau=TAU, linearization=lin)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_source(n):
+    h, b, c, _ = case(n)
+    S2, S3 = empty(n), empty(n)
+    B.pfc_op_source(n, h, EPS, dev(b), dev(c), S2, S3)
+    ref = O.source_S(b, c, h, prm())
+    assert_close_field(host(S2), ref[1], FP64_RTOL, "S2")
+    assert_close_field(host(S3), ref[2], FP64_RTOL, "S3")
+
+
+@pytest.mark.parametrize("n", [2, 4, 12, 32])
+@pytest.mark.parametrize("lin", ["newton", "picard"])
+@pytest.mark.parametrize("sweeps", [1, 2])
+def test_smooth(n, lin, sweeps):
+    h, b, c, u = case(n)
+    S = O.source_S(b, c, h, prm(lin))
+    d = [dev(x) for x in u]
+    B.pfc_op_smooth(n, h, EPS, TAU, B.PFC_NEWTON if lin == "newton" else B.PFC_PICARD,
+                    sweeps, *d, *[dev(s) for s in S], dev(b))
+    ref = O.smooth(u, S, b, h, prm(lin), sweeps)
+    for g, r, name in zip(d, ref, ("phi", "mu", "om")):
+        assert_close_field(host(g), r, FP64_RTOL, name)
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_residual(n):
+    h, b, c, u = case(n)
+    S = O.source_S(b, c, h, prm())
+    r = [empty(n) for _ in range(3)]
+    B.pfc_op_residual(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S], dev(b), *r)
+    ref = O.residual(S, u, b, h, prm())
+    for g, x in zip(r, ref):
+        assert_close_field(host(g), x, FP64_RTOL, "r")
+
+
+@pytest.mark.parametrize("n", [2, 4, 12, 32])
+def test_residual_restrict_and_restrict(n):
+    h, b, c, u = case(n)
+    S = O.source_S(b, c, h, prm())
+    nc = n // 2
+    rc = [empty(nc) for _ in range(3)]
+    uc = [empty(nc) for _ in range(3)]
+    B.pfc_op_residual_restrict(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S],
+                               dev(b), *rc, *uc)
+    ref_r = [O.restrict(x) for x in O.residual(S, u, b, h, prm())]
+    for g, x in zip(rc, ref_r):
+        assert_close_field(host(g), x, FP64_RTOL, "rc")
+    for g, x in zip(uc, u):
+        assert_close_field(host(g), O.restrict(x), 1e-15, "uc")
+    bc = empty(nc)
+    B.pfc_op_restrict(n, dev(b), bc)
+    assert_close_field(host(bc), O.restrict(b), 1e-15, "bc")
+
+
+@pytest.mark.parametrize("nc", [1, 2, 6, 16])
+def test_coarse_source(nc):
+    h, b, c, u = case(nc)
+    rng = np.random.default_rng(7)
+    r = [rng.standard_normal((nc,) * 3) for _ in range(3)]
+    d = [dev(x) for x in r]
+    B.pfc_op_coarse_source(nc, h, EPS, TAU, *[dev(x) for x in u], dev(b), *d)
+    ref = [n_ + x for n_, x in zip(O.operator_N(u, b, h, prm()), r)]
+    for g, x in zip(d, ref):
+        assert_close_field(host(g), x, FP64_RTOL, "Sc")
+
+
+@pytest.mark.parametrize("n", [2, 4, 12, 32])
+def test_prolong_correct(n):
+    rng = np.random.default_rng(3 + n)
+    nc = n // 2
+    v = [rng.standard_normal((nc,) * 3) for _ in range(3)]
+    w = [rng.standard_normal((nc,) * 3) for _ in range(3)]
+    u = [rng.standard_normal((n,) * 3) for _ in range(3)]
+    du = [dev(x) for x in u]
+    B.pfc_op_prolong_correct(n, *[dev(x) for x in v], *[dev(x) for x in w], *du)
+    for g, x, vv, ww in zip(du, u, v, w):
+        assert_close_field(host(g), x + O.prolong(vv - ww), 1e-14, "u+Pe")
+
+
+@pytest.mark.parametrize("n", [2, 4, 8])
+@pytest.mark.parametrize("lin", ["newton", "picard"])
+def test_coarse_solve(n, lin):
+    """The coarsest-level solve reaches the unique solution of N(u) = S that the
+    oracle's dense Newton solve finds."""
+    L = 2.0 * n           # coarse spacing 2
+    h = L / n
+    rng = np.random.default_rng(11)
+    b = 0.2 + 0.1 * rng.standard_normal((n,) * 3)
+    c = b + 0.01 * rng.standard_normal((n,) * 3)
+    p = prm(lin)
+    S = O.source_S(b, c, h, p)
+    ref, _ = O.newton_dense(S, [b, 0 * b, 0 * b], b, h, p)
+    d = [dev(b), dev(0 * b), dev(0 * b)]
+    B.pfc_op_coarse_solve(n, h, EPS, TAU, B.PFC_NEWTON if lin == "newton" else B.PFC_PICARD,
+                          400, *d, *[dev(s) for s in S], dev(b))
+    got = [host(x) for x in d]
+    assert O.rms(O.residual(S, got, b, h, p)) < 1e-12
+    for g, r in zip(got, ref):
+        assert_close_field(g, r, 1e-11, "coarse")
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
+def test_diagnostics_and_residual_norm(n):
+    h, b, c, u = case(n)
+    a = u[0]
+    scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    out = B.pfc_op_diagnostics(n, h, EPS, dev(a), dev(b), scratch)
+    assert out[0] == pytest.approx(O.energy(a, h, EPS), rel=1e-12)
+    assert out[1] == pytest.approx(O.modified_energy(a, b, h, EPS), rel=1e-12)
+    assert out[2] == pytest.approx(O.mass(a, h), rel=1e-12)
+    assert out[3] == pytest.approx(O.grad_norm2_sq(a, h), rel=1e-12)
+    S = O.source_S(b, c, h, prm())
+    rms = B.pfc_op_residual_norm(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S],
+                                 dev(b), scratch)
+    assert rms == pytest.approx(O.rms(O.residual(S, u, b, h, prm())), rel=1e-12)
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
+def test_defect_and_correct(n):
+    h, b, c, u = case(n)
+    S = O.source_S(b, c, h, prm())
+    scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    r = [empty(n, torch.float32) for _ in range(3)]
+    q = empty(n, torch.float32)
+    rms = B.pfc_op_defect(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S], dev(b),
+                          *r, q, scratch)
+    ref = O.residual(S, u, b, h, prm())
+    assert rms == pytest.approx(O.rms(ref), rel=1e-12)
+    for g, x in zip(r, ref):
+        # FP64 residual rounded to FP32: half an FP32 ulp
+        assert_close_field(host(g), x, 2 ** -23, "r32")
+    assert_close_field(host(q), O.jacobian_coefficient(u[0], b, prm()), 2 ** -23, "q32")
+    # u += d: one FP64 rounding of the same sum on both sides -> bit-exact
+    rng = np.random.default_rng(5)
+    d = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    du = [dev(x) for x in u]
+    B.pfc_op_correct(n, *du, *[dev(x, torch.float32) for x in d])
+    for g, x, y in zip(du, u, d):
+        np.testing.assert_array_equal(host(g), x + y.astype(np.float64))
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
+@pytest.mark.parametrize("zero_init", [True, False])
+def test_linear_smoother_fp32(n, zero_init):
+    h, b, c, u = case(n)
+    p = prm()
+    q = O.jacobian_coefficient(u[0], b, p).astype(np.float32)
+    rng = np.random.default_rng(9)
+    r = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    d0 = [np.zeros((n,) * 3) if zero_init else 0.1 * rng.standard_normal((n,) * 3)
+          for _ in range(3)]
+    d0 = [x.astype(np.float32) for x in d0]
+    dd = [dev(x, torch.float32) for x in d0]
+    if zero_init:                       # contents must not matter
+        for t in dd:
+            t.fill_(float("nan"))
+    B.pfc_op_lin_smooth(n, h, EPS, TAU, 2, zero_init, *dd, *[dev(x, torch.float32) for x in r],
+                        dev(q, torch.float32))
+    ref = O.linear_smooth([x.astype(np.float64) for x in d0],
+                          [x.astype(np.float64) for x in r], q.astype(np.float64), h, p, 2)
+    for g, x in zip(dd, ref):
+        assert_close_field(host(g), x, 1e-5, "d32")

@@ -1,0 +1,179 @@
+"""Parity of the full CUDA time step (pfc_init / pfc_step / pfc_energy /
+pfc_mass through the C ABI) with the CPU oracle, and properties that hold at
+any size checked on the full-size workloads in the launch configuration the
+benchmark uses."""
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_helpers import host, rel_l2
+from oracle import pfc_oracle as O
+from paper_1611_06288_gb300 import binding as B
+from paper_1611_06288_gb300 import workloads as W
+from paper_1611_06288_gb300.solver import PFCSolver
+
+pytestmark = pytest.mark.gpu
+
+# Both sides converged to an RMS residual of 1e-12: the solution of N(u) = S
+# is unique (Prop. 3.1) and the residual-to-error gain is O(1), so the fields
+# agree to ~1e-11 relative; the bound of the method is 1e-10.
+PARITY_RTOL = 1e-10
+
+
+def oracle_run(phi0, steps, h, eps, dt, lin, tol=1e-12):
+    p = O.Params(eps=eps, tau=dt, linearization=lin)
+    traj = []
+
+    def cb(k, a, b, c, mu, om, res):
+        traj.append((a.copy(), mu.copy(), om.copy()))
+
+    O.run(phi0, steps, h, p, tol=tol, callback=cb)
+    return traj
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("smoother", ["newton", "picard"])
+def test_random16_ten_steps(precision, smoother):
+    """16^3, L = 32, eps = 0.025, phi0 = 0.07 + 0.07 U(-1,1), dt = 0.01, 10
+    steps with the phi^{-1} := phi^0 start: every step matches the oracle."""
+    wl = W.random16()
+    phi0 = wl.phi0()
+    ref = oracle_run(phi0, wl.steps, wl.h, wl.eps, wl.dt, smoother)
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-12, precision=precision,
+                  smoother=smoother, max_cycles=60)
+    for k in range(wl.steps):
+        st = s.step(1)
+        assert st.residual <= 1e-12
+        a, mu, om = host(s.phi()), host(s.mu()), host(s.omega())
+        assert rel_l2(a, ref[k][0]) <= PARITY_RTOL, (k, rel_l2(a, ref[k][0]))
+        assert rel_l2(mu, ref[k][1]) <= PARITY_RTOL
+        assert rel_l2(om, ref[k][2]) <= PARITY_RTOL
+    F, Fm = s.energy()
+    assert F == pytest.approx(O.energy(ref[-1][0], wl.h, wl.eps), rel=1e-10)
+    assert Fm == pytest.approx(O.modified_energy(ref[-1][0], ref[-2][0], wl.h, wl.eps),
+                               rel=1e-10)
+    assert s.mass() == pytest.approx(O.mass(phi0, wl.h), rel=1e-12)
+    assert s.step_index == wl.steps
+
+
+@pytest.mark.parametrize("n,coarsest", [(4, 2), (12, 6), (20, 10), (24, 6)])
+def test_uneven_sizes_and_level_counts(n, coarsest):
+    """Grids that are not powers of two and the smallest grid, against the
+    oracle (one step from a random start on a box with h = 1.5)."""
+    L = 1.5 * n
+    rng = np.random.default_rng(n)
+    phi0 = 0.1 + 0.1 * rng.uniform(-1, 1, (n,) * 3)
+    ref = oracle_run(phi0, 2, L / n, 0.2, 0.05, "newton")
+    for precision in ("fp64", "mixed"):
+        s = PFCSolver(n, L, 0.2, 0.05, phi0, tol=1e-12, coarsest=coarsest,
+                      precision=precision, max_cycles=200)
+        s.step(2)
+        assert rel_l2(host(s.phi()), ref[1][0]) <= PARITY_RTOL
+
+
+def test_constant_state_is_fixed_point():
+    n = 16
+    phi0 = np.full((n,) * 3, 0.3)
+    s = PFCSolver(n, 10.0, 0.3, 0.1, phi0, tol=1e-13)
+    s.step(3)
+    np.testing.assert_allclose(host(s.phi()), 0.3, rtol=1e-14)
+    np.testing.assert_allclose(host(s.mu()), 0.3 ** 3 + 0.7 * 0.3, rtol=1e-13)
+
+
+def test_start_from_two_levels_and_set_state():
+    """phi^1 given explicitly: the same trajectory as the oracle started from
+    (phi^0, phi^1); pfc_set_state restarts from a stored pair."""
+    wl = W.random16()
+    phi0 = wl.phi0()
+    p = O.Params(eps=wl.eps, tau=wl.dt)
+    phi1 = O.run(phi0, 1, wl.h, p, tol=1e-13)[0]
+    a_ref, *_ = O.run(phi0, 3, wl.h, p, tol=1e-13, phi1=phi1)
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, phi1=phi1, tol=1e-13)
+    assert s.step_index == 1
+    s.step(3)
+    assert rel_l2(host(s.phi()), a_ref) <= PARITY_RTOL
+    s.set_state(phi1, phi0)
+    s.step(3)
+    assert rel_l2(host(s.phi()), a_ref) <= PARITY_RTOL
+
+
+def test_energy_law_and_mass_on_gpu_trajectory():
+    """The discrete energy law of Eq. 1.10 and mass conservation hold along
+    the GPU trajectory (checked with the oracle's norms)."""
+    wl = W.cosine_table(16)
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-13, smoother="picard")
+    c = b = wl.phi0()
+    m0 = O.mass(b, wl.h)
+    for _ in range(4):
+        s.step(1)
+        a, mu = host(s.phi()), host(s.mu())
+        lhs = O.modified_energy(a, b, wl.h, wl.eps) - O.modified_energy(b, c, wl.h, wl.eps)
+        rhs = (-wl.dt * O.grad_norm2_sq(mu, wl.h)
+               - 0.5 * O.grad_norm2_sq(a - 2 * b + c, wl.h))
+        assert lhs == pytest.approx(rhs, rel=1e-7)
+        assert O.mass(a, wl.h) == pytest.approx(m0, rel=1e-13)
+        c, b = b, a
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_128_residual_by_oracle(precision):
+    """128^3 smooth-mode workload (L = 32, eps = 0.025, dt = 0.0125, tol 1e-9)
+    in the benchmark's configuration: after two steps the oracle evaluates
+    S - N(u) of the GPU result on the CPU in FP64 and finds it below the
+    tolerance; mass is conserved."""
+    wl = W.smooth_sweep(128)
+    phi0 = wl.phi0()
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision,
+                  inner_cycles=2 if precision == "mixed" else 1)
+    s.step(1)
+    b = phi0
+    a1 = host(s.phi())
+    s.step(1)
+    a, mu, om = host(s.phi()), host(s.mu()), host(s.omega())
+    p = O.Params(eps=wl.eps, tau=wl.dt)
+    r = O.residual(O.source_S(a1, b, wl.h, p), [a, mu, om], a1, wl.h, p)
+    assert O.rms(r) <= wl.tol * 1.0001
+    assert O.mass(a, wl.h) == pytest.approx(O.mass(phi0, wl.h), abs=1e-9 * wl.L ** 3)
+
+
+def test_full_size_256_polycrystal_one_step():
+    """256^3 polycrystal workload (h = pi/4, eps = 0.25, dt = 0.1), mixed
+    precision: the oracle's FP64 residual of the GPU step is below 1e-9 and
+    the energy reported by the GPU equals the oracle's F_h of the same field."""
+    wl = W.polycrystal(256)
+    phi0 = wl.phi0()
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision="mixed",
+                  inner_cycles=2)
+    st = s.step(1)
+    assert st.residual <= wl.tol
+    a, mu, om = host(s.phi()), host(s.mu()), host(s.omega())
+    p = O.Params(eps=wl.eps, tau=wl.dt)
+    r = O.residual(O.source_S(phi0, phi0, wl.h, p), [a, mu, om], phi0, wl.h, p)
+    assert O.rms(r) <= wl.tol * 1.0001
+    F, _ = s.energy()
+    assert F == pytest.approx(O.energy(a, wl.h, wl.eps), rel=1e-11)
+
+
+def test_error_codes():
+    wl = W.random16()
+    with pytest.raises(B.PFCError) as e:
+        PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-14, max_cycles=1).step(1)
+    assert e.value.code == B.PFC_ENOCONV
+    bad = wl.phi0()
+    bad[3, 4, 5] = np.nan
+    with pytest.raises(B.PFCError) as e:
+        PFCSolver(wl.n, wl.L, wl.eps, wl.dt, bad).step(1)
+    assert e.value.code == B.PFC_ENAN
+    with pytest.raises(B.PFCError) as e:
+        PFCSolver(6, 6.0, 0.1, 0.1, np.zeros((6, 6, 6)))
+    assert e.value.code == B.PFC_ESIZE
+    # a failed step leaves the state where it was
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-14, max_cycles=1)
+    before = host(s.phi())
+    with pytest.raises(B.PFCError):
+        s.step(1)
+    np.testing.assert_array_equal(host(s.phi()), before)
+    assert s.step_index == 0

@@ -277,6 +277,42 @@ def test_smoother_reduces_residual():
     assert O.rms(O.residual(S, u, b, wl.h, prm)) < 0.1 * r0
 
 
+def test_jacobian_matches_central_difference():
+    """J d of the linearisation equals (N(u + s d) - N(u - s d)) / 2s; the
+    cubic term makes the central difference exact up to s^2 |d|^3 terms."""
+    m, h = 8, 1.3
+    prm = O.Params(eps=0.2, tau=0.07)
+    b = 0.3 + rand_field(m, 0.1)
+    u = [b + rand_field(m, 0.05), rand_field(m), rand_field(m)]
+    d = [rand_field(m), rand_field(m), rand_field(m)]
+    s = 1e-4
+    up = [x + s * y for x, y in zip(u, d)]
+    um = [x - s * y for x, y in zip(u, d)]
+    fd = [(p_ - q_) / (2 * s) for p_, q_ in
+          zip(O.operator_N(up, b, h, prm), O.operator_N(um, b, h, prm))]
+    q = O.jacobian_coefficient(u[0], b, prm)
+    Jd = O.jacobian_apply(d, q, h, prm)
+    for x, y in zip(Jd, fd):
+        np.testing.assert_allclose(x, y, rtol=1e-7, atol=1e-7 * np.abs(y).max())
+
+
+def test_linear_smoother_converges_to_dense_solution():
+    """Sweeps of the linearised smoother converge to J^{-1} r computed with
+    the dense Jacobian and LAPACK."""
+    m, h = 4, 2.0
+    prm = O.Params(eps=0.1, tau=0.05)
+    b = 0.2 + rand_field(m, 0.1)
+    phi = b + rand_field(m, 0.05)
+    u = [phi, 0 * b, 0 * b]
+    r = [rand_field(m), rand_field(m), rand_field(m)]
+    J = O.jacobian_dense(u, b, h, prm)
+    ref = np.linalg.solve(J, np.concatenate([x.ravel() for x in r]))
+    q = O.jacobian_coefficient(phi, b, prm)
+    d = O.linear_smooth([0 * b, 0 * b, 0 * b], r, q, h, prm, 200)
+    got = np.concatenate([x.ravel() for x in d])
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+
+
 # --------------------------------------------------------------------------
 # Theorem 3.4 (second order in time) and Table 2 (multigrid complexity)
 # --------------------------------------------------------------------------
