@@ -165,6 +165,13 @@ class Params:
     3x3 system).  coarsest: levels of this size or smaller (or odd) are solved
     exactly.  prolongation: "trilinear" or "constant".  cubic: False drops the
     cubic term (an oracle-only switch used for the Fourier closed form).
+
+    smoother: "rb" is the paper's red-black sweep on every level; "hybrid"
+    keeps it on levels whose stiffness s = (6 tau/h^2)(18/h^4) is >= stiff_hi
+    or <= stiff_lo and uses ``jacobi_factor`` times as many damped collective
+    Jacobi sweeps (weight ``jacobi_weight``) on the levels in between, where
+    the red-black sweep is unstable (its red/black mode-pair amplification
+    exceeds 1) and its V-cycles stall or diverge.
     """
     eps: float
     tau: float
@@ -175,6 +182,11 @@ class Params:
     prolongation: str = "trilinear"
     cubic: bool = True
     mob: object = field(default=None, compare=False)
+    smoother: str = "hybrid"
+    jacobi_weight: float = 0.7
+    jacobi_factor: int = 2
+    stiff_hi: float = 1000.0
+    stiff_lo: float = 0.02
 
 
 def cubic_f(a, b):
@@ -250,7 +262,77 @@ def colour_mask(m):
     return (i + j + k) % 2
 
 
+def level_stiffness(h, prm: Params):
+    """s = kappa * 18/h^4 with kappa = 6 tau/h^2: the product of the
+    couplings that close the phi -> omega -> mu -> phi cycle of the
+    pointwise system relative to its identity part."""
+    return 108.0 * prm.tau / h ** 6
+
+
+def uses_jacobi(h, prm: Params):
+    s = level_stiffness(h, prm)
+    return prm.smoother == "hybrid" and prm.stiff_lo < s < prm.stiff_hi
+
+
 def smooth(u, S, b, h, prm: Params, sweeps):
+    """Smoothing of level h: ``sweeps`` red-black sweeps, or
+    ``jacobi_factor * sweeps`` damped Jacobi sweeps on hybrid levels."""
+    if uses_jacobi(h, prm):
+        return jacobi_smooth(u, S, b, h, prm, sweeps * prm.jacobi_factor)
+    return rb_smooth(u, S, b, h, prm, sweeps)
+
+
+def point_system(phi, mu, om, S, b, h, prm: Params):
+    """The Section 5 pointwise 3x3 system of every cell, with all six
+    neighbours at their current values: returns (A, rhs) for Cramer's rule."""
+    s1, s2, s3 = S
+    g = 1.0 / (h * h)
+    kap = prm.tau * g * face_mobility_sums(phi.shape, prm.mob)
+    if prm.mob is None:
+        flux_nb = neighbour_sum(mu)
+    else:
+        flux_nb = sum(prm.mob[ax] * np.roll(mu, -1, ax)
+                      + np.roll(prm.mob[ax], 1, ax) * np.roll(mu, 1, ax)
+                      for ax in AXES)
+    st1 = s1 + prm.tau * g * flux_nb
+    phin = phi
+    if not prm.cubic:
+        q = np.full_like(phi, 0.5 * (1.0 - prm.eps))
+        extra = 0.0
+    elif prm.linearization == "picard":
+        p = 0.25 * (phin * phin + b * b)
+        q = p + 0.5 * (1.0 - prm.eps)
+        extra = p * b
+    elif prm.linearization == "newton":
+        fp = cubic_fprime(phin, b)
+        q = fp + 0.5 * (1.0 - prm.eps)
+        extra = cubic_f(phin, b) - fp * phin
+    else:
+        raise ValueError(prm.linearization)
+    st2 = s2 + extra + g * neighbour_sum(om)
+    st3 = s3 + 0.5 * g * neighbour_sum(phi)
+    A = [[1.0, kap, 0.0],
+         [-q, 1.0, 6.0 * g],
+         [3.0 * g, 0.0, 1.0]]
+    return A, (st1, st2, st3)
+
+
+def jacobi_smooth(u, S, b, h, prm: Params, sweeps):
+    """Damped collective Jacobi: every cell solves its 3x3 system with the
+    neighbours of the previous sweep, and moves by ``jacobi_weight`` of the
+    change."""
+    phi, mu, om = (x.copy() for x in u)
+    w = prm.jacobi_weight
+    for _ in range(sweeps):
+        A, rhs = point_system(phi, mu, om, S, b, h, prm)
+        x1, x2, x3 = cramer3(A, rhs)
+        phi = phi + w * (x1 - phi)
+        mu = mu + w * (x2 - mu)
+        om = om + w * (x3 - om)
+    return [phi, mu, om]
+
+
+def rb_smooth(u, S, b, h, prm: Params, sweeps):
     """``sweeps`` red-black nonlinear Gauss-Seidel sweeps (Section 5).
 
     For every cell of the active colour the 3x3 system
@@ -267,42 +349,12 @@ def smooth(u, S, b, h, prm: Params, sweeps):
     are neighbours).
     """
     phi, mu, om = (x.copy() for x in u)
-    s1, s2, s3 = S
-    m = phi.shape[0]
-    colour = colour_mask(m)
-    g = 1.0 / (h * h)
-    msum = face_mobility_sums(phi.shape, prm.mob)
-    kap = prm.tau * g * msum
+    colour = colour_mask(phi.shape[0])
     for _ in range(sweeps):
         for col in (0, 1):
             sel = colour == col
-            if prm.mob is None:
-                flux_nb = neighbour_sum(mu)
-            else:
-                flux_nb = sum(prm.mob[ax] * np.roll(mu, -1, ax)
-                              + np.roll(prm.mob[ax], 1, ax) * np.roll(mu, 1, ax)
-                              for ax in AXES)
-            st1 = s1 + prm.tau * g * flux_nb
-            phin = phi
-            if not prm.cubic:
-                q = np.full_like(phi, 0.5 * (1.0 - prm.eps))
-                extra = 0.0
-            elif prm.linearization == "picard":
-                p = 0.25 * (phin * phin + b * b)
-                q = p + 0.5 * (1.0 - prm.eps)
-                extra = p * b
-            elif prm.linearization == "newton":
-                fp = cubic_fprime(phin, b)
-                q = fp + 0.5 * (1.0 - prm.eps)
-                extra = cubic_f(phin, b) - fp * phin
-            else:
-                raise ValueError(prm.linearization)
-            st2 = s2 + extra + g * neighbour_sum(om)
-            st3 = s3 + 0.5 * g * neighbour_sum(phi)
-            A = [[1.0, kap, 0.0],
-                 [-q, 1.0, 6.0 * g],
-                 [3.0 * g, 0.0, 1.0]]
-            x1, x2, x3 = cramer3(A, (st1, st2, st3))
+            A, rhs = point_system(phi, mu, om, S, b, h, prm)
+            x1, x2, x3 = cramer3(A, rhs)
             phi = np.where(sel, x1, phi)
             mu = np.where(sel, x2, mu)
             om = np.where(sel, x3, om)
@@ -330,26 +382,44 @@ def jacobian_apply(d, q, h, prm: Params):
     return [j1, j2, j3]
 
 
-def linear_smooth(d, r, q, h, prm: Params, sweeps):
-    """Red-black Gauss-Seidel on J d = r: the Section 5 pointwise 3x3 system
-    with q held fixed and no cubic right-hand-side term."""
-    dp, dm, dw = (x.copy() for x in d)
+def linear_point_system(d, r, q, h, prm: Params):
+    """The pointwise 3x3 system of J d = r (q frozen, no cubic right-hand
+    side term) with all neighbours at their current values."""
+    dp, dm, dw = d
     r1, r2, r3 = r
-    colour = colour_mask(dp.shape[0])
     g = 1.0 / (h * h)
     kap = prm.tau * g * face_mobility_sums(dp.shape, prm.mob)
+    st1 = r1 + prm.tau * g * neighbour_sum(dm)
+    st2 = r2 + g * neighbour_sum(dw)
+    st3 = r3 + 0.5 * g * neighbour_sum(dp)
+    return [[1.0, kap, 0.0], [-q, 1.0, 6.0 * g], [3.0 * g, 0.0, 1.0]], (st1, st2, st3)
+
+
+def linear_smooth(d, r, q, h, prm: Params, sweeps, kind="rb"):
+    """Relaxation of J d = r with the Section 5 pointwise system: red-black
+    Gauss-Seidel (kind "rb") or damped collective Jacobi (kind "jacobi",
+    weight ``prm.jacobi_weight``)."""
+    d = [x.copy() for x in d]
+    colour = colour_mask(d[0].shape[0])
     for _ in range(sweeps):
+        if kind == "jacobi":
+            A, rhs = linear_point_system(d, r, q, h, prm)
+            x = cramer3(A, rhs)
+            d = [y + prm.jacobi_weight * (xn - y) for y, xn in zip(d, x)]
+            continue
         for col in (0, 1):
             sel = colour == col
-            st1 = r1 + prm.tau * g * neighbour_sum(dm)
-            st2 = r2 + g * neighbour_sum(dw)
-            st3 = r3 + 0.5 * g * neighbour_sum(dp)
-            A = [[1.0, kap, 0.0], [-q, 1.0, 6.0 * g], [3.0 * g, 0.0, 1.0]]
-            x1, x2, x3 = cramer3(A, (st1, st2, st3))
-            dp = np.where(sel, x1, dp)
-            dm = np.where(sel, x2, dm)
-            dw = np.where(sel, x3, dw)
-    return [dp, dm, dw]
+            A, rhs = linear_point_system(d, r, q, h, prm)
+            x = cramer3(A, rhs)
+            d = [np.where(sel, xn, y) for y, xn in zip(d, x)]
+    return d
+
+
+def linear_smooth_level(d, r, q, h, prm: Params, sweeps):
+    """Level smoothing of J d = r under the same policy as ``smooth``."""
+    if uses_jacobi(h, prm):
+        return linear_smooth(d, r, q, h, prm, sweeps * prm.jacobi_factor, "jacobi")
+    return linear_smooth(d, r, q, h, prm, sweeps, "rb")
 
 
 # --------------------------------------------------------------------------

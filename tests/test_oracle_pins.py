@@ -265,6 +265,27 @@ def test_exact_solution_is_smoother_fixed_point():
             np.testing.assert_allclose(x, y, atol=1e-12 * (1 + np.abs(y).max()))
 
 
+def test_red_black_instability_and_hybrid_policy():
+    """On a stiff level the paper's red-black sweep alone amplifies the error
+    of a constant state (its red/black mode-pair amplification exceeds 1)
+    much faster than the damped Jacobi sweep (whose only growing mode is the
+    smooth one that the coarse grid removes), and the hybrid policy's FAS
+    converges where red-black V-cycles do not (h = 0.625, tau = 0.1)."""
+    n, h = 16, 0.625
+    c = np.full((n,) * 3, 0.3)
+    prm = O.Params(eps=0.3, tau=0.1, coarsest=2)
+    S = O.source_S(c, c, h, prm)
+    u0 = [c.copy(), 0 * c, 0 * c]
+    r0 = O.rms(O.residual(S, u0, c, h, prm))
+    r_rb = O.rms(O.residual(S, O.rb_smooth(u0, S, c, h, prm, 30), c, h, prm))
+    r_j = O.rms(O.residual(S, O.jacobi_smooth(u0, S, c, h, prm, 30), c, h, prm))
+    assert r_rb > 10 * r0 and r_j < 0.1 * r_rb
+    rb = O.solve_step(c, c, u0, h, O.Params(eps=0.3, tau=0.1, coarsest=2, smoother="rb"),
+                      1e-12, max_cycles=15)
+    hy = O.solve_step(c, c, u0, h, prm, 1e-12, max_cycles=15)
+    assert rb.history[-1] > 1e-6 and hy.history[-1] <= 1e-12
+
+
 def test_smoother_reduces_residual():
     """Several sweeps from a rough guess reduce the residual (Section 5 smoother)."""
     wl = W.random16()
@@ -308,9 +329,10 @@ def test_linear_smoother_converges_to_dense_solution():
     J = O.jacobian_dense(u, b, h, prm)
     ref = np.linalg.solve(J, np.concatenate([x.ravel() for x in r]))
     q = O.jacobian_coefficient(phi, b, prm)
-    d = O.linear_smooth([0 * b, 0 * b, 0 * b], r, q, h, prm, 200)
-    got = np.concatenate([x.ravel() for x in d])
-    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
+    for kind, sweeps in (("rb", 200), ("jacobi", 600)):
+        d = O.linear_smooth([0 * b, 0 * b, 0 * b], r, q, h, prm, sweeps, kind)
+        got = np.concatenate([x.ravel() for x in d])
+        np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12 * np.abs(ref).max())
 
 
 # --------------------------------------------------------------------------
@@ -335,15 +357,15 @@ def test_second_order_in_time():
 
 def test_table2_vcycle_counts(golden_dir):
     """V-cycles to tol 1e-8 at step 10 (Table 2, Section 6.1) with the paper's
-    Picard smoother, at 16^3 and 32^3: V(2,2) within +-2 of the printed
-    counts, and V(1,1) needs more cycles than V(2,2)."""
+    red-black Picard smoother on every level, at 16^3 and 32^3: V(2,2) within
+    +-2 of the printed counts, and V(1,1) needs more cycles than V(2,2)."""
     gold = json.load(open(os.path.join(golden_dir, "table2_vcycles.json")))
     for idx, n in enumerate((16, 32)):
         wl = W.cosine_table(n)
         counts = {}
         for nu in (1, 2):
             prm = O.Params(eps=wl.eps, tau=wl.dt, nu1=nu, nu2=nu,
-                           linearization="picard", coarsest=2)
+                           linearization="picard", coarsest=2, smoother="rb")
             *_, cycles = O.run(wl.phi0(), 10, wl.h, prm, tol=wl.tol)
             counts[nu] = cycles[-1]
         assert abs(counts[2] - gold["cycles"]["2,2"][idx]) <= 2, counts
