@@ -51,6 +51,14 @@ extern "C" {
 #define PFC_NEWTON 0    /* pointwise Newton linearisation of the cubic term */
 #define PFC_PICARD 1    /* the paper's local Picard linearisation (Section 5) */
 
+#define PFC_POLICY_HYBRID 0  /* red-black sweeps where the level stiffness
+                                s = 108 tau / h^6 is >= stiff_hi or <= stiff_lo,
+                                damped collective Jacobi sweeps in between */
+#define PFC_POLICY_RB     1  /* the paper's red-black sweep on every level */
+
+#define PFC_SWEEP_RB     0   /* level smoother kinds (pfc_level_info) */
+#define PFC_SWEEP_JACOBI 1
+
 typedef struct pfc_ctx pfc_ctx;   /* opaque; owns no device memory */
 
 typedef struct pfc_params {
@@ -68,6 +76,10 @@ typedef struct pfc_params {
                           than this; the last level is solved by sweeping to
                           convergence.  >= 2 */
   int    inner_cycles; /* PFC_MIXED: FP32 V-cycles per FP64 defect correction */
+  int    policy;       /* PFC_POLICY_HYBRID or PFC_POLICY_RB */
+  double jacobi_weight;/* damping of the collective Jacobi sweep, (0, 1] */
+  int    jacobi_factor;/* Jacobi sweeps per requested sweep on Jacobi levels */
+  double stiff_hi, stiff_lo; /* thresholds of the hybrid policy */
 } pfc_params;
 
 typedef struct pfc_step_stats {
@@ -79,8 +91,20 @@ typedef struct pfc_step_stats {
 } pfc_step_stats;
 
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
- * FP64, coarsest 2, inner_cycles 1.  n, L, eps, dt are set to 0. */
+ * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
+ * factor 2, stiff_hi 1000, stiff_lo 0.02.  n, L, eps, dt are set to 0.
+ *
+ * Why the hybrid policy: on the split system the red-black pointwise sweep
+ * of Section 5 amplifies the error pair made of the constant mode and the
+ * checkerboard mode by more than 1 per sweep once 108 tau/h^6 (the product
+ * of the tau/h^2, 6/h^2 and 3/h^2 couplings) is of order 1 to 1000, and its
+ * V-cycles then stall or diverge.  The damped collective Jacobi sweep does not
+ * couple the two modes. */
 void pfc_default_params(pfc_params* p);
+
+/* Size, spacing and smoother kind (PFC_SWEEP_*) of multigrid level `level`
+ * (0 = finest) for *p; PFC_EINVAL past the coarsest level.  Host only. */
+int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind);
 
 /* Bytes of device workspace pfc_init needs for *p (0 if *p is invalid). */
 size_t pfc_workspace_bytes(const pfc_params* p);
@@ -193,6 +217,16 @@ int pfc_op_smooth(int n, double h, double eps, double tau, int smoother,
                   const double* d_S1, const double* d_S2, const double* d_S3,
                   const double* d_b, void* stream);
 
+/* `sweeps` damped collective Jacobi sweeps on u = (phi, mu, om): every cell
+ * solves the same pointwise 3x3 system as pfc_op_smooth with the neighbours
+ * of the previous sweep and moves by `weight` of the change.  d_t1..3 are
+ * three scratch fields; the result is in d_phi, d_mu, d_om. */
+int pfc_op_jacobi(int n, double h, double eps, double tau, int smoother,
+                  int sweeps, double weight, double* d_phi, double* d_mu,
+                  double* d_om, double* d_t1, double* d_t2, double* d_t3,
+                  const double* d_S1, const double* d_S2, const double* d_S3,
+                  const double* d_b, void* stream);
+
 /* r = S - N(u) (Algorithm 1 "Residual"), full fine-grid fields. */
 int pfc_op_residual(int n, double h, double eps, double tau,
                     const double* d_phi, const double* d_mu, const double* d_om,
@@ -231,12 +265,13 @@ int pfc_op_prolong_correct(int n, const double* d_vc1, const double* d_vc2,
                            double* d_u1, double* d_u2, double* d_u3,
                            void* stream);
 
-/* Coarsest-level solve of N(u) = S by red-black sweeps until the largest
- * change is below 1e-15 (relative) or max_sweeps; one thread block.  n even,
- * n <= 16. */
+/* Coarsest-level solve of N(u) = S by sweeps until the largest relative
+ * change is below 1e-14 or max_sweeps; one thread block.  kind = PFC_SWEEP_RB
+ * or PFC_SWEEP_JACOBI (weight `weight`, scratch d_t1..3).  n even, n <= 16. */
 int pfc_op_coarse_solve(int n, double h, double eps, double tau, int smoother,
-                        int max_sweeps, double* d_phi, double* d_mu,
-                        double* d_om, const double* d_S1, const double* d_S2,
+                        int kind, double weight, int max_sweeps, double* d_phi,
+                        double* d_mu, double* d_om, double* d_t1, double* d_t2,
+                        double* d_t3, const double* d_S1, const double* d_S2,
                         const double* d_S3, const double* d_b, void* stream);
 
 /* Diagnostics of one field pair (Section 2 norms, Eq. 2.1), blocking:
@@ -280,6 +315,14 @@ int pfc_op_defect(int n, double h, double eps, double tau, const double* d_phi,
  * != 0 declares d = 0 on entry (d need not be initialised).  n even. */
 int pfc_op_lin_smooth(int n, double h, double eps, double tau, int sweeps,
                       int zero_init, float* d_d1, float* d_d2, float* d_d3,
+                      const float* d_r1, const float* d_r2, const float* d_r3,
+                      const float* d_q, void* stream);
+
+/* `sweeps` damped collective Jacobi sweeps in FP32 on J d = r (q frozen),
+ * scratch d_t1..3, result in d_d1..3; zero_init as for pfc_op_lin_smooth. */
+int pfc_op_lin_jacobi(int n, double h, double eps, double tau, int sweeps,
+                      double weight, int zero_init, float* d_d1, float* d_d2,
+                      float* d_d3, float* d_t1, float* d_t2, float* d_t3,
                       const float* d_r1, const float* d_r2, const float* d_r3,
                       const float* d_q, void* stream);
 

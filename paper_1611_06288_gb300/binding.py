@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(PKG, "libpfc.so")
 PFC_OK, PFC_EINVAL, PFC_ESIZE, PFC_ENOCONV, PFC_ENAN, PFC_ECUDA = 0, -1, -2, -3, -4, -5
 PFC_FP64, PFC_MIXED = 0, 1
 PFC_NEWTON, PFC_PICARD = 0, 1
+PFC_POLICY_HYBRID, PFC_POLICY_RB = 0, 1
+PFC_SWEEP_RB, PFC_SWEEP_JACOBI = 0, 1
 
 
 class PFCError(RuntimeError):
@@ -33,7 +35,10 @@ class pfc_params(ctypes.Structure):
                 ("dt", ctypes.c_double), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
                 ("tol", ctypes.c_double), ("max_cycles", ctypes.c_int),
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("coarsest", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("coarsest", ctypes.c_int), ("inner_cycles", ctypes.c_int),
+                ("policy", ctypes.c_int), ("jacobi_weight", ctypes.c_double),
+                ("jacobi_factor", ctypes.c_int), ("stiff_hi", ctypes.c_double),
+                ("stiff_lo", ctypes.c_double)]
 
 
 class pfc_step_stats(ctypes.Structure):
@@ -72,7 +77,11 @@ _SIGS = {
     "pfc_op_restrict": (_I, [_I, _P, _P, _P]),
     "pfc_op_coarse_source": (_I, [_I, _D, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_prolong_correct": (_I, [_I] + [_P] * 9 + [_P]),
-    "pfc_op_coarse_solve": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
+    "pfc_op_coarse_solve": (_I, [_I, _D, _D, _D, _I, _I, _D, _I] + [_P] * 10 + [_P]),
+    "pfc_op_jacobi": (_I, [_I, _D, _D, _D, _I, _I, _D] + [_P] * 10 + [_P]),
+    "pfc_op_lin_jacobi": (_I, [_I, _D, _D, _D, _I, _D, _I] + [_P] * 10 + [_P]),
+    "pfc_level_info": (_I, [ctypes.POINTER(pfc_params), _I, ctypes.POINTER(_I),
+                            ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "pfc_reduce_scratch_bytes": (_SZ, [_I]),
     "pfc_op_diagnostics": (_I, [_I, _D, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "pfc_op_residual_norm": (_I, [_I, _D, _D, _D] + [_P] * 8 + [ctypes.POINTER(_D), _P]),
@@ -266,11 +275,34 @@ def pfc_op_prolong_correct(n, vc1, vc2, vc3, wc1, wc2, wc3, u1, u2, u3, stream=N
           "pfc_op_prolong_correct")
 
 
-def pfc_op_coarse_solve(n, h, eps, tau, smoother, max_sweeps, phi, mu, om, S1, S2, S3, b,
-                        stream=None):
-    check(lib().pfc_op_coarse_solve(n, h, eps, tau, smoother, max_sweeps, ptr(phi), ptr(mu),
-                                    ptr(om), ptr(S1), ptr(S2), ptr(S3), ptr(b), stream),
+def pfc_op_coarse_solve(n, h, eps, tau, smoother, kind, weight, max_sweeps, phi, mu, om,
+                        t1, t2, t3, S1, S2, S3, b, stream=None):
+    check(lib().pfc_op_coarse_solve(n, h, eps, tau, smoother, kind, weight, max_sweeps,
+                                    ptr(phi), ptr(mu), ptr(om), ptr(t1), ptr(t2), ptr(t3),
+                                    ptr(S1), ptr(S2), ptr(S3), ptr(b), stream),
           "pfc_op_coarse_solve")
+
+
+def pfc_op_jacobi(n, h, eps, tau, smoother, sweeps, weight, phi, mu, om, t1, t2, t3,
+                  S1, S2, S3, b, stream=None):
+    check(lib().pfc_op_jacobi(n, h, eps, tau, smoother, sweeps, weight, ptr(phi), ptr(mu),
+                              ptr(om), ptr(t1), ptr(t2), ptr(t3), ptr(S1), ptr(S2), ptr(S3),
+                              ptr(b), stream), "pfc_op_jacobi")
+
+
+def pfc_op_lin_jacobi(n, h, eps, tau, sweeps, weight, zero_init, d1, d2, d3, t1, t2, t3,
+                      r1, r2, r3, q, stream=None):
+    check(lib().pfc_op_lin_jacobi(n, h, eps, tau, sweeps, weight, int(bool(zero_init)),
+                                  ptr(d1), ptr(d2), ptr(d3), ptr(t1), ptr(t2), ptr(t3),
+                                  ptr(r1), ptr(r2), ptr(r3), ptr(q), stream),
+          "pfc_op_lin_jacobi")
+
+
+def pfc_level_info(p: pfc_params, level: int):
+    n, h, kind = ctypes.c_int(), ctypes.c_double(), ctypes.c_int()
+    check(lib().pfc_level_info(ctypes.byref(p), level, ctypes.byref(n), ctypes.byref(h),
+                               ctypes.byref(kind)), "pfc_level_info")
+    return n.value, h.value, kind.value
 
 
 def pfc_reduce_scratch_bytes(n) -> int:

@@ -57,6 +57,10 @@ int validate(const pfc_params* p) {
   if (p->precision != PFC_FP64 && p->precision != PFC_MIXED) return PFC_EINVAL;
   if (p->smoother != PFC_NEWTON && p->smoother != PFC_PICARD) return PFC_EINVAL;
   if (p->precision == PFC_MIXED && p->inner_cycles < 1) return PFC_EINVAL;
+  if (p->policy != PFC_POLICY_HYBRID && p->policy != PFC_POLICY_RB) return PFC_EINVAL;
+  if (!(p->jacobi_weight > 0 && p->jacobi_weight <= 1) || p->jacobi_factor < 1)
+    return PFC_EINVAL;
+  if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -79,8 +83,10 @@ struct Carver {
 
 struct Level64 {
   int n;
+  int kind;          // PFC_SWEEP_RB or PFC_SWEEP_JACOBI
   Lvl L;
   double *u[3], *w[3], *S[3], *b;   // level 0 uses only the ring/context fields
+  double* t[3];      // Jacobi ping-pong partner of u (and coarse-solve scratch)
 };
 
 }  // namespace pfc
@@ -94,6 +100,7 @@ struct pfc_ctx {
   double* ring[3];   // phi^{k-1}, phi^k, phi^{k+1} rotate through these
   int ic, ib, ia;
   double *mu, *om, *S2, *S3;
+  double* t0[3];     // level-0 Jacobi scratch
   double* partials;  // reduction partial sums
   double* dout;      // 8 device doubles of reduction results
   double* hout;      // 8 pinned host doubles
@@ -118,6 +125,11 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
   double* om = cv.take<double>(n3);
   double* S2 = cv.take<double>(n3);
   double* S3 = cv.take<double>(n3);
+  const bool fp64 = p->precision == PFC_FP64;
+  for (int q = 0; q < 3; ++q) {
+    double* f = fp64 ? cv.take<double>(n3) : nullptr;
+    if (c) c->t0[q] = f;
+  }
   if (c) {
     c->mu = mu;
     c->om = om;
@@ -126,13 +138,15 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
     c->nl = nl;
     for (int l = 0; l < nl; ++l) c->sizes[l] = sizes[l];
   }
-  for (int l = 1; l < nl; ++l) {
+  // the FP64 coarse hierarchy is used by the FAS path only
+  for (int l = 1; l < nl && fp64; ++l) {
     const int64_t m3 = (int64_t)sizes[l] * sizes[l] * sizes[l];
     Level64 lv;
     for (int q = 0; q < 3; ++q) lv.u[q] = cv.take<double>(m3);
     for (int q = 0; q < 3; ++q) lv.w[q] = cv.take<double>(m3);
     for (int q = 0; q < 3; ++q) lv.S[q] = cv.take<double>(m3);
     lv.b = cv.take<double>(m3);
+    for (int q = 0; q < 3; ++q) lv.t[q] = cv.take<double>(m3);
     if (c) c->lev[l] = lv;
   }
   double* partials = cv.take<double>((size_t)kReduceBlocks * kReduceComps);
@@ -160,6 +174,27 @@ void level0(pfc_ctx* c, Level64* lv) {
   lv->S[1] = c->S2;
   lv->S[2] = c->S3;
   lv->b = c->ring[c->ib];
+  lv->kind = c->lev[0].kind;
+  for (int q = 0; q < 3; ++q) lv->t[q] = c->t0[q];
+}
+
+// Pre- or post-smoothing of one level under the level's smoother kind.
+int smooth_level(pfc_ctx* c, int l, const Level64& lv, int sweeps) {
+  if (sweeps <= 0) return PFC_OK;
+  cudaStream_t st = c->st;
+  Prof* pr = &c->prof;
+  if (lv.kind == PFC_SWEEP_JACOBI) {
+    const int js = sweeps * c->p.jacobi_factor;
+    PFC_TIMED(pr, PFC_K_SMOOTH, l, js, st,
+              launch_jacobi(lv.L, c->p.smoother, js, c->p.jacobi_weight, lv.u[0], lv.u[1],
+                            lv.u[2], lv.t[0], lv.t[1], lv.t[2], lv.S[0], lv.S[1], lv.S[2],
+                            lv.b, st));
+  } else {
+    PFC_TIMED(pr, PFC_K_SMOOTH, l, 2 * sweeps, st,
+              launch_smooth(lv.L, c->p.smoother, sweeps, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
+                            lv.S[1], lv.S[2], lv.b, st));
+  }
+  return PFC_OK;
 }
 
 int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
@@ -168,15 +203,14 @@ int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
   Prof* pr = &c->prof;
   if (l == c->nl - 1) {
     PFC_TIMED(pr, PFC_K_COARSE_SOLVE, l, 1, st,
-              launch_coarse_solve(lv.L, lin, 200, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
+              launch_coarse_solve(lv.L, lin, lv.kind, c->p.jacobi_weight, 400, lv.u[0],
+                                  lv.u[1], lv.u[2], lv.t[0], lv.t[1], lv.t[2], lv.S[0],
                                   lv.S[1], lv.S[2], lv.b, st));
     return PFC_OK;
   }
   Level64& cl = c->lev[l + 1];
-  if (c->p.nu1 > 0)
-    PFC_TIMED(pr, PFC_K_SMOOTH, l, 2 * c->p.nu1, st,
-              launch_smooth(lv.L, lin, c->p.nu1, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
-                            lv.S[1], lv.S[2], lv.b, st));
+  int rc0 = smooth_level(c, l, lv, c->p.nu1);
+  if (rc0) return rc0;
   PFC_TIMED(pr, PFC_K_RESIDUAL_RESTRICT, l, 1, st,
             launch_residual_restrict(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
                                      lv.S[2], lv.b, cl.S[0], cl.S[1], cl.S[2], cl.u[0],
@@ -192,11 +226,7 @@ int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
   PFC_CUDA(launch_prolong_add(lv.n, cl.w[0], cl.w[1], cl.w[2], lv.u[0], lv.u[1], lv.u[2],
                               st));
   prof_end(pr, PFC_K_PROLONG, l, 2, st);
-  if (c->p.nu2 > 0)
-    PFC_TIMED(pr, PFC_K_SMOOTH, l, 2 * c->p.nu2, st,
-              launch_smooth(lv.L, lin, c->p.nu2, lv.u[0], lv.u[1], lv.u[2], lv.S[0],
-                            lv.S[1], lv.S[2], lv.b, st));
-  return PFC_OK;
+  return smooth_level(c, l, lv, c->p.nu2);
 }
 
 // RMS residual of the level-0 iterate; blocking readback.
@@ -325,6 +355,23 @@ void pfc_default_params(pfc_params* p) {
   p->smoother = PFC_NEWTON;
   p->coarsest = 2;
   p->inner_cycles = 1;
+  p->policy = PFC_POLICY_HYBRID;
+  p->jacobi_weight = 0.7;
+  p->jacobi_factor = 2;
+  p->stiff_hi = 1000.0;
+  p->stiff_lo = 0.02;
+}
+
+int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {
+  if (validate(p) != PFC_OK || level < 0) return PFC_EINVAL;
+  int sizes[kMaxLevels];
+  const int nl = level_sizes(p, sizes);
+  if (level >= nl) return PFC_EINVAL;
+  const double hl = p->L / p->n * (double)(1 << level);
+  if (n) *n = sizes[level];
+  if (h) *h = hl;
+  if (kind) *kind = level_kind(p, hl);
+  return PFC_OK;
 }
 
 size_t pfc_workspace_bytes(const pfc_params* p) {
@@ -358,6 +405,7 @@ int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
   for (int l = 0; l < c->nl; ++l) {
     c->lev[l].n = c->sizes[l];
     c->lev[l].L = make_lvl(c->sizes[l], h, p->eps, p->dt);
+    c->lev[l].kind = level_kind(p, h);
     h *= 2.0;
   }
   e = cudaHostAlloc((void**)&c->hout, kReduceComps * sizeof(double), cudaHostAllocDefault);
@@ -586,16 +634,47 @@ int pfc_op_prolong_correct(int n, const double* vc1, const double* vc2, const do
   return PFC_OK;
 }
 
-int pfc_op_coarse_solve(int n, double h, double eps, double tau, int smoother,
-                        int max_sweeps, double* phi, double* mu, double* om,
-                        const double* S1, const double* S2, const double* S3,
-                        const double* b, void* stream) {
+int pfc_op_coarse_solve(int n, double h, double eps, double tau, int smoother, int kind,
+                        double weight, int max_sweeps, double* phi, double* mu, double* om,
+                        double* t1, double* t2, double* t3, const double* S1,
+                        const double* S2, const double* S3, const double* b,
+                        void* stream) {
   if (n < 2 || (n & 1) || n > 16 || max_sweeps < 1 || !phi || !mu || !om || !S1 || !S2 ||
       !S3 || !b)
     return PFC_EINVAL;
   if (smoother != PFC_NEWTON && smoother != PFC_PICARD) return PFC_EINVAL;
-  PFC_CUDA(launch_coarse_solve(make_lvl(n, h, eps, tau), smoother, max_sweeps, phi, mu, om,
-                               S1, S2, S3, b, (cudaStream_t)stream));
+  if (kind != PFC_SWEEP_RB && kind != PFC_SWEEP_JACOBI) return PFC_EINVAL;
+  if (kind == PFC_SWEEP_JACOBI && (!t1 || !t2 || !t3 || !(weight > 0 && weight <= 1)))
+    return PFC_EINVAL;
+  PFC_CUDA(launch_coarse_solve(make_lvl(n, h, eps, tau), smoother, kind, weight, max_sweeps,
+                               phi, mu, om, t1, t2, t3, S1, S2, S3, b,
+                               (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_jacobi(int n, double h, double eps, double tau, int smoother, int sweeps,
+                  double weight, double* phi, double* mu, double* om, double* t1, double* t2,
+                  double* t3, const double* S1, const double* S2, const double* S3,
+                  const double* b, void* stream) {
+  if (n < 1 || sweeps < 0 || !phi || !mu || !om || !t1 || !t2 || !t3 || !S1 || !S2 || !S3 ||
+      !b || !(weight > 0 && weight <= 1))
+    return PFC_EINVAL;
+  if (smoother != PFC_NEWTON && smoother != PFC_PICARD) return PFC_EINVAL;
+  PFC_CUDA(launch_jacobi(make_lvl(n, h, eps, tau), smoother, sweeps, weight, phi, mu, om, t1,
+                         t2, t3, S1, S2, S3, b, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_lin_jacobi(int n, double h, double eps, double tau, int sweeps, double weight,
+                      int zero_init, float* d1, float* d2, float* d3, float* t1, float* t2,
+                      float* t3, const float* r1, const float* r2, const float* r3,
+                      const float* q, void* stream) {
+  if (n < 1 || sweeps < 0 || !d1 || !d2 || !d3 || !t1 || !t2 || !t3 || !r1 || !r2 || !r3 ||
+      !q || !(weight > 0 && weight <= 1))
+    return PFC_EINVAL;
+  PFC_CUDA(launch_lin_jacobi32(make_lvl(n, h, eps, tau), sweeps, (float)weight,
+                               zero_init != 0, d1, d2, d3, t1, t2, t3, r1, r2, r3, q,
+                               (cudaStream_t)stream));
   return PFC_OK;
 }
 

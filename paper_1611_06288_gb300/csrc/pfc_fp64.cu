@@ -67,6 +67,34 @@ __global__ void k_smooth_colour(Lvl L, int colour, double* phi, double* mu, doub
 }
 
 // ---------------------------------------------------------------------------
+// a2/a7 on levels of intermediate stiffness: one damped collective Jacobi
+// sweep, (phi, mu, om) -> (tp, tm, tw).  Every cell solves the same pointwise
+// system with the neighbours of the previous sweep and moves by w of the
+// change.
+// ---------------------------------------------------------------------------
+template <int LIN>
+__global__ void k_jacobi64(Lvl L, double w, const double* __restrict__ phi,
+                           const double* __restrict__ mu, const double* __restrict__ om,
+                           double* __restrict__ tp, double* __restrict__ tm,
+                           double* __restrict__ tw, const double* __restrict__ S1,
+                           const double* __restrict__ S2, const double* __restrict__ S3,
+                           const double* __restrict__ b) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  const double p0 = __ldg(phi + s.c), m0 = __ldg(mu + s.c), w0 = __ldg(om + s.c);
+  double np, nm, nw;
+  point_solve<LIN>(L, nbsum(phi, s), nbsum(mu, s), nbsum(om, s), p0, __ldg(b + s.c),
+                   __ldg(S1 + s.c), __ldg(S2 + s.c), __ldg(S3 + s.c), np, nm, nw);
+  tp[s.c] = fma(w, np - p0, p0);
+  tm[s.c] = fma(w, nm - m0, m0);
+  tw[s.c] = fma(w, nw - w0, w0);
+}
+
+// ---------------------------------------------------------------------------
 // a3: residual r = S - N(u), full fields (used by the primitive op)
 // ---------------------------------------------------------------------------
 __global__ void k_residual(Lvl L, const double* __restrict__ phi,
@@ -227,39 +255,68 @@ __global__ void k_prolong_add(int n, const double* __restrict__ e1,
 }
 
 // ---------------------------------------------------------------------------
-// a5: coarsest level: red-black sweeps in one thread block until the largest
-// relative change falls below 1e-14 or max_sweeps.  Neighbours are read with
-// coherent loads because this block wrote them in the previous half-sweep.
+// a5: coarsest level: sweeps in one thread block until the largest relative
+// change falls below 1e-14 or max_sweeps.  Red-black (kind 0) updates in
+// place; damped Jacobi (kind 1) computes every cell into t and copies back.
+// Neighbours are read with coherent loads because this block wrote them in
+// the previous half-sweep.
 // ---------------------------------------------------------------------------
 template <int LIN>
-__global__ void k_coarse_solve(Lvl L, int max_sweeps, double* phi, double* mu, double* om,
+__global__ void k_coarse_solve(Lvl L, int kind, double w, int max_sweeps, double* phi,
+                               double* mu, double* om, double* t1, double* t2, double* t3,
                                const double* S1, const double* S2, const double* S3,
                                const double* b) {
   __shared__ double red[32];
   __shared__ int done;
   const int n = L.n, half = n >> 1;
-  const int cells = half * n * n;
+  const int ncell = n * n * n;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double change = 0.0;
-    for (int colour = 0; colour < 2; ++colour) {
-      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-        const int p = t % half, r = t / half;
-        const int j = r % n, k = r / n;
-        const int i = 2 * p + ((j + k + colour) & 1);
+    if (kind == PFC_SWEEP_JACOBI) {
+      for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+        const int i = t % n, j = (t / n) % n, k = t / (n * n);
         const Stencil s = stencil_at(i, j, k, n);
-        const double op = phi[s.c], om_ = mu[s.c], ow = om[s.c];
+        const double p0 = phi[s.c], m0 = mu[s.c], w0 = om[s.c];
         double np, nm, nw;
         point_solve<LIN>(L, nbsum_coherent(phi, s), nbsum_coherent(mu, s),
-                         nbsum_coherent(om, s), op, b[s.c], S1[s.c], S2[s.c], S3[s.c],
-                         np, nm, nw);
-        phi[s.c] = np;
-        mu[s.c] = nm;
-        om[s.c] = nw;
-        change = fmax(change, fabs(np - op) / (1.0 + fabs(np)));
-        change = fmax(change, fabs(nm - om_) / (1.0 + fabs(nm)));
-        change = fmax(change, fabs(nw - ow) / (1.0 + fabs(nw)));
+                         nbsum_coherent(om, s), p0, b[s.c], S1[s.c], S2[s.c], S3[s.c], np,
+                         nm, nw);
+        t1[s.c] = fma(w, np - p0, p0);
+        t2[s.c] = fma(w, nm - m0, m0);
+        t3[s.c] = fma(w, nw - w0, w0);
       }
       __syncthreads();
+      for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+        change = fmax(change, fabs(t1[t] - phi[t]) / (1.0 + fabs(t1[t])));
+        change = fmax(change, fabs(t2[t] - mu[t]) / (1.0 + fabs(t2[t])));
+        change = fmax(change, fabs(t3[t] - om[t]) / (1.0 + fabs(t3[t])));
+        phi[t] = t1[t];
+        mu[t] = t2[t];
+        om[t] = t3[t];
+      }
+      __syncthreads();
+    } else {
+      const int cells = half * n * n;
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+          const int p = t % half, r = t / half;
+          const int j = r % n, k = r / n;
+          const int i = 2 * p + ((j + k + colour) & 1);
+          const Stencil s = stencil_at(i, j, k, n);
+          const double op = phi[s.c], om_ = mu[s.c], ow = om[s.c];
+          double np, nm, nw;
+          point_solve<LIN>(L, nbsum_coherent(phi, s), nbsum_coherent(mu, s),
+                           nbsum_coherent(om, s), op, b[s.c], S1[s.c], S2[s.c], S3[s.c],
+                           np, nm, nw);
+          phi[s.c] = np;
+          mu[s.c] = nm;
+          om[s.c] = nw;
+          change = fmax(change, fabs(np - op) / (1.0 + fabs(np)));
+          change = fmax(change, fabs(nm - om_) / (1.0 + fabs(nm)));
+          change = fmax(change, fabs(nw - ow) / (1.0 + fabs(nw)));
+        }
+        __syncthreads();
+      }
     }
     // block max of the change
     for (int o = 16; o > 0; o >>= 1) change = fmax(change, __shfl_down_sync(0xffffffffu, change, o));
@@ -267,7 +324,7 @@ __global__ void k_coarse_solve(Lvl L, int max_sweeps, double* phi, double* mu, d
     __syncthreads();
     if (threadIdx.x == 0) {
       double m = 0.0;
-      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) m = fmax(m, red[w]);
+      for (int q = 0; q < (int)((blockDim.x + 31) >> 5); ++q) m = fmax(m, red[q]);
       done = (m < 1e-14);
     }
     __syncthreads();
@@ -384,6 +441,35 @@ cudaError_t launch_smooth(const Lvl& L, int lin, int sweeps, double* phi, double
   return cudaGetLastError();
 }
 
+cudaError_t launch_jacobi(const Lvl& L, int lin, int sweeps, double w, double* phi,
+                          double* mu, double* om, double* t1, double* t2, double* t3,
+                          const double* S1, const double* S2, const double* S3,
+                          const double* b, cudaStream_t st) {
+  const int64_t cells = (int64_t)L.n * L.n * L.n;
+  double* src[3] = {phi, mu, om};
+  double* dst[3] = {t1, t2, t3};
+  for (int s = 0; s < sweeps; ++s) {
+    if (lin == PFC_NEWTON)
+      k_jacobi64<PFC_NEWTON><<<grid_for(cells), kThreads, 0, st>>>(
+          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], S1, S2, S3, b);
+    else
+      k_jacobi64<PFC_PICARD><<<grid_for(cells), kThreads, 0, st>>>(
+          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], S1, S2, S3, b);
+    for (int q = 0; q < 3; ++q) {
+      double* x = src[q];
+      src[q] = dst[q];
+      dst[q] = x;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && (sweeps & 1)) {
+    for (int q = 0; q < 3 && e == cudaSuccess; ++q)
+      e = cudaMemcpyAsync(q == 0 ? phi : q == 1 ? mu : om, src[q], cells * sizeof(double),
+                          cudaMemcpyDeviceToDevice, st);
+  }
+  return e;
+}
+
 cudaError_t launch_residual(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, double* r1, double* r2,
@@ -438,19 +524,19 @@ cudaError_t launch_prolong_add(int n, const double* e1, const double* e2,
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_solve(const Lvl& L, int lin, int max_sweeps, double* phi,
-                                double* mu, double* om, const double* S1,
-                                const double* S2, const double* S3, const double* b,
-                                cudaStream_t st) {
-  const int work = (L.n / 2) * L.n * L.n;
+cudaError_t launch_coarse_solve(const Lvl& L, int lin, int kind, double w, int max_sweeps,
+                                double* phi, double* mu, double* om, double* t1, double* t2,
+                                double* t3, const double* S1, const double* S2,
+                                const double* S3, const double* b, cudaStream_t st) {
+  const int work = L.n * L.n * L.n;
   int threads = ((work + 31) / 32) * 32;
   if (threads > 1024) threads = 1024;
   if (lin == PFC_NEWTON)
-    k_coarse_solve<PFC_NEWTON><<<1, threads, 0, st>>>(L, max_sweeps, phi, mu, om, S1, S2,
-                                                       S3, b);
+    k_coarse_solve<PFC_NEWTON><<<1, threads, 0, st>>>(L, kind, w, max_sweeps, phi, mu, om,
+                                                       t1, t2, t3, S1, S2, S3, b);
   else
-    k_coarse_solve<PFC_PICARD><<<1, threads, 0, st>>>(L, max_sweeps, phi, mu, om, S1, S2,
-                                                       S3, b);
+    k_coarse_solve<PFC_PICARD><<<1, threads, 0, st>>>(L, kind, w, max_sweeps, phi, mu, om,
+                                                       t1, t2, t3, S1, S2, S3, b);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,12 @@ cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double
 cudaError_t launch_smooth(const Lvl& L, int lin, int sweeps, double* phi, double* mu,
                           double* om, const double* S1, const double* S2,
                           const double* S3, const double* b, cudaStream_t st);
+// `sweeps` damped collective Jacobi sweeps ping-ponging through t1..3; the
+// result is left in phi, mu, om.
+cudaError_t launch_jacobi(const Lvl& L, int lin, int sweeps, double w, double* phi,
+                          double* mu, double* om, double* t1, double* t2, double* t3,
+                          const double* S1, const double* S2, const double* S3,
+                          const double* b, cudaStream_t st);
 cudaError_t launch_residual(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, double* r1, double* r2,
@@ -61,10 +67,17 @@ cudaError_t launch_coarse_diff(int nc, const double* v1, const double* v2,
 cudaError_t launch_prolong_add(int n, const double* e1, const double* e2,
                                const double* e3, double* u1, double* u2, double* u3,
                                cudaStream_t st);
-cudaError_t launch_coarse_solve(const Lvl& L, int lin, int max_sweeps, double* phi,
-                                double* mu, double* om, const double* S1,
-                                const double* S2, const double* S3, const double* b,
-                                cudaStream_t st);
+cudaError_t launch_coarse_solve(const Lvl& L, int lin, int kind, double w, int max_sweeps,
+                                double* phi, double* mu, double* om, double* t1, double* t2,
+                                double* t3, const double* S1, const double* S2,
+                                const double* S3, const double* b, cudaStream_t st);
+
+// Smoother kind of a level of spacing h under the parameters' policy.
+inline int level_kind(const pfc_params* p, double h) {
+  if (p->policy == PFC_POLICY_RB) return PFC_SWEEP_RB;
+  const double s = 108.0 * p->dt / (h * h * h * h * h * h);
+  return (s > p->stiff_lo && s < p->stiff_hi) ? PFC_SWEEP_JACOBI : PFC_SWEEP_RB;
+}
 // Sum over cells of r1^2 + r2^2 + r3^2 -> partials (one per block), then the
 // fixed-order final sum into out[0] (device).
 cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double* mu,

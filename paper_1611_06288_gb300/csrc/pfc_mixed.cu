@@ -139,6 +139,38 @@ __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* 
   d3[s.c] = dw;
 }
 
+// One damped collective Jacobi sweep on J d = r, d -> t.  ZERO: d = 0 on
+// entry (nothing is read from d).
+template <bool ZERO>
+__global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
+                               const float* __restrict__ d2, const float* __restrict__ d3,
+                               float* __restrict__ t1, float* __restrict__ t2,
+                               float* __restrict__ t3, const float* __restrict__ r1,
+                               const float* __restrict__ r2, const float* __restrict__ r3,
+                               const float* __restrict__ q) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
+  if (!ZERO) {
+    sp = nbsum(d1, s);
+    sm_ = nbsum(d2, s);
+    sw = nbsum(d3, s);
+    p0 = __ldg(d1 + s.c);
+    m0 = __ldg(d2 + s.c);
+    w0 = __ldg(d3 + s.c);
+  }
+  float dp, dm, dw;
+  lin_point(L, sp, sm_, sw, __ldg(q + s.c), __ldg(r1 + s.c), __ldg(r2 + s.c),
+            __ldg(r3 + s.c), dp, dm, dw);
+  t1[s.c] = fmaf(w, dp - p0, p0);
+  t2[s.c] = fmaf(w, dm - m0, m0);
+  t3[s.c] = fmaf(w, dw - w0, w0);
+}
+
 // rho = r - J d at the 8 children of each coarse cell, averaged.
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
@@ -208,12 +240,13 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
   d3[t] = fmaf(w, interp8f(e3, o000, o100, o010, o001, o110, o101, o011, o111), d3[t]);
 }
 
-// Coarsest level of the linear problem: start from zero, red-black sweeps in
-// one block until the largest change is below 1e-7 of the largest value or
-// max_sweeps.
-__global__ void k_lin_coarse_solve32(LvlF L, int max_sweeps, float* d1, float* d2,
-                                     float* d3, const float* r1, const float* r2,
-                                     const float* r3, const float* q) {
+// Coarsest level of the linear problem: start from zero, sweeps in one block
+// (red-black, kind 0, or damped Jacobi through t, kind 1) until the largest
+// change is below 1e-7 of the largest value or max_sweeps.
+__global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, float* d1,
+                                     float* d2, float* d3, float* t1, float* t2, float* t3,
+                                     const float* r1, const float* r2, const float* r3,
+                                     const float* q) {
   __shared__ float red[2][32];
   __shared__ int done;
   const int n = L.n, half = n >> 1;
@@ -226,23 +259,46 @@ __global__ void k_lin_coarse_solve32(LvlF L, int max_sweeps, float* d1, float* d
   __syncthreads();
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     float change = 0.f, size = 0.f;
-    for (int colour = 0; colour < 2; ++colour) {
-      for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
-        const int p = t % half, r = t / half;
-        const int j = r % n, k = r / n;
-        const int i = 2 * p + ((j + k + colour) & 1);
+    if (kind == PFC_SWEEP_JACOBI) {
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        const int i = t % n, j = (t / n) % n, k = t / (n * n);
         const Stencil s = stencil_at(i, j, k, n);
         float dp, dm, dw;
         lin_point(L, nbsum_coherent(d1, s), nbsum_coherent(d2, s), nbsum_coherent(d3, s),
                   q[s.c], r1[s.c], r2[s.c], r3[s.c], dp, dm, dw);
-        change = fmaxf(change, fmaxf(fabsf(dp - d1[s.c]),
-                                     fmaxf(fabsf(dm - d2[s.c]), fabsf(dw - d3[s.c]))));
-        size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
-        d1[s.c] = dp;
-        d2[s.c] = dm;
-        d3[s.c] = dw;
+        t1[s.c] = fmaf(w, dp - d1[s.c], d1[s.c]);
+        t2[s.c] = fmaf(w, dm - d2[s.c], d2[s.c]);
+        t3[s.c] = fmaf(w, dw - d3[s.c], d3[s.c]);
       }
       __syncthreads();
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        change = fmaxf(change, fmaxf(fabsf(t1[t] - d1[t]),
+                                     fmaxf(fabsf(t2[t] - d2[t]), fabsf(t3[t] - d3[t]))));
+        size = fmaxf(size, fmaxf(fabsf(t1[t]), fmaxf(fabsf(t2[t]), fabsf(t3[t]))));
+        d1[t] = t1[t];
+        d2[t] = t2[t];
+        d3[t] = t3[t];
+      }
+      __syncthreads();
+    } else {
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
+          const int p = t % half, r = t / half;
+          const int j = r % n, k = r / n;
+          const int i = 2 * p + ((j + k + colour) & 1);
+          const Stencil s = stencil_at(i, j, k, n);
+          float dp, dm, dw;
+          lin_point(L, nbsum_coherent(d1, s), nbsum_coherent(d2, s), nbsum_coherent(d3, s),
+                    q[s.c], r1[s.c], r2[s.c], r3[s.c], dp, dm, dw);
+          change = fmaxf(change, fmaxf(fabsf(dp - d1[s.c]),
+                                       fmaxf(fabsf(dm - d2[s.c]), fabsf(dw - d3[s.c]))));
+          size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+          d1[s.c] = dp;
+          d2[s.c] = dm;
+          d3[s.c] = dw;
+        }
+        __syncthreads();
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       change = fmaxf(change, __shfl_down_sync(0xffffffffu, change, o));
@@ -255,9 +311,9 @@ __global__ void k_lin_coarse_solve32(LvlF L, int max_sweeps, float* d1, float* d
     __syncthreads();
     if (threadIdx.x == 0) {
       float c = 0.f, z = 0.f;
-      for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) {
-        c = fmaxf(c, red[0][w]);
-        z = fmaxf(z, red[1][w]);
+      for (int v = 0; v < (int)((blockDim.x + 31) >> 5); ++v) {
+        c = fmaxf(c, red[0][v]);
+        z = fmaxf(z, red[1][v]);
       }
       done = (c <= 1e-7f * z);
     }
@@ -286,9 +342,38 @@ struct Ctx32 {
   const pfc_params* p;
   int nl;
   LvlF L[kMaxLevelsMixed];
+  int kind[kMaxLevelsMixed];   // PFC_SWEEP_RB or PFC_SWEEP_JACOBI per level
+  float w;                     // Jacobi weight
+  int jfactor;                 // Jacobi sweeps per requested sweep
   cudaStream_t st;
   Prof* pr;
 };
+
+cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* const* d,
+                     float* const* t, float* const* r, const float* q, cudaStream_t st) {
+  const int64_t cells = (int64_t)L.n * L.n * L.n;
+  float* src[3] = {d[0], d[1], d[2]};
+  float* dst[3] = {t[0], t[1], t[2]};
+  for (int s = 0; s < sweeps; ++s) {
+    if (zero_init && s == 0)
+      k_lin_jacobi32<true><<<grid_for(cells), kThreads, 0, st>>>(
+          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    else
+      k_lin_jacobi32<false><<<grid_for(cells), kThreads, 0, st>>>(
+          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    for (int c = 0; c < 3; ++c) {
+      float* x = src[c];
+      src[c] = dst[c];
+      dst[c] = x;
+    }
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && (sweeps & 1)) {
+    for (int c = 0; c < 3 && e == cudaSuccess; ++c)
+      e = cudaMemcpyAsync(d[c], src[c], cells * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  }
+  return e;
+}
 
 cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   const LvlF& L = c.L[l];
@@ -298,6 +383,12 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   const float* q = c.mx->q[l];
   if (sweeps <= 0) return cudaSuccess;
   prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
+  if (c.kind[l] == PFC_SWEEP_JACOBI) {
+    const int js = sweeps * c.jfactor;
+    cudaError_t e = jacobi32(L, js, c.w, zero_init, d, c.mx->t[l], r, q, c.st);
+    prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
+    return e;
+  }
   for (int s = 0; s < sweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       if (zero_init && s == 0 && colour == 0)
@@ -316,13 +407,13 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
   if (l == c.nl - 1) {
-    const int work = (L.n / 2) * L.n * L.n;
+    const int work = L.n * L.n * L.n;
     int threads = ((work + 31) / 32) * 32;
     if (threads > 1024) threads = 1024;
     prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
-    k_lin_coarse_solve32<<<1, threads, 0, c.st>>>(L, 200, mx.d[l][0], mx.d[l][1],
-                                                  mx.d[l][2], mx.r[l][0], mx.r[l][1],
-                                                  mx.r[l][2], mx.q[l]);
+    k_lin_coarse_solve32<<<1, threads, 0, c.st>>>(
+        L, c.kind[l], c.w, 400, mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.t[l][0], mx.t[l][1],
+        mx.t[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l]);
     prof_end(c.pr, PFC_K_LIN_COARSE, l, 1, c.st);
     return cudaGetLastError();
   }
@@ -385,9 +476,22 @@ cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float*
   c.p = nullptr;
   c.nl = 1;
   c.L[0] = to_f32(L);
+  c.kind[0] = PFC_SWEEP_RB;
+  c.w = 1.f;
+  c.jfactor = 1;
   c.st = st;
   c.pr = nullptr;
   return smooth32(c, 0, sweeps, zero_init);
+}
+
+cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_init,
+                                float* d1, float* d2, float* d3, float* t1, float* t2,
+                                float* t3, const float* r1, const float* r2, const float* r3,
+                                const float* q, cudaStream_t st) {
+  float* d[3] = {d1, d2, d3};
+  float* t[3] = {t1, t2, t3};
+  float* r[3] = {(float*)r1, (float*)r2, (float*)r3};
+  return jacobi32(to_f32(L), sweeps, w, zero_init, d, t, r, q, st);
 }
 
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
@@ -407,10 +511,13 @@ int mixed_solve(MixedBufs& mx, const Lvl& L0, const pfc_params& p, int nl,
   c.nl = nl;
   c.st = st;
   c.pr = pr;
+  c.w = (float)p.jacobi_weight;
+  c.jfactor = p.jacobi_factor;
   {
     double h = p.L / p.n;
     for (int l = 0; l < nl; ++l) {
       c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
+      c.kind[l] = level_kind(&p, h);
       h *= 2.0;
     }
   }

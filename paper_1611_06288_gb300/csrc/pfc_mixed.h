@@ -28,6 +28,7 @@ constexpr int kMaxLevelsMixed = 24;
 
 struct MixedBufs {
   float* d[kMaxLevelsMixed][3];   // correction (d_phi, d_mu, d_om) per level
+  float* t[kMaxLevelsMixed][3];   // Jacobi ping-pong partner of d
   float* r[kMaxLevelsMixed][3];   // right-hand side per level
   float* q[kMaxLevelsMixed];      // frozen cubic-term Jacobian + (1-eps)/2
 };
@@ -38,6 +39,7 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
   for (int l = 0; l < nl; ++l) {
     const size_t m3 = (size_t)sizes[l] * sizes[l] * sizes[l];
     for (int c = 0; c < 3; ++c) mx->d[l][c] = take(m3);
+    for (int c = 0; c < 3; ++c) mx->t[l][c] = take(m3);
     for (int c = 0; c < 3; ++c) mx->r[l][c] = take(m3);
     mx->q[l] = take(m3);
   }
@@ -60,6 +62,10 @@ cudaError_t launch_residual64_to32(const Lvl& L, const double* phi, const double
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
                                 float* d2, float* d3, const float* r1, const float* r2,
                                 const float* r3, const float* q, cudaStream_t st);
+cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_init,
+                                float* d1, float* d2, float* d3, float* t1, float* t2,
+                                float* t3, const float* r1, const float* r2, const float* r3,
+                                const float* q, cudaStream_t st);
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
                              const float* d2, const float* d3, cudaStream_t st);
 

@@ -48,15 +48,39 @@ def test_default_params_and_workspace(libpfc):
     assert B.pfc_workspace_bytes(p) == 0          # n, L, dt unset -> invalid
     p.n, p.L, p.eps, p.dt = 16, 32.0, 0.025, 0.01
     n16 = B.pfc_workspace_bytes(p)
-    # 7 fine FP64 fields + 10 per coarse level (8, 4, 2) + reduction buffers
-    fields = 7 * 16 ** 3 + 10 * (8 ** 3 + 4 ** 3 + 2 ** 3)
-    assert fields * 8 <= n16 <= fields * 8 + 200_000
+    # 10 fine FP64 fields (3 levels of phi, mu, omega, S2, S3, 3 Jacobi
+    # scratch) + 13 per coarse level (8, 4, 2) + reduction buffers
+    fields = 10 * 16 ** 3 + 13 * (8 ** 3 + 4 ** 3 + 2 ** 3)
+    assert fields * 8 <= n16 <= fields * 8 + 100_000
     p.precision = B.PFC_MIXED
     assert B.pfc_workspace_bytes(p) > n16
     p.n = 6                                   # 6 -> 3: odd coarsest level
     assert B.pfc_workspace_bytes(p) == 0
     p.n, p.coarsest = 12, 6                   # 12 -> 6: accepted
     assert B.pfc_workspace_bytes(p) > 0
+
+
+def test_level_policy(libpfc):
+    """Level sizes and the hybrid smoother choice (host-side): red-black where
+    108 tau/h^6 >= 1000 or <= 0.02, damped Jacobi in between."""
+    p = B.pfc_default_params()
+    p.n, p.L, p.eps, p.dt = 128, 32.0, 0.025, 0.0125
+    info = []
+    lvl = 0
+    while True:
+        try:
+            info.append(B.pfc_level_info(p, lvl))
+        except B.PFCError:
+            break
+        lvl += 1
+    assert [x[0] for x in info] == [128, 64, 32, 16, 8, 4, 2]
+    for n, h, kind in info:
+        s = 108 * p.dt / h ** 6
+        want = B.PFC_SWEEP_JACOBI if 0.02 < s < 1000 else B.PFC_SWEEP_RB
+        assert kind == want and h == 32.0 / n
+    assert [x[2] for x in info][:3] == [B.PFC_SWEEP_RB, B.PFC_SWEEP_JACOBI, B.PFC_SWEEP_JACOBI]
+    p.policy = B.PFC_POLICY_RB
+    assert all(B.pfc_level_info(p, l)[2] == B.PFC_SWEEP_RB for l in range(7))
 
 
 def test_validation_errors_without_gpu(libpfc):

@@ -55,7 +55,7 @@ def test_smooth(n, lin, sweeps):
     d = [dev(x) for x in u]
     B.pfc_op_smooth(n, h, EPS, TAU, B.PFC_NEWTON if lin == "newton" else B.PFC_PICARD,
                     sweeps, *d, *[dev(s) for s in S], dev(b))
-    ref = O.smooth(u, S, b, h, prm(lin), sweeps)
+    ref = O.rb_smooth(u, S, b, h, prm(lin), sweeps)
     for g, r, name in zip(d, ref, ("phi", "mu", "om")):
         assert_close_field(host(g), r, FP64_RTOL, name)
 
@@ -115,9 +115,26 @@ def test_prolong_correct(n):
         assert_close_field(host(g), x + O.prolong(vv - ww), 1e-14, "u+Pe")
 
 
+@pytest.mark.parametrize("n", [4, 12, 32])
+@pytest.mark.parametrize("lin", ["newton", "picard"])
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+def test_jacobi(n, lin, sweeps):
+    h, b, c, u = case(n)
+    p = prm(lin)
+    S = O.source_S(b, c, h, p)
+    d = [dev(x) for x in u]
+    t = [empty(n) for _ in range(3)]
+    B.pfc_op_jacobi(n, h, EPS, TAU, B.PFC_NEWTON if lin == "newton" else B.PFC_PICARD,
+                    sweeps, 0.7, *d, *t, *[dev(s_) for s_ in S], dev(b))
+    ref = O.jacobi_smooth(u, S, b, h, p, sweeps)
+    for g, r, name in zip(d, ref, ("phi", "mu", "om")):
+        assert_close_field(host(g), r, FP64_RTOL, name)
+
+
 @pytest.mark.parametrize("n", [2, 4, 8])
 @pytest.mark.parametrize("lin", ["newton", "picard"])
-def test_coarse_solve(n, lin):
+@pytest.mark.parametrize("kind", ["rb", "jacobi"])
+def test_coarse_solve(n, lin, kind):
     """The coarsest-level solve reaches the unique solution of N(u) = S that the
     oracle's dense Newton solve finds."""
     L = 2.0 * n           # coarse spacing 2
@@ -129,8 +146,10 @@ def test_coarse_solve(n, lin):
     S = O.source_S(b, c, h, p)
     ref, _ = O.newton_dense(S, [b, 0 * b, 0 * b], b, h, p)
     d = [dev(b), dev(0 * b), dev(0 * b)]
+    t = [empty(n) for _ in range(3)]
     B.pfc_op_coarse_solve(n, h, EPS, TAU, B.PFC_NEWTON if lin == "newton" else B.PFC_PICARD,
-                          400, *d, *[dev(s) for s in S], dev(b))
+                          B.PFC_SWEEP_RB if kind == "rb" else B.PFC_SWEEP_JACOBI, 0.7, 2000,
+                          *d, *t, *[dev(s) for s in S], dev(b))
     got = [host(x) for x in d]
     assert O.rms(O.residual(S, got, b, h, p)) < 1e-12
     for g, r in zip(got, ref):
@@ -196,5 +215,29 @@ def test_linear_smoother_fp32(n, zero_init):
                         dev(q, torch.float32))
     ref = O.linear_smooth([x.astype(np.float64) for x in d0],
                           [x.astype(np.float64) for x in r], q.astype(np.float64), h, p, 2)
+    for g, x in zip(dd, ref):
+        assert_close_field(host(g), x, 1e-5, "d32")
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
+@pytest.mark.parametrize("zero_init", [True, False])
+@pytest.mark.parametrize("sweeps", [1, 2, 3])
+def test_linear_jacobi_fp32(n, zero_init, sweeps):
+    h, b, c, u = case(n)
+    p = prm()
+    q = O.jacobian_coefficient(u[0], b, p).astype(np.float32)
+    rng = np.random.default_rng(19)
+    r = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    d0 = [np.zeros((n,) * 3, np.float32) if zero_init
+          else (0.1 * rng.standard_normal((n,) * 3)).astype(np.float32) for _ in range(3)]
+    dd = [dev(x, torch.float32) for x in d0]
+    if zero_init:
+        for t_ in dd:
+            t_.fill_(float("nan"))
+    tt = [empty(n, torch.float32) for _ in range(3)]
+    B.pfc_op_lin_jacobi(n, h, EPS, TAU, sweeps, 0.7, zero_init, *dd, *tt,
+                        *[dev(x, torch.float32) for x in r], dev(q, torch.float32))
+    ref = O.linear_smooth([x.astype(np.float64) for x in d0], [x.astype(np.float64) for x in r],
+                          q.astype(np.float64), h, p, sweeps, "jacobi")
     for g, x in zip(dd, ref):
         assert_close_field(host(g), x, 1e-5, "d32")
