@@ -104,7 +104,8 @@ def test_energy_law_and_mass_on_gpu_trajectory():
     """The discrete energy law of Eq. 1.10 and mass conservation hold along
     the GPU trajectory (checked with the oracle's norms)."""
     wl = W.cosine_table(16)
-    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-13, smoother="picard")
+    # at h = 0.2 the FP64 rounding floor of the residual is near 1e-13
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-12, smoother="picard")
     c = b = wl.phi0()
     m0 = O.mass(b, wl.h)
     for _ in range(4):
