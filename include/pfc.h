@@ -291,6 +291,28 @@ int pfc_op_residual_norm(int n, double h, double eps, double tau,
                          const double* d_b, void* d_scratch, double* out,
                          void* stream);
 
+/* Same result as pfc_op_residual_norm, but the caller passes no scratch and
+ * nothing is allocated: the per-tile partial sums live in a fixed device
+ * array inside the library (512 KiB, loaded with the library and kept by
+ * every GPU that loads it until the process exits).  The paper has no
+ * counterpart; this exists for callers that cannot allocate device memory
+ * themselves, e.g. a host application whose device memory is reserved up
+ * front by its own pool allocator, or a latency-critical loop that cannot
+ * afford the device-wide synchronisation of cudaMalloc/cudaFree.
+ * Limit: n^3 <= 256^3 cells; larger grids return PFC_ESIZE (with a message in
+ * pfc_last_error) and must use pfc_op_residual_norm.
+ * The first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every tile slot is rewritten by each call, so no state
+ * carries over that needs clearing; all calls on a device share the array, so
+ * calls that overlap on the GPU (concurrent streams, threads) race and must
+ * be serialised by the caller.  Blocking, like pfc_op_residual_norm. */
+int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
+                                const double* d_phi, const double* d_mu,
+                                const double* d_om, const double* d_S1,
+                                const double* d_S2, const double* d_S3,
+                                const double* d_b, double* out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Primitive operations of the mixed-precision path (PFC_MIXED).  The outer
  * loop is an FP64 defect correction: r = S - N(u) in FP64, then an FP32

@@ -85,6 +85,8 @@ _SIGS = {
     "pfc_reduce_scratch_bytes": (_SZ, [_I]),
     "pfc_op_diagnostics": (_I, [_I, _D, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "pfc_op_residual_norm": (_I, [_I, _D, _D, _D] + [_P] * 8 + [ctypes.POINTER(_D), _P]),
+    "pfc_op_residual_norm_static": (_I, [_I, _D, _D, _D] + [_P] * 7 +
+                                    [ctypes.POINTER(_D), _P]),
     "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
     "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
@@ -127,7 +129,7 @@ def strerror(code: int) -> str:
 
 def check(rc: int, what: str) -> None:
     if rc != PFC_OK:
-        detail = lib().pfc_last_error().decode() if rc == PFC_ECUDA else ""
+        detail = lib().pfc_last_error().decode() if rc in (PFC_ECUDA, PFC_ESIZE) else ""
         raise PFCError(rc, what, detail)
 
 
@@ -321,6 +323,16 @@ def pfc_op_residual_norm(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, scratch, st
     check(lib().pfc_op_residual_norm(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1),
                                      ptr(S2), ptr(S3), ptr(b), ptr(scratch),
                                      ctypes.byref(out), stream), "pfc_op_residual_norm")
+    return out.value
+
+
+def pfc_op_residual_norm_static(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, stream=None):
+    """RMS residual with the library's own static scratch (no allocation)."""
+    out = ctypes.c_double()
+    check(lib().pfc_op_residual_norm_static(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om),
+                                            ptr(S1), ptr(S2), ptr(S3), ptr(b),
+                                            ctypes.byref(out), stream),
+          "pfc_op_residual_norm_static")
     return out.value
 
 

@@ -305,6 +305,10 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
 
 }  // namespace
 
+void set_last_error(const char* msg) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
 void prof_begin(Prof* pr, int cls, cudaStream_t st) {
   if (!pr || !((pr->mask >> cls) & 1u)) return;
   if (pr->pending == Prof::kPool) {

@@ -27,6 +27,9 @@ struct Prof {
   long long cnt[PFC_K_COUNT][PFC_PROFILE_LEVELS];
   long long launches = 0;   // every kernel launch of the context, timed or not
 };
+// Detail string returned by pfc_last_error() on this host thread.
+void set_last_error(const char* msg);
+
 // No-ops unless pr is non-null and the class is enabled.
 void prof_begin(Prof* pr, int cls, cudaStream_t st);
 void prof_end(Prof* pr, int cls, int level, int nlaunch, cudaStream_t st);
