@@ -121,10 +121,17 @@ int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
              const double* any_phi1, void* stream);
 
 /* Advance nsteps time steps of Eq. 1.10.  Each step forms S (Eqs. 5.8-5.10)
- * and runs V-cycles until the RMS residual <= tol.  Blocking: reads the
- * residual back once per cycle.  On PFC_ENOCONV / PFC_ENAN the state holds
- * the last iterate of the failing step (not advanced).  stats may be NULL. */
+ * and runs V-cycles (or defect corrections) until the RMS residual <= tol.
+ * By default a step is one CUDA graph launch whose convergence loop is a
+ * device-side WHILE node (the graph of each of the three positions of the
+ * phi ring is built on first use); with graphs off, or while kernel timing is
+ * enabled, the loop runs on the host with one readback per iteration.
+ * Blocking.  On PFC_ENOCONV / PFC_ENAN phi is not advanced (mu and omega are
+ * reset to zero after a NaN).  stats may be NULL. */
 int pfc_step(pfc_ctx* ctx, int nsteps, pfc_step_stats* stats);
+
+/* Switch the graph execution of pfc_step on (default) or off. */
+int pfc_use_graphs(pfc_ctx* ctx, int on);
 
 /* Replace the state by (phi^k, phi^{k-1}) = (any_phi, any_phi_prev);
  * any_phi_prev NULL means phi^{k-1} := phi^k.  mu and omega are kept as warm

@@ -67,6 +67,7 @@ _SIGS = {
     "pfc_step_index": (_I, [_P]),
     "pfc_diagnostics": (_I, [_P, ctypes.POINTER(_D)]),
     "pfc_launch_count": (ctypes.c_longlong, [_P]),
+    "pfc_use_graphs": (_I, [_P, _I]),
     "pfc_destroy": (None, [_P]),
     "pfc_strerror": (ctypes.c_char_p, [_I]),
     "pfc_last_error": (ctypes.c_char_p, []),
@@ -212,6 +213,10 @@ def pfc_diagnostics(ctx) -> list[float]:
     out = (ctypes.c_double * 4)()
     check(lib().pfc_diagnostics(ctx, out), "pfc_diagnostics")
     return list(out)
+
+
+def pfc_use_graphs(ctx, on: bool) -> None:
+    check(lib().pfc_use_graphs(ctx, int(bool(on))), "pfc_use_graphs")
 
 
 def pfc_launch_count(ctx) -> int:

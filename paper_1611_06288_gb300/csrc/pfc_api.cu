@@ -107,6 +107,13 @@ struct pfc_ctx {
   pfc::MixedBufs mx; // FP32 hierarchy of the mixed path
   int step;
   pfc::Prof prof;    // optional event timing of launches
+  pfc::StepState* dstate;  // device convergence state of the current step
+  pfc::StepState* hstate;  // pinned host copy
+  int use_graphs;    // run each step as one graph launch (default on)
+  struct Graph {
+    cudaGraphExec_t exec;
+    long long launches_pre, launches_body;
+  } graph[3];        // one per position of the phi ring
 };
 
 namespace pfc {
@@ -151,9 +158,11 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
   }
   double* partials = cv.take<double>((size_t)kReduceBlocks * kReduceComps);
   double* dout = cv.take<double>(kReduceComps);
+  StepState* dstate = cv.take<StepState>(1);
   if (c) {
     c->partials = partials;
     c->dout = dout;
+    c->dstate = dstate;
   }
   if (p->precision == PFC_MIXED) {
     MixedBufs mx;
@@ -229,29 +238,35 @@ int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
   return smooth_level(c, l, lv, c->p.nu2);
 }
 
-// RMS residual of the level-0 iterate; blocking readback.
-int residual_rms(pfc_ctx* c, const Level64& lv, double* rms) {
+// Sum of squared residuals of the level-0 iterate (to dout[0]) and the
+// convergence decision into dstate.
+int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
+                            int use_handle, int first) {
   cudaStream_t st = c->st;
-  PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
-            launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
-                                  lv.S[2], lv.b, c->partials, c->dout, st));
-  PFC_CUDA(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, st));
-  PFC_CUDA(cudaStreamSynchronize(st));
-  prof_harvest(&c->prof);
+  if (c->p.precision == PFC_MIXED) {
+    PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
+                                  &c->prof));
+  } else {
+    PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
+              launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
+                                    lv.S[2], lv.b, c->partials, c->dout, st));
+  }
   const double n3 = (double)c->p.n * c->p.n * c->p.n;
-  *rms = sqrt(c->hout[0] / (3.0 * n3));
+  PFC_CUDA(launch_decide(h, use_handle, c->dout, c->dstate, 1.0 / (3.0 * n3), c->p.tol,
+                         c->p.max_cycles, first, st));
+  c->prof.launches += 1;
   return PFC_OK;
 }
 
-int step_once(pfc_ctx* c, pfc_step_stats* stats) {
-  Level64 lv;
-  level0(c, &lv);
+// Work of a step before its convergence loop: S2, S3 (Eqs. 5.9-5.10), phi^k on
+// the coarse levels (FAS path), the initial guess phi^{k+1} := phi^k, and the
+// first residual and decision.
+int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int use_handle) {
   const double* cprev = c->ring[c->ic];
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
   Prof* pr = &c->prof;
   PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
             launch_source(lv.L, lv.b, cprev, c->S2, c->S3, c->st));
-  // phi^k on every level (inside the coarse cubic terms of the FAS path)
   if (c->p.precision == PFC_FP64) {
     const double* fine = lv.b;
     for (int l = 1; l < c->nl; ++l) {
@@ -262,32 +277,127 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   }
   PFC_CUDA(cudaMemcpyAsync(lv.u[0], lv.b, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
                            c->st));
-  int rc = PFC_OK;
-  int cycles = 0;
-  double res0 = 0, res = 0;
+  return enqueue_residual_decide(c, lv, h, use_handle, 1);
+}
+
+// One iteration of the convergence loop: a V-cycle (FP64 FAS) or a defect
+// correction (mixed), then the residual and decision.
+int enqueue_body(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
+                 int use_handle) {
   if (c->p.precision == PFC_MIXED) {
-    rc = mixed_solve(c->mx, lv.L, c->p, c->nl, c->sizes, lv.u, lv.S, lv.b, c->partials,
-                     c->dout, c->hout, c->st, pr, &cycles, &res0, &res);
-    if (rc == PFC_ECUDA) snprintf(g_last_error, sizeof(g_last_error), "mixed path CUDA error");
+    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, lv.u, c->st, &c->prof));
   } else {
-    rc = residual_rms(c, lv, &res);
+    int rc = vcycle64(c, 0, lv);
     if (rc) return rc;
-    res0 = res;
-    while (!(res <= c->p.tol)) {
-      if (!isfinite(res)) { rc = PFC_ENAN; break; }
-      if (cycles >= c->p.max_cycles) { rc = PFC_ENOCONV; break; }
-      rc = vcycle64(c, 0, lv);
-      if (rc) return rc;
-      ++cycles;
-      rc = residual_rms(c, lv, &res);
-      if (rc) return rc;
+  }
+  return enqueue_residual_decide(c, lv, h, use_handle, 0);
+}
+
+int read_state(pfc_ctx* c) {
+  PFC_CUDA(cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState), cudaMemcpyDeviceToHost,
+                           c->st));
+  PFC_CUDA(cudaStreamSynchronize(c->st));
+  prof_harvest(&c->prof);
+  return PFC_OK;
+}
+
+// Build the graph of one step for the current ring position: pre-loop work,
+// then a WHILE node whose body is one loop iteration; k_decide sets the
+// condition on the device, so a step needs one launch and one readback.
+int build_graph(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
+  cudaGraph_t G = nullptr;
+  PFC_CUDA(cudaGraphCreate(&G, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(c->st, G, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(G);
+    return cuda_fail(e, "graph setup");
+  }
+  long long l0 = c->prof.launches;
+  int rc = enqueue_pre(c, lv, h, 1);
+  g->launches_pre = c->prof.launches - l0;
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaGraphNode_t cnode;
+  if (rc == PFC_OK) {
+    e = cudaStreamGetCaptureInfo(c->st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cnode, G, deps, nullptr, ndeps, &cp);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(c->st, &cnode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState), cudaMemcpyDeviceToHost,
+                          c->st);
+  }
+  cudaGraph_t cap = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(c->st, &cap);
+  if (rc == PFC_OK && e == cudaSuccess) e = e2;
+  if (rc == PFC_OK && e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(c->st, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      l0 = c->prof.launches;
+      rc = enqueue_body(c, lv, h, 1);
+      g->launches_body = c->prof.launches - l0;
+      cudaGraph_t bcap = nullptr;
+      e2 = cudaStreamEndCapture(c->st, &bcap);
+      if (e == cudaSuccess) e = e2;
     }
   }
+  if (rc == PFC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, G, 0);
+  cudaGraphDestroy(G);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    g->exec = nullptr;
+    return cuda_fail(e, "graph build");
+  }
+  return PFC_OK;
+}
+
+int step_once(pfc_ctx* c, pfc_step_stats* stats) {
+  Level64 lv;
+  level0(c, &lv);
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  int rc = PFC_OK;
+  if (c->use_graphs && c->prof.mask == 0) {
+    pfc_ctx::Graph* g = &c->graph[c->ia];
+    if (!g->exec) {
+      rc = build_graph(c, lv, g);
+      if (rc) return rc;
+    }
+    PFC_CUDA(cudaGraphLaunch(g->exec, c->st));
+    PFC_CUDA(cudaStreamSynchronize(c->st));
+    c->prof.launches += g->launches_pre + g->launches_body * (long long)c->hstate->iters;
+  } else {
+    rc = enqueue_pre(c, lv, 0, 0);
+    if (rc == PFC_OK) rc = read_state(c);
+    while (rc == PFC_OK && c->hstate->status == kStepRunning) {
+      rc = enqueue_body(c, lv, 0, 0);
+      if (rc == PFC_OK) rc = read_state(c);
+    }
+    if (rc) return rc;
+  }
+  const StepState s = *c->hstate;
+  if (s.status == kStepNaN) rc = PFC_ENAN;
+  else if (s.status == kStepNoConv) rc = PFC_ENOCONV;
+  else if (s.status != kStepConverged) rc = PFC_ECUDA;
   if (stats) {
-    stats->cycles_last = cycles;
-    stats->cycles_total += cycles;
-    stats->residual = res;
-    stats->residual0 = res0;
+    stats->cycles_last = s.iters;
+    stats->cycles_total += s.iters;
+    stats->residual = s.rms;
+    stats->residual0 = s.rms0;
   }
   if (rc == PFC_ENAN) {
     cudaMemsetAsync(c->mu, 0, n3 * sizeof(double), c->st);
@@ -413,10 +523,15 @@ int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
     h *= 2.0;
   }
   e = cudaHostAlloc((void**)&c->hout, kReduceComps * sizeof(double), cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&c->hstate, sizeof(StepState), cudaHostAllocDefault);
   if (e != cudaSuccess) {
+    if (c->hout) cudaFreeHost(c->hout);
     free(c);
     return cuda_fail(e, "cudaHostAlloc");
   }
+  memset(c->hstate, 0, sizeof(StepState));
+  c->use_graphs = 1;
   c->ic = 0;
   c->ib = 1;
   c->ia = 2;
@@ -515,6 +630,12 @@ int pfc_mass(pfc_ctx* c, double* mass) {
 
 long long pfc_launch_count(const pfc_ctx* c) { return c ? c->prof.launches : -1; }
 
+int pfc_use_graphs(pfc_ctx* c, int on) {
+  if (!c) return PFC_EINVAL;
+  c->use_graphs = on ? 1 : 0;
+  return PFC_OK;
+}
+
 int pfc_step_index(const pfc_ctx* c) { return c ? c->step : -1; }
 
 int pfc_profile_enable(pfc_ctx* c, unsigned mask) {
@@ -545,7 +666,10 @@ int pfc_profile_read(pfc_ctx* c, int kclass, int level, long long* launches, dou
 void pfc_destroy(pfc_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
+  for (int r = 0; r < 3; ++r)
+    if (c->graph[r].exec) cudaGraphExecDestroy(c->graph[r].exec);
   if (c->hout) cudaFreeHost(c->hout);
+  if (c->hstate) cudaFreeHost(c->hstate);
   if (c->prof.created)
     for (int i = 0; i < 2 * Prof::kPool; ++i) cudaEventDestroy(c->prof.ev[i]);
   free(c);

@@ -410,6 +410,32 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
   }
 }
 
+// Convergence test of Algorithm 1's loop (RMS residual against the tolerance,
+// NaN, cycle budget) on the device.
+__global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
+                         const double* sum, StepState* s, double inv_3n3, double tol,
+                         int max_iter, int first) {
+  const double rms = sqrt(sum[0] * inv_3n3);
+  if (first) {
+    s->iters = 0;
+    s->rms0 = rms;
+  } else {
+    s->iters += 1;
+  }
+  s->rms = rms;
+  int status;
+  if (rms <= tol)
+    status = kStepConverged;
+  else if (!isfinite(rms))
+    status = kStepNaN;
+  else if (s->iters >= max_iter)
+    status = kStepNoConv;
+  else
+    status = kStepRunning;
+  s->status = status;
+  if (use_handle) cudaGraphSetConditional(handle, status == kStepRunning ? 1u : 0u);
+}
+
 inline int reduce_blocks(int64_t cells) {
   const int64_t nb = (cells + kReduceThreads - 1) / kReduceThreads;
   return (int)(nb < kReduceBlocks ? nb : kReduceBlocks);
@@ -547,6 +573,13 @@ cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double*
   const int nb = reduce_blocks((int64_t)L.n * L.n * L.n);
   k_residual_norm2<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, partials);
   k_reduce_final<1><<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
+                          const double* sum, StepState* state, double inv_3n3, double tol,
+                          int max_iter, int first, cudaStream_t st) {
+  k_decide<<<1, 1, 0, st>>>(handle, use_handle, sum, state, inv_3n3, tol, max_iter, first);
   return cudaGetLastError();
 }
 

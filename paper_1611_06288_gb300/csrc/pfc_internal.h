@@ -27,6 +27,22 @@ struct Prof {
   long long cnt[PFC_K_COUNT][PFC_PROFILE_LEVELS];
   long long launches = 0;   // every kernel launch of the context, timed or not
 };
+// Convergence state of one time step, kept in device memory and read back
+// once per step (graph mode) or once per cycle (timed mode).
+struct StepState {
+  double rms0;   // RMS residual of the initial guess
+  double rms;    // latest RMS residual
+  int iters;     // V-cycles (FP64) or defect corrections (mixed) done
+  int status;    // kStepRunning, kStepConverged, kStepNaN, kStepNoConv
+};
+constexpr int kStepRunning = 0, kStepConverged = 1, kStepNaN = 2, kStepNoConv = 3;
+
+// From the reduced sum of squared residuals at sum[0]: update *state and,
+// if use_handle, set the WHILE condition of the step graph to "keep going".
+cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
+                          const double* sum, StepState* state, double inv_3n3, double tol,
+                          int max_iter, int first, cudaStream_t st);
+
 // Detail string returned by pfc_last_error() on this host thread.
 void set_last_error(const char* msg);
 

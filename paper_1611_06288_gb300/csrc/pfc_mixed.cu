@@ -322,6 +322,264 @@ __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, 
   }
 }
 
+
+// ---------------------------------------------------------------------------
+// Coarse tail: every level of at most kTailMaxN^3 cells of one FP32 V-cycle
+// (pre-smoothing, residual + restriction, coarsest solve, prolongation +
+// correction, post-smoothing) in a single launch of one thread block.  The
+// stages are separated by __syncthreads(); data written by the block is read
+// back with coherent loads.  On these grids the separate kernels were pure
+// launch latency.
+// ---------------------------------------------------------------------------
+constexpr int kTailMaxN = 16;
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailThreads = 1024;
+
+struct TailLevel {
+  LvlF L;
+  int kind;
+  float* d[3];
+  float* t[3];
+  float* r[3];
+  const float* q;
+};
+
+struct TailParams {
+  int nlev;          // levels in the tail; the last one is the coarsest
+  int nu1, nu2, jfactor, coarse_sweeps;
+  int zero_init;     // the top tail level starts from d = 0
+  float w;
+  TailLevel lv[kTailMaxLevels];
+};
+
+__device__ __forceinline__ void tail_cell(int t, int n, int& i, int& j, int& k) {
+  i = t % n;
+  j = (t / n) % n;
+  k = t / (n * n);
+}
+
+__device__ void tail_smooth(const TailLevel& T, int sweeps, int jfactor, float w, bool zero) {
+  const int n = T.L.n, cells = n * n * n;
+  if (sweeps <= 0) return;
+  if (T.kind == PFC_SWEEP_JACOBI) {
+    const int js = sweeps * jfactor;
+    float* src[3] = {T.d[0], T.d[1], T.d[2]};
+    float* dst[3] = {T.t[0], T.t[1], T.t[2]};
+    for (int s = 0; s < js; ++s) {
+      const bool z = zero && s == 0;
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        int i, j, k;
+        tail_cell(t, n, i, j, k);
+        const Stencil st = stencil_at(i, j, k, n);
+        float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
+        if (!z) {
+          sp = nbsum_coherent(src[0], st);
+          sm_ = nbsum_coherent(src[1], st);
+          sw = nbsum_coherent(src[2], st);
+          p0 = src[0][t];
+          m0 = src[1][t];
+          w0 = src[2][t];
+        }
+        float dp, dm, dw;
+        lin_point(T.L, sp, sm_, sw, T.q[t], T.r[0][t], T.r[1][t], T.r[2][t], dp, dm, dw);
+        dst[0][t] = fmaf(w, dp - p0, p0);
+        dst[1][t] = fmaf(w, dm - m0, m0);
+        dst[2][t] = fmaf(w, dw - w0, w0);
+      }
+      __syncthreads();
+      for (int c = 0; c < 3; ++c) {
+        float* x = src[c];
+        src[c] = dst[c];
+        dst[c] = x;
+      }
+    }
+    if (js & 1) {
+      for (int t = threadIdx.x; t < cells; t += blockDim.x)
+        for (int c = 0; c < 3; ++c) T.d[c][t] = src[c][t];
+      __syncthreads();
+    }
+    return;
+  }
+  const int half = n >> 1, ccells = half * n * n;
+  for (int s = 0; s < sweeps; ++s) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const bool z = zero && s == 0 && colour == 0;
+      for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
+        const int p = t % half, rr = t / half;
+        const int j = rr % n, k = rr / n;
+        const int i = 2 * p + ((j + k + colour) & 1);
+        const Stencil st = stencil_at(i, j, k, n);
+        float sp = 0.f, sm_ = 0.f, sw = 0.f;
+        if (!z) {
+          sp = nbsum_coherent(T.d[0], st);
+          sm_ = nbsum_coherent(T.d[1], st);
+          sw = nbsum_coherent(T.d[2], st);
+        }
+        float dp, dm, dw;
+        lin_point(T.L, sp, sm_, sw, T.q[st.c], T.r[0][st.c], T.r[1][st.c], T.r[2][st.c], dp,
+                  dm, dw);
+        T.d[0][st.c] = dp;
+        T.d[1][st.c] = dm;
+        T.d[2][st.c] = dw;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// rho = r - J d on level T, averaged onto the next level's right-hand side.
+__device__ void tail_restrict(const TailLevel& T, float* const* rc) {
+  const int n = T.L.n, nc = n >> 1, ccells = nc * nc * nc;
+  for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
+    int I, J, K;
+    tail_cell(t, nc, I, J, K);
+    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    for (int c = 0; c < 8; ++c) {
+      const Stencil st = stencil_at(2 * I + (c & 1), 2 * J + ((c >> 1) & 1), 2 * K + (c >> 2), n);
+      const float p = T.d[0][st.c], m = T.d[1][st.c], w = T.d[2][st.c];
+      const float lm = fmaf(-6.f, m, nbsum_coherent(T.d[1], st));
+      const float lw = fmaf(-6.f, w, nbsum_coherent(T.d[2], st));
+      const float lp = fmaf(-6.f, p, nbsum_coherent(T.d[0], st));
+      a1 += T.r[0][st.c] - fmaf(-T.L.tg, lm, p);
+      a2 += T.r[1][st.c] - (fmaf(-T.q[st.c], p, m) - T.L.g * lw);
+      a3 += T.r[2][st.c] - fmaf(-T.L.gh, lp, w);
+    }
+    rc[0][t] = 0.125f * a1;
+    rc[1][t] = 0.125f * a2;
+    rc[2][t] = 0.125f * a3;
+  }
+  __syncthreads();
+}
+
+// d_fine += P d_coarse (trilinear, weights 27, 9, 3, 1 over 64).
+__device__ void tail_prolong(int n, float* const* e, float* const* d) {
+  const int nc = n >> 1, cells = n * n * n;
+  const int nn = nc * nc;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+    int i, j, k;
+    tail_cell(t, n, i, j, k);
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
+    const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
+    const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
+    const int o000 = I + J * nc + K * nn, o100 = I2 + J * nc + K * nn,
+              o010 = I + J2 * nc + K * nn, o001 = I + J * nc + K2 * nn,
+              o110 = I2 + J2 * nc + K * nn, o101 = I2 + J * nc + K2 * nn,
+              o011 = I + J2 * nc + K2 * nn, o111 = I2 + J2 * nc + K2 * nn;
+    for (int c = 0; c < 3; ++c) {
+      const float* x = e[c];
+      const float g2 = (x[o100] + x[o010]) + x[o001];
+      const float g3 = (x[o110] + x[o101]) + x[o011];
+      float acc = fmaf(3.f, g3, x[o111]);
+      acc = fmaf(9.f, g2, acc);
+      acc = fmaf(27.f, x[o000], acc);
+      d[c][t] = fmaf(1.0f / 64.0f, acc, d[c][t]);
+    }
+  }
+  __syncthreads();
+}
+
+// Coarsest level: from d = 0, sweeps until the largest change is <= 1e-7 of
+// the largest value or `max_sweeps`.
+__device__ void tail_coarse(const TailLevel& T, float w, int max_sweeps, float (*red)[32],
+                            int* done) {
+  const int n = T.L.n, cells = n * n * n;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x)
+    for (int c = 0; c < 3; ++c) T.d[c][t] = 0.f;
+  __syncthreads();
+  const int half = n >> 1, ccells = half * n * n;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float change = 0.f, size = 0.f;
+    if (T.kind == PFC_SWEEP_JACOBI) {
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        int i, j, k;
+        tail_cell(t, n, i, j, k);
+        const Stencil st = stencil_at(i, j, k, n);
+        float dp, dm, dw;
+        lin_point(T.L, nbsum_coherent(T.d[0], st), nbsum_coherent(T.d[1], st),
+                  nbsum_coherent(T.d[2], st), T.q[t], T.r[0][t], T.r[1][t], T.r[2][t], dp,
+                  dm, dw);
+        T.t[0][t] = fmaf(w, dp - T.d[0][t], T.d[0][t]);
+        T.t[1][t] = fmaf(w, dm - T.d[1][t], T.d[1][t]);
+        T.t[2][t] = fmaf(w, dw - T.d[2][t], T.d[2][t]);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        for (int c = 0; c < 3; ++c) {
+          change = fmaxf(change, fabsf(T.t[c][t] - T.d[c][t]));
+          size = fmaxf(size, fabsf(T.t[c][t]));
+          T.d[c][t] = T.t[c][t];
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
+          const int p = t % half, rr = t / half;
+          const int j = rr % n, k = rr / n;
+          const int i = 2 * p + ((j + k + colour) & 1);
+          const Stencil st = stencil_at(i, j, k, n);
+          float dp, dm, dw;
+          lin_point(T.L, nbsum_coherent(T.d[0], st), nbsum_coherent(T.d[1], st),
+                    nbsum_coherent(T.d[2], st), T.q[st.c], T.r[0][st.c], T.r[1][st.c],
+                    T.r[2][st.c], dp, dm, dw);
+          change = fmaxf(change, fmaxf(fabsf(dp - T.d[0][st.c]),
+                                       fmaxf(fabsf(dm - T.d[1][st.c]), fabsf(dw - T.d[2][st.c]))));
+          size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+          T.d[0][st.c] = dp;
+          T.d[1][st.c] = dm;
+          T.d[2][st.c] = dw;
+        }
+        __syncthreads();
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      change = fmaxf(change, __shfl_down_sync(0xffffffffu, change, o));
+      size = fmaxf(size, __shfl_down_sync(0xffffffffu, size, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = change;
+      red[1][threadIdx.x >> 5] = size;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float c = 0.f, z = 0.f;
+      for (int v = 0; v < (int)((blockDim.x + 31) >> 5); ++v) {
+        c = fmaxf(c, red[0][v]);
+        z = fmaxf(z, red[1][v]);
+      }
+      *done = (c <= 1e-7f * z);
+    }
+    __syncthreads();
+    if (*done) break;
+  }
+}
+
+__global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
+  __shared__ float red[2][32];
+  __shared__ int done;
+  const int last = P.nlev - 1;
+  for (int l = 0; l < last; ++l) {
+    const TailLevel& T = P.lv[l];
+    const bool zero = (l > 0) || P.zero_init;
+    if (P.nu1 > 0) {
+      tail_smooth(T, P.nu1, P.jfactor, P.w, zero);
+    } else if (zero) {
+      const int cells = T.L.n * T.L.n * T.L.n;
+      for (int t = threadIdx.x; t < cells; t += blockDim.x)
+        for (int c = 0; c < 3; ++c) T.d[c][t] = 0.f;
+      __syncthreads();
+    }
+    tail_restrict(T, P.lv[l + 1].r);
+  }
+  tail_coarse(P.lv[last], P.w, P.coarse_sweeps, red, &done);
+  for (int l = last - 1; l >= 0; --l) {
+    const TailLevel& T = P.lv[l];
+    tail_prolong(T.L.n, P.lv[l + 1].d, T.d);
+    tail_smooth(T, P.nu2, P.jfactor, P.w, false);
+  }
+}
+
 __global__ void k_correct64(int64_t cells, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
                             const float* __restrict__ d2, const float* __restrict__ d3) {
@@ -403,9 +661,37 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   return cudaGetLastError();
 }
 
+cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
+  MixedBufs& mx = *c.mx;
+  TailParams P;
+  P.nlev = c.nl - l0;
+  P.nu1 = c.p->nu1;
+  P.nu2 = c.p->nu2;
+  P.jfactor = c.jfactor;
+  P.coarse_sweeps = 400;
+  P.zero_init = zero_init ? 1 : 0;
+  P.w = c.w;
+  for (int l = l0; l < c.nl; ++l) {
+    TailLevel& T = P.lv[l - l0];
+    T.L = c.L[l];
+    T.kind = c.kind[l];
+    for (int q = 0; q < 3; ++q) {
+      T.d[q] = mx.d[l][q];
+      T.t[q] = mx.t[l][q];
+      T.r[q] = mx.r[l][q];
+    }
+    T.q = mx.q[l];
+  }
+  prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
+  k_lin_tail32<<<1, kTailThreads, 0, c.st>>>(P);
+  prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
+  return cudaGetLastError();
+}
+
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
+  if (L.n <= kTailMaxN && c.nl - l <= kTailMaxLevels) return tail32(c, l, zero_init);
   if (l == c.nl - 1) {
     const int work = L.n * L.n * L.n;
     int threads = ((work + 31) / 32) * 32;
@@ -501,10 +787,20 @@ cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const fl
   return cudaGetLastError();
 }
 
-int mixed_solve(MixedBufs& mx, const Lvl& L0, const pfc_params& p, int nl,
-                const int* sizes, double* const u[3], double* const S[3], const double* b,
-                double* partials, double* dout, double* hout, cudaStream_t st,
-                Prof* pr, int* outer, double* res0, double* res) {
+cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                 double* const S[3], const double* b, double* partials,
+                                 double* dout, cudaStream_t st, Prof* pr) {
+  prof_begin(pr, PFC_K_DEFECT, st);
+  cudaError_t e = launch_residual64_to32(L0, u[0], u[1], u[2], S[0], S[1], S[2], b,
+                                         mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0], partials,
+                                         dout, st);
+  prof_end(pr, PFC_K_DEFECT, 0, 2, st);
+  return e;
+}
+
+cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
+                                     const int* sizes, double* const u[3], cudaStream_t st,
+                                     Prof* pr) {
   Ctx32 c;
   c.mx = &mx;
   c.p = &p;
@@ -513,57 +809,27 @@ int mixed_solve(MixedBufs& mx, const Lvl& L0, const pfc_params& p, int nl,
   c.pr = pr;
   c.w = (float)p.jacobi_weight;
   c.jfactor = p.jacobi_factor;
-  {
-    double h = p.L / p.n;
-    for (int l = 0; l < nl; ++l) {
-      c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
-      c.kind[l] = level_kind(&p, h);
-      h *= 2.0;
-    }
+  double h = p.L / p.n;
+  for (int l = 0; l < nl; ++l) {
+    c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
+    c.kind[l] = level_kind(&p, h);
+    h *= 2.0;
   }
-  const double n3 = (double)p.n * p.n * p.n;
-  auto fp64_residual = [&](double* r) -> int {
-    prof_begin(pr, PFC_K_DEFECT, st);
-    cudaError_t e = launch_residual64_to32(L0, u[0], u[1], u[2], S[0], S[1], S[2], b,
-                                           mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0],
-                                           partials, dout, st);
-    prof_end(pr, PFC_K_DEFECT, 0, 2, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(hout, dout, sizeof(double), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return PFC_ECUDA;
-    prof_harvest(pr);
-    *r = sqrt(hout[0] / (3.0 * n3));
-    return PFC_OK;
-  };
-  int rc = fp64_residual(res);
-  if (rc) return rc;
-  *res0 = *res;
-  *outer = 0;
-  while (!(*res <= p.tol)) {
-    if (!isfinite(*res)) return PFC_ENAN;
-    if (*outer >= p.max_cycles) return PFC_ENOCONV;
-    cudaError_t e = cudaSuccess;
-    for (int l = 1; l < nl && e == cudaSuccess; ++l) {
-      prof_begin(pr, PFC_K_RESTRICT, st);
-      k_restrict32<<<grid_for((int64_t)sizes[l] * sizes[l] * sizes[l]), kThreads, 0, st>>>(
-          sizes[l - 1], mx.q[l - 1], mx.q[l]);
-      prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
-      e = cudaGetLastError();
-    }
-    for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic)
-      e = vcycle32(c, 0, ic == 0);
-    if (e == cudaSuccess) {
-      prof_begin(pr, PFC_K_CORRECT, st);
-      e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st);
-      prof_end(pr, PFC_K_CORRECT, 0, 1, st);
-    }
-    if (e != cudaSuccess) return PFC_ECUDA;
-    *outer += 1;
-    rc = fp64_residual(res);
-    if (rc) return rc;
+  cudaError_t e = cudaSuccess;
+  for (int l = 1; l < nl && e == cudaSuccess; ++l) {
+    prof_begin(pr, PFC_K_RESTRICT, st);
+    k_restrict32<<<grid_for((int64_t)sizes[l] * sizes[l] * sizes[l]), kThreads, 0, st>>>(
+        sizes[l - 1], mx.q[l - 1], mx.q[l]);
+    prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
+    e = cudaGetLastError();
   }
-  return PFC_OK;
+  for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic) e = vcycle32(c, 0, ic == 0);
+  if (e == cudaSuccess) {
+    prof_begin(pr, PFC_K_CORRECT, st);
+    e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st);
+    prof_end(pr, PFC_K_CORRECT, 0, 1, st);
+  }
+  return e;
 }
 
 }  // namespace pfc

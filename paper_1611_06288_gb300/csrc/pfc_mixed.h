@@ -45,13 +45,17 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
   }
 }
 
-// One time step's solve.  u/S/b are the FP64 level-0 fields; partials/dout/
-// hout are the reduction buffers.  Returns PFC_OK, PFC_ENOCONV, PFC_ENAN or
-// PFC_ECUDA; *outer = defect corrections done, *res0/*res = first/last RMS.
-int mixed_solve(MixedBufs& mx, const Lvl& L0, const pfc_params& p, int nl,
-                const int* sizes, double* const u[3], double* const S[3], const double* b,
-                double* partials, double* dout, double* hout, cudaStream_t st,
-                Prof* pr, int* outer, double* res0, double* res);
+// FP64 defect r = S - N(u) -> FP32 r and q on level 0, and the sum of |r|^2 at
+// dout[0] (two launches).
+cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                 double* const S[3], const double* b, double* partials,
+                                 double* dout, cudaStream_t st, Prof* pr);
+
+// One defect correction after mixed_enqueue_defect: q restricted to every
+// level, p.inner_cycles FP32 V-cycles on J d = r from d = 0, then u += d.
+cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
+                                     const int* sizes, double* const u[3], cudaStream_t st,
+                                     Prof* pr);
 
 // Primitive launches of the FP32 kernels (for the C ABI checks).
 cudaError_t launch_residual64_to32(const Lvl& L, const double* phi, const double* mu,

@@ -126,6 +126,10 @@ class PFCSolver:
                     out[(name, lvl)] = (n, ms)
         return out
 
+    def use_graphs(self, on: bool = True) -> None:
+        """Run each step as one CUDA graph launch (default) or host-driven."""
+        B.pfc_use_graphs(self.ctx, on)
+
     @property
     def launches(self) -> int:
         return B.pfc_launch_count(self.ctx)

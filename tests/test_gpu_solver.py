@@ -36,14 +36,17 @@ def oracle_run(phi0, steps, h, eps, dt, lin, tol=1e-12):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("smoother", ["newton", "picard"])
-def test_random16_ten_steps(precision, smoother):
+@pytest.mark.parametrize("graphs", [True, False])
+def test_random16_ten_steps(precision, smoother, graphs):
     """16^3, L = 32, eps = 0.025, phi0 = 0.07 + 0.07 U(-1,1), dt = 0.01, 10
-    steps with the phi^{-1} := phi^0 start: every step matches the oracle."""
+    steps with the phi^{-1} := phi^0 start: every step matches the oracle, with
+    the device-side (graph) loop and with the host-driven loop."""
     wl = W.random16()
     phi0 = wl.phi0()
     ref = oracle_run(phi0, wl.steps, wl.h, wl.eps, wl.dt, smoother)
     s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-12, precision=precision,
                   smoother=smoother, max_cycles=60)
+    s.use_graphs(graphs)
     for k in range(wl.steps):
         st = s.step(1)
         assert st.residual <= 1e-12
@@ -158,21 +161,46 @@ def test_full_size_256_polycrystal_one_step():
     assert F == pytest.approx(O.energy(a, wl.h, wl.eps), rel=1e-11)
 
 
-def test_error_codes():
+def test_graph_and_host_loops_agree_at_64():
+    """64^3 smooth mode (h = 0.5, tau = 0.0125, hybrid levels): the graph
+    loop and the host loop take the same number of cycles and give the same
+    fields to rounding."""
+    wl = W.smooth_sweep(64)
+    out = []
+    for graphs in (True, False):
+        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-10, precision="mixed",
+                      inner_cycles=2)
+        s.use_graphs(graphs)
+        cyc = [s.step(1).cycles_last for _ in range(3)]
+        out.append((cyc, host(s.phi())))
+    assert out[0][0] == out[1][0]
+    assert rel_l2(out[0][1], out[1][1]) <= 1e-12
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_error_codes(graphs):
     wl = W.random16()
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-14, max_cycles=1)
+    s.use_graphs(graphs)
     with pytest.raises(B.PFCError) as e:
-        PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-14, max_cycles=1).step(1)
+        s.step(1)
     assert e.value.code == B.PFC_ENOCONV
     bad = wl.phi0()
     bad[3, 4, 5] = np.nan
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, bad)
+    s.use_graphs(graphs)
     with pytest.raises(B.PFCError) as e:
-        PFCSolver(wl.n, wl.L, wl.eps, wl.dt, bad).step(1)
+        s.step(1)
     assert e.value.code == B.PFC_ENAN
+    # after a NaN the state can be replaced and stepping resumes
+    s.set_state(wl.phi0())
+    s.step(1)
     with pytest.raises(B.PFCError) as e:
         PFCSolver(6, 6.0, 0.1, 0.1, np.zeros((6, 6, 6)))
     assert e.value.code == B.PFC_ESIZE
     # a failed step leaves the state where it was
     s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-14, max_cycles=1)
+    s.use_graphs(graphs)
     before = host(s.phi())
     with pytest.raises(B.PFCError):
         s.step(1)
