@@ -110,6 +110,7 @@ struct pfc_ctx {
   pfc::StepState* dstate;  // device convergence state of the current step
   pfc::StepState* hstate;  // pinned host copy
   int use_graphs;    // run each step as one graph launch (default on)
+  cudaStream_t cap_st;  // private stream the step graphs are captured on
   struct Graph {
     cudaGraphExec_t exec;
     long long launches_pre, launches_body;
@@ -304,7 +305,21 @@ int read_state(pfc_ctx* c) {
 // Build the graph of one step for the current ring position: pre-loop work,
 // then a WHILE node whose body is one loop iteration; k_decide sets the
 // condition on the device, so a step needs one launch and one readback.
+int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g);
+
+// Capture on the context's private stream (the caller's stream may be the
+// legacy default stream, which cannot be captured); the graph is launched on
+// the caller's stream.
 int build_graph(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
+  if (!c->cap_st) PFC_CUDA(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
+  cudaStream_t user = c->st;
+  c->st = c->cap_st;
+  int rc = build_graph_on(c, lv, g);
+  c->st = user;
+  return rc;
+}
+
+int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
   cudaGraph_t G = nullptr;
   PFC_CUDA(cudaGraphCreate(&G, 0));
   cudaGraphConditionalHandle h;
@@ -668,6 +683,7 @@ void pfc_destroy(pfc_ctx* c) {
   cudaStreamSynchronize(c->st);
   for (int r = 0; r < 3; ++r)
     if (c->graph[r].exec) cudaGraphExecDestroy(c->graph[r].exec);
+  if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->hout) cudaFreeHost(c->hout);
   if (c->hstate) cudaFreeHost(c->hstate);
   if (c->prof.created)
