@@ -548,20 +548,68 @@ __device__ void tail_coarse(const TailLevel& T, float w, int max_sweeps, float (
         c = fmaxf(c, red[0][v]);
         z = fmaxf(z, red[1][v]);
       }
-      *done = (c <= 1e-7f * z);
+      *done = (c <= 1e-6f * z);
     }
     __syncthreads();
     if (*done) break;
   }
 }
 
+// The whole tail lives in shared memory: per level d(3), t(3), r(3), q.  The
+// top level's r and q (and d when it does not start from zero) are loaded
+// from global memory, the lower levels' q are restricted in shared memory,
+// and the top level's d is stored back at the end.
 __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
+  extern __shared__ float smem[];
   __shared__ float red[2][32];
   __shared__ int done;
+  TailLevel S[kTailMaxLevels];
+  {
+    float* base = smem;
+    for (int l = 0; l < P.nlev; ++l) {
+      const int cells = P.lv[l].L.n * P.lv[l].L.n * P.lv[l].L.n;
+      S[l].L = P.lv[l].L;
+      S[l].kind = P.lv[l].kind;
+      for (int c = 0; c < 3; ++c) {
+        S[l].d[c] = base + c * cells;
+        S[l].t[c] = base + (3 + c) * cells;
+        S[l].r[c] = base + (6 + c) * cells;
+      }
+      S[l].q = base + 9 * cells;
+      base += 10 * cells;
+    }
+  }
+  const TailLevel& G = P.lv[0];
+  const bool zero_top = P.zero_init != 0;
+  {
+    const int cells = G.L.n * G.L.n * G.L.n;
+    float* q0 = const_cast<float*>(S[0].q);
+    for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+      for (int c = 0; c < 3; ++c) {
+        S[0].r[c][t] = G.r[c][t];
+        if (!zero_top) S[0].d[c][t] = G.d[c][t];
+      }
+      q0[t] = G.q[t];
+    }
+    __syncthreads();
+    for (int l = 1; l < P.nlev; ++l) {
+      const int n = S[l - 1].L.n, nc = n >> 1, cc = nc * nc * nc;
+      float* qc = const_cast<float*>(S[l].q);
+      for (int t = threadIdx.x; t < cc; t += blockDim.x) {
+        int I, J, K;
+        tail_cell(t, nc, I, J, K);
+        float acc = 0.f;
+        for (int c = 0; c < 8; ++c)
+          acc += S[l - 1].q[(2 * I + (c & 1)) + n * ((2 * J + ((c >> 1) & 1)) + n * (2 * K + (c >> 2)))];
+        qc[t] = 0.125f * acc;
+      }
+      __syncthreads();
+    }
+  }
   const int last = P.nlev - 1;
   for (int l = 0; l < last; ++l) {
-    const TailLevel& T = P.lv[l];
-    const bool zero = (l > 0) || P.zero_init;
+    const TailLevel& T = S[l];
+    const bool zero = (l > 0) || zero_top;
     if (P.nu1 > 0) {
       tail_smooth(T, P.nu1, P.jfactor, P.w, zero);
     } else if (zero) {
@@ -570,15 +618,27 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
         for (int c = 0; c < 3; ++c) T.d[c][t] = 0.f;
       __syncthreads();
     }
-    tail_restrict(T, P.lv[l + 1].r);
+    tail_restrict(T, S[l + 1].r);
   }
-  tail_coarse(P.lv[last], P.w, P.coarse_sweeps, red, &done);
+  tail_coarse(S[last], P.w, P.coarse_sweeps, red, &done);
   for (int l = last - 1; l >= 0; --l) {
-    const TailLevel& T = P.lv[l];
-    tail_prolong(T.L.n, P.lv[l + 1].d, T.d);
+    const TailLevel& T = S[l];
+    tail_prolong(T.L.n, S[l + 1].d, T.d);
     tail_smooth(T, P.nu2, P.jfactor, P.w, false);
   }
+  const int cells = G.L.n * G.L.n * G.L.n;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x)
+    for (int c = 0; c < 3; ++c) G.d[c][t] = S[0].d[c][t];
 }
+
+// Shared memory of the tail starting at level l0 (10 floats per cell per level).
+size_t tail_smem_bytes(const int* sizes, int l0, int nl) {
+  size_t cells = 0;
+  for (int l = l0; l < nl; ++l) cells += (size_t)sizes[l] * sizes[l] * sizes[l];
+  return cells * 10 * sizeof(float);
+}
+
+constexpr size_t kTailMaxSmem = 227 * 1024;
 
 __global__ void k_correct64(int64_t cells, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
@@ -668,7 +728,7 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
   P.nu1 = c.p->nu1;
   P.nu2 = c.p->nu2;
   P.jfactor = c.jfactor;
-  P.coarse_sweeps = 400;
+  P.coarse_sweeps = 64;
   P.zero_init = zero_init ? 1 : 0;
   P.w = c.w;
   for (int l = l0; l < c.nl; ++l) {
@@ -682,8 +742,18 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
     }
     T.q = mx.q[l];
   }
+  int sizes[kMaxLevelsMixed];
+  for (int l = 0; l < c.nl; ++l) sizes[l] = c.L[l].n;
+  const size_t smem = tail_smem_bytes(sizes, l0, c.nl);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_lin_tail32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTailMaxSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
   prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
-  k_lin_tail32<<<1, kTailThreads, 0, c.st>>>(P);
+  k_lin_tail32<<<1, kTailThreads, smem, c.st>>>(P);
   prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
   return cudaGetLastError();
 }
@@ -691,7 +761,11 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
-  if (L.n <= kTailMaxN && c.nl - l <= kTailMaxLevels) return tail32(c, l, zero_init);
+  if (L.n <= kTailMaxN && c.nl - l <= kTailMaxLevels) {
+    int sizes[kMaxLevelsMixed];
+    for (int q = 0; q < c.nl; ++q) sizes[q] = c.L[q].n;
+    if (tail_smem_bytes(sizes, l, c.nl) <= kTailMaxSmem) return tail32(c, l, zero_init);
+  }
   if (l == c.nl - 1) {
     const int work = L.n * L.n * L.n;
     int threads = ((work + 31) / 32) * 32;
