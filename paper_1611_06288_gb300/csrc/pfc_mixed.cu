@@ -638,7 +638,7 @@ size_t tail_smem_bytes(const int* sizes, int l0, int nl) {
   return cells * 10 * sizeof(float);
 }
 
-constexpr size_t kTailMaxSmem = 227 * 1024;
+constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 KiB
 
 __global__ void k_correct64(int64_t cells, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
