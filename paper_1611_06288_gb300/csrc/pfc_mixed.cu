@@ -326,209 +326,279 @@ __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, 
 // ---------------------------------------------------------------------------
 // Coarse tail: every level of at most kTailMaxN^3 cells of one FP32 V-cycle
 // (pre-smoothing, residual + restriction, coarsest solve, prolongation +
-// correction, post-smoothing) in a single launch of one thread block.  The
-// stages are separated by __syncthreads(); data written by the block is read
-// back with coherent loads.  On these grids the separate kernels were pure
-// launch latency.
+// correction, post-smoothing) in a single launch of one thread block whose
+// levels all live in shared memory.  On these grids separate kernels were
+// pure launch latency.  Each thread owns a fixed (i, j) column and walks k
+// with a stride, so no cell index is divided per cell.
 // ---------------------------------------------------------------------------
 constexpr int kTailMaxN = 16;
 constexpr int kTailMaxLevels = 8;
 constexpr int kTailThreads = 1024;
-
-struct TailLevel {
-  LvlF L;
-  int kind;
-  float* d[3];
-  float* t[3];
-  float* r[3];
-  const float* q;
-};
 
 struct TailParams {
   int nlev;          // levels in the tail; the last one is the coarsest
   int nu1, nu2, jfactor, coarse_sweeps;
   int zero_init;     // the top tail level starts from d = 0
   float w;
-  TailLevel lv[kTailMaxLevels];
+  LvlF L[kTailMaxLevels];
+  int kind[kTailMaxLevels];
+  float* gd[3];      // top level in global memory
+  const float* gr[3];
+  const float* gq;
 };
 
-__device__ __forceinline__ void tail_cell(int t, int n, int& i, int& j, int& k) {
-  i = t % n;
-  j = (t / n) % n;
-  k = t / (n * n);
+// Fields of one level in shared memory: d(3), t(3), r(3), q, n^3 floats each.
+struct SLev {
+  float *d0, *d1, *d2, *t0, *t1, *t2, *r0, *r1, *r2, *q;
+};
+
+__device__ __forceinline__ SLev slev(float* smem, const TailParams& P, int l) {
+  int off = 0;
+  for (int m = 0; m < l; ++m) off += 10 * P.L[m].n * P.L[m].n * P.L[m].n;
+  const int c = P.L[l].n * P.L[l].n * P.L[l].n;
+  float* b = smem + off;
+  SLev S;
+  S.d0 = b;
+  S.d1 = b + c;
+  S.d2 = b + 2 * c;
+  S.t0 = b + 3 * c;
+  S.t1 = b + 4 * c;
+  S.t2 = b + 5 * c;
+  S.r0 = b + 6 * c;
+  S.r1 = b + 7 * c;
+  S.r2 = b + 8 * c;
+  S.q = b + 9 * c;
+  return S;
 }
 
-__device__ void tail_smooth(const TailLevel& T, int sweeps, int jfactor, float w, bool zero) {
-  const int n = T.L.n, cells = n * n * n;
+// Column walker: thread -> (i, j, k0); k advances by kstep.
+struct Walk {
+  int n, i, j, k0, kstep, im, ip, jm, jp;
+  bool active;
+  __device__ __forceinline__ Walk(int n_) : n(n_) {
+    const int plane = n * n;
+    kstep = blockDim.x / plane;
+    if (kstep > n) kstep = n;
+    const int tid = threadIdx.x;
+    k0 = tid / plane;
+    const int rem = tid - k0 * plane;
+    j = rem / n;
+    i = rem - j * n;
+    active = k0 < kstep;
+    im = (i == 0) ? n - 1 : i - 1;
+    ip = (i + 1 == n) ? 0 : i + 1;
+    jm = (j == 0) ? n - 1 : j - 1;
+    jp = (j + 1 == n) ? 0 : j + 1;
+  }
+  // linear indices of (i, j, k) and its six neighbours
+  __device__ __forceinline__ void at(int k, int& c, int& xm, int& xp, int& ym, int& yp, int& zm,
+                                     int& zp) const {
+    const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+    const int row = n * (j + n * k);
+    c = row + i;
+    xm = row + im;
+    xp = row + ip;
+    ym = i + n * (jm + n * k);
+    yp = i + n * (jp + n * k);
+    zm = i + n * (j + n * km);
+    zp = i + n * (j + n * kp);
+  }
+};
+
+__device__ __forceinline__ float nb6(const float* v, int xm, int xp, int ym, int yp, int zm,
+                                     int zp) {
+  return ((v[xm] + v[xp]) + (v[ym] + v[yp])) + (v[zm] + v[zp]);
+}
+
+__device__ void tail_smooth(const LvlF& L, int kind, SLev S, int sweeps, int jfactor, float w,
+                            bool zero) {
   if (sweeps <= 0) return;
-  if (T.kind == PFC_SWEEP_JACOBI) {
+  const Walk W(L.n);
+  int c, xm, xp, ym, yp, zm, zp;
+  if (kind == PFC_SWEEP_JACOBI) {
     const int js = sweeps * jfactor;
-    float* src[3] = {T.d[0], T.d[1], T.d[2]};
-    float* dst[3] = {T.t[0], T.t[1], T.t[2]};
+    float *s0 = S.d0, *s1 = S.d1, *s2 = S.d2, *o0 = S.t0, *o1 = S.t1, *o2 = S.t2;
     for (int s = 0; s < js; ++s) {
       const bool z = zero && s == 0;
-      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-        int i, j, k;
-        tail_cell(t, n, i, j, k);
-        const Stencil st = stencil_at(i, j, k, n);
-        float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
-        if (!z) {
-          sp = nbsum_coherent(src[0], st);
-          sm_ = nbsum_coherent(src[1], st);
-          sw = nbsum_coherent(src[2], st);
-          p0 = src[0][t];
-          m0 = src[1][t];
-          w0 = src[2][t];
+      if (W.active) {
+        for (int k = W.k0; k < L.n; k += W.kstep) {
+          W.at(k, c, xm, xp, ym, yp, zm, zp);
+          float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
+          if (!z) {
+            sp = nb6(s0, xm, xp, ym, yp, zm, zp);
+            sm_ = nb6(s1, xm, xp, ym, yp, zm, zp);
+            sw = nb6(s2, xm, xp, ym, yp, zm, zp);
+            p0 = s0[c];
+            m0 = s1[c];
+            w0 = s2[c];
+          }
+          float dp, dm, dw;
+          lin_point(L, sp, sm_, sw, S.q[c], S.r0[c], S.r1[c], S.r2[c], dp, dm, dw);
+          o0[c] = fmaf(w, dp - p0, p0);
+          o1[c] = fmaf(w, dm - m0, m0);
+          o2[c] = fmaf(w, dw - w0, w0);
         }
-        float dp, dm, dw;
-        lin_point(T.L, sp, sm_, sw, T.q[t], T.r[0][t], T.r[1][t], T.r[2][t], dp, dm, dw);
-        dst[0][t] = fmaf(w, dp - p0, p0);
-        dst[1][t] = fmaf(w, dm - m0, m0);
-        dst[2][t] = fmaf(w, dw - w0, w0);
       }
       __syncthreads();
-      for (int c = 0; c < 3; ++c) {
-        float* x = src[c];
-        src[c] = dst[c];
-        dst[c] = x;
-      }
+      float* x;
+      x = s0; s0 = o0; o0 = x;
+      x = s1; s1 = o1; o1 = x;
+      x = s2; s2 = o2; o2 = x;
     }
     if (js & 1) {
-      for (int t = threadIdx.x; t < cells; t += blockDim.x)
-        for (int c = 0; c < 3; ++c) T.d[c][t] = src[c][t];
+      if (W.active) {
+        for (int k = W.k0; k < L.n; k += W.kstep) {
+          W.at(k, c, xm, xp, ym, yp, zm, zp);
+          S.d0[c] = s0[c];
+          S.d1[c] = s1[c];
+          S.d2[c] = s2[c];
+        }
+      }
       __syncthreads();
     }
     return;
   }
-  const int half = n >> 1, ccells = half * n * n;
   for (int s = 0; s < sweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       const bool z = zero && s == 0 && colour == 0;
-      for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
-        const int p = t % half, rr = t / half;
-        const int j = rr % n, k = rr / n;
-        const int i = 2 * p + ((j + k + colour) & 1);
-        const Stencil st = stencil_at(i, j, k, n);
-        float sp = 0.f, sm_ = 0.f, sw = 0.f;
-        if (!z) {
-          sp = nbsum_coherent(T.d[0], st);
-          sm_ = nbsum_coherent(T.d[1], st);
-          sw = nbsum_coherent(T.d[2], st);
+      if (W.active) {
+        for (int k = W.k0; k < L.n; k += W.kstep) {
+          if (((W.i + W.j + k) & 1) != colour) continue;
+          W.at(k, c, xm, xp, ym, yp, zm, zp);
+          float sp = 0.f, sm_ = 0.f, sw = 0.f;
+          if (!z) {
+            sp = nb6(S.d0, xm, xp, ym, yp, zm, zp);
+            sm_ = nb6(S.d1, xm, xp, ym, yp, zm, zp);
+            sw = nb6(S.d2, xm, xp, ym, yp, zm, zp);
+          }
+          float dp, dm, dw;
+          lin_point(L, sp, sm_, sw, S.q[c], S.r0[c], S.r1[c], S.r2[c], dp, dm, dw);
+          S.d0[c] = dp;
+          S.d1[c] = dm;
+          S.d2[c] = dw;
         }
-        float dp, dm, dw;
-        lin_point(T.L, sp, sm_, sw, T.q[st.c], T.r[0][st.c], T.r[1][st.c], T.r[2][st.c], dp,
-                  dm, dw);
-        T.d[0][st.c] = dp;
-        T.d[1][st.c] = dm;
-        T.d[2][st.c] = dw;
       }
       __syncthreads();
     }
   }
 }
 
-// rho = r - J d on level T, averaged onto the next level's right-hand side.
-__device__ void tail_restrict(const TailLevel& T, float* const* rc) {
-  const int n = T.L.n, nc = n >> 1, ccells = nc * nc * nc;
-  for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
-    int I, J, K;
-    tail_cell(t, nc, I, J, K);
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    for (int c = 0; c < 8; ++c) {
-      const Stencil st = stencil_at(2 * I + (c & 1), 2 * J + ((c >> 1) & 1), 2 * K + (c >> 2), n);
-      const float p = T.d[0][st.c], m = T.d[1][st.c], w = T.d[2][st.c];
-      const float lm = fmaf(-6.f, m, nbsum_coherent(T.d[1], st));
-      const float lw = fmaf(-6.f, w, nbsum_coherent(T.d[2], st));
-      const float lp = fmaf(-6.f, p, nbsum_coherent(T.d[0], st));
-      a1 += T.r[0][st.c] - fmaf(-T.L.tg, lm, p);
-      a2 += T.r[1][st.c] - (fmaf(-T.q[st.c], p, m) - T.L.g * lw);
-      a3 += T.r[2][st.c] - fmaf(-T.L.gh, lp, w);
+// rho = r - J d on the fine level F, averaged onto the coarse level's r.
+__device__ void tail_restrict(const LvlF& L, SLev F, SLev C) {
+  const int n = L.n;
+  const Walk W(n >> 1);
+  if (W.active) {
+    for (int K = W.k0; K < W.n; K += W.kstep) {
+      float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int ch = 0; ch < 8; ++ch) {
+        const Stencil st = stencil_at(2 * W.i + (ch & 1), 2 * W.j + ((ch >> 1) & 1),
+                                      2 * K + (ch >> 2), n);
+        const int c = (int)st.c;
+        const float p = F.d0[c], m = F.d1[c], w = F.d2[c];
+        const float lm = fmaf(-6.f, m, nbsum_coherent(F.d1, st));
+        const float lw = fmaf(-6.f, w, nbsum_coherent(F.d2, st));
+        const float lp = fmaf(-6.f, p, nbsum_coherent(F.d0, st));
+        a1 += F.r0[c] - fmaf(-L.tg, lm, p);
+        a2 += F.r1[c] - (fmaf(-F.q[c], p, m) - L.g * lw);
+        a3 += F.r2[c] - fmaf(-L.gh, lp, w);
+      }
+      const int cc = W.i + W.n * (W.j + W.n * K);
+      C.r0[cc] = 0.125f * a1;
+      C.r1[cc] = 0.125f * a2;
+      C.r2[cc] = 0.125f * a3;
     }
-    rc[0][t] = 0.125f * a1;
-    rc[1][t] = 0.125f * a2;
-    rc[2][t] = 0.125f * a3;
   }
   __syncthreads();
 }
 
-// d_fine += P d_coarse (trilinear, weights 27, 9, 3, 1 over 64).
-__device__ void tail_prolong(int n, float* const* e, float* const* d) {
-  const int nc = n >> 1, cells = n * n * n;
-  const int nn = nc * nc;
+// d_F += P d_C (trilinear, weights 27, 9, 3, 1 over 64).
+__device__ void tail_prolong(int n, SLev C, SLev F) {
+  const int nc = n >> 1, nn = nc * nc;
+  const Walk W(n);
+  if (W.active) {
+    const int I = W.i >> 1, J = W.j >> 1;
+    const int I2 = ((W.i & 1) ? I + 1 : I - 1 + nc) % nc;
+    const int J2 = ((W.j & 1) ? J + 1 : J - 1 + nc) % nc;
+    for (int k = W.k0; k < n; k += W.kstep) {
+      const int K = k >> 1;
+      const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
+      const int o000 = I + J * nc + K * nn, o100 = I2 + J * nc + K * nn,
+                o010 = I + J2 * nc + K * nn, o001 = I + J * nc + K2 * nn,
+                o110 = I2 + J2 * nc + K * nn, o101 = I2 + J * nc + K2 * nn,
+                o011 = I + J2 * nc + K2 * nn, o111 = I2 + J2 * nc + K2 * nn;
+      const int c = W.i + n * (W.j + n * k);
+      const float* e[3] = {C.d0, C.d1, C.d2};
+      float* d[3] = {F.d0, F.d1, F.d2};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float* x = e[q];
+        const float g2 = (x[o100] + x[o010]) + x[o001];
+        const float g3 = (x[o110] + x[o101]) + x[o011];
+        float acc = fmaf(3.f, g3, x[o111]);
+        acc = fmaf(9.f, g2, acc);
+        acc = fmaf(27.f, x[o000], acc);
+        d[q][c] = fmaf(1.0f / 64.0f, acc, d[q][c]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Coarsest level: from d = 0, sweeps until the largest change is <= 1e-6 of
+// the largest value or `max_sweeps` (the outer FP64 loop absorbs the rest).
+__device__ void tail_coarse(const LvlF& L, int kind, SLev S, float w, int max_sweeps,
+                            float (*red)[32], int* done) {
+  const int n = L.n, cells = n * n * n;
   for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-    int i, j, k;
-    tail_cell(t, n, i, j, k);
-    const int I = i >> 1, J = j >> 1, K = k >> 1;
-    const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
-    const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
-    const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
-    const int o000 = I + J * nc + K * nn, o100 = I2 + J * nc + K * nn,
-              o010 = I + J2 * nc + K * nn, o001 = I + J * nc + K2 * nn,
-              o110 = I2 + J2 * nc + K * nn, o101 = I2 + J * nc + K2 * nn,
-              o011 = I + J2 * nc + K2 * nn, o111 = I2 + J2 * nc + K2 * nn;
-    for (int c = 0; c < 3; ++c) {
-      const float* x = e[c];
-      const float g2 = (x[o100] + x[o010]) + x[o001];
-      const float g3 = (x[o110] + x[o101]) + x[o011];
-      float acc = fmaf(3.f, g3, x[o111]);
-      acc = fmaf(9.f, g2, acc);
-      acc = fmaf(27.f, x[o000], acc);
-      d[c][t] = fmaf(1.0f / 64.0f, acc, d[c][t]);
-    }
+    S.d0[t] = 0.f;
+    S.d1[t] = 0.f;
+    S.d2[t] = 0.f;
   }
   __syncthreads();
-}
-
-// Coarsest level: from d = 0, sweeps until the largest change is <= 1e-7 of
-// the largest value or `max_sweeps`.
-__device__ void tail_coarse(const TailLevel& T, float w, int max_sweeps, float (*red)[32],
-                            int* done) {
-  const int n = T.L.n, cells = n * n * n;
-  for (int t = threadIdx.x; t < cells; t += blockDim.x)
-    for (int c = 0; c < 3; ++c) T.d[c][t] = 0.f;
-  __syncthreads();
-  const int half = n >> 1, ccells = half * n * n;
+  const Walk W(n);
+  int c, xm, xp, ym, yp, zm, zp;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     float change = 0.f, size = 0.f;
-    if (T.kind == PFC_SWEEP_JACOBI) {
-      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-        int i, j, k;
-        tail_cell(t, n, i, j, k);
-        const Stencil st = stencil_at(i, j, k, n);
-        float dp, dm, dw;
-        lin_point(T.L, nbsum_coherent(T.d[0], st), nbsum_coherent(T.d[1], st),
-                  nbsum_coherent(T.d[2], st), T.q[t], T.r[0][t], T.r[1][t], T.r[2][t], dp,
-                  dm, dw);
-        T.t[0][t] = fmaf(w, dp - T.d[0][t], T.d[0][t]);
-        T.t[1][t] = fmaf(w, dm - T.d[1][t], T.d[1][t]);
-        T.t[2][t] = fmaf(w, dw - T.d[2][t], T.d[2][t]);
+    if (kind == PFC_SWEEP_JACOBI) {
+      if (W.active) {
+        for (int k = W.k0; k < n; k += W.kstep) {
+          W.at(k, c, xm, xp, ym, yp, zm, zp);
+          float dp, dm, dw;
+          lin_point(L, nb6(S.d0, xm, xp, ym, yp, zm, zp), nb6(S.d1, xm, xp, ym, yp, zm, zp),
+                    nb6(S.d2, xm, xp, ym, yp, zm, zp), S.q[c], S.r0[c], S.r1[c], S.r2[c], dp,
+                    dm, dw);
+          S.t0[c] = fmaf(w, dp - S.d0[c], S.d0[c]);
+          S.t1[c] = fmaf(w, dm - S.d1[c], S.d1[c]);
+          S.t2[c] = fmaf(w, dw - S.d2[c], S.d2[c]);
+        }
       }
       __syncthreads();
       for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-        for (int c = 0; c < 3; ++c) {
-          change = fmaxf(change, fabsf(T.t[c][t] - T.d[c][t]));
-          size = fmaxf(size, fabsf(T.t[c][t]));
-          T.d[c][t] = T.t[c][t];
-        }
+        change = fmaxf(change, fmaxf(fabsf(S.t0[t] - S.d0[t]),
+                                     fmaxf(fabsf(S.t1[t] - S.d1[t]), fabsf(S.t2[t] - S.d2[t]))));
+        size = fmaxf(size, fmaxf(fabsf(S.t0[t]), fmaxf(fabsf(S.t1[t]), fabsf(S.t2[t]))));
+        S.d0[t] = S.t0[t];
+        S.d1[t] = S.t1[t];
+        S.d2[t] = S.t2[t];
       }
       __syncthreads();
     } else {
       for (int colour = 0; colour < 2; ++colour) {
-        for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
-          const int p = t % half, rr = t / half;
-          const int j = rr % n, k = rr / n;
-          const int i = 2 * p + ((j + k + colour) & 1);
-          const Stencil st = stencil_at(i, j, k, n);
-          float dp, dm, dw;
-          lin_point(T.L, nbsum_coherent(T.d[0], st), nbsum_coherent(T.d[1], st),
-                    nbsum_coherent(T.d[2], st), T.q[st.c], T.r[0][st.c], T.r[1][st.c],
-                    T.r[2][st.c], dp, dm, dw);
-          change = fmaxf(change, fmaxf(fabsf(dp - T.d[0][st.c]),
-                                       fmaxf(fabsf(dm - T.d[1][st.c]), fabsf(dw - T.d[2][st.c]))));
-          size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
-          T.d[0][st.c] = dp;
-          T.d[1][st.c] = dm;
-          T.d[2][st.c] = dw;
+        if (W.active) {
+          for (int k = W.k0; k < n; k += W.kstep) {
+            if (((W.i + W.j + k) & 1) != colour) continue;
+            W.at(k, c, xm, xp, ym, yp, zm, zp);
+            float dp, dm, dw;
+            lin_point(L, nb6(S.d0, xm, xp, ym, yp, zm, zp), nb6(S.d1, xm, xp, ym, yp, zm, zp),
+                      nb6(S.d2, xm, xp, ym, yp, zm, zp), S.q[c], S.r0[c], S.r1[c], S.r2[c],
+                      dp, dm, dw);
+            change = fmaxf(change, fmaxf(fabsf(dp - S.d0[c]),
+                                         fmaxf(fabsf(dm - S.d1[c]), fabsf(dw - S.d2[c]))));
+            size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+            S.d0[c] = dp;
+            S.d1[c] = dm;
+            S.d2[c] = dw;
+          }
         }
         __syncthreads();
       }
@@ -543,92 +613,87 @@ __device__ void tail_coarse(const TailLevel& T, float w, int max_sweeps, float (
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      float c = 0.f, z = 0.f;
+      float cmax = 0.f, z = 0.f;
       for (int v = 0; v < (int)((blockDim.x + 31) >> 5); ++v) {
-        c = fmaxf(c, red[0][v]);
+        cmax = fmaxf(cmax, red[0][v]);
         z = fmaxf(z, red[1][v]);
       }
-      *done = (c <= 1e-6f * z);
+      *done = (cmax <= 1e-6f * z);
     }
     __syncthreads();
     if (*done) break;
   }
 }
 
-// The whole tail lives in shared memory: per level d(3), t(3), r(3), q.  The
-// top level's r and q (and d when it does not start from zero) are loaded
-// from global memory, the lower levels' q are restricted in shared memory,
-// and the top level's d is stored back at the end.
+// The whole tail lives in shared memory.  The top level's r and q (and d
+// when it does not start from zero) are loaded from global memory, the lower
+// levels' q are restricted in shared memory, and the top level's d is stored
+// back at the end.
 __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
   extern __shared__ float smem[];
   __shared__ float red[2][32];
   __shared__ int done;
-  TailLevel S[kTailMaxLevels];
-  {
-    float* base = smem;
-    for (int l = 0; l < P.nlev; ++l) {
-      const int cells = P.lv[l].L.n * P.lv[l].L.n * P.lv[l].L.n;
-      S[l].L = P.lv[l].L;
-      S[l].kind = P.lv[l].kind;
-      for (int c = 0; c < 3; ++c) {
-        S[l].d[c] = base + c * cells;
-        S[l].t[c] = base + (3 + c) * cells;
-        S[l].r[c] = base + (6 + c) * cells;
-      }
-      S[l].q = base + 9 * cells;
-      base += 10 * cells;
-    }
-  }
-  const TailLevel& G = P.lv[0];
   const bool zero_top = P.zero_init != 0;
   {
-    const int cells = G.L.n * G.L.n * G.L.n;
-    float* q0 = const_cast<float*>(S[0].q);
+    const SLev S0 = slev(smem, P, 0);
+    const int cells = P.L[0].n * P.L[0].n * P.L[0].n;
     for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-      for (int c = 0; c < 3; ++c) {
-        S[0].r[c][t] = G.r[c][t];
-        if (!zero_top) S[0].d[c][t] = G.d[c][t];
+      S0.r0[t] = P.gr[0][t];
+      S0.r1[t] = P.gr[1][t];
+      S0.r2[t] = P.gr[2][t];
+      S0.q[t] = P.gq[t];
+      if (!zero_top) {
+        S0.d0[t] = P.gd[0][t];
+        S0.d1[t] = P.gd[1][t];
+        S0.d2[t] = P.gd[2][t];
       }
-      q0[t] = G.q[t];
     }
     __syncthreads();
     for (int l = 1; l < P.nlev; ++l) {
-      const int n = S[l - 1].L.n, nc = n >> 1, cc = nc * nc * nc;
-      float* qc = const_cast<float*>(S[l].q);
-      for (int t = threadIdx.x; t < cc; t += blockDim.x) {
-        int I, J, K;
-        tail_cell(t, nc, I, J, K);
-        float acc = 0.f;
-        for (int c = 0; c < 8; ++c)
-          acc += S[l - 1].q[(2 * I + (c & 1)) + n * ((2 * J + ((c >> 1) & 1)) + n * (2 * K + (c >> 2)))];
-        qc[t] = 0.125f * acc;
+      const SLev F = slev(smem, P, l - 1), C = slev(smem, P, l);
+      const int n = P.L[l - 1].n;
+      const Walk W(n >> 1);
+      if (W.active) {
+        for (int K = W.k0; K < W.n; K += W.kstep) {
+          float acc = 0.f;
+          for (int ch = 0; ch < 8; ++ch)
+            acc += F.q[(2 * W.i + (ch & 1)) + n * ((2 * W.j + ((ch >> 1) & 1)) + n * (2 * K + (ch >> 2)))];
+          C.q[W.i + W.n * (W.j + W.n * K)] = 0.125f * acc;
+        }
       }
       __syncthreads();
     }
   }
   const int last = P.nlev - 1;
   for (int l = 0; l < last; ++l) {
-    const TailLevel& T = S[l];
+    const SLev S = slev(smem, P, l);
     const bool zero = (l > 0) || zero_top;
     if (P.nu1 > 0) {
-      tail_smooth(T, P.nu1, P.jfactor, P.w, zero);
+      tail_smooth(P.L[l], P.kind[l], S, P.nu1, P.jfactor, P.w, zero);
     } else if (zero) {
-      const int cells = T.L.n * T.L.n * T.L.n;
-      for (int t = threadIdx.x; t < cells; t += blockDim.x)
-        for (int c = 0; c < 3; ++c) T.d[c][t] = 0.f;
+      const int cells = P.L[l].n * P.L[l].n * P.L[l].n;
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        S.d0[t] = 0.f;
+        S.d1[t] = 0.f;
+        S.d2[t] = 0.f;
+      }
       __syncthreads();
     }
-    tail_restrict(T, S[l + 1].r);
+    tail_restrict(P.L[l], S, slev(smem, P, l + 1));
   }
-  tail_coarse(S[last], P.w, P.coarse_sweeps, red, &done);
+  tail_coarse(P.L[last], P.kind[last], slev(smem, P, last), P.w, P.coarse_sweeps, red, &done);
   for (int l = last - 1; l >= 0; --l) {
-    const TailLevel& T = S[l];
-    tail_prolong(T.L.n, S[l + 1].d, T.d);
-    tail_smooth(T, P.nu2, P.jfactor, P.w, false);
+    const SLev S = slev(smem, P, l);
+    tail_prolong(P.L[l].n, slev(smem, P, l + 1), S);
+    tail_smooth(P.L[l], P.kind[l], S, P.nu2, P.jfactor, P.w, false);
   }
-  const int cells = G.L.n * G.L.n * G.L.n;
-  for (int t = threadIdx.x; t < cells; t += blockDim.x)
-    for (int c = 0; c < 3; ++c) G.d[c][t] = S[0].d[c][t];
+  const SLev S0 = slev(smem, P, 0);
+  const int cells = P.L[0].n * P.L[0].n * P.L[0].n;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+    P.gd[0][t] = S0.d0[t];
+    P.gd[1][t] = S0.d1[t];
+    P.gd[2][t] = S0.d2[t];
+  }
 }
 
 // Shared memory of the tail starting at level l0 (10 floats per cell per level).
@@ -728,20 +793,18 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
   P.nu1 = c.p->nu1;
   P.nu2 = c.p->nu2;
   P.jfactor = c.jfactor;
-  P.coarse_sweeps = 64;
+  P.coarse_sweeps = 32;
   P.zero_init = zero_init ? 1 : 0;
   P.w = c.w;
   for (int l = l0; l < c.nl; ++l) {
-    TailLevel& T = P.lv[l - l0];
-    T.L = c.L[l];
-    T.kind = c.kind[l];
-    for (int q = 0; q < 3; ++q) {
-      T.d[q] = mx.d[l][q];
-      T.t[q] = mx.t[l][q];
-      T.r[q] = mx.r[l][q];
-    }
-    T.q = mx.q[l];
+    P.L[l - l0] = c.L[l];
+    P.kind[l - l0] = c.kind[l];
   }
+  for (int q = 0; q < 3; ++q) {
+    P.gd[q] = mx.d[l0][q];
+    P.gr[q] = mx.r[l0][q];
+  }
+  P.gq = mx.q[l0];
   int sizes[kMaxLevelsMixed];
   for (int l = 0; l < c.nl; ++l) sizes[l] = c.L[l].n;
   const size_t smem = tail_smem_bytes(sizes, l0, c.nl);
