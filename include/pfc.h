@@ -78,7 +78,8 @@ typedef struct pfc_params {
   int    inner_cycles; /* PFC_MIXED: FP32 V-cycles per FP64 defect correction */
   int    policy;       /* PFC_POLICY_HYBRID or PFC_POLICY_RB */
   double jacobi_weight;/* damping of the collective Jacobi sweep, (0, 1] */
-  int    jacobi_factor;/* Jacobi sweeps per requested sweep on Jacobi levels */
+  int    jacobi_factor;/* Jacobi sweeps per requested sweep on coarse Jacobi levels */
+  int    jacobi_factor0;/* the same on the finest level */
   double stiff_hi, stiff_lo; /* thresholds of the hybrid policy */
 } pfc_params;
 
@@ -92,7 +93,8 @@ typedef struct pfc_step_stats {
 
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
- * factor 2, stiff_hi 1000, stiff_lo 0.02.  n, L, eps, dt are set to 0.
+ * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.02.  n, L, eps,
+ * dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

@@ -37,7 +37,8 @@ class pfc_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("coarsest", ctypes.c_int), ("inner_cycles", ctypes.c_int),
                 ("policy", ctypes.c_int), ("jacobi_weight", ctypes.c_double),
-                ("jacobi_factor", ctypes.c_int), ("stiff_hi", ctypes.c_double),
+                ("jacobi_factor", ctypes.c_int), ("jacobi_factor0", ctypes.c_int),
+                ("stiff_hi", ctypes.c_double),
                 ("stiff_lo", ctypes.c_double)]
 
 

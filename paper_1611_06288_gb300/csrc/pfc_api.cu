@@ -58,7 +58,8 @@ int validate(const pfc_params* p) {
   if (p->smoother != PFC_NEWTON && p->smoother != PFC_PICARD) return PFC_EINVAL;
   if (p->precision == PFC_MIXED && p->inner_cycles < 1) return PFC_EINVAL;
   if (p->policy != PFC_POLICY_HYBRID && p->policy != PFC_POLICY_RB) return PFC_EINVAL;
-  if (!(p->jacobi_weight > 0 && p->jacobi_weight <= 1) || p->jacobi_factor < 1)
+  if (!(p->jacobi_weight > 0 && p->jacobi_weight <= 1) || p->jacobi_factor < 1 ||
+      p->jacobi_factor0 < 1)
     return PFC_EINVAL;
   if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
   int sizes[kMaxLevels];
@@ -194,7 +195,7 @@ int smooth_level(pfc_ctx* c, int l, const Level64& lv, int sweeps) {
   cudaStream_t st = c->st;
   Prof* pr = &c->prof;
   if (lv.kind == PFC_SWEEP_JACOBI) {
-    const int js = sweeps * c->p.jacobi_factor;
+    const int js = sweeps * (l == 0 ? c->p.jacobi_factor0 : c->p.jacobi_factor);
     PFC_TIMED(pr, PFC_K_SMOOTH, l, js, st,
               launch_jacobi(lv.L, c->p.smoother, js, c->p.jacobi_weight, lv.u[0], lv.u[1],
                             lv.u[2], lv.t[0], lv.t[1], lv.t[2], lv.S[0], lv.S[1], lv.S[2],
@@ -486,7 +487,8 @@ void pfc_default_params(pfc_params* p) {
   p->inner_cycles = 1;
   p->policy = PFC_POLICY_HYBRID;
   p->jacobi_weight = 0.7;
-  p->jacobi_factor = 2;
+  p->jacobi_factor = 4;
+  p->jacobi_factor0 = 2;
   p->stiff_hi = 1000.0;
   p->stiff_lo = 0.02;
 }

@@ -337,7 +337,7 @@ constexpr int kTailThreads = 1024;
 
 struct TailParams {
   int nlev;          // levels in the tail; the last one is the coarsest
-  int nu1, nu2, jfactor, coarse_sweeps;
+  int nu1, nu2, jfactor, jfactor_top, coarse_sweeps;
   int zero_init;     // the top tail level starts from d = 0
   float w;
   LvlF L[kTailMaxLevels];
@@ -603,6 +603,7 @@ __device__ void tail_coarse(const LvlF& L, int kind, SLev S, float w, int max_sw
         __syncthreads();
       }
     }
+    if ((sweep & 3) != 3) continue;   // test convergence every fourth sweep
     for (int o = 16; o > 0; o >>= 1) {
       change = fmaxf(change, __shfl_down_sync(0xffffffffu, change, o));
       size = fmaxf(size, __shfl_down_sync(0xffffffffu, size, o));
@@ -669,7 +670,7 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
     const SLev S = slev(smem, P, l);
     const bool zero = (l > 0) || zero_top;
     if (P.nu1 > 0) {
-      tail_smooth(P.L[l], P.kind[l], S, P.nu1, P.jfactor, P.w, zero);
+      tail_smooth(P.L[l], P.kind[l], S, P.nu1, l == 0 ? P.jfactor_top : P.jfactor, P.w, zero);
     } else if (zero) {
       const int cells = P.L[l].n * P.L[l].n * P.L[l].n;
       for (int t = threadIdx.x; t < cells; t += blockDim.x) {
@@ -685,7 +686,7 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
   for (int l = last - 1; l >= 0; --l) {
     const SLev S = slev(smem, P, l);
     tail_prolong(P.L[l].n, slev(smem, P, l + 1), S);
-    tail_smooth(P.L[l], P.kind[l], S, P.nu2, P.jfactor, P.w, false);
+    tail_smooth(P.L[l], P.kind[l], S, P.nu2, l == 0 ? P.jfactor_top : P.jfactor, P.w, false);
   }
   const SLev S0 = slev(smem, P, 0);
   const int cells = P.L[0].n * P.L[0].n * P.L[0].n;
@@ -727,7 +728,8 @@ struct Ctx32 {
   LvlF L[kMaxLevelsMixed];
   int kind[kMaxLevelsMixed];   // PFC_SWEEP_RB or PFC_SWEEP_JACOBI per level
   float w;                     // Jacobi weight
-  int jfactor;                 // Jacobi sweeps per requested sweep
+  int jfactor;                 // Jacobi sweeps per requested sweep (coarse levels)
+  int jfactor0;                // the same on the finest level
   cudaStream_t st;
   Prof* pr;
 };
@@ -767,7 +769,7 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   if (sweeps <= 0) return cudaSuccess;
   prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
   if (c.kind[l] == PFC_SWEEP_JACOBI) {
-    const int js = sweeps * c.jfactor;
+    const int js = sweeps * (l == 0 ? c.jfactor0 : c.jfactor);
     cudaError_t e = jacobi32(L, js, c.w, zero_init, d, c.mx->t[l], r, q, c.st);
     prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
     return e;
@@ -793,7 +795,8 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
   P.nu1 = c.p->nu1;
   P.nu2 = c.p->nu2;
   P.jfactor = c.jfactor;
-  P.coarse_sweeps = 32;
+  P.jfactor_top = l0 == 0 ? c.jfactor0 : c.jfactor;
+  P.coarse_sweeps = 24;
   P.zero_init = zero_init ? 1 : 0;
   P.w = c.w;
   for (int l = l0; l < c.nl; ++l) {
@@ -902,6 +905,7 @@ cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float*
   c.kind[0] = PFC_SWEEP_RB;
   c.w = 1.f;
   c.jfactor = 1;
+  c.jfactor0 = 1;
   c.st = st;
   c.pr = nullptr;
   return smooth32(c, 0, sweeps, zero_init);
@@ -946,6 +950,7 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
   c.pr = pr;
   c.w = (float)p.jacobi_weight;
   c.jfactor = p.jacobi_factor;
+  c.jfactor0 = p.jacobi_factor0;
   double h = p.L / p.n;
   for (int l = 0; l < nl; ++l) {
     c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
