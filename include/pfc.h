@@ -93,7 +93,7 @@ typedef struct pfc_step_stats {
 
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
- * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.02.  n, L, eps,
+ * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25.  n, L, eps,
  * dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep

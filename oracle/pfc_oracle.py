@@ -186,7 +186,7 @@ class Params:
     jacobi_weight: float = 0.7
     jacobi_factor: int = 2
     stiff_hi: float = 1000.0
-    stiff_lo: float = 0.02
+    stiff_lo: float = 0.25
 
 
 def cubic_f(a, b):

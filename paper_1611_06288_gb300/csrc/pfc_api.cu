@@ -490,7 +490,7 @@ void pfc_default_params(pfc_params* p) {
   p->jacobi_factor = 4;
   p->jacobi_factor0 = 2;
   p->stiff_hi = 1000.0;
-  p->stiff_lo = 0.02;
+  p->stiff_lo = 0.25;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {

@@ -62,7 +62,7 @@ def test_default_params_and_workspace(libpfc):
 
 def test_level_policy(libpfc):
     """Level sizes and the hybrid smoother choice (host-side): red-black where
-    108 tau/h^6 >= 1000 or <= 0.02, damped Jacobi in between."""
+    108 tau/h^6 >= 1000 or <= 0.25, damped Jacobi in between."""
     p = B.pfc_default_params()
     p.n, p.L, p.eps, p.dt = 128, 32.0, 0.025, 0.0125
     info = []
@@ -76,7 +76,7 @@ def test_level_policy(libpfc):
     assert [x[0] for x in info] == [128, 64, 32, 16, 8, 4, 2]
     for n, h, kind in info:
         s = 108 * p.dt / h ** 6
-        want = B.PFC_SWEEP_JACOBI if 0.02 < s < 1000 else B.PFC_SWEEP_RB
+        want = B.PFC_SWEEP_JACOBI if 0.25 < s < 1000 else B.PFC_SWEEP_RB
         assert kind == want and h == 32.0 / n
     assert [x[2] for x in info][:3] == [B.PFC_SWEEP_RB, B.PFC_SWEEP_JACOBI, B.PFC_SWEEP_JACOBI]
     p.policy = B.PFC_POLICY_RB
