@@ -330,6 +330,13 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
  * q = f'(phi) + (1-eps)/2, f(a) = (a+b)(a^2+b^2)/4, depends on u), then
  * u += d.  The paper has no mixed-precision form; this is a solver strategy
  * whose fixed point is the FP64 solution of N(u) = S.
+ *
+ * Every FP32 field (float*) below is stored colour-split: within each x-row
+ * (j, k) the n/2 cells with (i+j+k) even come first, ordered by i/2, then the
+ * n/2 cells with (i+j+k) odd; cell (i, j, k) is element
+ * (k*n + j)*n + ((i+j+k) & 1)*(n/2) + i/2.  A red-black half-sweep then reads
+ * and writes contiguous runs of one colour.  FP64 fields keep the natural
+ * layout.
  * --------------------------------------------------------------------- */
 
 /* FP64 residual r = S - N(u) stored as floats in d_r1..3, the coefficient

@@ -38,8 +38,56 @@ __device__ __forceinline__ void cell_of(int64_t t, int n, int& i, int& j, int& k
   k = (int)(r / n);
 }
 
-// FP64 residual r = S - N(u) -> FP32 copy, q = f'(phi) + (1-eps)/2 -> FP32,
-// and per-block partial sums of |r|^2 in FP64.
+// ---------------------------------------------------------------------------
+// Colour-split layout of the FP32 fields.  Within every x-row (j, k) of an
+// even-sized level the n/2 cells of colour 0 ((i+j+k) even) come first,
+// ordered by i/2, then the n/2 cells of colour 1.  A red-black half-sweep then
+// reads and writes contiguous runs of one colour only, and every neighbour of
+// a cell lies in the other colour's half of its row or of the adjacent rows.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t split_index(int i, int j, int k, int n) {
+  return ((int64_t)k * n + j) * n + ((i + j + k) & 1) * (n >> 1) + (i >> 1);
+}
+
+// The cell (p, j, k) of colour `colour` (i = 2p + ((j+k+colour) & 1)) and its six
+// neighbours, as split-layout indices.
+__device__ __forceinline__ Stencil split_stencil(int p, int j, int k, int colour, int n) {
+  const int half = n >> 1;
+  const int sigma = (j + k + colour) & 1;
+  const int jm = (j == 0) ? n - 1 : j - 1, jp = (j + 1 == n) ? 0 : j + 1;
+  const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+  int pm = p - 1 + sigma;
+  if (pm < 0) pm += half;
+  int pp = p + sigma;
+  if (pp >= half) pp -= half;
+  const int oc = (1 - colour) * half;
+  const int64_t row = ((int64_t)k * n + j) * n;
+  Stencil s;
+  s.c = row + colour * half + p;
+  s.xm = row + oc + pm;
+  s.xp = row + oc + pp;
+  s.ym = ((int64_t)k * n + jm) * n + oc + p;
+  s.yp = ((int64_t)k * n + jp) * n + oc + p;
+  s.zm = ((int64_t)km * n + j) * n + oc + p;
+  s.zp = ((int64_t)kp * n + j) * n + oc + p;
+  return s;
+}
+
+// Split-order thread index t -> (p, j, k, colour).
+__device__ __forceinline__ void split_cell(int64_t t, int n, int& p, int& j, int& k,
+                                           int& colour) {
+  const int half = n >> 1;
+  const int x = (int)(t % n);
+  const int64_t r = t / n;
+  j = (int)(r % n);
+  k = (int)(r / n);
+  colour = x >= half;
+  p = x - colour * half;
+}
+
+// FP64 residual r = S - N(u) -> FP32 copy, q = f'(phi) + (1-eps)/2 -> FP32
+// (both in the colour-split layout), and per-block partial sums of |r|^2 in
+// FP64.
 __global__ void k_residual64_to32(Lvl L, const double* __restrict__ phi,
                                   const double* __restrict__ mu,
                                   const double* __restrict__ om,
@@ -61,10 +109,11 @@ __global__ void k_residual64_to32(Lvl L, const double* __restrict__ phi,
     double x, y, z;
     residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
     acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
-    r1[t] = (float)x;
-    r2[t] = (float)y;
-    r3[t] = (float)z;
-    q[t] = (float)(cubic_fp(__ldg(phi + t), __ldg(b + t)) + L.c1);
+    const int64_t o = split_index(i, j, k, n);
+    r1[o] = (float)x;
+    r2[o] = (float)y;
+    r3[o] = (float)z;
+    q[o] = (float)(cubic_fp(__ldg(phi + t), __ldg(b + t)) + L.c1);
   }
   block_sum<1>(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
@@ -78,6 +127,7 @@ __global__ void k_reduce1(const double* __restrict__ partials, int nparts, doubl
   if (threadIdx.x == 0) out[0] = acc[0];
 }
 
+// 8-cell average of a split-layout field onto the (split-layout) level n/2.
 __global__ void k_restrict32(int n, const float* __restrict__ f, float* __restrict__ c) {
   const int nc = n >> 1;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -86,11 +136,9 @@ __global__ void k_restrict32(int n, const float* __restrict__ f, float* __restri
   cell_of(t, nc, I, J, K);
   float acc = 0.f;
 #pragma unroll
-  for (int s = 0; s < 8; ++s) {
-    const int64_t i = 2 * I + (s & 1), j = 2 * J + ((s >> 1) & 1), k = 2 * K + (s >> 2);
-    acc += __ldg(f + i + n * (j + (int64_t)n * k));
-  }
-  c[t] = 0.125f * acc;
+  for (int s = 0; s < 8; ++s)
+    acc += __ldg(f + split_index(2 * I + (s & 1), 2 * J + ((s >> 1) & 1), 2 * K + (s >> 2), n));
+  c[split_index(I, J, K, nc)] = 0.125f * acc;
 }
 
 // Pointwise solve of the linearised 3x3 system (q frozen):
@@ -110,9 +158,10 @@ __device__ __forceinline__ void lin_point(const LvlF& L, float sp, float sm_, fl
   dw = fmaf(-L.g3, dp, st3);
 }
 
-// One colour of a linear red-black sweep.  ZERO: the correction is known to
-// be zero everywhere before this half-sweep (first red pass from d = 0), so no
-// neighbour is read.
+// One colour of a linear red-black sweep on split-layout fields: thread t
+// owns the t-th cell of the colour, so the colour's cells are read and
+// written as contiguous runs.  ZERO: d = 0 everywhere before this half-sweep
+// (first red pass from d = 0), so no neighbour is read.
 template <bool ZERO>
 __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* d3,
                                const float* __restrict__ r1, const float* __restrict__ r2,
@@ -123,8 +172,7 @@ __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* 
   const int p = (int)(t % half);
   const int64_t r = t / half;
   const int j = (int)(r % n), k = (int)(r / n);
-  const int i = 2 * p + ((j + k + colour) & 1);
-  const Stencil s = stencil_at(i, j, k, n);
+  const Stencil s = split_stencil(p, j, k, colour, n);
   float sp = 0.f, sm_ = 0.f, sw = 0.f;
   if (!ZERO) {
     sp = nbsum(d1, s);
@@ -139,8 +187,8 @@ __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* 
   d3[s.c] = dw;
 }
 
-// One damped collective Jacobi sweep on J d = r, d -> t.  ZERO: d = 0 on
-// entry (nothing is read from d).
+// One damped collective Jacobi sweep on J d = r, d -> t (split layout).
+// ZERO: d = 0 on entry (nothing is read from d).
 template <bool ZERO>
 __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
                                const float* __restrict__ d2, const float* __restrict__ d3,
@@ -151,9 +199,9 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
   const int n = L.n;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n * n) return;
-  int i, j, k;
-  cell_of(t, n, i, j, k);
-  const Stencil s = stencil_at(i, j, k, n);
+  int p, j, k, colour;
+  split_cell(t, n, p, j, k, colour);
+  const Stencil s = split_stencil(p, j, k, colour, n);
   float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
   if (!ZERO) {
     sp = nbsum(d1, s);
@@ -171,7 +219,8 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
   t3[s.c] = fmaf(w, dw - w0, w0);
 }
 
-// rho = r - J d at the 8 children of each coarse cell, averaged.
+// rho = r - J d at the 8 children of each coarse cell, averaged (split layout
+// on both levels).
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
                                           const float* __restrict__ d3,
@@ -190,7 +239,7 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
-    const Stencil s = stencil_at(i, j, k, n);
+    const Stencil s = split_stencil(i >> 1, j, k, (i + j + k) & 1, n);
     const float p = __ldg(d1 + s.c), m = __ldg(d2 + s.c), w = __ldg(d3 + s.c);
     const float lm = fmaf(-6.f, m, nbsum(d2, s));
     const float lw = fmaf(-6.f, w, nbsum(d3, s));
@@ -199,9 +248,10 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
     a2 += __ldg(r2 + s.c) - (fmaf(-__ldg(q + s.c), p, m) - L.g * lw);
     a3 += __ldg(r3 + s.c) - fmaf(-L.gh, lp, w);
   }
-  c1[t] = 0.125f * a1;
-  c2[t] = 0.125f * a2;
-  c3[t] = 0.125f * a3;
+  const int64_t o = split_index(I, J, K, nc);
+  c1[o] = 0.125f * a1;
+  c2[o] = 0.125f * a2;
+  c3[o] = 0.125f * a3;
 }
 
 __device__ __forceinline__ float interp8f(const float* __restrict__ e, int64_t o000,
@@ -215,7 +265,8 @@ __device__ __forceinline__ float interp8f(const float* __restrict__ e, int64_t o
   return fmaf(27.f, __ldg(e + o000), acc);
 }
 
-// d += P e (trilinear, weights 27, 9, 3, 1 over 64).
+// d += P e (trilinear, weights 27, 9, 3, 1 over 64), split layout on both
+// levels; threads walk the fine level in split order.
 __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
                                 float* __restrict__ d1, float* __restrict__ d2,
@@ -223,26 +274,27 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
   const int nc = n >> 1;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * n * n) return;
-  int i, j, k;
-  cell_of(t, n, i, j, k);
+  int p, j, k, colour;
+  split_cell(t, n, p, j, k, colour);
+  const int i = 2 * p + ((j + k + colour) & 1);
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
   const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
   const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
-  const int64_t nn = (int64_t)nc * nc;
-  const int64_t zK = K * nn, zK2 = K2 * nn, yJ = (int64_t)J * nc, yJ2 = (int64_t)J2 * nc;
-  const int64_t o000 = I + yJ + zK, o100 = I2 + yJ + zK, o010 = I + yJ2 + zK,
-                o001 = I + yJ + zK2, o110 = I2 + yJ2 + zK, o101 = I2 + yJ + zK2,
-                o011 = I + yJ2 + zK2, o111 = I2 + yJ2 + zK2;
+  const int64_t o000 = split_index(I, J, K, nc), o100 = split_index(I2, J, K, nc),
+                o010 = split_index(I, J2, K, nc), o001 = split_index(I, J, K2, nc),
+                o110 = split_index(I2, J2, K, nc), o101 = split_index(I2, J, K2, nc),
+                o011 = split_index(I, J2, K2, nc), o111 = split_index(I2, J2, K2, nc);
   const float w = 1.0f / 64.0f;
   d1[t] = fmaf(w, interp8f(e1, o000, o100, o010, o001, o110, o101, o011, o111), d1[t]);
   d2[t] = fmaf(w, interp8f(e2, o000, o100, o010, o001, o110, o101, o011, o111), d2[t]);
   d3[t] = fmaf(w, interp8f(e3, o000, o100, o010, o001, o110, o101, o011, o111), d3[t]);
 }
 
-// Coarsest level of the linear problem: start from zero, sweeps in one block
-// (red-black, kind 0, or damped Jacobi through t, kind 1) until the largest
-// change is below 1e-7 of the largest value or max_sweeps.
+// Coarsest level of the linear problem when it is not part of a tail launch:
+// start from zero, sweeps in one block (red-black, kind 0, or damped Jacobi
+// through t, kind 1) until the largest change is below 1e-6 of the largest
+// value or max_sweeps.  Split layout.
 __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, float* d1,
                                      float* d2, float* d3, float* t1, float* t2, float* t3,
                                      const float* r1, const float* r2, const float* r3,
@@ -261,8 +313,9 @@ __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, 
     float change = 0.f, size = 0.f;
     if (kind == PFC_SWEEP_JACOBI) {
       for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-        const int i = t % n, j = (t / n) % n, k = t / (n * n);
-        const Stencil s = stencil_at(i, j, k, n);
+        int p, j, k, colour;
+        split_cell(t, n, p, j, k, colour);
+        const Stencil s = split_stencil(p, j, k, colour, n);
         float dp, dm, dw;
         lin_point(L, nbsum_coherent(d1, s), nbsum_coherent(d2, s), nbsum_coherent(d3, s),
                   q[s.c], r1[s.c], r2[s.c], r3[s.c], dp, dm, dw);
@@ -283,10 +336,8 @@ __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, 
     } else {
       for (int colour = 0; colour < 2; ++colour) {
         for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
-          const int p = t % half, r = t / half;
-          const int j = r % n, k = r / n;
-          const int i = 2 * p + ((j + k + colour) & 1);
-          const Stencil s = stencil_at(i, j, k, n);
+          const int p = t % half, rr = t / half;
+          const Stencil s = split_stencil(p, rr % n, rr / n, colour, n);
           float dp, dm, dw;
           lin_point(L, nbsum_coherent(d1, s), nbsum_coherent(d2, s), nbsum_coherent(d3, s),
                     q[s.c], r1[s.c], r2[s.c], r3[s.c], dp, dm, dw);
@@ -315,13 +366,12 @@ __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, 
         c = fmaxf(c, red[0][v]);
         z = fmaxf(z, red[1][v]);
       }
-      done = (c <= 1e-7f * z);
+      done = (c <= 1e-6f * z);
     }
     __syncthreads();
     if (done) break;
   }
 }
-
 
 // ---------------------------------------------------------------------------
 // Coarse tail: every level of at most kTailMaxN^3 cells of one FP32 V-cycle
@@ -637,16 +687,20 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
   const bool zero_top = P.zero_init != 0;
   {
     const SLev S0 = slev(smem, P, 0);
-    const int cells = P.L[0].n * P.L[0].n * P.L[0].n;
+    const int n0 = P.L[0].n;
+    const int cells = n0 * n0 * n0;
     for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-      S0.r0[t] = P.gr[0][t];
-      S0.r1[t] = P.gr[1][t];
-      S0.r2[t] = P.gr[2][t];
-      S0.q[t] = P.gq[t];
+      int p, j, k, colour;
+      split_cell(t, n0, p, j, k, colour);
+      const int o = (2 * p + ((j + k + colour) & 1)) + n0 * (j + n0 * k);   // natural index
+      S0.r0[o] = P.gr[0][t];
+      S0.r1[o] = P.gr[1][t];
+      S0.r2[o] = P.gr[2][t];
+      S0.q[o] = P.gq[t];
       if (!zero_top) {
-        S0.d0[t] = P.gd[0][t];
-        S0.d1[t] = P.gd[1][t];
-        S0.d2[t] = P.gd[2][t];
+        S0.d0[o] = P.gd[0][t];
+        S0.d1[o] = P.gd[1][t];
+        S0.d2[o] = P.gd[2][t];
       }
     }
     __syncthreads();
@@ -689,11 +743,15 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
     tail_smooth(P.L[l], P.kind[l], S, P.nu2, l == 0 ? P.jfactor_top : P.jfactor, P.w, false);
   }
   const SLev S0 = slev(smem, P, 0);
-  const int cells = P.L[0].n * P.L[0].n * P.L[0].n;
+  const int n0 = P.L[0].n;
+  const int cells = n0 * n0 * n0;
   for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-    P.gd[0][t] = S0.d0[t];
-    P.gd[1][t] = S0.d1[t];
-    P.gd[2][t] = S0.d2[t];
+    int p, j, k, colour;
+    split_cell(t, n0, p, j, k, colour);
+    const int o = (2 * p + ((j + k + colour) & 1)) + n0 * (j + n0 * k);
+    P.gd[0][t] = S0.d0[o];
+    P.gd[1][t] = S0.d1[o];
+    P.gd[2][t] = S0.d2[o];
   }
 }
 
@@ -706,14 +764,18 @@ size_t tail_smem_bytes(const int* sizes, int l0, int nl) {
 
 constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 KiB
 
-__global__ void k_correct64(int64_t cells, double* __restrict__ u1, double* __restrict__ u2,
+// u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
+__global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
                             const float* __restrict__ d2, const float* __restrict__ d3) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cells) return;
-  u1[t] += (double)__ldg(d1 + t);
-  u2[t] += (double)__ldg(d2 + t);
-  u3[t] += (double)__ldg(d3 + t);
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const int64_t o = split_index(i, j, k, n);
+  u1[t] += (double)__ldg(d1 + o);
+  u2[t] += (double)__ldg(d2 + o);
+  u3[t] += (double)__ldg(d3 + o);
 }
 
 inline int nblocks_reduce(int64_t cells) {
@@ -924,7 +986,7 @@ cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_ini
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
                              const float* d2, const float* d3, cudaStream_t st) {
   const int64_t cells = (int64_t)n * n * n;
-  k_correct64<<<grid_for(cells), kThreads, 0, st>>>(cells, u1, u2, u3, d1, d2, d3);
+  k_correct64<<<grid_for(cells), kThreads, 0, st>>>(n, u1, u2, u3, d1, d2, d3);
   return cudaGetLastError();
 }
 

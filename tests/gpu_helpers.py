@@ -26,3 +26,23 @@ def assert_close_field(got, ref, rtol, what=""):
     scale = max(float(np.abs(ref).max()), 1.0)
     err = float(np.abs(got - ref).max())
     assert err <= rtol * scale, f"{what}: max err {err:.3e} > {rtol:.1e} * {scale:.3e}"
+
+
+def split_perm(n):
+    """Position of every natural-order cell in the colour-split FP32 layout:
+    within each x-row the cells with (i+j+k) even come first (by i//2), then
+    the odd ones."""
+    k, j, i = np.indices((n, n, n))
+    return ((k * n + j) * n + ((i + j + k) & 1) * (n // 2) + (i >> 1)).ravel()
+
+
+def to_split(x):
+    n = x.shape[0]
+    y = np.empty(x.size, dtype=x.dtype)
+    y[split_perm(n)] = x.ravel()
+    return y.reshape(x.shape)
+
+
+def from_split(y):
+    n = y.shape[0]
+    return y.ravel()[split_perm(n)].reshape(y.shape)

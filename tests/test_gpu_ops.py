@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import assert_close_field, dev, empty, host
+from gpu_helpers import assert_close_field, dev, empty, from_split, host, split_perm, to_split
 from oracle import pfc_oracle as O
 from paper_1611_06288_gb300 import binding as B
 
@@ -184,14 +184,15 @@ def test_defect_and_correct(n):
     ref = O.residual(S, u, b, h, prm())
     assert rms == pytest.approx(O.rms(ref), rel=1e-12)
     for g, x in zip(r, ref):
-        # FP64 residual rounded to FP32: half an FP32 ulp
-        assert_close_field(host(g), x, 2 ** -23, "r32")
-    assert_close_field(host(q), O.jacobian_coefficient(u[0], b, prm()), 2 ** -23, "q32")
+        # FP64 residual rounded to FP32: half an FP32 ulp (colour-split layout)
+        assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
+    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 2 ** -23,
+                       "q32")
     # u += d: one FP64 rounding of the same sum on both sides -> bit-exact
     rng = np.random.default_rng(5)
     d = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
     du = [dev(x) for x in u]
-    B.pfc_op_correct(n, *du, *[dev(x, torch.float32) for x in d])
+    B.pfc_op_correct(n, *du, *[dev(to_split(x), torch.float32) for x in d])
     for g, x, y in zip(du, u, d):
         np.testing.assert_array_equal(host(g), x + y.astype(np.float64))
 
@@ -207,16 +208,17 @@ def test_linear_smoother_fp32(n, zero_init):
     d0 = [np.zeros((n,) * 3) if zero_init else 0.1 * rng.standard_normal((n,) * 3)
           for _ in range(3)]
     d0 = [x.astype(np.float32) for x in d0]
-    dd = [dev(x, torch.float32) for x in d0]
+    dd = [dev(to_split(x), torch.float32) for x in d0]
     if zero_init:                       # contents must not matter
         for t in dd:
             t.fill_(float("nan"))
-    B.pfc_op_lin_smooth(n, h, EPS, TAU, 2, zero_init, *dd, *[dev(x, torch.float32) for x in r],
-                        dev(q, torch.float32))
+    B.pfc_op_lin_smooth(n, h, EPS, TAU, 2, zero_init, *dd,
+                        *[dev(to_split(x), torch.float32) for x in r],
+                        dev(to_split(q), torch.float32))
     ref = O.linear_smooth([x.astype(np.float64) for x in d0],
                           [x.astype(np.float64) for x in r], q.astype(np.float64), h, p, 2)
     for g, x in zip(dd, ref):
-        assert_close_field(host(g), x, 1e-5, "d32")
+        assert_close_field(from_split(host(g)), x, 1e-5, "d32")
 
 
 @pytest.mark.parametrize("n", [4, 12, 32])
@@ -230,14 +232,23 @@ def test_linear_jacobi_fp32(n, zero_init, sweeps):
     r = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
     d0 = [np.zeros((n,) * 3, np.float32) if zero_init
           else (0.1 * rng.standard_normal((n,) * 3)).astype(np.float32) for _ in range(3)]
-    dd = [dev(x, torch.float32) for x in d0]
+    dd = [dev(to_split(x), torch.float32) for x in d0]
     if zero_init:
         for t_ in dd:
             t_.fill_(float("nan"))
     tt = [empty(n, torch.float32) for _ in range(3)]
     B.pfc_op_lin_jacobi(n, h, EPS, TAU, sweeps, 0.7, zero_init, *dd, *tt,
-                        *[dev(x, torch.float32) for x in r], dev(q, torch.float32))
+                        *[dev(to_split(x), torch.float32) for x in r],
+                        dev(to_split(q), torch.float32))
     ref = O.linear_smooth([x.astype(np.float64) for x in d0], [x.astype(np.float64) for x in r],
                           q.astype(np.float64), h, p, sweeps, "jacobi")
     for g, x in zip(dd, ref):
-        assert_close_field(host(g), x, 1e-5, "d32")
+        assert_close_field(from_split(host(g)), x, 1e-5, "d32")
+
+
+@pytest.mark.parametrize("n", [2, 4, 12])
+def test_split_layout_is_a_permutation(n):
+    perm = split_perm(n)
+    assert sorted(perm.tolist()) == list(range(n ** 3))
+    x = np.arange(n ** 3, dtype=np.float64).reshape((n,) * 3)
+    np.testing.assert_array_equal(from_split(to_split(x)), x)
