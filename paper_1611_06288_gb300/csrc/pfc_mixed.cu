@@ -12,6 +12,23 @@ constexpr int kThreads = 256;
 
 inline unsigned grid_for(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
 
+// 3-D launch over an nx * ny * nz index box: x is the fastest (contiguous)
+// index, 256 threads per block; kernels read (x, y, z) from the grid and
+// never divide.
+struct Launch3 {
+  dim3 grid, block;
+};
+inline Launch3 launch3(int nx, int ny, int nz) {
+  int bx = 1;
+  while (bx < nx && bx < 128) bx <<= 1;
+  int by = 256 / bx;
+  if (by > ny) by = ny;
+  Launch3 l;
+  l.block = dim3(bx, by, 1);
+  l.grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by, nz);
+  return l;
+}
+
 // FP32 constants of one level of the linearised system.
 struct LvlF {
   int n;
@@ -45,12 +62,12 @@ __device__ __forceinline__ void cell_of(int64_t t, int n, int& i, int& j, int& k
 // reads and writes contiguous runs of one colour only, and every neighbour of
 // a cell lies in the other colour's half of its row or of the adjacent rows.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t split_index(int i, int j, int k, int n) {
-  return ((int64_t)k * n + j) * n + ((i + j + k) & 1) * (n >> 1) + (i >> 1);
+__device__ __forceinline__ int split_index(int i, int j, int k, int n) {
+  return (k * n + j) * n + ((i + j + k) & 1) * (n >> 1) + (i >> 1);
 }
 
 // The cell (p, j, k) of colour `colour` (i = 2p + ((j+k+colour) & 1)) and its six
-// neighbours, as split-layout indices.
+// neighbours, as split-layout indices (32-bit arithmetic: n^3 < 2^31).
 __device__ __forceinline__ Stencil split_stencil(int p, int j, int k, int colour, int n) {
   const int half = n >> 1;
   const int sigma = (j + k + colour) & 1;
@@ -61,15 +78,15 @@ __device__ __forceinline__ Stencil split_stencil(int p, int j, int k, int colour
   int pp = p + sigma;
   if (pp >= half) pp -= half;
   const int oc = (1 - colour) * half;
-  const int64_t row = ((int64_t)k * n + j) * n;
+  const int row = (k * n + j) * n;
   Stencil s;
   s.c = row + colour * half + p;
   s.xm = row + oc + pm;
   s.xp = row + oc + pp;
-  s.ym = ((int64_t)k * n + jm) * n + oc + p;
-  s.yp = ((int64_t)k * n + jp) * n + oc + p;
-  s.zm = ((int64_t)km * n + j) * n + oc + p;
-  s.zp = ((int64_t)kp * n + j) * n + oc + p;
+  s.ym = (k * n + jm) * n + oc + p;
+  s.yp = (k * n + jp) * n + oc + p;
+  s.zm = (km * n + j) * n + oc + p;
+  s.zp = (kp * n + j) * n + oc + p;
   return s;
 }
 
@@ -130,10 +147,9 @@ __global__ void k_reduce1(const double* __restrict__ partials, int nparts, doubl
 // 8-cell average of a split-layout field onto the (split-layout) level n/2.
 __global__ void k_restrict32(int n, const float* __restrict__ f, float* __restrict__ c) {
   const int nc = n >> 1;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nc * nc * nc) return;
-  int I, J, K;
-  cell_of(t, nc, I, J, K);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
+            K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
   float acc = 0.f;
 #pragma unroll
   for (int s = 0; s < 8; ++s)
@@ -167,11 +183,9 @@ __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* 
                                const float* __restrict__ r1, const float* __restrict__ r2,
                                const float* __restrict__ r3, const float* __restrict__ q) {
   const int n = L.n, half = n >> 1;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)half * n * n) return;
-  const int p = (int)(t % half);
-  const int64_t r = t / half;
-  const int j = (int)(r % n), k = (int)(r / n);
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (p >= half || j >= n) return;
   const Stencil s = split_stencil(p, j, k, colour, n);
   float sp = 0.f, sm_ = 0.f, sw = 0.f;
   if (!ZERO) {
@@ -196,12 +210,12 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
                                float* __restrict__ t3, const float* __restrict__ r1,
                                const float* __restrict__ r2, const float* __restrict__ r3,
                                const float* __restrict__ q) {
-  const int n = L.n;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n * n) return;
-  int p, j, k, colour;
-  split_cell(t, n, p, j, k, colour);
-  const Stencil s = split_stencil(p, j, k, colour, n);
+  const int n = L.n, half = n >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (x >= n || j >= n) return;
+  const int colour = x >= half;
+  const Stencil s = split_stencil(x - colour * half, j, k, colour, n);
   float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
   if (!ZERO) {
     sp = nbsum(d1, s);
@@ -231,10 +245,9 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           float* __restrict__ c1, float* __restrict__ c2,
                                           float* __restrict__ c3) {
   const int n = L.n, nc = n >> 1;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)nc * nc * nc) return;
-  int I, J, K;
-  cell_of(t, nc, I, J, K);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
+            K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
   float a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
@@ -248,7 +261,7 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
     a2 += __ldg(r2 + s.c) - (fmaf(-__ldg(q + s.c), p, m) - L.g * lw);
     a3 += __ldg(r3 + s.c) - fmaf(-L.gh, lp, w);
   }
-  const int64_t o = split_index(I, J, K, nc);
+  const int o = split_index(I, J, K, nc);
   c1[o] = 0.125f * a1;
   c2[o] = 0.125f * a2;
   c3[o] = 0.125f * a3;
@@ -271,20 +284,21 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
                                 float* __restrict__ d1, float* __restrict__ d2,
                                 float* __restrict__ d3) {
-  const int nc = n >> 1;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n * n) return;
-  int p, j, k, colour;
-  split_cell(t, n, p, j, k, colour);
-  const int i = 2 * p + ((j + k + colour) & 1);
+  const int nc = n >> 1, half = n >> 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (x >= n || j >= n) return;
+  const int colour = x >= half;
+  const int i = 2 * (x - colour * half) + ((j + k + colour) & 1);
+  const int t = (k * n + j) * n + x;
   const int I = i >> 1, J = j >> 1, K = k >> 1;
   const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
   const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
   const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
-  const int64_t o000 = split_index(I, J, K, nc), o100 = split_index(I2, J, K, nc),
-                o010 = split_index(I, J2, K, nc), o001 = split_index(I, J, K2, nc),
-                o110 = split_index(I2, J2, K, nc), o101 = split_index(I2, J, K2, nc),
-                o011 = split_index(I, J2, K2, nc), o111 = split_index(I2, J2, K2, nc);
+  const int o000 = split_index(I, J, K, nc), o100 = split_index(I2, J, K, nc),
+            o010 = split_index(I, J2, K, nc), o001 = split_index(I, J, K2, nc),
+            o110 = split_index(I2, J2, K, nc), o101 = split_index(I2, J, K2, nc),
+            o011 = split_index(I, J2, K2, nc), o111 = split_index(I2, J2, K2, nc);
   const float w = 1.0f / 64.0f;
   d1[t] = fmaf(w, interp8f(e1, o000, o100, o010, o001, o110, o101, o011, o111), d1[t]);
   d2[t] = fmaf(w, interp8f(e2, o000, o100, o010, o001, o110, o101, o011, o111), d2[t]);
@@ -768,11 +782,11 @@ constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 K
 __global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
                             const float* __restrict__ d2, const float* __restrict__ d3) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n * n) return;
-  int i, j, k;
-  cell_of(t, n, i, j, k);
-  const int64_t o = split_index(i, j, k, n);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const int o = split_index(i, j, k, n);
   u1[t] += (double)__ldg(d1 + o);
   u2[t] += (double)__ldg(d2 + o);
   u3[t] += (double)__ldg(d3 + o);
@@ -799,14 +813,15 @@ struct Ctx32 {
 cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* const* d,
                      float* const* t, float* const* r, const float* q, cudaStream_t st) {
   const int64_t cells = (int64_t)L.n * L.n * L.n;
+  const Launch3 g = launch3(L.n, L.n, L.n);
   float* src[3] = {d[0], d[1], d[2]};
   float* dst[3] = {t[0], t[1], t[2]};
   for (int s = 0; s < sweeps; ++s) {
     if (zero_init && s == 0)
-      k_lin_jacobi32<true><<<grid_for(cells), kThreads, 0, st>>>(
+      k_lin_jacobi32<true><<<g.grid, g.block, 0, st>>>(
           L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
     else
-      k_lin_jacobi32<false><<<grid_for(cells), kThreads, 0, st>>>(
+      k_lin_jacobi32<false><<<g.grid, g.block, 0, st>>>(
           L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
     for (int c = 0; c < 3; ++c) {
       float* x = src[c];
@@ -836,14 +851,15 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
     prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
     return e;
   }
+  const Launch3 g = launch3(L.n / 2, L.n, L.n);
   for (int s = 0; s < sweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       if (zero_init && s == 0 && colour == 0)
-        k_lin_smooth32<true><<<grid_for(work), kThreads, 0, c.st>>>(L, colour, d[0], d[1],
-                                                                    d[2], r[0], r[1], r[2], q);
+        k_lin_smooth32<true><<<g.grid, g.block, 0, c.st>>>(L, colour, d[0], d[1], d[2], r[0],
+                                                           r[1], r[2], q);
       else
-        k_lin_smooth32<false><<<grid_for(work), kThreads, 0, c.st>>>(
-            L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
+        k_lin_smooth32<false><<<g.grid, g.block, 0, c.st>>>(L, colour, d[0], d[1], d[2], r[0],
+                                                            r[1], r[2], q);
     }
   }
   prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps, c.st);
@@ -918,15 +934,17 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   }
   if (e != cudaSuccess) return e;
   const int nc = L.n / 2;
+  const Launch3 gr = launch3(nc, nc, nc);
   prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
-  k_lin_residual_restrict32<<<grid_for((int64_t)nc * nc * nc), kThreads, 0, c.st>>>(
+  k_lin_residual_restrict32<<<gr.grid, gr.block, 0, c.st>>>(
       L, mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l],
       mx.r[l + 1][0], mx.r[l + 1][1], mx.r[l + 1][2]);
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
+  const Launch3 gp = launch3(L.n, L.n, L.n);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
-  k_prolong_add32<<<grid_for((int64_t)L.n * L.n * L.n), kThreads, 0, c.st>>>(
+  k_prolong_add32<<<gp.grid, gp.block, 0, c.st>>>(
       L.n, mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
       mx.d[l][2]);
   prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
@@ -985,8 +1003,8 @@ cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_ini
 
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
                              const float* d2, const float* d3, cudaStream_t st) {
-  const int64_t cells = (int64_t)n * n * n;
-  k_correct64<<<grid_for(cells), kThreads, 0, st>>>(n, u1, u2, u3, d1, d2, d3);
+  const Launch3 g = launch3(n, n, n);
+  k_correct64<<<g.grid, g.block, 0, st>>>(n, u1, u2, u3, d1, d2, d3);
   return cudaGetLastError();
 }
 
@@ -1021,9 +1039,9 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
   }
   cudaError_t e = cudaSuccess;
   for (int l = 1; l < nl && e == cudaSuccess; ++l) {
+    const Launch3 g = launch3(sizes[l], sizes[l], sizes[l]);
     prof_begin(pr, PFC_K_RESTRICT, st);
-    k_restrict32<<<grid_for((int64_t)sizes[l] * sizes[l] * sizes[l]), kThreads, 0, st>>>(
-        sizes[l - 1], mx.q[l - 1], mx.q[l]);
+    k_restrict32<<<g.grid, g.block, 0, st>>>(sizes[l - 1], mx.q[l - 1], mx.q[l]);
     prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
     e = cudaGetLastError();
   }
