@@ -83,7 +83,8 @@ def test_constant_state_is_fixed_point():
     s = PFCSolver(n, 10.0, 0.3, 0.1, phi0, tol=1e-13)
     s.step(3)
     np.testing.assert_allclose(host(s.phi()), 0.3, rtol=1e-13)
-    np.testing.assert_allclose(host(s.mu()), 0.3 ** 3 + 0.7 * 0.3, rtol=1e-13)
+    # mu carries the residual tolerance (1e-13) times O(1) gains
+    np.testing.assert_allclose(host(s.mu()), 0.3 ** 3 + 0.7 * 0.3, rtol=1e-11)
 
 
 def test_start_from_two_levels_and_set_state():
