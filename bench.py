@@ -76,6 +76,19 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate_replicas(local_seconds: float, steps: int, world_size: int, device=None):
+    """Whole-job throughput of independent replicas: every rank advanced its
+    own grid `steps` steps in `local_seconds`; the job time is the maximum
+    over ranks (all_reduce MAX) and the value is all steps / that time."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+    if world_size > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return t_max, world_size * steps / t_max
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -276,12 +289,7 @@ def run_ours(args):
     dom_launches, dom_time = B.pfc_profile_read(s.ctx, B.KERNEL_CLASSES.index(dom_cls), dom_lvl)
     s.profile([])
 
-    t_local = ms_total / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if ws > 1:
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-    t_max = float(t.item())
-    value = ws * args.steps / t_max
+    t_max, value = aggregate_replicas(ms_total / 1e3, args.steps, ws, dev)
 
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
