@@ -2,6 +2,8 @@
 // FP32 linear multigrid for the correction (see pfc_mixed.h).
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "pfc_internal.h"
 #include "pfc_mixed.h"
 
@@ -779,6 +781,328 @@ size_t tail_smem_bytes(const int* sizes, int l0, int nl) {
 constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 KiB
 
 // u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
+// ---------------------------------------------------------------------------
+// Cluster V-cycle: the FP32 sub-V-cycle of every level of at most
+// kClusterMaxN^3 cells in one launch of a thread-block cluster.  Stages are
+// separated by the cluster's hardware barrier (release/acquire at cluster
+// scope); levels of at most kClusterSoloCells cells run in CTA 0 alone with
+// block barriers.  Fields stay in global memory (split layout, L2-resident at
+// these sizes) and are read with L2 loads, because other CTAs of the cluster
+// wrote them.
+// ---------------------------------------------------------------------------
+namespace cgx = cooperative_groups;
+
+constexpr int kClusterMaxN = 32;
+constexpr int kClusterCTAs = 8;
+constexpr int kClusterThreads = 1024;
+constexpr int kClusterSoloCells = 512;
+constexpr int kClusterMaxLevels = 8;
+
+struct ClLevel {
+  LvlF L;
+  int kind;
+  float* d[3];
+  float* t[3];
+  float* r[3];
+  const float* q;
+};
+
+struct ClusterParams {
+  int nlev, nu1, nu2, jfactor, jfactor_top, coarse_sweeps, zero_init;
+  float w;
+  ClLevel lv[kClusterMaxLevels];
+};
+
+__device__ __forceinline__ float nbs_cg(const float* v, const Stencil& s) {
+  return ((__ldcg(v + s.xm) + __ldcg(v + s.xp)) + (__ldcg(v + s.ym) + __ldcg(v + s.yp))) +
+         (__ldcg(v + s.zm) + __ldcg(v + s.zp));
+}
+
+// Work team of a stage: the whole cluster, or CTA 0 alone on small levels.
+struct Team {
+  int first, stride;   // this thread's first work index and the team's size
+  bool member, solo;
+  __device__ __forceinline__ Team(bool solo_, unsigned rank) : solo(solo_) {
+    if (solo) {
+      member = rank == 0;
+      first = threadIdx.x;
+      stride = blockDim.x;
+    } else {
+      member = true;
+      first = (int)rank * blockDim.x + threadIdx.x;
+      stride = kClusterCTAs * blockDim.x;
+    }
+  }
+  __device__ __forceinline__ void sync() const {
+    if (solo)
+      __syncthreads();
+    else
+      cgx::this_cluster().sync();
+  }
+};
+
+__device__ __forceinline__ bool cl_solo(const LvlF& L) {
+  return L.n * L.n * L.n <= kClusterSoloCells;
+}
+
+__device__ void cl_smooth(const ClLevel& T, int sweeps, int jfactor, float w, bool zero,
+                          const Team& tm) {
+  if (sweeps <= 0) return;
+  const LvlF& L = T.L;
+  const int n = L.n, half = n >> 1, cells = n * n * n;
+  if (T.kind == PFC_SWEEP_JACOBI) {
+    const int js = sweeps * jfactor;
+    float *s0 = T.d[0], *s1 = T.d[1], *s2 = T.d[2], *o0 = T.t[0], *o1 = T.t[1], *o2 = T.t[2];
+    for (int sw = 0; sw < js; ++sw) {
+      const bool z = zero && sw == 0;
+      if (tm.member) {
+        for (int t = tm.first; t < cells; t += tm.stride) {
+          const int x = t % n, r = t / n, j = r % n, k = r / n;
+          const int colour = x >= half;
+          const Stencil s = split_stencil(x - colour * half, j, k, colour, n);
+          float sp = 0.f, sm_ = 0.f, sw_ = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
+          if (!z) {
+            sp = nbs_cg(s0, s);
+            sm_ = nbs_cg(s1, s);
+            sw_ = nbs_cg(s2, s);
+            p0 = __ldcg(s0 + s.c);
+            m0 = __ldcg(s1 + s.c);
+            w0 = __ldcg(s2 + s.c);
+          }
+          float dp, dm, dw;
+          lin_point(L, sp, sm_, sw_, __ldcg(T.q + s.c), __ldcg(T.r[0] + s.c),
+                    __ldcg(T.r[1] + s.c), __ldcg(T.r[2] + s.c), dp, dm, dw);
+          __stcg(o0 + s.c, fmaf(w, dp - p0, p0));
+          __stcg(o1 + s.c, fmaf(w, dm - m0, m0));
+          __stcg(o2 + s.c, fmaf(w, dw - w0, w0));
+        }
+      }
+      tm.sync();
+      float* x;
+      x = s0; s0 = o0; o0 = x;
+      x = s1; s1 = o1; o1 = x;
+      x = s2; s2 = o2; o2 = x;
+    }
+    if (js & 1) {
+      if (tm.member) {
+        for (int t = tm.first; t < cells; t += tm.stride) {
+          __stcg(T.d[0] + t, __ldcg(s0 + t));
+          __stcg(T.d[1] + t, __ldcg(s1 + t));
+          __stcg(T.d[2] + t, __ldcg(s2 + t));
+        }
+      }
+      tm.sync();
+    }
+    return;
+  }
+  const int ccells = half * n * n;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    for (int colour = 0; colour < 2; ++colour) {
+      const bool z = zero && sw == 0 && colour == 0;
+      if (tm.member) {
+        for (int t = tm.first; t < ccells; t += tm.stride) {
+          const int p = t % half, r = t / half;
+          const Stencil s = split_stencil(p, r % n, r / n, colour, n);
+          float sp = 0.f, sm_ = 0.f, sw_ = 0.f;
+          if (!z) {
+            sp = nbs_cg(T.d[0], s);
+            sm_ = nbs_cg(T.d[1], s);
+            sw_ = nbs_cg(T.d[2], s);
+          }
+          float dp, dm, dw;
+          lin_point(L, sp, sm_, sw_, __ldcg(T.q + s.c), __ldcg(T.r[0] + s.c),
+                    __ldcg(T.r[1] + s.c), __ldcg(T.r[2] + s.c), dp, dm, dw);
+          __stcg(T.d[0] + s.c, dp);
+          __stcg(T.d[1] + s.c, dm);
+          __stcg(T.d[2] + s.c, dw);
+        }
+      }
+      tm.sync();
+    }
+  }
+}
+
+__device__ void cl_zero(const ClLevel& T, const Team& tm) {
+  const int cells = T.L.n * T.L.n * T.L.n;
+  if (tm.member) {
+    for (int t = tm.first; t < cells; t += tm.stride) {
+      __stcg(T.d[0] + t, 0.f);
+      __stcg(T.d[1] + t, 0.f);
+      __stcg(T.d[2] + t, 0.f);
+    }
+  }
+  tm.sync();
+}
+
+// rho = r - J d on F, averaged onto C.r (team of the fine level).
+__device__ void cl_restrict(const ClLevel& F, const ClLevel& C, const Team& tm) {
+  const LvlF& L = F.L;
+  const int n = L.n, nc = n >> 1, ccells = nc * nc * nc;
+  if (tm.member) {
+    for (int t = tm.first; t < ccells; t += tm.stride) {
+      const int I = t % nc, r = t / nc, J = r % nc, K = r / nc;
+      float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int ch = 0; ch < 8; ++ch) {
+        const int i = 2 * I + (ch & 1), j = 2 * J + ((ch >> 1) & 1), k = 2 * K + (ch >> 2);
+        const Stencil s = split_stencil(i >> 1, j, k, (i + j + k) & 1, n);
+        const float p = __ldcg(F.d[0] + s.c), m = __ldcg(F.d[1] + s.c), w = __ldcg(F.d[2] + s.c);
+        const float lm = fmaf(-6.f, m, nbs_cg(F.d[1], s));
+        const float lw = fmaf(-6.f, w, nbs_cg(F.d[2], s));
+        const float lp = fmaf(-6.f, p, nbs_cg(F.d[0], s));
+        a1 += __ldcg(F.r[0] + s.c) - fmaf(-L.tg, lm, p);
+        a2 += __ldcg(F.r[1] + s.c) - (fmaf(-__ldcg(F.q + s.c), p, m) - L.g * lw);
+        a3 += __ldcg(F.r[2] + s.c) - fmaf(-L.gh, lp, w);
+      }
+      const int o = split_index(I, J, K, nc);
+      __stcg(C.r[0] + o, 0.125f * a1);
+      __stcg(C.r[1] + o, 0.125f * a2);
+      __stcg(C.r[2] + o, 0.125f * a3);
+    }
+  }
+  tm.sync();
+}
+
+// F.d += P C.d (team of the fine level).
+__device__ void cl_prolong(const ClLevel& C, const ClLevel& F, const Team& tm) {
+  const int n = F.L.n, nc = n >> 1, half = n >> 1, cells = n * n * n;
+  if (tm.member) {
+    for (int t = tm.first; t < cells; t += tm.stride) {
+      const int x = t % n, r = t / n, j = r % n, k = r / n;
+      const int colour = x >= half;
+      const int i = 2 * (x - colour * half) + ((j + k + colour) & 1);
+      const int I = i >> 1, J = j >> 1, K = k >> 1;
+      const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
+      const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
+      const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
+      const int o000 = split_index(I, J, K, nc), o100 = split_index(I2, J, K, nc),
+                o010 = split_index(I, J2, K, nc), o001 = split_index(I, J, K2, nc),
+                o110 = split_index(I2, J2, K, nc), o101 = split_index(I2, J, K2, nc),
+                o011 = split_index(I, J2, K2, nc), o111 = split_index(I2, J2, K2, nc);
+      for (int c = 0; c < 3; ++c) {
+        const float* e = C.d[c];
+        const float g2 = (__ldcg(e + o100) + __ldcg(e + o010)) + __ldcg(e + o001);
+        const float g3 = (__ldcg(e + o110) + __ldcg(e + o101)) + __ldcg(e + o011);
+        float acc = fmaf(3.f, g3, __ldcg(e + o111));
+        acc = fmaf(9.f, g2, acc);
+        acc = fmaf(27.f, __ldcg(e + o000), acc);
+        __stcg(F.d[c] + t, fmaf(1.0f / 64.0f, acc, __ldcg(F.d[c] + t)));
+      }
+    }
+  }
+  tm.sync();
+}
+
+// Coarsest level, in CTA 0: from d = 0, sweeps until the largest change is
+// <= 1e-6 of the largest value (tested every fourth sweep) or max_sweeps.
+__device__ void cl_coarse(const ClLevel& T, float w, int max_sweeps, float (*red)[32],
+                          int* done) {
+  const LvlF& L = T.L;
+  const int n = L.n, half = n >> 1, cells = n * n * n, ccells = half * n * n;
+  for (int t = threadIdx.x; t < cells; t += blockDim.x)
+    for (int c = 0; c < 3; ++c) __stcg(T.d[c] + t, 0.f);
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    float change = 0.f, size = 0.f;
+    if (T.kind == PFC_SWEEP_JACOBI) {
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        const int x = t % n, r = t / n;
+        const int colour = x >= half;
+        const Stencil s = split_stencil(x - colour * half, r % n, r / n, colour, n);
+        float dp, dm, dw;
+        lin_point(L, nbs_cg(T.d[0], s), nbs_cg(T.d[1], s), nbs_cg(T.d[2], s),
+                  __ldcg(T.q + s.c), __ldcg(T.r[0] + s.c), __ldcg(T.r[1] + s.c),
+                  __ldcg(T.r[2] + s.c), dp, dm, dw);
+        const float p0 = __ldcg(T.d[0] + s.c), m0 = __ldcg(T.d[1] + s.c),
+                    w0 = __ldcg(T.d[2] + s.c);
+        __stcg(T.t[0] + s.c, fmaf(w, dp - p0, p0));
+        __stcg(T.t[1] + s.c, fmaf(w, dm - m0, m0));
+        __stcg(T.t[2] + s.c, fmaf(w, dw - w0, w0));
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        for (int c = 0; c < 3; ++c) {
+          const float nv = __ldcg(T.t[c] + t);
+          change = fmaxf(change, fabsf(nv - __ldcg(T.d[c] + t)));
+          size = fmaxf(size, fabsf(nv));
+          __stcg(T.d[c] + t, nv);
+        }
+      }
+      __syncthreads();
+    } else {
+      for (int colour = 0; colour < 2; ++colour) {
+        for (int t = threadIdx.x; t < ccells; t += blockDim.x) {
+          const int p = t % half, r = t / half;
+          const Stencil s = split_stencil(p, r % n, r / n, colour, n);
+          float dp, dm, dw;
+          lin_point(L, nbs_cg(T.d[0], s), nbs_cg(T.d[1], s), nbs_cg(T.d[2], s),
+                    __ldcg(T.q + s.c), __ldcg(T.r[0] + s.c), __ldcg(T.r[1] + s.c),
+                    __ldcg(T.r[2] + s.c), dp, dm, dw);
+          change = fmaxf(change, fmaxf(fabsf(dp - __ldcg(T.d[0] + s.c)),
+                                       fmaxf(fabsf(dm - __ldcg(T.d[1] + s.c)),
+                                             fabsf(dw - __ldcg(T.d[2] + s.c)))));
+          size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+          __stcg(T.d[0] + s.c, dp);
+          __stcg(T.d[1] + s.c, dm);
+          __stcg(T.d[2] + s.c, dw);
+        }
+        __syncthreads();
+      }
+    }
+    if ((sweep & 3) != 3) continue;
+    for (int o = 16; o > 0; o >>= 1) {
+      change = fmaxf(change, __shfl_down_sync(0xffffffffu, change, o));
+      size = fmaxf(size, __shfl_down_sync(0xffffffffu, size, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = change;
+      red[1][threadIdx.x >> 5] = size;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float cmax = 0.f, z = 0.f;
+      for (int v = 0; v < (int)((blockDim.x + 31) >> 5); ++v) {
+        cmax = fmaxf(cmax, red[0][v]);
+        z = fmaxf(z, red[1][v]);
+      }
+      *done = (cmax <= 1e-6f * z);
+    }
+    __syncthreads();
+    if (*done) break;
+  }
+}
+
+__global__ void __launch_bounds__(kClusterThreads) k_lin_cluster32(ClusterParams P) {
+  __shared__ float red[2][32];
+  __shared__ int done;
+  const unsigned rank = cgx::this_cluster().block_rank();
+  const int last = P.nlev - 1;
+  for (int l = 0; l < last; ++l) {
+    const bool solo = cl_solo(P.lv[l].L);
+    const Team tm(solo, rank);
+    const bool zero = (l > 0) || P.zero_init;
+    const int jf = l == 0 ? P.jfactor_top : P.jfactor;
+    if (P.nu1 > 0)
+      cl_smooth(P.lv[l], P.nu1, jf, P.w, zero, tm);
+    else if (zero)
+      cl_zero(P.lv[l], tm);
+    cl_restrict(P.lv[l], P.lv[l + 1], tm);
+  }
+  // the coarsest level runs in CTA 0; the cluster barrier after it publishes
+  // its result to the other CTAs
+  if (!cl_solo(P.lv[last].L) || last == 0) cgx::this_cluster().sync();
+  if (rank == 0) cl_coarse(P.lv[last], P.w, P.coarse_sweeps, red, &done);
+  cgx::this_cluster().sync();
+  for (int l = last - 1; l >= 0; --l) {
+    const bool solo = cl_solo(P.lv[l].L);
+    const Team tm(solo, rank);
+    const int jf = l == 0 ? P.jfactor_top : P.jfactor;
+    cl_prolong(P.lv[l + 1], P.lv[l], tm);
+    cl_smooth(P.lv[l], P.nu2, jf, P.w, false, tm);
+    // a solo level hands its result to the cluster level above it
+    if (solo && l > 0 && !cl_solo(P.lv[l - 1].L)) cgx::this_cluster().sync();
+  }
+}
+
 __global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
                             const float* __restrict__ d2, const float* __restrict__ d3) {
@@ -806,6 +1130,7 @@ struct Ctx32 {
   float w;                     // Jacobi weight
   int jfactor;                 // Jacobi sweeps per requested sweep (coarse levels)
   int jfactor0;                // the same on the finest level
+  int use_cluster;             // levels <= 32^3 in one cluster launch
   cudaStream_t st;
   Prof* pr;
 };
@@ -902,9 +1227,51 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
   return cudaGetLastError();
 }
 
+cudaError_t cluster32(const Ctx32& c, int l0, bool zero_init) {
+  MixedBufs& mx = *c.mx;
+  ClusterParams P;
+  P.nlev = c.nl - l0;
+  P.nu1 = c.p->nu1;
+  P.nu2 = c.p->nu2;
+  P.jfactor = c.jfactor;
+  P.jfactor_top = l0 == 0 ? c.jfactor0 : c.jfactor;
+  P.coarse_sweeps = 24;
+  P.zero_init = zero_init ? 1 : 0;
+  P.w = c.w;
+  for (int l = l0; l < c.nl; ++l) {
+    ClLevel& T = P.lv[l - l0];
+    T.L = c.L[l];
+    T.kind = c.kind[l];
+    for (int q = 0; q < 3; ++q) {
+      T.d[q] = mx.d[l][q];
+      T.t[q] = mx.t[l][q];
+      T.r[q] = mx.r[l][q];
+    }
+    T.q = mx.q[l];
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCTAs, 1, 1);
+  cfg.blockDim = dim3(kClusterThreads, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c.st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kClusterCTAs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_lin_cluster32, P);
+  prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
+  return e;
+}
+
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
+  if (L.n <= kClusterMaxN && c.nl - l <= kClusterMaxLevels && c.use_cluster)
+    return cluster32(c, l, zero_init);
   if (L.n <= kTailMaxN && c.nl - l <= kTailMaxLevels) {
     int sizes[kMaxLevelsMixed];
     for (int q = 0; q < c.nl; ++q) sizes[q] = c.L[q].n;
@@ -986,6 +1353,7 @@ cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float*
   c.w = 1.f;
   c.jfactor = 1;
   c.jfactor0 = 1;
+  c.use_cluster = 0;
   c.st = st;
   c.pr = nullptr;
   return smooth32(c, 0, sweeps, zero_init);
@@ -1031,6 +1399,7 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
   c.w = (float)p.jacobi_weight;
   c.jfactor = p.jacobi_factor;
   c.jfactor0 = p.jacobi_factor0;
+  c.use_cluster = 1;
   double h = p.L / p.n;
   for (int l = 0; l < nl; ++l) {
     c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
