@@ -810,6 +810,7 @@ constexpr int kDsmCTAs = 8;
 constexpr int kDsmThreads = 1024;
 constexpr int kDsmMaxN = 32;
 constexpr int kDsmMaxSlab = 4;
+constexpr size_t kDsmMaxSmem = 226 * 1024;   // + 272 B static <= 227 KiB per block
 
 struct DsmParams {
   int nslab;         // slab levels, finest first
@@ -1319,7 +1320,7 @@ int dsm_plan(const Ctx32& c, int l0, size_t* smem) {
   if (ns == 0 || l >= c.nl || c.nl - l > kTailMaxLevels) return 0;
   for (int m = l; m < c.nl; ++m) floats += 10 * (size_t)c.L[m].n * c.L[m].n * c.L[m].n;
   *smem = floats * sizeof(float);
-  return (*smem <= kTailMaxSmem) ? ns : 0;
+  return (*smem <= kDsmMaxSmem) ? ns : 0;
 }
 
 cudaError_t dsm32(const Ctx32& c, int l0, int ns, size_t smem, bool zero_init) {
@@ -1363,7 +1364,7 @@ cudaError_t dsm32(const Ctx32& c, int l0, int ns, size_t smem, bool zero_init) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_lin_dsm32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kTailMaxSmem);
+                                         (int)kDsmMaxSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
