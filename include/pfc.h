@@ -81,6 +81,10 @@ typedef struct pfc_params {
   int    jacobi_factor;/* Jacobi sweeps per requested sweep on coarse Jacobi levels */
   int    jacobi_factor0;/* the same on the finest level */
   double stiff_hi, stiff_lo; /* thresholds of the hybrid policy */
+  double coarse_stiffness;   /* also stop coarsening at the first level (below
+                                the finest, of at most 16^3 cells) whose
+                                stiffness 108 tau/h^6 is <= this: there the
+                                system is nearly pointwise and sweeps solve it */
 } pfc_params;
 
 typedef struct pfc_step_stats {
@@ -93,8 +97,8 @@ typedef struct pfc_step_stats {
 
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
- * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25.  n, L, eps,
- * dt are set to 0.
+ * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
+ * coarse_stiffness 0.05.  n, L, eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

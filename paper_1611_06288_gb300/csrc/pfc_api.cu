@@ -37,13 +37,19 @@ constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Level sizes: halve while the size is even and larger than `coarsest`.
+// Level sizes: halve while the size is even and larger than `coarsest`, and
+// stop early at the first coarse level of at most 16^3 cells whose stiffness
+// 108 tau/h^6 is at most coarse_stiffness.
 int level_sizes(const pfc_params* p, int* sizes) {
   int n = p->n, nl = 0;
+  double h = p->L / p->n;
   sizes[nl++] = n;
   while (n % 2 == 0 && n > p->coarsest && nl < kMaxLevels) {
     n /= 2;
+    h *= 2.0;
     sizes[nl++] = n;
+    const double s = 108.0 * p->dt / (h * h * h * h * h * h);
+    if (n <= 16 && s <= p->coarse_stiffness) break;
   }
   return nl;
 }
@@ -62,6 +68,7 @@ int validate(const pfc_params* p) {
       p->jacobi_factor0 < 1)
     return PFC_EINVAL;
   if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
+  if (!(p->coarse_stiffness >= 0)) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -491,6 +498,7 @@ void pfc_default_params(pfc_params* p) {
   p->jacobi_factor0 = 2;
   p->stiff_hi = 1000.0;
   p->stiff_lo = 0.25;
+  p->coarse_stiffness = 0.05;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {

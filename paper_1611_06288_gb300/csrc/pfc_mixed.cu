@@ -2,8 +2,6 @@
 // FP32 linear multigrid for the correction (see pfc_mixed.h).
 #include <math.h>
 
-#include <cooperative_groups.h>
-
 #include "pfc_internal.h"
 #include "pfc_mixed.h"
 
@@ -792,391 +790,6 @@ size_t tail_smem_bytes(const int* sizes, int l0, int nl) {
 constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 KiB
 
 // u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
-// ---------------------------------------------------------------------------
-// Cluster V-cycle in distributed shared memory.  One launch of a cluster of
-// kDsmCTAs CTAs runs the FP32 sub-V-cycle of every level of at most
-// kDsmMaxN^3 cells.  Levels with n >= kDsmCTAs ("slab" levels) are split in
-// z-slabs of n / kDsmCTAs planes, one per CTA, in shared memory (natural
-// layout inside the slab); a z-neighbour across a slab edge is read from the
-// neighbouring CTA's shared memory through map_shared_rank.  Stages on slab
-// levels end with the cluster barrier (release/acquire at cluster scope).  The
-// levels below live in CTA 0's shared memory and run the single-block tail
-// routines; the slab level above them restricts into / prolongs from CTA 0's
-// copy remotely.
-// ---------------------------------------------------------------------------
-namespace cgx = cooperative_groups;
-
-constexpr int kDsmCTAs = 8;
-constexpr int kDsmThreads = 1024;
-constexpr int kDsmMaxN = 32;
-constexpr int kDsmMaxSlab = 4;
-constexpr size_t kDsmMaxSmem = 226 * 1024;   // + 272 B static <= 227 KiB per block
-
-struct DsmParams {
-  int nslab;         // slab levels, finest first
-  int nu1, nu2, jfactor, jfactor_top, zero_init;
-  float w;
-  LvlF L[kDsmMaxSlab];
-  int kind[kDsmMaxSlab];
-  float* gd[3];      // top slab level in global memory (split layout)
-  const float* gr[3];
-  const float* gq;
-  TailParams tail;   // levels below the slabs, in CTA 0 (zero-initialised)
-};
-
-// One slab level of this CTA: planes [rank*P, rank*P + P) of an n^3 level.
-struct Slab {
-  int n, P, plane;
-  float *d0, *d1, *d2, *t0, *t1, *t2, *r0, *r1, *r2, *q;
-};
-
-__device__ __forceinline__ Slab slab_at(float* smem, const DsmParams& D, int s) {
-  int off = 0;
-  for (int m = 0; m < s; ++m) off += 10 * (D.L[m].n / kDsmCTAs) * D.L[m].n * D.L[m].n;
-  Slab S;
-  S.n = D.L[s].n;
-  S.P = S.n / kDsmCTAs;
-  S.plane = S.n * S.n;
-  const int c = S.P * S.plane;
-  float* b = smem + off;
-  S.d0 = b;
-  S.d1 = b + c;
-  S.d2 = b + 2 * c;
-  S.t0 = b + 3 * c;
-  S.t1 = b + 4 * c;
-  S.t2 = b + 5 * c;
-  S.r0 = b + 6 * c;
-  S.r1 = b + 7 * c;
-  S.r2 = b + 8 * c;
-  S.q = b + 9 * c;
-  return S;
-}
-
-__device__ __forceinline__ float* tail_base(float* smem, const DsmParams& D) {
-  int off = 0;
-  for (int m = 0; m < D.nslab; ++m) off += 10 * (D.L[m].n / kDsmCTAs) * D.L[m].n * D.L[m].n;
-  return smem + off;
-}
-
-// Start of global plane kg of a slab array, in the CTA that owns it.
-__device__ __forceinline__ float* plane_ptr(float* local, int kg, int P, int plane, int rank) {
-  const int owner = kg / P;
-  float* base = (owner == rank) ? local : cgx::this_cluster().map_shared_rank(local, owner);
-  return base + (kg - owner * P) * plane;
-}
-
-// Cell walker over this CTA's slab: thread -> (i, j, kl0), kl advances by kstep.
-struct SWalk {
-  int n, P, i, j, k0, kstep, im, ip, jm, jp;
-  bool active;
-  __device__ __forceinline__ SWalk(int n_, int P_) : n(n_), P(P_) {
-    const int plane = n * n;
-    kstep = blockDim.x / plane;
-    if (kstep < 1) kstep = 1;
-    if (kstep > P) kstep = P;
-    const int tid = threadIdx.x;
-    k0 = tid / plane;
-    const int rem = tid - k0 * plane;
-    j = rem / n;
-    i = rem - j * n;
-    active = (tid < plane * kstep);
-    im = (i == 0) ? n - 1 : i - 1;
-    ip = (i + 1 == n) ? 0 : i + 1;
-    jm = (j == 0) ? n - 1 : j - 1;
-    jp = (j + 1 == n) ? 0 : j + 1;
-  }
-};
-
-// Sum of the six neighbours of (i, j, local plane kl) of a slab array.
-__device__ __forceinline__ float slab_nb(float* a, const SWalk& W, int kl, int rank) {
-  const int n = W.n, plane = n * n, P = W.P;
-  const float* row = a + kl * plane;
-  float s = (row[W.im + n * W.j] + row[W.ip + n * W.j]) + (row[W.i + n * W.jm] + row[W.i + n * W.jp]);
-  const int kg = rank * P + kl;
-  const int ng = n;   // planes in the whole level
-  const int km = (kg == 0) ? ng - 1 : kg - 1, kp = (kg + 1 == ng) ? 0 : kg + 1;
-  const int ij = W.i + n * W.j;
-  const float zm = (kl > 0) ? a[(kl - 1) * plane + ij] : plane_ptr(a, km, P, plane, rank)[ij];
-  const float zp = (kl + 1 < P) ? a[(kl + 1) * plane + ij] : plane_ptr(a, kp, P, plane, rank)[ij];
-  return s + (zm + zp);
-}
-
-__device__ void slab_smooth(const LvlF& L, int kind, Slab S, int rank, int sweeps, int jf,
-                            float w, bool zero) {
-  if (sweeps <= 0) return;
-  const SWalk W(S.n, S.P);
-  const int plane = S.plane;
-  auto cl = cgx::this_cluster();
-  if (kind == PFC_SWEEP_JACOBI) {
-    const int js = sweeps * jf;
-    float *s0 = S.d0, *s1 = S.d1, *s2 = S.d2, *o0 = S.t0, *o1 = S.t1, *o2 = S.t2;
-    for (int sw = 0; sw < js; ++sw) {
-      const bool z = zero && sw == 0;
-      if (W.active) {
-        for (int kl = W.k0; kl < S.P; kl += W.kstep) {
-          const int c = W.i + S.n * W.j + kl * plane;
-          float sp = 0.f, sm_ = 0.f, sw_ = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
-          if (!z) {
-            sp = slab_nb(s0, W, kl, rank);
-            sm_ = slab_nb(s1, W, kl, rank);
-            sw_ = slab_nb(s2, W, kl, rank);
-            p0 = s0[c];
-            m0 = s1[c];
-            w0 = s2[c];
-          }
-          float dp, dm, dw;
-          lin_point(L, sp, sm_, sw_, S.q[c], S.r0[c], S.r1[c], S.r2[c], dp, dm, dw);
-          o0[c] = fmaf(w, dp - p0, p0);
-          o1[c] = fmaf(w, dm - m0, m0);
-          o2[c] = fmaf(w, dw - w0, w0);
-        }
-      }
-      cl.sync();
-      float* x;
-      x = s0; s0 = o0; o0 = x;
-      x = s1; s1 = o1; o1 = x;
-      x = s2; s2 = o2; o2 = x;
-    }
-    if (js & 1) {
-      if (W.active) {
-        for (int kl = W.k0; kl < S.P; kl += W.kstep) {
-          const int c = W.i + S.n * W.j + kl * plane;
-          S.d0[c] = s0[c];
-          S.d1[c] = s1[c];
-          S.d2[c] = s2[c];
-        }
-      }
-      cl.sync();
-    }
-    return;
-  }
-  for (int sw = 0; sw < sweeps; ++sw) {
-    for (int colour = 0; colour < 2; ++colour) {
-      const bool z = zero && sw == 0 && colour == 0;
-      if (W.active) {
-        for (int kl = W.k0; kl < S.P; kl += W.kstep) {
-          if (((W.i + W.j + rank * S.P + kl) & 1) != colour) continue;
-          const int c = W.i + S.n * W.j + kl * plane;
-          float sp = 0.f, sm_ = 0.f, sw_ = 0.f;
-          if (!z) {
-            sp = slab_nb(S.d0, W, kl, rank);
-            sm_ = slab_nb(S.d1, W, kl, rank);
-            sw_ = slab_nb(S.d2, W, kl, rank);
-          }
-          float dp, dm, dw;
-          lin_point(L, sp, sm_, sw_, S.q[c], S.r0[c], S.r1[c], S.r2[c], dp, dm, dw);
-          S.d0[c] = dp;
-          S.d1[c] = dm;
-          S.d2[c] = dw;
-        }
-      }
-      cl.sync();
-    }
-  }
-}
-
-// J-residual of the slab at (i, j, kl), one component at a time.
-__device__ __forceinline__ void slab_jres(const LvlF& L, const Slab& F, const SWalk& W, int kl,
-                                          int rank, float& a1, float& a2, float& a3) {
-  const int c = W.i + F.n * W.j + kl * F.plane;
-  const float p = F.d0[c], m = F.d1[c], w = F.d2[c];
-  const float lm = fmaf(-6.f, m, slab_nb(F.d1, W, kl, rank));
-  const float lw = fmaf(-6.f, w, slab_nb(F.d2, W, kl, rank));
-  const float lp = fmaf(-6.f, p, slab_nb(F.d0, W, kl, rank));
-  a1 = F.r0[c] - fmaf(-L.tg, lm, p);
-  a2 = F.r1[c] - (fmaf(-F.q[c], p, m) - L.g * lw);
-  a3 = F.r2[c] - fmaf(-L.gh, lp, w);
-}
-
-// Restriction of rho = r - J d from slab F into the coarse level whose cell
-// (I, J, K) lives at dst(K) + I + nc*J (dst returns the plane's address).
-template <class Dst>
-__device__ void slab_restrict(const LvlF& L, const Slab& F, int rank, Dst dst) {
-  const int n = F.n, nc = n >> 1;
-  // one thread per (fine cell): accumulate each coarse cell from its 8
-  // children by a fixed-order pass over the children of each coarse cell
-  const int ccount = (F.P / 2) * nc * nc;
-  for (int t = threadIdx.x; t < ccount; t += blockDim.x) {
-    const int I = t % nc, rr = t / nc, J = rr % nc, Kl = rr / nc;
-    float a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    for (int ch = 0; ch < 8; ++ch) {
-      SWalk W(n, F.P);   // reuse the neighbour logic for an arbitrary child
-      W.i = 2 * I + (ch & 1);
-      W.j = 2 * J + ((ch >> 1) & 1);
-      W.im = (W.i == 0) ? n - 1 : W.i - 1;
-      W.ip = (W.i + 1 == n) ? 0 : W.i + 1;
-      W.jm = (W.j == 0) ? n - 1 : W.j - 1;
-      W.jp = (W.j + 1 == n) ? 0 : W.j + 1;
-      float x1, x2, x3;
-      slab_jres(L, F, W, 2 * Kl + (ch >> 2), rank, x1, x2, x3);
-      a1 += x1;
-      a2 += x2;
-      a3 += x3;
-    }
-    const int Kg = rank * (F.P / 2) + Kl;
-    dst(Kg, I + nc * J, 0.125f * a1, 0.125f * a2, 0.125f * a3);
-  }
-  cgx::this_cluster().sync();
-}
-
-// Prolongation into slab F: src(Kg, ij, c) returns component c of the coarse
-// correction at global coarse plane Kg and in-plane index ij.
-template <class Src>
-__device__ void slab_prolong(const Slab& F, int rank, Src src) {
-  const int n = F.n, nc = n >> 1;
-  const SWalk W(n, F.P);
-  if (W.active) {
-    const int I = W.i >> 1, J = W.j >> 1;
-    const int I2 = ((W.i & 1) ? I + 1 : I - 1 + nc) % nc;
-    const int J2 = ((W.j & 1) ? J + 1 : J - 1 + nc) % nc;
-    for (int kl = W.k0; kl < F.P; kl += W.kstep) {
-      const int kg = rank * F.P + kl;
-      const int K = kg >> 1;
-      const int K2 = ((kg & 1) ? K + 1 : K - 1 + nc) % nc;
-      const int c = W.i + n * W.j + kl * F.plane;
-      float* d[3] = {F.d0, F.d1, F.d2};
-      for (int q = 0; q < 3; ++q) {
-        const float g2 = (src(K, I2 + nc * J, q) + src(K, I + nc * J2, q)) + src(K2, I + nc * J, q);
-        const float g3 = (src(K, I2 + nc * J2, q) + src(K2, I2 + nc * J, q)) + src(K2, I + nc * J2, q);
-        float acc = fmaf(3.f, g3, src(K2, I2 + nc * J2, q));
-        acc = fmaf(9.f, g2, acc);
-        acc = fmaf(27.f, src(K, I + nc * J, q), acc);
-        d[q][c] = fmaf(1.0f / 64.0f, acc, d[q][c]);
-      }
-    }
-  }
-  cgx::this_cluster().sync();
-}
-
-__global__ void __launch_bounds__(kDsmThreads) k_lin_dsm32(DsmParams D) {
-  extern __shared__ float smem[];
-  __shared__ float red[2][32];
-  __shared__ int done;
-  auto cl = cgx::this_cluster();
-  const int rank = (int)cl.block_rank();
-  const bool zero_top = D.zero_init != 0;
-  float* tb = tail_base(smem, D);
-  const TailParams& TP = D.tail;
-  // top slab level from global memory (split layout)
-  {
-    const Slab S = slab_at(smem, D, 0);
-    const int n = S.n, cells = S.P * S.plane;
-    for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-      const int i = t % n, rr = t / n, j = rr % n, kl = rr / n;
-      const int g = split_index(i, j, rank * S.P + kl, n);
-      S.r0[t] = D.gr[0][g];
-      S.r1[t] = D.gr[1][g];
-      S.r2[t] = D.gr[2][g];
-      S.q[t] = D.gq[g];
-      if (!zero_top) {
-        S.d0[t] = D.gd[0][g];
-        S.d1[t] = D.gd[1][g];
-        S.d2[t] = D.gd[2][g];
-      }
-    }
-    __syncthreads();
-  }
-  // q on the lower slab levels (children are in the same CTA) and on the
-  // first tail level (written into CTA 0)
-  for (int s = 1; s <= D.nslab; ++s) {
-    const Slab F = slab_at(smem, D, s - 1);
-    const int n = F.n, nc = n >> 1, ccount = (F.P / 2) * nc * nc;
-    float* cq = nullptr;
-    if (s < D.nslab) {
-      cq = slab_at(smem, D, s).q;
-    } else {
-      cq = cl.map_shared_rank(slev(tb, TP, 0).q, 0);
-    }
-    for (int t = threadIdx.x; t < ccount; t += blockDim.x) {
-      const int I = t % nc, rr = t / nc, J = rr % nc, Kl = rr / nc;
-      float acc = 0.f;
-      for (int ch = 0; ch < 8; ++ch)
-        acc += F.q[(2 * I + (ch & 1)) + n * (2 * J + ((ch >> 1) & 1)) +
-                   (2 * Kl + (ch >> 2)) * F.plane];
-      const int o = (s < D.nslab) ? (I + nc * J + Kl * nc * nc)
-                                  : (I + nc * J + (rank * (F.P / 2) + Kl) * nc * nc);
-      cq[o] = 0.125f * acc;
-    }
-    __syncthreads();
-  }
-  cl.sync();
-  if (rank == 0) tail_qrestrict(tb, TP);
-  // down: smooth and restrict every slab level
-  for (int s = 0; s < D.nslab; ++s) {
-    const Slab S = slab_at(smem, D, s);
-    const bool zero = (s > 0) || zero_top;
-    const int jf = s == 0 ? D.jfactor_top : D.jfactor;
-    if (D.nu1 > 0) {
-      slab_smooth(D.L[s], D.kind[s], S, rank, D.nu1, jf, D.w, zero);
-    } else if (zero) {
-      for (int t = threadIdx.x; t < S.P * S.plane; t += blockDim.x) {
-        S.d0[t] = 0.f;
-        S.d1[t] = 0.f;
-        S.d2[t] = 0.f;
-      }
-      cl.sync();
-    }
-    if (s + 1 < D.nslab) {
-      const Slab C = slab_at(smem, D, s + 1);
-      const int cp = C.plane;
-      slab_restrict(D.L[s], S, rank, [&](int Kg, int ij, float a, float b, float c) {
-        const int o = ij + (Kg - rank * C.P) * cp;
-        C.r0[o] = a;
-        C.r1[o] = b;
-        C.r2[o] = c;
-      });
-    } else {
-      const SLev T0 = slev(tb, TP, 0);
-      float* r0 = cl.map_shared_rank(T0.r0, 0);
-      float* r1 = cl.map_shared_rank(T0.r1, 0);
-      float* r2 = cl.map_shared_rank(T0.r2, 0);
-      const int nc = S.n >> 1, cp = nc * nc;
-      slab_restrict(D.L[s], S, rank, [&](int Kg, int ij, float a, float b, float c) {
-        r0[ij + Kg * cp] = a;
-        r1[ij + Kg * cp] = b;
-        r2[ij + Kg * cp] = c;
-      });
-    }
-  }
-  // levels below the slabs: CTA 0
-  if (rank == 0) tail_vcycle(tb, TP, true, red, &done);
-  cl.sync();
-  // up: prolong and post-smooth every slab level
-  for (int s = D.nslab - 1; s >= 0; --s) {
-    const Slab S = slab_at(smem, D, s);
-    if (s == D.nslab - 1) {
-      const SLev T0 = slev(tb, TP, 0);
-      const float* e0 = cl.map_shared_rank(T0.d0, 0);
-      const float* e1 = cl.map_shared_rank(T0.d1, 0);
-      const float* e2 = cl.map_shared_rank(T0.d2, 0);
-      const int nc = S.n >> 1, cp = nc * nc;
-      slab_prolong(S, rank, [&](int K, int ij, int q) {
-        const float* e = q == 0 ? e0 : (q == 1 ? e1 : e2);
-        return e[ij + K * cp];
-      });
-    } else {
-      const Slab C = slab_at(smem, D, s + 1);
-      slab_prolong(S, rank, [&](int K, int ij, int q) {
-        float* e = q == 0 ? C.d0 : (q == 1 ? C.d1 : C.d2);
-        return plane_ptr(e, K, C.P, C.plane, rank)[ij];
-      });
-    }
-    slab_smooth(D.L[s], D.kind[s], S, rank, D.nu2, s == 0 ? D.jfactor_top : D.jfactor, D.w,
-                false);
-  }
-  // top slab level back to global memory
-  {
-    const Slab S = slab_at(smem, D, 0);
-    const int n = S.n, cells = S.P * S.plane;
-    for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-      const int i = t % n, rr = t / n, j = rr % n, kl = rr / n;
-      const int g = split_index(i, j, rank * S.P + kl, n);
-      D.gd[0][g] = S.d0[t];
-      D.gd[1][g] = S.d1[t];
-      D.gd[2][g] = S.d2[t];
-    }
-  }
-}
 
 __global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
@@ -1205,7 +818,6 @@ struct Ctx32 {
   float w;                     // Jacobi weight
   int jfactor;                 // Jacobi sweeps per requested sweep (coarse levels)
   int jfactor0;                // the same on the finest level
-  int use_cluster;             // levels <= 32^3 in one cluster launch
   cudaStream_t st;
   Prof* pr;
 };
@@ -1302,98 +914,9 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
   return cudaGetLastError();
 }
 
-// Levels handled by one k_lin_dsm32 launch from level l0: slab levels while
-// the size is a multiple of kDsmCTAs and >= 2 kDsmCTAs, then at least one tail
-// level; returns the number of slab levels (0 if the cluster path does not
-// apply) and the shared memory it needs.
-int dsm_plan(const Ctx32& c, int l0, size_t* smem) {
-  if (c.L[l0].n > kDsmMaxN) return 0;
-  int ns = 0;
-  size_t floats = 0;
-  int l = l0;
-  while (l < c.nl && ns < kDsmMaxSlab && c.L[l].n % kDsmCTAs == 0 && c.L[l].n >= 2 * kDsmCTAs &&
-         (c.L[l].n / kDsmCTAs) % 2 == 0) {
-    floats += 10 * (size_t)(c.L[l].n / kDsmCTAs) * c.L[l].n * c.L[l].n;
-    ++ns;
-    ++l;
-  }
-  if (ns == 0 || l >= c.nl || c.nl - l > kTailMaxLevels) return 0;
-  for (int m = l; m < c.nl; ++m) floats += 10 * (size_t)c.L[m].n * c.L[m].n * c.L[m].n;
-  *smem = floats * sizeof(float);
-  return (*smem <= kDsmMaxSmem) ? ns : 0;
-}
-
-cudaError_t dsm32(const Ctx32& c, int l0, int ns, size_t smem, bool zero_init) {
-  MixedBufs& mx = *c.mx;
-  DsmParams D;
-  D.nslab = ns;
-  D.nu1 = c.p->nu1;
-  D.nu2 = c.p->nu2;
-  D.jfactor = c.jfactor;
-  D.jfactor_top = l0 == 0 ? c.jfactor0 : c.jfactor;
-  D.zero_init = zero_init ? 1 : 0;
-  D.w = c.w;
-  for (int s = 0; s < ns; ++s) {
-    D.L[s] = c.L[l0 + s];
-    D.kind[s] = c.kind[l0 + s];
-  }
-  for (int q = 0; q < 3; ++q) {
-    D.gd[q] = mx.d[l0][q];
-    D.gr[q] = mx.r[l0][q];
-  }
-  D.gq = mx.q[l0];
-  TailParams& P = D.tail;
-  const int lt = l0 + ns;
-  P.nlev = c.nl - lt;
-  P.nu1 = c.p->nu1;
-  P.nu2 = c.p->nu2;
-  P.jfactor = c.jfactor;
-  P.jfactor_top = c.jfactor;
-  P.coarse_sweeps = 24;
-  P.zero_init = 1;
-  P.w = c.w;
-  for (int l = lt; l < c.nl; ++l) {
-    P.L[l - lt] = c.L[l];
-    P.kind[l - lt] = c.kind[l];
-  }
-  for (int q = 0; q < 3; ++q) {
-    P.gd[q] = nullptr;
-    P.gr[q] = nullptr;
-  }
-  P.gq = nullptr;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_lin_dsm32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kDsmMaxSmem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kDsmCTAs, 1, 1);
-  cfg.blockDim = dim3(kDsmThreads, 1, 1);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = c.st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kDsmCTAs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_lin_dsm32, D);
-  prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
-  return e;
-}
-
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
-  if (c.use_cluster) {
-    size_t smem = 0;
-    const int ns = dsm_plan(c, l, &smem);
-    if (ns > 0) return dsm32(c, l, ns, smem, zero_init);
-  }
   if (L.n <= kTailMaxN && c.nl - l <= kTailMaxLevels) {
     int sizes[kMaxLevelsMixed];
     for (int q = 0; q < c.nl; ++q) sizes[q] = c.L[q].n;
@@ -1475,7 +998,6 @@ cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float*
   c.w = 1.f;
   c.jfactor = 1;
   c.jfactor0 = 1;
-  c.use_cluster = 0;
   c.st = st;
   c.pr = nullptr;
   return smooth32(c, 0, sweeps, zero_init);
@@ -1521,7 +1043,6 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
   c.w = (float)p.jacobi_weight;
   c.jfactor = p.jacobi_factor;
   c.jfactor0 = p.jacobi_factor0;
-  c.use_cluster = 1;
   double h = p.L / p.n;
   for (int l = 0; l < nl; ++l) {
     c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));

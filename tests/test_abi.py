@@ -49,8 +49,9 @@ def test_default_params_and_workspace(libpfc):
     p.n, p.L, p.eps, p.dt = 16, 32.0, 0.025, 0.01
     n16 = B.pfc_workspace_bytes(p)
     # 10 fine FP64 fields (3 levels of phi, mu, omega, S2, S3, 3 Jacobi
-    # scratch) + 13 per coarse level (8, 4, 2) + reduction buffers
-    fields = 10 * 16 ** 3 + 13 * (8 ** 3 + 4 ** 3 + 2 ** 3)
+    # scratch) + 13 per coarse level + reduction buffers; at h = 2 the
+    # hierarchy stops at 8^3 (108 tau/h^6 = 0.017 at 16^3, 2.6e-4 at 8^3)
+    fields = 10 * 16 ** 3 + 13 * 8 ** 3
     assert fields * 8 <= n16 <= fields * 8 + 100_000
     p.precision = B.PFC_MIXED
     assert B.pfc_workspace_bytes(p) > n16
@@ -73,14 +74,17 @@ def test_level_policy(libpfc):
         except B.PFCError:
             break
         lvl += 1
-    assert [x[0] for x in info] == [128, 64, 32, 16, 8, 4, 2]
+    # coarsening stops at 16^3: h = 2, 108 tau/h^6 = 0.021 <= 0.05
+    assert [x[0] for x in info] == [128, 64, 32, 16]
     for n, h, kind in info:
         s = 108 * p.dt / h ** 6
         want = B.PFC_SWEEP_JACOBI if 0.25 < s < 1000 else B.PFC_SWEEP_RB
         assert kind == want and h == 32.0 / n
     assert [x[2] for x in info][:3] == [B.PFC_SWEEP_RB, B.PFC_SWEEP_JACOBI, B.PFC_SWEEP_JACOBI]
     p.policy = B.PFC_POLICY_RB
-    assert all(B.pfc_level_info(p, l)[2] == B.PFC_SWEEP_RB for l in range(7))
+    assert all(B.pfc_level_info(p, l)[2] == B.PFC_SWEEP_RB for l in range(4))
+    p.coarse_stiffness = 0.0                  # full hierarchy down to 2^3
+    assert B.pfc_level_info(p, 6)[0] == 2
 
 
 def test_validation_errors_without_gpu(libpfc):
