@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--inner-cycles", type=int, default=3)
-    ap.add_argument("--jacobi-factor", type=int, default=4)
+    ap.add_argument("--jacobi-factor", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

@@ -81,10 +81,11 @@ typedef struct pfc_params {
   int    jacobi_factor;/* Jacobi sweeps per requested sweep on coarse Jacobi levels */
   int    jacobi_factor0;/* the same on the finest level */
   double stiff_hi, stiff_lo; /* thresholds of the hybrid policy */
-  double coarse_stiffness;   /* also stop coarsening at the first level (below
-                                the finest, of at most 16^3 cells) whose
-                                stiffness 108 tau/h^6 is <= this: there the
-                                system is nearly pointwise and sweeps solve it */
+  double coarse_stiffness;   /* PFC_MIXED: also stop coarsening at the first
+                                level (below the finest, of at most 16^3
+                                cells) whose stiffness 108 tau/h^6 is <= this:
+                                there the system is nearly pointwise and FP32
+                                sweeps solve it */
 } pfc_params;
 
 typedef struct pfc_step_stats {

@@ -37,9 +37,11 @@ constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Level sizes: halve while the size is even and larger than `coarsest`, and
-// stop early at the first coarse level of at most 16^3 cells whose stiffness
-// 108 tau/h^6 is at most coarse_stiffness.
+// Level sizes: halve while the size is even and larger than `coarsest`; the
+// mixed path also stops at the first coarse level of at most 16^3 cells whose
+// stiffness 108 tau/h^6 is at most coarse_stiffness (its coarsest solve runs
+// in FP32 in one block; the FP64 path keeps coarsening because one SM's FP64
+// rate makes a large single-block FP64 solve slow).
 int level_sizes(const pfc_params* p, int* sizes) {
   int n = p->n, nl = 0;
   double h = p->L / p->n;
@@ -49,7 +51,7 @@ int level_sizes(const pfc_params* p, int* sizes) {
     h *= 2.0;
     sizes[nl++] = n;
     const double s = 108.0 * p->dt / (h * h * h * h * h * h);
-    if (n <= 16 && s <= p->coarse_stiffness) break;
+    if (p->precision == PFC_MIXED && n <= 16 && s <= p->coarse_stiffness) break;
   }
   return nl;
 }

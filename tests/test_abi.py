@@ -49,9 +49,8 @@ def test_default_params_and_workspace(libpfc):
     p.n, p.L, p.eps, p.dt = 16, 32.0, 0.025, 0.01
     n16 = B.pfc_workspace_bytes(p)
     # 10 fine FP64 fields (3 levels of phi, mu, omega, S2, S3, 3 Jacobi
-    # scratch) + 13 per coarse level + reduction buffers; at h = 2 the
-    # hierarchy stops at 8^3 (108 tau/h^6 = 0.017 at 16^3, 2.6e-4 at 8^3)
-    fields = 10 * 16 ** 3 + 13 * 8 ** 3
+    # scratch) + 13 per coarse level (8, 4, 2) + reduction buffers
+    fields = 10 * 16 ** 3 + 13 * (8 ** 3 + 4 ** 3 + 2 ** 3)
     assert fields * 8 <= n16 <= fields * 8 + 100_000
     p.precision = B.PFC_MIXED
     assert B.pfc_workspace_bytes(p) > n16
@@ -66,6 +65,7 @@ def test_level_policy(libpfc):
     108 tau/h^6 >= 1000 or <= 0.25, damped Jacobi in between."""
     p = B.pfc_default_params()
     p.n, p.L, p.eps, p.dt = 128, 32.0, 0.025, 0.0125
+    p.precision = B.PFC_MIXED
     info = []
     lvl = 0
     while True:
@@ -84,6 +84,8 @@ def test_level_policy(libpfc):
     p.policy = B.PFC_POLICY_RB
     assert all(B.pfc_level_info(p, l)[2] == B.PFC_SWEEP_RB for l in range(4))
     p.coarse_stiffness = 0.0                  # full hierarchy down to 2^3
+    assert B.pfc_level_info(p, 6)[0] == 2
+    p.coarse_stiffness, p.precision = 0.05, B.PFC_FP64   # FP64 path: full hierarchy
     assert B.pfc_level_info(p, 6)[0] == 2
 
 
