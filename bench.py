@@ -55,6 +55,18 @@ KERNEL_BYTES = {
 }
 
 
+# FP64-ALU-bound kernel classes: algorithmic FP64 flops per cell of one
+# counted launch (FMA = 2), launches per group.  The defect evaluates three
+# 7-point Laplacians (7 flops each), the residual rows (3 + 12 + 3, the cubic
+# term 6 of them), the Jacobian coefficient q (9) and |r|^2 (6): 54 flops.
+KERNEL_FLOPS = {"defect": (54.0, 2)}
+
+# FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
+# sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
+# x 2 flops x 152 SMs x 2.07 GHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,18 +306,26 @@ def run_ours(args):
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
     m = n >> dom_lvl
-    per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
-    launch_bytes = per_cell * m ** 3 * per_group
-    groups = dom_launches / per_group
-    achieved = launch_bytes * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+    if dom_cls in KERNEL_FLOPS:
+        per_cell, per_group = KERNEL_FLOPS[dom_cls]
+        groups = dom_launches / per_group
+        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e12 if dom_time > 0 else 0.0
+        bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
+        peak_src = "FP64: 2 FMA lanes/SM/clock x 152 SMs x 2.07 GHz (derived; see DESIGN.md)"
+    else:
+        per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
+        groups = dom_launches / per_group
+        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
+        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+        peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak,
+                "unit": unit, "frac": achieved / peak, "traffic": None,
                 "kernel": f"{dom_cls} (level {dom_lvl}, {m}^3)",
                 "ms_per_launch": dom_time / max(groups, 1),
                 "timing": f"CUDA events around each launch, {prof_steps} host-driven steps "
                           f"after the timed region ({1e3 * prof_steps / ms_instr:.1f} steps/s "
                           f"with the events)",
-                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"}
+                "peak_source": peak_src}
 
     # ---- plain FP64 FAS path, same workload and tolerance -----------------
     s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="fp64")

@@ -86,6 +86,9 @@ typedef struct pfc_params {
                                 cells) whose stiffness 108 tau/h^6 is <= this:
                                 there the system is nearly pointwise and FP32
                                 sweeps solve it */
+  int    coarse_sweeps;      /* PFC_MIXED: most FP32 sweeps on the coarsest
+                                level (stopping earlier once the largest change
+                                is below 1e-6 of the largest value) */
 } pfc_params;
 
 typedef struct pfc_step_stats {
@@ -99,7 +102,7 @@ typedef struct pfc_step_stats {
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
- * coarse_stiffness 0.05.  n, L, eps, dt are set to 0.
+ * coarse_stiffness 0.05, coarse_sweeps 8.  n, L, eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

@@ -39,7 +39,8 @@ class pfc_params(ctypes.Structure):
                 ("policy", ctypes.c_int), ("jacobi_weight", ctypes.c_double),
                 ("jacobi_factor", ctypes.c_int), ("jacobi_factor0", ctypes.c_int),
                 ("stiff_hi", ctypes.c_double),
-                ("stiff_lo", ctypes.c_double), ("coarse_stiffness", ctypes.c_double)]
+                ("stiff_lo", ctypes.c_double), ("coarse_stiffness", ctypes.c_double),
+                ("coarse_sweeps", ctypes.c_int)]
 
 
 class pfc_step_stats(ctypes.Structure):

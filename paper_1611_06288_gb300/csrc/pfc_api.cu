@@ -70,7 +70,7 @@ int validate(const pfc_params* p) {
       p->jacobi_factor0 < 1)
     return PFC_EINVAL;
   if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
-  if (!(p->coarse_stiffness >= 0)) return PFC_EINVAL;
+  if (!(p->coarse_stiffness >= 0) || p->coarse_sweeps < 1) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -501,6 +501,7 @@ void pfc_default_params(pfc_params* p) {
   p->stiff_hi = 1000.0;
   p->stiff_lo = 0.25;
   p->coarse_stiffness = 0.05;
+  p->coarse_sweeps = 8;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {
