@@ -102,7 +102,7 @@ typedef struct pfc_step_stats {
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
- * coarse_stiffness 0.05, coarse_sweeps 8.  n, L, eps, dt are set to 0.
+ * coarse_stiffness 0.05, coarse_sweeps 4.  n, L, eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

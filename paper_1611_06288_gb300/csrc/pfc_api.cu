@@ -501,7 +501,7 @@ void pfc_default_params(pfc_params* p) {
   p->stiff_hi = 1000.0;
   p->stiff_lo = 0.25;
   p->coarse_stiffness = 0.05;
-  p->coarse_sweeps = 8;
+  p->coarse_sweeps = 4;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {

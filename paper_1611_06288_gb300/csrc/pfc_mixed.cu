@@ -234,90 +234,6 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
 }
 
 
-// Two damped Jacobi sweeps on J d = r in one launch (d -> t), for the
-// latency-bound middle levels: each block loads an 8^3 tile with a 2-cell
-// periodic halo into shared memory, runs the first sweep on the tile plus a
-// 1-cell halo and the second on the tile.  ZERO: d = 0 on entry.
-constexpr int kJ2Tile = 8, kJ2Halo = 2;
-constexpr int kJ2Ext = kJ2Tile + 2 * kJ2Halo;        // 12
-constexpr int kJ2Mid = kJ2Tile + 2;                  // 10
-
-template <bool ZERO>
-__global__ void __launch_bounds__(512) k_lin_jacobi2x32(LvlF L, float w, const float* __restrict__ d1,
-                                                        const float* __restrict__ d2,
-                                                        const float* __restrict__ d3,
-                                                        float* __restrict__ t1,
-                                                        float* __restrict__ t2,
-                                                        float* __restrict__ t3,
-                                                        const float* __restrict__ r1,
-                                                        const float* __restrict__ r2,
-                                                        const float* __restrict__ r3,
-                                                        const float* __restrict__ q) {
-  __shared__ float sd[3][kJ2Ext * kJ2Ext * kJ2Ext];   // old d on the 12^3 box
-  __shared__ float sm[3][kJ2Mid * kJ2Mid * kJ2Mid];   // first-sweep d on the 10^3 box
-  __shared__ float sr[4][kJ2Mid * kJ2Mid * kJ2Mid];   // r1, r2, r3, q on the 10^3 box
-  const int n = L.n;
-  const int x0 = blockIdx.x * kJ2Tile, y0 = blockIdx.y * kJ2Tile, z0 = blockIdx.z * kJ2Tile;
-  const int tid = threadIdx.x;
-  auto wrap = [n](int v) { return v < 0 ? v + n : (v >= n ? v - n : v); };
-  // load the 12^3 box of d and the 10^3 box of r, q
-  for (int e = tid; e < kJ2Ext * kJ2Ext * kJ2Ext; e += blockDim.x) {
-    const int ex = e % kJ2Ext, ey = (e / kJ2Ext) % kJ2Ext, ez = e / (kJ2Ext * kJ2Ext);
-    const int gx = wrap(x0 + ex - kJ2Halo), gy = wrap(y0 + ey - kJ2Halo), gz = wrap(z0 + ez - kJ2Halo);
-    const int g = split_index(gx, gy, gz, n);
-    if (!ZERO) {
-      sd[0][e] = __ldg(d1 + g);
-      sd[1][e] = __ldg(d2 + g);
-      sd[2][e] = __ldg(d3 + g);
-    }
-    if (ex >= 1 && ex <= kJ2Mid && ey >= 1 && ey <= kJ2Mid && ez >= 1 && ez <= kJ2Mid) {
-      const int m = (ex - 1) + kJ2Mid * ((ey - 1) + kJ2Mid * (ez - 1));
-      sr[0][m] = __ldg(r1 + g);
-      sr[1][m] = __ldg(r2 + g);
-      sr[2][m] = __ldg(r3 + g);
-      sr[3][m] = __ldg(q + g);
-    }
-  }
-  __syncthreads();
-  // first sweep on the 10^3 box
-  constexpr int E = kJ2Ext, E2 = kJ2Ext * kJ2Ext;
-  for (int m = tid; m < kJ2Mid * kJ2Mid * kJ2Mid; m += blockDim.x) {
-    const int mx = m % kJ2Mid, my = (m / kJ2Mid) % kJ2Mid, mz = m / (kJ2Mid * kJ2Mid);
-    const int e = (mx + 1) + E * ((my + 1) + E * (mz + 1));
-    float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
-    if (!ZERO) {
-      sp = ((sd[0][e - 1] + sd[0][e + 1]) + (sd[0][e - E] + sd[0][e + E])) + (sd[0][e - E2] + sd[0][e + E2]);
-      sm_ = ((sd[1][e - 1] + sd[1][e + 1]) + (sd[1][e - E] + sd[1][e + E])) + (sd[1][e - E2] + sd[1][e + E2]);
-      sw = ((sd[2][e - 1] + sd[2][e + 1]) + (sd[2][e - E] + sd[2][e + E])) + (sd[2][e - E2] + sd[2][e + E2]);
-      p0 = sd[0][e];
-      m0 = sd[1][e];
-      w0 = sd[2][e];
-    }
-    float dp, dm, dw;
-    lin_point(L, sp, sm_, sw, sr[3][m], sr[0][m], sr[1][m], sr[2][m], dp, dm, dw);
-    sm[0][m] = fmaf(w, dp - p0, p0);
-    sm[1][m] = fmaf(w, dm - m0, m0);
-    sm[2][m] = fmaf(w, dw - w0, w0);
-  }
-  __syncthreads();
-  // second sweep on the 8^3 tile
-  constexpr int M = kJ2Mid, M2 = kJ2Mid * kJ2Mid;
-  {
-    const int tx = tid % kJ2Tile, ty = (tid / kJ2Tile) % kJ2Tile, tz = tid / (kJ2Tile * kJ2Tile);
-    const int m = (tx + 1) + M * ((ty + 1) + M * (tz + 1));
-    const float sp = ((sm[0][m - 1] + sm[0][m + 1]) + (sm[0][m - M] + sm[0][m + M])) + (sm[0][m - M2] + sm[0][m + M2]);
-    const float sm_ = ((sm[1][m - 1] + sm[1][m + 1]) + (sm[1][m - M] + sm[1][m + M])) + (sm[1][m - M2] + sm[1][m + M2]);
-    const float sw = ((sm[2][m - 1] + sm[2][m + 1]) + (sm[2][m - M] + sm[2][m + M])) + (sm[2][m - M2] + sm[2][m + M2]);
-    const float p0 = sm[0][m], m0 = sm[1][m], w0 = sm[2][m];
-    float dp, dm, dw;
-    lin_point(L, sp, sm_, sw, sr[3][m], sr[0][m], sr[1][m], sr[2][m], dp, dm, dw);
-    const int g = split_index(x0 + tx, y0 + ty, z0 + tz, n);
-    t1[g] = fmaf(w, dp - p0, p0);
-    t2[g] = fmaf(w, dm - m0, m0);
-    t3[g] = fmaf(w, dw - w0, w0);
-  }
-}
-
 __global__ void k_copy3(int cells, const float* __restrict__ a1, const float* __restrict__ a2,
                         const float* __restrict__ a3, float* __restrict__ b1,
                         float* __restrict__ b2, float* __restrict__ b3) {
@@ -917,37 +833,24 @@ struct Ctx32 {
   Prof* pr;
 };
 
-// `sweeps` damped Jacobi sweeps d -> t -> d ...; on levels of 16^3 to 64^3
-// cells with n % 8 == 0 two sweeps share one launch.  The result ends in d.
+// `sweeps` damped Jacobi sweeps d -> t -> d ...; the result ends in d.
 cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* const* d,
                      float* const* t, float* const* r, const float* q, cudaStream_t st) {
   const int n = L.n;
   const int64_t cells = (int64_t)n * n * n;
   const Launch3 g = launch3(n, n, n);
-  const bool pairs = n >= 16 && n <= 64 && n % kJ2Tile == 0;
   float* src[3] = {d[0], d[1], d[2]};
   float* dst[3] = {t[0], t[1], t[2]};
   int done = 0;
   while (done < sweeps) {
     const bool z = zero_init && done == 0;
-    if (pairs && sweeps - done >= 2) {
-      const dim3 grid(n / kJ2Tile, n / kJ2Tile, n / kJ2Tile);
-      if (z)
-        k_lin_jacobi2x32<true><<<grid, 512, 0, st>>>(L, w, src[0], src[1], src[2], dst[0], dst[1],
-                                                      dst[2], r[0], r[1], r[2], q);
-      else
-        k_lin_jacobi2x32<false><<<grid, 512, 0, st>>>(L, w, src[0], src[1], src[2], dst[0],
-                                                       dst[1], dst[2], r[0], r[1], r[2], q);
-      done += 2;
-    } else {
-      if (z)
-        k_lin_jacobi32<true><<<g.grid, g.block, 0, st>>>(
-            L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
-      else
-        k_lin_jacobi32<false><<<g.grid, g.block, 0, st>>>(
-            L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
-      done += 1;
-    }
+    if (z)
+      k_lin_jacobi32<true><<<g.grid, g.block, 0, st>>>(
+          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    else
+      k_lin_jacobi32<false><<<g.grid, g.block, 0, st>>>(
+          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    done += 1;
     for (int c = 0; c < 3; ++c) {
       float* x = src[c];
       src[c] = dst[c];
