@@ -378,19 +378,17 @@ __global__ void k_reduce_final(const double* __restrict__ partials, int nparts,
 }
 
 // Raw per-cell sums for F_h (Eq. 2.1), the modified energy and the mass.
+// ||grad_h a||^2 is taken as -(a, Delta_h a) (summation by parts, Lemma 2.1),
+// reusing the Laplacian that ||Delta_h a||^2 needs.
 __global__ void k_diagnostics(int n, const double* __restrict__ a,
                               const double* __restrict__ b, double* partials) {
   __shared__ double sm[32 * 6];
-  const int64_t cells = (int64_t)n * n * n;
+  const int cells = n * n * n;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    cell_of(t, n, i, j, k);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
     const Stencil s = stencil_at(i, j, k, n);
     const double x = __ldg(a + s.c);
-    const double dx = __ldg(a + s.xp) - x, dy = __ldg(a + s.yp) - x,
-                 dz = __ldg(a + s.zp) - x;
     const double lap = fma(-6.0, x, nbsum(a, s));
     const double y = x - __ldg(b + s.c);
     const double ex = (__ldg(a + s.xp) - __ldg(b + s.xp)) - y;
@@ -399,7 +397,7 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
     const double x2 = x * x;
     acc[0] = fma(x2, x2, acc[0]);
     acc[1] += x2;
-    acc[2] = fma(dx, dx, fma(dy, dy, fma(dz, dz, acc[2])));
+    acc[2] = fma(-x, lap, acc[2]);
     acc[3] = fma(lap, lap, acc[3]);
     acc[4] = fma(ex, ex, fma(ey, ey, fma(ez, ez, acc[4])));
     acc[5] += x;
@@ -408,32 +406,6 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
   if (threadIdx.x == 0) {
     for (int c = 0; c < 6; ++c) partials[(int64_t)blockIdx.x * 6 + c] = acc[c];
   }
-}
-
-// Convergence test of Algorithm 1's loop (RMS residual against the tolerance,
-// NaN, cycle budget) on the device.
-__global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
-                         const double* sum, StepState* s, double inv_3n3, double tol,
-                         int max_iter, int first) {
-  const double rms = sqrt(sum[0] * inv_3n3);
-  if (first) {
-    s->iters = 0;
-    s->rms0 = rms;
-  } else {
-    s->iters += 1;
-  }
-  s->rms = rms;
-  int status;
-  if (rms <= tol)
-    status = kStepConverged;
-  else if (!isfinite(rms))
-    status = kStepNaN;
-  else if (s->iters >= max_iter)
-    status = kStepNoConv;
-  else
-    status = kStepRunning;
-  s->status = status;
-  if (use_handle) cudaGraphSetConditional(handle, status == kStepRunning ? 1u : 0u);
 }
 
 inline int reduce_blocks(int64_t cells) {

@@ -104,7 +104,8 @@ __device__ __forceinline__ void split_cell(int64_t t, int n, int& p, int& j, int
 
 // FP64 residual r = S - N(u) -> FP32 copy, q = f'(phi) + (1-eps)/2 -> FP32
 // (both in the colour-split layout), and per-block partial sums of |r|^2 in
-// FP64.
+// FP64.  q only feeds the FP32 correction solve, so it is formed in FP32 from
+// FP32 copies of phi and b, keeping GB300's narrow FP64 pipe for the residual.
 __global__ void k_residual64_to32(Lvl L, const double* __restrict__ phi,
                                   const double* __restrict__ mu,
                                   const double* __restrict__ om,
@@ -116,21 +117,21 @@ __global__ void k_residual64_to32(Lvl L, const double* __restrict__ phi,
                                   float* __restrict__ q, double* partials) {
   __shared__ double sm[32];
   const int n = L.n;
-  const int64_t cells = (int64_t)n * n * n;
+  const int cells = n * n * n;
+  const float c1 = (float)L.c1;
   double acc[1] = {0.0};
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int i, j, k;
-    cell_of(t, n, i, j, k);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
     const Stencil s = stencil_at(i, j, k, n);
     double x, y, z;
     residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
     acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
-    const int64_t o = split_index(i, j, k, n);
+    const int o = split_index(i, j, k, n);
     r1[o] = (float)x;
     r2[o] = (float)y;
     r3[o] = (float)z;
-    q[o] = (float)(cubic_fp(__ldg(phi + t), __ldg(b + t)) + L.c1);
+    const float pf = (float)__ldg(phi + t), bf = (float)__ldg(b + t);
+    q[o] = fmaf(0.75f * pf, pf, fmaf(0.5f * pf, bf, fmaf(0.25f * bf, bf, c1)));
   }
   block_sum<1>(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];

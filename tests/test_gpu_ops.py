@@ -186,7 +186,8 @@ def test_defect_and_correct(n):
     for g, x in zip(r, ref):
         # FP64 residual rounded to FP32: half an FP32 ulp (colour-split layout)
         assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
-    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 2 ** -23,
+    # q = f'(phi) + (1-eps)/2 is formed in FP32 arithmetic: a few FP32 ulps
+    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 1e-6,
                        "q32")
     # u += d: one FP64 rounding of the same sum on both sides -> bit-exact
     rng = np.random.default_rng(5)
