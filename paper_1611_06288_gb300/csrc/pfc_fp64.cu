@@ -408,6 +408,32 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
   }
 }
 
+// Convergence test of Algorithm 1's loop (RMS residual against the tolerance,
+// NaN, cycle budget) on the device.
+__global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
+                         const double* sum, StepState* s, double inv_3n3, double tol,
+                         int max_iter, int first) {
+  const double rms = sqrt(sum[0] * inv_3n3);
+  if (first) {
+    s->iters = 0;
+    s->rms0 = rms;
+  } else {
+    s->iters += 1;
+  }
+  s->rms = rms;
+  int status;
+  if (rms <= tol)
+    status = kStepConverged;
+  else if (!isfinite(rms))
+    status = kStepNaN;
+  else if (s->iters >= max_iter)
+    status = kStepNoConv;
+  else
+    status = kStepRunning;
+  s->status = status;
+  if (use_handle) cudaGraphSetConditional(handle, status == kStepRunning ? 1u : 0u);
+}
+
 inline int reduce_blocks(int64_t cells) {
   const int64_t nb = (cells + kReduceThreads - 1) / kReduceThreads;
   return (int)(nb < kReduceBlocks ? nb : kReduceBlocks);
