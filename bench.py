@@ -4,10 +4,11 @@ defect-correction multigrid) on GB300.
 
 Workload: 128^3 cells, L = 32, eps = 0.025, phi0 = 0.1 sin(2 pi x/L)
 cos(2 pi y/L) sin(2 pi z/L), dt = 0.0125, residual tolerance 1e-9 (RMS of the
-three FP64 components).  A "step" is one full time step: source, multigrid
-cycles until the FP64 residual is below the tolerance, and the energy/mass
-diagnostics.  The headline value is the mixed-precision path (FP64 defect
-correction around FP32 multigrid); the plain FP64 FAS path is timed beside it.
+three components).  A "step" is one full time step: source, multigrid
+cycles until the residual is below the tolerance, and the energy/mass
+diagnostics.  The headline value is the mixed-precision path (double-float
+defect correction around FP32 multigrid); the plain FP64 FAS path is timed
+beside it.
 
 Prints one JSON line (rank 0).  Under torchrun every rank advances its own
 replica (no collective on the data path; weak scaling).
@@ -38,11 +39,11 @@ WORKLOAD = {"workload": "smooth-mode 128^3", "n": 128, "L": 32.0, "eps": 0.025,
 # Algorithmic bytes per cell of one counted launch, and launches per timed
 # group, for each kernel class (minimum traffic: every field touched once).
 KERNEL_BYTES = {
-    "defect": (64.0, 2),          # read phi,mu,om,b,S2,S3 (48) write r32 x3, q32 (16)
+    "defect": (64.0, 2),          # read df phi,mu,om,b,S2,S3 (48) write r32 x3, q32 (16)
     "lin_smooth": (20.0, 1),      # per colour pass: half of read d (12) + r,q (16) + write d (12)
     "lin_restrict": (29.5, 1),    # read d,r,q (28) + write coarse r (12/8)
     "lin_prolong": (25.5, 1),     # read+write d (24) + coarse d (12/8)
-    "correct": (60.0, 1),         # read u (24) d (12) write u (24)
+    "correct": (60.0, 1),         # read df u (24) d (12) write df u (24)
     "smooth": (40.0, 1),          # per colour pass: half of (u 24 + S2,S3 16 + b 8 + phi 8 + write u 24)
     "residual_norm": (48.0, 2),   # read u, b, S2, S3
     "residual_restrict": (57.0, 1),
@@ -54,17 +55,6 @@ KERNEL_BYTES = {
     "lin_coarse": (0.0, 1),
 }
 
-
-# FP64-ALU-bound kernel classes: algorithmic FP64 flops per cell of one
-# counted launch (FMA = 2), launches per group.  The defect evaluates three
-# 7-point Laplacians (7 flops each), the residual rows (3 + 12 + 3, the cubic
-# term 6 of them), the Jacobian coefficient q (9) and |r|^2 (6): 54 flops.
-KERNEL_FLOPS = {"defect": (54.0, 2)}
-
-# FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
-# sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
-# x 2 flops x 152 SMs x 2.07 GHz.
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
 def parse():
@@ -306,18 +296,11 @@ def run_ours(args):
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
     m = n >> dom_lvl
-    if dom_cls in KERNEL_FLOPS:
-        per_cell, per_group = KERNEL_FLOPS[dom_cls]
-        groups = dom_launches / per_group
-        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e12 if dom_time > 0 else 0.0
-        bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
-        peak_src = "FP64: 2 FMA lanes/SM/clock x 152 SMs x 2.07 GHz (derived; see DESIGN.md)"
-    else:
-        per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
-        groups = dom_launches / per_group
-        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
-        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
-        peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
+    per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
+    groups = dom_launches / per_group
+    achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
+    bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+    peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
     roofline = {"bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak, "traffic": None,
                 "kernel": f"{dom_cls} (level {dom_lvl}, {m}^3)",

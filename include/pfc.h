@@ -46,7 +46,7 @@ extern "C" {
 #define PFC_ECUDA   -5  /* a CUDA runtime call failed */
 
 #define PFC_FP64  0     /* FAS V-cycles entirely in FP64 (Algorithm 1) */
-#define PFC_MIXED 1     /* FP64 defect correction around FP32 multigrid */
+#define PFC_MIXED 1     /* double-float defect correction around FP32 multigrid */
 
 #define PFC_NEWTON 0    /* pointwise Newton linearisation of the cubic term */
 #define PFC_PICARD 1    /* the paper's local Picard linearisation (Section 5) */
@@ -67,15 +67,16 @@ typedef struct pfc_params {
   double eps;          /* model epsilon, 0 <= eps < 1 */
   double dt;           /* time step tau > 0 */
   int    nu1, nu2;     /* pre/post smoothing sweeps (Algorithm 1); >= 0 */
-  double tol;          /* absolute tolerance on the FP64 fine-grid residual,
-                          RMS over the three components */
+  double tol;          /* absolute tolerance on the fine-grid residual (FP64;
+                          double-float on the mixed path), RMS over the three
+                          components */
   int    max_cycles;   /* V-cycles (or defect corrections) per step */
   int    precision;    /* PFC_FP64 or PFC_MIXED */
   int    smoother;     /* PFC_NEWTON or PFC_PICARD (FP64 path) */
   int    coarsest;     /* coarsen while the level size is even and larger
                           than this; the last level is solved by sweeping to
                           convergence.  >= 2 */
-  int    inner_cycles; /* PFC_MIXED: FP32 V-cycles per FP64 defect correction */
+  int    inner_cycles; /* PFC_MIXED: FP32 V-cycles per defect correction */
   int    policy;       /* PFC_POLICY_HYBRID or PFC_POLICY_RB */
   double jacobi_weight;/* damping of the collective Jacobi sweep, (0, 1] */
   int    jacobi_factor;/* Jacobi sweeps per requested sweep on coarse Jacobi levels */
@@ -195,12 +196,12 @@ const char* pfc_last_error(void);
 #define PFC_K_PROLONG           5   /* FP64 correction e = v - w, u += P e */
 #define PFC_K_COARSE_SOLVE      6   /* FP64 coarsest-level solve */
 #define PFC_K_RESIDUAL_NORM     7   /* FP64 residual norm (convergence test) */
-#define PFC_K_DEFECT            8   /* mixed: FP64 residual -> FP32, q */
+#define PFC_K_DEFECT            8   /* mixed: df residual -> FP32, q */
 #define PFC_K_LIN_SMOOTH        9   /* mixed: FP32 red-black half-sweeps */
 #define PFC_K_LIN_RESTRICT     10   /* mixed: FP32 residual + restriction */
 #define PFC_K_LIN_PROLONG      11   /* mixed: FP32 d += P d_c */
 #define PFC_K_LIN_COARSE       12   /* mixed: FP32 coarsest-level solve */
-#define PFC_K_CORRECT          13   /* mixed: u += d in FP64 */
+#define PFC_K_CORRECT          13   /* mixed: u += d in double-float */
 #define PFC_K_COUNT            14
 #define PFC_PROFILE_LEVELS     24
 
@@ -300,6 +301,12 @@ int pfc_op_diagnostics(int n, double h, double eps, const double* d_a,
                        const double* d_b, void* d_scratch, double* out,
                        void* stream);
 
+/* The same diagnostics of df fields d_a, d_b (2*n^3 floats each, see the df
+ * layout below), with the per-cell terms and all sums in double-float. */
+int pfc_op_diagnostics_df(int n, double h, double eps, const float* d_a,
+                          const float* d_b, void* d_scratch, double* out,
+                          void* stream);
+
 /* RMS residual sqrt(sum_c sum r_c^2 / (3 n^3)) of u (blocking). */
 int pfc_op_residual_norm(int n, double h, double eps, double tau,
                          const double* d_phi, const double* d_mu,
@@ -332,27 +339,49 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
 
 /* ------------------------------------------------------------------------
  * Primitive operations of the mixed-precision path (PFC_MIXED).  The outer
- * loop is an FP64 defect correction: r = S - N(u) in FP64, then an FP32
- * multigrid solve of J d = r, with J the Jacobian of N at u (Eqs. 5.4-5.6
- * differentiated in phi: only the cubic term's coefficient
+ * loop is a defect correction in double-float arithmetic: r = S - N(u), then
+ * an FP32 multigrid solve of J d = r, with J the Jacobian of N at u (Eqs.
+ * 5.4-5.6 differentiated in phi: only the cubic term's coefficient
  * q = f'(phi) + (1-eps)/2, f(a) = (a+b)(a^2+b^2)/4, depends on u), then
- * u += d.  The paper has no mixed-precision form; this is a solver strategy
- * whose fixed point is the FP64 solution of N(u) = S.
+ * u += d.  The paper computes in FP64 and has no mixed-precision form; this
+ * is a solver strategy whose fixed point is the solution of N(u) = S up to
+ * the double-float rounding of the residual.
  *
- * Every FP32 field (float*) below is stored colour-split: within each x-row
- * (j, k) the n/2 cells with (i+j+k) even come first, ordered by i/2, then the
- * n/2 cells with (i+j+k) odd; cell (i, j, k) is element
+ * A df field ("double-float") is 2*n^3 floats in natural cell order: cell c
+ * holds hi at [2c] and lo at [2c+1], value hi + lo with |lo| <= ulp(hi)/2,
+ * a 48-bit significand (unit roundoff 2^-48 ~ 3.6e-15).  The mixed path keeps
+ * phi, mu, omega, S2 and S3 in this form because GB300 issues FP32 at about
+ * 60 times its FP64 rate; pfc_get_* and pfc_set_state convert at the
+ * boundary, so callers of the context API see FP64 fields only.
+ *
+ * Every FP32 field (float*, not df) below is stored colour-split: within each
+ * x-row (j, k) the n/2 cells with (i+j+k) even come first, ordered by i/2,
+ * then the n/2 cells with (i+j+k) odd; cell (i, j, k) is element
  * (k*n + j)*n + ((i+j+k) & 1)*(n/2) + i/2.  A red-black half-sweep then reads
- * and writes contiguous runs of one colour.  FP64 fields keep the natural
- * layout.
+ * and writes contiguous runs of one colour.  n must be even.
  * --------------------------------------------------------------------- */
 
-/* FP64 residual r = S - N(u) stored as floats in d_r1..3, the coefficient
- * q = f'(phi) + (1-eps)/2 as floats in d_q, and *out = RMS of the FP64
- * residual (blocking).  d_scratch: pfc_reduce_scratch_bytes(n) bytes. */
-int pfc_op_defect(int n, double h, double eps, double tau, const double* d_phi,
-                  const double* d_mu, const double* d_om, const double* d_S1,
-                  const double* d_S2, const double* d_S3, const double* d_b,
+/* d_y = df(d_x) for `count` values: hi = FP32 rounding of x, lo = FP32
+ * rounding of x - hi.  d_y may equal d_x (in-place conversion of 8-byte
+ * slots); otherwise the arrays must not overlap. */
+int pfc_op_df_from_f64(long long count, const double* d_x, float* d_y, void* stream);
+
+/* d_x = hi + lo (exact in FP64) for `count` df values; in place allowed. */
+int pfc_op_df_to_f64(long long count, const float* d_y, double* d_x, void* stream);
+
+/* S2 and S3 of Eqs. 5.9-5.10 from df fields b = phi^k and c = phi^{k-1},
+ * written as df fields, computed in double-float (pfc_op_source in FP64). */
+int pfc_op_source_df(int n, double h, double eps, const float* d_b,
+                     const float* d_c, float* d_S2, float* d_S3, void* stream);
+
+/* Residual r = S - N(u) of the df fields (phi, mu, om), sources S1..S3 and
+ * b, evaluated in double-float and rounded to FP32 into d_r1..3; the
+ * coefficient q = f'(phi) + (1-eps)/2 in FP32 from the hi parts of phi and b
+ * into d_q; *out = RMS of the residual (blocking).  d_scratch:
+ * pfc_reduce_scratch_bytes(n) bytes.  n even. */
+int pfc_op_defect(int n, double h, double eps, double tau, const float* d_phi,
+                  const float* d_mu, const float* d_om, const float* d_S1,
+                  const float* d_S2, const float* d_S3, const float* d_b,
                   float* d_r1, float* d_r2, float* d_r3, float* d_q,
                   void* d_scratch, double* out, void* stream);
 
@@ -372,8 +401,9 @@ int pfc_op_lin_jacobi(int n, double h, double eps, double tau, int sweeps,
                       const float* d_r1, const float* d_r2, const float* d_r3,
                       const float* d_q, void* stream);
 
-/* u += d (FP64 += FP32) for the three components. */
-int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
+/* u += d for the three components: df fields d_u1..3 plus the colour-split
+ * FP32 corrections d_d1..3, in double-float.  n even. */
+int pfc_op_correct(int n, float* d_u1, float* d_u2, float* d_u3,
                    const float* d_d1, const float* d_d2, const float* d_d3,
                    void* stream);
 

@@ -87,12 +87,16 @@ _SIGS = {
                             ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "pfc_reduce_scratch_bytes": (_SZ, [_I]),
     "pfc_op_diagnostics": (_I, [_I, _D, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
+    "pfc_op_diagnostics_df": (_I, [_I, _D, _D, _P, _P, _P, ctypes.POINTER(_D), _P]),
     "pfc_op_residual_norm": (_I, [_I, _D, _D, _D] + [_P] * 8 + [ctypes.POINTER(_D), _P]),
     "pfc_op_residual_norm_static": (_I, [_I, _D, _D, _D] + [_P] * 7 +
                                     [ctypes.POINTER(_D), _P]),
     "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
     "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
+    "pfc_op_df_from_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
+    "pfc_op_df_to_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
+    "pfc_op_source_df": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
     "pfc_profile_enable": (_I, [_P, ctypes.c_uint]),
     "pfc_profile_read": (_I, [_P, _I, _I, ctypes.POINTER(ctypes.c_longlong),
                               ctypes.POINTER(_D)]),
@@ -325,6 +329,13 @@ def pfc_op_diagnostics(n, h, eps, a, b, scratch, stream=None):
     return list(out)
 
 
+def pfc_op_diagnostics_df(n, h, eps, a, b, scratch, stream=None):
+    out = (ctypes.c_double * 4)()
+    check(lib().pfc_op_diagnostics_df(n, h, eps, ptr(a), ptr(b), ptr(scratch), out, stream),
+          "pfc_op_diagnostics_df")
+    return list(out)
+
+
 def pfc_op_residual_norm(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, scratch, stream=None):
     out = ctypes.c_double()
     check(lib().pfc_op_residual_norm(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1),
@@ -357,6 +368,19 @@ def pfc_op_lin_smooth(n, h, eps, tau, sweeps, zero_init, d1, d2, d3, r1, r2, r3,
     check(lib().pfc_op_lin_smooth(n, h, eps, tau, sweeps, int(bool(zero_init)), ptr(d1),
                                   ptr(d2), ptr(d3), ptr(r1), ptr(r2), ptr(r3), ptr(q),
                                   stream), "pfc_op_lin_smooth")
+
+
+def pfc_op_df_from_f64(count, x, y, stream=None):
+    check(lib().pfc_op_df_from_f64(count, ptr(x), ptr(y), stream), "pfc_op_df_from_f64")
+
+
+def pfc_op_df_to_f64(count, y, x, stream=None):
+    check(lib().pfc_op_df_to_f64(count, ptr(y), ptr(x), stream), "pfc_op_df_to_f64")
+
+
+def pfc_op_source_df(n, h, eps, b, c, S2, S3, stream=None):
+    check(lib().pfc_op_source_df(n, h, eps, ptr(b), ptr(c), ptr(S2), ptr(S3), stream),
+          "pfc_op_source_df")
 
 
 def pfc_op_correct(n, u1, u2, u3, d1, d2, d3, stream=None):

@@ -37,6 +37,11 @@ constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// The mixed path stores phi, mu, omega, S2 and S3 as (hi, lo) FP32 pairs in
+// the same 8-byte slots the FP64 path uses for doubles.
+inline float2* as_df(double* p) { return reinterpret_cast<float2*>(p); }
+inline const float2* as_df(const double* p) { return reinterpret_cast<const float2*>(p); }
+
 // Level sizes: halve while the size is even and larger than `coarsest`; the
 // mixed path also stops at the first coarse level of at most 16^3 cells whose
 // stiffness 108 tau/h^6 is at most coarse_stiffness (its coarsest solve runs
@@ -109,7 +114,7 @@ struct pfc_ctx {
   pfc::Level64 lev[pfc::kMaxLevels];
   double* ring[3];   // phi^{k-1}, phi^k, phi^{k+1} rotate through these
   int ic, ib, ia;
-  double *mu, *om, *S2, *S3;
+  double *mu, *om, *S2, *S3;  // ring, mu .. S3: doubles (FP64) or df pairs (mixed)
   double* t0[3];     // level-0 Jacobi scratch
   double* partials;  // reduction partial sums
   double* dout;      // 8 device doubles of reduction results
@@ -255,7 +260,13 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
                             int use_handle, int first) {
   cudaStream_t st = c->st;
   if (c->p.precision == PFC_MIXED) {
-    PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
+    float2* u[3];
+    float2* S[3];
+    for (int q = 0; q < 3; ++q) {
+      u[q] = as_df(lv.u[q]);
+      S[q] = as_df(lv.S[q]);
+    }
+    PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, u, S, as_df(lv.b), c->partials, c->dout, st,
                                   &c->prof));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
@@ -276,8 +287,14 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   const double* cprev = c->ring[c->ic];
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
   Prof* pr = &c->prof;
-  PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
-            launch_source(lv.L, lv.b, cprev, c->S2, c->S3, c->st));
+  if (c->p.precision == PFC_MIXED) {
+    PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
+              launch_source_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),
+                               c->st));
+  } else {
+    PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
+              launch_source(lv.L, lv.b, cprev, c->S2, c->S3, c->st));
+  }
   if (c->p.precision == PFC_FP64) {
     const double* fine = lv.b;
     for (int l = 1; l < c->nl; ++l) {
@@ -296,7 +313,8 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
 int enqueue_body(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
                  int use_handle) {
   if (c->p.precision == PFC_MIXED) {
-    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, lv.u, c->st, &c->prof));
+    float2* u[3] = {as_df(lv.u[0]), as_df(lv.u[1]), as_df(lv.u[2])};
+    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, u, c->st, &c->prof));
   } else {
     int rc = vcycle64(c, 0, lv);
     if (rc) return rc;
@@ -581,10 +599,17 @@ int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
 
 int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev) {
   if (!c || !any_phi) return PFC_EINVAL;
-  const size_t bytes = (size_t)c->p.n * c->p.n * c->p.n * sizeof(double);
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  const size_t bytes = (size_t)n3 * sizeof(double);
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ib], any_phi, bytes, cudaMemcpyDefault, c->st));
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ic], any_phi_prev ? any_phi_prev : any_phi, bytes,
                            cudaMemcpyDefault, c->st));
+  if (c->p.precision == PFC_MIXED) {
+    // the mixed path keeps phi as df pairs: convert in place
+    PFC_CUDA(launch_df_from_f64(n3, c->ring[c->ib], as_df(c->ring[c->ib]), c->st));
+    PFC_CUDA(launch_df_from_f64(n3, c->ring[c->ic], as_df(c->ring[c->ic]), c->st));
+    c->prof.launches += 2;
+  }
   return PFC_OK;
 }
 
@@ -598,9 +623,19 @@ int pfc_step(pfc_ctx* c, int nsteps, pfc_step_stats* stats) {
   return PFC_OK;
 }
 
+// Copy a state field out as FP64.  The mixed path's df fields are converted
+// first into ring[ia], the slot of phi^{k+1}, which holds nothing between
+// steps (each step starts by overwriting it with phi^k).
 static int copy_field(pfc_ctx* c, const double* src, double* dst) {
   if (!c || !dst) return PFC_EINVAL;
-  const size_t bytes = (size_t)c->p.n * c->p.n * c->p.n * sizeof(double);
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  const size_t bytes = (size_t)n3 * sizeof(double);
+  if (c->p.precision == PFC_MIXED) {
+    double* stage = c->ring[c->ia];
+    PFC_CUDA(launch_df_to_f64(n3, as_df(src), stage, c->st));
+    c->prof.launches += 1;
+    src = stage;
+  }
   PFC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->st));
   return PFC_OK;
 }
@@ -616,9 +651,12 @@ int pfc_get_omega(pfc_ctx* c, double* any_dst) {
 }
 
 static int diagnostics(int n, double h, double eps, const double* a, const double* b,
-                       double* partials, double* dout, double* hout, cudaStream_t st,
-                       double* res) {
-  PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
+                       bool df_fields, double* partials, double* dout, double* hout,
+                       cudaStream_t st, double* res) {
+  if (df_fields)
+    PFC_CUDA(launch_diagnostics_df(n, as_df(a), as_df(b), partials, dout, st));
+  else
+    PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
   PFC_CUDA(cudaMemcpyAsync(hout, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
   PFC_CUDA(cudaStreamSynchronize(st));
   const double h3 = h * h * h;
@@ -635,7 +673,7 @@ int pfc_diagnostics(pfc_ctx* c, double out[4]) {
   if (!c || !out) return PFC_EINVAL;
   c->prof.launches += 2;
   return diagnostics(c->p.n, c->p.L / c->p.n, c->p.eps, c->ring[c->ib], c->ring[c->ic],
-                     c->partials, c->dout, c->hout, c->st, out);
+                     c->p.precision == PFC_MIXED, c->partials, c->dout, c->hout, c->st, out);
 }
 
 int pfc_energy(pfc_ctx* c, double* F, double* F_modified) {
@@ -840,24 +878,25 @@ size_t pfc_reduce_scratch_bytes(int n) {
   return ((size_t)kReduceBlocks * kReduceComps + kReduceComps) * sizeof(double);
 }
 
-int pfc_op_diagnostics(int n, double h, double eps, const double* a, const double* b,
-                       void* scratch, double* out, void* stream) {
+static int op_diagnostics(int n, double h, double eps, const double* a, const double* b,
+                          bool df_fields, void* scratch, double* out, void* stream) {
   if (n < 2 || !a || !b || !scratch || !out || !(h > 0)) return PFC_EINVAL;
   double* partials = (double*)scratch;
   double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
   double hout[8];
-  cudaStream_t st = (cudaStream_t)stream;
-  PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
-  PFC_CUDA(cudaMemcpyAsync(hout, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  PFC_CUDA(cudaStreamSynchronize(st));
-  const double h3 = h * h * h;
-  const double F = 0.25 * h3 * hout[0] + 0.5 * (1.0 - eps) * h3 * hout[1] - h * hout[2] +
-                   0.5 * hout[3] / h;
-  out[0] = F;
-  out[1] = F + 0.5 * h * hout[4];
-  out[2] = h3 * hout[5];
-  out[3] = h * hout[2];
-  return PFC_OK;
+  return diagnostics(n, h, eps, a, b, df_fields, partials, dout, hout, (cudaStream_t)stream,
+                     out);
+}
+
+int pfc_op_diagnostics(int n, double h, double eps, const double* a, const double* b,
+                       void* scratch, double* out, void* stream) {
+  return op_diagnostics(n, h, eps, a, b, false, scratch, out, stream);
+}
+
+int pfc_op_diagnostics_df(int n, double h, double eps, const float* a, const float* b,
+                          void* scratch, double* out, void* stream) {
+  return op_diagnostics(n, h, eps, reinterpret_cast<const double*>(a),
+                        reinterpret_cast<const double*>(b), true, scratch, out, stream);
 }
 
 int pfc_op_residual_norm(int n, double h, double eps, double tau, const double* phi,
@@ -878,19 +917,42 @@ int pfc_op_residual_norm(int n, double h, double eps, double tau, const double* 
   return PFC_OK;
 }
 
-int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
-                  const double* mu, const double* om, const double* S1, const double* S2,
-                  const double* S3, const double* b, float* r1, float* r2, float* r3,
-                  float* q, void* scratch, double* out, void* stream) {
-  if (n < 2 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 || !r2 || !r3 || !q ||
-      !scratch || !out)
+int pfc_op_df_from_f64(long long count, const double* x, float* y, void* stream) {
+  if (count < 0 || (count > 0 && (!x || !y))) return PFC_EINVAL;
+  PFC_CUDA(launch_df_from_f64(count, x, reinterpret_cast<float2*>(y), (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_df_to_f64(long long count, const float* y, double* x, void* stream) {
+  if (count < 0 || (count > 0 && (!x || !y))) return PFC_EINVAL;
+  PFC_CUDA(launch_df_to_f64(count, reinterpret_cast<const float2*>(y), x,
+                            (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_source_df(int n, double h, double eps, const float* b, const float* c, float* S2,
+                     float* S3, void* stream) {
+  if (n < 1 || !(h > 0) || !b || !c || !S2 || !S3) return PFC_EINVAL;
+  PFC_CUDA(launch_source_df(make_lvl(n, h, eps, 1.0), reinterpret_cast<const float2*>(b),
+                            reinterpret_cast<const float2*>(c), reinterpret_cast<float2*>(S2),
+                            reinterpret_cast<float2*>(S3), (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_defect(int n, double h, double eps, double tau, const float* phi, const float* mu,
+                  const float* om, const float* S1, const float* S2, const float* S3,
+                  const float* b, float* r1, float* r2, float* r3, float* q, void* scratch,
+                  double* out, void* stream) {
+  if (n < 2 || (n & 1) || !(h > 0) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 ||
+      !r2 || !r3 || !q || !scratch || !out)
     return PFC_EINVAL;
   double* partials = (double*)scratch;
   double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
   double hv = 0;
   cudaStream_t st = (cudaStream_t)stream;
-  PFC_CUDA(launch_residual64_to32(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b, r1,
-                                  r2, r3, q, partials, dout, st));
+  auto D = [](const float* p) { return reinterpret_cast<const float2*>(p); };
+  PFC_CUDA(launch_defect_df(make_lvl(n, h, eps, tau), D(phi), D(mu), D(om), D(S1), D(S2),
+                            D(S3), D(b), r1, r2, r3, q, partials, dout, st));
   PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
   PFC_CUDA(cudaStreamSynchronize(st));
   *out = sqrt(hv / (3.0 * (double)n * n * n));
@@ -907,10 +969,11 @@ int pfc_op_lin_smooth(int n, double h, double eps, double tau, int sweeps, int z
   return PFC_OK;
 }
 
-int pfc_op_correct(int n, double* u1, double* u2, double* u3, const float* d1,
-                   const float* d2, const float* d3, void* stream) {
-  if (n < 1 || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;
-  PFC_CUDA(launch_correct64(n, u1, u2, u3, d1, d2, d3, (cudaStream_t)stream));
+int pfc_op_correct(int n, float* u1, float* u2, float* u3, const float* d1, const float* d2,
+                   const float* d3, void* stream) {
+  if (n < 2 || (n & 1) || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;
+  PFC_CUDA(launch_correct_df(n, reinterpret_cast<float2*>(u1), reinterpret_cast<float2*>(u2),
+                             reinterpret_cast<float2*>(u3), d1, d2, d3, (cudaStream_t)stream));
   return PFC_OK;
 }
 

@@ -149,6 +149,13 @@ __device__ __forceinline__ void operator_at(const Lvl& L, const Stencil& s,
   n3 = fma(-L.gh, lphi, w);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may be scheduled while its predecessor drains; pdl_wait()
+// blocks until the predecessor has completed and its writes are visible (a
+// no-op for a normal launch), pdl_trigger() lets the successor be scheduled.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 // Block-wide sum of NV doubles into thread 0 (fixed order: deterministic).
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* 32*NV */) {

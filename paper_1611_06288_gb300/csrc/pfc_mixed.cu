@@ -1,7 +1,8 @@
-// Mixed-precision defect correction: FP64 residual and Jacobian coefficient,
-// FP32 linear multigrid for the correction (see pfc_mixed.h).
+// Mixed-precision defect correction: double-float residual, source and
+// update, FP32 linear multigrid for the correction (see pfc_mixed.h).
 #include <math.h>
 
+#include "pfc_df.cuh"
 #include "pfc_internal.h"
 #include "pfc_mixed.h"
 
@@ -11,6 +12,26 @@ namespace {
 constexpr int kThreads = 256;
 
 inline unsigned grid_for(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
+
+// Kernel launch that, when `pdl` is set, carries programmatic stream
+// serialization (PDL): the kernel may be scheduled while its predecessor
+// drains and must call pdl_wait() before it touches memory.  Profiled runs
+// launch without it so that the events around each kernel time it alone.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
 
 // 3-D launch over an nx * ny * nz index box: x is the fastest (contiguous)
 // index, 256 threads per block; kernels read (x, y, z) from the grid and
@@ -102,39 +123,234 @@ __device__ __forceinline__ void split_cell(int64_t t, int n, int& p, int& j, int
   p = x - colour * half;
 }
 
-// FP64 residual r = S - N(u) -> FP32 copy, q = f'(phi) + (1-eps)/2 -> FP32
-// (both in the colour-split layout), and per-block partial sums of |r|^2 in
-// FP64.  q only feeds the FP32 correction solve, so it is formed in FP32 from
-// FP32 copies of phi and b, keeping GB300's narrow FP64 pipe for the residual.
-__global__ void k_residual64_to32(Lvl L, const double* __restrict__ phi,
-                                  const double* __restrict__ mu,
-                                  const double* __restrict__ om,
-                                  const double* __restrict__ S1,
-                                  const double* __restrict__ S2,
-                                  const double* __restrict__ S3,
-                                  const double* __restrict__ b, float* __restrict__ r1,
-                                  float* __restrict__ r2, float* __restrict__ r3,
-                                  float* __restrict__ q, double* partials) {
-  __shared__ double sm[32];
+// Constants of the double-float operator on one level.
+struct LvlD {
+  int n;
+  df tg;     // tau/h^2
+  df g;      // 1/h^2
+  df gh;     // 1/(2 h^2)
+  df c1;     // (1 - eps)/2
+  float c1f;
+};
+
+LvlD to_df(const Lvl& L) {
+  LvlD d;
+  d.n = L.n;
+  d.tg = df_const(L.tg);
+  d.g = df_const(L.g);
+  d.gh = df_const(L.gh);
+  d.c1 = df_const(L.c1);
+  d.c1f = (float)L.c1;
+  return d;
+}
+
+// Natural-order indices of a cell's six periodic neighbours (32-bit: n^3 < 2^31).
+struct Nb6 {
+  int xm, xp, ym, yp, zm, zp;
+};
+
+__device__ __forceinline__ Nb6 nb6_at(int t, int i, int j, int k, int n) {
+  const int nn = n * n;
+  Nb6 s;
+  s.xm = (i == 0) ? t + n - 1 : t - 1;
+  s.xp = (i + 1 == n) ? t - (n - 1) : t + 1;
+  s.ym = (j == 0) ? t + nn - n : t - n;
+  s.yp = (j + 1 == n) ? t - (nn - n) : t + n;
+  s.zm = (k == 0) ? t + n * nn - nn : t - nn;
+  s.zp = (k + 1 == n) ? t - (n * nn - nn) : t + nn;
+  return s;
+}
+
+// Unscaled 7-point Laplacian (neighbour sum - 6 centre) of a df field.
+__device__ __forceinline__ df df_lap(const float2* __restrict__ v, const Nb6& s, df c) {
+  const df sum = df_sum6(df_ld(v, s.xm), df_ld(v, s.xp), df_ld(v, s.ym), df_ld(v, s.yp),
+                         df_ld(v, s.zm), df_ld(v, s.zp));
+  return df_sub(sum, df_mul_f(c, 6.f));
+}
+
+// Block-wide FP32 sum into thread 0 (fixed order: deterministic).
+__device__ __forceinline__ float block_sum_f(float v, float* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sm[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = (lane < nw) ? sm[lane] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  }
+  return v;
+}
+
+// Defect of the outer loop: r = S - N(u) (Eqs. 5.4-5.6, M = 1) evaluated in
+// double-float from df fields, rounded to FP32 into the colour-split r1..r3;
+// q = f'(phi) + (1-eps)/2 (Jacobian of the cubic term of Eq. 5.2) in FP32
+// from the hi parts of phi and b, colour-split; per-block partial sums of
+// |r|^2 (FP32 within a block, one double per block).
+__global__ void k_defect_df(LvlD L, const float2* __restrict__ phi,
+                            const float2* __restrict__ mu, const float2* __restrict__ om,
+                            const float2* __restrict__ S1, const float2* __restrict__ S2,
+                            const float2* __restrict__ S3, const float2* __restrict__ b,
+                            float* __restrict__ r1, float* __restrict__ r2,
+                            float* __restrict__ r3, float* __restrict__ q, double* partials) {
+  __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
-  const float c1 = (float)L.c1;
-  double acc[1] = {0.0};
+  float acc = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
     const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
-    const Stencil s = stencil_at(i, j, k, n);
-    double x, y, z;
-    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
-    acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
+    const Nb6 s = nb6_at(t, i, j, k, n);
+    const df p = df_ld(phi, t), m = df_ld(mu, t), w = df_ld(om, t), bb = df_ld(b, t);
+    const df lmu = df_lap(mu, s, m);
+    const df lom = df_lap(om, s, w);
+    const df lphi = df_lap(phi, s, p);
+    // N1 = phi - tau Lap mu
+    const df x = df_sub(df_ld(S1, t), df_sub(p, df_mul(L.tg, lmu)));
+    // N2 = mu - (phi+b)(phi^2+b^2)/4 - (1-eps)/2 phi - Lap om
+    const df f = df_scale2(df_mul(df_add(p, bb), df_add(df_sqr(p), df_sqr(bb))), 0.25f);
+    df n2 = df_sub(df_sub(m, f), df_mul(L.c1, p));
+    n2 = df_sub(n2, df_mul(L.g, lom));
+    const df y = df_sub(df_ld(S2, t), n2);
+    // N3 = omega - Lap phi / 2
+    const df z = df_sub(df_ld(S3, t), df_sub(w, df_mul(L.gh, lphi)));
+    const float xf = df_round(x), yf = df_round(y), zf = df_round(z);
+    acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
     const int o = split_index(i, j, k, n);
-    r1[o] = (float)x;
-    r2[o] = (float)y;
-    r3[o] = (float)z;
-    const float pf = (float)__ldg(phi + t), bf = (float)__ldg(b + t);
-    q[o] = fmaf(0.75f * pf, pf, fmaf(0.5f * pf, bf, fmaf(0.25f * bf, bf, c1)));
+    r1[o] = xf;
+    r2[o] = yf;
+    r3[o] = zf;
+    const float pf = p.hi, bf = bb.hi;
+    q[o] = fmaf(0.75f * pf, pf, fmaf(0.5f * pf, bf, fmaf(0.25f * bf, bf, L.c1f)));
   }
-  block_sum<1>(acc, sm);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+  acc = block_sum_f(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
+// S2 = (1-eps)/2 b + 3 Lap b - Lap c and S3 = Lap b / 2 (Eqs. 5.9-5.10) in
+// double-float (S1 = b needs no work).
+__global__ void k_source_df(LvlD L, const float2* __restrict__ b, const float2* __restrict__ c,
+                            float2* __restrict__ S2, float2* __restrict__ S3) {
+  const int n = L.n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const Nb6 s = nb6_at(t, i, j, k, n);
+  const df bb = df_ld(b, t);
+  const df lb = df_mul(L.g, df_lap(b, s, bb));
+  const df lc = df_mul(L.g, df_lap(c, s, df_ld(c, t)));
+  df_st(S2, t, df_add(df_mul_f(lb, 3.f), df_sub(df_mul(L.c1, bb), lc)));
+  df_st(S3, t, df_scale2(lb, 0.5f));
+}
+
+// Block-wide df sums of NV values into thread 0 (fixed order: deterministic).
+template <int NV>
+__device__ __forceinline__ void block_sum_df(df (&v)[NV], float2* sm /* 32 * NV */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    df x = v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      df y;
+      y.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
+      y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
+      x = df_add(x, y);
+    }
+    if (lane == 0) sm[c * 32 + wid] = make_float2(x.hi, x.lo);
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) {
+      const float2 w = (lane < nw) ? sm[c * 32 + lane] : make_float2(0.f, 0.f);
+      df x;
+      x.hi = w.x;
+      x.lo = w.y;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        df y;
+        y.hi = __shfl_down_sync(0xffffffffu, x.hi, o);
+        y.lo = __shfl_down_sync(0xffffffffu, x.lo, o);
+        x = df_add(x, y);
+      }
+      v[c] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Raw per-cell sums of the energy F_h (Eq. 2.1), the modified energy and the
+// mass of the df fields a = phi^k, b = phi^{k-1}, in double-float:
+// sum a^4, sum a^2, sum |D a|^2 (as -(a, Lap a), summation by parts, Lemma
+// 2.1), sum (Lap a)^2, sum |D(a-b)|^2 (forward faces), sum a.  One df partial
+// per block and component.
+__global__ void k_diagnostics_df(int n, const float2* __restrict__ a,
+                                 const float2* __restrict__ b, float2* partials) {
+  __shared__ float2 sm[32 * 6];
+  const int cells = n * n * n;
+  df acc[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) acc[c] = df{0.f, 0.f};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const Nb6 s = nb6_at(t, i, j, k, n);
+    const df x = df_ld(a, t);
+    const df axp = df_ld(a, s.xp), ayp = df_ld(a, s.yp), azp = df_ld(a, s.zp);
+    const df lap = df_sub(df_sum6(df_ld(a, s.xm), axp, df_ld(a, s.ym), ayp, df_ld(a, s.zm), azp),
+                          df_mul_f(x, 6.f));
+    const df y = df_sub(x, df_ld(b, t));
+    const df ex = df_sub(df_sub(axp, df_ld(b, s.xp)), y);
+    const df ey = df_sub(df_sub(ayp, df_ld(b, s.yp)), y);
+    const df ez = df_sub(df_sub(azp, df_ld(b, s.zp)), y);
+    const df x2 = df_sqr(x);
+    acc[0] = df_add(acc[0], df_sqr(x2));
+    acc[1] = df_add(acc[1], x2);
+    acc[2] = df_sub(acc[2], df_mul(x, lap));
+    acc[3] = df_add(acc[3], df_sqr(lap));
+    acc[4] = df_add(acc[4], df_add(df_add(df_sqr(ex), df_sqr(ey)), df_sqr(ez)));
+    acc[5] = df_add(acc[5], x);
+  }
+  block_sum_df<6>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) partials[blockIdx.x * 6 + c] = make_float2(acc[c].hi, acc[c].lo);
+  }
+}
+
+// Fixed-order df sum of the block partials -> out[0..5] as doubles.
+__global__ void k_reduce_df6(const float2* __restrict__ partials, int nparts, double* out) {
+  __shared__ float2 sm[32 * 6];
+  df acc[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) acc[c] = df{0.f, 0.f};
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) acc[c] = df_add(acc[c], df_ld(partials, p * 6 + c));
+  }
+  block_sum_df<6>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) out[c] = (double)acc[c].hi + (double)acc[c].lo;
+  }
+}
+
+// FP64 <-> df conversions of whole fields; in place allowed (each thread
+// reads its 8 bytes before writing them).
+__global__ void k_df_from_f64(int64_t count, const double* x, float2* y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const df v = df_from_double(x[t]);
+  y[t] = make_float2(v.hi, v.lo);
+}
+
+__global__ void k_df_to_f64(int64_t count, const float2* y, double* x) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  x[t] = df_to_double(y[t]);
 }
 
 __global__ void k_reduce1(const double* __restrict__ partials, int nparts, double* out) {
@@ -147,6 +363,8 @@ __global__ void k_reduce1(const double* __restrict__ partials, int nparts, doubl
 
 // 8-cell average of a split-layout field onto the (split-layout) level n/2.
 __global__ void k_restrict32(int n, const float* __restrict__ f, float* __restrict__ c) {
+  pdl_wait();
+  pdl_trigger();
   const int nc = n >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
             K = blockIdx.z;
@@ -183,6 +401,8 @@ template <bool ZERO>
 __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* d3,
                                const float* __restrict__ r1, const float* __restrict__ r2,
                                const float* __restrict__ r3, const float* __restrict__ q) {
+  pdl_wait();
+  pdl_trigger();
   const int n = L.n, half = n >> 1;
   const int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
             k = blockIdx.z;
@@ -211,6 +431,8 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
                                float* __restrict__ t3, const float* __restrict__ r1,
                                const float* __restrict__ r2, const float* __restrict__ r3,
                                const float* __restrict__ q) {
+  pdl_wait();
+  pdl_trigger();
   const int n = L.n, half = n >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
             k = blockIdx.z;
@@ -238,6 +460,8 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
 __global__ void k_copy3(int cells, const float* __restrict__ a1, const float* __restrict__ a2,
                         const float* __restrict__ a3, float* __restrict__ b1,
                         float* __restrict__ b2, float* __restrict__ b3) {
+  pdl_wait();
+  pdl_trigger();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cells) return;
   b1[t] = a1[t];
@@ -256,6 +480,8 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ q,
                                           float* __restrict__ c1, float* __restrict__ c2,
                                           float* __restrict__ c3) {
+  pdl_wait();
+  pdl_trigger();
   const int n = L.n, nc = n >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
             K = blockIdx.z;
@@ -296,6 +522,8 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
                                 float* __restrict__ d1, float* __restrict__ d2,
                                 float* __restrict__ d3) {
+  pdl_wait();
+  pdl_trigger();
   const int nc = n >> 1, half = n >> 1;
   const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
             k = blockIdx.z;
@@ -753,6 +981,8 @@ __device__ void tail_vcycle(float* smem, const TailParams& P, bool zero_top, flo
 // levels' q are restricted in shared memory, and the top level's d is stored
 // back at the end.
 __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ float smem[];
   __shared__ float red[2][32];
   __shared__ int done;
@@ -803,17 +1033,20 @@ constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 K
 
 // u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
 
-__global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
-                            double* __restrict__ u3, const float* __restrict__ d1,
-                            const float* __restrict__ d2, const float* __restrict__ d3) {
+// u += d: df state plus the FP32 correction (colour-split), per component.
+__global__ void k_correct_df(int n, float2* __restrict__ u1, float2* __restrict__ u2,
+                             float2* __restrict__ u3, const float* __restrict__ d1,
+                             const float* __restrict__ d2, const float* __restrict__ d3) {
+  pdl_wait();
+  pdl_trigger();
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
             k = blockIdx.z;
   if (i >= n || j >= n) return;
   const int t = (k * n + j) * n + i;
   const int o = split_index(i, j, k, n);
-  u1[t] += (double)__ldg(d1 + o);
-  u2[t] += (double)__ldg(d2 + o);
-  u3[t] += (double)__ldg(d3 + o);
+  df_st(u1, t, df_add_f(df_ld(u1, t), __ldg(d1 + o)));
+  df_st(u2, t, df_add_f(df_ld(u2, t), __ldg(d2 + o)));
+  df_st(u3, t, df_add_f(df_ld(u3, t), __ldg(d3 + o)));
 }
 
 inline int nblocks_reduce(int64_t cells) {
@@ -836,21 +1069,19 @@ struct Ctx32 {
 
 // `sweeps` damped Jacobi sweeps d -> t -> d ...; the result ends in d.
 cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* const* d,
-                     float* const* t, float* const* r, const float* q, cudaStream_t st) {
+                     float* const* t, float* const* r, const float* q, cudaStream_t st,
+                     bool pdl) {
   const int n = L.n;
   const int64_t cells = (int64_t)n * n * n;
   const Launch3 g = launch3(n, n, n);
   float* src[3] = {d[0], d[1], d[2]};
   float* dst[3] = {t[0], t[1], t[2]};
   int done = 0;
-  while (done < sweeps) {
+  cudaError_t e = cudaSuccess;
+  while (done < sweeps && e == cudaSuccess) {
     const bool z = zero_init && done == 0;
-    if (z)
-      k_lin_jacobi32<true><<<g.grid, g.block, 0, st>>>(
-          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
-    else
-      k_lin_jacobi32<false><<<g.grid, g.block, 0, st>>>(
-          L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    e = launch_k(pdl, z ? k_lin_jacobi32<true> : k_lin_jacobi32<false>, g.grid, g.block, 0, st,
+                 L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
     done += 1;
     for (int c = 0; c < 3; ++c) {
       float* x = src[c];
@@ -858,12 +1089,9 @@ cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* 
       dst[c] = x;
     }
   }
-  cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess && src[0] != d[0]) {
-    k_copy3<<<grid_for(cells), kThreads, 0, st>>>((int)cells, src[0], src[1], src[2], d[0], d[1],
-                                                  d[2]);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess && src[0] != d[0])
+    e = launch_k(pdl, k_copy3, dim3(grid_for(cells)), dim3(kThreads), 0, st, (int)cells, src[0],
+                 src[1], src[2], d[0], d[1], d[2]);
   return e;
 }
 
@@ -877,23 +1105,21 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
   if (c.kind[l] == PFC_SWEEP_JACOBI) {
     const int js = sweeps * (l == 0 ? c.jfactor0 : c.jfactor);
-    cudaError_t e = jacobi32(L, js, c.w, zero_init, d, c.mx->t[l], r, q, c.st);
+    cudaError_t e = jacobi32(L, js, c.w, zero_init, d, c.mx->t[l], r, q, c.st, c.pr == nullptr);
     prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
     return e;
   }
   const Launch3 g = launch3(L.n / 2, L.n, L.n);
-  for (int s = 0; s < sweeps; ++s) {
-    for (int colour = 0; colour < 2; ++colour) {
-      if (zero_init && s == 0 && colour == 0)
-        k_lin_smooth32<true><<<g.grid, g.block, 0, c.st>>>(L, colour, d[0], d[1], d[2], r[0],
-                                                           r[1], r[2], q);
-      else
-        k_lin_smooth32<false><<<g.grid, g.block, 0, c.st>>>(L, colour, d[0], d[1], d[2], r[0],
-                                                            r[1], r[2], q);
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < sweeps && e == cudaSuccess; ++s) {
+    for (int colour = 0; colour < 2 && e == cudaSuccess; ++colour) {
+      const bool z = zero_init && s == 0 && colour == 0;
+      e = launch_k(c.pr == nullptr, z ? k_lin_smooth32<true> : k_lin_smooth32<false>, g.grid,
+                   g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
     }
   }
   prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps, c.st);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
@@ -927,9 +1153,9 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
     attr_set = true;
   }
   prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
-  k_lin_tail32<<<1, kTailThreads, smem, c.st>>>(P);
+  cudaError_t e = launch_k(c.pr == nullptr, k_lin_tail32, dim3(1), dim3(kTailThreads), smem, c.st, P);
   prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
-  return cudaGetLastError();
+  return e;
 }
 
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
@@ -966,33 +1192,60 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   const int nc = L.n / 2;
   const Launch3 gr = launch3(nc, nc, nc);
   prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
-  k_lin_residual_restrict32<<<gr.grid, gr.block, 0, c.st>>>(
-      L, mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l],
-      mx.r[l + 1][0], mx.r[l + 1][1], mx.r[l + 1][2]);
+  e = launch_k(c.pr == nullptr, k_lin_residual_restrict32, gr.grid, gr.block, 0, c.st, L,
+               mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l],
+               mx.r[l + 1][0], mx.r[l + 1][1], mx.r[l + 1][2]);
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
   const Launch3 gp = launch3(L.n, L.n, L.n);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
-  k_prolong_add32<<<gp.grid, gp.block, 0, c.st>>>(
-      L.n, mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
-      mx.d[l][2]);
+  e = launch_k(c.pr == nullptr, k_prolong_add32, gp.grid, gp.block, 0, c.st, L.n,
+               mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
+               mx.d[l][2]);
   prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (e != cudaSuccess) return e;
   return smooth32(c, l, c.p->nu2, false);
 }
 
 }  // namespace
 
-cudaError_t launch_residual64_to32(const Lvl& L, const double* phi, const double* mu,
-                                   const double* om, const double* S1, const double* S2,
-                                   const double* S3, const double* b, float* r1, float* r2,
-                                   float* r3, float* q, double* partials, double* out,
-                                   cudaStream_t st) {
+cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
+                             const float2* om, const float2* S1, const float2* S2,
+                             const float2* S3, const float2* b, float* r1, float* r2, float* r3,
+                             float* q, double* partials, double* out, cudaStream_t st) {
   const int nb = nblocks_reduce((int64_t)L.n * L.n * L.n);
-  k_residual64_to32<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1, r2,
-                                                   r3, q, partials);
+  k_defect_df<<<nb, kReduceThreads, 0, st>>>(to_df(L), phi, mu, om, S1, S2, S3, b, r1, r2, r3,
+                                             q, partials);
   k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_df(const Lvl& L, const float2* b, const float2* c, float2* S2,
+                             float2* S3, cudaStream_t st) {
+  const Launch3 g = launch3(L.n, L.n, L.n);
+  k_source_df<<<g.grid, g.block, 0, st>>>(to_df(L), b, c, S2, S3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics_df(int n, const float2* a, const float2* b, double* partials,
+                                  double* out, cudaStream_t st) {
+  const int nb = nblocks_reduce((int64_t)n * n * n);
+  float2* parts = reinterpret_cast<float2*>(partials);
+  k_diagnostics_df<<<nb, kReduceThreads, 0, st>>>(n, a, b, parts);
+  k_reduce_df6<<<1, kReduceThreads, 0, st>>>(parts, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_df_from_f64<<<grid_for(count), kThreads, 0, st>>>(count, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_df_to_f64<<<grid_for(count), kThreads, 0, st>>>(count, y, x);
   return cudaGetLastError();
 }
 
@@ -1028,29 +1281,27 @@ cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_ini
   float* d[3] = {d1, d2, d3};
   float* t[3] = {t1, t2, t3};
   float* r[3] = {(float*)r1, (float*)r2, (float*)r3};
-  return jacobi32(to_f32(L), sweeps, w, zero_init, d, t, r, q, st);
+  return jacobi32(to_f32(L), sweeps, w, zero_init, d, t, r, q, st, true);
 }
 
-cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
-                             const float* d2, const float* d3, cudaStream_t st) {
+cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const float* d1,
+                              const float* d2, const float* d3, cudaStream_t st, bool pdl) {
   const Launch3 g = launch3(n, n, n);
-  k_correct64<<<g.grid, g.block, 0, st>>>(n, u1, u2, u3, d1, d2, d3);
-  return cudaGetLastError();
+  return launch_k(pdl, k_correct_df, g.grid, g.block, 0, st, n, u1, u2, u3, d1, d2, d3);
 }
 
-cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
-                                 double* const S[3], const double* b, double* partials,
+cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],
+                                 float2* const S[3], const float2* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr) {
   prof_begin(pr, PFC_K_DEFECT, st);
-  cudaError_t e = launch_residual64_to32(L0, u[0], u[1], u[2], S[0], S[1], S[2], b,
-                                         mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0], partials,
-                                         dout, st);
+  cudaError_t e = launch_defect_df(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
+                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
 
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
-                                     const int* sizes, double* const u[3], cudaStream_t st,
+                                     const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr) {
   Ctx32 c;
   c.mx = &mx;
@@ -1071,14 +1322,15 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
   for (int l = 1; l < nl && e == cudaSuccess; ++l) {
     const Launch3 g = launch3(sizes[l], sizes[l], sizes[l]);
     prof_begin(pr, PFC_K_RESTRICT, st);
-    k_restrict32<<<g.grid, g.block, 0, st>>>(sizes[l - 1], mx.q[l - 1], mx.q[l]);
+    e = launch_k(pr == nullptr, k_restrict32, g.grid, g.block, 0, st, sizes[l - 1],
+                 mx.q[l - 1], mx.q[l]);
     prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
-    e = cudaGetLastError();
   }
   for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic) e = vcycle32(c, 0, ic == 0);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
-    e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st);
+    e = launch_correct_df(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,
+                          pr == nullptr);
     prof_end(pr, PFC_K_CORRECT, 0, 1, st);
   }
   return e;

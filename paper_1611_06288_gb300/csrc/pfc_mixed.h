@@ -1,18 +1,22 @@
-// Mixed-precision time-step solve: FP64 defect correction around an FP32
-// multigrid solve of the linearised split system.
+// Mixed-precision time-step solve: a double-float defect correction around
+// an FP32 multigrid solve of the linearised split system.
 //
-// Outer loop (FP64): r = S - N(u) with the FP64 operator of Eqs. 5.4-5.6, the
-// RMS of r checked against the tolerance, and q = f'(phi) + (1-eps)/2 (the
-// Jacobian of the cubic term of Eq. 5.2 at the current phi) formed in FP64.
+// Outer loop (double-float, see pfc_df.cuh): phi, mu, omega, S2 and S3 are
+// held as (hi, lo) FP32 pairs with a 48-bit significand; r = S - N(u) with
+// the operator of Eqs. 5.4-5.6, the RMS of r checked against the tolerance,
+// q = f'(phi) + (1-eps)/2 (the Jacobian of the cubic term of Eq. 5.2 at the
+// current phi) formed in FP32.
 // Inner solve (FP32): J d = r with
 //   J1 d = d_phi - tau Lap d_mu
 //   J2 d = d_mu - q d_phi - Lap d_om
 //   J3 d = d_om - Lap d_phi / 2
-// by V-cycles of red-black Gauss-Seidel with the same pointwise 3x3 system as
-// the FP64 smoother (q frozen), 8-cell restriction of the residual and of q,
-// and trilinear prolongation of the correction.  Then u += d in FP64.
-// The fixed point is the FP64 solution of N(u) = S: the FP32 part only
-// computes corrections.
+// by V-cycles of red-black Gauss-Seidel or damped collective Jacobi with the
+// same pointwise 3x3 system as the FP64 smoother (q frozen), 8-cell
+// restriction of the residual and of q, and trilinear prolongation of the
+// correction.  Then u += d in double-float.
+// The fixed point is the solution of N(u) = S to the df rounding of the
+// residual (a few 2^-48 of its operands): the FP32 part only computes
+// corrections.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,24 +49,37 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
   }
 }
 
-// FP64 defect r = S - N(u) -> FP32 r and q on level 0, and the sum of |r|^2 at
-// dout[0] (two launches).
-cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
-                                 double* const S[3], const double* b, double* partials,
+// Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
+// sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
+cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],
+                                 float2* const S[3], const float2* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr);
 
 // One defect correction after mixed_enqueue_defect: q restricted to every
 // level, p.inner_cycles FP32 V-cycles on J d = r from d = 0, then u += d.
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
-                                     const int* sizes, double* const u[3], cudaStream_t st,
+                                     const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr);
 
+// S2, S3 of Eqs. 5.9-5.10 from df fields b = phi^k, c = phi^{k-1}.
+cudaError_t launch_source_df(const Lvl& L, const float2* b, const float2* c, float2* S2,
+                             float2* S3, cudaStream_t st);
+
+// The raw sums of launch_diagnostics (out[0..5]) from df fields a = phi^k,
+// b = phi^{k-1}, in double-float; partials: kReduceBlocks * 6 float2 slots
+// (the FP64 path's partial-sum buffer).
+cudaError_t launch_diagnostics_df(int n, const float2* a, const float2* b, double* partials,
+                                  double* out, cudaStream_t st);
+
+// Whole-field conversions FP64 <-> df (count cells; in place allowed).
+cudaError_t launch_df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
+cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStream_t st);
+
 // Primitive launches of the FP32 kernels (for the C ABI checks).
-cudaError_t launch_residual64_to32(const Lvl& L, const double* phi, const double* mu,
-                                   const double* om, const double* S1, const double* S2,
-                                   const double* S3, const double* b, float* r1, float* r2,
-                                   float* r3, float* q, double* partials, double* out,
-                                   cudaStream_t st);
+cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
+                             const float2* om, const float2* S1, const float2* S2,
+                             const float2* S3, const float2* b, float* r1, float* r2, float* r3,
+                             float* q, double* partials, double* out, cudaStream_t st);
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
                                 float* d2, float* d3, const float* r1, const float* r2,
                                 const float* r3, const float* q, cudaStream_t st);
@@ -70,7 +87,8 @@ cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_ini
                                 float* d1, float* d2, float* d3, float* t1, float* t2,
                                 float* t3, const float* r1, const float* r2, const float* r3,
                                 const float* q, cudaStream_t st);
-cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
-                             const float* d2, const float* d3, cudaStream_t st);
+cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const float* d1,
+                              const float* d2, const float* d3, cudaStream_t st,
+                              bool pdl = true);
 
 }  // namespace pfc

@@ -46,3 +46,27 @@ def to_split(x):
 def from_split(y):
     n = y.shape[0]
     return y.ravel()[split_perm(n)].reshape(y.shape)
+
+
+def to_df(x):
+    """FP64 array -> double-float pairs (..., 2) float32: hi = FP32 rounding of
+    x, lo = FP32 rounding of x - hi (the remainder is exact in FP64)."""
+    x = np.asarray(x, dtype=np.float64)
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    return np.stack([hi, lo], axis=-1)
+
+
+def from_df(y):
+    """Double-float pairs -> FP64 values hi + lo (exact)."""
+    y = np.asarray(y)
+    return y[..., 0].astype(np.float64) + y[..., 1].astype(np.float64)
+
+
+def dev_df(x):
+    return torch.from_numpy(np.ascontiguousarray(to_df(x))).to("cuda")
+
+
+def host_df(t):
+    torch.cuda.synchronize()
+    return from_df(t.detach().cpu().numpy())
