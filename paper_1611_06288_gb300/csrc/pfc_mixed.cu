@@ -471,6 +471,9 @@ __global__ void k_copy3(int cells, const float* __restrict__ a1, const float* __
 
 // rho = r - J d at the 8 children of each coarse cell, averaged (split layout
 // on both levels).
+// ZERO: d = 0 on entry (no pre-smoothing from a zero start), so rho = r and d
+// is not read.
+template <bool ZERO>
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
                                           const float* __restrict__ d3,
@@ -491,6 +494,12 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   for (int c = 0; c < 8; ++c) {
     const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
     const Stencil s = split_stencil(i >> 1, j, k, (i + j + k) & 1, n);
+    if (ZERO) {
+      a1 += __ldg(r1 + s.c);
+      a2 += __ldg(r2 + s.c);
+      a3 += __ldg(r3 + s.c);
+      continue;
+    }
     const float p = __ldg(d1 + s.c), m = __ldg(d2 + s.c), w = __ldg(d3 + s.c);
     const float lm = fmaf(-6.f, m, nbsum(d2, s));
     const float lw = fmaf(-6.f, w, nbsum(d3, s));
@@ -517,7 +526,9 @@ __device__ __forceinline__ float interp8f(const float* __restrict__ e, int64_t o
 }
 
 // d += P e (trilinear, weights 27, 9, 3, 1 over 64), split layout on both
-// levels; threads walk the fine level in split order.
+// levels; threads walk the fine level in split order.  ASSIGN: d = P e (d was
+// zero and is not read).
+template <bool ASSIGN>
 __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
                                 float* __restrict__ d1, float* __restrict__ d2,
@@ -540,9 +551,10 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
             o110 = split_index(I2, J2, K, nc), o101 = split_index(I2, J, K2, nc),
             o011 = split_index(I, J2, K2, nc), o111 = split_index(I2, J2, K2, nc);
   const float w = 1.0f / 64.0f;
-  d1[t] = fmaf(w, interp8f(e1, o000, o100, o010, o001, o110, o101, o011, o111), d1[t]);
-  d2[t] = fmaf(w, interp8f(e2, o000, o100, o010, o001, o110, o101, o011, o111), d2[t]);
-  d3[t] = fmaf(w, interp8f(e3, o000, o100, o010, o001, o110, o101, o011, o111), d3[t]);
+  const float z1 = ASSIGN ? 0.f : d1[t], z2 = ASSIGN ? 0.f : d2[t], z3 = ASSIGN ? 0.f : d3[t];
+  d1[t] = fmaf(w, interp8f(e1, o000, o100, o010, o001, o110, o101, o011, o111), z1);
+  d2[t] = fmaf(w, interp8f(e2, o000, o100, o010, o001, o110, o101, o011, o111), z2);
+  d3[t] = fmaf(w, interp8f(e3, o000, o100, o010, o001, o110, o101, o011, o111), z3);
 }
 
 // Coarsest level of the linear problem when it is not part of a tail launch:
@@ -1177,22 +1189,18 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
     prof_end(c.pr, PFC_K_LIN_COARSE, l, 1, c.st);
     return cudaGetLastError();
   }
-  cudaError_t e;
-  if (c.p->nu1 > 0) {
-    e = smooth32(c, l, c.p->nu1, zero_init);
-  } else {
-    e = cudaSuccess;
-    if (zero_init) {
-      const size_t bytes = (size_t)L.n * L.n * L.n * sizeof(float);
-      for (int q = 0; q < 3 && e == cudaSuccess; ++q)
-        e = cudaMemsetAsync(mx.d[l][q], 0, bytes, c.st);
-    }
-  }
+  cudaError_t e = cudaSuccess;
+  // without pre-smoothing from a zero start d stays 0 until the prolongation,
+  // which then assigns instead of adding
+  const bool dzero = c.p->nu1 <= 0 && zero_init;
+  if (c.p->nu1 > 0) e = smooth32(c, l, c.p->nu1, zero_init);
   if (e != cudaSuccess) return e;
   const int nc = L.n / 2;
   const Launch3 gr = launch3(nc, nc, nc);
   prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
-  e = launch_k(c.pr == nullptr, k_lin_residual_restrict32, gr.grid, gr.block, 0, c.st, L,
+  e = launch_k(c.pr == nullptr,
+               dzero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
+               gr.grid, gr.block, 0, c.st, L,
                mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l],
                mx.r[l + 1][0], mx.r[l + 1][1], mx.r[l + 1][2]);
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
@@ -1200,7 +1208,8 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
   const Launch3 gp = launch3(L.n, L.n, L.n);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
-  e = launch_k(c.pr == nullptr, k_prolong_add32, gp.grid, gp.block, 0, c.st, L.n,
+  e = launch_k(c.pr == nullptr, dzero ? k_prolong_add32<true> : k_prolong_add32<false>,
+               gp.grid, gp.block, 0, c.st, L.n,
                mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
                mx.d[l][2]);
   prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);

@@ -62,6 +62,25 @@ def test_random16_ten_steps(precision, smoother, graphs):
     assert s.step_index == wl.steps
 
 
+@pytest.mark.parametrize("nu", [(0, 1), (1, 0), (0, 2), (1, 2)])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_mixed_cycle_shapes(nu, graphs):
+    """Mixed path with V(nu1, nu2) inner cycles, including no pre-smoothing
+    (the zero-start restriction and assigning prolongation) and no
+    post-smoothing: the converged steps match the oracle."""
+    n, L = 32, 48.0           # levels 32 (global memory) and 16 (shared-memory tail)
+    rng = np.random.default_rng(32)
+    phi0 = 0.1 + 0.1 * rng.uniform(-1, 1, (n,) * 3)
+    ref = oracle_run(phi0, 2, L / n, 0.2, 0.05, "newton")
+    s = PFCSolver(n, L, 0.2, 0.05, phi0, tol=1e-12, precision="mixed", nu1=nu[0], nu2=nu[1],
+                  inner_cycles=2, coarse_sweeps=2, max_cycles=80)
+    s.use_graphs(graphs)
+    for k in range(2):
+        st = s.step(1)
+        assert st.residual <= 1e-12
+        assert rel_l2(host(s.phi()), ref[k][0]) <= PARITY_RTOL
+
+
 @pytest.mark.parametrize("n,coarsest", [(4, 2), (12, 6), (20, 10), (24, 6)])
 def test_uneven_sizes_and_level_counts(n, coarsest):
     """Grids that are not powers of two and the smallest grid, against the
@@ -126,13 +145,13 @@ def test_energy_law_and_mass_on_gpu_trajectory():
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_full_size_128_residual_by_oracle(precision):
     """128^3 smooth-mode workload (L = 32, eps = 0.025, dt = 0.0125, tol 1e-9)
-    in the benchmark's configuration: after two steps the oracle evaluates
+    in the benchmark's configuration (the workload's mixed-path settings): after two steps the oracle evaluates
     S - N(u) of the GPU result on the CPU in FP64 and finds it below the
     tolerance; mass is conserved."""
     wl = W.smooth_sweep(128)
     phi0 = wl.phi0()
-    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision,
-                  inner_cycles=2 if precision == "mixed" else 1)
+    kw = wl.mixed() if precision == "mixed" else {}
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision, **kw)
     s.step(1)
     b = phi0
     a1 = host(s.phi())
@@ -151,7 +170,7 @@ def test_full_size_256_polycrystal_one_step():
     wl = W.polycrystal(256)
     phi0 = wl.phi0()
     s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision="mixed",
-                  inner_cycles=2)
+                  **wl.mixed())
     st = s.step(1)
     assert st.residual <= wl.tol
     a, mu, om = host(s.phi()), host(s.mu()), host(s.omega())
