@@ -401,6 +401,28 @@ int pfc_op_lin_jacobi(int n, double h, double eps, double tau, int sweeps,
                       const float* d_r1, const float* d_r2, const float* d_r3,
                       const float* d_q, void* stream);
 
+/* Restricted residual of the linear system, rho_c = I (r - J d): the 8-cell
+ * average of r - J d with (J d)1 = d_phi - tau Lap d_mu, (J d)2 = d_mu -
+ * q d_phi - Lap d_om, (J d)3 = d_om - Lap d_phi / 2 (Eqs. 5.4-5.6
+ * differentiated in phi), from the level of n^3 cells (n divisible by 4) to
+ * the colour-split d_c1..3 of (n/2)^3.  zero_init != 0 declares d = 0 (d
+ * and q are then not read and may be NULL). */
+int pfc_op_lin_residual_restrict(int n, double h, double eps, double tau,
+                                 int zero_init, const float* d_d1,
+                                 const float* d_d2, const float* d_d3,
+                                 const float* d_r1, const float* d_r2,
+                                 const float* d_r3, const float* d_q,
+                                 float* d_c1, float* d_c2, float* d_c3,
+                                 void* stream);
+
+/* d += P e (assign != 0: d = P e, d not read), P the trilinear cell-centred
+ * prolongation (weights 27, 9, 3, 1 over 64) from the colour-split
+ * (n/2)^3 fields d_e1..3 to the colour-split n^3 fields d_d1..3; n divisible
+ * by 4. */
+int pfc_op_lin_prolong(int n, int assign, const float* d_e1, const float* d_e2,
+                       const float* d_e3, float* d_d1, float* d_d2, float* d_d3,
+                       void* stream);
+
 /* u += d for the three components: df fields d_u1..3 plus the colour-split
  * FP32 corrections d_d1..3, in double-float.  n even. */
 int pfc_op_correct(int n, float* d_u1, float* d_u2, float* d_u3,

@@ -94,6 +94,8 @@ _SIGS = {
     "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
     "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
+    "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
+    "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
     "pfc_op_df_from_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_df_to_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_source_df": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
@@ -368,6 +370,19 @@ def pfc_op_lin_smooth(n, h, eps, tau, sweeps, zero_init, d1, d2, d3, r1, r2, r3,
     check(lib().pfc_op_lin_smooth(n, h, eps, tau, sweeps, int(bool(zero_init)), ptr(d1),
                                   ptr(d2), ptr(d3), ptr(r1), ptr(r2), ptr(r3), ptr(q),
                                   stream), "pfc_op_lin_smooth")
+
+
+def pfc_op_lin_residual_restrict(n, h, eps, tau, zero_init, d1, d2, d3, r1, r2, r3, q, c1, c2,
+                                 c3, stream=None):
+    check(lib().pfc_op_lin_residual_restrict(n, h, eps, tau, int(bool(zero_init)), ptr(d1),
+                                             ptr(d2), ptr(d3), ptr(r1), ptr(r2), ptr(r3),
+                                             ptr(q), ptr(c1), ptr(c2), ptr(c3), stream),
+          "pfc_op_lin_residual_restrict")
+
+
+def pfc_op_lin_prolong(n, assign, e1, e2, e3, d1, d2, d3, stream=None):
+    check(lib().pfc_op_lin_prolong(n, int(bool(assign)), ptr(e1), ptr(e2), ptr(e3), ptr(d1),
+                                   ptr(d2), ptr(d3), stream), "pfc_op_lin_prolong")
 
 
 def pfc_op_df_from_f64(count, x, y, stream=None):

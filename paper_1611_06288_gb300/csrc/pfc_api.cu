@@ -969,6 +969,26 @@ int pfc_op_lin_smooth(int n, double h, double eps, double tau, int sweeps, int z
   return PFC_OK;
 }
 
+int pfc_op_lin_residual_restrict(int n, double h, double eps, double tau, int zero_init,
+                                 const float* d1, const float* d2, const float* d3,
+                                 const float* r1, const float* r2, const float* r3,
+                                 const float* q, float* c1, float* c2, float* c3,
+                                 void* stream) {
+  if (n < 2 || (n & 3) || !(h > 0) || !r1 || !r2 || !r3 || !c1 || !c2 || !c3 ||
+      (!zero_init && (!d1 || !d2 || !d3 || !q)))
+    return PFC_EINVAL;
+  PFC_CUDA(launch_lin_residual_restrict32(make_lvl(n, h, eps, tau), zero_init != 0, d1, d2, d3,
+                                          r1, r2, r3, q, c1, c2, c3, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, const float* e3,
+                       float* d1, float* d2, float* d3, void* stream) {
+  if (n < 2 || (n & 3) || !e1 || !e2 || !e3 || !d1 || !d2 || !d3) return PFC_EINVAL;
+  PFC_CUDA(launch_prolong32(n, assign != 0, e1, e2, e3, d1, d2, d3, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
 int pfc_op_correct(int n, float* u1, float* u2, float* u3, const float* d1, const float* d2,
                    const float* d3, void* stream) {
   if (n < 2 || (n & 1) || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;

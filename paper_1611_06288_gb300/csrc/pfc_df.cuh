@@ -141,6 +141,44 @@ __device__ __forceinline__ df df_sum6(df v0, df v1, df v2, df v3, df v4, df v5) 
   return r;
 }
 
+// Unnormalised double-float accumulator for sums that are rounded to FP32 at
+// the end: hi collects the hi parts exactly (two_sum), lo collects their
+// rounding errors and the lo parts in plain FP32.  The value hi + lo carries
+// an absolute error of a few 2^-48 times the sum of the magnitudes added,
+// like a chain of df_add, at 8 instead of 11 operations per term and without
+// renormalising in between.
+struct dacc {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dacc dacc_of(df a) {
+  dacc r;
+  r.hi = a.hi;
+  r.lo = a.lo;
+  return r;
+}
+
+__device__ __forceinline__ void dacc_add(dacc& a, float hi, float lo) {
+  float s, e;
+  two_sum(a.hi, hi, s, e);
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(e, lo));
+}
+
+__device__ __forceinline__ void dacc_add(dacc& a, df b) { dacc_add(a, b.hi, b.lo); }
+__device__ __forceinline__ void dacc_sub(dacc& a, df b) { dacc_add(a, -b.hi, -b.lo); }
+
+// k * a for a df constant k and an unnormalised pair a: hi = fl(k.hi a.hi),
+// lo = its exact rounding error plus the cross terms (k.lo a.lo dropped).
+__device__ __forceinline__ dacc dacc_mul(df k, dacc a) {
+  dacc r;
+  r.hi = __fmul_rn(k.hi, a.hi);
+  r.lo = __fmaf_rn(k.lo, a.hi, __fmaf_rn(k.hi, a.lo, __fmaf_rn(k.hi, a.hi, -r.hi)));
+  return r;
+}
+
+__device__ __forceinline__ float dacc_round(dacc a) { return __fadd_rn(a.hi, a.lo); }
+
 // The value rounded to FP32.
 __device__ __forceinline__ float df_round(df a) { return __fadd_rn(a.hi, a.lo); }
 

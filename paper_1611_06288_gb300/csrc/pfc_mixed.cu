@@ -184,17 +184,54 @@ __device__ __forceinline__ float block_sum_f(float v, float* sm) {
   return v;
 }
 
+// Unscaled 7-point Laplacian (neighbour sum - 6 centre) of a df field as an
+// unnormalised pair: -6 c split exactly by one FMA, then the six neighbours.
+__device__ __forceinline__ dacc dacc_lap(const float2* __restrict__ v, const Nb6& s, df c) {
+  dacc L;
+  L.hi = __fmul_rn(-6.f, c.hi);
+  L.lo = __fmaf_rn(-6.f, c.lo, __fmaf_rn(-6.f, c.hi, -L.hi));
+  dacc_add(L, df_ld(v, s.xm));
+  dacc_add(L, df_ld(v, s.xp));
+  dacc_add(L, df_ld(v, s.ym));
+  dacc_add(L, df_ld(v, s.yp));
+  dacc_add(L, df_ld(v, s.zm));
+  dacc_add(L, df_ld(v, s.zp));
+  return L;
+}
+
+// f(p, b) = (p+b)(p^2+b^2)/4 (Eq. 5.2) from df operands as an unnormalised
+// pair: each factor is formed exactly in its hi part plus an FP32 correction.
+__device__ __forceinline__ dacc dacc_cubic(df p, df b) {
+  dacc s;                                     // p + b
+  two_sum(p.hi, b.hi, s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(p.lo, b.lo));
+  const float p2 = __fmul_rn(p.hi, p.hi), b2 = __fmul_rn(b.hi, b.hi);
+  const float p2e = __fmaf_rn(__fadd_rn(p.hi, p.hi), p.lo, __fmaf_rn(p.hi, p.hi, -p2));
+  const float b2e = __fmaf_rn(__fadd_rn(b.hi, b.hi), b.lo, __fmaf_rn(b.hi, b.hi, -b2));
+  dacc t;                                     // p^2 + b^2
+  two_sum(p2, b2, t.hi, t.lo);
+  t.lo = __fadd_rn(t.lo, __fadd_rn(p2e, b2e));
+  dacc f;                                     // s t / 4 (the 1/4 is exact)
+  const float hi = __fmul_rn(s.hi, t.hi);
+  const float lo =
+      __fmaf_rn(s.lo, t.hi, __fmaf_rn(s.hi, t.lo, __fmaf_rn(s.hi, t.hi, -hi)));
+  f.hi = __fmul_rn(0.25f, hi);
+  f.lo = __fmul_rn(0.25f, lo);
+  return f;
+}
+
 // Defect of the outer loop: r = S - N(u) (Eqs. 5.4-5.6, M = 1) evaluated in
-// double-float from df fields, rounded to FP32 into the colour-split r1..r3;
+// double-float from df fields, every component one unnormalised sum of its
+// terms rounded to FP32 into the colour-split r1..r3;
 // q = f'(phi) + (1-eps)/2 (Jacobian of the cubic term of Eq. 5.2) in FP32
 // from the hi parts of phi and b, colour-split; per-block partial sums of
 // |r|^2 (FP32 within a block, one double per block).
-__global__ void k_defect_df(LvlD L, const float2* __restrict__ phi,
-                            const float2* __restrict__ mu, const float2* __restrict__ om,
-                            const float2* __restrict__ S1, const float2* __restrict__ S2,
-                            const float2* __restrict__ S3, const float2* __restrict__ b,
-                            float* __restrict__ r1, float* __restrict__ r2,
-                            float* __restrict__ r3, float* __restrict__ q, double* partials) {
+__global__ void __launch_bounds__(256, 6) k_defect_df(
+    LvlD L, const float2* __restrict__ phi, const float2* __restrict__ mu,
+    const float2* __restrict__ om, const float2* __restrict__ S1,
+    const float2* __restrict__ S2, const float2* __restrict__ S3,
+    const float2* __restrict__ b, float* __restrict__ r1, float* __restrict__ r2,
+    float* __restrict__ r3, float* __restrict__ q, double* partials) {
   __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
@@ -202,20 +239,27 @@ __global__ void k_defect_df(LvlD L, const float2* __restrict__ phi,
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
     const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
     const Nb6 s = nb6_at(t, i, j, k, n);
-    const df p = df_ld(phi, t), m = df_ld(mu, t), w = df_ld(om, t), bb = df_ld(b, t);
-    const df lmu = df_lap(mu, s, m);
-    const df lom = df_lap(om, s, w);
-    const df lphi = df_lap(phi, s, p);
-    // N1 = phi - tau Lap mu
-    const df x = df_sub(df_ld(S1, t), df_sub(p, df_mul(L.tg, lmu)));
-    // N2 = mu - (phi+b)(phi^2+b^2)/4 - (1-eps)/2 phi - Lap om
-    const df f = df_scale2(df_mul(df_add(p, bb), df_add(df_sqr(p), df_sqr(bb))), 0.25f);
-    df n2 = df_sub(df_sub(m, f), df_mul(L.c1, p));
-    n2 = df_sub(n2, df_mul(L.g, lom));
-    const df y = df_sub(df_ld(S2, t), n2);
-    // N3 = omega - Lap phi / 2
-    const df z = df_sub(df_ld(S3, t), df_sub(w, df_mul(L.gh, lphi)));
-    const float xf = df_round(x), yf = df_round(y), zf = df_round(z);
+    const df p = df_ld(phi, t), bb = df_ld(b, t);
+    // r1 = S1 - phi + tau/h^2 Lap mu
+    dacc x = dacc_of(df_ld(S1, t));
+    dacc_sub(x, p);
+    const dacc tl = dacc_mul(L.tg, dacc_lap(mu, s, df_ld(mu, t)));
+    dacc_add(x, tl.hi, tl.lo);
+    // r2 = S2 - mu + f(phi, b) + (1-eps)/2 phi + 1/h^2 Lap om
+    dacc y = dacc_of(df_ld(S2, t));
+    dacc_sub(y, df_ld(mu, t));
+    const dacc f = dacc_cubic(p, bb);
+    dacc_add(y, f.hi, f.lo);
+    const dacc cp = dacc_mul(L.c1, dacc_of(p));
+    dacc_add(y, cp.hi, cp.lo);
+    const dacc gl = dacc_mul(L.g, dacc_lap(om, s, df_ld(om, t)));
+    dacc_add(y, gl.hi, gl.lo);
+    // r3 = S3 - omega + 1/(2h^2) Lap phi
+    dacc z = dacc_of(df_ld(S3, t));
+    dacc_sub(z, df_ld(om, t));
+    const dacc hl = dacc_mul(L.gh, dacc_lap(phi, s, p));
+    dacc_add(z, hl.hi, hl.lo);
+    const float xf = dacc_round(x), yf = dacc_round(y), zf = dacc_round(z);
     acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
     const int o = split_index(i, j, k, n);
     r1[o] = xf;
@@ -471,8 +515,71 @@ __global__ void k_copy3(int cells, const float* __restrict__ a1, const float* __
 
 // rho = r - J d at the 8 children of each coarse cell, averaged (split layout
 // on both levels).
-// ZERO: d = 0 on entry (no pre-smoothing from a zero start), so rho = r and d
-// is not read.
+// Fine split-layout indices of the eight children of coarse cell (I, J, K)
+// (in[8]: per fine row of the 2x2x2 block, the two cells at position I of
+// the two colour halves) and of the 24 face neighbours of the block outside
+// it (out[24]).  Cell (i, j, k) of the split layout sits in the half of
+// colour (i+j+k)&1 at position i/2 of its row; n even.
+__device__ __forceinline__ void block_indices(int I, int J, int K, int n, int (&in)[8],
+                                              int (&out)[24]) {
+  const int half = n >> 1;
+  const int j0 = 2 * J, k0 = 2 * K;
+  const int jm = (j0 == 0) ? n - 1 : j0 - 1, jp = (j0 + 2 == n) ? 0 : j0 + 2;
+  const int km = (k0 == 0) ? n - 1 : k0 - 1, kp = (k0 + 2 == n) ? 0 : k0 + 2;
+  const int Im = (I == 0) ? half - 1 : I - 1, Ip = (I + 1 == half) ? 0 : I + 1;
+  int o = 0;
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int j = j0 + jj, k = k0 + kk;
+      const int rw = (k * n + j) * n, par = (j + k) & 1;
+      in[2 * (2 * kk + jj)] = rw + I;
+      in[2 * (2 * kk + jj) + 1] = rw + half + I;
+      out[o++] = rw + (1 - par) * half + Im;   // (2I-1, j, k)
+      out[o++] = rw + par * half + Ip;         // (2I+2, j, k)
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+    const int k = k0 + kk;
+    out[o++] = (k * n + jm) * n + I;           // (2I and 2I+1, j0-1, k)
+    out[o++] = (k * n + jm) * n + half + I;
+    out[o++] = (k * n + jp) * n + I;           // (2I and 2I+1, j0+2, k)
+    out[o++] = (k * n + jp) * n + half + I;
+  }
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj) {
+    const int j = j0 + jj;
+    out[o++] = (km * n + j) * n + I;           // (2I and 2I+1, j, k0-1)
+    out[o++] = (km * n + j) * n + half + I;
+    out[o++] = (kp * n + j) * n + I;           // (2I and 2I+1, j, k0+2)
+    out[o++] = (kp * n + j) * n + half + I;
+  }
+}
+
+// Sums of a field over the eight children (s_in) and over the 24 outside
+// face neighbours (s_out).  Summed over the children, the 7-point Laplacian's
+// interior faces cancel: sum_children Lap v = s_out - 3 s_in (unscaled).
+__device__ __forceinline__ void block_sums(const float* __restrict__ v, const int (&in)[8],
+                                           const int (&out)[24], float& s_in, float& s_out) {
+  float a = 0.f, b = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a += __ldg(v + in[c]);
+#pragma unroll
+  for (int c = 0; c < 24; ++c) b += __ldg(v + out[c]);
+  s_in = a;
+  s_out = b;
+}
+
+// Restricted residual of the linear system: the average over the eight
+// children of r - J d, with
+//   (J d)1 = d_phi - tau/h^2 Lap d_mu
+//   (J d)2 = d_mu - q d_phi - 1/h^2 Lap d_om
+//   (J d)3 = d_om - 1/(2h^2) Lap d_phi,
+// the averaged Laplacians taken from the block sums above and q d_phi summed
+// cell by cell.  One thread per coarse cell.  ZERO: d = 0 on entry (no
+// pre-smoothing from a zero start), so rho = r and d is not read.
 template <bool ZERO>
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
@@ -489,24 +596,25 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
             K = blockIdx.z;
   if (I >= nc || J >= nc) return;
+  int in[8], out[24];
+  block_indices(I, J, K, n, in, out);
   float a1 = 0.f, a2 = 0.f, a3 = 0.f;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const int i = 2 * I + (c & 1), j = 2 * J + ((c >> 1) & 1), k = 2 * K + (c >> 2);
-    const Stencil s = split_stencil(i >> 1, j, k, (i + j + k) & 1, n);
-    if (ZERO) {
-      a1 += __ldg(r1 + s.c);
-      a2 += __ldg(r2 + s.c);
-      a3 += __ldg(r3 + s.c);
-      continue;
-    }
-    const float p = __ldg(d1 + s.c), m = __ldg(d2 + s.c), w = __ldg(d3 + s.c);
-    const float lm = fmaf(-6.f, m, nbsum(d2, s));
-    const float lw = fmaf(-6.f, w, nbsum(d3, s));
-    const float lp = fmaf(-6.f, p, nbsum(d1, s));
-    a1 += __ldg(r1 + s.c) - fmaf(-L.tg, lm, p);
-    a2 += __ldg(r2 + s.c) - (fmaf(-__ldg(q + s.c), p, m) - L.g * lw);
-    a3 += __ldg(r3 + s.c) - fmaf(-L.gh, lp, w);
+    a1 += __ldg(r1 + in[c]);
+    a2 += __ldg(r2 + in[c]);
+    a3 += __ldg(r3 + in[c]);
+  }
+  if (!ZERO) {
+    float pin, pout, min_, mout, win, wout, qp = 0.f;
+    block_sums(d1, in, out, pin, pout);
+    block_sums(d2, in, out, min_, mout);
+    block_sums(d3, in, out, win, wout);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) qp = fmaf(__ldg(q + in[c]), __ldg(d1 + in[c]), qp);
+    a1 = fmaf(L.tg, fmaf(-3.f, min_, mout), a1 - pin);
+    a2 = fmaf(L.g, fmaf(-3.f, win, wout), (a2 - min_) + qp);
+    a3 = fmaf(L.gh, fmaf(-3.f, pin, pout), a3 - win);
   }
   const int o = split_index(I, J, K, nc);
   c1[o] = 0.125f * a1;
@@ -514,20 +622,41 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   c3[o] = 0.125f * a3;
 }
 
-__device__ __forceinline__ float interp8f(const float* __restrict__ e, int64_t o000,
-                                          int64_t o100, int64_t o010, int64_t o001,
-                                          int64_t o110, int64_t o101, int64_t o011,
-                                          int64_t o111) {
-  const float g2 = (__ldg(e + o100) + __ldg(e + o010)) + __ldg(e + o001);
-  const float g3 = (__ldg(e + o110) + __ldg(e + o101)) + __ldg(e + o011);
-  float acc = fmaf(3.f, g3, __ldg(e + o111));
-  acc = fmaf(9.f, g2, acc);
-  return fmaf(27.f, __ldg(e + o000), acc);
+// Trilinear cell-centred prolongation of one coarse field onto the eight
+// children of coarse cell (I, J, K), as three one-dimensional passes: the
+// child on the low side of an axis takes (3 e_0 + e_-1)/4, on the high side
+// (3 e_0 + e_+1)/4 (together the weights 27, 9, 3, 1 over 64).  cidx[z][y][x]
+// are the split-layout indices of the 3x3x3 coarse neighbourhood; out[kk][jj]
+// [a] receives the child (2I+a, 2J+jj, 2K+kk).
+__device__ __forceinline__ void prolong_block(const float* __restrict__ e, const int (&cidx)[27],
+                                              float (&out)[8]) {
+  float zx[3][3][2];                           // [y][x][child z]
+#pragma unroll
+  for (int y = 0; y < 3; ++y) {
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      const float lo = __ldg(e + cidx[0 * 9 + y * 3 + x]);
+      const float mid = __ldg(e + cidx[1 * 9 + y * 3 + x]);
+      const float hi = __ldg(e + cidx[2 * 9 + y * 3 + x]);
+      zx[y][x][0] = fmaf(3.f, mid, lo);
+      zx[y][x][1] = fmaf(3.f, mid, hi);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      float yx[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
+      out[(2 * kk + jj) * 2 + 0] = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);
+      out[(2 * kk + jj) * 2 + 1] = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);
+    }
+  }
 }
 
-// d += P e (trilinear, weights 27, 9, 3, 1 over 64), split layout on both
-// levels; threads walk the fine level in split order.  ASSIGN: d = P e (d was
-// zero and is not read).
+// d += P e (ASSIGN: d = P e; d was zero and is not read), split layout on
+// both levels, one thread per coarse cell writing its eight children.
 template <bool ASSIGN>
 __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
@@ -536,25 +665,40 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
   pdl_wait();
   pdl_trigger();
   const int nc = n >> 1, half = n >> 1;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
-            k = blockIdx.z;
-  if (x >= n || j >= n) return;
-  const int colour = x >= half;
-  const int i = 2 * (x - colour * half) + ((j + k + colour) & 1);
-  const int t = (k * n + j) * n + x;
-  const int I = i >> 1, J = j >> 1, K = k >> 1;
-  const int I2 = ((i & 1) ? I + 1 : I - 1 + nc) % nc;
-  const int J2 = ((j & 1) ? J + 1 : J - 1 + nc) % nc;
-  const int K2 = ((k & 1) ? K + 1 : K - 1 + nc) % nc;
-  const int o000 = split_index(I, J, K, nc), o100 = split_index(I2, J, K, nc),
-            o010 = split_index(I, J2, K, nc), o001 = split_index(I, J, K2, nc),
-            o110 = split_index(I2, J2, K, nc), o101 = split_index(I2, J, K2, nc),
-            o011 = split_index(I, J2, K2, nc), o111 = split_index(I2, J2, K2, nc);
-  const float w = 1.0f / 64.0f;
-  const float z1 = ASSIGN ? 0.f : d1[t], z2 = ASSIGN ? 0.f : d2[t], z3 = ASSIGN ? 0.f : d3[t];
-  d1[t] = fmaf(w, interp8f(e1, o000, o100, o010, o001, o110, o101, o011, o111), z1);
-  d2[t] = fmaf(w, interp8f(e2, o000, o100, o010, o001, o110, o101, o011, o111), z2);
-  d3[t] = fmaf(w, interp8f(e3, o000, o100, o010, o001, o110, o101, o011, o111), z3);
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
+            K = blockIdx.z;
+  if (I >= nc || J >= nc) return;
+  int cidx[27];
+  {
+    const int Is[3] = {(I == 0) ? nc - 1 : I - 1, I, (I + 1 == nc) ? 0 : I + 1};
+    const int Js[3] = {(J == 0) ? nc - 1 : J - 1, J, (J + 1 == nc) ? 0 : J + 1};
+    const int Ks[3] = {(K == 0) ? nc - 1 : K - 1, K, (K + 1 == nc) ? 0 : K + 1};
+#pragma unroll
+    for (int z = 0; z < 3; ++z)
+#pragma unroll
+      for (int y = 0; y < 3; ++y)
+#pragma unroll
+        for (int x = 0; x < 3; ++x) cidx[z * 9 + y * 3 + x] = split_index(Is[x], Js[y], Ks[z], nc);
+  }
+  int fidx[8];
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int i = 2 * I + a, j = 2 * J + jj, k = 2 * K + kk;
+        fidx[(2 * kk + jj) * 2 + a] = (k * n + j) * n + ((i + j + k) & 1) * half + I;
+      }
+  const float* e[3] = {e1, e2, e3};
+  float* d[3] = {d1, d2, d3};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    float v[8];
+    prolong_block(e[f], cidx, v);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) d[f][fidx[c]] = ASSIGN ? v[c] : v[c] + d[f][fidx[c]];
+  }
 }
 
 // Coarsest level of the linear problem when it is not part of a tail launch:
@@ -1061,9 +1205,23 @@ __global__ void k_correct_df(int n, float2* __restrict__ u1, float2* __restrict_
   df_st(u3, t, df_add_f(df_ld(u3, t), __ldg(d3 + o)));
 }
 
-inline int nblocks_reduce(int64_t cells) {
-  const int64_t nb = (cells + kReduceThreads - 1) / kReduceThreads;
-  return (int)(nb < kReduceBlocks ? nb : kReduceBlocks);
+// Blocks of a grid-stride reduction kernel: one full wave (resident blocks per
+// SM from the occupancy calculator times the SM count), no more than the work
+// needs and than kReduceBlocks partial-sum slots.
+template <class Kernel>
+int wave_blocks(Kernel kernel, int64_t cells) {
+  int dev = 0, sms = 0, occ = 0;
+  int nb = kReduceBlocks;
+  if (cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kReduceThreads, 0) ==
+          cudaSuccess &&
+      occ > 0 && sms > 0)
+    nb = occ * sms;
+  if (nb > kReduceBlocks) nb = kReduceBlocks;
+  const int64_t need = (cells + kReduceThreads - 1) / kReduceThreads;
+  if (need < nb) nb = (int)need;
+  return nb < 1 ? 1 : nb;
 }
 
 struct Ctx32 {
@@ -1206,7 +1364,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
   if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
-  const Launch3 gp = launch3(L.n, L.n, L.n);
+  const Launch3 gp = launch3(nc, nc, nc);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
   e = launch_k(c.pr == nullptr, dzero ? k_prolong_add32<true> : k_prolong_add32<false>,
                gp.grid, gp.block, 0, c.st, L.n,
@@ -1223,7 +1381,7 @@ cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,
                              float* q, double* partials, double* out, cudaStream_t st) {
-  const int nb = nblocks_reduce((int64_t)L.n * L.n * L.n);
+  const int nb = wave_blocks(k_defect_df, (int64_t)L.n * L.n * L.n);
   k_defect_df<<<nb, kReduceThreads, 0, st>>>(to_df(L), phi, mu, om, S1, S2, S3, b, r1, r2, r3,
                                              q, partials);
   k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
@@ -1239,7 +1397,7 @@ cudaError_t launch_source_df(const Lvl& L, const float2* b, const float2* c, flo
 
 cudaError_t launch_diagnostics_df(int n, const float2* a, const float2* b, double* partials,
                                   double* out, cudaStream_t st) {
-  const int nb = nblocks_reduce((int64_t)n * n * n);
+  const int nb = wave_blocks(k_diagnostics_df, (int64_t)n * n * n);
   float2* parts = reinterpret_cast<float2*>(partials);
   k_diagnostics_df<<<nb, kReduceThreads, 0, st>>>(n, a, b, parts);
   k_reduce_df6<<<1, kReduceThreads, 0, st>>>(parts, nb, out);
@@ -1256,6 +1414,25 @@ cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStre
   if (count <= 0) return cudaSuccess;
   k_df_to_f64<<<grid_for(count), kThreads, 0, st>>>(count, y, x);
   return cudaGetLastError();
+}
+
+cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float* d1,
+                                          const float* d2, const float* d3, const float* r1,
+                                          const float* r2, const float* r3, const float* q,
+                                          float* c1, float* c2, float* c3, cudaStream_t st) {
+  const int nc = L.n / 2;
+  const Launch3 g = launch3(nc, nc, nc);
+  return launch_k(true,
+                  zero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
+                  g.grid, g.block, 0, st, to_f32(L), d1, d2, d3, r1, r2, r3, q, c1, c2, c3);
+}
+
+cudaError_t launch_prolong32(int n, bool assign, const float* e1, const float* e2,
+                             const float* e3, float* d1, float* d2, float* d3, cudaStream_t st) {
+  const int nc = n / 2;
+  const Launch3 g = launch3(nc, nc, nc);
+  return launch_k(true, assign ? k_prolong_add32<true> : k_prolong_add32<false>, g.grid,
+                  g.block, 0, st, n, e1, e2, e3, d1, d2, d3);
 }
 
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,

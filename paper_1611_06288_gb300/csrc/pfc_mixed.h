@@ -80,6 +80,12 @@ cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,
                              float* q, double* partials, double* out, cudaStream_t st);
+cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float* d1,
+                                          const float* d2, const float* d3, const float* r1,
+                                          const float* r2, const float* r3, const float* q,
+                                          float* c1, float* c2, float* c3, cudaStream_t st);
+cudaError_t launch_prolong32(int n, bool assign, const float* e1, const float* e2,
+                             const float* e3, float* d1, float* d2, float* d3, cudaStream_t st);
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
                                 float* d2, float* d3, const float* r1, const float* r2,
                                 const float* r3, const float* q, cudaStream_t st);

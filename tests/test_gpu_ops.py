@@ -262,6 +262,52 @@ def test_defect_and_correct(n):
 
 
 @pytest.mark.parametrize("n", [4, 12, 32])
+@pytest.mark.parametrize("zero", [False, True])
+def test_linear_residual_restrict_fp32(n, zero):
+    """I (r - J d) in FP32 (block sums: the Laplacians' interior faces cancel
+    over the eight children) against the oracle's restrict(r - J d) in FP64,
+    colour-split on both levels; d = 0 for the zero-start variant."""
+    h, b, c, u = case(n)
+    p = prm()
+    rng = np.random.default_rng(21 + n)
+    q = O.jacobian_coefficient(u[0], b, p).astype(np.float32)
+    r = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    d = [np.zeros((n,) * 3, np.float32) if zero else
+         (0.1 * rng.standard_normal((n,) * 3)).astype(np.float32) for _ in range(3)]
+    f64 = lambda xs: [x.astype(np.float64) for x in xs]
+    ref = [O.restrict(x) for x in
+           (np.array(rr) - jd for rr, jd in zip(f64(r), O.jacobian_apply(f64(d), q.astype(np.float64), h, p)))]
+    nc = n // 2
+    cc = [empty(nc, torch.float32) for _ in range(3)]
+    dd = [dev(to_split(x), torch.float32) for x in d]
+    B.pfc_op_lin_residual_restrict(n, h, EPS, TAU, zero, *(None, None, None) if zero else dd,
+                                   *[dev(to_split(x), torch.float32) for x in r],
+                                   None if zero else dev(to_split(q), torch.float32), *cc)
+    # FP32 sums of O(1) terms scaled by up to 12/h^2 ~ 19: a few FP32 ulps of that
+    for g, x in zip(cc, ref):
+        assert_close_field(from_split(host(g)), x, 2e-6, "rho")
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
+@pytest.mark.parametrize("assign", [False, True])
+def test_linear_prolong_fp32(n, assign):
+    """d += P e (or d = P e) in FP32, three one-dimensional passes, against
+    the oracle's trilinear prolongation in FP64 (colour-split layouts)."""
+    rng = np.random.default_rng(31 + n)
+    nc = n // 2
+    e = [rng.standard_normal((nc,) * 3).astype(np.float32) for _ in range(3)]
+    d0 = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    dd = [dev(to_split(x), torch.float32) for x in d0]
+    if assign:
+        for t in dd:
+            t.fill_(float("nan"))            # must not be read
+    B.pfc_op_lin_prolong(n, assign, *[dev(to_split(x), torch.float32) for x in e], *dd)
+    for g, x, y in zip(dd, d0, e):
+        ref = O.prolong(y.astype(np.float64)) + (0.0 if assign else x.astype(np.float64))
+        assert_close_field(from_split(host(g)), ref, 1e-6, "d+Pe")
+
+
+@pytest.mark.parametrize("n", [4, 12, 32])
 @pytest.mark.parametrize("zero_init", [True, False])
 def test_linear_smoother_fp32(n, zero_init):
     h, b, c, u = case(n)
