@@ -57,6 +57,12 @@ KERNEL_BYTES = {
 
 
 
+# DRAM bytes (read + write) of one launch of a kernel class, from the ncu
+# capture summarised in profiles/ (cold L2); None where no capture of the
+# current kernel exists.
+NCU_TRAFFIC = {"defect": 118.0e6}   # profiles/k_defect_df_128.md
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -312,8 +318,11 @@ def run_ours(args):
     achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
     bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
     peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
+    traffic = NCU_TRAFFIC.get(dom_cls)
     roofline = {"bound": bound, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak, "traffic": None,
+                "unit": unit, "frac": achieved / peak,
+                "traffic": traffic / 1e9 if traffic is not None else None,
+                "traffic_unit": "GB per launch (ncu dram__bytes_read + write)",
                 "kernel": f"{dom_cls} (level {dom_lvl}, {m}^3)",
                 "ms_per_launch": dom_time / max(groups, 1),
                 "timing": f"CUDA events around each launch, {prof_steps} host-driven steps "
