@@ -6,9 +6,9 @@ Workload: 128^3 cells, L = 32, eps = 0.025, phi0 = 0.1 sin(2 pi x/L)
 cos(2 pi y/L) sin(2 pi z/L), dt = 0.0125, residual tolerance 1e-9 (RMS of the
 three components).  A "step" is one full time step: source, multigrid
 cycles until the residual is below the tolerance, and the energy/mass
-diagnostics.  The headline value is the mixed-precision path (double-float
-defect correction around FP32 multigrid); the plain FP64 FAS path is timed
-beside it.
+diagnostics.  The headline value is the mixed-precision path (FP64 defect
+correction around FP32 multigrid); the plain FP64 FAS path and the same
+correction with a double-float outer loop are timed beside it.
 
 Prints one JSON line (rank 0).  Under torchrun every rank advances its own
 replica (no collective on the data path; weak scaling).
@@ -32,6 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "steps/s at 128^3 (mixed vs FP64 GPU, residual 1e-9); % HBM roof per V-cycle"
+# arithmetic of each path: FP64 outer loop around FP32 multigrid, or the outer
+# loop in double-float (FP32 pairs) around FP32 multigrid
+DTYPES = {"mixed": "f64+f32", "mixed_df": "df32+f32", "fp64": "f64"}
 UNIT = "steps/s"
 WORKLOAD = {"workload": "smooth-mode 128^3", "n": 128, "L": 32.0, "eps": 0.025,
             "dt": 0.0125, "tol": 1e-9, "phi0": "0.1 sin(2pi x/L) cos(2pi y/L) sin(2pi z/L)"}
@@ -57,10 +60,21 @@ KERNEL_BYTES = {
 
 
 
-# DRAM bytes (read + write) of one launch of a kernel class, from the ncu
-# capture summarised in profiles/ (cold L2); None where no capture of the
-# current kernel exists.
-NCU_TRAFFIC = {"defect": 118.0e6}   # profiles/k_defect_df_128.md
+# DRAM bytes (read + write) of one launch of a kernel class of a precision,
+# from the ncu capture summarised in profiles/ (cold L2); absent where no
+# capture of the current kernel exists.
+NCU_TRAFFIC = {("mixed_df", "defect"): 118.0e6}   # profiles/k_defect_df_128.md
+
+# FP64-ALU-bound kernel classes of a precision: algorithmic FP64 flops per
+# cell of one counted launch (FMA = 2) and launches per group.  The FP64
+# defect evaluates three 7-point Laplacians (21), the residual rows (18, the
+# cubic term 6 of them), |r|^2 (6) and the Newton coefficient q (9): 54.
+KERNEL_FLOPS = {("mixed", "defect"): (54.0, 2)}
+
+# FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
+# sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
+# x 2 flops x 152 SMs x 2.07 GHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.07e9 / 1e12
 
 
 def parse():
@@ -77,6 +91,9 @@ def parse():
     ap.add_argument("--nu2", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # the headline path: FP64 defect correction around FP32 multigrid; the
+    # double-float form is timed beside it
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df"])
     return ap.parse_args()
 
 
@@ -282,8 +299,8 @@ def run_ours(args):
         return total, cycles
 
     # ---- mixed path (headline) --------------------------------------------
-    s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="mixed",
-                  **mixed_kw)
+    s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                  precision=args.precision, **mixed_kw)
     for _ in range(args.warmup):
         s.step(1)
         s.diagnostics()
@@ -313,12 +330,19 @@ def run_ours(args):
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
     m = n >> dom_lvl
-    per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
-    groups = dom_launches / per_group
-    achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
-    bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
-    peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
-    traffic = NCU_TRAFFIC.get(dom_cls)
+    if (args.precision, dom_cls) in KERNEL_FLOPS:
+        per_cell, per_group = KERNEL_FLOPS[(args.precision, dom_cls)]
+        groups = dom_launches / per_group
+        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e12 if dom_time > 0 else 0.0
+        bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
+        peak_src = "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz (derived)"
+    else:
+        per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
+        groups = dom_launches / per_group
+        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
+        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+        peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
+    traffic = NCU_TRAFFIC.get((args.precision, dom_cls))
     roofline = {"bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak,
                 "traffic": traffic / 1e9 if traffic is not None else None,
@@ -340,12 +364,25 @@ def run_ours(args):
             "cycles_per_step": cyc64}
     s64.close()
 
+    # ---- the other mixed form, same workload, tolerance and settings -------
+    other = "mixed_df" if args.precision == "mixed" else "mixed"
+    so = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision=other,
+                   **mixed_kw)
+    for _ in range(args.warmup):
+        so.step(1)
+        so.diagnostics()
+    ms_o, cyc_o = time_steps(so, args.steps)
+    alt = {"precision": other, "dtype": DTYPES[other], "value": args.steps / (ms_o / 1e3),
+           "unit": UNIT, "steps": args.steps, "ms_per_step": ms_o / args.steps,
+           "cycles_per_step": cyc_o}
+    so.close()
+
     # ---- end to end through the C ABI with host buffers -------------------
     pin_a = torch.from_numpy(phi0.copy()).pin_memory()
     pin_b = torch.from_numpy(phi0.copy()).pin_memory()
     pin_out = torch.empty_like(pin_a).pin_memory()
-    se = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="mixed",
-                   **mixed_kw)
+    se = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                   precision=args.precision, **mixed_kw)
     e2e_steps = max(1, min(args.steps, 10))
 
     def host_step():
@@ -378,10 +415,10 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "df32+f32",
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": WORKLOAD["workload"], "n": n, "L": wl.L, "eps": wl.eps,
-                       "dt": wl.dt, "tol": wl.tol, "precision": "mixed",
+                       "dt": wl.dt, "tol": wl.tol, "precision": args.precision,
                        "solver": mixed_kw, "step_execution": "CUDA graph",
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MiB write) before every timed step"},
@@ -389,6 +426,7 @@ def run_ours(args):
             "dof_updates_per_s": value * cells,
             "fp64": fp64,
             "mixed_over_fp64": value / ws / fp64["value"],
+            ("mixed_df" if args.precision == "mixed" else "mixed_fp64_outer"): alt,
             "roofline": roofline,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -46,7 +46,9 @@ extern "C" {
 #define PFC_ECUDA   -5  /* a CUDA runtime call failed */
 
 #define PFC_FP64  0     /* FAS V-cycles entirely in FP64 (Algorithm 1) */
-#define PFC_MIXED 1     /* double-float defect correction around FP32 multigrid */
+#define PFC_MIXED 1     /* FP64 defect correction around FP32 multigrid */
+#define PFC_MIXED_DF 2  /* the same with the outer state, residual, update and
+                           energy/mass sums in double-float (FP32 pairs) */
 
 #define PFC_NEWTON 0    /* pointwise Newton linearisation of the cubic term */
 #define PFC_PICARD 1    /* the paper's local Picard linearisation (Section 5) */
@@ -68,26 +70,26 @@ typedef struct pfc_params {
   double dt;           /* time step tau > 0 */
   int    nu1, nu2;     /* pre/post smoothing sweeps (Algorithm 1); >= 0 */
   double tol;          /* absolute tolerance on the fine-grid residual (FP64;
-                          double-float on the mixed path), RMS over the three
+                          double-float for PFC_MIXED_DF), RMS over the three
                           components */
   int    max_cycles;   /* V-cycles (or defect corrections) per step */
-  int    precision;    /* PFC_FP64 or PFC_MIXED */
+  int    precision;    /* PFC_FP64, PFC_MIXED or PFC_MIXED_DF */
   int    smoother;     /* PFC_NEWTON or PFC_PICARD (FP64 path) */
   int    coarsest;     /* coarsen while the level size is even and larger
                           than this; the last level is solved by sweeping to
                           convergence.  >= 2 */
-  int    inner_cycles; /* PFC_MIXED: FP32 V-cycles per defect correction */
+  int    inner_cycles; /* mixed paths: FP32 V-cycles per defect correction */
   int    policy;       /* PFC_POLICY_HYBRID or PFC_POLICY_RB */
   double jacobi_weight;/* damping of the collective Jacobi sweep, (0, 1] */
   int    jacobi_factor;/* Jacobi sweeps per requested sweep on coarse Jacobi levels */
   int    jacobi_factor0;/* the same on the finest level */
   double stiff_hi, stiff_lo; /* thresholds of the hybrid policy */
-  double coarse_stiffness;   /* PFC_MIXED: also stop coarsening at the first
+  double coarse_stiffness;   /* mixed paths: also stop coarsening at the first
                                 level (below the finest, of at most 16^3
                                 cells) whose stiffness 108 tau/h^6 is <= this:
                                 there the system is nearly pointwise and FP32
                                 sweeps solve it */
-  int    coarse_sweeps;      /* PFC_MIXED: most FP32 sweeps on the coarsest
+  int    coarse_sweeps;      /* mixed paths: most FP32 sweeps on the coarsest
                                 level (stopping earlier once the largest change
                                 is below 1e-6 of the largest value) */
 } pfc_params;
@@ -196,12 +198,12 @@ const char* pfc_last_error(void);
 #define PFC_K_PROLONG           5   /* FP64 correction e = v - w, u += P e */
 #define PFC_K_COARSE_SOLVE      6   /* FP64 coarsest-level solve */
 #define PFC_K_RESIDUAL_NORM     7   /* FP64 residual norm (convergence test) */
-#define PFC_K_DEFECT            8   /* mixed: df residual -> FP32, q */
+#define PFC_K_DEFECT            8   /* mixed: FP64 or df residual -> FP32, q */
 #define PFC_K_LIN_SMOOTH        9   /* mixed: FP32 red-black half-sweeps */
 #define PFC_K_LIN_RESTRICT     10   /* mixed: FP32 residual + restriction */
 #define PFC_K_LIN_PROLONG      11   /* mixed: FP32 d += P d_c */
 #define PFC_K_LIN_COARSE       12   /* mixed: FP32 coarsest-level solve */
-#define PFC_K_CORRECT          13   /* mixed: u += d in double-float */
+#define PFC_K_CORRECT          13   /* mixed: u += d in FP64 or double-float */
 #define PFC_K_COUNT            14
 #define PFC_PROFILE_LEVELS     24
 
@@ -338,18 +340,19 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
                                 const double* d_b, double* out, void* stream);
 
 /* ------------------------------------------------------------------------
- * Primitive operations of the mixed-precision path (PFC_MIXED).  The outer
- * loop is a defect correction in double-float arithmetic: r = S - N(u), then
- * an FP32 multigrid solve of J d = r, with J the Jacobian of N at u (Eqs.
- * 5.4-5.6 differentiated in phi: only the cubic term's coefficient
- * q = f'(phi) + (1-eps)/2, f(a) = (a+b)(a^2+b^2)/4, depends on u), then
- * u += d.  The paper computes in FP64 and has no mixed-precision form; this
- * is a solver strategy whose fixed point is the solution of N(u) = S up to
- * the double-float rounding of the residual.
+ * Primitive operations of the mixed-precision paths.  The outer loop is a
+ * defect correction: r = S - N(u), then an FP32 multigrid solve of J d = r,
+ * with J the Jacobian of N at u (Eqs. 5.4-5.6 differentiated in phi: only the
+ * cubic term's coefficient q = f'(phi) + (1-eps)/2, f(a) = (a+b)(a^2+b^2)/4,
+ * depends on u), then u += d.  PFC_MIXED keeps u, r, q and the energy/mass
+ * sums in FP64; PFC_MIXED_DF keeps them in double-float.  The paper computes
+ * in FP64 and has no mixed-precision form; this is a solver strategy whose
+ * fixed point is the solution of N(u) = S up to the rounding of the outer
+ * residual.
  *
  * A df field ("double-float") is 2*n^3 floats in natural cell order: cell c
  * holds hi at [2c] and lo at [2c+1], value hi + lo with |lo| <= ulp(hi)/2,
- * a 48-bit significand (unit roundoff 2^-48 ~ 3.6e-15).  The mixed path keeps
+ * a 48-bit significand (unit roundoff 2^-48 ~ 3.6e-15).  PFC_MIXED_DF keeps
  * phi, mu, omega, S2 and S3 in this form because GB300 issues FP32 at about
  * 60 times its FP64 rate; pfc_get_* and pfc_set_state convert at the
  * boundary, so callers of the context API see FP64 fields only.
@@ -360,6 +363,21 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
  * (k*n + j)*n + ((i+j+k) & 1)*(n/2) + i/2.  A red-black half-sweep then reads
  * and writes contiguous runs of one colour.  n must be even.
  * --------------------------------------------------------------------- */
+
+/* FP64 residual r = S - N(u) rounded to FP32 into d_r1..3, the coefficient
+ * q = f'(phi) + (1-eps)/2 formed in FP64 and rounded to FP32 into d_q, and
+ * *out = RMS of the FP64 residual (blocking).  d_scratch:
+ * pfc_reduce_scratch_bytes(n) bytes.  n even. */
+int pfc_op_defect(int n, double h, double eps, double tau, const double* d_phi,
+                  const double* d_mu, const double* d_om, const double* d_S1,
+                  const double* d_S2, const double* d_S3, const double* d_b,
+                  float* d_r1, float* d_r2, float* d_r3, float* d_q,
+                  void* d_scratch, double* out, void* stream);
+
+/* u += d (FP64 += FP32) for the three components; d colour-split.  n even. */
+int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
+                   const float* d_d1, const float* d_d2, const float* d_d3,
+                   void* stream);
 
 /* d_y = df(d_x) for `count` values: hi = FP32 rounding of x, lo = FP32
  * rounding of x - hi.  d_y may equal d_x (in-place conversion of 8-byte
@@ -379,7 +397,7 @@ int pfc_op_source_df(int n, double h, double eps, const float* d_b,
  * coefficient q = f'(phi) + (1-eps)/2 in FP32 from the hi parts of phi and b
  * into d_q; *out = RMS of the residual (blocking).  d_scratch:
  * pfc_reduce_scratch_bytes(n) bytes.  n even. */
-int pfc_op_defect(int n, double h, double eps, double tau, const float* d_phi,
+int pfc_op_defect_df(int n, double h, double eps, double tau, const float* d_phi,
                   const float* d_mu, const float* d_om, const float* d_S1,
                   const float* d_S2, const float* d_S3, const float* d_b,
                   float* d_r1, float* d_r2, float* d_r3, float* d_q,
@@ -425,7 +443,7 @@ int pfc_op_lin_prolong(int n, int assign, const float* d_e1, const float* d_e2,
 
 /* u += d for the three components: df fields d_u1..3 plus the colour-split
  * FP32 corrections d_d1..3, in double-float.  n even. */
-int pfc_op_correct(int n, float* d_u1, float* d_u2, float* d_u3,
+int pfc_op_correct_df(int n, float* d_u1, float* d_u2, float* d_u3,
                    const float* d_d1, const float* d_d2, const float* d_d3,
                    void* stream);
 

@@ -15,7 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libpfc.so")
 
 PFC_OK, PFC_EINVAL, PFC_ESIZE, PFC_ENOCONV, PFC_ENAN, PFC_ECUDA = 0, -1, -2, -3, -4, -5
-PFC_FP64, PFC_MIXED = 0, 1
+PFC_FP64, PFC_MIXED, PFC_MIXED_DF = 0, 1, 2
 PFC_NEWTON, PFC_PICARD = 0, 1
 PFC_POLICY_HYBRID, PFC_POLICY_RB = 0, 1
 PFC_SWEEP_RB, PFC_SWEEP_JACOBI = 0, 1
@@ -94,6 +94,8 @@ _SIGS = {
     "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
     "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
+    "pfc_op_defect_df": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
+    "pfc_op_correct_df": (_I, [_I] + [_P] * 6 + [_P]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
     "pfc_op_df_from_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
@@ -365,6 +367,15 @@ def pfc_op_defect(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, scr
     return out.value
 
 
+def pfc_op_defect_df(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, scratch,
+                  stream=None):
+    out = ctypes.c_double()
+    check(lib().pfc_op_defect_df(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1), ptr(S2),
+                              ptr(S3), ptr(b), ptr(r1), ptr(r2), ptr(r3), ptr(q),
+                              ptr(scratch), ctypes.byref(out), stream), "pfc_op_defect_df")
+    return out.value
+
+
 def pfc_op_lin_smooth(n, h, eps, tau, sweeps, zero_init, d1, d2, d3, r1, r2, r3, q,
                       stream=None):
     check(lib().pfc_op_lin_smooth(n, h, eps, tau, sweeps, int(bool(zero_init)), ptr(d1),
@@ -401,3 +412,9 @@ def pfc_op_source_df(n, h, eps, b, c, S2, S3, stream=None):
 def pfc_op_correct(n, u1, u2, u3, d1, d2, d3, stream=None):
     check(lib().pfc_op_correct(n, ptr(u1), ptr(u2), ptr(u3), ptr(d1), ptr(d2), ptr(d3),
                                stream), "pfc_op_correct")
+
+
+
+def pfc_op_correct_df(n, u1, u2, u3, d1, d2, d3, stream=None):
+    check(lib().pfc_op_correct_df(n, ptr(u1), ptr(u2), ptr(u3), ptr(d1), ptr(d2), ptr(d3),
+                               stream), "pfc_op_correct_df")

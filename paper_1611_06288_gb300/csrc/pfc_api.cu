@@ -42,6 +42,10 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline float2* as_df(double* p) { return reinterpret_cast<float2*>(p); }
 inline const float2* as_df(const double* p) { return reinterpret_cast<const float2*>(p); }
 
+// The mixed paths (FP32 correction solves) and the one whose state is df.
+inline bool is_mixed(const pfc_params* p) { return p->precision != PFC_FP64; }
+inline bool df_state(const pfc_params* p) { return p->precision == PFC_MIXED_DF; }
+
 // Level sizes: halve while the size is even and larger than `coarsest`; the
 // mixed path also stops at the first coarse level of at most 16^3 cells whose
 // stiffness 108 tau/h^6 is at most coarse_stiffness (its coarsest solve runs
@@ -56,7 +60,7 @@ int level_sizes(const pfc_params* p, int* sizes) {
     h *= 2.0;
     sizes[nl++] = n;
     const double s = 108.0 * p->dt / (h * h * h * h * h * h);
-    if (p->precision == PFC_MIXED && n <= 16 && s <= p->coarse_stiffness) break;
+    if (p->precision != PFC_FP64 && n <= 16 && s <= p->coarse_stiffness) break;
   }
   return nl;
 }
@@ -67,9 +71,10 @@ int validate(const pfc_params* p) {
   if (!(p->L > 0) || !(p->eps >= 0 && p->eps < 1) || !(p->dt > 0)) return PFC_EINVAL;
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1) return PFC_EINVAL;
   if (!(p->tol > 0) || p->max_cycles < 1 || p->coarsest < 2) return PFC_EINVAL;
-  if (p->precision != PFC_FP64 && p->precision != PFC_MIXED) return PFC_EINVAL;
+  if (p->precision != PFC_FP64 && p->precision != PFC_MIXED && p->precision != PFC_MIXED_DF)
+    return PFC_EINVAL;
   if (p->smoother != PFC_NEWTON && p->smoother != PFC_PICARD) return PFC_EINVAL;
-  if (p->precision == PFC_MIXED && p->inner_cycles < 1) return PFC_EINVAL;
+  if (p->precision != PFC_FP64 && p->inner_cycles < 1) return PFC_EINVAL;
   if (p->policy != PFC_POLICY_HYBRID && p->policy != PFC_POLICY_RB) return PFC_EINVAL;
   if (!(p->jacobi_weight > 0 && p->jacobi_weight <= 1) || p->jacobi_factor < 1 ||
       p->jacobi_factor0 < 1)
@@ -180,7 +185,7 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
     c->dout = dout;
     c->dstate = dstate;
   }
-  if (p->precision == PFC_MIXED) {
+  if (is_mixed(p)) {
     MixedBufs mx;
     mixed_carve(&mx, p->n, nl, sizes, [&](size_t count) { return cv.take<float>(count); });
     if (c) c->mx = mx;
@@ -259,7 +264,7 @@ int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
 int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
                             int use_handle, int first) {
   cudaStream_t st = c->st;
-  if (c->p.precision == PFC_MIXED) {
+  if (df_state(&c->p)) {
     float2* u[3];
     float2* S[3];
     for (int q = 0; q < 3; ++q) {
@@ -267,6 +272,9 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
       S[q] = as_df(lv.S[q]);
     }
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, u, S, as_df(lv.b), c->partials, c->dout, st,
+                                  &c->prof));
+  } else if (is_mixed(&c->p)) {
+    PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
                                   &c->prof));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
@@ -287,7 +295,7 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   const double* cprev = c->ring[c->ic];
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
   Prof* pr = &c->prof;
-  if (c->p.precision == PFC_MIXED) {
+  if (df_state(&c->p)) {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
               launch_source_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),
                                c->st));
@@ -312,9 +320,11 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
 // correction (mixed), then the residual and decision.
 int enqueue_body(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
                  int use_handle) {
-  if (c->p.precision == PFC_MIXED) {
+  if (df_state(&c->p)) {
     float2* u[3] = {as_df(lv.u[0]), as_df(lv.u[1]), as_df(lv.u[2])};
     PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, u, c->st, &c->prof));
+  } else if (is_mixed(&c->p)) {
+    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, lv.u, c->st, &c->prof));
   } else {
     int rc = vcycle64(c, 0, lv);
     if (rc) return rc;
@@ -604,8 +614,8 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ib], any_phi, bytes, cudaMemcpyDefault, c->st));
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ic], any_phi_prev ? any_phi_prev : any_phi, bytes,
                            cudaMemcpyDefault, c->st));
-  if (c->p.precision == PFC_MIXED) {
-    // the mixed path keeps phi as df pairs: convert in place
+  if (df_state(&c->p)) {
+    // PFC_MIXED_DF keeps phi as df pairs: convert in place
     PFC_CUDA(launch_df_from_f64(n3, c->ring[c->ib], as_df(c->ring[c->ib]), c->st));
     PFC_CUDA(launch_df_from_f64(n3, c->ring[c->ic], as_df(c->ring[c->ic]), c->st));
     c->prof.launches += 2;
@@ -623,14 +633,14 @@ int pfc_step(pfc_ctx* c, int nsteps, pfc_step_stats* stats) {
   return PFC_OK;
 }
 
-// Copy a state field out as FP64.  The mixed path's df fields are converted
+// Copy a state field out as FP64.  PFC_MIXED_DF's df fields are converted
 // first into ring[ia], the slot of phi^{k+1}, which holds nothing between
 // steps (each step starts by overwriting it with phi^k).
 static int copy_field(pfc_ctx* c, const double* src, double* dst) {
   if (!c || !dst) return PFC_EINVAL;
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
   const size_t bytes = (size_t)n3 * sizeof(double);
-  if (c->p.precision == PFC_MIXED) {
+  if (df_state(&c->p)) {
     double* stage = c->ring[c->ia];
     PFC_CUDA(launch_df_to_f64(n3, as_df(src), stage, c->st));
     c->prof.launches += 1;
@@ -673,7 +683,7 @@ int pfc_diagnostics(pfc_ctx* c, double out[4]) {
   if (!c || !out) return PFC_EINVAL;
   c->prof.launches += 2;
   return diagnostics(c->p.n, c->p.L / c->p.n, c->p.eps, c->ring[c->ib], c->ring[c->ic],
-                     c->p.precision == PFC_MIXED, c->partials, c->dout, c->hout, c->st, out);
+                     df_state(&c->p), c->partials, c->dout, c->hout, c->st, out);
 }
 
 int pfc_energy(pfc_ctx* c, double* F, double* F_modified) {
@@ -939,7 +949,26 @@ int pfc_op_source_df(int n, double h, double eps, const float* b, const float* c
   return PFC_OK;
 }
 
-int pfc_op_defect(int n, double h, double eps, double tau, const float* phi, const float* mu,
+int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
+                  const double* mu, const double* om, const double* S1, const double* S2,
+                  const double* S3, const double* b, float* r1, float* r2, float* r3,
+                  float* q, void* scratch, double* out, void* stream) {
+  if (n < 2 || (n & 1) || !(h > 0) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 ||
+      !r2 || !r3 || !q || !scratch || !out)
+    return PFC_EINVAL;
+  double* partials = (double*)scratch;
+  double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
+  double hv = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  PFC_CUDA(launch_defect64(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b, r1, r2, r3, q,
+                           partials, dout, st));
+  PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  *out = sqrt(hv / (3.0 * (double)n * n * n));
+  return PFC_OK;
+}
+
+int pfc_op_defect_df(int n, double h, double eps, double tau, const float* phi, const float* mu,
                   const float* om, const float* S1, const float* S2, const float* S3,
                   const float* b, float* r1, float* r2, float* r3, float* q, void* scratch,
                   double* out, void* stream) {
@@ -989,8 +1018,15 @@ int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, cons
   return PFC_OK;
 }
 
-int pfc_op_correct(int n, float* u1, float* u2, float* u3, const float* d1, const float* d2,
-                   const float* d3, void* stream) {
+int pfc_op_correct(int n, double* u1, double* u2, double* u3, const float* d1,
+                   const float* d2, const float* d3, void* stream) {
+  if (n < 2 || (n & 1) || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;
+  PFC_CUDA(launch_correct64(n, u1, u2, u3, d1, d2, d3, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_correct_df(int n, float* u1, float* u2, float* u3, const float* d1,
+                      const float* d2, const float* d3, void* stream) {
   if (n < 2 || (n & 1) || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;
   PFC_CUDA(launch_correct_df(n, reinterpret_cast<float2*>(u1), reinterpret_cast<float2*>(u2),
                              reinterpret_cast<float2*>(u3), d1, d2, d3, (cudaStream_t)stream));

@@ -123,6 +123,40 @@ __device__ __forceinline__ void split_cell(int64_t t, int n, int& p, int& j, int
   p = x - colour * half;
 }
 
+// Defect of the FP64 outer loop (PFC_MIXED): r = S - N(u) in FP64 (Eqs.
+// 5.4-5.6, M = 1) rounded to FP32 into the colour-split r1..r3, the Newton
+// coefficient q = f'(phi) + (1-eps)/2 of the cubic term in FP64 rounded to
+// FP32, and per-block FP64 partial sums of |r|^2.
+__global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restrict__ phi,
+                                                  const double* __restrict__ mu,
+                                                  const double* __restrict__ om,
+                                                  const double* __restrict__ S1,
+                                                  const double* __restrict__ S2,
+                                                  const double* __restrict__ S3,
+                                                  const double* __restrict__ b,
+                                                  float* __restrict__ r1, float* __restrict__ r2,
+                                                  float* __restrict__ r3, float* __restrict__ q,
+                                                  double* partials) {
+  __shared__ double sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  double acc[1] = {0.0};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const Stencil s = stencil_at(i, j, k, n);
+    double x, y, z;
+    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
+    acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
+    const int o = split_index(i, j, k, n);
+    r1[o] = (float)x;
+    r2[o] = (float)y;
+    r3[o] = (float)z;
+    q[o] = (float)(cubic_fp(__ldg(phi + t), __ldg(b + t)) + L.c1);
+  }
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
 // Constants of the double-float operator on one level.
 struct LvlD {
   int n;
@@ -1189,6 +1223,22 @@ constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 K
 
 // u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
 
+// u += d (FP64 += FP32, colour-split d), per component.
+__global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
+                            double* __restrict__ u3, const float* __restrict__ d1,
+                            const float* __restrict__ d2, const float* __restrict__ d3) {
+  pdl_wait();
+  pdl_trigger();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const int o = split_index(i, j, k, n);
+  u1[t] += (double)__ldg(d1 + o);
+  u2[t] += (double)__ldg(d2 + o);
+  u3[t] += (double)__ldg(d3 + o);
+}
+
 // u += d: df state plus the FP32 correction (colour-split), per component.
 __global__ void k_correct_df(int n, float2* __restrict__ u1, float2* __restrict__ u2,
                              float2* __restrict__ u3, const float* __restrict__ d1,
@@ -1377,6 +1427,23 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
 
 }  // namespace
 
+cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
+                            const double* om, const double* S1, const double* S2,
+                            const double* S3, const double* b, float* r1, float* r2, float* r3,
+                            float* q, double* partials, double* out, cudaStream_t st) {
+  const int nb = wave_blocks(k_defect64, (int64_t)L.n * L.n * L.n);
+  k_defect64<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q,
+                                            partials);
+  k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
+                             const float* d2, const float* d3, cudaStream_t st, bool pdl) {
+  const Launch3 g = launch3(n, n, n);
+  return launch_k(pdl, k_correct64, g.grid, g.block, 0, st, n, u1, u2, u3, d1, d2, d3);
+}
+
 cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,
@@ -1476,6 +1543,16 @@ cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const f
   return launch_k(pdl, k_correct_df, g.grid, g.block, 0, st, n, u1, u2, u3, d1, d2, d3);
 }
 
+cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                 double* const S[3], const double* b, double* partials,
+                                 double* dout, cudaStream_t st, Prof* pr) {
+  prof_begin(pr, PFC_K_DEFECT, st);
+  cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
+                                  mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st);
+  prof_end(pr, PFC_K_DEFECT, 0, 2, st);
+  return e;
+}
+
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],
                                  float2* const S[3], const float2* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr) {
@@ -1486,9 +1563,12 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3
   return e;
 }
 
-cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
-                                     const int* sizes, float2* const u[3], cudaStream_t st,
-                                     Prof* pr) {
+namespace {
+
+// q restricted to every level, then p.inner_cycles FP32 V-cycles on J d = r
+// from d = 0 (the part of a correction shared by both outer precisions).
+cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int* sizes,
+                          cudaStream_t st, Prof* pr) {
   Ctx32 c;
   c.mx = &mx;
   c.p = &p;
@@ -1513,6 +1593,28 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
     prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
   }
   for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic) e = vcycle32(c, 0, ic == 0);
+  return e;
+}
+
+}  // namespace
+
+cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
+                                     const int* sizes, double* const u[3], cudaStream_t st,
+                                     Prof* pr) {
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr);
+  if (e == cudaSuccess) {
+    prof_begin(pr, PFC_K_CORRECT, st);
+    e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,
+                         pr == nullptr);
+    prof_end(pr, PFC_K_CORRECT, 0, 1, st);
+  }
+  return e;
+}
+
+cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
+                                     const int* sizes, float2* const u[3], cudaStream_t st,
+                                     Prof* pr) {
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct_df(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,

@@ -1,11 +1,12 @@
-// Mixed-precision time-step solve: a double-float defect correction around
-// an FP32 multigrid solve of the linearised split system.
+// Mixed-precision time-step solves: a defect correction around an FP32
+// multigrid solve of the linearised split system.
 //
-// Outer loop (double-float, see pfc_df.cuh): phi, mu, omega, S2 and S3 are
-// held as (hi, lo) FP32 pairs with a 48-bit significand; r = S - N(u) with
-// the operator of Eqs. 5.4-5.6, the RMS of r checked against the tolerance,
-// q = f'(phi) + (1-eps)/2 (the Jacobian of the cubic term of Eq. 5.2 at the
-// current phi) formed in FP32.
+// Outer loop: r = S - N(u) with the operator of Eqs. 5.4-5.6, the RMS of r
+// checked against the tolerance, and q = f'(phi) + (1-eps)/2 (the Jacobian of
+// the cubic term of Eq. 5.2 at the current phi).  PFC_MIXED keeps phi, mu,
+// omega, S2, S3, r, q and the sums in FP64; PFC_MIXED_DF keeps the state in
+// double-float (hi, lo) FP32 pairs with a 48-bit significand (pfc_df.cuh) and
+// forms q in FP32.
 // Inner solve (FP32): J d = r with
 //   J1 d = d_phi - tau Lap d_mu
 //   J2 d = d_mu - q d_phi - Lap d_om
@@ -13,10 +14,9 @@
 // by V-cycles of red-black Gauss-Seidel or damped collective Jacobi with the
 // same pointwise 3x3 system as the FP64 smoother (q frozen), 8-cell
 // restriction of the residual and of q, and trilinear prolongation of the
-// correction.  Then u += d in double-float.
-// The fixed point is the solution of N(u) = S to the df rounding of the
-// residual (a few 2^-48 of its operands): the FP32 part only computes
-// corrections.
+// correction.  Then u += d in the outer precision.
+// The fixed point is the solution of N(u) = S to the rounding of the outer
+// residual: the FP32 part only computes corrections.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,6 +49,12 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
   }
 }
 
+// Defect r = S - N(u) of the FP64 state (PFC_MIXED) -> FP32 r and q on
+// level 0, and the FP64 sum of |r|^2 at dout[0] (two launches).
+cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                 double* const S[3], const double* b, double* partials,
+                                 double* dout, cudaStream_t st, Prof* pr);
+
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],
@@ -56,7 +62,11 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3
                                  double* dout, cudaStream_t st, Prof* pr);
 
 // One defect correction after mixed_enqueue_defect: q restricted to every
-// level, p.inner_cycles FP32 V-cycles on J d = r from d = 0, then u += d.
+// level, p.inner_cycles FP32 V-cycles on J d = r from d = 0, then u += d in
+// FP64 (PFC_MIXED) or double-float (PFC_MIXED_DF).
+cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
+                                     const int* sizes, double* const u[3], cudaStream_t st,
+                                     Prof* pr);
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr);
@@ -76,6 +86,13 @@ cudaError_t launch_df_from_f64(int64_t count, const double* x, float2* y, cudaSt
 cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStream_t st);
 
 // Primitive launches of the FP32 kernels (for the C ABI checks).
+cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
+                            const double* om, const double* S1, const double* S2,
+                            const double* S3, const double* b, float* r1, float* r2, float* r3,
+                            float* q, double* partials, double* out, cudaStream_t st);
+cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
+                             const float* d2, const float* d3, cudaStream_t st,
+                             bool pdl = true);
 cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,

@@ -11,7 +11,7 @@ import torch
 
 from . import binding as B
 
-_PREC = {"fp64": B.PFC_FP64, "mixed": B.PFC_MIXED}
+_PREC = {"fp64": B.PFC_FP64, "mixed": B.PFC_MIXED, "mixed_df": B.PFC_MIXED_DF}
 _LIN = {"newton": B.PFC_NEWTON, "picard": B.PFC_PICARD}
 
 

@@ -229,6 +229,34 @@ def test_source_df(n):
 
 @pytest.mark.parametrize("n", [2, 4, 12, 32])
 def test_defect_and_correct(n):
+    """FP64 outer loop (PFC_MIXED): FP64 residual and Newton coefficient
+    rounded to FP32, FP64 update."""
+    h, b, c, u = case(n)
+    S = O.source_S(b, c, h, prm())
+    scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    r = [empty(n, torch.float32) for _ in range(3)]
+    q = empty(n, torch.float32)
+    rms = B.pfc_op_defect(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S], dev(b),
+                          *r, q, scratch)
+    ref = O.residual(S, u, b, h, prm())
+    assert rms == pytest.approx(O.rms(ref), rel=1e-12)
+    for g, x in zip(r, ref):
+        # FP64 residual rounded to FP32: half an FP32 ulp (colour-split layout)
+        assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
+    # q formed in FP64 and rounded once: half an FP32 ulp
+    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 2 ** -23,
+                       "q32")
+    # u += d: one FP64 rounding of the same sum on both sides -> bit-exact
+    rng = np.random.default_rng(5)
+    d = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    du = [dev(x) for x in u]
+    B.pfc_op_correct(n, *du, *[dev(to_split(x), torch.float32) for x in d])
+    for g, x, y in zip(du, u, d):
+        np.testing.assert_array_equal(host(g), x + y.astype(np.float64))
+
+
+@pytest.mark.parametrize("n", [2, 4, 12, 32])
+def test_defect_and_correct_df(n):
     h, b, c, u = case(n)
     # the oracle sees exactly the values the df fields hold
     b = from_df(to_df(b))
@@ -237,7 +265,7 @@ def test_defect_and_correct(n):
     scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
     r = [empty(n, torch.float32) for _ in range(3)]
     q = empty(n, torch.float32)
-    rms = B.pfc_op_defect(n, h, EPS, TAU, *[dev_df(x) for x in u], *[dev_df(s) for s in S],
+    rms = B.pfc_op_defect_df(n, h, EPS, TAU, *[dev_df(x) for x in u], *[dev_df(s) for s in S],
                           dev_df(b), *r, q, scratch)
     ref = O.residual(S, u, b, h, prm())
     # |r|^2 summed in FP32 within a thread block: relative error ~1e-6
@@ -252,13 +280,13 @@ def test_defect_and_correct(n):
     rng = np.random.default_rng(5)
     d = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
     du = [dev_df(x) for x in u]
-    B.pfc_op_correct(n, *du, *[dev(to_split(x), torch.float32) for x in d])
+    B.pfc_op_correct_df(n, *du, *[dev(to_split(x), torch.float32) for x in d])
     for g, x, y in zip(du, u, d):
         exact = x + y.astype(np.float64)
         err = np.abs(host_df(g) - exact)
         assert np.all(err <= 4 * 2.0 ** -48 * (np.abs(x) + np.abs(exact)) + 1e-300)
     with pytest.raises(B.PFCError):
-        B.pfc_op_correct(3, *du, *r)                  # n must be even
+        B.pfc_op_correct_df(3, *du, *r)                  # n must be even
 
 
 @pytest.mark.parametrize("n", [4, 12, 32])

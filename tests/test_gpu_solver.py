@@ -34,7 +34,7 @@ def oracle_run(phi0, steps, h, eps, dt, lin, tol=1e-12):
     return traj
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
 @pytest.mark.parametrize("smoother", ["newton", "picard"])
 @pytest.mark.parametrize("graphs", [True, False])
 def test_random16_ten_steps(precision, smoother, graphs):
@@ -62,9 +62,10 @@ def test_random16_ten_steps(precision, smoother, graphs):
     assert s.step_index == wl.steps
 
 
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
 @pytest.mark.parametrize("nu", [(0, 1), (1, 0), (0, 2), (1, 2)])
 @pytest.mark.parametrize("graphs", [True, False])
-def test_mixed_cycle_shapes(nu, graphs):
+def test_mixed_cycle_shapes(nu, graphs, precision):
     """Mixed path with V(nu1, nu2) inner cycles, including no pre-smoothing
     (the zero-start restriction and assigning prolongation) and no
     post-smoothing: the converged steps match the oracle."""
@@ -72,7 +73,7 @@ def test_mixed_cycle_shapes(nu, graphs):
     rng = np.random.default_rng(32)
     phi0 = 0.1 + 0.1 * rng.uniform(-1, 1, (n,) * 3)
     ref = oracle_run(phi0, 2, L / n, 0.2, 0.05, "newton")
-    s = PFCSolver(n, L, 0.2, 0.05, phi0, tol=1e-12, precision="mixed", nu1=nu[0], nu2=nu[1],
+    s = PFCSolver(n, L, 0.2, 0.05, phi0, tol=1e-12, precision=precision, nu1=nu[0], nu2=nu[1],
                   inner_cycles=2, coarse_sweeps=2, max_cycles=80)
     s.use_graphs(graphs)
     for k in range(2):
@@ -89,7 +90,7 @@ def test_uneven_sizes_and_level_counts(n, coarsest):
     rng = np.random.default_rng(n)
     phi0 = 0.1 + 0.1 * rng.uniform(-1, 1, (n,) * 3)
     ref = oracle_run(phi0, 2, L / n, 0.2, 0.05, "newton")
-    for precision in ("fp64", "mixed"):
+    for precision in ("fp64", "mixed", "mixed_df"):
         s = PFCSolver(n, L, 0.2, 0.05, phi0, tol=1e-12, coarsest=coarsest,
                       precision=precision, max_cycles=200)
         s.step(2)
@@ -142,7 +143,7 @@ def test_energy_law_and_mass_on_gpu_trajectory():
         c, b = b, a
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp64"])
 def test_full_size_128_residual_by_oracle(precision):
     """128^3 smooth-mode workload (L = 32, eps = 0.025, dt = 0.0125, tol 1e-9)
     in the benchmark's configuration (the workload's mixed-path settings): after two steps the oracle evaluates
@@ -150,7 +151,7 @@ def test_full_size_128_residual_by_oracle(precision):
     tolerance; mass is conserved."""
     wl = W.smooth_sweep(128)
     phi0 = wl.phi0()
-    kw = wl.mixed() if precision == "mixed" else {}
+    kw = wl.mixed() if precision != "fp64" else {}
     s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision, **kw)
     s.step(1)
     b = phi0
@@ -163,13 +164,14 @@ def test_full_size_128_residual_by_oracle(precision):
     assert O.mass(a, wl.h) == pytest.approx(O.mass(phi0, wl.h), abs=1e-9 * wl.L ** 3)
 
 
-def test_full_size_256_polycrystal_one_step():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_full_size_256_polycrystal_one_step(precision):
     """256^3 polycrystal workload (h = pi/4, eps = 0.25, dt = 0.1), mixed
     precision: the oracle's FP64 residual of the GPU step is below 1e-9 and
     the energy reported by the GPU equals the oracle's F_h of the same field."""
     wl = W.polycrystal(256)
     phi0 = wl.phi0()
-    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision="mixed",
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision,
                   **wl.mixed())
     st = s.step(1)
     assert st.residual <= wl.tol
@@ -181,14 +183,15 @@ def test_full_size_256_polycrystal_one_step():
     assert F == pytest.approx(O.energy(a, wl.h, wl.eps), rel=1e-11)
 
 
-def test_graph_and_host_loops_agree_at_64():
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
+def test_graph_and_host_loops_agree_at_64(precision):
     """64^3 smooth mode (h = 0.5, tau = 0.0125, hybrid levels): the graph
     loop and the host loop take the same number of cycles and give the same
     fields to rounding."""
     wl = W.smooth_sweep(64)
     out = []
     for graphs in (True, False):
-        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-10, precision="mixed",
+        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=1e-10, precision=precision,
                       inner_cycles=2)
         s.use_graphs(graphs)
         cyc = [s.step(1).cycles_last for _ in range(3)]
