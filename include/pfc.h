@@ -92,7 +92,20 @@ typedef struct pfc_params {
   int    coarse_sweeps;      /* mixed paths: most FP32 sweeps on the coarsest
                                 level (stopping earlier once the largest change
                                 is below 1e-6 of the largest value) */
+  int    guess;              /* initial iterate of a step: PFC_GUESS_PREVIOUS
+                                or PFC_GUESS_EXTRAPOLATE */
 } pfc_params;
+
+#define PFC_GUESS_PREVIOUS    0  /* phi^{k+1} := phi^k; mu, omega from the last
+                                    step */
+#define PFC_GUESS_EXTRAPOLATE 1  /* phi^{k+1} := 2 phi^k - phi^{k-1} (second
+                                    order in tau), then the omega and mu that
+                                    satisfy rows 3 and 2 of N(u) = S exactly:
+                                    omega = Lap(phi + phi^k)/2, mu = S2 +
+                                    f(phi, phi^k) + (1-eps)/2 phi + Lap omega.
+                                    The step converges to the same solution
+                                    (Prop. 3.1) from a residual O(tau^2) in
+                                    the first row only. */
 
 typedef struct pfc_step_stats {
   int    steps;        /* steps completed by the call */
@@ -105,7 +118,8 @@ typedef struct pfc_step_stats {
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
- * coarse_stiffness 0.05, coarse_sweeps 4.  n, L, eps, dt are set to 0.
+ * coarse_stiffness 0.05, coarse_sweeps 4, guess PFC_GUESS_PREVIOUS.  n, L,
+ * eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the
@@ -379,6 +393,14 @@ int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
                    const float* d_d1, const float* d_d2, const float* d_d3,
                    void* stream);
 
+/* The PFC_GUESS_EXTRAPOLATE initial iterate from b = phi^k, c = phi^{k-1}:
+ * S2, S3 of Eqs. 5.9-5.10 into d_S2, d_S3, and phi_g = 2b - c,
+ * omega_g = (3 Lap b - Lap c)/2, mu_g = S2 + f(phi_g, b) + (1-eps)/2 phi_g
+ * + Lap omega_g into d_phi, d_om, d_mu (two launches), all FP64. */
+int pfc_op_guess(int n, double h, double eps, const double* d_b, const double* d_c,
+                 double* d_S2, double* d_S3, double* d_phi, double* d_mu,
+                 double* d_om, void* stream);
+
 /* d_y = df(d_x) for `count` values: hi = FP32 rounding of x, lo = FP32
  * rounding of x - hi.  d_y may equal d_x (in-place conversion of 8-byte
  * slots); otherwise the arrays must not overlap. */
@@ -391,6 +413,11 @@ int pfc_op_df_to_f64(long long count, const float* d_y, double* d_x, void* strea
  * written as df fields, computed in double-float (pfc_op_source in FP64). */
 int pfc_op_source_df(int n, double h, double eps, const float* d_b,
                      const float* d_c, float* d_S2, float* d_S3, void* stream);
+
+/* pfc_op_guess on df fields (all arithmetic in double-float). */
+int pfc_op_guess_df(int n, double h, double eps, const float* d_b, const float* d_c,
+                    float* d_S2, float* d_S3, float* d_phi, float* d_mu,
+                    float* d_om, void* stream);
 
 /* Residual r = S - N(u) of the df fields (phi, mu, om), sources S1..S3 and
  * b, evaluated in double-float and rounded to FP32 into d_r1..3; the

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(PKG, "libpfc.so")
 
 PFC_OK, PFC_EINVAL, PFC_ESIZE, PFC_ENOCONV, PFC_ENAN, PFC_ECUDA = 0, -1, -2, -3, -4, -5
 PFC_FP64, PFC_MIXED, PFC_MIXED_DF = 0, 1, 2
+PFC_GUESS_PREVIOUS, PFC_GUESS_EXTRAPOLATE = 0, 1
 PFC_NEWTON, PFC_PICARD = 0, 1
 PFC_POLICY_HYBRID, PFC_POLICY_RB = 0, 1
 PFC_SWEEP_RB, PFC_SWEEP_JACOBI = 0, 1
@@ -40,7 +41,7 @@ class pfc_params(ctypes.Structure):
                 ("jacobi_factor", ctypes.c_int), ("jacobi_factor0", ctypes.c_int),
                 ("stiff_hi", ctypes.c_double),
                 ("stiff_lo", ctypes.c_double), ("coarse_stiffness", ctypes.c_double),
-                ("coarse_sweeps", ctypes.c_int)]
+                ("coarse_sweeps", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
 class pfc_step_stats(ctypes.Structure):
@@ -98,6 +99,8 @@ _SIGS = {
     "pfc_op_correct_df": (_I, [_I] + [_P] * 6 + [_P]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
+    "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
+    "pfc_op_guess_df": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_df_from_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_df_to_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_source_df": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
@@ -394,6 +397,16 @@ def pfc_op_lin_residual_restrict(n, h, eps, tau, zero_init, d1, d2, d3, r1, r2, 
 def pfc_op_lin_prolong(n, assign, e1, e2, e3, d1, d2, d3, stream=None):
     check(lib().pfc_op_lin_prolong(n, int(bool(assign)), ptr(e1), ptr(e2), ptr(e3), ptr(d1),
                                    ptr(d2), ptr(d3), stream), "pfc_op_lin_prolong")
+
+
+def pfc_op_guess(n, h, eps, b, c, S2, S3, phi, mu, om, stream=None):
+    check(lib().pfc_op_guess(n, h, eps, ptr(b), ptr(c), ptr(S2), ptr(S3), ptr(phi), ptr(mu),
+                             ptr(om), stream), "pfc_op_guess")
+
+
+def pfc_op_guess_df(n, h, eps, b, c, S2, S3, phi, mu, om, stream=None):
+    check(lib().pfc_op_guess_df(n, h, eps, ptr(b), ptr(c), ptr(S2), ptr(S3), ptr(phi), ptr(mu),
+                                ptr(om), stream), "pfc_op_guess_df")
 
 
 def pfc_op_df_from_f64(count, x, y, stream=None):

@@ -81,6 +81,7 @@ int validate(const pfc_params* p) {
     return PFC_EINVAL;
   if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
   if (!(p->coarse_stiffness >= 0) || p->coarse_sweeps < 1) return PFC_EINVAL;
+  if (p->guess != PFC_GUESS_PREVIOUS && p->guess != PFC_GUESS_EXTRAPOLATE) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -295,7 +296,16 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   const double* cprev = c->ring[c->ic];
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
   Prof* pr = &c->prof;
-  if (df_state(&c->p)) {
+  const bool extrapolate = c->p.guess == PFC_GUESS_EXTRAPOLATE;
+  if (extrapolate && df_state(&c->p)) {
+    PFC_TIMED(pr, PFC_K_SOURCE, 0, 2, c->st,
+              launch_guess_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),
+                              as_df(lv.u[0]), as_df(lv.u[1]), as_df(lv.u[2]), c->st));
+  } else if (extrapolate) {
+    PFC_TIMED(pr, PFC_K_SOURCE, 0, 2, c->st,
+              launch_guess(lv.L, lv.b, cprev, c->S2, c->S3, lv.u[0], lv.u[1], lv.u[2],
+                           c->st));
+  } else if (df_state(&c->p)) {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
               launch_source_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),
                                c->st));
@@ -311,8 +321,9 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
       fine = c->lev[l].b;
     }
   }
-  PFC_CUDA(cudaMemcpyAsync(lv.u[0], lv.b, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
-                           c->st));
+  if (!extrapolate)
+    PFC_CUDA(cudaMemcpyAsync(lv.u[0], lv.b, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                             c->st));
   return enqueue_residual_decide(c, lv, h, use_handle, 1);
 }
 
@@ -530,6 +541,7 @@ void pfc_default_params(pfc_params* p) {
   p->stiff_lo = 0.25;
   p->coarse_stiffness = 0.05;
   p->coarse_sweeps = 4;
+  p->guess = PFC_GUESS_PREVIOUS;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {
@@ -924,6 +936,24 @@ int pfc_op_residual_norm(int n, double h, double eps, double tau, const double* 
   PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
   PFC_CUDA(cudaStreamSynchronize(st));
   *out = sqrt(hv / (3.0 * (double)n * n * n));
+  return PFC_OK;
+}
+
+int pfc_op_guess(int n, double h, double eps, const double* b, const double* c, double* S2,
+                 double* S3, double* phi, double* mu, double* om, void* stream) {
+  if (n < 1 || !(h > 0) || !b || !c || !S2 || !S3 || !phi || !mu || !om) return PFC_EINVAL;
+  PFC_CUDA(launch_guess(make_lvl(n, h, eps, 1.0), b, c, S2, S3, phi, mu, om,
+                        (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_guess_df(int n, double h, double eps, const float* b, const float* c, float* S2,
+                    float* S3, float* phi, float* mu, float* om, void* stream) {
+  if (n < 1 || !(h > 0) || !b || !c || !S2 || !S3 || !phi || !mu || !om) return PFC_EINVAL;
+  auto D = [](float* p) { return reinterpret_cast<float2*>(p); };
+  PFC_CUDA(launch_guess_df(make_lvl(n, h, eps, 1.0), reinterpret_cast<const float2*>(b),
+                           reinterpret_cast<const float2*>(c), D(S2), D(S3), D(phi), D(mu),
+                           D(om), (cudaStream_t)stream));
   return PFC_OK;
 }
 

@@ -39,6 +39,44 @@ __global__ void k_source(Lvl L, const double* __restrict__ b, const double* __re
   S3[s.c] = 0.5 * lb;
 }
 
+// S2, S3 as k_source, plus the first part of the extrapolated initial
+// iterate: phi_g = 2 b - c and omega_g = (3 Lap b - Lap c)/2 = Lap(phi_g + b)/2,
+// which satisfies row 3 of N(u) = S (Eq. 5.6) for phi_g.
+__global__ void k_source_guess(Lvl L, const double* __restrict__ b,
+                               const double* __restrict__ c, double* __restrict__ S2,
+                               double* __restrict__ S3, double* __restrict__ phig,
+                               double* __restrict__ omg) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  const double bb = __ldg(b + s.c), cc = __ldg(c + s.c);
+  const double lb = L.g * fma(-6.0, bb, nbsum(b, s));
+  const double lc = L.g * fma(-6.0, cc, nbsum(c, s));
+  S2[s.c] = fma(3.0, lb, fma(L.c1, bb, -lc));
+  S3[s.c] = 0.5 * lb;
+  phig[s.c] = fma(2.0, bb, -cc);
+  omg[s.c] = 0.5 * fma(3.0, lb, -lc);
+}
+
+// mu_g = S2 + f(phi_g, b) + (1-eps)/2 phi_g + Lap omega_g: row 2 of
+// N(u) = S (Eq. 5.5) solved for mu at the extrapolated phi_g, omega_g.
+__global__ void k_mu_guess(Lvl L, const double* __restrict__ phig,
+                           const double* __restrict__ omg, const double* __restrict__ b,
+                           const double* __restrict__ S2, double* __restrict__ mug) {
+  const int n = L.n;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  const double p = __ldg(phig + s.c);
+  const double lw = fma(-6.0, __ldg(omg + s.c), nbsum(omg, s));
+  mug[s.c] = fma(L.g, lw, fma(L.c1, p, __ldg(S2 + s.c) + cubic_f(p, __ldg(b + s.c))));
+}
+
 // ---------------------------------------------------------------------------
 // a2/a7: one colour of the red-black nonlinear Gauss-Seidel sweep (Section 5).
 // Thread t owns the t-th cell of the colour: i = 2p + ((j+k+colour) & 1).
@@ -440,6 +478,14 @@ inline int reduce_blocks(int64_t cells) {
 }
 
 }  // namespace
+
+cudaError_t launch_guess(const Lvl& L, const double* b, const double* c, double* S2,
+                         double* S3, double* phig, double* mug, double* omg, cudaStream_t st) {
+  const int64_t cells = (int64_t)L.n * L.n * L.n;
+  k_source_guess<<<grid_for(cells), kThreads, 0, st>>>(L, b, c, S2, S3, phig, omg);
+  k_mu_guess<<<grid_for(cells), kThreads, 0, st>>>(L, phig, omg, b, S2, mug);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double* S2,
                           double* S3, cudaStream_t st) {

@@ -53,6 +53,10 @@ void prof_end(Prof* pr, int cls, int level, int nlaunch, cudaStream_t st);
 void prof_harvest(Prof* pr);
 
 // FP64 kernels (pfc_fp64.cu).  All enqueue on `st` and return the launch error.
+// S2, S3 and the extrapolated initial iterate (phi_g, mu_g, omega_g) of a
+// step from b = phi^k, c = phi^{k-1} (two launches).
+cudaError_t launch_guess(const Lvl& L, const double* b, const double* c, double* S2,
+                         double* S3, double* phig, double* mug, double* omg, cudaStream_t st);
 cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double* S2,
                           double* S3, cudaStream_t st);
 cudaError_t launch_smooth(const Lvl& L, int lin, int sweeps, double* phi, double* mu,

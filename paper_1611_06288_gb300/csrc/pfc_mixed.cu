@@ -416,6 +416,50 @@ __global__ void k_reduce_df6(const float2* __restrict__ partials, int nparts, do
   }
 }
 
+// k_source_df plus phi_g = 2 b - c and omega_g = (3 Lap b - Lap c)/2 of the
+// extrapolated initial iterate, in double-float.
+__global__ void k_source_guess_df(LvlD L, const float2* __restrict__ b,
+                                  const float2* __restrict__ c, float2* __restrict__ S2,
+                                  float2* __restrict__ S3, float2* __restrict__ phig,
+                                  float2* __restrict__ omg) {
+  const int n = L.n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const Nb6 s = nb6_at(t, i, j, k, n);
+  const df bb = df_ld(b, t), cc = df_ld(c, t);
+  const df lb = df_mul(L.g, df_lap(b, s, bb));
+  const df lc = df_mul(L.g, df_lap(c, s, cc));
+  df_st(S2, t, df_add(df_mul_f(lb, 3.f), df_sub(df_mul(L.c1, bb), lc)));
+  df_st(S3, t, df_scale2(lb, 0.5f));
+  df_st(phig, t, df_sub(df_scale2(bb, 2.f), cc));
+  df_st(omg, t, df_scale2(df_sub(df_mul_f(lb, 3.f), lc), 0.5f));
+}
+
+// mu_g = S2 + f(phi_g, b) + (1-eps)/2 phi_g + Lap omega_g in double-float.
+__global__ void k_mu_guess_df(LvlD L, const float2* __restrict__ phig,
+                              const float2* __restrict__ omg, const float2* __restrict__ b,
+                              const float2* __restrict__ S2, float2* __restrict__ mug) {
+  const int n = L.n;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const Nb6 s = nb6_at(t, i, j, k, n);
+  const df p = df_ld(phig, t);
+  dacc m = dacc_of(df_ld(S2, t));
+  const dacc f = dacc_cubic(p, df_ld(b, t));
+  dacc_add(m, f.hi, f.lo);
+  const dacc cp = dacc_mul(L.c1, dacc_of(p));
+  dacc_add(m, cp.hi, cp.lo);
+  const dacc gl = dacc_mul(L.g, dacc_lap(omg, s, df_ld(omg, t)));
+  dacc_add(m, gl.hi, gl.lo);
+  df r;
+  two_sum(m.hi, m.lo, r.hi, r.lo);
+  df_st(mug, t, r);
+}
+
 // FP64 <-> df conversions of whole fields; in place allowed (each thread
 // reads its 8 bytes before writing them).
 __global__ void k_df_from_f64(int64_t count, const double* x, float2* y) {
@@ -1468,6 +1512,16 @@ cudaError_t launch_diagnostics_df(int n, const float2* a, const float2* b, doubl
   float2* parts = reinterpret_cast<float2*>(partials);
   k_diagnostics_df<<<nb, kReduceThreads, 0, st>>>(n, a, b, parts);
   k_reduce_df6<<<1, kReduceThreads, 0, st>>>(parts, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_guess_df(const Lvl& L, const float2* b, const float2* c, float2* S2,
+                            float2* S3, float2* phig, float2* mug, float2* omg,
+                            cudaStream_t st) {
+  const Launch3 g = launch3(L.n, L.n, L.n);
+  const LvlD D = to_df(L);
+  k_source_guess_df<<<g.grid, g.block, 0, st>>>(D, b, c, S2, S3, phig, omg);
+  k_mu_guess_df<<<g.grid, g.block, 0, st>>>(D, phig, omg, b, S2, mug);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,11 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
 cudaError_t launch_source_df(const Lvl& L, const float2* b, const float2* c, float2* S2,
                              float2* S3, cudaStream_t st);
 
+// launch_guess on df fields (double-float arithmetic).
+cudaError_t launch_guess_df(const Lvl& L, const float2* b, const float2* c, float2* S2,
+                            float2* S3, float2* phig, float2* mug, float2* omg,
+                            cudaStream_t st);
+
 // The raw sums of launch_diagnostics (out[0..5]) from df fields a = phi^k,
 // b = phi^{k-1}, in double-float; partials: kReduceBlocks * 6 float2 slots
 // (the FP64 path's partial-sum buffer).

@@ -19,7 +19,8 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
                 precision="fp64", smoother="newton", coarsest=2,
                 inner_cycles=1, policy="hybrid", jacobi_weight=0.7, jacobi_factor=4,
                 jacobi_factor0=2, stiff_hi=1000.0, stiff_lo=0.25,
-                coarse_stiffness=0.05, coarse_sweeps=4) -> B.pfc_params:
+                coarse_stiffness=0.05, coarse_sweeps=4,
+                guess="previous") -> B.pfc_params:
     p = B.pfc_default_params()
     p.n, p.L, p.eps, p.dt = int(n), float(L), float(eps), float(dt)
     p.tol, p.nu1, p.nu2, p.max_cycles = float(tol), int(nu1), int(nu2), int(max_cycles)
@@ -34,6 +35,7 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
     p.stiff_hi, p.stiff_lo = float(stiff_hi), float(stiff_lo)
     p.coarse_stiffness = float(coarse_stiffness)
     p.coarse_sweeps = int(coarse_sweeps)
+    p.guess = {"previous": B.PFC_GUESS_PREVIOUS, "extrapolate": B.PFC_GUESS_EXTRAPOLATE}[guess]
     return p
 
 

@@ -193,6 +193,42 @@ def test_diagnostics_df(n):
     assert out[3] == pytest.approx(O.grad_norm2_sq(a, h), rel=1e-12)
 
 
+def guess_ref(b, c, h):
+    """The extrapolated initial iterate written out from its definition:
+    phi = 2b - c, omega = Lap(phi + b)/2 (row 3), mu from row 2."""
+    S = O.source_S(b, c, h, prm())
+    phi = 2 * b - c
+    om = 0.5 * O.lap(phi + b, h)
+    mu = S[1] + O.cubic_f(phi, b) + 0.5 * (1 - EPS) * phi + O.lap(om, h)
+    return S, phi, mu, om
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_guess(n):
+    h, b, c, _ = case(n)
+    S, phi, mu, om = guess_ref(b, c, h)
+    out = [empty(n) for _ in range(5)]
+    B.pfc_op_guess(n, h, EPS, dev(b), dev(c), *out)
+    for g, x, name in zip(out, [S[1], S[2], phi, mu, om], ("S2", "S3", "phi", "mu", "om")):
+        assert_close_field(host(g), x, FP64_RTOL, name)
+    # the iterate satisfies rows 2 and 3 of N(u) = S: only row 1 is left
+    r = O.residual(S, [host(out[2]), host(out[3]), host(out[4])], b, h, prm())
+    scale = max(float(np.abs(host(out[3])).max()), 1.0)
+    assert float(np.abs(r[1]).max()) <= 1e-12 * scale
+    assert float(np.abs(r[2]).max()) <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_guess_df(n):
+    h, b, c, _ = case(n)
+    b, c = from_df(to_df(b)), from_df(to_df(c))
+    S, phi, mu, om = guess_ref(b, c, h)
+    out = [torch.empty((n, n, n, 2), dtype=torch.float32, device="cuda") for _ in range(5)]
+    B.pfc_op_guess_df(n, h, EPS, dev_df(b), dev_df(c), *out)
+    for g, x, name in zip(out, [S[1], S[2], phi, mu, om], ("S2", "S3", "phi", "mu", "om")):
+        assert_close_field(host_df(g), x, DF_RTOL, name)
+
+
 @pytest.mark.parametrize("n", [1, 2, 12, 32])
 def test_df_conversions(n):
     """FP64 -> (hi, lo) pairs and back, out of place and in place: bit-exact

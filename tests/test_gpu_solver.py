@@ -82,6 +82,36 @@ def test_mixed_cycle_shapes(nu, graphs, precision):
         assert rel_l2(host(s.phi()), ref[k][0]) <= PARITY_RTOL
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_df"])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_extrapolated_guess(precision, graphs):
+    """guess = extrapolate starts each step from 2 phi^k - phi^{k-1} with
+    omega and mu from rows 3 and 2: the same converged trajectory as the
+    oracle (which starts from phi^k), and on a smooth trajectory fewer
+    corrections than the plain start."""
+    wl = W.random16()
+    phi0 = wl.phi0()
+    ref = oracle_run(phi0, 5, wl.h, wl.eps, wl.dt, "newton")
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-12, precision=precision,
+                  guess="extrapolate", max_cycles=60)
+    s.use_graphs(graphs)
+    for k in range(5):
+        st = s.step(1)
+        assert st.residual <= 1e-12
+        assert rel_l2(host(s.phi()), ref[k][0]) <= PARITY_RTOL
+        assert rel_l2(host(s.mu()), ref[k][1]) <= PARITY_RTOL
+    wl = W.smooth_sweep(32)
+    kw = wl.mixed() if precision != "fp64" else {}
+    cyc = {}
+    for guess in ("previous", "extrapolate"):
+        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=wl.tol, precision=precision,
+                      guess=guess, **kw)
+        s.use_graphs(graphs)
+        s.step(2)
+        cyc[guess] = s.step(4).cycles_total
+    assert cyc["extrapolate"] < cyc["previous"], cyc
+
+
 @pytest.mark.parametrize("n,coarsest", [(4, 2), (12, 6), (20, 10), (24, 6)])
 def test_uneven_sizes_and_level_counts(n, coarsest):
     """Grids that are not powers of two and the smallest grid, against the
