@@ -393,6 +393,14 @@ int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
                    const float* d_d1, const float* d_d2, const float* d_d3,
                    void* stream);
 
+/* The conversions of the FP64 outer loop, done on the integer pipe from the
+ * IEEE 754 bit layouts (GB300 converts FP64<->FP32 only at its FP64 rate):
+ * d_y[i] = d_x[i] rounded to FP32, to nearest with ties to even (overflow
+ * to infinity, results below the normal range, zeros, infinities and NaNs as
+ * the hardware conversion), and the exact widening of FP32 to FP64. */
+int pfc_op_round_f32(long long count, const double* d_x, float* d_y, void* stream);
+int pfc_op_widen_f64(long long count, const float* d_x, double* d_y, void* stream);
+
 /* The PFC_GUESS_EXTRAPOLATE initial iterate from b = phi^k, c = phi^{k-1}:
  * S2, S3 of Eqs. 5.9-5.10 into d_S2, d_S3, and phi_g = 2b - c,
  * omega_g = (3 Lap b - Lap c)/2, mu_g = S2 + f(phi_g, b) + (1-eps)/2 phi_g

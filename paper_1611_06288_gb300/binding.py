@@ -101,6 +101,8 @@ _SIGS = {
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
     "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_guess_df": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
+    "pfc_op_round_f32": (_I, [ctypes.c_longlong, _P, _P, _P]),
+    "pfc_op_widen_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_df_from_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_df_to_f64": (_I, [ctypes.c_longlong, _P, _P, _P]),
     "pfc_op_source_df": (_I, [_I, _D, _D, _P, _P, _P, _P, _P]),
@@ -407,6 +409,14 @@ def pfc_op_guess(n, h, eps, b, c, S2, S3, phi, mu, om, stream=None):
 def pfc_op_guess_df(n, h, eps, b, c, S2, S3, phi, mu, om, stream=None):
     check(lib().pfc_op_guess_df(n, h, eps, ptr(b), ptr(c), ptr(S2), ptr(S3), ptr(phi), ptr(mu),
                                 ptr(om), stream), "pfc_op_guess_df")
+
+
+def pfc_op_round_f32(count, x, y, stream=None):
+    check(lib().pfc_op_round_f32(count, ptr(x), ptr(y), stream), "pfc_op_round_f32")
+
+
+def pfc_op_widen_f64(count, x, y, stream=None):
+    check(lib().pfc_op_widen_f64(count, ptr(x), ptr(y), stream), "pfc_op_widen_f64")
 
 
 def pfc_op_df_from_f64(count, x, y, stream=None):

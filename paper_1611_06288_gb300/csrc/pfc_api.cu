@@ -957,6 +957,18 @@ int pfc_op_guess_df(int n, double h, double eps, const float* b, const float* c,
   return PFC_OK;
 }
 
+int pfc_op_round_f32(long long count, const double* x, float* y, void* stream) {
+  if (count < 0 || (count > 0 && (!x || !y))) return PFC_EINVAL;
+  PFC_CUDA(launch_round_f32(count, x, y, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
+int pfc_op_widen_f64(long long count, const float* x, double* y, void* stream) {
+  if (count < 0 || (count > 0 && (!x || !y))) return PFC_EINVAL;
+  PFC_CUDA(launch_widen_f64(count, x, y, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
 int pfc_op_df_from_f64(long long count, const double* x, float* y, void* stream) {
   if (count < 0 || (count > 0 && (!x || !y))) return PFC_EINVAL;
   PFC_CUDA(launch_df_from_f64(count, x, reinterpret_cast<float2*>(y), (cudaStream_t)stream));

@@ -149,6 +149,39 @@ __device__ __forceinline__ void operator_at(const Lvl& L, const Stencil& s,
   n3 = fma(-L.gh, lphi, w);
 }
 
+// FP64 <-> FP32 conversions on the integer pipe.  GB300 issues FP64<->FP32
+// conversions at its FP64 rate (about 2 per SM per clock, like a DFMA), so
+// the hot kernels form the bit patterns themselves from the IEEE 754 binary64
+// and binary32 layouts (sign | biased exponent | fraction; biases 1023 and
+// 127, fractions of 52 and 23 bits).  Zeros, subnormals, infinities and NaNs
+// take the hardware conversion.
+//
+// binary64 -> binary32, round to nearest, ties to even: the exponent is
+// rebiased (e - 896), the top 23 fraction bits are kept and the 29 dropped
+// ones decide the rounding (above half up; exactly half up when the kept bits
+// are odd).  A carry out of the fraction increments the exponent, and past
+// the largest finite float it yields the infinity IEEE 754 prescribes.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e < 897u || e > 1150u) return __double2float_rn(x);
+  const unsigned kept = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  unsigned bits = ((e - 896u) << 23) | kept;
+  bits += (rest > 0x10000000u || (rest == 0x10000000u && (kept & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | bits);
+}
+
+// binary32 -> binary64, exact: the exponent is rebiased (e + 896) and the 23
+// fraction bits become the top of the 52.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 255u) return (double)f;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xFFFFFu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
 // Programmatic dependent launch: a kernel launched with programmatic stream
 // serialization may be scheduled while its predecessor drains; pdl_wait()
 // blocks until the predecessor has completed and its writes are visible (a

@@ -123,40 +123,6 @@ __device__ __forceinline__ void split_cell(int64_t t, int n, int& p, int& j, int
   p = x - colour * half;
 }
 
-// Defect of the FP64 outer loop (PFC_MIXED): r = S - N(u) in FP64 (Eqs.
-// 5.4-5.6, M = 1) rounded to FP32 into the colour-split r1..r3, the Newton
-// coefficient q = f'(phi) + (1-eps)/2 of the cubic term in FP64 rounded to
-// FP32, and per-block FP64 partial sums of |r|^2.
-__global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restrict__ phi,
-                                                  const double* __restrict__ mu,
-                                                  const double* __restrict__ om,
-                                                  const double* __restrict__ S1,
-                                                  const double* __restrict__ S2,
-                                                  const double* __restrict__ S3,
-                                                  const double* __restrict__ b,
-                                                  float* __restrict__ r1, float* __restrict__ r2,
-                                                  float* __restrict__ r3, float* __restrict__ q,
-                                                  double* partials) {
-  __shared__ double sm[32];
-  const int n = L.n;
-  const int cells = n * n * n;
-  double acc[1] = {0.0};
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
-    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
-    const Stencil s = stencil_at(i, j, k, n);
-    double x, y, z;
-    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
-    acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
-    const int o = split_index(i, j, k, n);
-    r1[o] = (float)x;
-    r2[o] = (float)y;
-    r3[o] = (float)z;
-    q[o] = (float)(cubic_fp(__ldg(phi + t), __ldg(b + t)) + L.c1);
-  }
-  block_sum<1>(acc, sm);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
-}
-
 // Constants of the double-float operator on one level.
 struct LvlD {
   int n;
@@ -217,6 +183,59 @@ __device__ __forceinline__ float block_sum_f(float v, float* sm) {
   }
   return v;
 }
+
+// Neighbour sum of an FP64 field at the six indices of s (fixed order).
+__device__ __forceinline__ double nbsum64(const double* __restrict__ v, const Nb6& s) {
+  return ((__ldg(v + s.xm) + __ldg(v + s.xp)) + (__ldg(v + s.ym) + __ldg(v + s.yp))) +
+         (__ldg(v + s.zm) + __ldg(v + s.zp));
+}
+
+// Defect of the FP64 outer loop (PFC_MIXED): r = S - N(u) in FP64 (Eqs.
+// 5.4-5.6, M = 1) rounded to FP32 into the colour-split r1..r3, the Newton
+// coefficient q = f'(phi) + (1-eps)/2 of the cubic term in FP64 rounded to
+// FP32, and per-block sums of |r|^2 (of the FP32-rounded r, accumulated in
+// FP32 within a block: the sum only decides convergence).  f and f' share
+// phi^2, b^2 and phi b; the roundings to FP32 use the integer pipe.
+__global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restrict__ phi,
+                                                  const double* __restrict__ mu,
+                                                  const double* __restrict__ om,
+                                                  const double* __restrict__ S1,
+                                                  const double* __restrict__ S2,
+                                                  const double* __restrict__ S3,
+                                                  const double* __restrict__ b,
+                                                  float* __restrict__ r1, float* __restrict__ r2,
+                                                  float* __restrict__ r3, float* __restrict__ q,
+                                                  double* partials) {
+  __shared__ float sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  float acc = 0.f;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const Nb6 s = nb6_at(t, i, j, k, n);
+    const double p = __ldg(phi + t), m = __ldg(mu + t), w = __ldg(om + t);
+    const double bb = __ldg(b + t);
+    const double lmu = fma(-6.0, m, nbsum64(mu, s));
+    const double lom = fma(-6.0, w, nbsum64(om, s));
+    const double lphi = fma(-6.0, p, nbsum64(phi, s));
+    const double p2 = p * p, b2 = bb * bb, pb = p * bb;
+    const double f = 0.25 * ((p + bb) * (p2 + b2));          // f(phi, b), Eq. 5.2
+    const double fp = fma(0.75, p2, fma(0.5, pb, 0.25 * b2));  // df/dphi
+    const double x = __ldg(S1 + t) - fma(-L.tg, lmu, p);
+    const double y = __ldg(S2 + t) - (fma(-L.c1, p, m - f) - L.g * lom);
+    const double z = __ldg(S3 + t) - fma(-L.gh, lphi, w);
+    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
+    acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
+    const int o = split_index(i, j, k, n);
+    r1[o] = xf;
+    r2[o] = yf;
+    r3[o] = zf;
+    q[o] = d2f_rn(fp + L.c1);
+  }
+  acc = block_sum_f(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
 
 // Unscaled 7-point Laplacian (neighbour sum - 6 centre) of a df field as an
 // unnormalised pair: -6 c split exactly by one FMA, then the six neighbours.
@@ -458,6 +477,17 @@ __global__ void k_mu_guess_df(LvlD L, const float2* __restrict__ phig,
   df r;
   two_sum(m.hi, m.lo, r.hi, r.lo);
   df_st(mug, t, r);
+}
+
+// The integer-pipe conversions of the FP64 outer loop on whole arrays.
+__global__ void k_round_f32(int64_t count, const double* __restrict__ x, float* __restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) y[t] = d2f_rn(x[t]);
+}
+
+__global__ void k_widen_f64(int64_t count, const float* __restrict__ x, double* __restrict__ y) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) y[t] = f2d(x[t]);
 }
 
 // FP64 <-> df conversions of whole fields; in place allowed (each thread
@@ -1267,7 +1297,8 @@ constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 K
 
 // u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
 
-// u += d (FP64 += FP32, colour-split d), per component.
+// u += d (FP64 += FP32, colour-split d; the exact widening on the integer
+// pipe), per component.
 __global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__ u2,
                             double* __restrict__ u3, const float* __restrict__ d1,
                             const float* __restrict__ d2, const float* __restrict__ d3) {
@@ -1278,9 +1309,9 @@ __global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__
   if (i >= n || j >= n) return;
   const int t = (k * n + j) * n + i;
   const int o = split_index(i, j, k, n);
-  u1[t] += (double)__ldg(d1 + o);
-  u2[t] += (double)__ldg(d2 + o);
-  u3[t] += (double)__ldg(d3 + o);
+  u1[t] += f2d(__ldg(d1 + o));
+  u2[t] += f2d(__ldg(d2 + o));
+  u3[t] += f2d(__ldg(d3 + o));
 }
 
 // u += d: df state plus the FP32 correction (colour-split), per component.
@@ -1522,6 +1553,18 @@ cudaError_t launch_guess_df(const Lvl& L, const float2* b, const float2* c, floa
   const LvlD D = to_df(L);
   k_source_guess_df<<<g.grid, g.block, 0, st>>>(D, b, c, S2, S3, phig, omg);
   k_mu_guess_df<<<g.grid, g.block, 0, st>>>(D, phig, omg, b, S2, mug);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_round_f32(int64_t count, const double* x, float* y, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_round_f32<<<grid_for(count), kThreads, 0, st>>>(count, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen_f64(int64_t count, const float* x, double* y, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  k_widen_f64<<<grid_for(count), kThreads, 0, st>>>(count, x, y);
   return cudaGetLastError();
 }
 

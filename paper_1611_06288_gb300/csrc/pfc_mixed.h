@@ -86,6 +86,11 @@ cudaError_t launch_guess_df(const Lvl& L, const float2* b, const float2* c, floa
 cudaError_t launch_diagnostics_df(int n, const float2* a, const float2* b, double* partials,
                                   double* out, cudaStream_t st);
 
+// The FP64 -> FP32 rounding (nearest, ties to even) and exact FP32 -> FP64
+// widening that the FP64 outer loop performs on the integer pipe, on arrays.
+cudaError_t launch_round_f32(int64_t count, const double* x, float* y, cudaStream_t st);
+cudaError_t launch_widen_f64(int64_t count, const float* x, double* y, cudaStream_t st);
+
 // Whole-field conversions FP64 <-> df (count cells; in place allowed).
 cudaError_t launch_df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
 cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStream_t st);

@@ -229,6 +229,43 @@ def test_guess_df(n):
         assert_close_field(host_df(g), x, DF_RTOL, name)
 
 
+def test_integer_pipe_conversions():
+    """FP64 -> FP32 rounding and FP32 -> FP64 widening formed from the bit
+    fields: bit-exact against numpy's IEEE conversions (round to nearest,
+    ties to even) on random values over the whole float range, exact ties
+    (odd and even kept bits), carries into the exponent, overflow to
+    infinity, the normal/subnormal boundary, zeros, infinities and NaN."""
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(200000) * 10.0 ** rng.uniform(-45, 45, 200000)
+    f = rng.standard_normal(2000).astype(np.float32)
+    # exact halfway points between f and its neighbour away from zero
+    ties = f.astype(np.float64) + np.spacing(f).astype(np.float64) / 2
+    special = np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1.0, -1.0, 2.0 ** -126,
+                        2.0 ** -126 * (1 - 2 ** -30), 2.0 ** -149, 2.0 ** -150, 1e-300,
+                        3.4028234663852886e38, 3.4028235677973366e38, 3.5e38, 1e300,
+                        1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, 2.0 - 2.0 ** -25, 0.1, 1.0 / 3])
+    xs = np.concatenate([x, ties, -ties, special])
+    y = torch.empty(xs.size, dtype=torch.float32, device="cuda")
+    B.pfc_op_round_f32(xs.size, dev(xs), y)
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore"):
+        ref = xs.astype(np.float32)
+    got = y.cpu().numpy()
+    same = (got.view(np.uint32) == ref.view(np.uint32)) | (np.isnan(got) & np.isnan(ref))
+    assert same.all(), xs[~same][:5]
+    fs = np.concatenate([f, np.array([0.0, -0.0, np.inf, -np.inf, np.nan, 1e-45, -1e-40,
+                                      1.1754944e-38, 3.4028235e38], np.float32),
+                         (rng.standard_normal(50000) * 10.0 ** rng.uniform(-37, 37, 50000))
+                         .astype(np.float32)])
+    w = torch.empty(fs.size, dtype=torch.float64, device="cuda")
+    B.pfc_op_widen_f64(fs.size, dev(fs, torch.float32), w)
+    torch.cuda.synchronize()
+    gw = w.cpu().numpy()
+    rw = fs.astype(np.float64)
+    same = (gw.view(np.uint64) == rw.view(np.uint64)) | (np.isnan(gw) & np.isnan(rw))
+    assert same.all(), fs[~same][:5]
+
+
 @pytest.mark.parametrize("n", [1, 2, 12, 32])
 def test_df_conversions(n):
     """FP64 -> (hi, lo) pairs and back, out of place and in place: bit-exact
@@ -275,7 +312,8 @@ def test_defect_and_correct(n):
     rms = B.pfc_op_defect(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S], dev(b),
                           *r, q, scratch)
     ref = O.residual(S, u, b, h, prm())
-    assert rms == pytest.approx(O.rms(ref), rel=1e-12)
+    # |r|^2 of the FP32-rounded r, summed in FP32 within a block: ~1e-6
+    assert rms == pytest.approx(O.rms(ref), rel=1e-5)
     for g, x in zip(r, ref):
         # FP64 residual rounded to FP32: half an FP32 ulp (colour-split layout)
         assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
