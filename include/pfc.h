@@ -380,13 +380,16 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
 
 /* FP64 residual r = S - N(u) rounded to FP32 into d_r1..3, the coefficient
  * q = f'(phi) + (1-eps)/2 formed in FP64 and rounded to FP32 into d_q, and
- * *out = RMS of the FP64 residual (blocking).  d_scratch:
- * pfc_reduce_scratch_bytes(n) bytes.  n even. */
+ * *out = RMS of the residual (its FP32-rounded components, summed in FP32
+ * within a thread block; blocking).  d_lap (may be NULL) receives the
+ * unscaled 7-point Laplacian of phi (neighbour sum - 6 centre) the residual
+ * uses: the time step keeps it for the next steps' sources and diagnostics.
+ * d_scratch: pfc_reduce_scratch_bytes(n) bytes.  n even. */
 int pfc_op_defect(int n, double h, double eps, double tau, const double* d_phi,
                   const double* d_mu, const double* d_om, const double* d_S1,
                   const double* d_S2, const double* d_S3, const double* d_b,
                   float* d_r1, float* d_r2, float* d_r3, float* d_q,
-                  void* d_scratch, double* out, void* stream);
+                  void* d_scratch, double* out, double* d_lap, void* stream);
 
 /* u += d (FP64 += FP32) for the three components; d colour-split.  n even. */
 int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
@@ -430,13 +433,14 @@ int pfc_op_guess_df(int n, double h, double eps, const float* d_b, const float* 
 /* Residual r = S - N(u) of the df fields (phi, mu, om), sources S1..S3 and
  * b, evaluated in double-float and rounded to FP32 into d_r1..3; the
  * coefficient q = f'(phi) + (1-eps)/2 in FP32 from the hi parts of phi and b
- * into d_q; *out = RMS of the residual (blocking).  d_scratch:
+ * into d_q; *out = RMS of the residual (blocking); d_lap (may be NULL) the
+ * unscaled Laplacian of phi as a df field.  d_scratch:
  * pfc_reduce_scratch_bytes(n) bytes.  n even. */
 int pfc_op_defect_df(int n, double h, double eps, double tau, const float* d_phi,
                   const float* d_mu, const float* d_om, const float* d_S1,
                   const float* d_S2, const float* d_S3, const float* d_b,
                   float* d_r1, float* d_r2, float* d_r3, float* d_q,
-                  void* d_scratch, double* out, void* stream);
+                  void* d_scratch, double* out, float* d_lap, void* stream);
 
 /* `sweeps` red-black Gauss-Seidel sweeps in FP32 on J d = r with q frozen
  * (the same pointwise 3x3 system as pfc_op_smooth with q given).  zero_init

@@ -92,10 +92,10 @@ _SIGS = {
     "pfc_op_residual_norm": (_I, [_I, _D, _D, _D] + [_P] * 8 + [ctypes.POINTER(_D), _P]),
     "pfc_op_residual_norm_static": (_I, [_I, _D, _D, _D] + [_P] * 7 +
                                     [ctypes.POINTER(_D), _P]),
-    "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
+    "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P, _P]),
     "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
-    "pfc_op_defect_df": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P]),
+    "pfc_op_defect_df": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P, _P]),
     "pfc_op_correct_df": (_I, [_I] + [_P] * 6 + [_P]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
@@ -364,20 +364,20 @@ def pfc_op_residual_norm_static(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, stre
 
 
 def pfc_op_defect(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, scratch,
-                  stream=None):
+                  stream=None, lap=None):
     out = ctypes.c_double()
     check(lib().pfc_op_defect(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1), ptr(S2),
                               ptr(S3), ptr(b), ptr(r1), ptr(r2), ptr(r3), ptr(q),
-                              ptr(scratch), ctypes.byref(out), stream), "pfc_op_defect")
+                              ptr(scratch), ctypes.byref(out), ptr(lap), stream), "pfc_op_defect")
     return out.value
 
 
 def pfc_op_defect_df(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, scratch,
-                  stream=None):
+                  stream=None, lap=None):
     out = ctypes.c_double()
     check(lib().pfc_op_defect_df(n, h, eps, tau, ptr(phi), ptr(mu), ptr(om), ptr(S1), ptr(S2),
                               ptr(S3), ptr(b), ptr(r1), ptr(r2), ptr(r3), ptr(q),
-                              ptr(scratch), ctypes.byref(out), stream), "pfc_op_defect_df")
+                              ptr(scratch), ctypes.byref(out), ptr(lap), stream), "pfc_op_defect_df")
     return out.value
 
 

@@ -121,6 +121,8 @@ struct pfc_ctx {
   double* ring[3];   // phi^{k-1}, phi^k, phi^{k+1} rotate through these
   int ic, ib, ia;
   double *mu, *om, *S2, *S3;  // ring, mu .. S3: doubles (FP64) or df pairs (mixed)
+  double* lap[3];    // unscaled Laplacian of ring[r], written by the residual
+                     // kernels on the iterate and by pfc_set_state (same format)
   double* t0[3];     // level-0 Jacobi scratch
   double* partials;  // reduction partial sums
   double* dout;      // 8 device doubles of reduction results
@@ -149,6 +151,10 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
   for (int r = 0; r < 3; ++r) {
     double* f = cv.take<double>(n3);
     if (c) c->ring[r] = f;
+  }
+  for (int r = 0; r < 3; ++r) {
+    double* f = cv.take<double>(n3);
+    if (c) c->lap[r] = f;
   }
   double* mu = cv.take<double>(n3);
   double* om = cv.take<double>(n3);
@@ -273,14 +279,15 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
       S[q] = as_df(lv.S[q]);
     }
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, u, S, as_df(lv.b), c->partials, c->dout, st,
-                                  &c->prof));
+                                  &c->prof, as_df(c->lap[c->ia])));
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
-                                  &c->prof));
+                                  &c->prof, c->lap[c->ia]));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
               launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
-                                    lv.S[2], lv.b, c->partials, c->dout, st));
+                                    lv.S[2], lv.b, c->partials, c->dout, st,
+                                    c->lap[c->ia]));
   }
   const double n3 = (double)c->p.n * c->p.n * c->p.n;
   PFC_CUDA(launch_decide(h, use_handle, c->dout, c->dstate, 1.0 / (3.0 * n3), c->p.tol,
@@ -307,11 +314,13 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
                            c->st));
   } else if (df_state(&c->p)) {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
-              launch_source_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),
-                               c->st));
+              launch_source_cached_df(lv.L, as_df(lv.b), as_df(c->lap[c->ib]),
+                                      as_df(c->lap[c->ic]), as_df(c->S2), as_df(c->S3),
+                                      c->st));
   } else {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
-              launch_source(lv.L, lv.b, cprev, c->S2, c->S3, c->st));
+              launch_source_cached(lv.L, lv.b, c->lap[c->ib], c->lap[c->ic], c->S2, c->S3,
+                                   c->st));
   }
   if (c->p.precision == PFC_FP64) {
     const double* fine = lv.b;
@@ -630,6 +639,12 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
     // PFC_MIXED_DF keeps phi as df pairs: convert in place
     PFC_CUDA(launch_df_from_f64(n3, c->ring[c->ib], as_df(c->ring[c->ib]), c->st));
     PFC_CUDA(launch_df_from_f64(n3, c->ring[c->ic], as_df(c->ring[c->ic]), c->st));
+    PFC_CUDA(launch_laplacian_df(c->p.n, as_df(c->ring[c->ib]), as_df(c->lap[c->ib]), c->st));
+    PFC_CUDA(launch_laplacian_df(c->p.n, as_df(c->ring[c->ic]), as_df(c->lap[c->ic]), c->st));
+    c->prof.launches += 4;
+  } else {
+    PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ib], c->lap[c->ib], c->st));
+    PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ic], c->lap[c->ic], c->st));
     c->prof.launches += 2;
   }
   return PFC_OK;
@@ -672,11 +687,20 @@ int pfc_get_omega(pfc_ctx* c, double* any_dst) {
   return c ? copy_field(c, c->om, any_dst) : PFC_EINVAL;
 }
 
+// Energy, modified energy, mass and |grad a|^2 of a = phi^k, b = phi^{k-1};
+// with lapa, lapb (their stored unscaled Laplacians) the kernels skip the
+// stencils.
 static int diagnostics(int n, double h, double eps, const double* a, const double* b,
-                       bool df_fields, double* partials, double* dout, double* hout,
-                       cudaStream_t st, double* res) {
-  if (df_fields)
+                       const double* lapa, const double* lapb, bool df_fields,
+                       double* partials, double* dout, double* hout, cudaStream_t st,
+                       double* res) {
+  if (df_fields && lapa)
+    PFC_CUDA(launch_diagnostics_cached_df(n, as_df(a), as_df(b), as_df(lapa), as_df(lapb),
+                                          partials, dout, st));
+  else if (df_fields)
     PFC_CUDA(launch_diagnostics_df(n, as_df(a), as_df(b), partials, dout, st));
+  else if (lapa)
+    PFC_CUDA(launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st));
   else
     PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
   PFC_CUDA(cudaMemcpyAsync(hout, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -695,7 +719,8 @@ int pfc_diagnostics(pfc_ctx* c, double out[4]) {
   if (!c || !out) return PFC_EINVAL;
   c->prof.launches += 2;
   return diagnostics(c->p.n, c->p.L / c->p.n, c->p.eps, c->ring[c->ib], c->ring[c->ic],
-                     df_state(&c->p), c->partials, c->dout, c->hout, c->st, out);
+                     c->lap[c->ib], c->lap[c->ic], df_state(&c->p), c->partials, c->dout,
+                     c->hout, c->st, out);
 }
 
 int pfc_energy(pfc_ctx* c, double* F, double* F_modified) {
@@ -906,8 +931,8 @@ static int op_diagnostics(int n, double h, double eps, const double* a, const do
   double* partials = (double*)scratch;
   double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
   double hout[8];
-  return diagnostics(n, h, eps, a, b, df_fields, partials, dout, hout, (cudaStream_t)stream,
-                     out);
+  return diagnostics(n, h, eps, a, b, nullptr, nullptr, df_fields, partials, dout, hout,
+                     (cudaStream_t)stream, out);
 }
 
 int pfc_op_diagnostics(int n, double h, double eps, const double* a, const double* b,
@@ -994,7 +1019,7 @@ int pfc_op_source_df(int n, double h, double eps, const float* b, const float* c
 int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
                   const double* mu, const double* om, const double* S1, const double* S2,
                   const double* S3, const double* b, float* r1, float* r2, float* r3,
-                  float* q, void* scratch, double* out, void* stream) {
+                  float* q, void* scratch, double* out, double* lap, void* stream) {
   if (n < 2 || (n & 1) || !(h > 0) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 ||
       !r2 || !r3 || !q || !scratch || !out)
     return PFC_EINVAL;
@@ -1003,7 +1028,7 @@ int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
   double hv = 0;
   cudaStream_t st = (cudaStream_t)stream;
   PFC_CUDA(launch_defect64(make_lvl(n, h, eps, tau), phi, mu, om, S1, S2, S3, b, r1, r2, r3, q,
-                           partials, dout, st));
+                           partials, dout, st, lap));
   PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
   PFC_CUDA(cudaStreamSynchronize(st));
   *out = sqrt(hv / (3.0 * (double)n * n * n));
@@ -1013,7 +1038,7 @@ int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
 int pfc_op_defect_df(int n, double h, double eps, double tau, const float* phi, const float* mu,
                   const float* om, const float* S1, const float* S2, const float* S3,
                   const float* b, float* r1, float* r2, float* r3, float* q, void* scratch,
-                  double* out, void* stream) {
+                  double* out, float* lap, void* stream) {
   if (n < 2 || (n & 1) || !(h > 0) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !r1 ||
       !r2 || !r3 || !q || !scratch || !out)
     return PFC_EINVAL;
@@ -1023,7 +1048,8 @@ int pfc_op_defect_df(int n, double h, double eps, double tau, const float* phi, 
   cudaStream_t st = (cudaStream_t)stream;
   auto D = [](const float* p) { return reinterpret_cast<const float2*>(p); };
   PFC_CUDA(launch_defect_df(make_lvl(n, h, eps, tau), D(phi), D(mu), D(om), D(S1), D(S2),
-                            D(S3), D(b), r1, r2, r3, q, partials, dout, st));
+                            D(S3), D(b), r1, r2, r3, q, partials, dout, st,
+                            reinterpret_cast<float2*>(lap)));
   PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
   PFC_CUDA(cudaStreamSynchronize(st));
   *out = sqrt(hv / (3.0 * (double)n * n * n));

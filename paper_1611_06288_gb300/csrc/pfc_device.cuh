@@ -114,7 +114,8 @@ __device__ __forceinline__ void point_solve(const Lvl& L, double sphi, double sm
   om = fma(-L.g3, phi, st3);
 }
 
-// r = S - N(u) at one cell (Eqs. 5.4-5.6 with M = 1).
+// r = S - N(u) at one cell (Eqs. 5.4-5.6 with M = 1); lap receives the
+// unscaled 7-point Laplacian of phi (neighbour sum - 6 centre) it computes.
 __device__ __forceinline__ void residual_at(const Lvl& L, const Stencil& s,
                                             const double* __restrict__ phi,
                                             const double* __restrict__ mu,
@@ -123,7 +124,7 @@ __device__ __forceinline__ void residual_at(const Lvl& L, const Stencil& s,
                                             const double* __restrict__ S2,
                                             const double* __restrict__ S3,
                                             const double* __restrict__ b,
-                                            double& r1, double& r2, double& r3) {
+                                            double& r1, double& r2, double& r3, double& lap) {
   const double p = __ldg(phi + s.c), m = __ldg(mu + s.c), w = __ldg(om + s.c);
   const double bb = __ldg(b + s.c);
   const double lmu = fma(-6.0, m, nbsum(mu, s));
@@ -133,6 +134,20 @@ __device__ __forceinline__ void residual_at(const Lvl& L, const Stencil& s,
   r1 = __ldg(S1 + s.c) - fma(-L.tg, lmu, p);
   r2 = __ldg(S2 + s.c) - (fma(-L.c1, p, m - cubic_f(p, bb)) - L.g * lom);
   r3 = __ldg(S3 + s.c) - fma(-L.gh, lphi, w);
+  lap = lphi;
+}
+
+__device__ __forceinline__ void residual_at(const Lvl& L, const Stencil& s,
+                                            const double* __restrict__ phi,
+                                            const double* __restrict__ mu,
+                                            const double* __restrict__ om,
+                                            const double* __restrict__ S1,
+                                            const double* __restrict__ S2,
+                                            const double* __restrict__ S3,
+                                            const double* __restrict__ b,
+                                            double& r1, double& r2, double& r3) {
+  double lap;
+  residual_at(L, s, phi, mu, om, S1, S2, S3, b, r1, r2, r3, lap);
 }
 
 // N(u) at one cell (no source), coherent loads.

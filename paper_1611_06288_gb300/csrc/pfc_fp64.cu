@@ -77,6 +77,30 @@ __global__ void k_mu_guess(Lvl L, const double* __restrict__ phig,
   mug[s.c] = fma(L.g, lw, fma(L.c1, p, __ldg(S2 + s.c) + cubic_f(p, __ldg(b + s.c))));
 }
 
+// Unscaled 7-point Laplacian of a field (neighbour sum - 6 centre), the
+// quantity the residual kernels store for later reuse.
+__global__ void k_laplacian(int n, const double* __restrict__ v, double* __restrict__ lap) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * n * n) return;
+  int i, j, k;
+  cell_of(t, n, i, j, k);
+  const Stencil s = stencil_at(i, j, k, n);
+  lap[t] = fma(-6.0, __ldg(v + s.c), nbsum(v, s));
+}
+
+// S2, S3 of Eqs. 5.9-5.10 from the stored unscaled Laplacians of b = phi^k
+// and c = phi^{k-1}: the arithmetic of k_source without its two stencils.
+__global__ void k_source_cached(Lvl L, const double* __restrict__ b,
+                                const double* __restrict__ lapb, const double* __restrict__ lapc,
+                                double* __restrict__ S2, double* __restrict__ S3) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)L.n * L.n * L.n) return;
+  const double lb = L.g * __ldg(lapb + t);
+  const double lc = L.g * __ldg(lapc + t);
+  S2[t] = fma(3.0, lb, fma(L.c1, __ldg(b + t), -lc));
+  S3[t] = 0.5 * lb;
+}
+
 // ---------------------------------------------------------------------------
 // a2/a7: one colour of the red-black nonlinear Gauss-Seidel sweep (Section 5).
 // Thread t owns the t-th cell of the colour: i = 2p + ((j+k+colour) & 1).
@@ -379,7 +403,8 @@ __global__ void k_residual_norm2(Lvl L, const double* __restrict__ phi,
                                  const double* __restrict__ S1,
                                  const double* __restrict__ S2,
                                  const double* __restrict__ S3,
-                                 const double* __restrict__ b, double* partials) {
+                                 const double* __restrict__ b, double* partials,
+                                 double* __restrict__ lap) {
   __shared__ double sm[32];
   const int n = L.n;
   const int64_t cells = (int64_t)n * n * n;
@@ -389,9 +414,10 @@ __global__ void k_residual_norm2(Lvl L, const double* __restrict__ phi,
     int i, j, k;
     cell_of(t, n, i, j, k);
     const Stencil s = stencil_at(i, j, k, n);
-    double x, y, z;
-    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z);
+    double x, y, z, lp;
+    residual_at(L, s, phi, mu, om, S1, S2, S3, b, x, y, z, lp);
     acc[0] = fma(x, x, fma(y, y, fma(z, z, acc[0])));
+    if (lap) lap[t] = lp;
   }
   block_sum<1>(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
@@ -446,6 +472,33 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
   }
 }
 
+// The raw sums of k_diagnostics from the stored unscaled Laplacians of a and
+// b: -(a, Lap a) and (Lap a)^2 directly, and the forward-face sum of
+// |D(a-b)|^2 by summation by parts as -(a-b, Lap a - Lap b) (Lemma 2.1).
+__global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
+                                     const double* __restrict__ b,
+                                     const double* __restrict__ lapa,
+                                     const double* __restrict__ lapb, double* partials) {
+  __shared__ double sm[32 * 6];
+  const int cells = n * n * n;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const double x = __ldg(a + t), la = __ldg(lapa + t);
+    const double y = x - __ldg(b + t);
+    const double x2 = x * x;
+    acc[0] = fma(x2, x2, acc[0]);
+    acc[1] += x2;
+    acc[2] = fma(-x, la, acc[2]);
+    acc[3] = fma(la, la, acc[3]);
+    acc[4] = fma(-y, la - __ldg(lapb + t), acc[4]);
+    acc[5] += x;
+  }
+  block_sum<6>(acc, sm);
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < 6; ++c) partials[(int64_t)blockIdx.x * 6 + c] = acc[c];
+  }
+}
+
 // Convergence test of Algorithm 1's loop (RMS residual against the tolerance,
 // NaN, cycle budget) on the device.
 __global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
@@ -484,6 +537,27 @@ cudaError_t launch_guess(const Lvl& L, const double* b, const double* c, double*
   const int64_t cells = (int64_t)L.n * L.n * L.n;
   k_source_guess<<<grid_for(cells), kThreads, 0, st>>>(L, b, c, S2, S3, phig, omg);
   k_mu_guess<<<grid_for(cells), kThreads, 0, st>>>(L, phig, omg, b, S2, mug);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t st) {
+  k_laplacian<<<grid_for((int64_t)n * n * n), kThreads, 0, st>>>(n, v, lap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* lapb,
+                                 const double* lapc, double* S2, double* S3, cudaStream_t st) {
+  k_source_cached<<<grid_for((int64_t)L.n * L.n * L.n), kThreads, 0, st>>>(L, b, lapb, lapc,
+                                                                           S2, S3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
+                                      const double* lapa, const double* lapb, double* partials,
+                                      double* out, cudaStream_t st) {
+  const int nb = reduce_blocks((int64_t)n * n * n);
+  k_diagnostics_cached<<<nb, kReduceThreads, 0, st>>>(n, a, b, lapa, lapb, partials);
+  k_reduce_final<6><<<1, kReduceThreads, 0, st>>>(partials, nb, out);
   return cudaGetLastError();
 }
 
@@ -613,9 +687,10 @@ cudaError_t launch_coarse_solve(const Lvl& L, int lin, int kind, double w, int m
 cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double* mu,
                                   const double* om, const double* S1, const double* S2,
                                   const double* S3, const double* b, double* partials,
-                                  double* out, cudaStream_t st) {
+                                  double* out, cudaStream_t st, double* lap) {
   const int nb = reduce_blocks((int64_t)L.n * L.n * L.n);
-  k_residual_norm2<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, partials);
+  k_residual_norm2<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, partials,
+                                                  lap);
   k_reduce_final<1><<<1, kReduceThreads, 0, st>>>(partials, nb, out);
   return cudaGetLastError();
 }

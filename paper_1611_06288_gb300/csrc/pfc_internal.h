@@ -103,10 +103,20 @@ inline int level_kind(const pfc_params* p, double h) {
 }
 // Sum over cells of r1^2 + r2^2 + r3^2 -> partials (one per block), then the
 // fixed-order final sum into out[0] (device).
+// lap (may be null) receives the unscaled Laplacian of phi.
 cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double* mu,
                                   const double* om, const double* S1, const double* S2,
                                   const double* S3, const double* b, double* partials,
-                                  double* out, cudaStream_t st);
+                                  double* out, cudaStream_t st, double* lap = nullptr);
+// Unscaled 7-point Laplacian (neighbour sum - 6 centre) of a field.
+cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t st);
+// S2, S3 from b and the stored unscaled Laplacians of b and c.
+cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* lapb,
+                                 const double* lapc, double* S2, double* S3, cudaStream_t st);
+// launch_diagnostics from the stored unscaled Laplacians of a and b.
+cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
+                                      const double* lapa, const double* lapb, double* partials,
+                                      double* out, cudaStream_t st);
 // out[0..5] = sum a^4, sum a^2, sum |D a|^2 (faces), sum (Lap a)^2 (times h^4
 // removed: raw stencil sums), sum |D(a-b)|^2, sum a.  Raw sums; the host scales.
 cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,

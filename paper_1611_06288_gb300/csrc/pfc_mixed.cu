@@ -195,7 +195,8 @@ __device__ __forceinline__ double nbsum64(const double* __restrict__ v, const Nb
 // coefficient q = f'(phi) + (1-eps)/2 of the cubic term in FP64 rounded to
 // FP32, and per-block sums of |r|^2 (of the FP32-rounded r, accumulated in
 // FP32 within a block: the sum only decides convergence).  f and f' share
-// phi^2, b^2 and phi b; the roundings to FP32 use the integer pipe.
+// phi^2, b^2 and phi b; the roundings to FP32 use the integer pipe.  lap
+// (may be null) receives the unscaled Laplacian of phi for later reuse.
 __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restrict__ phi,
                                                   const double* __restrict__ mu,
                                                   const double* __restrict__ om,
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
                                                   const double* __restrict__ b,
                                                   float* __restrict__ r1, float* __restrict__ r2,
                                                   float* __restrict__ r3, float* __restrict__ q,
-                                                  double* partials) {
+                                                  double* partials, double* __restrict__ lap) {
   __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
     r2[o] = yf;
     r3[o] = zf;
     q[o] = d2f_rn(fp + L.c1);
+    if (lap) lap[t] = lphi;
   }
   acc = block_sum_f(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
@@ -278,13 +280,14 @@ __device__ __forceinline__ dacc dacc_cubic(df p, df b) {
 // terms rounded to FP32 into the colour-split r1..r3;
 // q = f'(phi) + (1-eps)/2 (Jacobian of the cubic term of Eq. 5.2) in FP32
 // from the hi parts of phi and b, colour-split; per-block partial sums of
-// |r|^2 (FP32 within a block, one double per block).
+// |r|^2 (FP32 within a block, one double per block); lap (may be null)
+// receives the unscaled Laplacian of phi as a df field.
 __global__ void __launch_bounds__(256, 6) k_defect_df(
     LvlD L, const float2* __restrict__ phi, const float2* __restrict__ mu,
     const float2* __restrict__ om, const float2* __restrict__ S1,
     const float2* __restrict__ S2, const float2* __restrict__ S3,
     const float2* __restrict__ b, float* __restrict__ r1, float* __restrict__ r2,
-    float* __restrict__ r3, float* __restrict__ q, double* partials) {
+    float* __restrict__ r3, float* __restrict__ q, double* partials, float2* __restrict__ lap) {
   __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
@@ -310,8 +313,14 @@ __global__ void __launch_bounds__(256, 6) k_defect_df(
     // r3 = S3 - omega + 1/(2h^2) Lap phi
     dacc z = dacc_of(df_ld(S3, t));
     dacc_sub(z, df_ld(om, t));
-    const dacc hl = dacc_mul(L.gh, dacc_lap(phi, s, p));
+    const dacc lphi = dacc_lap(phi, s, p);
+    const dacc hl = dacc_mul(L.gh, lphi);
     dacc_add(z, hl.hi, hl.lo);
+    if (lap) {
+      df v;
+      two_sum(lphi.hi, lphi.lo, v.hi, v.lo);
+      df_st(lap, t, v);
+    }
     const float xf = dacc_round(x), yf = dacc_round(y), zf = dacc_round(z);
     acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
     const int o = split_index(i, j, k, n);
@@ -477,6 +486,61 @@ __global__ void k_mu_guess_df(LvlD L, const float2* __restrict__ phig,
   df r;
   two_sum(m.hi, m.lo, r.hi, r.lo);
   df_st(mug, t, r);
+}
+
+// Unscaled 7-point Laplacian of a df field, as a df field.
+__global__ void k_laplacian_df(int n, const float2* __restrict__ v, float2* __restrict__ lap) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const dacc L = dacc_lap(v, nb6_at(t, i, j, k, n), df_ld(v, t));
+  df r;
+  two_sum(L.hi, L.lo, r.hi, r.lo);
+  df_st(lap, t, r);
+}
+
+// k_source_df from the stored df Laplacians of b and c.
+__global__ void k_source_cached_df(LvlD L, const float2* __restrict__ b,
+                                   const float2* __restrict__ lapb,
+                                   const float2* __restrict__ lapc, float2* __restrict__ S2,
+                                   float2* __restrict__ S3) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)L.n * L.n * L.n) return;
+  const int u = (int)t;
+  const df lb = df_mul(L.g, df_ld(lapb, u));
+  const df lc = df_mul(L.g, df_ld(lapc, u));
+  df_st(S2, u, df_add(df_mul_f(lb, 3.f), df_sub(df_mul(L.c1, df_ld(b, u)), lc)));
+  df_st(S3, u, df_scale2(lb, 0.5f));
+}
+
+// k_diagnostics_df from the stored df Laplacians of a and b (the face sum of
+// |D(a-b)|^2 by summation by parts, Lemma 2.1).
+__global__ void k_diagnostics_cached_df(int n, const float2* __restrict__ a,
+                                        const float2* __restrict__ b,
+                                        const float2* __restrict__ lapa,
+                                        const float2* __restrict__ lapb, float2* partials) {
+  __shared__ float2 sm[32 * 6];
+  const int cells = n * n * n;
+  df acc[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) acc[c] = df{0.f, 0.f};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const df x = df_ld(a, t), la = df_ld(lapa, t);
+    const df y = df_sub(x, df_ld(b, t));
+    const df x2 = df_sqr(x);
+    acc[0] = df_add(acc[0], df_sqr(x2));
+    acc[1] = df_add(acc[1], x2);
+    acc[2] = df_sub(acc[2], df_mul(x, la));
+    acc[3] = df_add(acc[3], df_sqr(la));
+    acc[4] = df_sub(acc[4], df_mul(y, df_sub(la, df_ld(lapb, t))));
+    acc[5] = df_add(acc[5], x);
+  }
+  block_sum_df<6>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) partials[blockIdx.x * 6 + c] = make_float2(acc[c].hi, acc[c].lo);
+  }
 }
 
 // The integer-pipe conversions of the FP64 outer loop on whole arrays.
@@ -730,41 +794,13 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   c3[o] = 0.125f * a3;
 }
 
-// Trilinear cell-centred prolongation of one coarse field onto the eight
-// children of coarse cell (I, J, K), as three one-dimensional passes: the
-// child on the low side of an axis takes (3 e_0 + e_-1)/4, on the high side
-// (3 e_0 + e_+1)/4 (together the weights 27, 9, 3, 1 over 64).  cidx[z][y][x]
-// are the split-layout indices of the 3x3x3 coarse neighbourhood; out[kk][jj]
-// [a] receives the child (2I+a, 2J+jj, 2K+kk).
-__device__ __forceinline__ void prolong_block(const float* __restrict__ e, const int (&cidx)[27],
-                                              float (&out)[8]) {
-  float zx[3][3][2];                           // [y][x][child z]
-#pragma unroll
-  for (int y = 0; y < 3; ++y) {
-#pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const float lo = __ldg(e + cidx[0 * 9 + y * 3 + x]);
-      const float mid = __ldg(e + cidx[1 * 9 + y * 3 + x]);
-      const float hi = __ldg(e + cidx[2 * 9 + y * 3 + x]);
-      zx[y][x][0] = fmaf(3.f, mid, lo);
-      zx[y][x][1] = fmaf(3.f, mid, hi);
-    }
-  }
-#pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      float yx[3];
-#pragma unroll
-      for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
-      out[(2 * kk + jj) * 2 + 0] = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);
-      out[(2 * kk + jj) * 2 + 1] = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);
-    }
-  }
-}
-
-// d += P e (ASSIGN: d = P e; d was zero and is not read), split layout on
-// both levels, one thread per coarse cell writing its eight children.
+// d += P e (ASSIGN: d = P e; d was zero and is not read), trilinear
+// cell-centred prolongation with the weights 27, 9, 3, 1 over 64 as three
+// one-dimensional passes: the child on the low side of an axis takes
+// (3 e_0 + e_-1)/4, on the high side (3 e_0 + e_+1)/4.  Split layout on both
+// levels; one thread per coarse cell (I, J, K) writes its eight children
+// from the 3x3x3 coarse neighbourhood.  Only the wrapped coarse coordinates
+// stay live; every index is formed at its load or store.
 template <bool ASSIGN>
 __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
@@ -772,40 +808,51 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 float* __restrict__ d3) {
   pdl_wait();
   pdl_trigger();
-  const int nc = n >> 1, half = n >> 1;
+  const int nc = n >> 1, half = n >> 1, hc = nc >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
             K = blockIdx.z;
   if (I >= nc || J >= nc) return;
-  int cidx[27];
-  {
-    const int Is[3] = {(I == 0) ? nc - 1 : I - 1, I, (I + 1 == nc) ? 0 : I + 1};
-    const int Js[3] = {(J == 0) ? nc - 1 : J - 1, J, (J + 1 == nc) ? 0 : J + 1};
-    const int Ks[3] = {(K == 0) ? nc - 1 : K - 1, K, (K + 1 == nc) ? 0 : K + 1};
-#pragma unroll
-    for (int z = 0; z < 3; ++z)
-#pragma unroll
-      for (int y = 0; y < 3; ++y)
-#pragma unroll
-        for (int x = 0; x < 3; ++x) cidx[z * 9 + y * 3 + x] = split_index(Is[x], Js[y], Ks[z], nc);
-  }
-  int fidx[8];
-#pragma unroll
-  for (int kk = 0; kk < 2; ++kk)
-#pragma unroll
-    for (int jj = 0; jj < 2; ++jj)
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        const int i = 2 * I + a, j = 2 * J + jj, k = 2 * K + kk;
-        fidx[(2 * kk + jj) * 2 + a] = (k * n + j) * n + ((i + j + k) & 1) * half + I;
-      }
+  const int Is[3] = {(I == 0) ? nc - 1 : I - 1, I, (I + 1 == nc) ? 0 : I + 1};
+  const int Js[3] = {(J == 0) ? nc - 1 : J - 1, J, (J + 1 == nc) ? 0 : J + 1};
+  const int Ks[3] = {(K == 0) ? nc - 1 : K - 1, K, (K + 1 == nc) ? 0 : K + 1};
   const float* e[3] = {e1, e2, e3};
   float* d[3] = {d1, d2, d3};
-#pragma unroll
+#pragma unroll 1
   for (int f = 0; f < 3; ++f) {
-    float v[8];
-    prolong_block(e[f], cidx, v);
+    const float* __restrict__ ef = e[f];
+    float zx[3][3][2];                         // [y][x][child z]: 3 e_mid + e_lo / e_hi
 #pragma unroll
-    for (int c = 0; c < 8; ++c) d[f][fidx[c]] = ASSIGN ? v[c] : v[c] + d[f][fidx[c]];
+    for (int y = 0; y < 3; ++y) {
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        float v[3];
+#pragma unroll
+        for (int z = 0; z < 3; ++z) {
+          const int idx = (Ks[z] * nc + Js[y]) * nc + ((Is[x] + Js[y] + Ks[z]) & 1) * hc +
+                          (Is[x] >> 1);
+          v[z] = __ldg(ef + idx);
+        }
+        zx[y][x][0] = fmaf(3.f, v[1], v[0]);
+        zx[y][x][1] = fmaf(3.f, v[1], v[2]);
+      }
+    }
+    float* __restrict__ df_ = d[f];
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        float yx[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
+        const int j = 2 * J + jj, k = 2 * K + kk;
+        const int row = (k * n + j) * n + I, par = (j + k) & 1;   // child a has colour a ^ par
+        const float v0 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);  // a = 0 (i = 2I)
+        const float v1 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);  // a = 1 (i = 2I + 1)
+        const int o0 = row + par * half, o1 = row + (1 - par) * half;
+        df_[o0] = ASSIGN ? v0 : v0 + df_[o0];
+        df_[o1] = ASSIGN ? v1 : v1 + df_[o1];
+      }
+    }
   }
 }
 
@@ -1505,10 +1552,11 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
 cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
-                            float* q, double* partials, double* out, cudaStream_t st) {
+                            float* q, double* partials, double* out, cudaStream_t st,
+                            double* lap) {
   const int nb = wave_blocks(k_defect64, (int64_t)L.n * L.n * L.n);
   k_defect64<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q,
-                                            partials);
+                                            partials, lap);
   k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
   return cudaGetLastError();
 }
@@ -1522,10 +1570,11 @@ cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const fl
 cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,
-                             float* q, double* partials, double* out, cudaStream_t st) {
+                             float* q, double* partials, double* out, cudaStream_t st,
+                             float2* lap) {
   const int nb = wave_blocks(k_defect_df, (int64_t)L.n * L.n * L.n);
   k_defect_df<<<nb, kReduceThreads, 0, st>>>(to_df(L), phi, mu, om, S1, S2, S3, b, r1, r2, r3,
-                                             q, partials);
+                                             q, partials, lap);
   k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
   return cudaGetLastError();
 }
@@ -1565,6 +1614,29 @@ cudaError_t launch_round_f32(int64_t count, const double* x, float* y, cudaStrea
 cudaError_t launch_widen_f64(int64_t count, const float* x, double* y, cudaStream_t st) {
   if (count <= 0) return cudaSuccess;
   k_widen_f64<<<grid_for(count), kThreads, 0, st>>>(count, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_laplacian_df(int n, const float2* v, float2* lap, cudaStream_t st) {
+  const Launch3 g = launch3(n, n, n);
+  k_laplacian_df<<<g.grid, g.block, 0, st>>>(n, v, lap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_source_cached_df(const Lvl& L, const float2* b, const float2* lapb,
+                                    const float2* lapc, float2* S2, float2* S3, cudaStream_t st) {
+  k_source_cached_df<<<grid_for((int64_t)L.n * L.n * L.n), kThreads, 0, st>>>(to_df(L), b, lapb,
+                                                                              lapc, S2, S3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics_cached_df(int n, const float2* a, const float2* b,
+                                         const float2* lapa, const float2* lapb,
+                                         double* partials, double* out, cudaStream_t st) {
+  const int nb = wave_blocks(k_diagnostics_cached_df, (int64_t)n * n * n);
+  float2* parts = reinterpret_cast<float2*>(partials);
+  k_diagnostics_cached_df<<<nb, kReduceThreads, 0, st>>>(n, a, b, lapa, lapb, parts);
+  k_reduce_df6<<<1, kReduceThreads, 0, st>>>(parts, nb, out);
   return cudaGetLastError();
 }
 
@@ -1642,20 +1714,20 @@ cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const f
 
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
-                                 double* dout, cudaStream_t st, Prof* pr) {
+                                 double* dout, cudaStream_t st, Prof* pr, double* lap) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
-                                  mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st);
+                                  mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
 
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],
                                  float2* const S[3], const float2* b, double* partials,
-                                 double* dout, cudaStream_t st, Prof* pr) {
+                                 double* dout, cudaStream_t st, Prof* pr, float2* lap) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect_df(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
-                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st);
+                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }

@@ -53,13 +53,13 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
 // level 0, and the FP64 sum of |r|^2 at dout[0] (two launches).
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
-                                 double* dout, cudaStream_t st, Prof* pr);
+                                 double* dout, cudaStream_t st, Prof* pr, double* lap);
 
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],
                                  float2* const S[3], const float2* b, double* partials,
-                                 double* dout, cudaStream_t st, Prof* pr);
+                                 double* dout, cudaStream_t st, Prof* pr, float2* lap);
 
 // One defect correction after mixed_enqueue_defect: q restricted to every
 // level, p.inner_cycles FP32 V-cycles on J d = r from d = 0, then u += d in
@@ -91,6 +91,15 @@ cudaError_t launch_diagnostics_df(int n, const float2* a, const float2* b, doubl
 cudaError_t launch_round_f32(int64_t count, const double* x, float* y, cudaStream_t st);
 cudaError_t launch_widen_f64(int64_t count, const float* x, double* y, cudaStream_t st);
 
+// df counterparts of launch_laplacian, launch_source_cached and
+// launch_diagnostics_cached.
+cudaError_t launch_laplacian_df(int n, const float2* v, float2* lap, cudaStream_t st);
+cudaError_t launch_source_cached_df(const Lvl& L, const float2* b, const float2* lapb,
+                                    const float2* lapc, float2* S2, float2* S3, cudaStream_t st);
+cudaError_t launch_diagnostics_cached_df(int n, const float2* a, const float2* b,
+                                         const float2* lapa, const float2* lapb,
+                                         double* partials, double* out, cudaStream_t st);
+
 // Whole-field conversions FP64 <-> df (count cells; in place allowed).
 cudaError_t launch_df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
 cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStream_t st);
@@ -99,14 +108,16 @@ cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStre
 cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
-                            float* q, double* partials, double* out, cudaStream_t st);
+                            float* q, double* partials, double* out, cudaStream_t st,
+                            double* lap = nullptr);
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
                              const float* d2, const float* d3, cudaStream_t st,
                              bool pdl = true);
 cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,
-                             float* q, double* partials, double* out, cudaStream_t st);
+                             float* q, double* partials, double* out, cudaStream_t st,
+                             float2* lap = nullptr);
 cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float* d1,
                                           const float* d2, const float* d3, const float* r1,
                                           const float* r2, const float* r3, const float* q,

@@ -48,9 +48,10 @@ def test_default_params_and_workspace(libpfc):
     assert B.pfc_workspace_bytes(p) == 0          # n, L, dt unset -> invalid
     p.n, p.L, p.eps, p.dt = 16, 32.0, 0.025, 0.01
     n16 = B.pfc_workspace_bytes(p)
-    # 10 fine FP64 fields (3 levels of phi, mu, omega, S2, S3, 3 Jacobi
-    # scratch) + 13 per coarse level (8, 4, 2) + reduction buffers
-    fields = 10 * 16 ** 3 + 13 * (8 ** 3 + 4 ** 3 + 2 ** 3)
+    # 13 fine FP64 fields (3 levels of phi and their 3 Laplacians, mu, omega,
+    # S2, S3, 3 Jacobi scratch) + 13 per coarse level (8, 4, 2) + reduction
+    # buffers
+    fields = 13 * 16 ** 3 + 13 * (8 ** 3 + 4 ** 3 + 2 ** 3)
     assert fields * 8 <= n16 <= fields * 8 + 100_000
     p.precision = B.PFC_MIXED
     assert B.pfc_workspace_bytes(p) > n16

@@ -309,11 +309,14 @@ def test_defect_and_correct(n):
     scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
     r = [empty(n, torch.float32) for _ in range(3)]
     q = empty(n, torch.float32)
+    lap = empty(n)
     rms = B.pfc_op_defect(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S], dev(b),
-                          *r, q, scratch)
+                          *r, q, scratch, lap=lap)
     ref = O.residual(S, u, b, h, prm())
     # |r|^2 of the FP32-rounded r, summed in FP32 within a block: ~1e-6
     assert rms == pytest.approx(O.rms(ref), rel=1e-5)
+    # the unscaled Laplacian of phi kept for the sources and diagnostics
+    assert_close_field(host(lap), h * h * O.lap(u[0], h), FP64_RTOL, "lap")
     for g, x in zip(r, ref):
         # FP64 residual rounded to FP32: half an FP32 ulp (colour-split layout)
         assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
@@ -339,8 +342,10 @@ def test_defect_and_correct_df(n):
     scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
     r = [empty(n, torch.float32) for _ in range(3)]
     q = empty(n, torch.float32)
+    lap = torch.empty((n, n, n, 2), dtype=torch.float32, device="cuda")
     rms = B.pfc_op_defect_df(n, h, EPS, TAU, *[dev_df(x) for x in u], *[dev_df(s) for s in S],
-                          dev_df(b), *r, q, scratch)
+                          dev_df(b), *r, q, scratch, lap=lap)
+    assert_close_field(host_df(lap), h * h * O.lap(u[0], h), DF_RTOL, "lap")
     ref = O.residual(S, u, b, h, prm())
     # |r|^2 summed in FP32 within a thread block: relative error ~1e-6
     assert rms == pytest.approx(O.rms(ref), rel=1e-5)
