@@ -63,7 +63,7 @@ KERNEL_BYTES = {
 # DRAM bytes (read + write) of one launch of a kernel class of a precision,
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
-NCU_TRAFFIC = {("mixed_df", "defect"): 118.0e6}   # profiles/k_defect_df_128.md
+NCU_TRAFFIC = {("mixed", "defect"): 133.7e6}   # profiles/k_defect64_128.md
 
 # FP64-ALU-bound kernel classes of a precision: algorithmic FP64 flops per
 # cell of one counted launch (FMA = 2) and launches per group.  The FP64
