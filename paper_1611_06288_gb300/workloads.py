@@ -137,6 +137,8 @@ class Workload:
             return smooth_mode(self.n, self.L)
         if self.name.startswith("polycrystal"):
             return polycrystal_seeds(self.n, self.L, seed=seed)
+        if self.name.startswith("growth"):
+            return uniform_01_start(self.n, seed=seed)
         if self.name.startswith("cosine"):
             return cosine_bump(self.n, self.L)
         raise KeyError(self.name)
@@ -172,6 +174,19 @@ def polycrystal(n: int = 256, steps: int = 2000, tol: float = 1e-9):
     kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 3), ("jacobi_factor", 3),
           ("coarse_sweeps", 2))
     return Workload(f"polycrystal{n}", n, n * math.pi / 4.0, 0.25, 0.1, steps, tol, kw)
+
+
+def growth(n: int = 128, steps: int = 10000, tol: float = 1e-9):
+    """Section 6.2 growth of a polycrystal: Omega = [0, 64]^3, eps = 0.25,
+    dt = 0.01, phi0 = 0.2 + 0.005 U[0, 1] (the grid is not stated; n = 128
+    gives h = 0.5).  Long runs of it are the energy/mass soak test.
+
+    Mixed-path settings: the finest level is in the damped-Jacobi regime
+    (108 tau/h^6 = 69 at h = 0.5), so V(1,2) with three cycles per
+    correction."""
+    kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 3), ("jacobi_factor", 3),
+          ("coarse_sweeps", 2))
+    return Workload(f"growth{n}", n, 64.0, 0.25, 0.01, steps, tol, kw)
 
 
 def cosine_table(n: int, dt: float = 1e-3, steps: int = 10, tol: float = 1e-8):
