@@ -354,6 +354,42 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
                                 const double* d_b, double* out, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Ensembles: `members` independent runs (1 <= members <= 1024) of one grid
+ * size n, box L, tau and solver settings (PFC_MIXED only), each with its own
+ * eps and initial field, advanced together: every kernel of a step covers
+ * all members, so the small grids of an ensemble share each launch and one
+ * CUDA graph runs the step of the whole ensemble.  Every field holds the
+ * members one after another (member m at offset m*n^3 of the n^3*members
+ * doubles passed to pfc_batch_init, pfc_set_state and pfc_get_*).  pfc_step
+ * ends a step when every member has converged (a converged member stays
+ * converged while the others continue; its further corrections only lower
+ * its residual) and returns PFC_ENOCONV or PFC_ENAN if any member fails;
+ * stats then report the most corrections and the largest residuals.
+ * pfc_energy, pfc_mass and pfc_diagnostics report member 0.
+ * --------------------------------------------------------------------- */
+
+/* Workspace bytes of an ensemble (0 if invalid: as pfc_workspace_bytes, and
+ * members > 1 requires PFC_MIXED). */
+size_t pfc_batch_workspace_bytes(const pfc_params* p, int members);
+
+/* As pfc_init for `members` runs: eps[m] (host array) replaces p->eps for
+ * member m; any_phi0 holds the members' initial fields one after another;
+ * each member starts with phi^{-1} := phi^0. */
+int pfc_batch_init(pfc_ctx** out, const pfc_params* p, int members, const double* eps,
+                   void* d_workspace, size_t workspace_bytes, const double* any_phi0,
+                   void* stream);
+
+/* Members of the context (1 for pfc_init), or -1 for NULL. */
+int pfc_batch_members(const pfc_ctx* c);
+
+/* out[4m .. 4m+3] = pfc_diagnostics of member m (host array of 4*members). */
+int pfc_batch_diagnostics(pfc_ctx* c, double* out);
+
+/* Per member, of the last step: corrections, final and initial RMS
+ * residuals (host arrays of `members`; any may be NULL). */
+int pfc_batch_status(const pfc_ctx* c, int* iters, double* residual, double* residual0);
+
+/* ------------------------------------------------------------------------
  * Primitive operations of the mixed-precision paths.  The outer loop is a
  * defect correction: r = S - N(u), then an FP32 multigrid solve of J d = r,
  * with J the Jacobian of N at u (Eqs. 5.4-5.6 differentiated in phi: only the

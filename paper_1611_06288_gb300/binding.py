@@ -97,6 +97,12 @@ _SIGS = {
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
     "pfc_op_defect_df": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P, _P]),
     "pfc_op_correct_df": (_I, [_I] + [_P] * 6 + [_P]),
+    "pfc_batch_workspace_bytes": (_SZ, [ctypes.POINTER(pfc_params), _I]),
+    "pfc_batch_init": (_I, [ctypes.POINTER(_P), ctypes.POINTER(pfc_params), _I,
+                            ctypes.POINTER(_D), _P, _SZ, _P, _P]),
+    "pfc_batch_members": (_I, [_P]),
+    "pfc_batch_diagnostics": (_I, [_P, ctypes.POINTER(_D)]),
+    "pfc_batch_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
     "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
@@ -184,6 +190,38 @@ def pfc_init(p: pfc_params, workspace, phi0, phi1=None, stream=None) -> ctypes.c
                         ptr(phi1), stream)
     check(rc, "pfc_init")
     return ctx
+
+
+def pfc_batch_workspace_bytes(p: pfc_params, members: int) -> int:
+    return lib().pfc_batch_workspace_bytes(ctypes.byref(p), members)
+
+
+def pfc_batch_init(p: pfc_params, eps, workspace, phi0, stream=None) -> ctypes.c_void_p:
+    members = len(eps)
+    e = (ctypes.c_double * members)(*[float(x) for x in eps])
+    ctx = ctypes.c_void_p()
+    rc = lib().pfc_batch_init(ctypes.byref(ctx), ctypes.byref(p), members, e, ptr(workspace),
+                              workspace.numel() * workspace.element_size(), ptr(phi0), stream)
+    check(rc, "pfc_batch_init")
+    return ctx
+
+
+def pfc_batch_members(ctx) -> int:
+    return lib().pfc_batch_members(ctx)
+
+
+def pfc_batch_diagnostics(ctx, members: int):
+    out = (ctypes.c_double * (4 * members))()
+    check(lib().pfc_batch_diagnostics(ctx, out), "pfc_batch_diagnostics")
+    return [tuple(out[4 * m:4 * m + 4]) for m in range(members)]
+
+
+def pfc_batch_status(ctx, members: int):
+    it = (ctypes.c_int * members)()
+    r = (ctypes.c_double * members)()
+    r0 = (ctypes.c_double * members)()
+    check(lib().pfc_batch_status(ctx, it, r, r0), "pfc_batch_status")
+    return list(it), list(r), list(r0)
 
 
 def pfc_step(ctx, nsteps: int = 1) -> pfc_step_stats:

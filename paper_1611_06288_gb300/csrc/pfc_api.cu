@@ -33,6 +33,7 @@ int cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 constexpr int kMaxLevels = 24;
+constexpr int kMaxMembers = 1024;   // ensemble members of one context (one decide block)
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -123,6 +124,10 @@ struct pfc_ctx {
   double *mu, *om, *S2, *S3;  // ring, mu .. S3: doubles (FP64) or df pairs (mixed)
   double* lap[3];    // unscaled Laplacian of ring[r], written by the residual
                      // kernels on the iterate and by pfc_set_state (same format)
+  int nb;            // ensemble members (1: a single problem); every field holds
+                     // the members one after another
+  double* c1m;       // (1 - eps_m)/2 per member on the device (null when nb == 1)
+  double* eps_host;  // eps per member on the host (nb entries)
   double* t0[3];     // level-0 Jacobi scratch
   double* partials;  // reduction partial sums
   double* dout;      // 8 device doubles of reduction results
@@ -143,9 +148,9 @@ struct pfc_ctx {
 namespace pfc {
 namespace {
 
-size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
+size_t carve(pfc_ctx* c, const pfc_params* p, char* base, int members) {
   Carver cv{base, 0};
-  const int64_t n3 = (int64_t)p->n * p->n * p->n;
+  const int64_t n3 = (int64_t)p->n * p->n * p->n * members;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   for (int r = 0; r < 3; ++r) {
@@ -185,16 +190,20 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base) {
     if (c) c->lev[l] = lv;
   }
   double* partials = cv.take<double>((size_t)kReduceBlocks * kReduceComps);
-  double* dout = cv.take<double>(kReduceComps);
-  StepState* dstate = cv.take<StepState>(1);
+  double* dout = cv.take<double>((size_t)kReduceComps * members);
+  StepState* dstate = cv.take<StepState>(members);
+  double* c1m = members > 1 ? cv.take<double>(members) : nullptr;
   if (c) {
     c->partials = partials;
     c->dout = dout;
     c->dstate = dstate;
+    c->c1m = c1m;
+    c->nb = members;
   }
   if (is_mixed(p)) {
     MixedBufs mx;
-    mixed_carve(&mx, p->n, nl, sizes, [&](size_t count) { return cv.take<float>(count); });
+    mixed_carve(
+        &mx, p->n, nl, sizes, [&](size_t count) { return cv.take<float>(count); }, members);
     if (c) c->mx = mx;
   }
   return cv.off;
@@ -282,7 +291,7 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
                                   &c->prof, as_df(c->lap[c->ia])));
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
-                                  &c->prof, c->lap[c->ia]));
+                                  &c->prof, c->lap[c->ia], c->nb, c->c1m));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
               launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
@@ -291,7 +300,7 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
   }
   const double n3 = (double)c->p.n * c->p.n * c->p.n;
   PFC_CUDA(launch_decide(h, use_handle, c->dout, c->dstate, 1.0 / (3.0 * n3), c->p.tol,
-                         c->p.max_cycles, first, st));
+                         c->p.max_cycles, first, st, c->nb));
   c->prof.launches += 1;
   return PFC_OK;
 }
@@ -301,7 +310,7 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
 // first residual and decision.
 int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int use_handle) {
   const double* cprev = c->ring[c->ic];
-  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   Prof* pr = &c->prof;
   const bool extrapolate = c->p.guess == PFC_GUESS_EXTRAPOLATE;
   if (extrapolate && df_state(&c->p)) {
@@ -320,7 +329,7 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   } else {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
               launch_source_cached(lv.L, lv.b, c->lap[c->ib], c->lap[c->ic], c->S2, c->S3,
-                                   c->st));
+                                   c->st, c->nb, c->c1m));
   }
   if (c->p.precision == PFC_FP64) {
     const double* fine = lv.b;
@@ -344,7 +353,8 @@ int enqueue_body(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
     float2* u[3] = {as_df(lv.u[0]), as_df(lv.u[1]), as_df(lv.u[2])};
     PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, u, c->st, &c->prof));
   } else if (is_mixed(&c->p)) {
-    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, lv.u, c->st, &c->prof));
+    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, lv.u, c->st, &c->prof,
+                                      c->nb));
   } else {
     int rc = vcycle64(c, 0, lv);
     if (rc) return rc;
@@ -353,8 +363,8 @@ int enqueue_body(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
 }
 
 int read_state(pfc_ctx* c) {
-  PFC_CUDA(cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState), cudaMemcpyDeviceToHost,
-                           c->st));
+  PFC_CUDA(cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState) * c->nb,
+                           cudaMemcpyDeviceToHost, c->st));
   PFC_CUDA(cudaStreamSynchronize(c->st));
   prof_harvest(&c->prof);
   return PFC_OK;
@@ -410,8 +420,8 @@ int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
       e = cudaStreamUpdateCaptureDependencies(c->st, &cnode, nullptr, 1,
                                               cudaStreamSetCaptureDependencies);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState), cudaMemcpyDeviceToHost,
-                          c->st);
+      e = cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState) * c->nb,
+                          cudaMemcpyDeviceToHost, c->st);
   }
   cudaGraph_t cap = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(c->st, &cap);
@@ -439,10 +449,29 @@ int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
   return PFC_OK;
 }
 
+// The step's outcome over all ensemble members: the worst status, the most
+// cycles and the largest residuals.
+StepState combined_state(const pfc_ctx* c) {
+  StepState s = c->hstate[0];
+  for (int m = 1; m < c->nb; ++m) {
+    const StepState& t = c->hstate[m];
+    if (t.iters > s.iters) s.iters = t.iters;
+    if (!(t.rms <= s.rms)) s.rms = t.rms;
+    if (!(t.rms0 <= s.rms0)) s.rms0 = t.rms0;
+    // NaN over no-convergence over running over converged
+    const int rank_t = t.status == kStepNaN ? 3 : t.status == kStepNoConv ? 2
+                       : t.status == kStepRunning ? 1 : 0;
+    const int rank_s = s.status == kStepNaN ? 3 : s.status == kStepNoConv ? 2
+                       : s.status == kStepRunning ? 1 : 0;
+    if (rank_t > rank_s) s.status = t.status;
+  }
+  return s;
+}
+
 int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   Level64 lv;
   level0(c, &lv);
-  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   int rc = PFC_OK;
   if (c->use_graphs && c->prof.mask == 0) {
     pfc_ctx::Graph* g = &c->graph[c->ia];
@@ -452,17 +481,18 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
     }
     PFC_CUDA(cudaGraphLaunch(g->exec, c->st));
     PFC_CUDA(cudaStreamSynchronize(c->st));
-    c->prof.launches += g->launches_pre + g->launches_body * (long long)c->hstate->iters;
+    c->prof.launches +=
+        g->launches_pre + g->launches_body * (long long)combined_state(c).iters;
   } else {
     rc = enqueue_pre(c, lv, 0, 0);
     if (rc == PFC_OK) rc = read_state(c);
-    while (rc == PFC_OK && c->hstate->status == kStepRunning) {
+    while (rc == PFC_OK && combined_state(c).status == kStepRunning) {
       rc = enqueue_body(c, lv, 0, 0);
       if (rc == PFC_OK) rc = read_state(c);
     }
     if (rc) return rc;
   }
-  const StepState s = *c->hstate;
+  const StepState s = combined_state(c);
   if (s.status == kStepNaN) rc = PFC_ENAN;
   else if (s.status == kStepNoConv) rc = PFC_ENOCONV;
   else if (s.status != kStepConverged) rc = PFC_ECUDA;
@@ -567,31 +597,44 @@ int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind)
 
 size_t pfc_workspace_bytes(const pfc_params* p) {
   if (validate(p) != PFC_OK) return 0;
-  return carve(nullptr, p, nullptr);
+  return carve(nullptr, p, nullptr, 1);
+}
+
+size_t pfc_batch_workspace_bytes(const pfc_params* p, int members) {
+  if (validate(p) != PFC_OK || members < 1 || members > kMaxMembers) return 0;
+  if (members > 1 && p->precision != PFC_MIXED) return 0;
+  return carve(nullptr, p, nullptr, members);
 }
 
 const char* pfc_last_error(void) { return g_last_error; }
 
-int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
-             size_t workspace_bytes, const double* any_phi0, const double* any_phi1,
-             void* stream) {
+// Context of `members` independent runs (one for pfc_init) sharing n, L, tau
+// and the solver settings, member m with eps[m] and its initial fields at
+// offset m n^3 of any_phi0 / any_phi1.
+static int init_members(pfc_ctx** out, const pfc_params* p, int members, const double* eps,
+                        void* d_workspace, size_t workspace_bytes, const double* any_phi0,
+                        const double* any_phi1, void* stream) {
   if (!out || !d_workspace || !any_phi0) return PFC_EINVAL;
   *out = nullptr;
   int v = validate(p);
   if (v) return v;
+  if (members < 1 || members > kMaxMembers) return PFC_EINVAL;
+  if (members > 1 && p->precision != PFC_MIXED) return PFC_EINVAL;
+  for (int m = 0; m < members; ++m)
+    if (!(eps[m] >= 0 && eps[m] < 1)) return PFC_EINVAL;
   if (((uintptr_t)d_workspace) % kAlign) return PFC_EINVAL;
   cudaPointerAttributes attr;
   cudaError_t e = cudaPointerGetAttributes(&attr, d_workspace);
   if (e != cudaSuccess) return cuda_fail(e, "cudaPointerGetAttributes(workspace)");
   if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
     return PFC_EINVAL;
-  const size_t need = carve(nullptr, p, nullptr);
+  const size_t need = carve(nullptr, p, nullptr, members);
   if (workspace_bytes < need) return PFC_ESIZE;
   pfc_ctx* c = (pfc_ctx*)calloc(1, sizeof(pfc_ctx));
   if (!c) return PFC_EINVAL;
   c->p = *p;
   c->st = (cudaStream_t)stream;
-  carve(c, p, (char*)d_workspace);
+  carve(c, p, (char*)d_workspace, members);
   double h = p->L / p->n;
   for (int l = 0; l < c->nl; ++l) {
     c->lev[l].n = c->sizes[l];
@@ -599,21 +642,38 @@ int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
     c->lev[l].kind = level_kind(p, h);
     h *= 2.0;
   }
-  e = cudaHostAlloc((void**)&c->hout, kReduceComps * sizeof(double), cudaHostAllocDefault);
+  c->eps_host = (double*)malloc(sizeof(double) * members);
+  if (!c->eps_host) {
+    free(c);
+    return PFC_EINVAL;
+  }
+  memcpy(c->eps_host, eps, sizeof(double) * members);
+  e = cudaHostAlloc((void**)&c->hout, kReduceComps * sizeof(double) * members,
+                    cudaHostAllocDefault);
   if (e == cudaSuccess)
-    e = cudaHostAlloc((void**)&c->hstate, sizeof(StepState), cudaHostAllocDefault);
+    e = cudaHostAlloc((void**)&c->hstate, sizeof(StepState) * members, cudaHostAllocDefault);
   if (e != cudaSuccess) {
     if (c->hout) cudaFreeHost(c->hout);
+    free(c->eps_host);
     free(c);
     return cuda_fail(e, "cudaHostAlloc");
   }
-  memset(c->hstate, 0, sizeof(StepState));
+  memset(c->hstate, 0, sizeof(StepState) * members);
   c->use_graphs = 1;
   c->ic = 0;
   c->ib = 1;
   c->ia = 2;
-  const size_t bytes = (size_t)p->n * p->n * p->n * sizeof(double);
-  int rc = pfc_set_state(c, any_phi1 ? any_phi1 : any_phi0, any_phi1 ? any_phi0 : nullptr);
+  int rc = PFC_OK;
+  if (c->c1m) {
+    for (int m = 0; m < members; ++m) c->hout[m] = 0.5 * (1.0 - eps[m]);
+    e = cudaMemcpyAsync(c->c1m, c->hout, sizeof(double) * members, cudaMemcpyHostToDevice,
+                        c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "cudaMemcpyAsync(eps)");
+  }
+  const size_t bytes = (size_t)p->n * p->n * p->n * members * sizeof(double);
+  if (rc == PFC_OK)
+    rc = pfc_set_state(c, any_phi1 ? any_phi1 : any_phi0, any_phi1 ? any_phi0 : nullptr);
   if (rc == PFC_OK) {
     e = cudaMemsetAsync(c->mu, 0, bytes, c->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->om, 0, bytes, c->st);
@@ -628,9 +688,25 @@ int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
   return PFC_OK;
 }
 
+int pfc_init(pfc_ctx** out, const pfc_params* p, void* d_workspace,
+             size_t workspace_bytes, const double* any_phi0, const double* any_phi1,
+             void* stream) {
+  if (!p) return PFC_EINVAL;
+  return init_members(out, p, 1, &p->eps, d_workspace, workspace_bytes, any_phi0, any_phi1,
+                      stream);
+}
+
+int pfc_batch_init(pfc_ctx** out, const pfc_params* p, int members, const double* eps,
+                   void* d_workspace, size_t workspace_bytes, const double* any_phi0,
+                   void* stream) {
+  if (!p || !eps) return PFC_EINVAL;
+  return init_members(out, p, members, eps, d_workspace, workspace_bytes, any_phi0, nullptr,
+                      stream);
+}
+
 int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev) {
   if (!c || !any_phi) return PFC_EINVAL;
-  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   const size_t bytes = (size_t)n3 * sizeof(double);
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ib], any_phi, bytes, cudaMemcpyDefault, c->st));
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ic], any_phi_prev ? any_phi_prev : any_phi, bytes,
@@ -643,8 +719,8 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
     PFC_CUDA(launch_laplacian_df(c->p.n, as_df(c->ring[c->ic]), as_df(c->lap[c->ic]), c->st));
     c->prof.launches += 4;
   } else {
-    PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ib], c->lap[c->ib], c->st));
-    PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ic], c->lap[c->ic], c->st));
+    PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ib], c->lap[c->ib], c->st, c->nb));
+    PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ic], c->lap[c->ic], c->st, c->nb));
     c->prof.launches += 2;
   }
   return PFC_OK;
@@ -665,7 +741,7 @@ int pfc_step(pfc_ctx* c, int nsteps, pfc_step_stats* stats) {
 // steps (each step starts by overwriting it with phi^k).
 static int copy_field(pfc_ctx* c, const double* src, double* dst) {
   if (!c || !dst) return PFC_EINVAL;
-  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   const size_t bytes = (size_t)n3 * sizeof(double);
   if (df_state(&c->p)) {
     double* stage = c->ring[c->ia];
@@ -687,41 +763,69 @@ int pfc_get_omega(pfc_ctx* c, double* any_dst) {
   return c ? copy_field(c, c->om, any_dst) : PFC_EINVAL;
 }
 
-// Energy, modified energy, mass and |grad a|^2 of a = phi^k, b = phi^{k-1};
-// with lapa, lapb (their stored unscaled Laplacians) the kernels skip the
+// Energy, modified energy, mass and |grad a|^2 of a = phi^k, b = phi^{k-1}
+// for `members` ensemble members (eps[m] each, res[4 m .. 4 m + 3]); with
+// lapa, lapb (their stored unscaled Laplacians) the kernels skip the
 // stencils.
-static int diagnostics(int n, double h, double eps, const double* a, const double* b,
-                       const double* lapa, const double* lapb, bool df_fields,
-                       double* partials, double* dout, double* hout, cudaStream_t st,
-                       double* res) {
+static int diagnostics(int n, double h, const double* eps, int members, const double* a,
+                       const double* b, const double* lapa, const double* lapb,
+                       bool df_fields, double* partials, double* dout, double* hout,
+                       cudaStream_t st, double* res) {
   if (df_fields && lapa)
     PFC_CUDA(launch_diagnostics_cached_df(n, as_df(a), as_df(b), as_df(lapa), as_df(lapb),
                                           partials, dout, st));
   else if (df_fields)
     PFC_CUDA(launch_diagnostics_df(n, as_df(a), as_df(b), partials, dout, st));
   else if (lapa)
-    PFC_CUDA(launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st));
+    PFC_CUDA(launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st, members));
   else
     PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
-  PFC_CUDA(cudaMemcpyAsync(hout, dout, 6 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaMemcpyAsync(hout, dout, kReduceComps * members * sizeof(double),
+                           cudaMemcpyDeviceToHost, st));
   PFC_CUDA(cudaStreamSynchronize(st));
   const double h3 = h * h * h;
-  const double F = 0.25 * h3 * hout[0] + 0.5 * (1.0 - eps) * h3 * hout[1] - h * hout[2] +
-                   0.5 * hout[3] / h;
-  res[0] = F;
-  res[1] = F + 0.5 * h * hout[4];
-  res[2] = h3 * hout[5];
-  res[3] = h * hout[2];
+  for (int m = 0; m < members; ++m) {
+    const double* o = hout + (size_t)m * kReduceComps;
+    const double F = 0.25 * h3 * o[0] + 0.5 * (1.0 - eps[m]) * h3 * o[1] - h * o[2] +
+                     0.5 * o[3] / h;
+    res[4 * m] = F;
+    res[4 * m + 1] = F + 0.5 * h * o[4];
+    res[4 * m + 2] = h3 * o[5];
+    res[4 * m + 3] = h * o[2];
+  }
   return PFC_OK;
+}
+
+int pfc_batch_diagnostics(pfc_ctx* c, double* out) {
+  if (!c || !out) return PFC_EINVAL;
+  c->prof.launches += 2;
+  return diagnostics(c->p.n, c->p.L / c->p.n, c->eps_host, c->nb, c->ring[c->ib],
+                     c->ring[c->ic], c->lap[c->ib], c->lap[c->ic], df_state(&c->p),
+                     c->partials, c->dout, c->hout, c->st, out);
 }
 
 int pfc_diagnostics(pfc_ctx* c, double out[4]) {
   if (!c || !out) return PFC_EINVAL;
-  c->prof.launches += 2;
-  return diagnostics(c->p.n, c->p.L / c->p.n, c->p.eps, c->ring[c->ib], c->ring[c->ic],
-                     c->lap[c->ib], c->lap[c->ic], df_state(&c->p), c->partials, c->dout,
-                     c->hout, c->st, out);
+  if (c->nb == 1) return pfc_batch_diagnostics(c, out);
+  double* all = (double*)malloc(sizeof(double) * 4 * c->nb);
+  if (!all) return PFC_EINVAL;
+  const int rc = pfc_batch_diagnostics(c, all);
+  if (rc == PFC_OK) memcpy(out, all, 4 * sizeof(double));
+  free(all);
+  return rc;
 }
+
+int pfc_batch_status(const pfc_ctx* c, int* iters, double* residual, double* residual0) {
+  if (!c) return PFC_EINVAL;
+  for (int m = 0; m < c->nb; ++m) {
+    if (iters) iters[m] = c->hstate[m].iters;
+    if (residual) residual[m] = c->hstate[m].rms;
+    if (residual0) residual0[m] = c->hstate[m].rms0;
+  }
+  return PFC_OK;
+}
+
+int pfc_batch_members(const pfc_ctx* c) { return c ? c->nb : -1; }
 
 int pfc_energy(pfc_ctx* c, double* F, double* F_modified) {
   double r[4];
@@ -784,6 +888,7 @@ void pfc_destroy(pfc_ctx* c) {
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->hout) cudaFreeHost(c->hout);
   if (c->hstate) cudaFreeHost(c->hstate);
+  free(c->eps_host);
   if (c->prof.created)
     for (int i = 0; i < 2 * Prof::kPool; ++i) cudaEventDestroy(c->prof.ev[i]);
   free(c);
@@ -931,7 +1036,7 @@ static int op_diagnostics(int n, double h, double eps, const double* a, const do
   double* partials = (double*)scratch;
   double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
   double hout[8];
-  return diagnostics(n, h, eps, a, b, nullptr, nullptr, df_fields, partials, dout, hout,
+  return diagnostics(n, h, &eps, 1, a, b, nullptr, nullptr, df_fields, partials, dout, hout,
                      (cudaStream_t)stream, out);
 }
 

@@ -79,9 +79,15 @@ __global__ void k_mu_guess(Lvl L, const double* __restrict__ phig,
 
 // Unscaled 7-point Laplacian of a field (neighbour sum - 6 centre), the
 // quantity the residual kernels store for later reuse.
-__global__ void k_laplacian(int n, const double* __restrict__ v, double* __restrict__ lap) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * n * n) return;
+__global__ void k_laplacian(int n, int members, const double* __restrict__ v,
+                            double* __restrict__ lap) {
+  const int64_t cells = (int64_t)n * n * n;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= cells * members) return;
+  const int64_t off = (t / cells) * cells;     // member after member
+  t -= off;
+  v += off;
+  lap += off;
   int i, j, k;
   cell_of(t, n, i, j, k);
   const Stencil s = stencil_at(i, j, k, n);
@@ -90,14 +96,19 @@ __global__ void k_laplacian(int n, const double* __restrict__ v, double* __restr
 
 // S2, S3 of Eqs. 5.9-5.10 from the stored unscaled Laplacians of b = phi^k
 // and c = phi^{k-1}: the arithmetic of k_source without its two stencils.
-__global__ void k_source_cached(Lvl L, const double* __restrict__ b,
+// Ensembles: `members` fields one after another, member m with (1-eps)/2 at
+// c1m[m] (c1m null: L.c1).
+__global__ void k_source_cached(Lvl L, int members, const double* __restrict__ c1m,
+                                const double* __restrict__ b,
                                 const double* __restrict__ lapb, const double* __restrict__ lapc,
                                 double* __restrict__ S2, double* __restrict__ S3) {
+  const int64_t cells = (int64_t)L.n * L.n * L.n;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)L.n * L.n * L.n) return;
+  if (t >= cells * members) return;
+  const double c1 = c1m ? c1m[t / cells] : L.c1;
   const double lb = L.g * __ldg(lapb + t);
   const double lc = L.g * __ldg(lapc + t);
-  S2[t] = fma(3.0, lb, fma(L.c1, __ldg(b + t), -lc));
+  S2[t] = fma(3.0, lb, fma(c1, __ldg(b + t), -lc));
   S3[t] = 0.5 * lb;
 }
 
@@ -423,10 +434,14 @@ __global__ void k_residual_norm2(Lvl L, const double* __restrict__ phi,
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
 }
 
+// Fixed-order sum of NV-component block partials; one block per ensemble
+// member, member m's sums at out[m * kReduceComps + c].
 template <int NV>
 __global__ void k_reduce_final(const double* __restrict__ partials, int nparts,
                                double* out) {
   __shared__ double sm[32 * NV];
+  partials += (size_t)blockIdx.x * nparts * NV;
+  out += (size_t)blockIdx.x * kReduceComps;
   double acc[NV];
 #pragma unroll
   for (int c = 0; c < NV; ++c) acc[c] = 0.0;
@@ -481,6 +496,9 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
                                      const double* __restrict__ lapb, double* partials) {
   __shared__ double sm[32 * 6];
   const int cells = n * n * n;
+  const size_t off = (size_t)blockIdx.y * cells;     // member of an ensemble
+  a += off, b += off, lapa += off, lapb += off;
+  partials += (size_t)blockIdx.y * gridDim.x * 6;
   double acc[6] = {0, 0, 0, 0, 0, 0};
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
     const double x = __ldg(a + t), la = __ldg(lapa + t);
@@ -502,27 +520,44 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
 // Convergence test of Algorithm 1's loop (RMS residual against the tolerance,
 // NaN, cycle budget) on the device.
 __global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
-                         const double* sum, StepState* s, double inv_3n3, double tol,
-                         int max_iter, int first) {
-  const double rms = sqrt(sum[0] * inv_3n3);
-  if (first) {
-    s->iters = 0;
-    s->rms0 = rms;
-  } else {
-    s->iters += 1;
+                         const double* sum, StepState* s, int members, double inv_3n3,
+                         double tol, int max_iter, int first) {
+  // one thread per ensemble member (sum[m] its sum of squared residuals);
+  // a member that has converged stays converged, and the loop runs while
+  // some member is still running and none has failed
+  const int m = threadIdx.x;
+  int running = 0, failed = 0;
+  if (m < members) {
+    StepState& st = s[m];
+    const double rms = sqrt(sum[m] * inv_3n3);
+    if (first) {
+      st.iters = 0;
+      st.rms0 = rms;
+      st.status = kStepRunning;
+    }
+    if (first || st.status == kStepRunning) {
+      if (!first) st.iters += 1;
+      st.rms = rms;
+      int status;
+      if (rms <= tol)
+        status = kStepConverged;
+      else if (!isfinite(rms))
+        status = kStepNaN;
+      else if (st.iters >= max_iter)
+        status = kStepNoConv;
+      else
+        status = kStepRunning;
+      st.status = status;
+    } else if (st.status == kStepConverged) {
+      st.rms = rms;
+    }
+    running = st.status == kStepRunning;
+    failed = st.status == kStepNaN || st.status == kStepNoConv;
   }
-  s->rms = rms;
-  int status;
-  if (rms <= tol)
-    status = kStepConverged;
-  else if (!isfinite(rms))
-    status = kStepNaN;
-  else if (s->iters >= max_iter)
-    status = kStepNoConv;
-  else
-    status = kStepRunning;
-  s->status = status;
-  if (use_handle) cudaGraphSetConditional(handle, status == kStepRunning ? 1u : 0u);
+  running = __syncthreads_or(running);
+  failed = __syncthreads_or(failed);
+  if (use_handle && threadIdx.x == 0)
+    cudaGraphSetConditional(handle, (running && !failed) ? 1u : 0u);
 }
 
 inline int reduce_blocks(int64_t cells) {
@@ -540,24 +575,28 @@ cudaError_t launch_guess(const Lvl& L, const double* b, const double* c, double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t st) {
-  k_laplacian<<<grid_for((int64_t)n * n * n), kThreads, 0, st>>>(n, v, lap);
+cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t st,
+                             int members) {
+  k_laplacian<<<grid_for((int64_t)n * n * n * members), kThreads, 0, st>>>(n, members, v, lap);
   return cudaGetLastError();
 }
 
 cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* lapb,
-                                 const double* lapc, double* S2, double* S3, cudaStream_t st) {
-  k_source_cached<<<grid_for((int64_t)L.n * L.n * L.n), kThreads, 0, st>>>(L, b, lapb, lapc,
-                                                                           S2, S3);
+                                 const double* lapc, double* S2, double* S3, cudaStream_t st,
+                                 int members, const double* c1m) {
+  k_source_cached<<<grid_for((int64_t)L.n * L.n * L.n * members), kThreads, 0, st>>>(
+      L, members, c1m, b, lapb, lapc, S2, S3);
   return cudaGetLastError();
 }
 
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
-                                      double* out, cudaStream_t st) {
-  const int nb = reduce_blocks((int64_t)n * n * n);
-  k_diagnostics_cached<<<nb, kReduceThreads, 0, st>>>(n, a, b, lapa, lapb, partials);
-  k_reduce_final<6><<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+                                      double* out, cudaStream_t st, int members) {
+  int nb = reduce_blocks((int64_t)n * n * n * members) / members;
+  if (nb < 1) nb = 1;
+  k_diagnostics_cached<<<dim3(nb, members), kReduceThreads, 0, st>>>(n, a, b, lapa, lapb,
+                                                                     partials);
+  k_reduce_final<6><<<members, kReduceThreads, 0, st>>>(partials, nb, out);
   return cudaGetLastError();
 }
 
@@ -697,8 +736,10 @@ cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double*
 
 cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
                           const double* sum, StepState* state, double inv_3n3, double tol,
-                          int max_iter, int first, cudaStream_t st) {
-  k_decide<<<1, 1, 0, st>>>(handle, use_handle, sum, state, inv_3n3, tol, max_iter, first);
+                          int max_iter, int first, cudaStream_t st, int members) {
+  const int threads = ((members + 31) / 32) * 32;
+  k_decide<<<1, threads, 0, st>>>(handle, use_handle, sum, state, members, inv_3n3, tol,
+                                  max_iter, first);
   return cudaGetLastError();
 }
 

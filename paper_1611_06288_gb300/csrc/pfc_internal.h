@@ -37,11 +37,13 @@ struct StepState {
 };
 constexpr int kStepRunning = 0, kStepConverged = 1, kStepNaN = 2, kStepNoConv = 3;
 
-// From the reduced sum of squared residuals at sum[0]: update *state and,
-// if use_handle, set the WHILE condition of the step graph to "keep going".
+// From the reduced sums of squared residuals sum[m] of `members` ensemble
+// members (1 for a single problem): update state[m] (a converged member stays
+// converged) and, if use_handle, set the WHILE condition of the step graph to
+// "keep going" while some member runs and none has failed.
 cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
                           const double* sum, StepState* state, double inv_3n3, double tol,
-                          int max_iter, int first, cudaStream_t st);
+                          int max_iter, int first, cudaStream_t st, int members = 1);
 
 // Detail string returned by pfc_last_error() on this host thread.
 void set_last_error(const char* msg);
@@ -109,14 +111,16 @@ cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double*
                                   const double* S3, const double* b, double* partials,
                                   double* out, cudaStream_t st, double* lap = nullptr);
 // Unscaled 7-point Laplacian (neighbour sum - 6 centre) of a field.
-cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t st);
+cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t st,
+                             int members = 1);
 // S2, S3 from b and the stored unscaled Laplacians of b and c.
 cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* lapb,
-                                 const double* lapc, double* S2, double* S3, cudaStream_t st);
+                                 const double* lapc, double* S2, double* S3, cudaStream_t st,
+                                 int members = 1, const double* c1m = nullptr);
 // launch_diagnostics from the stored unscaled Laplacians of a and b.
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
-                                      double* out, cudaStream_t st);
+                                      double* out, cudaStream_t st, int members = 1);
 // out[0..5] = sum a^4, sum a^2, sum |D a|^2 (faces), sum (Lap a)^2 (times h^4
 // removed: raw stencil sums), sum |D(a-b)|^2, sum a.  Raw sums; the host scales.
 cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,

@@ -69,13 +69,6 @@ inline LvlF to_f32(const Lvl& L) {
   return f;
 }
 
-__device__ __forceinline__ void cell_of(int64_t t, int n, int& i, int& j, int& k) {
-  i = (int)(t % n);
-  const int64_t r = t / n;
-  j = (int)(r % n);
-  k = (int)(r / n);
-}
-
 // ---------------------------------------------------------------------------
 // Colour-split layout of the FP32 fields.  Within every x-row (j, k) of an
 // even-sized level the n/2 cells of colour 0 ((i+j+k) even) come first,
@@ -85,6 +78,16 @@ __device__ __forceinline__ void cell_of(int64_t t, int n, int& i, int& j, int& k
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int split_index(int i, int j, int k, int n) {
   return (k * n + j) * n + ((i + j + k) & 1) * (n >> 1) + (i >> 1);
+}
+
+// Batched launches (ensembles of independent members of one grid size, stored
+// member after member): the grid's z extent covers members x planes.  Returns
+// the member of this block and reduces z to its plane; a single-member
+// launch has member 0.
+__device__ __forceinline__ int member_of(int& z, int planes) {
+  const int m = z / planes;
+  z -= m * planes;
+  return m;
 }
 
 // The cell (p, j, k) of colour `colour` (i = 2p + ((j+k+colour) & 1)) and its six
@@ -206,24 +209,32 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
                                                   const double* __restrict__ b,
                                                   float* __restrict__ r1, float* __restrict__ r2,
                                                   float* __restrict__ r3, float* __restrict__ q,
-                                                  double* partials, double* __restrict__ lap) {
+                                                  double* partials, double* __restrict__ lap,
+                                                  const double* __restrict__ c1m) {
   __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
+  const int m = blockIdx.y;                  // member of a batched launch
+  const size_t off = (size_t)m * cells;
+  phi += off, mu += off, om += off, S1 += off, S2 += off, S3 += off, b += off;
+  r1 += off, r2 += off, r3 += off, q += off;
+  if (lap) lap += off;
+  partials += (size_t)m * gridDim.x;
+  const double c1 = c1m ? c1m[m] : L.c1;
   float acc = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
     const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
     const Nb6 s = nb6_at(t, i, j, k, n);
-    const double p = __ldg(phi + t), m = __ldg(mu + t), w = __ldg(om + t);
+    const double p = __ldg(phi + t), mm = __ldg(mu + t), w = __ldg(om + t);
     const double bb = __ldg(b + t);
-    const double lmu = fma(-6.0, m, nbsum64(mu, s));
+    const double lmu = fma(-6.0, mm, nbsum64(mu, s));
     const double lom = fma(-6.0, w, nbsum64(om, s));
     const double lphi = fma(-6.0, p, nbsum64(phi, s));
     const double p2 = p * p, b2 = bb * bb, pb = p * bb;
     const double f = 0.25 * ((p + bb) * (p2 + b2));          // f(phi, b), Eq. 5.2
     const double fp = fma(0.75, p2, fma(0.5, pb, 0.25 * b2));  // df/dphi
     const double x = __ldg(S1 + t) - fma(-L.tg, lmu, p);
-    const double y = __ldg(S2 + t) - (fma(-L.c1, p, m - f) - L.g * lom);
+    const double y = __ldg(S2 + t) - (fma(-c1, p, mm - f) - L.g * lom);
     const double z = __ldg(S3 + t) - fma(-L.gh, lphi, w);
     const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
     acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
@@ -231,7 +242,7 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
     r1[o] = xf;
     r2[o] = yf;
     r3[o] = zf;
-    q[o] = d2f_rn(fp + L.c1);
+    q[o] = d2f_rn(fp + c1);
     if (lap) lap[t] = lphi;
   }
   acc = block_sum_f(acc, sm);
@@ -569,12 +580,15 @@ __global__ void k_df_to_f64(int64_t count, const float2* y, double* x) {
   x[t] = df_to_double(y[t]);
 }
 
+// Fixed-order sum of each member's partials (one block per member): out[m].
 __global__ void k_reduce1(const double* __restrict__ partials, int nparts, double* out) {
   __shared__ double sm[32];
+  const int m = blockIdx.x;
+  partials += (size_t)m * nparts;
   double acc[1] = {0.0};
   for (int p = threadIdx.x; p < nparts; p += blockDim.x) acc[0] += partials[p];
   block_sum<1>(acc, sm);
-  if (threadIdx.x == 0) out[0] = acc[0];
+  if (threadIdx.x == 0) out[m] = acc[0];
 }
 
 // 8-cell average of a split-layout field onto the (split-layout) level n/2.
@@ -582,9 +596,12 @@ __global__ void k_restrict32(int n, const float* __restrict__ f, float* __restri
   pdl_wait();
   pdl_trigger();
   const int nc = n >> 1;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
-            K = blockIdx.z;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  int K = blockIdx.z;
+  const int m = member_of(K, nc);
   if (I >= nc || J >= nc) return;
+  f += (size_t)m * n * n * n;
+  c += (size_t)m * nc * nc * nc;
   float acc = 0.f;
 #pragma unroll
   for (int s = 0; s < 8; ++s)
@@ -620,9 +637,11 @@ __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* 
   pdl_wait();
   pdl_trigger();
   const int n = L.n, half = n >> 1;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
-            k = blockIdx.z;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  const size_t off = (size_t)member_of(k, n) * n * n * n;
   if (p >= half || j >= n) return;
+  d1 += off, d2 += off, d3 += off, r1 += off, r2 += off, r3 += off, q += off;
   const Stencil s = split_stencil(p, j, k, colour, n);
   float sp = 0.f, sm_ = 0.f, sw = 0.f;
   if (!ZERO) {
@@ -650,9 +669,12 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
   pdl_wait();
   pdl_trigger();
   const int n = L.n, half = n >> 1;
-  const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
-            k = blockIdx.z;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  const size_t off = (size_t)member_of(k, n) * n * n * n;
   if (x >= n || j >= n) return;
+  d1 += off, d2 += off, d3 += off, t1 += off, t2 += off, t3 += off;
+  r1 += off, r2 += off, r3 += off, q += off;
   const int colour = x >= half;
   const Stencil s = split_stencil(x - colour * half, j, k, colour, n);
   float sp = 0.f, sm_ = 0.f, sw = 0.f, p0 = 0.f, m0 = 0.f, w0 = 0.f;
@@ -765,9 +787,13 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   pdl_wait();
   pdl_trigger();
   const int n = L.n, nc = n >> 1;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
-            K = blockIdx.z;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  int K = blockIdx.z;
+  const int m = member_of(K, nc);
   if (I >= nc || J >= nc) return;
+  const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
+  d1 += off, d2 += off, d3 += off, r1 += off, r2 += off, r3 += off, q += off;
+  c1 += offc, c2 += offc, c3 += offc;
   int in[8], out[24];
   block_indices(I, J, K, n, in, out);
   float a1 = 0.f, a2 = 0.f, a3 = 0.f;
@@ -809,9 +835,12 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
   pdl_wait();
   pdl_trigger();
   const int nc = n >> 1, half = n >> 1, hc = nc >> 1;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y,
-            K = blockIdx.z;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
+  int K = blockIdx.z;
+  const int m = member_of(K, nc);
   if (I >= nc || J >= nc) return;
+  const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
+  e1 += offc, e2 += offc, e3 += offc, d1 += off, d2 += off, d3 += off;
   const int Is[3] = {(I == 0) ? nc - 1 : I - 1, I, (I + 1 == nc) ? 0 : I + 1};
   const int Js[3] = {(J == 0) ? nc - 1 : J - 1, J, (J + 1 == nc) ? 0 : J + 1};
   const int Ks[3] = {(K == 0) ? nc - 1 : K - 1, K, (K + 1 == nc) ? 0 : K + 1};
@@ -868,6 +897,9 @@ __global__ void k_lin_coarse_solve32(LvlF L, int kind, float w, int max_sweeps, 
   __shared__ int done;
   const int n = L.n, half = n >> 1;
   const int cells = n * n * n, ccells = half * n * n;
+  const size_t off = (size_t)blockIdx.x * cells;     // one block per member
+  d1 += off, d2 += off, d3 += off, t1 += off, t2 += off, t3 += off;
+  r1 += off, r2 += off, r3 += off, q += off;
   for (int t = threadIdx.x; t < cells; t += blockDim.x) {
     d1[t] = 0.f;
     d2[t] = 0.f;
@@ -1299,6 +1331,15 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
   __shared__ int done;
   const bool zero_top = P.zero_init != 0;
   {
+    // one block per member of a batched launch
+    const size_t off = (size_t)blockIdx.x * P.L[0].n * P.L[0].n * P.L[0].n;
+    for (int c = 0; c < 3; ++c) {
+      P.gd[c] += off;
+      P.gr[c] += off;
+    }
+    P.gq += off;
+  }
+  {
     const SLev S0 = slev(smem, P, 0);
     const int n0 = P.L[0].n;
     const int cells = n0 * n0 * n0;
@@ -1351,9 +1392,11 @@ __global__ void k_correct64(int n, double* __restrict__ u1, double* __restrict__
                             const float* __restrict__ d2, const float* __restrict__ d3) {
   pdl_wait();
   pdl_trigger();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
-            k = blockIdx.z;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  const size_t off = (size_t)member_of(k, n) * n * n * n;
   if (i >= n || j >= n) return;
+  u1 += off, u2 += off, u3 += off, d1 += off, d2 += off, d3 += off;
   const int t = (k * n + j) * n + i;
   const int o = split_index(i, j, k, n);
   u1[t] += f2d(__ldg(d1 + o));
@@ -1407,15 +1450,16 @@ struct Ctx32 {
   int jfactor0;                // the same on the finest level
   cudaStream_t st;
   Prof* pr;
+  int nb = 1;                  // members of a batched ensemble (fields member after member)
 };
 
 // `sweeps` damped Jacobi sweeps d -> t -> d ...; the result ends in d.
 cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* const* d,
                      float* const* t, float* const* r, const float* q, cudaStream_t st,
-                     bool pdl) {
+                     bool pdl, int nb = 1) {
   const int n = L.n;
-  const int64_t cells = (int64_t)n * n * n;
-  const Launch3 g = launch3(n, n, n);
+  const int64_t cells = (int64_t)n * n * n * nb;
+  const Launch3 g = launch3(n, n, n * nb);
   float* src[3] = {d[0], d[1], d[2]};
   float* dst[3] = {t[0], t[1], t[2]};
   int done = 0;
@@ -1439,7 +1483,6 @@ cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* 
 
 cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   const LvlF& L = c.L[l];
-  const int64_t work = (int64_t)(L.n / 2) * L.n * L.n;
   float* const* d = c.mx->d[l];
   float* const* r = c.mx->r[l];
   const float* q = c.mx->q[l];
@@ -1447,11 +1490,12 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
   if (c.kind[l] == PFC_SWEEP_JACOBI) {
     const int js = sweeps * (l == 0 ? c.jfactor0 : c.jfactor);
-    cudaError_t e = jacobi32(L, js, c.w, zero_init, d, c.mx->t[l], r, q, c.st, c.pr == nullptr);
+    cudaError_t e =
+        jacobi32(L, js, c.w, zero_init, d, c.mx->t[l], r, q, c.st, c.pr == nullptr, c.nb);
     prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
     return e;
   }
-  const Launch3 g = launch3(L.n / 2, L.n, L.n);
+  const Launch3 g = launch3(L.n / 2, L.n, L.n * c.nb);
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < sweeps && e == cudaSuccess; ++s) {
     for (int colour = 0; colour < 2 && e == cudaSuccess; ++colour) {
@@ -1495,7 +1539,8 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
     attr_set = true;
   }
   prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
-  cudaError_t e = launch_k(c.pr == nullptr, k_lin_tail32, dim3(1), dim3(kTailThreads), smem, c.st, P);
+  cudaError_t e =
+      launch_k(c.pr == nullptr, k_lin_tail32, dim3(c.nb), dim3(kTailThreads), smem, c.st, P);
   prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
   return e;
 }
@@ -1513,7 +1558,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
     int threads = ((work + 31) / 32) * 32;
     if (threads > 1024) threads = 1024;
     prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
-    k_lin_coarse_solve32<<<1, threads, 0, c.st>>>(
+    k_lin_coarse_solve32<<<c.nb, threads, 0, c.st>>>(
         L, c.kind[l], c.w, 400, mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.t[l][0], mx.t[l][1],
         mx.t[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l]);
     prof_end(c.pr, PFC_K_LIN_COARSE, l, 1, c.st);
@@ -1526,7 +1571,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   if (c.p->nu1 > 0) e = smooth32(c, l, c.p->nu1, zero_init);
   if (e != cudaSuccess) return e;
   const int nc = L.n / 2;
-  const Launch3 gr = launch3(nc, nc, nc);
+  const Launch3 gr = launch3(nc, nc, nc * c.nb);
   prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
   e = launch_k(c.pr == nullptr,
                dzero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
@@ -1536,7 +1581,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
   if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
-  const Launch3 gp = launch3(nc, nc, nc);
+  const Launch3 gp = launch3(nc, nc, nc * c.nb);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
   e = launch_k(c.pr == nullptr, dzero ? k_prolong_add32<true> : k_prolong_add32<false>,
                gp.grid, gp.block, 0, c.st, L.n,
@@ -1553,17 +1598,23 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
                             float* q, double* partials, double* out, cudaStream_t st,
-                            double* lap) {
-  const int nb = wave_blocks(k_defect64, (int64_t)L.n * L.n * L.n);
-  k_defect64<<<nb, kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q,
-                                            partials, lap);
-  k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+                            double* lap, int members, const double* c1m) {
+  // one resident wave over all members: blocks per member = wave / members
+  const int wave = wave_blocks(k_defect64, (int64_t)L.n * L.n * L.n * members);
+  int nbx = wave / members;
+  const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
+  if (nbx > need) nbx = (int)need;
+  if (nbx < 1) nbx = 1;
+  k_defect64<<<dim3(nbx, members), kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1,
+                                                            r2, r3, q, partials, lap, c1m);
+  k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, nbx, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
-                             const float* d2, const float* d3, cudaStream_t st, bool pdl) {
-  const Launch3 g = launch3(n, n, n);
+                             const float* d2, const float* d3, cudaStream_t st, bool pdl,
+                             int members) {
+  const Launch3 g = launch3(n, n, n * members);
   return launch_k(pdl, k_correct64, g.grid, g.block, 0, st, n, u1, u2, u3, d1, d2, d3);
 }
 
@@ -1714,10 +1765,12 @@ cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const f
 
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
-                                 double* dout, cudaStream_t st, Prof* pr, double* lap) {
+                                 double* dout, cudaStream_t st, Prof* pr, double* lap,
+                                 int members, const double* c1m) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
-                                  mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap);
+                                  mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap,
+                                  members, c1m);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
@@ -1737,8 +1790,9 @@ namespace {
 // q restricted to every level, then p.inner_cycles FP32 V-cycles on J d = r
 // from d = 0 (the part of a correction shared by both outer precisions).
 cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int* sizes,
-                          cudaStream_t st, Prof* pr) {
+                          cudaStream_t st, Prof* pr, int members) {
   Ctx32 c;
+  c.nb = members;
   c.mx = &mx;
   c.p = &p;
   c.nl = nl;
@@ -1755,7 +1809,7 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
   }
   cudaError_t e = cudaSuccess;
   for (int l = 1; l < nl && e == cudaSuccess; ++l) {
-    const Launch3 g = launch3(sizes[l], sizes[l], sizes[l]);
+    const Launch3 g = launch3(sizes[l], sizes[l], sizes[l] * members);
     prof_begin(pr, PFC_K_RESTRICT, st);
     e = launch_k(pr == nullptr, k_restrict32, g.grid, g.block, 0, st, sizes[l - 1],
                  mx.q[l - 1], mx.q[l]);
@@ -1769,12 +1823,12 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
 
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, double* const u[3], cudaStream_t st,
-                                     Prof* pr) {
-  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr);
+                                     Prof* pr, int members) {
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, members);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,
-                         pr == nullptr);
+                         pr == nullptr, members);
     prof_end(pr, PFC_K_CORRECT, 0, 1, st);
   }
   return e;
@@ -1783,7 +1837,7 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr) {
-  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr);
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, 1);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct_df(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,

@@ -37,11 +37,13 @@ struct MixedBufs {
   float* q[kMaxLevelsMixed];      // frozen cubic-term Jacobian + (1-eps)/2
 };
 
+// The FP32 hierarchy of `members` ensemble members: each level's fields hold
+// the members one after another.
 template <class Take>
-void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
+void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take, int members = 1) {
   (void)n;
   for (int l = 0; l < nl; ++l) {
-    const size_t m3 = (size_t)sizes[l] * sizes[l] * sizes[l];
+    const size_t m3 = (size_t)sizes[l] * sizes[l] * sizes[l] * members;
     for (int c = 0; c < 3; ++c) mx->d[l][c] = take(m3);
     for (int c = 0; c < 3; ++c) mx->t[l][c] = take(m3);
     for (int c = 0; c < 3; ++c) mx->r[l][c] = take(m3);
@@ -51,9 +53,12 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take) {
 
 // Defect r = S - N(u) of the FP64 state (PFC_MIXED) -> FP32 r and q on
 // level 0, and the FP64 sum of |r|^2 at dout[0] (two launches).
+// With `members` > 1 the fields hold an ensemble member after member, each
+// member's (1-eps)/2 at c1m[m] and its sum at dout[m].
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
-                                 double* dout, cudaStream_t st, Prof* pr, double* lap);
+                                 double* dout, cudaStream_t st, Prof* pr, double* lap,
+                                 int members = 1, const double* c1m = nullptr);
 
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
@@ -66,7 +71,7 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3
 // FP64 (PFC_MIXED) or double-float (PFC_MIXED_DF).
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, double* const u[3], cudaStream_t st,
-                                     Prof* pr);
+                                     Prof* pr, int members = 1);
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr);
@@ -109,10 +114,11 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
                             float* q, double* partials, double* out, cudaStream_t st,
-                            double* lap = nullptr);
+                            double* lap = nullptr, int members = 1,
+                            const double* c1m = nullptr);
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
                              const float* d2, const float* d3, cudaStream_t st,
-                             bool pdl = true);
+                             bool pdl = true, int members = 1);
 cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,
                              const float2* om, const float2* S1, const float2* S2,
                              const float2* S3, const float2* b, float* r1, float* r2, float* r3,

@@ -1,0 +1,87 @@
+"""Batched ensemble run (the ensemble workload: independent runs with grids
+drawn from {32^3, 48^3, 64^3}, their own eps and initial fields, dt = 0.05,
+100 steps each), advanced one PFCBatch per grid size, against the same runs
+made one after another through single contexts.
+
+    python -m paper_1611_06288_gb300.ensemble [--count 96] [--steps 100] [--sequential]
+
+Prints one JSON line: member-steps per second batched (and sequential when
+asked), the corrections per step and the largest final residual per group.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import workloads as W
+from .solver import PFCBatch, PFCSolver
+
+
+def _timed(fn):
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    out = fn()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3, out
+
+
+def run(count=96, steps=100, sequential=False, L=32.0, dt=0.05, tol=1e-9, warmup=2):
+    groups = W.ensemble(count, L=L, dt=dt, steps=steps)
+    kw = dict(W.ENSEMBLE_SETTINGS, tol=tol, max_cycles=100)
+    out = {"count": count, "steps": steps, "L": L, "dt": dt, "tol": tol,
+           "groups": {n: len(e) for n, (e, _) in groups.items()}, "settings": W.ENSEMBLE_SETTINGS}
+    total = 0.0
+    per_group = {}
+    for n, (eps, phi0) in groups.items():
+        b = PFCBatch(n, L, eps, dt, phi0, **kw)
+        b.step(warmup)                      # builds the step graphs
+        b.close()
+        b = PFCBatch(n, L, eps, dt, phi0, **kw)
+
+        def go():
+            cyc = 0
+            for _ in range(steps):
+                cyc += b.step(1).cycles_last
+            return cyc
+
+        t, cyc = _timed(go)
+        _, res, _ = b.status()
+        per_group[n] = {"members": len(eps), "seconds": t, "corrections_per_step": cyc / steps,
+                        "max_final_residual": max(res)}
+        total += t
+        b.close()
+    out["batched"] = {"member_steps_per_s": count * steps / total, "seconds": total,
+                      "per_group": per_group}
+    if sequential:
+        tot = 0.0
+        for n, (eps, phi0) in groups.items():
+            for m in range(len(eps)):
+                s = PFCSolver(n, L, eps[m], dt, phi0[m], precision="mixed", **kw)
+                s.step(warmup)
+                s.set_state(phi0[m])
+                t, _ = _timed(lambda: s.step(steps))
+                tot += t
+                s.close()
+        out["sequential"] = {"member_steps_per_s": count * steps / tot, "seconds": tot}
+        out["batched_over_sequential"] = out["batched"]["member_steps_per_s"] / (
+            out["sequential"]["member_steps_per_s"])
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--count", type=int, default=96)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--sequential", action="store_true")
+    a = ap.parse_args()
+    print(json.dumps(run(a.count, a.steps, a.sequential)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

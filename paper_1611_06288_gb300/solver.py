@@ -154,3 +154,78 @@ class PFCSolver:
             self.close()
         except Exception:
             pass
+
+
+class PFCBatch:
+    """An ensemble of independent runs of one grid size, box and time step,
+    each with its own eps and initial field, advanced together (PFC_MIXED:
+    every kernel launch covers all members).
+
+    phi0: array or tensor of shape (members, n, n, n).
+    """
+
+    def __init__(self, n, L, eps, dt, phi0, device="cuda", stream=None, **solver_kw):
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise RuntimeError("PFCBatch runs on a CUDA device only")
+        self.eps = [float(e) for e in eps]
+        self.members = len(self.eps)
+        self.n, self.L, self.dt = int(n), float(L), float(dt)
+        solver_kw.setdefault("precision", "mixed")
+        self.params = make_params(n, L, self.eps[0], dt, **solver_kw)
+        nbytes = B.pfc_batch_workspace_bytes(self.params, self.members)
+        if nbytes == 0:
+            raise B.PFCError(B.PFC_EINVAL, "pfc_batch_workspace_bytes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if isinstance(phi0, np.ndarray):
+            phi0 = torch.from_numpy(np.ascontiguousarray(phi0, dtype=np.float64))
+        p0 = phi0.to(device=self.device, dtype=torch.float64).contiguous()
+        if tuple(p0.shape) != (self.members, self.n, self.n, self.n):
+            raise ValueError(f"phi0 must have shape {(self.members,) + (self.n,) * 3}")
+        with torch.cuda.stream(self.stream):
+            self.ctx = B.pfc_batch_init(self.params, self.eps, self.workspace, p0,
+                                        self.stream.cuda_stream)
+        self.stream.synchronize()
+
+    def step(self, nsteps: int = 1) -> B.pfc_step_stats:
+        return B.pfc_step(self.ctx, nsteps)
+
+    def _field(self, getter) -> torch.Tensor:
+        out = torch.empty((self.members,) + (self.n,) * 3, dtype=torch.float64,
+                          device=self.device)
+        getter(self.ctx, out)
+        self.stream.synchronize()
+        return out
+
+    def phi(self) -> torch.Tensor:
+        return self._field(B.pfc_get_phi)
+
+    def mu(self) -> torch.Tensor:
+        return self._field(B.pfc_get_mu)
+
+    def omega(self) -> torch.Tensor:
+        return self._field(B.pfc_get_omega)
+
+    def diagnostics(self) -> list[dict]:
+        return [{"energy": F, "modified_energy": Fm, "mass": m, "grad_sq": g}
+                for F, Fm, m, g in B.pfc_batch_diagnostics(self.ctx, self.members)]
+
+    def status(self):
+        """(corrections, final RMS residual, initial RMS residual) per member
+        of the last step."""
+        return B.pfc_batch_status(self.ctx, self.members)
+
+    def use_graphs(self, on: bool = True) -> None:
+        B.pfc_use_graphs(self.ctx, on)
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None) is not None:
+            B.pfc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -192,3 +192,31 @@ def growth(n: int = 128, steps: int = 10000, tol: float = 1e-9):
 def cosine_table(n: int, dt: float = 1e-3, steps: int = 10, tol: float = 1e-8):
     """Section 6.1 multigrid-complexity setting: [0, 3.2]^3, eps = 0.025."""
     return Workload(f"cosine{n}", n, 3.2, 0.025, dt, steps, tol)
+
+
+def ensemble(count: int = 96, sizes=(32, 48, 64), L: float = 32.0, dt: float = 0.05,
+             steps: int = 100, seed: int = DEFAULT_SEED):
+    """Batched-ensemble workload: `count` independent runs with grids drawn
+    from `sizes`, eps ~ U[0.02, 0.3], phi0 = m + 0.05 U(-1, 1) per cell with
+    the mean m ~ U[-0.3, 0.1], dt = 0.05, `steps` steps, on a box of side L
+    (the same for every size).  Returns {n: (eps list, phi0 array of shape
+    (members, n, n, n))} grouped by grid size, members in draw order.
+
+    Mixed-path settings (finest levels in the damped-Jacobi regime at
+    dt = 0.05, 108 dt/h^6 = 5.4-346): V(1,2), three cycles per correction."""
+    rng = np.random.default_rng(seed)
+    picks = rng.choice(len(sizes), size=count)
+    eps = rng.uniform(0.02, 0.3, count)
+    means = rng.uniform(-0.3, 0.1, count)
+    groups = {}
+    for m in range(count):
+        n = int(sizes[picks[m]])
+        phi = means[m] + 0.05 * rng.uniform(-1.0, 1.0, (n, n, n))
+        groups.setdefault(n, ([], []))
+        groups[n][0].append(float(eps[m]))
+        groups[n][1].append(phi)
+    return {n: (e, np.ascontiguousarray(np.stack(f))) for n, (e, f) in sorted(groups.items())}
+
+
+ENSEMBLE_SETTINGS = {"nu1": 1, "nu2": 2, "inner_cycles": 3, "jacobi_factor": 3,
+                     "coarse_sweeps": 2}

@@ -103,3 +103,22 @@ def test_validation_errors_without_gpu(libpfc):
     assert libpfc.pfc_op_smooth(5, 1.0, 0.1, 0.1, 0, 1, *([None] * 7), None) == B.PFC_EINVAL
     for code in (0, -1, -2, -3, -4, -5):
         assert B.strerror(code)
+
+
+def test_batch_workspace(libpfc):
+    """Ensemble workspaces: per-member fields and FP32 hierarchy scale with the
+    member count; more than one member needs PFC_MIXED."""
+    p = B.pfc_default_params()
+    p.n, p.L, p.eps, p.dt = 32, 32.0, 0.1, 0.05
+    p.precision = B.PFC_MIXED
+    one = B.pfc_batch_workspace_bytes(p, 1)
+    assert one == B.pfc_workspace_bytes(p)
+    four = B.pfc_batch_workspace_bytes(p, 4)
+    # 10 fine FP64 fields and at least the 10 FP32 fields of the finest level per member
+    assert four - one >= 3 * (10 * 8 + 10 * 4) * 32 ** 3
+    assert B.pfc_batch_workspace_bytes(p, 0) == 0
+    assert B.pfc_batch_workspace_bytes(p, 1025) == 0
+    p.precision = B.PFC_FP64
+    assert B.pfc_batch_workspace_bytes(p, 2) == 0
+    p.precision = B.PFC_MIXED_DF
+    assert B.pfc_batch_workspace_bytes(p, 2) == 0
