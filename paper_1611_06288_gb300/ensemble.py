@@ -4,6 +4,7 @@ drawn from {32^3, 48^3, 64^3}, their own eps and initial fields, dt = 0.05,
 made one after another through single contexts.
 
     python -m paper_1611_06288_gb300.ensemble [--count 96] [--steps 100] [--sequential]
+                                              [--autotune]
 
 Prints one JSON line: member-steps per second batched (and sequential when
 asked), the corrections per step and the largest final residual per group.
@@ -31,18 +32,25 @@ def _timed(fn):
     return a.elapsed_time(b) / 1e3, out
 
 
-def run(count=96, steps=100, sequential=False, L=32.0, dt=0.05, tol=1e-9, warmup=2):
+def run(count=96, steps=100, sequential=False, L=32.0, dt=0.05, tol=1e-9, warmup=2,
+        autotune=False):
     groups = W.ensemble(count, L=L, dt=dt, steps=steps)
     kw = dict(W.ENSEMBLE_SETTINGS, tol=tol, max_cycles=100)
+    tuned = {}
+    if autotune:
+        from .autotune import tune
+        for n, (eps, phi0) in groups.items():
+            tuned[n], _ = tune(n, L, eps, dt, phi0, tol=tol)
     out = {"count": count, "steps": steps, "L": L, "dt": dt, "tol": tol,
            "groups": {n: len(e) for n, (e, _) in groups.items()}, "settings": W.ENSEMBLE_SETTINGS}
     total = 0.0
     per_group = {}
     for n, (eps, phi0) in groups.items():
-        b = PFCBatch(n, L, eps, dt, phi0, **kw)
+        gkw = dict(kw, **tuned.get(n, {}))
+        b = PFCBatch(n, L, eps, dt, phi0, **gkw)
         b.step(warmup)                      # builds the step graphs
         b.close()
-        b = PFCBatch(n, L, eps, dt, phi0, **kw)
+        b = PFCBatch(n, L, eps, dt, phi0, **gkw)
 
         def go():
             cyc = 0
@@ -53,7 +61,7 @@ def run(count=96, steps=100, sequential=False, L=32.0, dt=0.05, tol=1e-9, warmup
         t, cyc = _timed(go)
         _, res, _ = b.status()
         per_group[n] = {"members": len(eps), "seconds": t, "corrections_per_step": cyc / steps,
-                        "max_final_residual": max(res)}
+                        "max_final_residual": max(res), "settings": tuned.get(n, W.ENSEMBLE_SETTINGS)}
         total += t
         b.close()
     out["batched"] = {"member_steps_per_s": count * steps / total, "seconds": total,
@@ -79,8 +87,10 @@ def main():
     ap.add_argument("--count", type=int, default=96)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--sequential", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="choose each group's cycle settings with autotune.tune first")
     a = ap.parse_args()
-    print(json.dumps(run(a.count, a.steps, a.sequential)), flush=True)
+    print(json.dumps(run(a.count, a.steps, a.sequential, autotune=a.autotune)), flush=True)
 
 
 if __name__ == "__main__":

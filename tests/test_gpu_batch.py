@@ -79,3 +79,19 @@ def test_batch_validation():
         PFCBatch(16, 32.0, [0.1, 1.5], 0.05, phi0)          # eps >= 1
     with pytest.raises(ValueError):
         PFCBatch(16, 32.0, eps, 0.05, phi0[:1])
+
+
+def test_autotune_picks_a_converging_setting():
+    """The autotuner on a 32^3 ensemble returns one of its candidates, and a
+    batch built with it converges."""
+    from paper_1611_06288_gb300.autotune import tune
+    eps, phi0 = members(32, 3, 7)
+    space = {"nu": [(0, 1), (1, 2)], "inner_cycles": [2], "jacobi_factor": [3],
+             "coarse_sweeps": [2]}
+    best, table = tune(32, 32.0, eps, 0.05, phi0, space=space, steps=2, warmup=1)
+    assert best in [kw for kw, _ in table] and len(table) == 2
+    b = PFCBatch(32, 32.0, eps, 0.05, phi0, tol=1e-9, **best)
+    b.step(2)
+    _, res, _ = b.status()
+    assert max(res) <= 1e-9
+    b.close()
