@@ -390,6 +390,30 @@ int pfc_batch_diagnostics(pfc_ctx* c, double* out);
 int pfc_batch_status(const pfc_ctx* c, int* iters, double* residual, double* residual0);
 
 /* ------------------------------------------------------------------------
+ * Discrete adjoint of one time step (gradients through the scheme).  Step k
+ * solves F(u; b, c, eps) = N(u; b) - S(b, c) = 0 for u = (phi^{k+1}, mu,
+ * omega) (Eqs. 5.4-5.10); given dL/dphi^{k+1} = d_gnext, the implicit
+ * function theorem gives psi from J^T psi = (d_gnext, 0, 0), J = dF/du at
+ * the solution, and
+ *   d_gk    += -(dF/db)^T psi = psi1 + (df/db + (1-eps)/2) psi2 + 3 Lap psi2
+ *              + Lap psi3 / 2,   df/db = (a^2 + 2ab + 3b^2)/4
+ *   d_gkm1  += -(dF/dc)^T psi = -Lap psi2
+ *   *eps_bar += -(dF/deps)^T psi = -sum psi2 (a + b) / 2
+ * with a = phi^{k+1} (d_phi_next) and b = phi^k (d_phi_k).  d_gkm1 may equal
+ * d_gk (the first step, phi^{-1} := phi^0).  Because J^T = S P J P S^-1 (P
+ * swaps the phi and mu components, S = diag(1, 1, 2)), the transposed system
+ * is solved as J z = (0, d_gnext, 0), psi = (z2, z1, 2 z3), by the context's
+ * own FP64 defect correction around FP32 V-cycles with q = f'(a, b) +
+ * (1-eps)/2, until the RMS residual is <= rtol times its initial value
+ * (PFC_ENOCONV after max_cycles corrections).  Needs a PFC_MIXED context of
+ * one member (its FP32 hierarchy and reduction scratch are used, its state
+ * is not touched); d_z: 3 n^3 doubles of scratch.  Blocking; *cycles (may be
+ * NULL) receives the corrections used. */
+int pfc_adjoint_step(pfc_ctx* c, const double* d_phi_next, const double* d_phi_k,
+                     const double* d_gnext, double* d_gk, double* d_gkm1, double* d_z,
+                     double rtol, int max_cycles, double* eps_bar, int* cycles);
+
+/* ------------------------------------------------------------------------
  * Primitive operations of the mixed-precision paths.  The outer loop is a
  * defect correction: r = S - N(u), then an FP32 multigrid solve of J d = r,
  * with J the Jacobian of N at u (Eqs. 5.4-5.6 differentiated in phi: only the

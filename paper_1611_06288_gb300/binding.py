@@ -101,6 +101,8 @@ _SIGS = {
     "pfc_batch_init": (_I, [ctypes.POINTER(_P), ctypes.POINTER(pfc_params), _I,
                             ctypes.POINTER(_D), _P, _SZ, _P, _P]),
     "pfc_batch_members": (_I, [_P]),
+    "pfc_adjoint_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _D, _I, ctypes.POINTER(_D),
+                              ctypes.POINTER(_I)]),
     "pfc_batch_diagnostics": (_I, [_P, ctypes.POINTER(_D)]),
     "pfc_batch_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
@@ -204,6 +206,16 @@ def pfc_batch_init(p: pfc_params, eps, workspace, phi0, stream=None) -> ctypes.c
                               workspace.numel() * workspace.element_size(), ptr(phi0), stream)
     check(rc, "pfc_batch_init")
     return ctx
+
+
+def pfc_adjoint_step(ctx, phi_next, phi_k, gnext, gk, gkm1, z, rtol=1e-10, max_cycles=50):
+    """One adjoint step (see pfc.h); returns (dL/deps contribution, corrections)."""
+    eb = ctypes.c_double(0.0)
+    cyc = ctypes.c_int(0)
+    check(lib().pfc_adjoint_step(ctx, ptr(phi_next), ptr(phi_k), ptr(gnext), ptr(gk), ptr(gkm1),
+                                 ptr(z), rtol, max_cycles, ctypes.byref(eb), ctypes.byref(cyc)),
+          "pfc_adjoint_step")
+    return eb.value, cyc.value
 
 
 def pfc_batch_members(ctx) -> int:

@@ -1,6 +1,8 @@
 // C ABI of libpfc (include/pfc.h): the solver context, the workspace carving,
 // the FAS V-cycle driver of Algorithm 1 and the primitive operations.
 #include <math.h>
+
+#include <cmath>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -813,6 +815,52 @@ int pfc_diagnostics(pfc_ctx* c, double out[4]) {
   if (rc == PFC_OK) memcpy(out, all, 4 * sizeof(double));
   free(all);
   return rc;
+}
+
+int pfc_adjoint_step(pfc_ctx* c, const double* phi_next, const double* phi_k,
+                     const double* gnext, double* gk, double* gkm1, double* z, double rtol,
+                     int max_cycles, double* eps_bar, int* cycles) {
+  if (!c || !phi_next || !phi_k || !gnext || !gk || !gkm1 || !z || !eps_bar ||
+      !(rtol > 0) || max_cycles < 1)
+    return PFC_EINVAL;
+  if (c->p.precision != PFC_MIXED || c->nb != 1) return PFC_EINVAL;
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
+  cudaStream_t st = c->st;
+  double* z1 = z;
+  double* z2 = z + n3;
+  double* z3 = z + 2 * n3;
+  PFC_CUDA(cudaMemsetAsync(z, 0, 3 * n3 * sizeof(double), st));
+  const Lvl& L0 = c->lev[0].L;
+  double* u[3] = {z1, z2, z3};
+  double rms0 = 0.0;
+  int it = 0;
+  for (;; ++it) {
+    // FP64 defect of J z = (0, g, 0): the linear outer loop
+    PFC_CUDA(launch_adj_defect64(L0, z1, z2, z3, gnext, phi_next, phi_k, c->mx.r[0][0],
+                                 c->mx.r[0][1], c->mx.r[0][2], c->mx.q[0], c->partials,
+                                 c->dout, st));
+    PFC_CUDA(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PFC_CUDA(cudaStreamSynchronize(st));
+    c->prof.launches += 2;
+    const double rms = sqrt(c->hout[0] / (3.0 * (double)n3));
+    if (!std::isfinite(rms)) return PFC_ENAN;
+    if (it == 0) rms0 = rms;
+    if (rms <= rtol * rms0 || rms == 0.0) break;
+    if (it >= max_cycles) {
+      if (cycles) *cycles = it;
+      return PFC_ENOCONV;
+    }
+    // FP32 V-cycles on J d = r (q frozen at the step's solution), z += d
+    PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, u, st, nullptr, 1));
+  }
+  PFC_CUDA(launch_adj_accumulate(L0, z1, z2, z3, phi_next, phi_k, gk, gkm1, c->partials,
+                                 c->dout, st));
+  PFC_CUDA(cudaMemcpyAsync(c->hout, c->dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  c->prof.launches += 2;
+  *eps_bar += c->hout[0];
+  if (cycles) *cycles = it;
+  return PFC_OK;
 }
 
 int pfc_batch_status(const pfc_ctx* c, int* iters, double* residual, double* residual0) {

@@ -249,6 +249,84 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
   if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
 }
 
+// Adjoint of a time step (the transposed linearised system).  With P the
+// swap of the phi and mu components and S = diag(1, 1, 2), J^T = S P J P S^-1
+// for J = [[I, -tau Lap, 0], [-diag(q), I, -Lap], [-Lap/2, 0, I]] (Eqs.
+// 5.4-5.6 differentiated in u), so J^T psi = (g, 0, 0) is solved as
+// J z = (0, g, 0) with psi = (z2, z1, 2 z3), by the forward correction
+// machinery.  This kernel is its FP64 defect r = (0, g, 0) - J z with
+// q = f'(a, b) + (1-eps)/2 at the step's solution a = phi^{k+1}, b = phi^k,
+// r and q rounded to FP32 (colour-split), per-block sums of |r|^2.
+__global__ void __launch_bounds__(256) k_adj_defect64(
+    Lvl L, const double* __restrict__ z1, const double* __restrict__ z2,
+    const double* __restrict__ z3, const double* __restrict__ g, const double* __restrict__ a,
+    const double* __restrict__ b, float* __restrict__ r1, float* __restrict__ r2,
+    float* __restrict__ r3, float* __restrict__ q, double* partials) {
+  __shared__ float sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  float acc = 0.f;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const Nb6 s = nb6_at(t, i, j, k, n);
+    const double x1 = __ldg(z1 + t), x2 = __ldg(z2 + t), x3 = __ldg(z3 + t);
+    const double l1 = fma(-6.0, x1, nbsum64(z1, s));
+    const double l2 = fma(-6.0, x2, nbsum64(z2, s));
+    const double l3 = fma(-6.0, x3, nbsum64(z3, s));
+    const double p = __ldg(a + t), bb = __ldg(b + t);
+    const double qq = fma(0.75 * p, p, fma(0.5 * p, bb, 0.25 * bb * bb)) + L.c1;
+    const double x = fma(L.tg, l2, -x1);                         // 0 - (z1 - tau Lap z2)
+    const double y = __ldg(g + t) - (fma(-qq, x1, x2) - L.g * l3);
+    const double zz = fma(L.gh, l1, -x3);                        // 0 - (z3 - Lap z1 / 2)
+    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(zz);
+    acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
+    const int o = split_index(i, j, k, n);
+    r1[o] = xf;
+    r2[o] = yf;
+    r3[o] = zf;
+    q[o] = d2f_rn(qq);
+  }
+  acc = block_sum_f(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
+// Gradient propagation of one adjoint step from psi = (z2, z1, 2 z3):
+//   dL/dphi^k     += psi1 + (df/db + (1-eps)/2) psi2 + 3 Lap psi2 + Lap psi3 / 2
+//   dL/dphi^{k-1} += -Lap psi2
+//   dL/deps       += -sum psi2 (a + b) / 2         (per-block partials)
+// (df/db = (a^2 + 2ab + 3b^2)/4 for f(a, b) = (a+b)(a^2+b^2)/4); when gkm1 ==
+// gk (the first step, phi^{-1} = phi^0) both terms go to gk.
+__global__ void __launch_bounds__(256) k_adj_accumulate(
+    Lvl L, const double* __restrict__ z1, const double* __restrict__ z2,
+    const double* __restrict__ z3, const double* __restrict__ a, const double* __restrict__ b,
+    double* gk, double* gkm1, double* partials) {
+  __shared__ double sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  const bool same = gk == gkm1;
+  double acc[1] = {0.0};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const Nb6 s = nb6_at(t, i, j, k, n);
+    const double x1 = __ldg(z1 + t), x2 = __ldg(z2 + t), x3 = __ldg(z3 + t);
+    const double lp2 = L.g * fma(-6.0, x1, nbsum64(z1, s));        // Lap psi2
+    const double lp3 = 2.0 * L.g * fma(-6.0, x3, nbsum64(z3, s));  // Lap psi3
+    const double p = __ldg(a + t), bb = __ldg(b + t);
+    const double dfb = 0.25 * fma(p, p, fma(2.0 * p, bb, 3.0 * bb * bb));
+    const double dk = fma(dfb + L.c1, x1, x2) + fma(3.0, lp2, 0.5 * lp3);
+    if (same) {
+      gk[t] += dk - lp2;
+    } else {
+      gk[t] += dk;
+      gkm1[t] -= lp2;
+    }
+    acc[0] = fma(-0.5 * x1, p + bb, acc[0]);
+  }
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+
 
 // Unscaled 7-point Laplacian (neighbour sum - 6 centre) of a df field as an
 // unnormalised pair: -6 c split exactly by one FMA, then the six neighbours.
@@ -1616,6 +1694,27 @@ cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const fl
                              int members) {
   const Launch3 g = launch3(n, n, n * members);
   return launch_k(pdl, k_correct64, g.grid, g.block, 0, st, n, u1, u2, u3, d1, d2, d3);
+}
+
+cudaError_t launch_adj_defect64(const Lvl& L, const double* z1, const double* z2,
+                                const double* z3, const double* g, const double* a,
+                                const double* b, float* r1, float* r2, float* r3, float* q,
+                                double* partials, double* out, cudaStream_t st) {
+  const int nb = wave_blocks(k_adj_defect64, (int64_t)L.n * L.n * L.n);
+  k_adj_defect64<<<nb, kReduceThreads, 0, st>>>(L, z1, z2, z3, g, a, b, r1, r2, r3, q,
+                                                partials);
+  k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_accumulate(const Lvl& L, const double* z1, const double* z2,
+                                  const double* z3, const double* a, const double* b,
+                                  double* gk, double* gkm1, double* partials, double* out,
+                                  cudaStream_t st) {
+  const int nb = wave_blocks(k_adj_accumulate, (int64_t)L.n * L.n * L.n);
+  k_adj_accumulate<<<nb, kReduceThreads, 0, st>>>(L, z1, z2, z3, a, b, gk, gkm1, partials);
+  k_reduce1<<<1, kReduceThreads, 0, st>>>(partials, nb, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_defect_df(const Lvl& L, const float2* phi, const float2* mu,

@@ -109,6 +109,20 @@ cudaError_t launch_diagnostics_cached_df(int n, const float2* a, const float2* b
 cudaError_t launch_df_from_f64(int64_t count, const double* x, float2* y, cudaStream_t st);
 cudaError_t launch_df_to_f64(int64_t count, const float2* y, double* x, cudaStream_t st);
 
+// Adjoint step: J^T psi = (g, 0, 0) is solved as J z = (0, g, 0), psi =
+// (z2, z1, 2 z3).  launch_adj_defect64: r = (0, g, 0) - J z in FP64 with q
+// at (a, b), to FP32 r, q on level 0, |r|^2 at out[0].  launch_adj_accumulate:
+// gk += -(dF/db)^T psi, gkm1 += -(dF/dc)^T psi (gkm1 may equal gk), out[0] =
+// -(dF/deps)^T psi.
+cudaError_t launch_adj_defect64(const Lvl& L, const double* z1, const double* z2,
+                                const double* z3, const double* g, const double* a,
+                                const double* b, float* r1, float* r2, float* r3, float* q,
+                                double* partials, double* out, cudaStream_t st);
+cudaError_t launch_adj_accumulate(const Lvl& L, const double* z1, const double* z2,
+                                  const double* z3, const double* a, const double* b,
+                                  double* gk, double* gkm1, double* partials, double* out,
+                                  cudaStream_t st);
+
 // Primitive launches of the FP32 kernels (for the C ABI checks).
 cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
