@@ -94,6 +94,18 @@ typedef struct pfc_params {
                                 is below 1e-6 of the largest value) */
   int    guess;              /* initial iterate of a step: PFC_GUESS_PREVIOUS
                                 or PFC_GUESS_EXTRAPOLATE */
+  double mobility_m0, mobility_m2;
+                             /* mobility M(phi) = m0 + m2 phi^2 (m0 > 0,
+                                m2 >= 0), evaluated on every face at
+                                A phi_*, phi_* = 3/2 phi^k - 1/2 phi^{k-1}
+                                (Section 5): N1 = phi - tau d(M D mu).
+                                m0 = 1, m2 = 0 (the default) is M == 1.
+                                Any other M needs PFC_MIXED and one member:
+                                the FP64 defect uses the face mobilities,
+                                the FP32 correction solve the reference
+                                mobility m0 + m2 mean(phi^2) measured at
+                                pfc_set_state (an approximate Jacobian: the
+                                converged state is exact) */
 } pfc_params;
 
 #define PFC_GUESS_PREVIOUS    0  /* phi^{k+1} := phi^k; mu, omega from the last
@@ -118,8 +130,8 @@ typedef struct pfc_step_stats {
 /* Fill *p with defaults: V(2,2), Newton smoother, tol 1e-9, max_cycles 50,
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
- * coarse_stiffness 0.05, coarse_sweeps 4, guess PFC_GUESS_PREVIOUS.  n, L,
- * eps, dt are set to 0.
+ * coarse_stiffness 0.05, coarse_sweeps 4, guess PFC_GUESS_PREVIOUS, mobility
+ * m0 = 1, m2 = 0.  n, L, eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

@@ -99,6 +99,17 @@ def div_M_grad(v, h, mob=None):
     return total
 
 
+def face_mobilities(b, c, m0, m2):
+    """M(A phi_*) on the faces i+1/2 of every axis for M(phi) = m0 + m2 phi^2
+    and phi_* = 3/2 b - 1/2 c (b = phi^k, c = phi^{k-1})."""
+    ps = 1.5 * b - 0.5 * c
+    mob = {}
+    for ax in AXES:
+        a = op_A(ps, ax)
+        mob[ax] = m0 + m2 * a * a
+    return mob
+
+
 def face_mobility_sums(shape, mob):
     """Sum of the six face mobilities around each cell (Section 5 smoother)."""
     if mob is None:
@@ -166,6 +177,12 @@ class Params:
     exactly.  prolongation: "trilinear" or "constant".  cubic: False drops the
     cubic term (an oracle-only switch used for the Fourier closed form).
 
+    mob: face mobilities of the current step (dict axis -> array), or None
+    for M == 1.  mobility: (m0, m2) for the variable mobility
+    M(phi) = m0 + m2 phi^2 evaluated by ``run`` at every step on the faces
+    at A phi_*, phi_* = 3/2 phi^k - 1/2 phi^{k-1} (Section 5's scheme with
+    the extrapolated argument), or None for M == 1.
+
     smoother: "rb" is the paper's red-black sweep on every level; "hybrid"
     keeps it on levels whose stiffness s = (6 tau/h^2)(18/h^4) is >= stiff_hi
     or <= stiff_lo and uses ``jacobi_factor`` times as many damped collective
@@ -182,6 +199,7 @@ class Params:
     prolongation: str = "trilinear"
     cubic: bool = True
     mob: object = field(default=None, compare=False)
+    mobility: object = field(default=None, compare=False)
     smoother: str = "hybrid"
     jacobi_weight: float = 0.7
     jacobi_factor: int = 2
@@ -614,7 +632,10 @@ def run(phi0, nsteps, h, prm: Params, tol, max_cycles=100, phi1=None,
     om = np.zeros_like(b)
     cycles = []
     for k in range(nsteps):
-        res = solve_step(b, c, [b, mu, om], h, prm, tol, max_cycles)
+        prm_k = prm
+        if prm.mobility is not None:
+            prm_k = replace(prm, mob=face_mobilities(b, c, *prm.mobility))
+        res = solve_step(b, c, [b, mu, om], h, prm_k, tol, max_cycles)
         phi_new, mu, om = res.u
         cycles.append(res.cycles)
         if callback is not None:

@@ -41,7 +41,8 @@ class pfc_params(ctypes.Structure):
                 ("jacobi_factor", ctypes.c_int), ("jacobi_factor0", ctypes.c_int),
                 ("stiff_hi", ctypes.c_double),
                 ("stiff_lo", ctypes.c_double), ("coarse_stiffness", ctypes.c_double),
-                ("coarse_sweeps", ctypes.c_int), ("guess", ctypes.c_int)]
+                ("coarse_sweeps", ctypes.c_int), ("guess", ctypes.c_int),
+                ("mobility_m0", ctypes.c_double), ("mobility_m2", ctypes.c_double)]
 
 
 class pfc_step_stats(ctypes.Structure):

@@ -45,6 +45,11 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 inline float2* as_df(double* p) { return reinterpret_cast<float2*>(p); }
 inline const float2* as_df(const double* p) { return reinterpret_cast<const float2*>(p); }
 
+// Whether M(phi) = m0 + m2 phi^2 differs from M == 1.
+inline bool variable_mobility(const pfc_params* p) {
+  return p->mobility_m0 != 1.0 || p->mobility_m2 != 0.0;
+}
+
 // The mixed paths (FP32 correction solves) and the one whose state is df.
 inline bool is_mixed(const pfc_params* p) { return p->precision != PFC_FP64; }
 inline bool df_state(const pfc_params* p) { return p->precision == PFC_MIXED_DF; }
@@ -85,6 +90,8 @@ int validate(const pfc_params* p) {
   if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
   if (!(p->coarse_stiffness >= 0) || p->coarse_sweeps < 1) return PFC_EINVAL;
   if (p->guess != PFC_GUESS_PREVIOUS && p->guess != PFC_GUESS_EXTRAPOLATE) return PFC_EINVAL;
+  if (!(p->mobility_m0 > 0) || !(p->mobility_m2 >= 0)) return PFC_EINVAL;
+  if (variable_mobility(p) && p->precision != PFC_MIXED) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -130,6 +137,8 @@ struct pfc_ctx {
                      // the members one after another
   double* c1m;       // (1 - eps_m)/2 per member on the device (null when nb == 1)
   double* eps_host;  // eps per member on the host (nb entries)
+  double* M[3];      // face mobilities of the current step (variable mobility only)
+  double tau_scale;  // reference mobility of the FP32 correction solve (1 for M == 1)
   double* t0[3];     // level-0 Jacobi scratch
   double* partials;  // reduction partial sums
   double* dout;      // 8 device doubles of reduction results
@@ -162,6 +171,10 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base, int members) {
   for (int r = 0; r < 3; ++r) {
     double* f = cv.take<double>(n3);
     if (c) c->lap[r] = f;
+  }
+  for (int q = 0; q < 3; ++q) {
+    double* f = variable_mobility(p) ? cv.take<double>(n3) : nullptr;
+    if (c) c->M[q] = f;
   }
   double* mu = cv.take<double>(n3);
   double* om = cv.take<double>(n3);
@@ -293,7 +306,8 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
                                   &c->prof, as_df(c->lap[c->ia])));
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
-                                  &c->prof, c->lap[c->ia], c->nb, c->c1m));
+                                  &c->prof, c->lap[c->ia], c->nb, c->c1m,
+                                  c->M[0] ? c->M : nullptr));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
               launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
@@ -344,6 +358,12 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   if (!extrapolate)
     PFC_CUDA(cudaMemcpyAsync(lv.u[0], lv.b, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
                              c->st));
+  if (c->M[0]) {
+    // M(A phi_*) of this step (Section 5: phi_* = 3/2 phi^k - 1/2 phi^{k-1})
+    PFC_CUDA(launch_face_mobility(c->p.n, c->p.mobility_m0, c->p.mobility_m2, lv.b, cprev,
+                                  c->M[0], c->M[1], c->M[2], c->st));
+    c->prof.launches += 1;
+  }
   return enqueue_residual_decide(c, lv, h, use_handle, 1);
 }
 
@@ -356,7 +376,7 @@ int enqueue_body(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
     PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, u, c->st, &c->prof));
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_correction(c->mx, c->p, c->nl, c->sizes, lv.u, c->st, &c->prof,
-                                      c->nb));
+                                      c->nb, c->tau_scale));
   } else {
     int rc = vcycle64(c, 0, lv);
     if (rc) return rc;
@@ -583,6 +603,8 @@ void pfc_default_params(pfc_params* p) {
   p->coarse_stiffness = 0.05;
   p->coarse_sweeps = 4;
   p->guess = PFC_GUESS_PREVIOUS;
+  p->mobility_m0 = 1.0;
+  p->mobility_m2 = 0.0;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {
@@ -622,6 +644,7 @@ static int init_members(pfc_ctx** out, const pfc_params* p, int members, const d
   if (v) return v;
   if (members < 1 || members > kMaxMembers) return PFC_EINVAL;
   if (members > 1 && p->precision != PFC_MIXED) return PFC_EINVAL;
+  if (members > 1 && variable_mobility(p)) return PFC_EINVAL;
   for (int m = 0; m < members; ++m)
     if (!(eps[m] >= 0 && eps[m] < 1)) return PFC_EINVAL;
   if (((uintptr_t)d_workspace) % kAlign) return PFC_EINVAL;
@@ -665,6 +688,7 @@ static int init_members(pfc_ctx** out, const pfc_params* p, int members, const d
   c->ic = 0;
   c->ib = 1;
   c->ia = 2;
+  c->tau_scale = 1.0;
   int rc = PFC_OK;
   if (c->c1m) {
     for (int m = 0; m < members; ++m) c->hout[m] = 0.5 * (1.0 - eps[m]);
@@ -724,6 +748,26 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
     PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ib], c->lap[c->ib], c->st, c->nb));
     PFC_CUDA(launch_laplacian(c->p.n, c->ring[c->ic], c->lap[c->ic], c->st, c->nb));
     c->prof.launches += 2;
+  }
+  if (variable_mobility(&c->p)) {
+    // reference mobility of the FP32 correction solve: m0 + m2 mean(phi^2)
+    // of the state (sum phi^2 is the diagnostics' second raw sum)
+    PFC_CUDA(launch_diagnostics_cached(c->p.n, c->ring[c->ib], c->ring[c->ic], c->lap[c->ib],
+                                       c->lap[c->ic], c->partials, c->dout, c->st));
+    PFC_CUDA(cudaMemcpyAsync(c->hout, c->dout, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->st));
+    PFC_CUDA(cudaStreamSynchronize(c->st));
+    c->prof.launches += 2;
+    const double scale = c->p.mobility_m0 + c->p.mobility_m2 * c->hout[1] / (double)n3;
+    if (scale != c->tau_scale) {
+      // the step graphs hold the FP32 level constants: rebuild them
+      for (int r = 0; r < 3; ++r)
+        if (c->graph[r].exec) {
+          cudaGraphExecDestroy(c->graph[r].exec);
+          c->graph[r].exec = nullptr;
+        }
+      c->tau_scale = scale;
+    }
   }
   return PFC_OK;
 }
@@ -823,7 +867,8 @@ int pfc_adjoint_step(pfc_ctx* c, const double* phi_next, const double* phi_k,
   if (!c || !phi_next || !phi_k || !gnext || !gk || !gkm1 || !z || !eps_bar ||
       !(rtol > 0) || max_cycles < 1)
     return PFC_EINVAL;
-  if (c->p.precision != PFC_MIXED || c->nb != 1) return PFC_EINVAL;
+  if (c->p.precision != PFC_MIXED || c->nb != 1 || variable_mobility(&c->p))
+    return PFC_EINVAL;
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n;
   cudaStream_t st = c->st;
   double* z1 = z;

@@ -200,6 +200,7 @@ __device__ __forceinline__ double nbsum64(const double* __restrict__ v, const Nb
 // FP32 within a block: the sum only decides convergence).  f and f' share
 // phi^2, b^2 and phi b; the roundings to FP32 use the integer pipe.  lap
 // (may be null) receives the unscaled Laplacian of phi for later reuse.
+template <bool MOB>
 __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restrict__ phi,
                                                   const double* __restrict__ mu,
                                                   const double* __restrict__ om,
@@ -210,7 +211,10 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
                                                   float* __restrict__ r1, float* __restrict__ r2,
                                                   float* __restrict__ r3, float* __restrict__ q,
                                                   double* partials, double* __restrict__ lap,
-                                                  const double* __restrict__ c1m) {
+                                                  const double* __restrict__ c1m,
+                                                  const double* __restrict__ Mx,
+                                                  const double* __restrict__ My,
+                                                  const double* __restrict__ Mz) {
   __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
@@ -227,7 +231,18 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
     const Nb6 s = nb6_at(t, i, j, k, n);
     const double p = __ldg(phi + t), mm = __ldg(mu + t), w = __ldg(om + t);
     const double bb = __ldg(b + t);
-    const double lmu = fma(-6.0, mm, nbsum64(mu, s));
+    // row 1: d(M D mu) with the face mobilities (MOB), else the Laplacian;
+    // M^x at t is the face i+1/2, at s.xm the face i-1/2
+    double lmu;
+    if (MOB) {
+      lmu = fma(__ldg(Mx + t), __ldg(mu + s.xp) - mm, __ldg(Mx + s.xm) * (__ldg(mu + s.xm) - mm));
+      lmu = fma(__ldg(My + t), __ldg(mu + s.yp) - mm,
+                fma(__ldg(My + s.ym), __ldg(mu + s.ym) - mm, lmu));
+      lmu = fma(__ldg(Mz + t), __ldg(mu + s.zp) - mm,
+                fma(__ldg(Mz + s.zm), __ldg(mu + s.zm) - mm, lmu));
+    } else {
+      lmu = fma(-6.0, mm, nbsum64(mu, s));
+    }
     const double lom = fma(-6.0, w, nbsum64(om, s));
     const double lphi = fma(-6.0, p, nbsum64(phi, s));
     const double p2 = p * p, b2 = bb * bb, pb = p * bb;
@@ -247,6 +262,27 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
   }
   acc = block_sum_f(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
+// Face mobilities of a step: M(A phi_*) on the faces i+1/2 of each axis for
+// M(phi) = m0 + m2 phi^2, phi_* = 3/2 b - 1/2 c (b = phi^k, c = phi^{k-1});
+// the face i+1/2 of an axis is stored at cell i.
+__global__ void k_face_mobility(int n, double m0, double m2, const double* __restrict__ b,
+                                const double* __restrict__ c, double* __restrict__ Mx,
+                                double* __restrict__ My, double* __restrict__ Mz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y,
+            k = blockIdx.z;
+  if (i >= n || j >= n) return;
+  const int t = (k * n + j) * n + i;
+  const Nb6 s = nb6_at(t, i, j, k, n);
+  const double ps = fma(1.5, __ldg(b + t), -0.5 * __ldg(c + t));
+  const double px = fma(1.5, __ldg(b + s.xp), -0.5 * __ldg(c + s.xp));
+  const double py = fma(1.5, __ldg(b + s.yp), -0.5 * __ldg(c + s.yp));
+  const double pz = fma(1.5, __ldg(b + s.zp), -0.5 * __ldg(c + s.zp));
+  const double ax = 0.5 * (ps + px), ay = 0.5 * (ps + py), az = 0.5 * (ps + pz);
+  Mx[t] = fma(m2 * ax, ax, m0);
+  My[t] = fma(m2 * ay, ay, m0);
+  Mz[t] = fma(m2 * az, az, m0);
 }
 
 // Adjoint of a time step (the transposed linearised system).  With P the
@@ -1676,16 +1712,28 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
                             float* q, double* partials, double* out, cudaStream_t st,
-                            double* lap, int members, const double* c1m) {
+                            double* lap, int members, const double* c1m, const double* Mx,
+                            const double* My, const double* Mz) {
   // one resident wave over all members: blocks per member = wave / members
-  const int wave = wave_blocks(k_defect64, (int64_t)L.n * L.n * L.n * members);
+  const int wave = wave_blocks(k_defect64<false>, (int64_t)L.n * L.n * L.n * members);
   int nbx = wave / members;
   const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
   if (nbx > need) nbx = (int)need;
   if (nbx < 1) nbx = 1;
-  k_defect64<<<dim3(nbx, members), kReduceThreads, 0, st>>>(L, phi, mu, om, S1, S2, S3, b, r1,
-                                                            r2, r3, q, partials, lap, c1m);
+  if (Mx)
+    k_defect64<true><<<dim3(nbx, members), kReduceThreads, 0, st>>>(
+        L, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, partials, lap, c1m, Mx, My, Mz);
+  else
+    k_defect64<false><<<dim3(nbx, members), kReduceThreads, 0, st>>>(
+        L, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, partials, lap, c1m, Mx, My, Mz);
   k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, nbx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
+                                 double* Mx, double* My, double* Mz, cudaStream_t st) {
+  const Launch3 g = launch3(n, n, n);
+  k_face_mobility<<<g.grid, g.block, 0, st>>>(n, m0, m2, b, c, Mx, My, Mz);
   return cudaGetLastError();
 }
 
@@ -1865,11 +1913,12 @@ cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const f
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
-                                 int members, const double* c1m) {
+                                 int members, const double* c1m, double* const M[3]) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap,
-                                  members, c1m);
+                                  members, c1m, M ? M[0] : nullptr, M ? M[1] : nullptr,
+                                  M ? M[2] : nullptr);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
@@ -1889,7 +1938,7 @@ namespace {
 // q restricted to every level, then p.inner_cycles FP32 V-cycles on J d = r
 // from d = 0 (the part of a correction shared by both outer precisions).
 cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int* sizes,
-                          cudaStream_t st, Prof* pr, int members) {
+                          cudaStream_t st, Prof* pr, int members, double tau_scale) {
   Ctx32 c;
   c.nb = members;
   c.mx = &mx;
@@ -1902,7 +1951,8 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
   c.jfactor0 = p.jacobi_factor0;
   double h = p.L / p.n;
   for (int l = 0; l < nl; ++l) {
-    c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt));
+    // the FP32 operator uses the reference mobility: tau M_ref in row 1
+    c.L[l] = to_f32(make_lvl(sizes[l], h, p.eps, p.dt * tau_scale));
     c.kind[l] = level_kind(&p, h);
     h *= 2.0;
   }
@@ -1922,8 +1972,8 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
 
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, double* const u[3], cudaStream_t st,
-                                     Prof* pr, int members) {
-  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, members);
+                                     Prof* pr, int members, double tau_scale) {
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, members, tau_scale);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,
@@ -1936,7 +1986,7 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr) {
-  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, 1);
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, 1, 1.0);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct_df(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,

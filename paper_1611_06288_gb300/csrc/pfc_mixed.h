@@ -58,7 +58,8 @@ void mixed_carve(MixedBufs* mx, int n, int nl, const int* sizes, Take take, int 
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
-                                 int members = 1, const double* c1m = nullptr);
+                                 int members = 1, const double* c1m = nullptr,
+                                 double* const M[3] = nullptr);
 
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
@@ -71,7 +72,7 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3
 // FP64 (PFC_MIXED) or double-float (PFC_MIXED_DF).
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, double* const u[3], cudaStream_t st,
-                                     Prof* pr, int members = 1);
+                                     Prof* pr, int members = 1, double tau_scale = 1.0);
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr);
@@ -129,7 +130,12 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap = nullptr, int members = 1,
-                            const double* c1m = nullptr);
+                            const double* c1m = nullptr, const double* Mx = nullptr,
+                            const double* My = nullptr, const double* Mz = nullptr);
+// Face mobilities M(A phi_*), phi_* = 3/2 b - 1/2 c, M(phi) = m0 + m2 phi^2,
+// face i+1/2 of each axis stored at cell i (FP64).
+cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
+                                 double* Mx, double* My, double* Mz, cudaStream_t st);
 cudaError_t launch_correct64(int n, double* u1, double* u2, double* u3, const float* d1,
                              const float* d2, const float* d3, cudaStream_t st,
                              bool pdl = true, int members = 1);

@@ -122,3 +122,21 @@ def test_batch_workspace(libpfc):
     assert B.pfc_batch_workspace_bytes(p, 2) == 0
     p.precision = B.PFC_MIXED_DF
     assert B.pfc_batch_workspace_bytes(p, 2) == 0
+
+
+def test_mobility_params(libpfc):
+    """M(phi) = m0 + m2 phi^2 needs m0 > 0, m2 >= 0, and anything but M == 1
+    needs PFC_MIXED; the face mobility fields are part of the workspace."""
+    p = B.pfc_default_params()
+    assert (p.mobility_m0, p.mobility_m2) == (1.0, 0.0)
+    p.n, p.L, p.eps, p.dt = 32, 32.0, 0.1, 0.05
+    p.precision = B.PFC_MIXED
+    base = B.pfc_workspace_bytes(p)
+    p.mobility_m2 = 5.0
+    assert B.pfc_workspace_bytes(p) >= base + 3 * 8 * 32 ** 3
+    p.mobility_m0 = 0.0
+    assert B.pfc_workspace_bytes(p) == 0
+    p.mobility_m0, p.precision = 1.0, B.PFC_FP64
+    assert B.pfc_workspace_bytes(p) == 0
+    p.precision = B.PFC_MIXED
+    assert B.pfc_batch_workspace_bytes(p, 2) > 0     # size only; pfc_batch_init refuses

@@ -371,3 +371,67 @@ def test_table2_vcycle_counts(golden_dir):
         assert abs(counts[2] - gold["cycles"]["2,2"][idx]) <= 2, counts
         assert counts[1] > counts[2]
         assert abs(counts[1] - gold["cycles"]["1,1"][idx]) <= 3, counts
+
+
+# --------------------------------------------------------------------------
+# Variable mobility M(A phi_*) (Section 5 scheme; M(phi) = m0 + m2 phi^2)
+# --------------------------------------------------------------------------
+
+def weighted_grad_sq(mu, mob, h):
+    """[M D mu, D mu] = sum over axes of h^3 sum_faces M (D mu)^2."""
+    return sum(O.face_ip(mob[ax] * O.op_D(mu, ax, h), O.op_D(mu, ax, h), ax, h)
+               for ax in O.AXES)
+
+
+def test_variable_mobility_energy_law_and_mass():
+    """With a phi-dependent mobility the scheme still conserves mass exactly
+    and dissipates the modified energy by tau [M D mu, D mu] +
+    1/2 ||grad(a - 2b + c)||^2 (the law of Eq. 1.10 with the face-weighted
+    d(M D mu) of Eq. 5.1, by summation by parts): a wrong face index, a
+    missing weight or the wrong argument phi_* breaks the identity."""
+    wl = W.random16()
+    m0m2 = (1.0, 40.0)                      # M from 1 to ~1.8 over the field
+    prm = O.Params(eps=wl.eps, tau=wl.dt, mobility=m0m2)
+    phi0 = wl.phi0()
+    mass0 = O.mass(phi0, wl.h)
+    checks = []
+
+    def cb(k, a, b, c, mu, om, res):
+        mob = O.face_mobilities(b, c, *m0m2)
+        lhs = O.modified_energy(a, b, wl.h, wl.eps) - O.modified_energy(b, c, wl.h, wl.eps)
+        rhs = (-wl.dt * weighted_grad_sq(mu, mob, wl.h)
+               - 0.5 * O.grad_norm2_sq(a - 2 * b + c, wl.h))
+        plain = -wl.dt * O.grad_norm2_sq(mu, wl.h) - 0.5 * O.grad_norm2_sq(a - 2 * b + c, wl.h)
+        checks.append((lhs, rhs, plain, O.mass(a, wl.h), res.history[-1]))
+
+    O.run(phi0, 4, wl.h, prm, tol=1e-13, callback=cb)
+    for lhs, rhs, plain, m, r in checks:
+        assert r <= 1e-13
+        assert lhs == pytest.approx(rhs, rel=1e-8, abs=1e-9)
+        assert abs(lhs - plain) > 1e-6 * abs(lhs)   # the weighting matters here
+        assert m == pytest.approx(mass0, rel=1e-12)
+
+
+def test_variable_mobility_fas_matches_dense_newton_8():
+    """FAS with face mobilities (restricted face by face to the coarse
+    levels) reaches the dense-Newton solution of N(u) = S at 8^3."""
+    m, L = 8, 16.0
+    h = L / m
+    b = 0.2 + rand_field(m, 0.1)
+    c = b + rand_field(m, 0.01)
+    mob = O.face_mobilities(b, c, 0.5, 20.0)
+    prm = O.Params(eps=0.1, tau=0.05, coarsest=2, mob=mob)
+    S = O.source_S(b, c, h, prm)
+    ref, _ = O.newton_dense(S, [b, 0 * b, 0 * b], b, h, prm)
+    assert O.rms(O.residual(S, ref, b, h, prm)) < 1e-13
+    res = O.solve_step(b, c, [b, 0 * b, 0 * b], h, prm, tol=1e-13)
+    for x, y in zip(res.u, ref):
+        np.testing.assert_allclose(x, y, atol=1e-11 * (1 + np.abs(y).max()))
+
+
+def test_unit_mobility_is_the_constant_scheme():
+    wl = W.random16()
+    a1 = O.run(wl.phi0(), 2, wl.h, O.Params(eps=wl.eps, tau=wl.dt), tol=1e-13)[0]
+    a2 = O.run(wl.phi0(), 2, wl.h, O.Params(eps=wl.eps, tau=wl.dt, mobility=(1.0, 0.0)),
+               tol=1e-13)[0]
+    np.testing.assert_allclose(a2, a1, atol=1e-13)
