@@ -380,8 +380,9 @@ int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
  * pfc_energy, pfc_mass and pfc_diagnostics report member 0.
  * --------------------------------------------------------------------- */
 
-/* Workspace bytes of an ensemble (0 if invalid: as pfc_workspace_bytes, and
- * members > 1 requires PFC_MIXED). */
+/* Workspace bytes of an ensemble (0 if invalid: as pfc_workspace_bytes;
+ * 1 <= members <= 1024 with 3 n members / 2 <= 65535, the launch grids'
+ * z extent; members > 1 requires PFC_MIXED). */
 size_t pfc_batch_workspace_bytes(const pfc_params* p, int members);
 
 /* As pfc_init for `members` runs: eps[m] (host array) replaces p->eps for

@@ -624,8 +624,15 @@ size_t pfc_workspace_bytes(const pfc_params* p) {
   return carve(nullptr, p, nullptr, 1);
 }
 
+// Ensemble sizes the launch grids can cover: the kernels put planes x members
+// (x 3 components in the transfers, 3 n/2 planes per member) on the grid's
+// z extent, which CUDA bounds by 65535.
+static bool members_fit(const pfc_params* p, int members) {
+  return members >= 1 && members <= kMaxMembers && 3LL * p->n * members / 2 <= 65535;
+}
+
 size_t pfc_batch_workspace_bytes(const pfc_params* p, int members) {
-  if (validate(p) != PFC_OK || members < 1 || members > kMaxMembers) return 0;
+  if (validate(p) != PFC_OK || !members_fit(p, members)) return 0;
   if (members > 1 && p->precision != PFC_MIXED) return 0;
   return carve(nullptr, p, nullptr, members);
 }
@@ -642,7 +649,7 @@ static int init_members(pfc_ctx** out, const pfc_params* p, int members, const d
   *out = nullptr;
   int v = validate(p);
   if (v) return v;
-  if (members < 1 || members > kMaxMembers) return PFC_EINVAL;
+  if (!members_fit(p, members)) return PFC_EINVAL;
   if (members > 1 && p->precision != PFC_MIXED) return PFC_EINVAL;
   if (members > 1 && variable_mobility(p)) return PFC_EINVAL;
   for (int m = 0; m < members; ++m)

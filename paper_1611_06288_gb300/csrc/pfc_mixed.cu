@@ -407,7 +407,7 @@ __device__ __forceinline__ dacc dacc_cubic(df p, df b) {
 // from the hi parts of phi and b, colour-split; per-block partial sums of
 // |r|^2 (FP32 within a block, one double per block); lap (may be null)
 // receives the unscaled Laplacian of phi as a df field.
-__global__ void __launch_bounds__(256, 6) k_defect_df(
+__global__ void __launch_bounds__(256, 5) k_defect_df(
     LvlD L, const float2* __restrict__ phi, const float2* __restrict__ mu,
     const float2* __restrict__ om, const float2* __restrict__ S1,
     const float2* __restrict__ S2, const float2* __restrict__ S3,
@@ -886,8 +886,10 @@ __device__ __forceinline__ void block_sums(const float* __restrict__ v, const in
 //   (J d)2 = d_mu - q d_phi - 1/h^2 Lap d_om
 //   (J d)3 = d_om - 1/(2h^2) Lap d_phi,
 // the averaged Laplacians taken from the block sums above and q d_phi summed
-// cell by cell.  One thread per coarse cell.  ZERO: d = 0 on entry (no
-// pre-smoothing from a zero start), so rho = r and d is not read.
+// cell by cell.  One thread per coarse cell and row: the grid's z extent
+// covers planes x 3 rows x members, so a thread loads the children of at most
+// four fields and the block of one.  ZERO: d = 0 on entry (no pre-smoothing
+// from a zero start), so rho = r and d is not read.
 template <bool ZERO>
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
@@ -903,44 +905,48 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   const int n = L.n, nc = n >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
   int K = blockIdx.z;
-  const int m = member_of(K, nc);
+  const int mf = member_of(K, nc);           // member * 3 + row
+  const int m = mf / 3, f = mf - 3 * m;
   if (I >= nc || J >= nc) return;
   const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
-  d1 += off, d2 += off, d3 += off, r1 += off, r2 += off, r3 += off, q += off;
-  c1 += offc, c2 += offc, c3 += offc;
+  // row f: own residual r_f and correction d_f, the field under the Laplacian
+  // (d_mu, d_om, d_phi) and its coefficient
+  const float* __restrict__ r = (f == 0 ? r1 : f == 1 ? r2 : r3) + off;
+  const float* __restrict__ dv = (f == 0 ? d1 : f == 1 ? d2 : d3) + off;
+  const float* __restrict__ dl = (f == 0 ? d2 : f == 1 ? d3 : d1) + off;
+  const float g = f == 0 ? L.tg : f == 1 ? L.g : L.gh;
+  float* __restrict__ cf = (f == 0 ? c1 : f == 1 ? c2 : c3) + offc;
   int in[8], out[24];
   block_indices(I, J, K, n, in, out);
-  float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  float a = 0.f;
 #pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    a1 += __ldg(r1 + in[c]);
-    a2 += __ldg(r2 + in[c]);
-    a3 += __ldg(r3 + in[c]);
-  }
+  for (int c = 0; c < 8; ++c) a += __ldg(r + in[c]);
   if (!ZERO) {
-    float pin, pout, min_, mout, win, wout, qp = 0.f;
-    block_sums(d1, in, out, pin, pout);
-    block_sums(d2, in, out, min_, mout);
-    block_sums(d3, in, out, win, wout);
+    float sv = 0.f, lin, lout;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) qp = fmaf(__ldg(q + in[c]), __ldg(d1 + in[c]), qp);
-    a1 = fmaf(L.tg, fmaf(-3.f, min_, mout), a1 - pin);
-    a2 = fmaf(L.g, fmaf(-3.f, win, wout), (a2 - min_) + qp);
-    a3 = fmaf(L.gh, fmaf(-3.f, pin, pout), a3 - win);
+    for (int c = 0; c < 8; ++c) sv += __ldg(dv + in[c]);
+    block_sums(dl, in, out, lin, lout);
+    a = fmaf(g, fmaf(-3.f, lin, lout), a - sv);
+    if (f == 1) {
+      const float* __restrict__ qm = q + off;
+      const float* __restrict__ p1 = d1 + off;
+      float qp = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) qp = fmaf(__ldg(qm + in[c]), __ldg(p1 + in[c]), qp);
+      a += qp;
+    }
   }
-  const int o = split_index(I, J, K, nc);
-  c1[o] = 0.125f * a1;
-  c2[o] = 0.125f * a2;
-  c3[o] = 0.125f * a3;
+  cf[split_index(I, J, K, nc)] = 0.125f * a;
 }
 
 // d += P e (ASSIGN: d = P e; d was zero and is not read), trilinear
 // cell-centred prolongation with the weights 27, 9, 3, 1 over 64 as three
 // one-dimensional passes: the child on the low side of an axis takes
 // (3 e_0 + e_-1)/4, on the high side (3 e_0 + e_+1)/4.  Split layout on both
-// levels; one thread per coarse cell (I, J, K) writes its eight children
-// from the 3x3x3 coarse neighbourhood.  Only the wrapped coarse coordinates
-// stay live; every index is formed at its load or store.
+// levels.  One thread per coarse cell (I, J, K) and component writes the
+// cell's eight children from its 3x3x3 coarse neighbourhood; the grid's z
+// extent covers planes x components x members, so each thread carries one
+// short load -> interpolate -> store chain.
 template <bool ASSIGN>
 __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
                                 const float* __restrict__ e2, const float* __restrict__ e3,
@@ -951,50 +957,54 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
   const int nc = n >> 1, half = n >> 1, hc = nc >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
   int K = blockIdx.z;
-  const int m = member_of(K, nc);
+  const int mf = member_of(K, nc);           // member * 3 + component
+  const int m = mf / 3, f = mf - 3 * m;
   if (I >= nc || J >= nc) return;
-  const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
-  e1 += offc, e2 += offc, e3 += offc, d1 += off, d2 += off, d3 += off;
+  const float* __restrict__ e = (f == 0 ? e1 : f == 1 ? e2 : e3) + (size_t)m * nc * nc * nc;
+  float* __restrict__ d = (f == 0 ? d1 : f == 1 ? d2 : d3) + (size_t)m * n * n * n;
   const int Is[3] = {(I == 0) ? nc - 1 : I - 1, I, (I + 1 == nc) ? 0 : I + 1};
   const int Js[3] = {(J == 0) ? nc - 1 : J - 1, J, (J + 1 == nc) ? 0 : J + 1};
   const int Ks[3] = {(K == 0) ? nc - 1 : K - 1, K, (K + 1 == nc) ? 0 : K + 1};
-  const float* e[3] = {e1, e2, e3};
-  float* d[3] = {d1, d2, d3};
-#pragma unroll 1
-  for (int f = 0; f < 3; ++f) {
-    const float* __restrict__ ef = e[f];
-    float zx[3][3][2];                         // [y][x][child z]: 3 e_mid + e_lo / e_hi
+  // the eight children's current values first (independent loads)
+  float old[8];
 #pragma unroll
-    for (int y = 0; y < 3; ++y) {
+  for (int kk = 0; kk < 2; ++kk)
 #pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        float v[3];
-#pragma unroll
-        for (int z = 0; z < 3; ++z) {
-          const int idx = (Ks[z] * nc + Js[y]) * nc + ((Is[x] + Js[y] + Ks[z]) & 1) * hc +
-                          (Is[x] >> 1);
-          v[z] = __ldg(ef + idx);
-        }
-        zx[y][x][0] = fmaf(3.f, v[1], v[0]);
-        zx[y][x][1] = fmaf(3.f, v[1], v[2]);
-      }
+    for (int jj = 0; jj < 2; ++jj) {
+      const int j = 2 * J + jj, k = 2 * K + kk;
+      const int row = (k * n + j) * n + I, par = (j + k) & 1;
+      old[(2 * kk + jj) * 2] = ASSIGN ? 0.f : d[row + par * half];
+      old[(2 * kk + jj) * 2 + 1] = ASSIGN ? 0.f : d[row + (1 - par) * half];
     }
-    float* __restrict__ df_ = d[f];
+  float zx[3][3][2];                         // [y][x][child z]: 3 e_mid + e_lo / e_hi
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
+  for (int y = 0; y < 3; ++y) {
 #pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        float yx[3];
+    for (int x = 0; x < 3; ++x) {
+      float v[3];
 #pragma unroll
-        for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
-        const int j = 2 * J + jj, k = 2 * K + kk;
-        const int row = (k * n + j) * n + I, par = (j + k) & 1;   // child a has colour a ^ par
-        const float v0 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);  // a = 0 (i = 2I)
-        const float v1 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);  // a = 1 (i = 2I + 1)
-        const int o0 = row + par * half, o1 = row + (1 - par) * half;
-        df_[o0] = ASSIGN ? v0 : v0 + df_[o0];
-        df_[o1] = ASSIGN ? v1 : v1 + df_[o1];
+      for (int z = 0; z < 3; ++z) {
+        const int idx = (Ks[z] * nc + Js[y]) * nc + ((Is[x] + Js[y] + Ks[z]) & 1) * hc +
+                        (Is[x] >> 1);
+        v[z] = __ldg(e + idx);
       }
+      zx[y][x][0] = fmaf(3.f, v[1], v[0]);
+      zx[y][x][1] = fmaf(3.f, v[1], v[2]);
+    }
+  }
+#pragma unroll
+  for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      float yx[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
+      const int j = 2 * J + jj, k = 2 * K + kk;
+      const int row = (k * n + j) * n + I, par = (j + k) & 1;   // child a has colour a ^ par
+      const float v0 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);  // a = 0 (i = 2I)
+      const float v1 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);  // a = 1 (i = 2I + 1)
+      d[row + par * half] = v0 + old[(2 * kk + jj) * 2];
+      d[row + (1 - par) * half] = v1 + old[(2 * kk + jj) * 2 + 1];
     }
   }
 }
@@ -1444,16 +1454,17 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
   __shared__ float red[2][32];
   __shared__ int done;
   const bool zero_top = P.zero_init != 0;
+  // one block per member of a batched launch; P itself stays unmodified (a
+  // written parameter struct would be copied to local memory)
+  const size_t off = (size_t)blockIdx.x * P.L[0].n * P.L[0].n * P.L[0].n;
+  float* const gd0 = P.gd[0] + off;
+  float* const gd1 = P.gd[1] + off;
+  float* const gd2 = P.gd[2] + off;
   {
-    // one block per member of a batched launch
-    const size_t off = (size_t)blockIdx.x * P.L[0].n * P.L[0].n * P.L[0].n;
-    for (int c = 0; c < 3; ++c) {
-      P.gd[c] += off;
-      P.gr[c] += off;
-    }
-    P.gq += off;
-  }
-  {
+    const float* const gr0 = P.gr[0] + off;
+    const float* const gr1 = P.gr[1] + off;
+    const float* const gr2 = P.gr[2] + off;
+    const float* const gq = P.gq + off;
     const SLev S0 = slev(smem, P, 0);
     const int n0 = P.L[0].n;
     const int cells = n0 * n0 * n0;
@@ -1461,14 +1472,14 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
       int p, j, k, colour;
       split_cell(t, n0, p, j, k, colour);
       const int o = (2 * p + ((j + k + colour) & 1)) + n0 * (j + n0 * k);   // natural index
-      S0.r0[o] = P.gr[0][t];
-      S0.r1[o] = P.gr[1][t];
-      S0.r2[o] = P.gr[2][t];
-      S0.q[o] = P.gq[t];
+      S0.r0[o] = gr0[t];
+      S0.r1[o] = gr1[t];
+      S0.r2[o] = gr2[t];
+      S0.q[o] = gq[t];
       if (!zero_top) {
-        S0.d0[o] = P.gd[0][t];
-        S0.d1[o] = P.gd[1][t];
-        S0.d2[o] = P.gd[2][t];
+        S0.d0[o] = gd0[t];
+        S0.d1[o] = gd1[t];
+        S0.d2[o] = gd2[t];
       }
     }
     __syncthreads();
@@ -1482,9 +1493,9 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
     int p, j, k, colour;
     split_cell(t, n0, p, j, k, colour);
     const int o = (2 * p + ((j + k + colour) & 1)) + n0 * (j + n0 * k);
-    P.gd[0][t] = S0.d0[o];
-    P.gd[1][t] = S0.d1[o];
-    P.gd[2][t] = S0.d2[o];
+    gd0[t] = S0.d0[o];
+    gd1[t] = S0.d1[o];
+    gd2[t] = S0.d2[o];
   }
 }
 
@@ -1685,7 +1696,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   if (c.p->nu1 > 0) e = smooth32(c, l, c.p->nu1, zero_init);
   if (e != cudaSuccess) return e;
   const int nc = L.n / 2;
-  const Launch3 gr = launch3(nc, nc, nc * c.nb);
+  const Launch3 gr = launch3(nc, nc, nc * c.nb * 3);
   prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
   e = launch_k(c.pr == nullptr,
                dzero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
@@ -1695,7 +1706,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
   if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
-  const Launch3 gp = launch3(nc, nc, nc * c.nb);
+  const Launch3 gp = launch3(nc, nc, nc * c.nb * 3);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
   e = launch_k(c.pr == nullptr, dzero ? k_prolong_add32<true> : k_prolong_add32<false>,
                gp.grid, gp.block, 0, c.st, L.n,
@@ -1855,7 +1866,7 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
                                           const float* r2, const float* r3, const float* q,
                                           float* c1, float* c2, float* c3, cudaStream_t st) {
   const int nc = L.n / 2;
-  const Launch3 g = launch3(nc, nc, nc);
+  const Launch3 g = launch3(nc, nc, nc * 3);
   return launch_k(true,
                   zero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
                   g.grid, g.block, 0, st, to_f32(L), d1, d2, d3, r1, r2, r3, q, c1, c2, c3);
@@ -1864,7 +1875,7 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
 cudaError_t launch_prolong32(int n, bool assign, const float* e1, const float* e2,
                              const float* e3, float* d1, float* d2, float* d3, cudaStream_t st) {
   const int nc = n / 2;
-  const Launch3 g = launch3(nc, nc, nc);
+  const Launch3 g = launch3(nc, nc, nc * 3);
   return launch_k(true, assign ? k_prolong_add32<true> : k_prolong_add32<false>, g.grid,
                   g.block, 0, st, n, e1, e2, e3, d1, d2, d3);
 }

@@ -118,6 +118,12 @@ def test_batch_workspace(libpfc):
     assert four - one >= 3 * (10 * 8 + 10 * 4) * 32 ** 3
     assert B.pfc_batch_workspace_bytes(p, 0) == 0
     assert B.pfc_batch_workspace_bytes(p, 1025) == 0
+    # the launch grids' z extent (65535) bounds 3 n members / 2
+    assert B.pfc_batch_workspace_bytes(p, 1024) > 0          # 3 * 32 * 1024 / 2 = 49152
+    p.n = 64
+    assert B.pfc_batch_workspace_bytes(p, 682) > 0           # 65472
+    assert B.pfc_batch_workspace_bytes(p, 683) == 0          # 65568
+    p.n = 32
     p.precision = B.PFC_FP64
     assert B.pfc_batch_workspace_bytes(p, 2) == 0
     p.precision = B.PFC_MIXED_DF
