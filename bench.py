@@ -63,13 +63,14 @@ KERNEL_BYTES = {
 # DRAM bytes (read + write) of one launch of a kernel class of a precision,
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
-NCU_TRAFFIC = {("mixed", "defect"): 133.7e6}   # profiles/k_defect64_128.md
+NCU_TRAFFIC = {("mixed", "defect"): 128.1e6}   # profiles/k_defect64_fx_128.md
 
-# FP64-ALU-bound kernel classes of a precision: algorithmic FP64 flops per
-# cell of one counted launch (FMA = 2) and launches per group.  The FP64
-# defect evaluates three 7-point Laplacians (21), the residual rows (18, the
-# cubic term 6 of them), |r|^2 (6) and the Newton coefficient q (9): 54.
-KERNEL_FLOPS = {("mixed", "defect"): (54.0, 2)}
+# FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
+# counted launch (FMA = 2) and launches per group.  The FP64 defect forms the
+# three Laplacians' neighbour sums in exact int64 fixed point (no FP64
+# flops) and its rows in 6 DFMA + 4 DADD + 2 DMUL per cell (ncu: DFMA, DADD
+# and DMUL thread-instruction rates 3:2:1): 18 flops.
+KERNEL_FLOPS = {("mixed", "defect"): (18.0, 2)}
 
 # FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
 # sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
@@ -188,10 +189,6 @@ def oracle_step_time(n: int):
     from paper_1611_06288_gb300 import workloads as W
     wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
     phi0 = wl.phi0()
-    mixed_kw = wl.mixed()
-    for k in ("inner_cycles", "jacobi_factor", "nu1", "nu2"):
-        if getattr(args, k) is not None:
-            mixed_kw[k] = getattr(args, k)
     prm = O.Params(eps=wl.eps, tau=wl.dt)
     t0 = time.perf_counter()
     res = O.solve_step(phi0, phi0, [phi0, 0 * phi0, 0 * phi0], wl.h, prm, wl.tol)
@@ -233,7 +230,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": steps, "warmup": warm, "ms_per_step": 1e3 * tot / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(WORKLOAD, n=n, l2="inputs > L2 not applicable (CPU)"),
+        "data": "synthetic", "config": dict(WORKLOAD, workload=f"smooth-mode {n}^3", n=n,
+                                            l2="inputs > L2 not applicable (CPU)"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                          "sample": f"{steps} full oracle time steps at {n}^3 from phi0 "
                                    f"(start rule), V-cycles {cycles}"},
@@ -417,7 +415,7 @@ def run_ours(args):
             "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD["workload"], "n": n, "L": wl.L, "eps": wl.eps,
+            "config": {"workload": f"smooth-mode {n}^3", "n": n, "L": wl.L, "eps": wl.eps,
                        "dt": wl.dt, "tol": wl.tol, "precision": args.precision,
                        "solver": mixed_kw, "step_execution": "CUDA graph",
                        "parallelism": f"replicas x{ws}",

@@ -3,6 +3,7 @@
 #include <math.h>
 
 #include "pfc_df.cuh"
+#include "pfc_fixed.cuh"
 #include "pfc_internal.h"
 #include "pfc_mixed.h"
 
@@ -262,6 +263,178 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
   }
   acc = block_sum_f(acc, sm);
   if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
+// The FP64 defect with the three Laplacians' neighbour sums formed exactly in
+// 64-bit fixed point on the integer pipe (pfc_fixed.cuh) and the rows in 12
+// FP64 operations (defect_rows); M = 1.  r and the norm are those of the
+// FP64 residual up to rounding order (the Laplacians: exact sums of the
+// quantised inputs and one rounding, instead of five FP64 roundings).
+//
+// Tiling: a block of kFxTX x kFxTY threads owns that column of cells over
+// `zc` planes starting at plane k0 and marches upwards in z.  Each thread
+// keeps the fixed-point images of its cell in the planes k-1, k, k+1 in
+// registers; the images of plane k, with a one-cell halo in x and y (wrapped
+// periodically), sit in shared memory for the four in-plane neighbours.  So
+// every value is loaded and converted once per block (plus the halo), not
+// once per neighbour, and the raw values of the next plane are loaded one
+// plane ahead.  Threads past the grid edge (n < kFxTX or n < kFxTY) load
+// wrapped cells to fill the tile and write nothing.
+//
+// Range: inputs with |v| >= 32, Inf or NaN have no fixed-point image.  From
+// the first plane whose tile holds such a value the block evaluates its
+// Laplacians in FP64 from global memory (a block vote per plane); a cell
+// whose own value in the plane above is out of range does so alone.  Same
+// outputs either way.  Per-block partial sums of |r|^2 as k_defect64.
+constexpr int kFxTX = 32, kFxTY = 8;
+
+// The three rows at one cell from the unscaled Laplacians, in 12 FP64
+// operations: x = S1 - phi + tau/h^2 Lap mu, y = S2 - mu + f + c1 phi +
+// 1/h^2 Lap om with f = (phi + b)(phi^2 + b^2)/4 (Eq. 5.2), z = S3 - om +
+// 1/(2h^2) Lap phi, each rounded to FP32 on the integer pipe.  The Newton
+// coefficient q = f'(phi) + c1 only feeds the FP32 preconditioner: it is
+// formed in FP32 from phi and b rounded to FP32 (a few FP32 roundings).
+__device__ __forceinline__ void defect_rows(const Lvl& L, double c1, float c1f, double p,
+                                            double mm, double w, double bb, double lmu,
+                                            double lom, double lphi, double s1, double s2,
+                                            double s3, float& xf, float& yf, float& zf,
+                                            float& qf) {
+  const double t = p + bb;
+  const double sq = fma(p, p, bb * bb);
+  const double x = fma(L.tg, lmu, s1 - p);
+  const double y = fma(L.g, lom, fma(c1, p, fma(0.25 * t, sq, s2 - mm)));
+  const double z = fma(L.gh, lphi, s3 - w);
+  xf = d2f_rn(x);
+  yf = d2f_rn(y);
+  zf = d2f_rn(z);
+  const float pf = d2f_rn(p), bf = d2f_rn(bb);
+  qf = fmaf(0.75f * pf, pf, fmaf(0.5f * pf, bf, fmaf(0.25f * bf, bf, c1f)));
+}
+
+__global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
+    Lvl L, int zc, const double* __restrict__ phi, const double* __restrict__ mu,
+    const double* __restrict__ om, const double* __restrict__ S1, const double* __restrict__ S2,
+    const double* __restrict__ S3, const double* __restrict__ b, float* __restrict__ r1,
+    float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
+    double* __restrict__ lap, const double* __restrict__ c1m) {
+  __shared__ int64_t tile[3][kFxTY + 2][kFxTX + 2];
+  __shared__ float sm[32];
+  const int n = L.n, nn = n * n;
+  const int chunks = (n + zc - 1) / zc;
+  int zb = blockIdx.z;
+  const int m = member_of(zb, chunks);
+  const size_t off = (size_t)m * nn * n;
+  const bool s1_is_b = S1 == b;              // S1 = phi^k at the finest level
+  phi += off, mu += off, om += off, S1 += off, S2 += off, S3 += off, b += off;
+  r1 += off, r2 += off, r3 += off, q += off;
+  if (lap) lap += off;
+  const double c1 = c1m ? c1m[m] : L.c1;
+  const float c1f = d2f_rn(c1);
+  const int tid = threadIdx.x, tx = tid % kFxTX, ty = tid / kFxTX;   // 1-D block
+  const int i0 = blockIdx.x * kFxTX, j0 = blockIdx.y * kFxTY;
+  const int k0 = zb * zc, k1 = min(n, k0 + zc);
+  const bool active = i0 + tx < n && j0 + ty < n;
+  const int iw = (i0 + tx) % n, jw = (j0 + ty) % n;     // wrapped own column
+  const int own = jw * n + iw;
+  // halo cell of this thread (tid < 2 kFxTY + 2 kFxTX): in-plane index and
+  // tile position
+  int hidx = -1, hy = 0, hx = 0;
+  if (tid < 2 * kFxTY) {
+    const int r = tid % kFxTY, side = tid / kFxTY;        // x = i0 - 1 or i0 + kFxTX
+    hy = r + 1;
+    hx = side ? kFxTX + 1 : 0;
+    hidx = ((j0 + r) % n) * n + (side ? (i0 + kFxTX) % n : (i0 - 1 + n) % n);
+  } else if (tid < 2 * kFxTY + 2 * kFxTX) {
+    const int h = tid - 2 * kFxTY, c = h % kFxTX, side = h / kFxTX;   // y = j0 - 1 or j0 + kFxTY
+    hx = c + 1;
+    hy = side ? kFxTY + 1 : 0;
+    hidx = (side ? (j0 + kFxTY) % n : (j0 - 1 + n) % n) * n + (i0 + c) % n;
+  }
+  const double* const fld[3] = {phi, mu, om};
+  // Software pipeline over the planes: at plane k the raw values of plane
+  // k+1 (own cell) and the halo of plane k arrived during plane k-1; the
+  // loads of plane k+2 and of the halo of plane k+1 are issued now.
+  // okc: the images this thread put in the tile so far are valid (block
+  // vote per plane); the own image of plane k+1 is checked per cell.
+  bool okc = true;
+  int64_t xm[3], xc[3];
+  double dc[3], dn[3], hraw[3];
+  {
+    const int km = (k0 - 1 + n) % n, kp = (k0 + 1) % n;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      xm[f] = fix_of(__ldg(fld[f] + km * nn + own), okc);
+      dc[f] = __ldg(fld[f] + k0 * nn + own);
+      xc[f] = fix_of(dc[f], okc);
+      dn[f] = __ldg(fld[f] + kp * nn + own);
+      hraw[f] = hidx >= 0 ? __ldg(fld[f] + k0 * nn + hidx) : 0.0;
+    }
+  }
+  bool fx_path = true;
+  float acc = 0.f;
+  for (int k = k0; k < k1; ++k) {
+    const int kp = (k + 1 == n) ? 0 : k + 1;
+    const int kp2 = (kp + 1 == n) ? 0 : kp + 1;
+    const int t = k * nn + own;
+    const double bb = __ldg(b + t), s2 = __ldg(S2 + t), s3 = __ldg(S3 + t);
+    const double s1 = s1_is_b ? bb : __ldg(S1 + t);
+    const bool more = k + 1 < k1;
+    double dnn[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) dnn[f] = more ? __ldg(fld[f] + kp2 * nn + own) : 0.0;
+    bool okn = true;
+    int64_t xn[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) xn[f] = fix_of(dn[f], okn);
+    __syncthreads();                       // the previous plane's tile reads are done
+    bool okt = okc;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      tile[f][ty + 1][tx + 1] = xc[f];
+      if (hidx >= 0) tile[f][hy][hx] = fix_of(hraw[f], okt);
+    }
+    fx_path = __syncthreads_and(fx_path && okt) != 0;
+    if (hidx >= 0 && more) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) hraw[f] = __ldg(fld[f] + kp * nn + hidx);
+    }
+    double lap3[3];
+    if (fx_path && okn) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+        lap3[f] = fix_to_double(fix_lap(tile[f][ty + 1][tx], tile[f][ty + 1][tx + 2],
+                                        tile[f][ty][tx + 1], tile[f][ty + 2][tx + 1], xm[f],
+                                        xn[f], xc[f]));
+    } else {
+      const Nb6 sn = nb6_at(t, iw, jw, k, n);
+#pragma unroll
+      for (int f = 0; f < 3; ++f) lap3[f] = fma(-6.0, dc[f], nbsum64(fld[f], sn));
+    }
+    if (active) {
+      float xf, yf, zf, qf;
+      defect_rows(L, c1, c1f, dc[0], dc[1], dc[2], bb, lap3[1], lap3[2], lap3[0], s1, s2, s3,
+                  xf, yf, zf, qf);
+      acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
+      const int o = split_index(iw, jw, k, n);
+      r1[o] = xf;
+      r2[o] = yf;
+      r3[o] = zf;
+      q[o] = qf;
+      if (lap) lap[t] = lap3[0];
+    }
+    okc = okn;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      xm[f] = xc[f];
+      xc[f] = xn[f];
+      dc[f] = dn[f];
+      dn[f] = dnn[f];
+    }
+  }
+  acc = block_sum_f(acc, sm);
+  if (tid == 0)
+    partials[(size_t)m * (gridDim.x * gridDim.y * chunks) +
+             ((size_t)zb * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)acc;
 }
 
 // Face mobilities of a step: M(A phi_*) on the faces i+1/2 of each axis for
@@ -1719,12 +1892,52 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
 
 }  // namespace
 
+// Planes per block of k_defect64_fx: the split of the n planes of a column
+// into chunks that minimises the busiest SM's load, ceil(blocks / SMs) x
+// (planes + 1/2 for the extra plane of z halo); 0 if even whole columns need
+// more partial-sum slots than `cap` (blocks = column tiles x chunks x
+// members).
+int fx_planes(int n, int members, int64_t cap) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1)
+    sms = 152;
+  const int64_t tiles =
+      (int64_t)((n + kFxTX - 1) / kFxTX) * ((n + kFxTY - 1) / kFxTY) * members;
+  int best = 0;
+  double best_cost = 0.0;
+  for (int chunks = 1; chunks <= n; ++chunks) {
+    const int zc = (n + chunks - 1) / chunks;
+    if ((n + zc - 1) / zc != chunks) continue;   // same split as a smaller count
+    const int64_t blocks = tiles * chunks;
+    if (blocks > cap || (int64_t)chunks * members > 65535) break;
+    const double cost = (double)((blocks + sms - 1) / sms) * (zc + 0.5);
+    if (best == 0 || cost < best_cost) {
+      best = zc;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
+
 cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* om, const double* S1, const double* S2,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap, int members, const double* c1m, const double* Mx,
                             const double* My, const double* Mz) {
+  if (!Mx) {
+    const int zc = fx_planes(L.n, members, (int64_t)kReduceBlocks * kReduceComps);
+    if (zc > 0) {
+      const int chunks = (L.n + zc - 1) / zc;
+      const dim3 grid((L.n + kFxTX - 1) / kFxTX, (L.n + kFxTY - 1) / kFxTY, chunks * members);
+      k_defect64_fx<<<grid, kFxTX * kFxTY, 0, st>>>(L, zc, phi, mu, om, S1, S2, S3, b, r1, r2,
+                                                     r3, q, partials, lap, c1m);
+      k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, grid.x * grid.y * chunks, out);
+      return cudaGetLastError();
+    }
+  }
   // one resident wave over all members: blocks per member = wave / members
   const int wave = wave_blocks(k_defect64<false>, (int64_t)L.n * L.n * L.n * members);
   int nbx = wave / members;

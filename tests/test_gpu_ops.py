@@ -300,7 +300,42 @@ def test_source_df(n):
     assert_close_field(host_df(S3), ref[2], DF_RTOL, "S3")
 
 
-@pytest.mark.parametrize("n", [2, 4, 12, 32])
+def check_defect(n, h, b, c, u):
+    """pfc_op_defect against the oracle's FP64 residual (Eqs. 5.4-5.6) and
+    Newton coefficient, both rounded to FP32, and the Laplacian of phi."""
+    S = O.source_S(b, c, h, prm())
+    scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    r = [empty(n, torch.float32) for _ in range(3)]
+    q = empty(n, torch.float32)
+    lap = empty(n)
+    rms = B.pfc_op_defect(n, h, EPS, TAU, *[dev(x) for x in u], *[dev(s) for s in S], dev(b),
+                          *r, q, scratch, lap=lap)
+    ref = O.residual(S, u, b, h, prm())
+    assert rms == pytest.approx(O.rms(ref), rel=1e-5)
+    assert_close_field(host(lap), h * h * O.lap(u[0], h), FP64_RTOL, "lap")
+    for g, x in zip(r, ref):
+        assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
+    # q feeds only the FP32 preconditioner and is formed in FP32 from phi and
+    # b rounded to FP32: 2 input roundings (each doubled in the squares) and
+    # five operation roundings of 2^-24 against terms that sum to at most
+    # about twice q (q >= c1 > 0): below 16 * 2^-24 = 2^-20 of max |q|
+    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 2 ** -20,
+                       "q32")
+
+
+def test_defect_values_beyond_fixed_point_range():
+    """The defect's neighbour sums run in 64-bit fixed point for |v| < 32; a
+    block that meets larger values (here mu = 40 in a few cells of one plane,
+    phi = -50 in one cell of another, n = 48: partial x tiles and several
+    z chunks) evaluates in FP64 from that plane on, with the same result."""
+    n = 48
+    h, b, c, u = case(n, seed=3)
+    u[1][20, 5:9, 30] = 40.0
+    u[0][7, 40, 2] = -50.0
+    check_defect(n, h, b, c, u)
+
+
+@pytest.mark.parametrize("n", [2, 4, 12, 32, 48])
 def test_defect_and_correct(n):
     """FP64 outer loop (PFC_MIXED): FP64 residual and Newton coefficient
     rounded to FP32, FP64 update."""
@@ -320,8 +355,8 @@ def test_defect_and_correct(n):
     for g, x in zip(r, ref):
         # FP64 residual rounded to FP32: half an FP32 ulp (colour-split layout)
         assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
-    # q formed in FP64 and rounded once: half an FP32 ulp
-    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 2 ** -23,
+    # q in FP32 from FP32-rounded phi and b (bound derived in check_defect)
+    assert_close_field(from_split(host(q)), O.jacobian_coefficient(u[0], b, prm()), 2 ** -20,
                        "q32")
     # u += d: one FP64 rounding of the same sum on both sides -> bit-exact
     rng = np.random.default_rng(5)
