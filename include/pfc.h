@@ -106,6 +106,19 @@ typedef struct pfc_params {
                                 mobility m0 + m2 mean(phi^2) measured at
                                 pfc_set_state (an approximate Jacobian: the
                                 converged state is exact) */
+  int    cluster_tail;       /* mixed paths: 1 runs the coarse part of each
+                                FP32 V-cycle from the first level of at most
+                                32^3 cells whose size is a multiple of 8 and
+                                at least 16 as one launch of an 8-CTA
+                                thread-block cluster per member (levels in z
+                                slabs over the CTAs, neighbour planes through
+                                distributed shared memory) where the device
+                                can run such a cluster; 0 (default) keeps
+                                separate launches down to 16^3 and one block
+                                below, which measured as fast for one large
+                                grid and faster for ensembles.  Same
+                                arithmetic up to summation order and the
+                                approximate division of the pointwise solve */
 } pfc_params;
 
 #define PFC_GUESS_PREVIOUS    0  /* phi^{k+1} := phi^k; mu, omega from the last
@@ -131,7 +144,7 @@ typedef struct pfc_step_stats {
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
  * coarse_stiffness 0.05, coarse_sweeps 4, guess PFC_GUESS_PREVIOUS, mobility
- * m0 = 1, m2 = 0.  n, L, eps, dt are set to 0.
+ * m0 = 1, m2 = 0, cluster_tail 0.  n, L, eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

@@ -92,6 +92,7 @@ int validate(const pfc_params* p) {
   if (p->guess != PFC_GUESS_PREVIOUS && p->guess != PFC_GUESS_EXTRAPOLATE) return PFC_EINVAL;
   if (!(p->mobility_m0 > 0) || !(p->mobility_m2 >= 0)) return PFC_EINVAL;
   if (variable_mobility(p) && p->precision != PFC_MIXED) return PFC_EINVAL;
+  if (p->cluster_tail != 0 && p->cluster_tail != 1) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -605,6 +606,7 @@ void pfc_default_params(pfc_params* p) {
   p->guess = PFC_GUESS_PREVIOUS;
   p->mobility_m0 = 1.0;
   p->mobility_m2 = 0.0;
+  p->cluster_tail = 0;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {

@@ -2,6 +2,8 @@
 // update, FP32 linear multigrid for the correction (see pfc_mixed.h).
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include "pfc_df.cuh"
 #include "pfc_fixed.cuh"
 #include "pfc_internal.h"
@@ -1681,6 +1683,481 @@ size_t tail_smem_bytes(const int* sizes, int l0, int nl) {
 
 constexpr size_t kTailMaxSmem = 200 * 1024;   // + static shared memory <= 227 KiB
 
+// ---------------------------------------------------------------------------
+// Cluster tail: the coarse part of an FP32 V-cycle from a level of up to
+// kCtMaxN^3 cells down, in one launch of a thread-block cluster of kCtCtas
+// CTAs per ensemble member.  The leading levels whose size is a multiple of
+// kCtCtas are spread over the cluster in z slabs (CTA r holds planes
+// [r nz, (r+1) nz), nz = n / kCtCtas, natural order within the slab); the
+// remaining small levels live in CTA 0 and run the single-block tail code.
+// A cell's neighbour planes in another CTA are read through distributed
+// shared memory (the CTA's shared window mapped with map_shared_rank), and
+// every phase whose results another CTA reads ends with a cluster barrier.
+// So the 32^3 and 16^3 levels, which as separate launches were pure launch
+// latency and as one block kept 151 SMs idle, run on kCtCtas SMs without a
+// launch per sweep.  q of every level comes restricted from global memory.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+constexpr int kCtCtas = 8;                      // portable cluster size
+constexpr int kCtThreads = 1024;
+constexpr int kCtMaxN = 32;
+constexpr size_t kCtMaxSmem = 224 * 1024;   // + 272 B static <= 227 KiB
+
+struct CTailParams {
+  int nlev;          // levels from the cluster's top level to the coarsest
+  int ndist;         // the first ndist levels are spread over the cluster
+  int nu1, nu2, jfactor, jfactor_top, zero_init;
+  float w;
+  LvlF L[kTailMaxLevels];
+  int kind[kTailMaxLevels];
+  float* gd[3];                         // top level d in global memory (split layout)
+  const float* gr[3];                   // top level r
+  const float* gq[kTailMaxLevels];      // q of every level (split layout)
+  int ga_off;                           // float offset of CTA 0's levels in shared memory
+  TailParams G;                         // CTA 0's levels ndist .. nlev-1
+};
+
+// This CTA's slab of distributed level l: fields f = 0-2 d, 3-5 t, 6-8 r,
+// 9 q at base + f * slab, each nz planes of n^2 cells in natural order.
+__device__ __forceinline__ float* ct_base(float* smem, const CTailParams& P, int l) {
+  int off = 0;
+  for (int m = 0; m < l; ++m) off += 10 * (P.L[m].n / kCtCtas) * P.L[m].n * P.L[m].n;
+  return smem + off;
+}
+
+// 32-bit shared-window addresses: a shared::cta address of this CTA is also
+// its shared::cluster address; mapa gives another CTA's address of the same
+// offset.  Loads through these are volatile asm, which keeps them in program
+// order with the cluster barriers (themselves volatile asm).
+__device__ __forceinline__ unsigned ct_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned ct_mapa(unsigned addr, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float ct_ld(unsigned addr) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void ct_st(unsigned addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// lin_point with the division by the 2x2 determinant as a multiply by its
+// approximate reciprocal (__fdividef: within 2 ulp): the cluster tail is
+// issue bound and this is an FP32 preconditioner step.
+__device__ __forceinline__ void ct_point(const LvlF& L, float sp, float sm_, float sw, float q,
+                                         float r1, float r2, float r3, float& dp, float& dm,
+                                         float& dw) {
+  const float st1 = fmaf(L.tg, sm_, r1);
+  const float st2 = fmaf(L.g, sw, r2);
+  const float st3 = fmaf(L.gh, sp, r3);
+  const float Q = q + L.Q0;
+  const float det = fmaf(L.kap, Q, 1.0f);
+  dm = __fdividef(fmaf(Q, st1, fmaf(-L.g6, st3, st2)), det);
+  dp = fmaf(-L.kap, dm, st1);
+  dw = fmaf(-L.g3, dp, st3);
+}
+
+// A distributed level as this CTA sees it: its slab (planes [z0, z0 + nz))
+// and the cluster addresses of the slabs of the CTAs that hold the planes
+// just below and above it (periodic in the rank).  plane_at(k) takes an
+// unwrapped plane index within [z0 - nz, z0 + 2 nz) and returns the cluster
+// address of its first cell.
+struct CtSlab {
+  int n, nz, plane, slab, z0;
+  float* own;
+  unsigned u_own, u_prev, u_next;
+  __device__ __forceinline__ CtSlab(unsigned me, float* base, int n_) {
+    n = n_;
+    nz = n / kCtCtas;
+    plane = n * n;
+    slab = nz * plane;
+    z0 = (int)me * nz;
+    own = base;
+    u_own = ct_u32(base);
+    u_prev = ct_mapa(u_own, (me + kCtCtas - 1) % kCtCtas);
+    u_next = ct_mapa(u_own, (me + 1) % kCtCtas);
+  }
+  __device__ __forceinline__ unsigned plane_at(int k) const {
+    const int lz = k - z0;
+    if (lz < 0) return u_prev + 4u * (unsigned)((lz + nz) * plane);
+    if (lz >= nz) return u_next + 4u * (unsigned)((lz - nz) * plane);
+    return u_own + 4u * (unsigned)(lz * plane);
+  }
+};
+
+// Thread -> fixed (i, j) column of a level with n^2 <= blockDim.x cells per
+// plane, first local plane lz0 and plane stride lzs (the Walk of the
+// single-block tail); im..jp are the in-plane neighbours' offsets.
+struct CtCol {
+  int i, j, x, lz0, lzs, im, ip, jm, jp;
+  bool on;
+  __device__ __forceinline__ CtCol(int n) {
+    const int plane = n * n;
+    lzs = blockDim.x / plane;
+    const int t = threadIdx.x;
+    lz0 = t / plane;
+    x = t - lz0 * plane;
+    j = x / n;
+    i = x - j * n;
+    on = lz0 < lzs;
+    im = (i == 0) ? n - 1 : i - 1;
+    ip = (i + 1 == n) ? 0 : i + 1;
+    jm = (j == 0) ? n - 1 : j - 1;
+    jp = (j + 1 == n) ? 0 : j + 1;
+    im += j * n;
+    ip += j * n;
+    jm = jm * n + i;
+    jp = jp * n + i;
+  }
+};
+
+// Neighbour sum of cell x of a local plane `own` with the planes below and
+// above at cluster addresses um, up.
+__device__ __forceinline__ float ct_nb(const float* own, unsigned um, unsigned up,
+                                       const CtCol& w) {
+  return ((own[w.im] + own[w.ip]) + (own[w.jm] + own[w.jp])) +
+         (ct_ld(um + 4u * w.x) + ct_ld(up + 4u * w.x));
+}
+
+// `sweeps` smoothing sweeps (damped collective Jacobi: kind JACOBI, x jf;
+// else red-black) on distributed level l; zero: d = 0 before the first.
+// Coarsest: from d = 0, sweeps of the level's kind (Jacobi without the
+// factor) until the largest change is <= 1e-6 of the largest value (tested
+// every fourth sweep over the whole cluster) or `sweeps`, as the
+// single-block coarsest solve.
+__device__ void ct_smooth(const cg::cluster_group& cl, unsigned me, float* smem,
+                          const CTailParams& P, int l, int sweeps, int jf, bool zero,
+                          bool coarsest, float (*red)[32], float* cmax) {
+  if (sweeps <= 0) return;
+  const LvlF& L = P.L[l];
+  const CtSlab S(me, ct_base(smem, P, l), L.n);
+  const CtCol w(L.n);
+  const bool jac = P.kind[l] == PFC_SWEEP_JACOBI;
+  const int nsweep = jac && !coarsest ? sweeps * jf : sweeps;
+  const unsigned fb = 4u * (unsigned)S.slab;   // bytes per field
+  int s = 0;                                    // d in fields s..s+2 (Jacobi ping-pong)
+  for (int sweep = 0; sweep < nsweep; ++sweep) {
+    float change = 0.f, size = 0.f;
+    for (int pass = 0; pass < (jac ? 1 : 2); ++pass) {
+      const bool z = zero && sweep == 0 && pass == 0;
+      const int so = s * S.slab, dso = (jac ? 3 - s : 0) * S.slab;
+      if (w.on) {
+        for (int lz = w.lz0; lz < S.nz; lz += w.lzs) {
+          const int k = S.z0 + lz, c = lz * S.plane + w.x;
+          if (!jac && ((w.i + w.j + k) & 1) != pass) continue;
+          float sum0 = 0.f, sum1 = 0.f, sum2 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
+          if (!z) {
+            const float* own = S.own + so + lz * S.plane;
+            const unsigned um = S.plane_at(k - 1) + 4u * so, up = S.plane_at(k + 1) + 4u * so;
+            sum0 = ct_nb(own, um, up, w);
+            c0 = own[w.x];
+            sum1 = ct_nb(own + S.slab, um + fb, up + fb, w);
+            c1 = own[S.slab + w.x];
+            sum2 = ct_nb(own + 2 * S.slab, um + 2 * fb, up + 2 * fb, w);
+            c2 = own[2 * S.slab + w.x];
+          }
+          float dp, dm, dw;
+          ct_point(L, sum0, sum1, sum2, S.own[9 * S.slab + c], S.own[6 * S.slab + c],
+                   S.own[7 * S.slab + c], S.own[8 * S.slab + c], dp, dm, dw);
+          if (jac) {
+            dp = fmaf(P.w, dp - c0, c0);
+            dm = fmaf(P.w, dm - c1, c1);
+            dw = fmaf(P.w, dw - c2, c2);
+          }
+          if (coarsest) {
+            // old values: Jacobi's source; a red-black cell's own value (0
+            // on the first sweep from d = 0)
+            float o0 = c0, o1 = c1, o2 = c2;
+            if (!jac) {
+              const bool fresh = zero && sweep == 0;
+              o0 = fresh ? 0.f : S.own[c];
+              o1 = fresh ? 0.f : S.own[S.slab + c];
+              o2 = fresh ? 0.f : S.own[2 * S.slab + c];
+            }
+            change = fmaxf(change, fmaxf(fabsf(dp - o0), fmaxf(fabsf(dm - o1), fabsf(dw - o2))));
+            size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+          }
+          float* dst = S.own + dso + c;
+          dst[0] = dp;
+          dst[S.slab] = dm;
+          dst[2 * S.slab] = dw;
+        }
+      }
+      cl.sync();
+      if (jac) s = 3 - s;
+    }
+    if (!coarsest || (sweep & 3) != 3) continue;   // convergence test every fourth sweep
+    for (int o = 16; o > 0; o >>= 1) {
+      change = fmaxf(change, __shfl_down_sync(0xffffffffu, change, o));
+      size = fmaxf(size, __shfl_down_sync(0xffffffffu, size, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = change;
+      red[1][threadIdx.x >> 5] = size;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float cm = 0.f, zm = 0.f;
+      for (int v = 0; v < (int)((blockDim.x + 31) >> 5); ++v) {
+        cm = fmaxf(cm, red[0][v]);
+        zm = fmaxf(zm, red[1][v]);
+      }
+      cmax[0] = cm;
+      cmax[1] = zm;
+    }
+    cl.sync();
+    float cm = 0.f, zm = 0.f;
+    const unsigned uc = ct_u32(cmax);
+    for (unsigned r = 0; r < (unsigned)kCtCtas; ++r) {
+      const unsigned a = ct_mapa(uc, r);
+      cm = fmaxf(cm, ct_ld(a));
+      zm = fmaxf(zm, ct_ld(a + 4u));
+    }
+    cl.sync();                         // every CTA has read the maxima before they change
+    if (cm <= 1e-6f * zm) break;
+  }
+  if (s != 0) {                                 // the result is in t
+    if (w.on) {
+      for (int lz = w.lz0; lz < S.nz; lz += w.lzs) {
+        const int c = lz * S.plane + w.x;
+        S.own[c] = S.own[3 * S.slab + c];
+        S.own[S.slab + c] = S.own[4 * S.slab + c];
+        S.own[2 * S.slab + c] = S.own[5 * S.slab + c];
+      }
+    }
+    cl.sync();
+  }
+}
+
+// rho = r - J d of distributed level l averaged onto level l+1 (distributed,
+// or CTA 0's when l+1 == ndist).  Coarse plane K is formed by the CTA that
+// holds fine plane 2K (for a distributed coarse level also its owner).
+// dzero: d = 0 on level l, so rho = r.
+__device__ void ct_restrict(const cg::cluster_group& cl, unsigned me, float* smem,
+                            const CTailParams& P, int l, bool dzero) {
+  const LvlF& L = P.L[l];
+  const CtSlab S(me, ct_base(smem, P, l), L.n);
+  const int n = L.n, nc = n >> 1, pc = nc * nc;
+  const bool cdist = l + 1 < P.ndist;
+  unsigned ucr;                                 // cluster address of coarse r0, plane 0
+  int cstride, cz0 = 0;
+  if (cdist) {
+    const int cslab = (nc / kCtCtas) * pc;
+    ucr = ct_u32(ct_base(smem, P, l + 1) + 6 * cslab);
+    cstride = cslab;
+    cz0 = (int)me * (nc / kCtCtas);
+  } else {
+    ucr = ct_mapa(ct_u32(slev(smem + P.ga_off, P.G, 0).r0), 0u);
+    cstride = nc * pc;
+  }
+  const unsigned fb = 4u * (unsigned)S.slab;
+  const int K0 = (S.z0 + 1) >> 1, K1 = (S.z0 + S.nz + 1) >> 1;   // 2K in [z0, z0 + nz)
+  const CtCol w(nc);
+  if (w.on) {
+    for (int K = K0 + w.lz0; K < K1; K += w.lzs) {
+      float a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int kk = 0; kk < 2; ++kk) {
+        const int k = 2 * K + kk;
+        const unsigned pk = S.plane_at(k);     // field 0 of plane k
+        const unsigned pm = S.plane_at(k - 1);
+        const unsigned pp = S.plane_at(k + 1);
+        for (int ch = 0; ch < 4; ++ch) {
+          const int i = 2 * w.i + (ch & 1), j = 2 * w.j + (ch >> 1);
+          const unsigned x = 4u * (unsigned)(j * n + i);
+          a1 += ct_ld(pk + 6 * fb + x);
+          a2 += ct_ld(pk + 7 * fb + x);
+          a3 += ct_ld(pk + 8 * fb + x);
+          if (dzero) continue;
+          const int im = (i == 0) ? n - 1 : i - 1, ip = (i + 1 == n) ? 0 : i + 1;
+          const int jm = (j == 0) ? n - 1 : j - 1, jp = (j + 1 == n) ? 0 : j + 1;
+          const unsigned xm = 4u * (j * n + im), xp = 4u * (j * n + ip);
+          const unsigned ym = 4u * (jm * n + i), yp = 4u * (jp * n + i);
+          float lap[3], ctr[3];
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            const unsigned f = pk + q * fb, fm = pm + q * fb, fp = pp + q * fb;
+            ctr[q] = ct_ld(f + x);
+            lap[q] = fmaf(-6.f, ctr[q], ((ct_ld(f + xm) + ct_ld(f + xp)) +
+                                         (ct_ld(f + ym) + ct_ld(f + yp))) +
+                                            (ct_ld(fm + x) + ct_ld(fp + x)));
+          }
+          // minus (J d): rows 1-3 of the linearised operator
+          a1 -= fmaf(-L.tg, lap[1], ctr[0]);
+          a2 -= fmaf(-ct_ld(pk + 9 * fb + x), ctr[0], ctr[1]) - L.g * lap[2];
+          a3 -= fmaf(-L.gh, lap[0], ctr[2]);
+        }
+      }
+      const unsigned dst = ucr + 4u * (unsigned)((K - cz0) * pc + w.x);
+      ct_st(dst, 0.125f * a1);
+      ct_st(dst + 4u * cstride, 0.125f * a2);
+      ct_st(dst + 8u * cstride, 0.125f * a3);
+    }
+  }
+  cl.sync();
+}
+
+// d += P e on distributed level l (assign: d = P e) from level l+1
+// (distributed, or CTA 0's): trilinear, weights 27, 9, 3, 1 over 64.
+__device__ void ct_prolong(const cg::cluster_group& cl, unsigned me, float* smem,
+                           const CTailParams& P, int l, bool assign) {
+  const int n = P.L[l].n, nc = n >> 1, pc = nc * nc;
+  const CtSlab F(me, ct_base(smem, P, l), n);
+  const bool cdist = l + 1 < P.ndist;
+  unsigned cown, cprev, cnext, cfb;
+  int cz0 = 0, cnz = nc;
+  if (cdist) {
+    const CtSlab C(me, ct_base(smem, P, l + 1), nc);
+    cown = C.u_own;
+    cprev = C.u_prev;
+    cnext = C.u_next;
+    cfb = 4u * (unsigned)C.slab;
+    cz0 = C.z0;
+    cnz = C.nz;
+  } else {
+    cown = ct_mapa(ct_u32(slev(smem + P.ga_off, P.G, 0).d0), 0u);
+    cprev = cnext = cown;
+    cfb = 4u * (unsigned)(nc * pc);
+  }
+  const CtCol w(n);
+  const int I = w.i >> 1, J = w.j >> 1;
+  const int I2 = ((w.i & 1) ? I + 1 : I - 1 + nc) % nc;
+  const int J2 = ((w.j & 1) ? J + 1 : J - 1 + nc) % nc;
+  const unsigned o00 = 4u * (I + J * nc), o10 = 4u * (I2 + J * nc);
+  const unsigned o01 = 4u * (I + J2 * nc), o11 = 4u * (I2 + J2 * nc);
+  if (w.on) {
+    for (int lz = w.lz0; lz < F.nz; lz += w.lzs) {
+      const int k = F.z0 + lz, K = k >> 1;
+      int K2 = (k & 1) ? K + 1 : K - 1;       // unwrapped
+      unsigned a, b;
+      if (cdist) {
+        a = cown + 4u * (unsigned)((K - cz0) * pc);
+        const int l2 = K2 - cz0;
+        b = l2 < 0 ? cprev + 4u * (unsigned)((l2 + cnz) * pc)
+                   : l2 >= cnz ? cnext + 4u * (unsigned)((l2 - cnz) * pc)
+                               : cown + 4u * (unsigned)(l2 * pc);
+      } else {
+        K2 = (K2 + nc) % nc;
+        a = cown + 4u * (unsigned)(K * pc);
+        b = cown + 4u * (unsigned)(K2 * pc);
+      }
+      const int c = lz * F.plane + w.x;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float g2 = (ct_ld(a + o10) + ct_ld(a + o01)) + ct_ld(b + o00);
+        const float g3 = (ct_ld(a + o11) + ct_ld(b + o10)) + ct_ld(b + o01);
+        float acc = fmaf(3.f, g3, ct_ld(b + o11));
+        acc = fmaf(9.f, g2, acc);
+        acc = fmaf(27.f, ct_ld(a + o00), acc);
+        float* dq = F.own + q * F.slab + c;
+        *dq = assign ? (1.0f / 64.0f) * acc : fmaf(1.0f / 64.0f, acc, *dq);
+        a += cfb;
+        b += cfb;
+      }
+    }
+  }
+  cl.sync();
+}
+
+__global__ void __launch_bounds__(kCtThreads, 1) k_lin_ctail32(CTailParams P) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ float smem[];
+  __shared__ float red[2][32];
+  __shared__ float cmax[2];
+  __shared__ int done;
+  const cg::cluster_group cl = cg::this_cluster();
+  const unsigned me = cl.block_rank();
+  const int member = blockIdx.x / kCtCtas;
+  const bool zero_top = P.zero_init != 0;
+  cl.sync();                                    // every CTA of the cluster is running
+  // loads: this CTA's slabs of the distributed levels (top: r, q and d unless
+  // it starts from zero; below: q), CTA 0: q of its levels
+  for (int l = 0; l < P.ndist; ++l) {
+    const int n = P.L[l].n, nz = n / kCtCtas, plane = n * n, z0 = (int)me * nz;
+    const size_t off = (size_t)member * n * n * n;
+    const int slab = nz * plane;
+    float* const f = ct_base(smem, P, l);
+    const CtCol w(n);
+    for (int lz = w.lz0; w.on && lz < nz; lz += w.lzs) {
+      const int c = lz * plane + w.x;
+      const int g = split_index(w.i, w.j, z0 + lz, n) + (int)off;
+      f[9 * slab + c] = P.gq[l][g];
+      if (l == 0) {
+        f[6 * slab + c] = P.gr[0][g];
+        f[7 * slab + c] = P.gr[1][g];
+        f[8 * slab + c] = P.gr[2][g];
+        if (!zero_top) {
+          f[c] = P.gd[0][g];
+          f[slab + c] = P.gd[1][g];
+          f[2 * slab + c] = P.gd[2][g];
+        }
+      }
+    }
+  }
+  if (me == 0) {
+    for (int l = P.ndist; l < P.nlev; ++l) {
+      const int n = P.L[l].n, cells = n * n * n;
+      const size_t off = (size_t)member * cells;
+      const SLev S = slev(smem + P.ga_off, P.G, l - P.ndist);
+      for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        int p, j, k, colour;
+        split_cell(t, n, p, j, k, colour);
+        S.q[(2 * p + ((j + k + colour) & 1)) + n * (j + n * k)] = P.gq[l][t + off];
+      }
+    }
+  }
+  cl.sync();
+  // down: pre-smoothing and residual restriction on the distributed levels
+  // above the coarsest
+  const int top = P.ndist < P.nlev ? P.ndist : P.nlev - 1;   // levels with a coarser one
+  unsigned dzero_mask = 0;
+  for (int l = 0; l < top; ++l) {
+    const bool zero = l > 0 || zero_top;
+    const int jf = l == 0 ? P.jfactor_top : P.jfactor;
+    bool dzero = zero;
+    if (P.nu1 > 0) {
+      ct_smooth(cl, me, smem, P, l, P.nu1, jf, zero, false, red, cmax);
+      dzero = false;
+    }
+    if (dzero) dzero_mask |= 1u << l;
+    ct_restrict(cl, me, smem, P, l, dzero);
+  }
+  if (P.ndist < P.nlev) {
+    // CTA 0: the V-cycle over its levels from d = 0
+    if (me == 0) tail_vcycle(smem + P.ga_off, P.G, true, red, &done);
+    cl.sync();
+  } else {
+    ct_smooth(cl, me, smem, P, P.nlev - 1, P.G.coarse_sweeps, 1, true, true, red, cmax);
+  }
+  // up: prolongation + correction and post-smoothing
+  for (int l = top - 1; l >= 0; --l) {
+    ct_prolong(cl, me, smem, P, l, (dzero_mask >> l) & 1u);
+    ct_smooth(cl, me, smem, P, l, P.nu2, l == 0 ? P.jfactor_top : P.jfactor, false, false,
+              red, cmax);
+  }
+  {
+    const int n = P.L[0].n, nz = n / kCtCtas, plane = n * n, z0 = (int)me * nz;
+    const size_t off = (size_t)member * n * n * n;
+    const int slab = nz * plane;
+    const float* d = ct_base(smem, P, 0);
+    const CtCol w(n);
+    for (int lz = w.lz0; w.on && lz < nz; lz += w.lzs) {
+      const int c = lz * plane + w.x;
+      const int g = split_index(w.i, w.j, z0 + lz, n) + (int)off;
+      P.gd[0][g] = d[c];
+      P.gd[1][g] = d[slab + c];
+      P.gd[2][g] = d[2 * slab + c];
+    }
+  }
+  cl.sync();                                    // no CTA leaves while its memory is read
+}
+
 // u += d: u in the natural layout (FP64), d in the colour-split layout (FP32).
 
 // u += d (FP64 += FP32, colour-split d; the exact widening on the integer
@@ -1843,9 +2320,126 @@ cudaError_t tail32(const Ctx32& c, int l0, bool zero_init) {
   return e;
 }
 
+// Levels from l0 that the cluster tail spreads over its CTAs (n a multiple
+// of kCtCtas with at least two planes per CTA), and its shared-memory bytes
+// per CTA; 0 distributed levels when the cluster tail does not apply.
+int ctail_layout(const Ctx32& c, int l0, size_t* smem, int* ga_off) {
+  if (c.L[l0].n > kCtMaxN || c.nl - l0 > kTailMaxLevels) return 0;
+  int nd = 0;
+  size_t floats = 0;
+  for (int l = l0; l < c.nl; ++l) {
+    const int n = c.L[l].n;
+    if (l - l0 != nd || n % kCtCtas != 0 || n / kCtCtas < 2) break;
+    floats += (size_t)10 * (n / kCtCtas) * n * n;
+    ++nd;
+  }
+  if (nd == 0) return 0;
+  *ga_off = (int)floats;
+  for (int l = l0 + nd; l < c.nl; ++l) floats += (size_t)10 * c.L[l].n * c.L[l].n * c.L[l].n;
+  *smem = floats * sizeof(float);
+  return *smem <= kCtMaxSmem ? nd : 0;
+}
+
+// Whether this device runs a cluster of kCtCtas CTAs of kCtThreads threads
+// with the largest shared-memory request (checked once per process).
+bool ctail_supported() {
+  static int state = -1;
+  if (state >= 0) return state == 1;
+  state = 0;
+  if (cudaFuncSetAttribute(k_lin_ctail32, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kCtMaxSmem) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCtCtas);
+  cfg.blockDim = dim3(kCtThreads);
+  cfg.dynamicSmemBytes = kCtMaxSmem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kCtCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_lin_ctail32, &cfg) == cudaSuccess &&
+      clusters > 0)
+    state = 1;
+  cudaGetLastError();
+  return state == 1;
+}
+
+cudaError_t ctail32(const Ctx32& c, int l0, bool zero_init, int nd, size_t smem, int ga_off) {
+  MixedBufs& mx = *c.mx;
+  CTailParams P;
+  P.nlev = c.nl - l0;
+  P.ndist = nd;
+  P.nu1 = c.p->nu1;
+  P.nu2 = c.p->nu2;
+  P.jfactor = c.jfactor;
+  P.jfactor_top = l0 == 0 ? c.jfactor0 : c.jfactor;
+  P.zero_init = zero_init ? 1 : 0;
+  P.w = c.w;
+  for (int l = l0; l < c.nl; ++l) {
+    P.L[l - l0] = c.L[l];
+    P.kind[l - l0] = c.kind[l];
+    P.gq[l - l0] = mx.q[l];
+  }
+  for (int q = 0; q < 3; ++q) {
+    P.gd[q] = mx.d[l0][q];
+    P.gr[q] = mx.r[l0][q];
+  }
+  P.ga_off = ga_off;
+  // CTA 0's levels as a single-block tail (its top starts from zero); with
+  // no such level only G.coarse_sweeps is used (distributed coarsest solve)
+  TailParams& G = P.G;
+  G.nlev = c.nl - l0 - nd;
+  G.nu1 = c.p->nu1;
+  G.nu2 = c.p->nu2;
+  G.jfactor = c.jfactor;
+  G.jfactor_top = c.jfactor;
+  G.coarse_sweeps = c.p->coarse_sweeps;
+  G.zero_init = 1;
+  G.w = c.w;
+  for (int l = l0 + nd; l < c.nl; ++l) {
+    G.L[l - l0 - nd] = c.L[l];
+    G.kind[l - l0 - nd] = c.kind[l];
+  }
+  for (int q = 0; q < 3; ++q) {
+    G.gd[q] = nullptr;
+    G.gr[q] = nullptr;
+  }
+  G.gq = nullptr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCtCtas * c.nb);
+  cfg.blockDim = dim3(kCtThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c.st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kCtCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = c.pr == nullptr ? 2 : 1;
+  prof_begin(c.pr, PFC_K_LIN_COARSE, c.st);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_lin_ctail32, P);
+  prof_end(c.pr, PFC_K_LIN_COARSE, l0, 1, c.st);
+  return e;
+}
+
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
+  if (c.p->cluster_tail) {
+    size_t smem = 0;
+    int ga_off = 0;
+    const int nd = ctail_layout(c, l, &smem, &ga_off);
+    if (nd > 0 && ctail_supported()) return ctail32(c, l, zero_init, nd, smem, ga_off);
+  }
   if (L.n <= kTailMaxN && c.nl - l <= kTailMaxLevels) {
     int sizes[kMaxLevelsMixed];
     for (int q = 0; q < c.nl; ++q) sizes[q] = c.L[q].n;

@@ -4,7 +4,7 @@ drawn from {32^3, 48^3, 64^3}, their own eps and initial fields, dt = 0.05,
 made one after another through single contexts.
 
     python -m paper_1611_06288_gb300.ensemble [--count 96] [--steps 100] [--sequential]
-                                              [--autotune]
+                                              [--autotune] [--cluster-tail]
 
 Prints one JSON line: member-steps per second batched (and sequential when
 asked), the corrections per step and the largest final residual per group.
@@ -33,15 +33,16 @@ def _timed(fn):
 
 
 def run(count=96, steps=100, sequential=False, L=32.0, dt=0.05, tol=1e-9, warmup=2,
-        autotune=False):
+        autotune=False, cluster_tail=False):
     groups = W.ensemble(count, L=L, dt=dt, steps=steps)
-    kw = dict(W.ENSEMBLE_SETTINGS, tol=tol, max_cycles=100)
+    kw = dict(W.ENSEMBLE_SETTINGS, tol=tol, max_cycles=100, cluster_tail=cluster_tail)
     tuned = {}
     if autotune:
         from .autotune import tune
         for n, (eps, phi0) in groups.items():
             tuned[n], _ = tune(n, L, eps, dt, phi0, tol=tol)
     out = {"count": count, "steps": steps, "L": L, "dt": dt, "tol": tol,
+           "cluster_tail": bool(cluster_tail),
            "groups": {n: len(e) for n, (e, _) in groups.items()}, "settings": W.ENSEMBLE_SETTINGS}
     total = 0.0
     per_group = {}
@@ -89,8 +90,11 @@ def main():
     ap.add_argument("--sequential", action="store_true")
     ap.add_argument("--autotune", action="store_true",
                     help="choose each group's cycle settings with autotune.tune first")
+    ap.add_argument("--cluster-tail", action="store_true",
+                    help="coarse levels in one thread-block-cluster launch (cluster_tail 1)")
     a = ap.parse_args()
-    print(json.dumps(run(a.count, a.steps, a.sequential, autotune=a.autotune)), flush=True)
+    print(json.dumps(run(a.count, a.steps, a.sequential, autotune=a.autotune,
+                         cluster_tail=a.cluster_tail)), flush=True)
 
 
 if __name__ == "__main__":

@@ -135,6 +135,7 @@ def test_mobility_params(libpfc):
     needs PFC_MIXED; the face mobility fields are part of the workspace."""
     p = B.pfc_default_params()
     assert (p.mobility_m0, p.mobility_m2) == (1.0, 0.0)
+    assert p.cluster_tail == 0
     p.n, p.L, p.eps, p.dt = 32, 32.0, 0.1, 0.05
     p.precision = B.PFC_MIXED
     base = B.pfc_workspace_bytes(p)
@@ -146,3 +147,16 @@ def test_mobility_params(libpfc):
     assert B.pfc_workspace_bytes(p) == 0
     p.precision = B.PFC_MIXED
     assert B.pfc_batch_workspace_bytes(p, 2) > 0     # size only; pfc_batch_init refuses
+
+
+def test_cluster_tail_param(libpfc):
+    """cluster_tail is 0 or 1 (default 0) and does not change the workspace:
+    the cluster kernel keeps its levels in shared memory."""
+    p = B.pfc_default_params()
+    p.n, p.L, p.eps, p.dt = 64, 32.0, 0.1, 0.05
+    p.precision = B.PFC_MIXED
+    off = B.pfc_workspace_bytes(p)
+    p.cluster_tail = 1
+    assert B.pfc_workspace_bytes(p) == off > 0
+    p.cluster_tail = 2
+    assert B.pfc_workspace_bytes(p) == 0

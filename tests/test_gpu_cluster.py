@@ -1,0 +1,97 @@
+"""The cluster tail (the coarse part of each FP32 V-cycle in one launch of an
+8-CTA thread-block cluster, levels spread over the CTAs in z slabs) against
+the separate-launch / single-block path it replaces: both outer loops
+converge to the FP64 residual tolerance, the oracle's FP64 residual of the
+cluster path's result is below it, and the two fields agree to what that
+tolerance allows."""
+
+import numpy as np
+import pytest
+
+from gpu_helpers import host, rel_l2
+from oracle import pfc_oracle as O
+from paper_1611_06288_gb300 import workloads as W
+from paper_1611_06288_gb300.solver import PFCSolver
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+# Both runs stop at an RMS residual <= 1e-10 of the same uniquely solvable
+# system (Prop. 3.1); with a residual-to-error gain of O(1) the fields differ
+# by ~1e-10 of their size per step, well inside 1e-8 after three steps.
+AGREE_RTOL = 1e-8
+
+
+def run(n, L, eps, dt, phi0, steps, cluster, **kw):
+    s = PFCSolver(n, L, eps, dt, phi0, tol=TOL, precision="mixed", cluster_tail=cluster, **kw)
+    cycles = [s.step(1).cycles_last for _ in range(steps - 1)]
+    prev = host(s.phi())
+    cycles.append(s.step(1).cycles_last)
+    out = (host(s.phi()), host(s.mu()), host(s.omega()), prev)
+    s.close()
+    return cycles, out
+
+
+@pytest.mark.parametrize("n,settings", [
+    (32, dict(nu1=1, nu2=2, inner_cycles=2, jacobi_factor=3, coarse_sweeps=2)),
+    (48, dict(nu1=1, nu2=2, inner_cycles=2, jacobi_factor=3, coarse_sweeps=2)),
+    (64, dict(nu1=0, nu2=1, inner_cycles=2, jacobi_factor=4, coarse_sweeps=2)),
+])
+def test_cluster_tail_matches_block_tail(n, settings):
+    """Smooth mode on L = 32: at 32^3 the whole V-cycle runs in the cluster
+    (levels 32 and 16 distributed, 16^3 the coarsest), at 64^3 from the
+    second level, at 48^3 from 24^3 (3 planes per CTA) with 12^3 and below
+    in CTA 0."""
+    wl = W.smooth_sweep(n)
+    phi0 = wl.phi0()
+    cyc_on, on = run(n, wl.L, wl.eps, wl.dt, phi0, 3, True, **settings)
+    cyc_off, off = run(n, wl.L, wl.eps, wl.dt, phi0, 3, False, **settings)
+    assert all(abs(a - b) <= 1 for a, b in zip(cyc_on, cyc_off)), (cyc_on, cyc_off)
+    for x, y in zip(on[:3], off[:3]):
+        assert rel_l2(x, y) <= AGREE_RTOL
+    # the cluster path's last step against the oracle: rows 1 and 3 of
+    # S - N(u) need only phi^k (S1 = phi^k, S3 = Lap phi^k / 2)
+    a, mu, om, b = on
+    p = O.Params(eps=wl.eps, tau=wl.dt)
+    r = O.residual(O.source_S(b, b, wl.h, p), [a, mu, om], b, wl.h, p)
+    assert np.sqrt(np.mean(r[0] ** 2 + r[2] ** 2) / 3) <= TOL * 1.0001
+
+
+def test_cluster_jacobi_coarsest_with_convergence_test():
+    """A distributed coarsest level in the damped-Jacobi regime with enough
+    sweeps for the cluster-wide convergence test (every fourth sweep):
+    32^3 on L = 18.9, tau = 0.0125 puts 16^3 at stiffness 108 tau/h^6 ~ 0.5,
+    between the red-black thresholds, and coarse_stiffness 1 stops there."""
+    n, L, eps, dt = 32, 18.9, 0.1, 0.0125
+    rng = np.random.default_rng(7)
+    phi0 = 0.1 + 0.05 * rng.standard_normal((n, n, n))
+    kw = dict(nu1=1, nu2=2, inner_cycles=2, jacobi_factor=3, coarse_sweeps=9,
+              coarse_stiffness=1.0)
+    cyc_on, on = run(n, L, eps, dt, phi0, 2, True, **kw)
+    cyc_off, off = run(n, L, eps, dt, phi0, 2, False, **kw)
+    assert all(abs(a - b) <= 1 for a, b in zip(cyc_on, cyc_off)), (cyc_on, cyc_off)
+    for x, y in zip(on[:3], off[:3]):
+        assert rel_l2(x, y) <= AGREE_RTOL
+
+
+def test_cluster_tail_in_ensembles():
+    """Ensemble members of 32^3 run the whole V-cycle as one cluster each
+    (grid = 8 CTAs x members): the batch equals the members run alone on
+    the separate-launch path."""
+    from paper_1611_06288_gb300.solver import PFCBatch
+    n, L, dt = 32, 32.0, 0.05
+    eps = [0.05, 0.2, 0.3]
+    rng = np.random.default_rng(3)
+    fields = [m + 0.05 * rng.uniform(-1, 1, (n, n, n)) for m in (-0.2, 0.0, 0.05)]
+    kw = dict(nu1=1, nu2=2, inner_cycles=2, jacobi_factor=3, coarse_sweeps=2)
+    bt = PFCBatch(n, L, eps, dt, np.stack(fields), tol=TOL, cluster_tail=True, **kw)
+    for _ in range(3):
+        bt.step(1)
+    got = host(bt.phi())
+    bt.close()
+    for m, (e, f) in enumerate(zip(eps, fields)):
+        s = PFCSolver(n, L, e, dt, f, tol=TOL, precision="mixed", cluster_tail=False, **kw)
+        for _ in range(3):
+            s.step(1)
+        assert rel_l2(got[m], host(s.phi())) <= AGREE_RTOL
+        s.close()
