@@ -180,6 +180,42 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+# Algorithmic HBM bytes of one FP32 V-cycle of the mixed path that does not
+# start from d = 0 (the second and later V-cycles of a defect correction):
+# every field a kernel reads or writes counted once per pass (FP32, 4 B).
+# Level 0: full residual restriction (d, r, q read, coarse r written:
+# 28 + 12/8 B/cell), additive prolongation (d read and written, coarse d
+# read: 24 + 12/8), post-smoothing; lower levels start from d = 0: the
+# restriction reads only r (12 + 12/8) and the prolongation assigns d
+# (12 + 12/8).  A red-black sweep is two colour passes of 20 B/cell (half
+# of: d 12, r and q 16, d written 12); a damped Jacobi sweep reads d, r, q
+# and writes t (40 B/cell), an odd count adds one copy back (24 B/cell).
+# The coarse tail (from the first level of at most 16^3 cells) reads r and q
+# and writes d of its top level (28 B/cell); its lower levels stay in
+# shared memory.
+# ---------------------------------------------------------------------------
+
+def vcycle_bytes(params, levels):
+    """levels: [(n, kind)] of the mixed hierarchy, finest first."""
+    from paper_1611_06288_gb300 import binding as B
+    total = 0.0
+    for l, (m, kind) in enumerate(levels):
+        cells = float(m) ** 3
+        if m <= 16:
+            total += 28.0 * cells
+            break
+        first = l == 0
+        total += cells * ((28.0 + 1.5) if first else (12.0 + 1.5))          # restriction
+        total += cells * ((24.0 + 1.5) if first else (12.0 + 1.5))          # prolongation
+        if kind == B.PFC_SWEEP_JACOBI:
+            sweeps = params.nu2 * (params.jacobi_factor0 if first else params.jacobi_factor)
+            total += cells * (40.0 * sweeps + (24.0 if sweeps % 2 else 0.0))
+        else:
+            total += cells * 40.0 * params.nu2
+    return total
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
@@ -325,6 +361,45 @@ def run_ours(args):
 
     t_max, value = aggregate_replicas(ms_total / 1e3, args.steps, ws, dev)
 
+    # one FP32 V-cycle, graph-launched: the step time with one more V-cycle
+    # per correction, at the same corrections per step, minus the step time
+    # as configured, per correction (no events inside the graph)
+    vcyc = None
+    if args.precision == "mixed" and mixed_kw.get("nu1", 0) == 0:
+        vk = max(10, min(args.steps, 40))
+        res = {}
+        for extra in (0, 1):
+            kw = dict(mixed_kw, inner_cycles=mixed_kw.get("inner_cycles", 1) + extra)
+            sv = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                           precision="mixed", **kw)
+            for _ in range(args.warmup):
+                sv.step(1)
+            res[extra] = time_steps(sv, vk, diag=False)
+            if extra == 0:
+                levels = []
+                for lv in range(24):
+                    try:
+                        m, _, kind = B.pfc_level_info(sv.params, lv)
+                    except B.PFCError:
+                        break
+                    levels.append((m, kind))
+                vbytes = vcycle_bytes(sv.params, levels)
+            sv.close()
+        (t0_ms, c0), (t1_ms, c1) = res[0], res[1]
+        if c0 == c1 and sum(c0) > 0:
+            v_ms = (t1_ms - t0_ms) / sum(c0)
+            peaks_v, src_v = measured_peaks()
+            gbs = vbytes / (v_ms / 1e3) / 1e9
+            vcyc = {"ms": v_ms, "algorithmic_bytes": vbytes, "achieved": gbs, "unit": "GB/s",
+                    "peak": peaks_v["hbm_gbs"], "frac": gbs / peaks_v["hbm_gbs"],
+                    "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src_v})",
+                    "levels": [m for m, _ in levels],
+                    "method": f"({vk} steps at inner_cycles+1 - {vk} steps as configured) / "
+                              f"{sum(c0)} corrections, graph-launched, L2 flushed per step; "
+                              f"a V-cycle that does not start from d = 0"}
+        else:
+            vcyc = {"ms": None, "reason": f"corrections differ: {c0} vs {c1}"}
+
     # roofline of the dominant kernel
     peaks, peak_src = measured_peaks()
     m = n >> dom_lvl
@@ -426,6 +501,7 @@ def run_ours(args):
             "mixed_over_fp64": value / ws / fp64["value"],
             ("mixed_df" if args.precision == "mixed" else "mixed_fp64_outer"): alt,
             "roofline": roofline,
+            "vcycle": vcyc,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,

@@ -910,7 +910,10 @@ __device__ __forceinline__ void lin_point(const LvlF& L, float sp, float sm_, fl
   const float st3 = fmaf(L.gh, sp, r3);
   const float Q = q + L.Q0;
   const float det = fmaf(L.kap, Q, 1.0f);
-  dm = fmaf(Q, st1, fmaf(-L.g6, st3, st2)) / det;
+  // the division by the 2x2 determinant within 2 ulp (__fdividef): an FP32
+  // preconditioner step, and the IEEE division was a fifth of the sweep's
+  // instructions
+  dm = __fdividef(fmaf(Q, st1, fmaf(-L.g6, st3, st2)), det);
   dp = fmaf(-L.kap, dm, st1);
   dw = fmaf(-L.g3, dp, st3);
 }
@@ -944,6 +947,70 @@ __global__ void k_lin_smooth32(LvlF L, int colour, float* d1, float* d2, float* 
   d1[s.c] = dp;
   d2[s.c] = dm;
   d3[s.c] = dw;
+}
+
+// The same colour pass with two adjacent cells of the colour's half-row per
+// thread (positions p0 = 2t and p0 + 1; n a multiple of 4, so every pair is
+// 8-byte aligned): own r, q, the y and z neighbours and the results move as
+// float2, and the pair's x neighbours in the other half are that half's
+// pair (p0, p0 + 1) plus one cell on the side the colour's offset sigma =
+// (j + k + colour) & 1 points to.  Same sums in the same order as above.
+template <bool ZERO>
+__global__ void k_lin_smooth32x2(LvlF L, int colour, float* d1, float* d2, float* d3,
+                                 const float* __restrict__ r1, const float* __restrict__ r2,
+                                 const float* __restrict__ r3, const float* __restrict__ q) {
+  pdl_wait();
+  pdl_trigger();
+  const int n = L.n, half = n >> 1;
+  const int p0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  const size_t off = (size_t)member_of(k, n) * n * n * n;
+  if (p0 >= half || j >= n) return;
+  d1 += off, d2 += off, d3 += off, r1 += off, r2 += off, r3 += off, q += off;
+  const int sigma = (j + k + colour) & 1;
+  const int jm = (j == 0) ? n - 1 : j - 1, jp = (j + 1 == n) ? 0 : j + 1;
+  const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+  const int oc = (1 - colour) * half;
+  const int row = (k * n + j) * n;
+  const int c = row + colour * half + p0;                // own pair
+  const int xo = row + oc + p0;                          // other half, same positions
+  int xe = sigma ? p0 + 2 : p0 - 1;                      // the extra x neighbour
+  if (xe < 0) xe += half;
+  if (xe >= half) xe -= half;
+  xe += row + oc;
+  const int ym = (k * n + jm) * n + oc + p0, yp = (k * n + jp) * n + oc + p0;
+  const int zm = (km * n + j) * n + oc + p0, zp = (kp * n + j) * n + oc + p0;
+  float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
+  if (!ZERO) {
+    const float* f[3] = {d1, d2, d3};
+    float* acc[3] = {s0, s1, s2};
+#pragma unroll
+    for (int q3 = 0; q3 < 3; ++q3) {
+      const float* v = f[q3];
+      const float2 a = __ldg(reinterpret_cast<const float2*>(v + xo));
+      const float e = __ldg(v + xe);
+      const float2 y0 = __ldg(reinterpret_cast<const float2*>(v + ym));
+      const float2 y1 = __ldg(reinterpret_cast<const float2*>(v + yp));
+      const float2 z0 = __ldg(reinterpret_cast<const float2*>(v + zm));
+      const float2 z1 = __ldg(reinterpret_cast<const float2*>(v + zp));
+      // cell p0: (xm, xp) = sigma ? (a.x, a.y) : (e, a.x); cell p0+1: sigma ? (a.y, e) : (a.x, a.y)
+      const float xm0 = sigma ? a.x : e, xp0 = sigma ? a.y : a.x;
+      const float xm1 = sigma ? a.y : a.x, xp1 = sigma ? e : a.y;
+      acc[q3][0] = ((xm0 + xp0) + (y0.x + y1.x)) + (z0.x + z1.x);
+      acc[q3][1] = ((xm1 + xp1) + (y0.y + y1.y)) + (z0.y + z1.y);
+    }
+  }
+  const float2 qq = __ldg(reinterpret_cast<const float2*>(q + c));
+  const float2 ra = __ldg(reinterpret_cast<const float2*>(r1 + c));
+  const float2 rb = __ldg(reinterpret_cast<const float2*>(r2 + c));
+  const float2 rc = __ldg(reinterpret_cast<const float2*>(r3 + c));
+  float2 dp, dm, dw;
+  lin_point(L, s0[0], s1[0], s2[0], qq.x, ra.x, rb.x, rc.x, dp.x, dm.x, dw.x);
+  lin_point(L, s0[1], s1[1], s2[1], qq.y, ra.y, rb.y, rc.y, dp.y, dm.y, dw.y);
+  *reinterpret_cast<float2*>(d1 + c) = dp;
+  *reinterpret_cast<float2*>(d2 + c) = dm;
+  *reinterpret_cast<float2*>(d3 + c) = dw;
 }
 
 // One damped collective Jacobi sweep on J d = r, d -> t (split layout).
@@ -1747,22 +1814,6 @@ __device__ __forceinline__ void ct_st(unsigned addr, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
-// lin_point with the division by the 2x2 determinant as a multiply by its
-// approximate reciprocal (__fdividef: within 2 ulp): the cluster tail is
-// issue bound and this is an FP32 preconditioner step.
-__device__ __forceinline__ void ct_point(const LvlF& L, float sp, float sm_, float sw, float q,
-                                         float r1, float r2, float r3, float& dp, float& dm,
-                                         float& dw) {
-  const float st1 = fmaf(L.tg, sm_, r1);
-  const float st2 = fmaf(L.g, sw, r2);
-  const float st3 = fmaf(L.gh, sp, r3);
-  const float Q = q + L.Q0;
-  const float det = fmaf(L.kap, Q, 1.0f);
-  dm = __fdividef(fmaf(Q, st1, fmaf(-L.g6, st3, st2)), det);
-  dp = fmaf(-L.kap, dm, st1);
-  dw = fmaf(-L.g3, dp, st3);
-}
-
 // A distributed level as this CTA sees it: its slab (planes [z0, z0 + nz))
 // and the cluster addresses of the slabs of the CTAs that hold the planes
 // just below and above it (periodic in the rank).  plane_at(k) takes an
@@ -1863,7 +1914,7 @@ __device__ void ct_smooth(const cg::cluster_group& cl, unsigned me, float* smem,
             c2 = own[2 * S.slab + w.x];
           }
           float dp, dm, dw;
-          ct_point(L, sum0, sum1, sum2, S.own[9 * S.slab + c], S.own[6 * S.slab + c],
+          lin_point(L, sum0, sum1, sum2, S.own[9 * S.slab + c], S.own[6 * S.slab + c],
                    S.own[7 * S.slab + c], S.own[8 * S.slab + c], dp, dm, dw);
           if (jac) {
             dp = fmaf(P.w, dp - c0, c0);
@@ -2270,13 +2321,18 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
     prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
     return e;
   }
-  const Launch3 g = launch3(L.n / 2, L.n, L.n * c.nb);
+  const bool pairs = L.n % 4 == 0;              // two cells per thread, float2 moves
+  const Launch3 g = launch3(pairs ? L.n / 4 : L.n / 2, L.n, L.n * c.nb);
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < sweeps && e == cudaSuccess; ++s) {
     for (int colour = 0; colour < 2 && e == cudaSuccess; ++colour) {
       const bool z = zero_init && s == 0 && colour == 0;
-      e = launch_k(c.pr == nullptr, z ? k_lin_smooth32<true> : k_lin_smooth32<false>, g.grid,
-                   g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
+      if (pairs)
+        e = launch_k(c.pr == nullptr, z ? k_lin_smooth32x2<true> : k_lin_smooth32x2<false>,
+                     g.grid, g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
+      else
+        e = launch_k(c.pr == nullptr, z ? k_lin_smooth32<true> : k_lin_smooth32<false>,
+                     g.grid, g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
     }
   }
   prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps, c.st);
