@@ -1051,6 +1051,78 @@ __global__ void k_lin_jacobi32(LvlF L, float w, const float* __restrict__ d1,
 }
 
 
+// The same sweep with two adjacent cells of one half-row per thread (n a
+// multiple of 4): the neighbour pattern of k_lin_smooth32x2 for the pair's
+// colour, own d, r, q and the results as float2.
+template <bool ZERO>
+__global__ void k_lin_jacobi32x2(LvlF L, float w, const float* __restrict__ d1,
+                                 const float* __restrict__ d2, const float* __restrict__ d3,
+                                 float* __restrict__ t1, float* __restrict__ t2,
+                                 float* __restrict__ t3, const float* __restrict__ r1,
+                                 const float* __restrict__ r2, const float* __restrict__ r3,
+                                 const float* __restrict__ q) {
+  pdl_wait();
+  pdl_trigger();
+  const int n = L.n, half = n >> 1;
+  const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  const size_t off = (size_t)member_of(k, n) * n * n * n;
+  if (x >= n || j >= n) return;
+  d1 += off, d2 += off, d3 += off, t1 += off, t2 += off, t3 += off;
+  r1 += off, r2 += off, r3 += off, q += off;
+  const int colour = x >= half, p0 = x - colour * half;
+  const int sigma = (j + k + colour) & 1;
+  const int jm = (j == 0) ? n - 1 : j - 1, jp = (j + 1 == n) ? 0 : j + 1;
+  const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+  const int oc = (1 - colour) * half;
+  const int row = (k * n + j) * n;
+  const int c = row + colour * half + p0;
+  const int xo = row + oc + p0;
+  int xe = sigma ? p0 + 2 : p0 - 1;
+  if (xe < 0) xe += half;
+  if (xe >= half) xe -= half;
+  xe += row + oc;
+  const int ym = (k * n + jm) * n + oc + p0, yp = (k * n + jp) * n + oc + p0;
+  const int zm = (km * n + j) * n + oc + p0, zp = (kp * n + j) * n + oc + p0;
+  float s0[2] = {0.f, 0.f}, s1[2] = {0.f, 0.f}, s2[2] = {0.f, 0.f};
+  float2 o0 = make_float2(0.f, 0.f), o1 = o0, o2 = o0;
+  if (!ZERO) {
+    const float* f[3] = {d1, d2, d3};
+    float* acc[3] = {s0, s1, s2};
+#pragma unroll
+    for (int q3 = 0; q3 < 3; ++q3) {
+      const float* v = f[q3];
+      const float2 a = __ldg(reinterpret_cast<const float2*>(v + xo));
+      const float e = __ldg(v + xe);
+      const float2 y0 = __ldg(reinterpret_cast<const float2*>(v + ym));
+      const float2 y1 = __ldg(reinterpret_cast<const float2*>(v + yp));
+      const float2 z0 = __ldg(reinterpret_cast<const float2*>(v + zm));
+      const float2 z1 = __ldg(reinterpret_cast<const float2*>(v + zp));
+      const float xm0 = sigma ? a.x : e, xp0 = sigma ? a.y : a.x;
+      const float xm1 = sigma ? a.y : a.x, xp1 = sigma ? e : a.y;
+      acc[q3][0] = ((xm0 + xp0) + (y0.x + y1.x)) + (z0.x + z1.x);
+      acc[q3][1] = ((xm1 + xp1) + (y0.y + y1.y)) + (z0.y + z1.y);
+    }
+    o0 = __ldg(reinterpret_cast<const float2*>(d1 + c));
+    o1 = __ldg(reinterpret_cast<const float2*>(d2 + c));
+    o2 = __ldg(reinterpret_cast<const float2*>(d3 + c));
+  }
+  const float2 qq = __ldg(reinterpret_cast<const float2*>(q + c));
+  const float2 ra = __ldg(reinterpret_cast<const float2*>(r1 + c));
+  const float2 rb = __ldg(reinterpret_cast<const float2*>(r2 + c));
+  const float2 rc = __ldg(reinterpret_cast<const float2*>(r3 + c));
+  float2 dp, dm, dw;
+  lin_point(L, s0[0], s1[0], s2[0], qq.x, ra.x, rb.x, rc.x, dp.x, dm.x, dw.x);
+  lin_point(L, s0[1], s1[1], s2[1], qq.y, ra.y, rb.y, rc.y, dp.y, dm.y, dw.y);
+  *reinterpret_cast<float2*>(t1 + c) =
+      make_float2(fmaf(w, dp.x - o0.x, o0.x), fmaf(w, dp.y - o0.y, o0.y));
+  *reinterpret_cast<float2*>(t2 + c) =
+      make_float2(fmaf(w, dm.x - o1.x, o1.x), fmaf(w, dm.y - o1.y, o1.y));
+  *reinterpret_cast<float2*>(t3 + c) =
+      make_float2(fmaf(w, dw.x - o2.x, o2.x), fmaf(w, dw.y - o2.y, o2.y));
+}
+
 __global__ void k_copy3(int cells, const float* __restrict__ a1, const float* __restrict__ a2,
                         const float* __restrict__ a3, float* __restrict__ b1,
                         float* __restrict__ b2, float* __restrict__ b3) {
@@ -2285,15 +2357,20 @@ cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* 
                      bool pdl, int nb = 1) {
   const int n = L.n;
   const int64_t cells = (int64_t)n * n * n * nb;
-  const Launch3 g = launch3(n, n, n * nb);
+  const bool pairs = n % 4 == 0;                // two cells per thread, float2 moves
+  const Launch3 g = launch3(pairs ? n / 2 : n, n, n * nb);
   float* src[3] = {d[0], d[1], d[2]};
   float* dst[3] = {t[0], t[1], t[2]};
   int done = 0;
   cudaError_t e = cudaSuccess;
   while (done < sweeps && e == cudaSuccess) {
     const bool z = zero_init && done == 0;
-    e = launch_k(pdl, z ? k_lin_jacobi32<true> : k_lin_jacobi32<false>, g.grid, g.block, 0, st,
-                 L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    if (pairs)
+      e = launch_k(pdl, z ? k_lin_jacobi32x2<true> : k_lin_jacobi32x2<false>, g.grid, g.block, 0,
+                   st, L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
+    else
+      e = launch_k(pdl, z ? k_lin_jacobi32<true> : k_lin_jacobi32<false>, g.grid, g.block, 0,
+                   st, L, w, src[0], src[1], src[2], dst[0], dst[1], dst[2], r[0], r[1], r[2], q);
     done += 1;
     for (int c = 0; c < 3; ++c) {
       float* x = src[c];
