@@ -458,13 +458,15 @@ def run_ours(args):
                    precision=args.precision, **mixed_kw)
     e2e_steps = max(1, min(args.steps, 10))
 
+    bufs = [pin_a, pin_b, pin_out]               # phi^k, phi^{k-1}, phi^{k+1}: rotated
+
     def host_step():
-        B.pfc_set_state(se.ctx, pin_a, pin_b)     # H2D of phi^k, phi^{k-1}
+        a, b, out = bufs
+        B.pfc_set_state(se.ctx, a, b)             # H2D of phi^k, phi^{k-1}
         B.pfc_step(se.ctx, 1)
-        B.pfc_get_phi(se.ctx, pin_out)            # D2H of phi^{k+1}
+        B.pfc_get_phi(se.ctx, out)                # D2H of phi^{k+1}
         B.pfc_diagnostics(se.ctx)                 # D2H of the diagnostics (blocking)
-        pin_b.copy_(pin_a)
-        pin_a.copy_(pin_out)
+        bufs[:] = [out, a, b]
 
     host_step()
     barrier()
