@@ -1257,28 +1257,47 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
 // cell-centred prolongation with the weights 27, 9, 3, 1 over 64 as three
 // one-dimensional passes: the child on the low side of an axis takes
 // (3 e_0 + e_-1)/4, on the high side (3 e_0 + e_+1)/4.  Split layout on both
-// levels.  One thread per coarse cell (I, J, K) and component writes the
-// cell's eight children from its 3x3x3 coarse neighbourhood; the grid's z
-// extent covers planes x components x members, so each thread carries one
-// short load -> interpolate -> store chain.
+// levels.  A block of kPrTI x kPrTJ threads owns that tile of coarse cells
+// of one plane K and one component (the grid's z extent covers planes x
+// components x members): it stages the tile's 3x3x3 neighbourhood (one-cell
+// periodic halo, planes K-1..K+1) in shared memory in natural order with one
+// load per value, then each thread writes its coarse cell's eight children
+// from there.
+constexpr int kPrTI = 32, kPrTJ = 8;
+
 template <bool ASSIGN>
-__global__ void k_prolong_add32(int n, const float* __restrict__ e1,
-                                const float* __restrict__ e2, const float* __restrict__ e3,
-                                float* __restrict__ d1, float* __restrict__ d2,
-                                float* __restrict__ d3) {
+__global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
+    int n, const float* __restrict__ e1, const float* __restrict__ e2,
+    const float* __restrict__ e3, float* __restrict__ d1, float* __restrict__ d2,
+    float* __restrict__ d3) {
   pdl_wait();
   pdl_trigger();
+  __shared__ float sh[3][kPrTJ + 2][kPrTI + 2];
   const int nc = n >> 1, half = n >> 1, hc = nc >> 1;
-  const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
   int K = blockIdx.z;
   const int mf = member_of(K, nc);           // member * 3 + component
   const int m = mf / 3, f = mf - 3 * m;
-  if (I >= nc || J >= nc) return;
   const float* __restrict__ e = (f == 0 ? e1 : f == 1 ? e2 : e3) + (size_t)m * nc * nc * nc;
   float* __restrict__ d = (f == 0 ? d1 : f == 1 ? d2 : d3) + (size_t)m * n * n * n;
-  const int Is[3] = {(I == 0) ? nc - 1 : I - 1, I, (I + 1 == nc) ? 0 : I + 1};
-  const int Js[3] = {(J == 0) ? nc - 1 : J - 1, J, (J + 1 == nc) ? 0 : J + 1};
-  const int Ks[3] = {(K == 0) ? nc - 1 : K - 1, K, (K + 1 == nc) ? 0 : K + 1};
+  const int I0 = blockIdx.x * kPrTI, J0 = blockIdx.y * kPrTJ;
+  constexpr int kW = kPrTI + 2, kPlane = (kPrTJ + 2) * kW;
+  for (int t = threadIdx.x; t < 3 * kPlane; t += blockDim.x) {
+    const int z = t / kPlane, rem = t - z * kPlane, y = rem / kW, x = rem - y * kW;
+    // periodic wraps without a division (the tile may exceed the grid when
+    // nc < kPrTI: then more than one wrap)
+    int Ig = I0 + x - 1, Jg = J0 + y - 1, Kg = K + z - 1;
+    if (Ig < 0) Ig += nc;
+    while (Ig >= nc) Ig -= nc;
+    if (Jg < 0) Jg += nc;
+    while (Jg >= nc) Jg -= nc;
+    if (Kg < 0) Kg += nc;
+    if (Kg >= nc) Kg -= nc;
+    sh[z][y][x] = __ldg(e + (Kg * nc + Jg) * nc + ((Ig + Jg + Kg) & 1) * hc + (Ig >> 1));
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kPrTI, ty = threadIdx.x / kPrTI;
+  const int I = I0 + tx, J = J0 + ty;
+  if (I >= nc || J >= nc) return;
   // the eight children's current values first (independent loads)
   float old[8];
 #pragma unroll
@@ -1295,15 +1314,10 @@ __global__ void k_prolong_add32(int n, const float* __restrict__ e1,
   for (int y = 0; y < 3; ++y) {
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
-      float v[3];
-#pragma unroll
-      for (int z = 0; z < 3; ++z) {
-        const int idx = (Ks[z] * nc + Js[y]) * nc + ((Is[x] + Js[y] + Ks[z]) & 1) * hc +
-                        (Is[x] >> 1);
-        v[z] = __ldg(e + idx);
-      }
-      zx[y][x][0] = fmaf(3.f, v[1], v[0]);
-      zx[y][x][1] = fmaf(3.f, v[1], v[2]);
+      const float v0 = sh[0][ty + y][tx + x], v1 = sh[1][ty + y][tx + x];
+      const float v2 = sh[2][ty + y][tx + x];
+      zx[y][x][0] = fmaf(3.f, v1, v0);
+      zx[y][x][1] = fmaf(3.f, v1, v2);
     }
   }
 #pragma unroll
@@ -2606,10 +2620,10 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
   if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
-  const Launch3 gp = launch3(nc, nc, nc * c.nb * 3);
+  const dim3 gp((nc + kPrTI - 1) / kPrTI, (nc + kPrTJ - 1) / kPrTJ, nc * c.nb * 3);
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
   e = launch_k(c.pr == nullptr, dzero ? k_prolong_add32<true> : k_prolong_add32<false>,
-               gp.grid, gp.block, 0, c.st, L.n,
+               gp, dim3(kPrTI * kPrTJ), 0, c.st, L.n,
                mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
                mx.d[l][2]);
   prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
@@ -2815,9 +2829,9 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
 cudaError_t launch_prolong32(int n, bool assign, const float* e1, const float* e2,
                              const float* e3, float* d1, float* d2, float* d3, cudaStream_t st) {
   const int nc = n / 2;
-  const Launch3 g = launch3(nc, nc, nc * 3);
-  return launch_k(true, assign ? k_prolong_add32<true> : k_prolong_add32<false>, g.grid,
-                  g.block, 0, st, n, e1, e2, e3, d1, d2, d3);
+  const dim3 g((nc + kPrTI - 1) / kPrTI, (nc + kPrTJ - 1) / kPrTJ, nc * 3);
+  return launch_k(true, assign ? k_prolong_add32<true> : k_prolong_add32<false>, g,
+                  dim3(kPrTI * kPrTJ), 0, st, n, e1, e2, e3, d1, d2, d3);
 }
 
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
