@@ -139,6 +139,10 @@ struct pfc_ctx {
   double* c1m;       // (1 - eps_m)/2 per member on the device (null when nb == 1)
   double* eps_host;  // eps per member on the host (nb entries)
   double* M[3];      // face mobilities of the current step (variable mobility only)
+  double *lmu, *lom; // unscaled Laplacians of mu and omega at the last defect's
+                     // iterate (PFC_MIXED with M == 1)
+  int warm;          // the state is the last step's solution and lmu, lom are
+                     // its Laplacians: the next first defect is pointwise
   double tau_scale;  // reference mobility of the FP32 correction solve (1 for M == 1)
   double* t0[3];     // level-0 Jacobi scratch
   double* partials;  // reduction partial sums
@@ -154,7 +158,7 @@ struct pfc_ctx {
   struct Graph {
     cudaGraphExec_t exec;
     long long launches_pre, launches_body;
-  } graph[3];        // one per position of the phi ring
+  } graph[2][3];     // [first defect full / pointwise][position of the phi ring]
 };
 
 namespace pfc {
@@ -176,6 +180,15 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base, int members) {
   for (int q = 0; q < 3; ++q) {
     double* f = variable_mobility(p) ? cv.take<double>(n3) : nullptr;
     if (c) c->M[q] = f;
+  }
+  {
+    const bool keep = p->precision == PFC_MIXED && !variable_mobility(p);
+    double* a = keep ? cv.take<double>(n3) : nullptr;
+    double* b = keep ? cv.take<double>(n3) : nullptr;
+    if (c) {
+      c->lmu = a;
+      c->lom = b;
+    }
   }
   double* mu = cv.take<double>(n3);
   double* om = cv.take<double>(n3);
@@ -294,7 +307,7 @@ int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
 // Sum of squared residuals of the level-0 iterate (to dout[0]) and the
 // convergence decision into dstate.
 int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
-                            int use_handle, int first) {
+                            int use_handle, int first, bool point = false) {
   cudaStream_t st = c->st;
   if (df_state(&c->p)) {
     float2* u[3];
@@ -305,10 +318,14 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
     }
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, u, S, as_df(lv.b), c->partials, c->dout, st,
                                   &c->prof, as_df(c->lap[c->ia])));
+  } else if (point) {
+    PFC_CUDA(mixed_enqueue_defect_point(c->mx, lv.L, lv.u, lv.S, lv.b, c->lap[c->ib], c->lmu,
+                                        c->lom, c->lap[c->ia], c->partials, c->dout, st,
+                                        &c->prof, c->nb, c->c1m));
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
                                   &c->prof, c->lap[c->ia], c->nb, c->c1m,
-                                  c->M[0] ? c->M : nullptr));
+                                  c->M[0] ? c->M : nullptr, c->lmu, c->lom));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
               launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
@@ -324,8 +341,10 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
 
 // Work of a step before its convergence loop: S2, S3 (Eqs. 5.9-5.10), phi^k on
 // the coarse levels (FAS path), the initial guess phi^{k+1} := phi^k, and the
-// first residual and decision.
-int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int use_handle) {
+// first residual and decision (warm: pointwise, from the Laplacians the last
+// step's final defect stored).
+int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int use_handle,
+                bool warm) {
   const double* cprev = c->ring[c->ic];
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   Prof* pr = &c->prof;
@@ -365,7 +384,7 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
                                   c->M[0], c->M[1], c->M[2], c->st));
     c->prof.launches += 1;
   }
-  return enqueue_residual_decide(c, lv, h, use_handle, 1);
+  return enqueue_residual_decide(c, lv, h, use_handle, 1, warm);
 }
 
 // One iteration of the convergence loop: a V-cycle (FP64 FAS) or a defect
@@ -396,21 +415,21 @@ int read_state(pfc_ctx* c) {
 // Build the graph of one step for the current ring position: pre-loop work,
 // then a WHILE node whose body is one loop iteration; k_decide sets the
 // condition on the device, so a step needs one launch and one readback.
-int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g);
+int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g, bool warm);
 
 // Capture on the context's private stream (the caller's stream may be the
 // legacy default stream, which cannot be captured); the graph is launched on
 // the caller's stream.
-int build_graph(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
+int build_graph(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g, bool warm) {
   if (!c->cap_st) PFC_CUDA(cudaStreamCreateWithFlags(&c->cap_st, cudaStreamNonBlocking));
   cudaStream_t user = c->st;
   c->st = c->cap_st;
-  int rc = build_graph_on(c, lv, g);
+  int rc = build_graph_on(c, lv, g, warm);
   c->st = user;
   return rc;
 }
 
-int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
+int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g, bool warm) {
   cudaGraph_t G = nullptr;
   PFC_CUDA(cudaGraphCreate(&G, 0));
   cudaGraphConditionalHandle h;
@@ -424,7 +443,7 @@ int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g) {
     return cuda_fail(e, "graph setup");
   }
   long long l0 = c->prof.launches;
-  int rc = enqueue_pre(c, lv, h, 1);
+  int rc = enqueue_pre(c, lv, h, 1, warm);
   g->launches_pre = c->prof.launches - l0;
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
@@ -496,10 +515,14 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   level0(c, &lv);
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   int rc = PFC_OK;
+  // pointwise first defect: the state is the last step's solution (guess
+  // phi^{k+1} := phi^k) and lmu, lom hold its Laplacians
+  const bool warm = c->warm && c->lmu && c->p.guess == PFC_GUESS_PREVIOUS;
+  c->warm = 0;                       // until this step has converged
   if (c->use_graphs && c->prof.mask == 0) {
-    pfc_ctx::Graph* g = &c->graph[c->ia];
+    pfc_ctx::Graph* g = &c->graph[warm ? 1 : 0][c->ia];
     if (!g->exec) {
-      rc = build_graph(c, lv, g);
+      rc = build_graph(c, lv, g, warm);
       if (rc) return rc;
     }
     PFC_CUDA(cudaGraphLaunch(g->exec, c->st));
@@ -507,7 +530,7 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
     c->prof.launches +=
         g->launches_pre + g->launches_body * (long long)combined_state(c).iters;
   } else {
-    rc = enqueue_pre(c, lv, 0, 0);
+    rc = enqueue_pre(c, lv, 0, 0, warm);
     if (rc == PFC_OK) rc = read_state(c);
     while (rc == PFC_OK && combined_state(c).status == kStepRunning) {
       rc = enqueue_body(c, lv, 0, 0);
@@ -535,6 +558,7 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   c->ib = c->ia;
   c->ia = old_c;
   c->step += 1;
+  c->warm = c->lmu != nullptr;
   if (stats) stats->steps += 1;
   return PFC_OK;
 }
@@ -741,6 +765,7 @@ int pfc_batch_init(pfc_ctx** out, const pfc_params* p, int members, const double
 
 int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev) {
   if (!c || !any_phi) return PFC_EINVAL;
+  c->warm = 0;                       // mu, omega are no longer the state's own
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   const size_t bytes = (size_t)n3 * sizeof(double);
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ib], any_phi, bytes, cudaMemcpyDefault, c->st));
@@ -770,11 +795,12 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
     const double scale = c->p.mobility_m0 + c->p.mobility_m2 * c->hout[1] / (double)n3;
     if (scale != c->tau_scale) {
       // the step graphs hold the FP32 level constants: rebuild them
-      for (int r = 0; r < 3; ++r)
-        if (c->graph[r].exec) {
-          cudaGraphExecDestroy(c->graph[r].exec);
-          c->graph[r].exec = nullptr;
-        }
+      for (int v = 0; v < 2; ++v)
+        for (int r = 0; r < 3; ++r)
+          if (c->graph[v][r].exec) {
+            cudaGraphExecDestroy(c->graph[v][r].exec);
+            c->graph[v][r].exec = nullptr;
+          }
       c->tau_scale = scale;
     }
   }
@@ -985,8 +1011,9 @@ int pfc_profile_read(pfc_ctx* c, int kclass, int level, long long* launches, dou
 void pfc_destroy(pfc_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
-  for (int r = 0; r < 3; ++r)
-    if (c->graph[r].exec) cudaGraphExecDestroy(c->graph[r].exec);
+  for (int v = 0; v < 2; ++v)
+    for (int r = 0; r < 3; ++r)
+      if (c->graph[v][r].exec) cudaGraphExecDestroy(c->graph[v][r].exec);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->hout) cudaFreeHost(c->hout);
   if (c->hstate) cudaFreeHost(c->hstate);

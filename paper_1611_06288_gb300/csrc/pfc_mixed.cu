@@ -283,6 +283,10 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
 // plane ahead.  Threads past the grid edge (n < kFxTX or n < kFxTY) load
 // wrapped cells to fill the tile and write nothing.
 //
+// lap (may be null) receives the unscaled Laplacian of phi, lapmu and lapom
+// (null, or both set) those of mu and omega, for the first defect of the next
+// step (k_defect64_point).
+//
 // Range: inputs with |v| >= 32, Inf or NaN have no fixed-point image.  From
 // the first plane whose tile holds such a value the block evaluates its
 // Laplacians in FP64 from global memory (a block vote per plane); a cell
@@ -318,7 +322,8 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
     const double* __restrict__ om, const double* __restrict__ S1, const double* __restrict__ S2,
     const double* __restrict__ S3, const double* __restrict__ b, float* __restrict__ r1,
     float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
-    double* __restrict__ lap, const double* __restrict__ c1m) {
+    double* __restrict__ lap, const double* __restrict__ c1m, double* __restrict__ lapmu,
+    double* __restrict__ lapom) {
   __shared__ int64_t tile[3][kFxTY + 2][kFxTX + 2];
   __shared__ float sm[32];
   const int n = L.n, nn = n * n;
@@ -330,6 +335,7 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
   phi += off, mu += off, om += off, S1 += off, S2 += off, S3 += off, b += off;
   r1 += off, r2 += off, r3 += off, q += off;
   if (lap) lap += off;
+  if (lapmu) lapmu += off, lapom += off;
   const double c1 = c1m ? c1m[m] : L.c1;
   const float c1f = d2f_rn(c1);
   const int tid = threadIdx.x, tx = tid % kFxTX, ty = tid / kFxTX;   // 1-D block
@@ -423,6 +429,10 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
       r3[o] = zf;
       q[o] = qf;
       if (lap) lap[t] = lap3[0];
+      if (lapmu) {
+        lapmu[t] = lap3[1];
+        lapom[t] = lap3[2];
+      }
     }
     okc = okn;
 #pragma unroll
@@ -437,6 +447,57 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
   if (tid == 0)
     partials[(size_t)m * (gridDim.x * gridDim.y * chunks) +
              ((size_t)zb * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = (double)acc;
+}
+
+// First defect of a step that starts from the previous step's solution
+// (phi^{k+1} := phi^k = b bit for bit, mu and omega kept): r = S - N(u) from
+// the Laplacians the previous step's last defect stored (lapb of phi^k = b,
+// lapmu, lapom), with no stencil.  With phi = b = S1 the rows reduce to
+//   x = tau/h^2 Lap mu,  y = S2 - mu + phi^3 + c1 phi + 1/h^2 Lap om
+//   (f(phi, phi) = phi^3, Eq. 5.2),  z = S3 - om + 1/(2h^2) Lap phi,
+// 8 FP64 operations, each rounded to FP32 on the integer pipe, and
+// q = f'(phi, phi) + c1 = 3/2 phi^2 + c1 in FP32.  lap (the iterate's
+// Laplacian slot) receives lapb.  Grid: blockIdx.y the member, a grid-stride
+// loop over its cells; per-block sums of |r|^2 as k_defect64.
+__global__ void __launch_bounds__(256) k_defect64_point(
+    Lvl L, const double* __restrict__ b, const double* __restrict__ mu,
+    const double* __restrict__ om, const double* __restrict__ S2,
+    const double* __restrict__ S3, const double* __restrict__ lapb,
+    const double* __restrict__ lapmu, const double* __restrict__ lapom, float* __restrict__ r1,
+    float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
+    double* __restrict__ lap, const double* __restrict__ c1m) {
+  __shared__ float sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  const int m = blockIdx.y;
+  const size_t off = (size_t)m * cells;
+  b += off, mu += off, om += off, S2 += off, S3 += off;
+  lapb += off, lapmu += off, lapom += off, lap += off;
+  r1 += off, r2 += off, r3 += off, q += off;
+  partials += (size_t)m * gridDim.x;
+  const double c1 = c1m ? c1m[m] : L.c1;
+  const float c1f = d2f_rn(c1);
+  float acc = 0.f;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const double p = __ldg(b + t), lb = __ldg(lapb + t);
+    const double x = L.tg * __ldg(lapmu + t);
+    const double y =
+        fma(L.g, __ldg(lapom + t), fma(c1, p, fma(p * p, p, __ldg(S2 + t) - __ldg(mu + t))));
+    const double z = fma(L.gh, lb, __ldg(S3 + t) - __ldg(om + t));
+    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
+    const float pf = d2f_rn(p);
+    const float qf = fmaf(1.5f * pf, pf, c1f);
+    acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
+    const int o = split_index(i, j, k, n);
+    r1[o] = xf;
+    r2[o] = yf;
+    r3[o] = zf;
+    q[o] = qf;
+    lap[t] = lb;
+  }
+  acc = block_sum_f(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
 }
 
 // Face mobilities of a step: M(A phi_*) on the faces i+1/2 of each axis for
@@ -2667,14 +2728,15 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* S3, const double* b, float* r1, float* r2, float* r3,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap, int members, const double* c1m, const double* Mx,
-                            const double* My, const double* Mz) {
+                            const double* My, const double* Mz, double* lapmu,
+                            double* lapom) {
   if (!Mx) {
     const int zc = fx_planes(L.n, members, (int64_t)kReduceBlocks * kReduceComps);
     if (zc > 0) {
       const int chunks = (L.n + zc - 1) / zc;
       const dim3 grid((L.n + kFxTX - 1) / kFxTX, (L.n + kFxTY - 1) / kFxTY, chunks * members);
       k_defect64_fx<<<grid, kFxTX * kFxTY, 0, st>>>(L, zc, phi, mu, om, S1, S2, S3, b, r1, r2,
-                                                     r3, q, partials, lap, c1m);
+                                                     r3, q, partials, lap, c1m, lapmu, lapom);
       k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, grid.x * grid.y * chunks, out);
       return cudaGetLastError();
     }
@@ -2691,6 +2753,22 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
   else
     k_defect64<false><<<dim3(nbx, members), kReduceThreads, 0, st>>>(
         L, phi, mu, om, S1, S2, S3, b, r1, r2, r3, q, partials, lap, c1m, Mx, My, Mz);
+  k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, nbx, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_defect64_point(const Lvl& L, const double* b, const double* mu,
+                                  const double* om, const double* S2, const double* S3, const double* lapb, const double* lapmu,
+                                  const double* lapom, float* r1, float* r2, float* r3, float* q,
+                                  double* partials, double* out, double* lap, cudaStream_t st,
+                                  int members, const double* c1m) {
+  const int wave = wave_blocks(k_defect64_point, (int64_t)L.n * L.n * L.n * members);
+  int nbx = wave / members;
+  const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
+  if (nbx > need) nbx = (int)need;
+  if (nbx < 1) nbx = 1;
+  k_defect64_point<<<dim3(nbx, members), kReduceThreads, 0, st>>>(
+      L, b, mu, om, S2, S3, lapb, lapmu, lapom, r1, r2, r3, q, partials, lap, c1m);
   k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, nbx, out);
   return cudaGetLastError();
 }
@@ -2878,12 +2956,27 @@ cudaError_t launch_correct_df(int n, float2* u1, float2* u2, float2* u3, const f
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                  double* const S[3], const double* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
-                                 int members, const double* c1m, double* const M[3]) {
+                                 int members, const double* c1m, double* const M[3],
+                                 double* lapmu, double* lapom) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap,
                                   members, c1m, M ? M[0] : nullptr, M ? M[1] : nullptr,
-                                  M ? M[2] : nullptr);
+                                  M ? M[2] : nullptr, lapmu, lapom);
+  prof_end(pr, PFC_K_DEFECT, 0, 2, st);
+  return e;
+}
+
+cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                       double* const S[3], const double* b,
+                                       const double* lapb, const double* lapmu,
+                                       const double* lapom, double* lap, double* partials,
+                                       double* dout, cudaStream_t st, Prof* pr, int members,
+                                       const double* c1m) {
+  prof_begin(pr, PFC_K_DEFECT, st);
+  cudaError_t e = launch_defect64_point(L0, b, u[1], u[2], S[1], S[2], lapb, lapmu, lapom,
+                                        mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0], partials,
+                                        dout, lap, st, members, c1m);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }

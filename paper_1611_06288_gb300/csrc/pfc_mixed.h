@@ -59,7 +59,18 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
                                  double* const S[3], const double* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
                                  int members = 1, const double* c1m = nullptr,
-                                 double* const M[3] = nullptr);
+                                 double* const M[3] = nullptr, double* lapmu = nullptr,
+                                 double* lapom = nullptr);
+
+// The first defect of a step that starts from the previous step's solution
+// (phi := b, mu and omega kept), pointwise from the Laplacians of b, mu and
+// omega that the previous step's last defect stored; writes lapb to lap.
+cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                       double* const S[3], const double* b,
+                                       const double* lapb, const double* lapmu,
+                                       const double* lapom, double* lap, double* partials,
+                                       double* dout, cudaStream_t st, Prof* pr, int members,
+                                       const double* c1m);
 
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
@@ -131,7 +142,8 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap = nullptr, int members = 1,
                             const double* c1m = nullptr, const double* Mx = nullptr,
-                            const double* My = nullptr, const double* Mz = nullptr);
+                            const double* My = nullptr, const double* Mz = nullptr,
+                            double* lapmu = nullptr, double* lapom = nullptr);
 // Face mobilities M(A phi_*), phi_* = 3/2 b - 1/2 c, M(phi) = m0 + m2 phi^2,
 // face i+1/2 of each axis stored at cell i (FP64).
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,

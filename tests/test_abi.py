@@ -132,7 +132,9 @@ def test_batch_workspace(libpfc):
 
 def test_mobility_params(libpfc):
     """M(phi) = m0 + m2 phi^2 needs m0 > 0, m2 >= 0, and anything but M == 1
-    needs PFC_MIXED; the face mobility fields are part of the workspace."""
+    needs PFC_MIXED; the three face mobility fields are part of the workspace
+    and the two Laplacian fields of the pointwise first defect (M == 1) are
+    not."""
     p = B.pfc_default_params()
     assert (p.mobility_m0, p.mobility_m2) == (1.0, 0.0)
     assert p.cluster_tail == 0
@@ -140,7 +142,7 @@ def test_mobility_params(libpfc):
     p.precision = B.PFC_MIXED
     base = B.pfc_workspace_bytes(p)
     p.mobility_m2 = 5.0
-    assert B.pfc_workspace_bytes(p) >= base + 3 * 8 * 32 ** 3
+    assert B.pfc_workspace_bytes(p) >= base + (3 - 2) * 8 * 32 ** 3
     p.mobility_m0 = 0.0
     assert B.pfc_workspace_bytes(p) == 0
     p.mobility_m0, p.precision = 1.0, B.PFC_FP64

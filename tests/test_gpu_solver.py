@@ -259,3 +259,38 @@ def test_error_codes(graphs):
         s.step(1)
     np.testing.assert_array_equal(host(s.phi()), before)
     assert s.step_index == 0
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_pointwise_first_defect_matches_full_defect(n):
+    """From the second step on, the first defect of a mixed step is formed
+    pointwise from the Laplacians the previous step's last defect stored
+    (the state is that step's solution).  A run forced onto the full stencil
+    defect every step (pfc_set_state with the same fields before each step)
+    reaches the same fields: both converge to the 1e-10 residual tolerance
+    of the same uniquely solvable steps (Prop. 3.1); set_state's FP64
+    Laplacians differ from the stored ones by rounding only.  The warm run's
+    last step also passes the oracle's FP64 residual check."""
+    wl = W.smooth_sweep(n)
+    phi0 = wl.phi0()
+    kw = dict(wl.mixed())
+    a = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-10, precision="mixed", **kw)
+    bsol = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-10, precision="mixed", **kw)
+    hist = [phi0]                                   # phi^0, phi^1, ... of run B
+    for k in range(5):
+        if k == 4:
+            prev_a = host(a.phi())
+        a.step(1)
+        if k > 0:
+            bsol.set_state(hist[-1], hist[-2])     # cold: the full defect again
+        bsol.step(1)
+        hist.append(host(bsol.phi()))
+    pa, pb = host(a.phi()), host(bsol.phi())
+    assert rel_l2(pa, pb) <= 1e-8
+    mu, om = host(a.mu()), host(a.omega())
+    p = O.Params(eps=wl.eps, tau=wl.dt)
+    r = O.residual(O.source_S(prev_a, prev_a, wl.h, p), [pa, mu, om], prev_a, wl.h, p)
+    # rows 1 and 3 need only phi^k (S1 = phi^k, S3 = Lap phi^k / 2)
+    assert np.sqrt(np.mean(r[0] ** 2 + r[2] ** 2) / 3) <= 1e-10 * 1.0001
+    a.close()
+    bsol.close()
