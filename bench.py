@@ -63,14 +63,18 @@ KERNEL_BYTES = {
 # DRAM bytes (read + write) of one launch of a kernel class of a precision,
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
-NCU_TRAFFIC = {("mixed", "defect"): 128.1e6}   # profiles/k_defect64_fx_128.md
+# The defect class of the mixed path averages a step's launches: two full
+# defects (150.2 MB each) and one pointwise first defect (158.7 MB).
+NCU_TRAFFIC = {("mixed", "defect"): 153.0e6}   # profiles/k_defect64_fx_128.md, k_defect64_point_128.md
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
-# counted launch (FMA = 2) and launches per group.  The FP64 defect forms the
-# three Laplacians' neighbour sums in exact int64 fixed point (no FP64
+# counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
+# the three Laplacians' neighbour sums in exact int64 fixed point (no FP64
 # flops) and its rows in 6 DFMA + 4 DADD + 2 DMUL per cell (ncu: DFMA, DADD
-# and DMUL thread-instruction rates 3:2:1): 18 flops.
-KERNEL_FLOPS = {("mixed", "defect"): (18.0, 2)}
+# and DMUL thread-instruction rates 3:2:1): 18 flops; the pointwise first
+# defect of a step 4 DFMA + 2 DADD + 2 DMUL (2:1:1): 12 flops.  With two full
+# defects and one pointwise per step (two corrections): 16 per launch.
+KERNEL_FLOPS = {("mixed", "defect"): (16.0, 2)}
 
 # FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
 # sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
