@@ -337,7 +337,10 @@ def run_ours(args):
         return total, cycles
 
     # ---- mixed path (headline) --------------------------------------------
-    s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+    # every leg forms the energy/mass diagnostics of each new state inside the
+    # step (step_diagnostics): the timed step includes them, with no extra
+    # host round trip
+    s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, step_diagnostics=True,
                   precision=args.precision, **mixed_kw)
     for _ in range(args.warmup):
         s.step(1)
@@ -375,6 +378,7 @@ def run_ours(args):
         for extra in (0, 1):
             kw = dict(mixed_kw, inner_cycles=mixed_kw.get("inner_cycles", 1) + extra)
             sv = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                           step_diagnostics=True,
                            precision="mixed", **kw)
             for _ in range(args.warmup):
                 sv.step(1)
@@ -432,7 +436,8 @@ def run_ours(args):
                 "peak_source": peak_src}
 
     # ---- plain FP64 FAS path, same workload and tolerance -----------------
-    s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="fp64")
+    s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="fp64",
+                    step_diagnostics=True)
     for _ in range(min(args.warmup, 2)):
         s64.step(1)
         s64.diagnostics()
@@ -444,6 +449,7 @@ def run_ours(args):
     # ---- the other mixed form, same workload, tolerance and settings -------
     other = "mixed_df" if args.precision == "mixed" else "mixed"
     so = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision=other,
+                   step_diagnostics=True,
                    **mixed_kw)
     for _ in range(args.warmup):
         so.step(1)
@@ -458,7 +464,7 @@ def run_ours(args):
     pin_a = torch.from_numpy(phi0.copy()).pin_memory()
     pin_b = torch.from_numpy(phi0.copy()).pin_memory()
     pin_out = torch.empty_like(pin_a).pin_memory()
-    se = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+    se = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, step_diagnostics=True,
                    precision=args.precision, **mixed_kw)
     e2e_steps = max(1, min(args.steps, 10))
 

@@ -119,6 +119,13 @@ typedef struct pfc_params {
                                 grid and faster for ensembles.  Same
                                 arithmetic up to summation order and the
                                 approximate division of the pointwise solve */
+  int    step_diagnostics;   /* 1: every step also forms the energy/mass sums
+                                of its new state in the same graph launch
+                                (no further launch or synchronisation), and
+                                pfc_diagnostics, pfc_batch_diagnostics,
+                                pfc_energy and pfc_mass return them until the
+                                state changes; 0 (default): they are formed
+                                on request */
 } pfc_params;
 
 #define PFC_GUESS_PREVIOUS    0  /* phi^{k+1} := phi^k; mu, omega from the last
@@ -144,7 +151,8 @@ typedef struct pfc_step_stats {
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
  * coarse_stiffness 0.05, coarse_sweeps 4, guess PFC_GUESS_PREVIOUS, mobility
- * m0 = 1, m2 = 0, cluster_tail 0.  n, L, eps, dt are set to 0.
+ * m0 = 1, m2 = 0, cluster_tail 0, step_diagnostics 0.  n, L, eps, dt are set
+ * to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

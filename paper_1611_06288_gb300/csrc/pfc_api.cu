@@ -93,6 +93,7 @@ int validate(const pfc_params* p) {
   if (!(p->mobility_m0 > 0) || !(p->mobility_m2 >= 0)) return PFC_EINVAL;
   if (variable_mobility(p) && p->precision != PFC_MIXED) return PFC_EINVAL;
   if (p->cluster_tail != 0 && p->cluster_tail != 1) return PFC_EINVAL;
+  if (p->step_diagnostics != 0 && p->step_diagnostics != 1) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -148,6 +149,9 @@ struct pfc_ctx {
   double* partials;  // reduction partial sums
   double* dout;      // 8 device doubles of reduction results
   double* hout;      // 8 pinned host doubles
+  double* hdiag;     // pinned: the raw diagnostics sums formed by the last step
+                     // (step_diagnostics), valid while diag_valid
+  int diag_valid;
   pfc::MixedBufs mx; // FP32 hierarchy of the mixed path
   int step;
   pfc::Prof prof;    // optional event timing of launches
@@ -302,6 +306,43 @@ int vcycle64(pfc_ctx* c, int l, const Level64& lv) {
                               st));
   prof_end(pr, PFC_K_PROLONG, l, 2, st);
   return smooth_level(c, l, lv, c->p.nu2);
+}
+
+// F_h, the modified energy, the mass and ||grad phi||^2 of every member from
+// the six raw sums of the diagnostics kernel.
+void diagnostics_finish(int n, double h, const double* eps, int members,
+                               const double* hout, double* res) {
+  (void)n;
+  const double h3 = h * h * h;
+  for (int m = 0; m < members; ++m) {
+    const double* o = hout + (size_t)m * kReduceComps;
+    const double F = 0.25 * h3 * o[0] + 0.5 * (1.0 - eps[m]) * h3 * o[1] - h * o[2] +
+                     0.5 * o[3] / h;
+    res[4 * m] = F;
+    res[4 * m + 1] = F + 0.5 * h * o[4];
+    res[4 * m + 2] = h3 * o[5];
+    res[4 * m + 3] = h * o[2];
+  }
+}
+
+// Diagnostics kernels of the state (a, b) and their raw sums copied to hout
+// (asynchronous).
+cudaError_t enqueue_diagnostics(int n, int members, const double* a, const double* b,
+                                const double* lapa, const double* lapb, bool df_fields,
+                                double* partials, double* dout, double* hout, cudaStream_t st) {
+  cudaError_t e;
+  if (df_fields && lapa)
+    e = launch_diagnostics_cached_df(n, as_df(a), as_df(b), as_df(lapa), as_df(lapb), partials,
+                                     dout, st);
+  else if (df_fields)
+    e = launch_diagnostics_df(n, as_df(a), as_df(b), partials, dout, st);
+  else if (lapa)
+    e = launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st, members);
+  else
+    e = launch_diagnostics(n, a, b, partials, dout, st);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(hout, dout, kReduceComps * members * sizeof(double),
+                         cudaMemcpyDeviceToHost, st);
 }
 
 // Sum of squared residuals of the level-0 iterate (to dout[0]) and the
@@ -464,6 +505,13 @@ int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g, bool warm) 
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState) * c->nb,
                           cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess && c->p.step_diagnostics) {
+      // the new state's energy/mass sums in the same graph launch
+      e = enqueue_diagnostics(c->p.n, c->nb, c->ring[c->ia], c->ring[c->ib], c->lap[c->ia],
+                              c->lap[c->ib], df_state(&c->p), c->partials, c->dout, c->hdiag,
+                              c->st);
+      g->launches_pre += 2;
+    }
   }
   cudaGraph_t cap = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(c->st, &cap);
@@ -519,6 +567,7 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   // phi^{k+1} := phi^k) and lmu, lom hold its Laplacians
   const bool warm = c->warm && c->lmu && c->p.guess == PFC_GUESS_PREVIOUS;
   c->warm = 0;                       // until this step has converged
+  c->diag_valid = 0;
   if (c->use_graphs && c->prof.mask == 0) {
     pfc_ctx::Graph* g = &c->graph[warm ? 1 : 0][c->ia];
     if (!g->exec) {
@@ -535,6 +584,13 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
     while (rc == PFC_OK && combined_state(c).status == kStepRunning) {
       rc = enqueue_body(c, lv, 0, 0);
       if (rc == PFC_OK) rc = read_state(c);
+    }
+    if (rc == PFC_OK && c->p.step_diagnostics) {
+      PFC_CUDA(enqueue_diagnostics(c->p.n, c->nb, c->ring[c->ia], c->ring[c->ib], c->lap[c->ia],
+                                   c->lap[c->ib], df_state(&c->p), c->partials, c->dout,
+                                   c->hdiag, c->st));
+      PFC_CUDA(cudaStreamSynchronize(c->st));
+      c->prof.launches += 2;
     }
     if (rc) return rc;
   }
@@ -559,6 +615,7 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   c->ia = old_c;
   c->step += 1;
   c->warm = c->lmu != nullptr;
+  c->diag_valid = c->p.step_diagnostics;
   if (stats) stats->steps += 1;
   return PFC_OK;
 }
@@ -631,6 +688,7 @@ void pfc_default_params(pfc_params* p) {
   p->mobility_m0 = 1.0;
   p->mobility_m2 = 0.0;
   p->cluster_tail = 0;
+  p->step_diagnostics = 0;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {
@@ -710,8 +768,12 @@ static int init_members(pfc_ctx** out, const pfc_params* p, int members, const d
                     cudaHostAllocDefault);
   if (e == cudaSuccess)
     e = cudaHostAlloc((void**)&c->hstate, sizeof(StepState) * members, cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc((void**)&c->hdiag, kReduceComps * sizeof(double) * members,
+                      cudaHostAllocDefault);
   if (e != cudaSuccess) {
     if (c->hout) cudaFreeHost(c->hout);
+    if (c->hstate) cudaFreeHost(c->hstate);
     free(c->eps_host);
     free(c);
     return cuda_fail(e, "cudaHostAlloc");
@@ -766,6 +828,7 @@ int pfc_batch_init(pfc_ctx** out, const pfc_params* p, int members, const double
 int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev) {
   if (!c || !any_phi) return PFC_EINVAL;
   c->warm = 0;                       // mu, omega are no longer the state's own
+  c->diag_valid = 0;
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   const size_t bytes = (size_t)n3 * sizeof(double);
   PFC_CUDA(cudaMemcpyAsync(c->ring[c->ib], any_phi, bytes, cudaMemcpyDefault, c->st));
@@ -852,33 +915,20 @@ static int diagnostics(int n, double h, const double* eps, int members, const do
                        const double* b, const double* lapa, const double* lapb,
                        bool df_fields, double* partials, double* dout, double* hout,
                        cudaStream_t st, double* res) {
-  if (df_fields && lapa)
-    PFC_CUDA(launch_diagnostics_cached_df(n, as_df(a), as_df(b), as_df(lapa), as_df(lapb),
-                                          partials, dout, st));
-  else if (df_fields)
-    PFC_CUDA(launch_diagnostics_df(n, as_df(a), as_df(b), partials, dout, st));
-  else if (lapa)
-    PFC_CUDA(launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st, members));
-  else
-    PFC_CUDA(launch_diagnostics(n, a, b, partials, dout, st));
-  PFC_CUDA(cudaMemcpyAsync(hout, dout, kReduceComps * members * sizeof(double),
-                           cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(enqueue_diagnostics(n, members, a, b, lapa, lapb, df_fields, partials, dout, hout,
+                               st));
   PFC_CUDA(cudaStreamSynchronize(st));
-  const double h3 = h * h * h;
-  for (int m = 0; m < members; ++m) {
-    const double* o = hout + (size_t)m * kReduceComps;
-    const double F = 0.25 * h3 * o[0] + 0.5 * (1.0 - eps[m]) * h3 * o[1] - h * o[2] +
-                     0.5 * o[3] / h;
-    res[4 * m] = F;
-    res[4 * m + 1] = F + 0.5 * h * o[4];
-    res[4 * m + 2] = h3 * o[5];
-    res[4 * m + 3] = h * o[2];
-  }
+  diagnostics_finish(n, h, eps, members, hout, res);
   return PFC_OK;
 }
 
 int pfc_batch_diagnostics(pfc_ctx* c, double* out) {
   if (!c || !out) return PFC_EINVAL;
+  if (c->diag_valid) {
+    // formed by the last step (step_diagnostics): no further GPU work
+    diagnostics_finish(c->p.n, c->p.L / c->p.n, c->eps_host, c->nb, c->hdiag, out);
+    return PFC_OK;
+  }
   c->prof.launches += 2;
   return diagnostics(c->p.n, c->p.L / c->p.n, c->eps_host, c->nb, c->ring[c->ib],
                      c->ring[c->ic], c->lap[c->ib], c->lap[c->ic], df_state(&c->p),
@@ -1017,6 +1067,7 @@ void pfc_destroy(pfc_ctx* c) {
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
   if (c->hout) cudaFreeHost(c->hout);
   if (c->hstate) cudaFreeHost(c->hstate);
+  if (c->hdiag) cudaFreeHost(c->hdiag);
   free(c->eps_host);
   if (c->prof.created)
     for (int i = 0; i < 2 * Prof::kPool; ++i) cudaEventDestroy(c->prof.ev[i]);

@@ -32,6 +32,7 @@ def soak(n=128, steps=10000, precision="mixed", every=1, device="cuda", workload
     wl = W.growth(n, steps) if workload == "growth" else W.polycrystal(n, steps)
     kw = wl.mixed() if precision != "fp64" else {}
     s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), device=device, tol=wl.tol,
+                  step_diagnostics=every == 1,
                   precision=precision, max_cycles=100, **kw)
     try:
         d = s.diagnostics()

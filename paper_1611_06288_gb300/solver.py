@@ -20,7 +20,8 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
                 inner_cycles=1, policy="hybrid", jacobi_weight=0.7, jacobi_factor=4,
                 jacobi_factor0=2, stiff_hi=1000.0, stiff_lo=0.25,
                 coarse_stiffness=0.05, coarse_sweeps=4,
-                guess="previous", mobility=(1.0, 0.0), cluster_tail=False) -> B.pfc_params:
+                guess="previous", mobility=(1.0, 0.0), cluster_tail=False,
+                step_diagnostics=False) -> B.pfc_params:
     p = B.pfc_default_params()
     p.n, p.L, p.eps, p.dt = int(n), float(L), float(eps), float(dt)
     p.tol, p.nu1, p.nu2, p.max_cycles = float(tol), int(nu1), int(nu2), int(max_cycles)
@@ -38,6 +39,7 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
     p.guess = {"previous": B.PFC_GUESS_PREVIOUS, "extrapolate": B.PFC_GUESS_EXTRAPOLATE}[guess]
     p.mobility_m0, p.mobility_m2 = float(mobility[0]), float(mobility[1])
     p.cluster_tail = 1 if cluster_tail else 0
+    p.step_diagnostics = 1 if step_diagnostics else 0
     return p
 
 

@@ -162,3 +162,15 @@ def test_cluster_tail_param(libpfc):
     assert B.pfc_workspace_bytes(p) == off > 0
     p.cluster_tail = 2
     assert B.pfc_workspace_bytes(p) == 0
+
+
+def test_step_diagnostics_param(libpfc):
+    """step_diagnostics is 0 (default) or 1 and needs no workspace."""
+    p = B.pfc_default_params()
+    assert p.step_diagnostics == 0
+    p.n, p.L, p.eps, p.dt = 32, 32.0, 0.1, 0.05
+    base = B.pfc_workspace_bytes(p)
+    p.step_diagnostics = 1
+    assert B.pfc_workspace_bytes(p) == base > 0
+    p.step_diagnostics = 2
+    assert B.pfc_workspace_bytes(p) == 0

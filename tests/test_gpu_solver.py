@@ -294,3 +294,30 @@ def test_pointwise_first_defect_matches_full_defect(n):
     assert np.sqrt(np.mean(r[0] ** 2 + r[2] ** 2) / 3) <= 1e-10 * 1.0001
     a.close()
     bsol.close()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp64"])
+def test_step_diagnostics_match_on_request(precision):
+    """step_diagnostics forms the energy/mass sums of each new state inside
+    the step's graph; pfc_diagnostics then returns them without a launch.
+    They equal the on-request values bit for bit (same kernels, same
+    inputs), and after pfc_set_state they are formed on request again."""
+    wl = W.smooth_sweep(32)
+    phi0 = wl.phi0()
+    kw = wl.mixed() if precision != "fp64" else {}
+    runs = []
+    for sd in (True, False):
+        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-10, precision=precision,
+                      step_diagnostics=sd, **kw)
+        out = []
+        for _ in range(3):
+            s.step(1)
+            launches = B.pfc_launch_count(s.ctx)
+            out.append(s.diagnostics())
+            if sd:
+                assert B.pfc_launch_count(s.ctx) == launches      # nothing launched
+        s.set_state(host(s.phi()))
+        out.append(s.diagnostics())
+        runs.append(out)
+        s.close()
+    assert runs[0] == runs[1]
