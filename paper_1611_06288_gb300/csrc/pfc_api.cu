@@ -329,7 +329,8 @@ void diagnostics_finish(int n, double h, const double* eps, int members,
 // (asynchronous).
 cudaError_t enqueue_diagnostics(int n, int members, const double* a, const double* b,
                                 const double* lapa, const double* lapb, bool df_fields,
-                                double* partials, double* dout, double* hout, cudaStream_t st) {
+                                double* partials, double* dout, double* hout, cudaStream_t st,
+                                bool pdl = false) {
   cudaError_t e;
   if (df_fields && lapa)
     e = launch_diagnostics_cached_df(n, as_df(a), as_df(b), as_df(lapa), as_df(lapb), partials,
@@ -337,7 +338,7 @@ cudaError_t enqueue_diagnostics(int n, int members, const double* a, const doubl
   else if (df_fields)
     e = launch_diagnostics_df(n, as_df(a), as_df(b), partials, dout, st);
   else if (lapa)
-    e = launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st, members);
+    e = launch_diagnostics_cached(n, a, b, lapa, lapb, partials, dout, st, members, pdl);
   else
     e = launch_diagnostics(n, a, b, partials, dout, st);
   if (e != cudaSuccess) return e;
@@ -375,7 +376,7 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
   }
   const double n3 = (double)c->p.n * c->p.n * c->p.n;
   PFC_CUDA(launch_decide(h, use_handle, c->dout, c->dstate, 1.0 / (3.0 * n3), c->p.tol,
-                         c->p.max_cycles, first, st, c->nb));
+                         c->p.max_cycles, first, st, c->nb, c->prof.mask == 0));
   c->prof.launches += 1;
   return PFC_OK;
 }
@@ -406,7 +407,7 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   } else {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
               launch_source_cached(lv.L, lv.b, c->lap[c->ib], c->lap[c->ic], c->S2, c->S3,
-                                   c->st, c->nb, c->c1m));
+                                   c->st, c->nb, c->c1m, c->prof.mask == 0));
   }
   if (c->p.precision == PFC_FP64) {
     const double* fine = lv.b;
@@ -509,7 +510,7 @@ int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g, bool warm) 
       // the new state's energy/mass sums in the same graph launch
       e = enqueue_diagnostics(c->p.n, c->nb, c->ring[c->ia], c->ring[c->ib], c->lap[c->ia],
                               c->lap[c->ib], df_state(&c->p), c->partials, c->dout, c->hdiag,
-                              c->st);
+                              c->st, c->prof.mask == 0);
       g->launches_pre += 2;
     }
   }

@@ -204,6 +204,24 @@ __device__ __forceinline__ double f2d(float f) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// Launch with programmatic stream serialization when `pdl` is set (the
+// kernel must call pdl_wait() before it reads what its predecessor wrote).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+
 // Block-wide sum of NV doubles into thread 0 (fixed order: deterministic).
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* 32*NV */) {

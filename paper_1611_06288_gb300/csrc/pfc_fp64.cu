@@ -102,6 +102,8 @@ __global__ void k_source_cached(Lvl L, int members, const double* __restrict__ c
                                 const double* __restrict__ b,
                                 const double* __restrict__ lapb, const double* __restrict__ lapc,
                                 double* __restrict__ S2, double* __restrict__ S3) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t cells = (int64_t)L.n * L.n * L.n;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cells * members) return;
@@ -439,6 +441,8 @@ __global__ void k_residual_norm2(Lvl L, const double* __restrict__ phi,
 template <int NV>
 __global__ void k_reduce_final(const double* __restrict__ partials, int nparts,
                                double* out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sm[32 * NV];
   partials += (size_t)blockIdx.x * nparts * NV;
   out += (size_t)blockIdx.x * kReduceComps;
@@ -494,6 +498,8 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
                                      const double* __restrict__ b,
                                      const double* __restrict__ lapa,
                                      const double* __restrict__ lapb, double* partials) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sm[32 * 6];
   const int cells = n * n * n;
   const size_t off = (size_t)blockIdx.y * cells;     // member of an ensemble
@@ -522,6 +528,8 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
 __global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
                          const double* sum, StepState* s, int members, double inv_3n3,
                          double tol, int max_iter, int first) {
+  pdl_wait();
+  pdl_trigger();
   // one thread per ensemble member (sum[m] its sum of squared residuals);
   // a member that has converged stays converged, and the loop runs while
   // some member is still running and none has failed
@@ -583,21 +591,22 @@ cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t s
 
 cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* lapb,
                                  const double* lapc, double* S2, double* S3, cudaStream_t st,
-                                 int members, const double* c1m) {
-  k_source_cached<<<grid_for((int64_t)L.n * L.n * L.n * members), kThreads, 0, st>>>(
-      L, members, c1m, b, lapb, lapc, S2, S3);
-  return cudaGetLastError();
+                                 int members, const double* c1m, bool pdl) {
+  return launch_ex(pdl, k_source_cached, dim3(grid_for((int64_t)L.n * L.n * L.n * members)),
+                   dim3(kThreads), 0, st, L, members, c1m, b, lapb, lapc, S2, S3);
 }
 
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
-                                      double* out, cudaStream_t st, int members) {
+                                      double* out, cudaStream_t st, int members, bool pdl) {
   int nb = reduce_blocks((int64_t)n * n * n * members) / members;
   if (nb < 1) nb = 1;
-  k_diagnostics_cached<<<dim3(nb, members), kReduceThreads, 0, st>>>(n, a, b, lapa, lapb,
-                                                                     partials);
-  k_reduce_final<6><<<members, kReduceThreads, 0, st>>>(partials, nb, out);
-  return cudaGetLastError();
+  cudaError_t e = launch_ex(pdl, k_diagnostics_cached, dim3(nb, members), dim3(kReduceThreads), 0,
+                            st, n, a, b, lapa, lapb, partials);
+  if (e == cudaSuccess)
+    e = launch_ex(pdl, k_reduce_final<6>, dim3(members), dim3(kReduceThreads), 0, st,
+                  (const double*)partials, nb, out);
+  return e;
 }
 
 cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double* S2,
@@ -736,11 +745,10 @@ cudaError_t launch_residual_norm2(const Lvl& L, const double* phi, const double*
 
 cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
                           const double* sum, StepState* state, double inv_3n3, double tol,
-                          int max_iter, int first, cudaStream_t st, int members) {
+                          int max_iter, int first, cudaStream_t st, int members, bool pdl) {
   const int threads = ((members + 31) / 32) * 32;
-  k_decide<<<1, threads, 0, st>>>(handle, use_handle, sum, state, members, inv_3n3, tol,
-                                  max_iter, first);
-  return cudaGetLastError();
+  return launch_ex(pdl, k_decide, dim3(1), dim3(threads), 0, st, handle, use_handle, sum, state,
+                   members, inv_3n3, tol, max_iter, first);
 }
 
 cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,

@@ -43,7 +43,8 @@ constexpr int kStepRunning = 0, kStepConverged = 1, kStepNaN = 2, kStepNoConv = 
 // "keep going" while some member runs and none has failed.
 cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
                           const double* sum, StepState* state, double inv_3n3, double tol,
-                          int max_iter, int first, cudaStream_t st, int members = 1);
+                          int max_iter, int first, cudaStream_t st, int members = 1,
+                          bool pdl = false);
 
 // Detail string returned by pfc_last_error() on this host thread.
 void set_last_error(const char* msg);
@@ -116,11 +117,12 @@ cudaError_t launch_laplacian(int n, const double* v, double* lap, cudaStream_t s
 // S2, S3 from b and the stored unscaled Laplacians of b and c.
 cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* lapb,
                                  const double* lapc, double* S2, double* S3, cudaStream_t st,
-                                 int members = 1, const double* c1m = nullptr);
+                                 int members = 1, const double* c1m = nullptr, bool pdl = false);
 // launch_diagnostics from the stored unscaled Laplacians of a and b.
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
-                                      double* out, cudaStream_t st, int members = 1);
+                                      double* out, cudaStream_t st, int members = 1,
+                                      bool pdl = false);
 // out[0..5] = sum a^4, sum a^2, sum |D a|^2 (faces), sum (Lap a)^2 (times h^4
 // removed: raw stencil sums), sum |D(a-b)|^2, sum a.  Raw sums; the host scales.
 cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,

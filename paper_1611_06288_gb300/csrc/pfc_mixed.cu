@@ -324,6 +324,8 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
     float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
     double* __restrict__ lap, const double* __restrict__ c1m, double* __restrict__ lapmu,
     double* __restrict__ lapom) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int64_t tile[3][kFxTY + 2][kFxTX + 2];
   __shared__ float sm[32];
   const int n = L.n, nn = n * n;
@@ -466,6 +468,8 @@ __global__ void __launch_bounds__(256) k_defect64_point(
     const double* __restrict__ lapmu, const double* __restrict__ lapom, float* __restrict__ r1,
     float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
     double* __restrict__ lap, const double* __restrict__ c1m) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ float sm[32];
   const int n = L.n;
   const int cells = n * n * n;
@@ -932,6 +936,8 @@ __global__ void k_df_to_f64(int64_t count, const float2* y, double* x) {
 
 // Fixed-order sum of each member's partials (one block per member): out[m].
 __global__ void k_reduce1(const double* __restrict__ partials, int nparts, double* out) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double sm[32];
   const int m = blockIdx.x;
   partials += (size_t)m * nparts;
@@ -2729,16 +2735,19 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap, int members, const double* c1m, const double* Mx,
                             const double* My, const double* Mz, double* lapmu,
-                            double* lapom) {
+                            double* lapom, bool pdl) {
   if (!Mx) {
     const int zc = fx_planes(L.n, members, (int64_t)kReduceBlocks * kReduceComps);
     if (zc > 0) {
       const int chunks = (L.n + zc - 1) / zc;
       const dim3 grid((L.n + kFxTX - 1) / kFxTX, (L.n + kFxTY - 1) / kFxTY, chunks * members);
-      k_defect64_fx<<<grid, kFxTX * kFxTY, 0, st>>>(L, zc, phi, mu, om, S1, S2, S3, b, r1, r2,
-                                                     r3, q, partials, lap, c1m, lapmu, lapom);
-      k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, grid.x * grid.y * chunks, out);
-      return cudaGetLastError();
+      cudaError_t e = launch_ex(pdl, k_defect64_fx, grid, dim3(kFxTX * kFxTY), 0, st, L, zc, phi,
+                                mu, om, S1, S2, S3, b, r1, r2, r3, q, partials, lap, c1m, lapmu,
+                                lapom);
+      if (e == cudaSuccess)
+        e = launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st,
+                      (const double*)partials, (int)(grid.x * grid.y * chunks), out);
+      return e;
     }
   }
   // one resident wave over all members: blocks per member = wave / members
@@ -2761,16 +2770,19 @@ cudaError_t launch_defect64_point(const Lvl& L, const double* b, const double* m
                                   const double* om, const double* S2, const double* S3, const double* lapb, const double* lapmu,
                                   const double* lapom, float* r1, float* r2, float* r3, float* q,
                                   double* partials, double* out, double* lap, cudaStream_t st,
-                                  int members, const double* c1m) {
+                                  int members, const double* c1m, bool pdl) {
   const int wave = wave_blocks(k_defect64_point, (int64_t)L.n * L.n * L.n * members);
   int nbx = wave / members;
   const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
   if (nbx > need) nbx = (int)need;
   if (nbx < 1) nbx = 1;
-  k_defect64_point<<<dim3(nbx, members), kReduceThreads, 0, st>>>(
-      L, b, mu, om, S2, S3, lapb, lapmu, lapom, r1, r2, r3, q, partials, lap, c1m);
-  k_reduce1<<<members, kReduceThreads, 0, st>>>(partials, nbx, out);
-  return cudaGetLastError();
+  cudaError_t e = launch_ex(pdl, k_defect64_point, dim3(nbx, members), dim3(kReduceThreads), 0,
+                            st, L, b, mu, om, S2, S3, lapb, lapmu, lapom, r1, r2, r3, q, partials,
+                            lap, c1m);
+  if (e == cudaSuccess)
+    e = launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st,
+                  (const double*)partials, nbx, out);
+  return e;
 }
 
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
@@ -2962,7 +2974,7 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap,
                                   members, c1m, M ? M[0] : nullptr, M ? M[1] : nullptr,
-                                  M ? M[2] : nullptr, lapmu, lapom);
+                                  M ? M[2] : nullptr, lapmu, lapom, !pr || pr->mask == 0);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
@@ -2976,7 +2988,7 @@ cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* con
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64_point(L0, b, u[1], u[2], S[1], S[2], lapb, lapmu, lapom,
                                         mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0], partials,
-                                        dout, lap, st, members, c1m);
+                                        dout, lap, st, members, c1m, !pr || pr->mask == 0);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }

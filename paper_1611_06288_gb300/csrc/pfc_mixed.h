@@ -143,7 +143,8 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             double* lap = nullptr, int members = 1,
                             const double* c1m = nullptr, const double* Mx = nullptr,
                             const double* My = nullptr, const double* Mz = nullptr,
-                            double* lapmu = nullptr, double* lapom = nullptr);
+                            double* lapmu = nullptr, double* lapom = nullptr,
+                            bool pdl = false);
 // Face mobilities M(A phi_*), phi_* = 3/2 b - 1/2 c, M(phi) = m0 + m2 phi^2,
 // face i+1/2 of each axis stored at cell i (FP64).
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
