@@ -126,6 +126,12 @@ typedef struct pfc_params {
                                 pfc_energy and pfc_mass return them until the
                                 state changes; 0 (default): they are formed
                                 on request */
+  int    defect_planes;      /* PFC_MIXED: planes per thread block of the FP64
+                                defect (its tiles are 32 x 8 cells x this many
+                                planes); 0 (default) chooses them from the SM
+                                count (fewest waves), a value > 0 fixes them
+                                (an autotuner's choice; larger than n means
+                                n) */
 } pfc_params;
 
 #define PFC_GUESS_PREVIOUS    0  /* phi^{k+1} := phi^k; mu, omega from the last
@@ -151,8 +157,8 @@ typedef struct pfc_step_stats {
  * FP64, coarsest 2, inner_cycles 1, hybrid policy with Jacobi weight 0.7,
  * factor 4 (2 on the finest level), stiff_hi 1000, stiff_lo 0.25,
  * coarse_stiffness 0.05, coarse_sweeps 4, guess PFC_GUESS_PREVIOUS, mobility
- * m0 = 1, m2 = 0, cluster_tail 0, step_diagnostics 0.  n, L, eps, dt are set
- * to 0.
+ * m0 = 1, m2 = 0, cluster_tail 0, step_diagnostics 0, defect_planes 0.  n, L,
+ * eps, dt are set to 0.
  *
  * Why the hybrid policy: on the split system the red-black pointwise sweep
  * of Section 5 amplifies the error pair made of the constant mode and the

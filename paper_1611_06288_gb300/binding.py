@@ -43,7 +43,8 @@ class pfc_params(ctypes.Structure):
                 ("stiff_lo", ctypes.c_double), ("coarse_stiffness", ctypes.c_double),
                 ("coarse_sweeps", ctypes.c_int), ("guess", ctypes.c_int),
                 ("mobility_m0", ctypes.c_double), ("mobility_m2", ctypes.c_double),
-                ("cluster_tail", ctypes.c_int), ("step_diagnostics", ctypes.c_int)]
+                ("cluster_tail", ctypes.c_int), ("step_diagnostics", ctypes.c_int),
+                ("defect_planes", ctypes.c_int)]
 
 
 class pfc_step_stats(ctypes.Structure):

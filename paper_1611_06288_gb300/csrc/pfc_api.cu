@@ -94,6 +94,7 @@ int validate(const pfc_params* p) {
   if (variable_mobility(p) && p->precision != PFC_MIXED) return PFC_EINVAL;
   if (p->cluster_tail != 0 && p->cluster_tail != 1) return PFC_EINVAL;
   if (p->step_diagnostics != 0 && p->step_diagnostics != 1) return PFC_EINVAL;
+  if (p->defect_planes < 0) return PFC_EINVAL;
   int sizes[kMaxLevels];
   const int nl = level_sizes(p, sizes);
   const int nc = sizes[nl - 1];
@@ -367,7 +368,8 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
                                   &c->prof, c->lap[c->ia], c->nb, c->c1m,
-                                  c->M[0] ? c->M : nullptr, c->lmu, c->lom));
+                                  c->M[0] ? c->M : nullptr, c->lmu, c->lom,
+                                  c->p.defect_planes));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
               launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
@@ -690,6 +692,7 @@ void pfc_default_params(pfc_params* p) {
   p->mobility_m2 = 0.0;
   p->cluster_tail = 0;
   p->step_diagnostics = 0;
+  p->defect_planes = 0;
 }
 
 int pfc_level_info(const pfc_params* p, int level, int* n, double* h, int* kind) {

@@ -2735,9 +2735,17 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap, int members, const double* c1m, const double* Mx,
                             const double* My, const double* Mz, double* lapmu,
-                            double* lapom, bool pdl) {
+                            double* lapom, bool pdl, int planes) {
   if (!Mx) {
-    const int zc = fx_planes(L.n, members, (int64_t)kReduceBlocks * kReduceComps);
+    const int64_t cap = (int64_t)kReduceBlocks * kReduceComps;
+    int zc = fx_planes(L.n, members, cap);
+    if (planes > 0 && zc > 0) {
+      // a fixed choice, where its blocks fit the partial-sum buffer and grid
+      const int z = planes < L.n ? planes : L.n, ch = (L.n + z - 1) / z;
+      const int64_t blocks = (int64_t)((L.n + kFxTX - 1) / kFxTX) *
+                             ((L.n + kFxTY - 1) / kFxTY) * ch * members;
+      if (blocks <= cap && (int64_t)ch * members <= 65535) zc = z;
+    }
     if (zc > 0) {
       const int chunks = (L.n + zc - 1) / zc;
       const dim3 grid((L.n + kFxTX - 1) / kFxTX, (L.n + kFxTY - 1) / kFxTY, chunks * members);
@@ -2969,12 +2977,13 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
                                  double* const S[3], const double* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
                                  int members, const double* c1m, double* const M[3],
-                                 double* lapmu, double* lapom) {
+                                 double* lapmu, double* lapom, int planes) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap,
                                   members, c1m, M ? M[0] : nullptr, M ? M[1] : nullptr,
-                                  M ? M[2] : nullptr, lapmu, lapom, !pr || pr->mask == 0);
+                                  M ? M[2] : nullptr, lapmu, lapom, !pr || pr->mask == 0,
+                                  planes);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }

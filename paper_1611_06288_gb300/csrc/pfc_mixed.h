@@ -60,7 +60,7 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
                                  int members = 1, const double* c1m = nullptr,
                                  double* const M[3] = nullptr, double* lapmu = nullptr,
-                                 double* lapom = nullptr);
+                                 double* lapom = nullptr, int planes = 0);
 
 // The first defect of a step that starts from the previous step's solution
 // (phi := b, mu and omega kept), pointwise from the Laplacians of b, mu and
@@ -144,7 +144,7 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* c1m = nullptr, const double* Mx = nullptr,
                             const double* My = nullptr, const double* Mz = nullptr,
                             double* lapmu = nullptr, double* lapom = nullptr,
-                            bool pdl = false);
+                            bool pdl = false, int planes = 0);
 // Face mobilities M(A phi_*), phi_* = 3/2 b - 1/2 c, M(phi) = m0 + m2 phi^2,
 // face i+1/2 of each axis stored at cell i (FP64).
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,

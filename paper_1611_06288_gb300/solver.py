@@ -21,7 +21,7 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
                 jacobi_factor0=2, stiff_hi=1000.0, stiff_lo=0.25,
                 coarse_stiffness=0.05, coarse_sweeps=4,
                 guess="previous", mobility=(1.0, 0.0), cluster_tail=False,
-                step_diagnostics=False) -> B.pfc_params:
+                step_diagnostics=False, defect_planes=0) -> B.pfc_params:
     p = B.pfc_default_params()
     p.n, p.L, p.eps, p.dt = int(n), float(L), float(eps), float(dt)
     p.tol, p.nu1, p.nu2, p.max_cycles = float(tol), int(nu1), int(nu2), int(max_cycles)
@@ -40,6 +40,7 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
     p.mobility_m0, p.mobility_m2 = float(mobility[0]), float(mobility[1])
     p.cluster_tail = 1 if cluster_tail else 0
     p.step_diagnostics = 1 if step_diagnostics else 0
+    p.defect_planes = int(defect_planes)
     return p
 
 

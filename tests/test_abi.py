@@ -174,3 +174,19 @@ def test_step_diagnostics_param(libpfc):
     assert B.pfc_workspace_bytes(p) == base > 0
     p.step_diagnostics = 2
     assert B.pfc_workspace_bytes(p) == 0
+
+
+def test_defect_planes_param(libpfc):
+    """defect_planes is >= 0 (default 0, the SM-count heuristic) and needs no
+    workspace: a fixed depth whose blocks would not fit the per-block partial
+    sums falls back to the heuristic at launch."""
+    p = B.pfc_default_params()
+    assert p.defect_planes == 0
+    p.n, p.L, p.eps, p.dt = 64, 32.0, 0.1, 0.05
+    p.precision = B.PFC_MIXED
+    base = B.pfc_workspace_bytes(p)
+    for z in (1, 8, 64, 1000):
+        p.defect_planes = z
+        assert B.pfc_workspace_bytes(p) == base > 0
+    p.defect_planes = -1
+    assert B.pfc_workspace_bytes(p) == 0

@@ -3,7 +3,7 @@ the choice of the fastest converged candidate."""
 
 import pytest
 
-from paper_1611_06288_gb300.autotune import DEFAULT_SPACE, candidates, select
+from paper_1611_06288_gb300.autotune import DEFAULT_SPACE, candidates, select, tile_candidates
 
 
 def test_candidates_cover_the_space():
@@ -12,6 +12,16 @@ def test_candidates_cover_the_space():
          * len(DEFAULT_SPACE["jacobi_factor"]) * len(DEFAULT_SPACE["coarse_sweeps"]))
     assert len(c) == n and len({tuple(sorted(x.items())) for x in c}) == n
     assert {(x["nu1"], x["nu2"]) for x in c} == set(DEFAULT_SPACE["nu"])
+    assert all("defect_planes" not in x for x in c)
+
+
+def test_tile_stage_keeps_the_cycle_settings():
+    best = {"nu1": 0, "nu2": 1, "inner_cycles": 2, "jacobi_factor": 4, "coarse_sweeps": 2}
+    t = tile_candidates(best)
+    assert [x["defect_planes"] for x in t] == DEFAULT_SPACE["defect_planes"]
+    assert all({k: v for k, v in x.items() if k != "defect_planes"} == best for x in t)
+    assert 0 in DEFAULT_SPACE["defect_planes"]        # the heuristic stays a candidate
+    assert tile_candidates(best, {"nu": [(0, 1)]}) == []
 
 
 def test_select_fastest_converged():

@@ -87,9 +87,10 @@ def test_autotune_picks_a_converging_setting():
     from paper_1611_06288_gb300.autotune import tune
     eps, phi0 = members(32, 3, 7)
     space = {"nu": [(0, 1), (1, 2)], "inner_cycles": [2], "jacobi_factor": [3],
-             "coarse_sweeps": [2]}
+             "coarse_sweeps": [2], "defect_planes": [0, 8]}
     best, table = tune(32, 32.0, eps, 0.05, phi0, space=space, steps=2, warmup=1)
-    assert best in [kw for kw, _ in table] and len(table) == 2
+    assert best in [kw for kw, _ in table] and len(table) == 4
+    assert best["defect_planes"] in (0, 8)
     b = PFCBatch(32, 32.0, eps, 0.05, phi0, tol=1e-9, **best)
     b.step(2)
     _, res, _ = b.status()

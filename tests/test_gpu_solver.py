@@ -321,3 +321,37 @@ def test_step_diagnostics_match_on_request(precision):
         runs.append(out)
         s.close()
     assert runs[0] == runs[1]
+
+
+@pytest.mark.parametrize("n", [48, 64])
+def test_defect_tile_depth_does_not_change_the_step(n):
+    """defect_planes fixes the planes per block of the FP64 defect (the
+    autotuner's tile dimension): 1 plane per block, ragged last columns
+    (5 planes of 48 or 64), one column per tile (n and beyond) and the
+    heuristic's choice.  Each cell's rows are the same arithmetic whatever the
+    tile, so r and the iterates are identical; only the residual norm's
+    summation order changes.  Equal cycle counts therefore give bit-equal
+    fields.  Each thread sums the three rows' squares over its planes and the
+    block over its threads in FP32 (positive terms: relative error <=
+    (terms - 1) 2^-24), so each norm is within (3n + 256) 2^-24 relative of
+    the exact sum and two tilings' norms within twice that."""
+    wl = W.smooth_sweep(n)
+    phi0 = wl.phi0()
+    kw = dict(wl.mixed())
+    out = {}
+    for z in (0, 1, 5, n, 4 * n):
+        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-10, precision="mixed",
+                      defect_planes=z, **kw)
+        cyc, res = [], []
+        for _ in range(3):
+            st = s.step(1)
+            cyc.append(st.cycles_last)
+            res.append(st.residual)
+        out[z] = (cyc, res, host(s.phi()), host(s.mu()), host(s.omega()))
+        s.close()
+    cyc0, res0, *f0 = out[0]
+    for z, (cyc, res, *f) in out.items():
+        assert cyc == cyc0, (z, cyc, cyc0)
+        np.testing.assert_allclose(res, res0, rtol=2 * (3 * n + 256) * 2.0 ** -24, atol=0)
+        for x, y in zip(f, f0):
+            assert np.array_equal(x, y), z
