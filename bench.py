@@ -210,7 +210,13 @@ def vcycle_bytes(params, levels):
             break
         first = l == 0
         total += cells * ((28.0 + 1.5) if first else (12.0 + 1.5))          # restriction
-        total += cells * ((24.0 + 1.5) if first else (12.0 + 1.5))          # prolongation
+        # prolongation: d read and written (first level: the measured V-cycle
+        # starts from d != 0) or written; before a red-black pass of colour 0
+        # only the colour-1 half of d is touched
+        dbytes = 24.0 if first else 12.0
+        if kind != B.PFC_SWEEP_JACOBI and params.nu2 > 0:
+            dbytes /= 2
+        total += cells * (dbytes + 1.5)
         if kind == B.PFC_SWEEP_JACOBI:
             sweeps = params.nu2 * (params.jacobi_factor0 if first else params.jacobi_factor)
             total += cells * (40.0 * sweeps + (24.0 if sweeps % 2 else 0.0))

@@ -572,10 +572,16 @@ int pfc_op_lin_residual_restrict(int n, double h, double eps, double tau,
                                  float* d_c1, float* d_c2, float* d_c3,
                                  void* stream);
 
-/* d += P e (assign != 0: d = P e, d not read), P the trilinear cell-centred
- * prolongation (weights 27, 9, 3, 1 over 64) from the colour-split
- * (n/2)^3 fields d_e1..3 to the colour-split n^3 fields d_d1..3; n divisible
- * by 4. */
+/* d += P e, P the trilinear cell-centred prolongation (weights 27, 9, 3, 1
+ * over 64) from the colour-split (n/2)^3 fields d_e1..3 to the colour-split
+ * n^3 fields d_d1..3; n divisible by 4.  `assign` holds flags:
+ * PFC_PROLONG_ASSIGN: d = P e (d not read); PFC_PROLONG_SKIP_COLOUR0: the
+ * colour-0 cells (the first half of each colour-split row) are neither read
+ * nor written, as inside the V-cycle when a red-black pass of colour 0
+ * follows (it recomputes those cells without reading them).  Other bits:
+ * PFC_EINVAL. */
+#define PFC_PROLONG_ASSIGN        1
+#define PFC_PROLONG_SKIP_COLOUR0  2
 int pfc_op_lin_prolong(int n, int assign, const float* d_e1, const float* d_e2,
                        const float* d_e3, float* d_d1, float* d_d2, float* d_d3,
                        void* stream);

@@ -20,6 +20,7 @@ PFC_GUESS_PREVIOUS, PFC_GUESS_EXTRAPOLATE = 0, 1
 PFC_NEWTON, PFC_PICARD = 0, 1
 PFC_POLICY_HYBRID, PFC_POLICY_RB = 0, 1
 PFC_SWEEP_RB, PFC_SWEEP_JACOBI = 0, 1
+PFC_PROLONG_ASSIGN, PFC_PROLONG_SKIP_COLOUR0 = 1, 2
 
 
 class PFCError(RuntimeError):
@@ -450,7 +451,8 @@ def pfc_op_lin_residual_restrict(n, h, eps, tau, zero_init, d1, d2, d3, r1, r2, 
 
 
 def pfc_op_lin_prolong(n, assign, e1, e2, e3, d1, d2, d3, stream=None):
-    check(lib().pfc_op_lin_prolong(n, int(bool(assign)), ptr(e1), ptr(e2), ptr(e3), ptr(d1),
+    """assign: a bool, or the flags PFC_PROLONG_ASSIGN | PFC_PROLONG_SKIP_COLOUR0."""
+    check(lib().pfc_op_lin_prolong(n, int(assign), ptr(e1), ptr(e2), ptr(e3), ptr(d1),
                                    ptr(d2), ptr(d3), stream), "pfc_op_lin_prolong")
 
 

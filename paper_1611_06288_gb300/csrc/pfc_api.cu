@@ -1371,7 +1371,10 @@ int pfc_op_lin_residual_restrict(int n, double h, double eps, double tau, int ze
 int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, const float* e3,
                        float* d1, float* d2, float* d3, void* stream) {
   if (n < 2 || (n & 3) || !e1 || !e2 || !e3 || !d1 || !d2 || !d3) return PFC_EINVAL;
-  PFC_CUDA(launch_prolong32(n, assign != 0, e1, e2, e3, d1, d2, d3, (cudaStream_t)stream));
+  if (assign < 0 || assign > (PFC_PROLONG_ASSIGN | PFC_PROLONG_SKIP_COLOUR0)) return PFC_EINVAL;
+  PFC_CUDA(launch_prolong32(n, (assign & PFC_PROLONG_ASSIGN) != 0,
+                            (assign & PFC_PROLONG_SKIP_COLOUR0) != 0, e1, e2, e3, d1, d2, d3,
+                            (cudaStream_t)stream));
   return PFC_OK;
 }
 

@@ -1325,83 +1325,135 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
 // one-dimensional passes: the child on the low side of an axis takes
 // (3 e_0 + e_-1)/4, on the high side (3 e_0 + e_+1)/4.  Split layout on both
 // levels.  A block of kPrTI x kPrTJ threads owns that tile of coarse cells
-// of one plane K and one component (the grid's z extent covers planes x
-// components x members): it stages the tile's 3x3x3 neighbourhood (one-cell
-// periodic halo, planes K-1..K+1) in shared memory in natural order with one
-// load per value, then each thread writes its coarse cell's eight children
-// from there.
-constexpr int kPrTI = 32, kPrTJ = 8;
+// over `zc` (<= kPrZ) consecutive planes K0.. of one component (the grid's z
+// extent covers plane chunks x components x members): it stages the tile's
+// neighbourhood (one-cell periodic halo, planes K0-1..K0+zc) in shared
+// memory in natural order with one load per value, then each thread writes
+// its coarse cells' eight children from there, plane after plane.  The
+// children's current values are loaded before the staging, so those loads,
+// the staging and the stores of the earlier planes overlap.
+//
+// SKIP0: the children of colour 0 (the first half of each fine row) are
+// neither read nor written.  A red-black pass of colour 0 that follows
+// recomputes every colour-0 cell from its colour-1 neighbours alone (the
+// pointwise 3x3 solve does not read the cell's own value), so the values the
+// prolongation would put there are never used: the pass sees the same inputs
+// either way, and half of the fine-level traffic of the prolongation goes.
+constexpr int kPrTI = 32, kPrTJ = 8, kPrZ = 4;
 
-template <bool ASSIGN>
+template <bool ASSIGN, bool SKIP0>
 __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
-    int n, const float* __restrict__ e1, const float* __restrict__ e2,
+    int n, int zc, const float* __restrict__ e1, const float* __restrict__ e2,
     const float* __restrict__ e3, float* __restrict__ d1, float* __restrict__ d2,
     float* __restrict__ d3) {
   pdl_wait();
   pdl_trigger();
-  __shared__ float sh[3][kPrTJ + 2][kPrTI + 2];
+  constexpr int kW = kPrTI + 2, kPlane = (kPrTJ + 2) * kW;
+  __shared__ float sh[kPrZ + 2][kPrTJ + 2][kW];
   const int nc = n >> 1, half = n >> 1, hc = nc >> 1;
-  int K = blockIdx.z;
-  const int mf = member_of(K, nc);           // member * 3 + component
+  const int chunks = (nc + zc - 1) / zc;
+  int kb = blockIdx.z;
+  const int mf = member_of(kb, chunks);      // member * 3 + component
   const int m = mf / 3, f = mf - 3 * m;
+  const int K0 = kb * zc, nz = min(zc, nc - K0);
   const float* __restrict__ e = (f == 0 ? e1 : f == 1 ? e2 : e3) + (size_t)m * nc * nc * nc;
   float* __restrict__ d = (f == 0 ? d1 : f == 1 ? d2 : d3) + (size_t)m * n * n * n;
   const int I0 = blockIdx.x * kPrTI, J0 = blockIdx.y * kPrTJ;
-  constexpr int kW = kPrTI + 2, kPlane = (kPrTJ + 2) * kW;
-  for (int t = threadIdx.x; t < 3 * kPlane; t += blockDim.x) {
+  const int tx = threadIdx.x % kPrTI, ty = threadIdx.x / kPrTI;
+  const int I = I0 + tx, J = J0 + ty;
+  const bool own = I < nc && J < nc;
+  // the children's current values first: old[z][(2 kk + jj) * 2 + a]
+  float old[kPrZ][8];
+#pragma unroll
+  for (int z = 0; z < kPrZ; ++z)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) old[z][c] = 0.f;
+  if (!ASSIGN && own) {
+#pragma unroll
+    for (int z = 0; z < kPrZ; ++z) {
+      if (z < nz) {
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj) {
+            const int j = 2 * J + jj, k = 2 * (K0 + z) + kk;
+            const int row = (k * n + j) * n + I, par = (j + k) & 1;
+            if (!SKIP0 || par == 1) old[z][(2 * kk + jj) * 2] = d[row + par * half];
+            if (!SKIP0 || par == 0) old[z][(2 * kk + jj) * 2 + 1] = d[row + (1 - par) * half];
+          }
+      }
+    }
+  }
+  for (int t = threadIdx.x; t < (nz + 2) * kPlane; t += blockDim.x) {
     const int z = t / kPlane, rem = t - z * kPlane, y = rem / kW, x = rem - y * kW;
     // periodic wraps without a division (the tile may exceed the grid when
     // nc < kPrTI: then more than one wrap)
-    int Ig = I0 + x - 1, Jg = J0 + y - 1, Kg = K + z - 1;
+    int Ig = I0 + x - 1, Jg = J0 + y - 1, Kg = K0 + z - 1;
     if (Ig < 0) Ig += nc;
     while (Ig >= nc) Ig -= nc;
     if (Jg < 0) Jg += nc;
     while (Jg >= nc) Jg -= nc;
     if (Kg < 0) Kg += nc;
-    if (Kg >= nc) Kg -= nc;
+    while (Kg >= nc) Kg -= nc;
     sh[z][y][x] = __ldg(e + (Kg * nc + Jg) * nc + ((Ig + Jg + Kg) & 1) * hc + (Ig >> 1));
   }
   __syncthreads();
-  const int tx = threadIdx.x % kPrTI, ty = threadIdx.x / kPrTI;
-  const int I = I0 + tx, J = J0 + ty;
-  if (I >= nc || J >= nc) return;
-  // the eight children's current values first (independent loads)
-  float old[8];
+  if (!own) return;
 #pragma unroll
-  for (int kk = 0; kk < 2; ++kk)
+  for (int z = 0; z < kPrZ; ++z) {
+    if (z >= nz) break;
+    float zx[3][3][2];                       // [y][x][child z]: 3 e_mid + e_lo / e_hi
 #pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      const int j = 2 * J + jj, k = 2 * K + kk;
-      const int row = (k * n + j) * n + I, par = (j + k) & 1;
-      old[(2 * kk + jj) * 2] = ASSIGN ? 0.f : d[row + par * half];
-      old[(2 * kk + jj) * 2 + 1] = ASSIGN ? 0.f : d[row + (1 - par) * half];
+    for (int y = 0; y < 3; ++y) {
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const float v0 = sh[z][ty + y][tx + x], v1 = sh[z + 1][ty + y][tx + x];
+        const float v2 = sh[z + 2][ty + y][tx + x];
+        zx[y][x][0] = fmaf(3.f, v1, v0);
+        zx[y][x][1] = fmaf(3.f, v1, v2);
+      }
     }
-  float zx[3][3][2];                         // [y][x][child z]: 3 e_mid + e_lo / e_hi
 #pragma unroll
-  for (int y = 0; y < 3; ++y) {
+    for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
-    for (int x = 0; x < 3; ++x) {
-      const float v0 = sh[0][ty + y][tx + x], v1 = sh[1][ty + y][tx + x];
-      const float v2 = sh[2][ty + y][tx + x];
-      zx[y][x][0] = fmaf(3.f, v1, v0);
-      zx[y][x][1] = fmaf(3.f, v1, v2);
-    }
-  }
+      for (int jj = 0; jj < 2; ++jj) {
+        float yx[3];
 #pragma unroll
-  for (int kk = 0; kk < 2; ++kk) {
-#pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      float yx[3];
-#pragma unroll
-      for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
-      const int j = 2 * J + jj, k = 2 * K + kk;
-      const int row = (k * n + j) * n + I, par = (j + k) & 1;   // child a has colour a ^ par
-      const float v0 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);  // a = 0 (i = 2I)
-      const float v1 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);  // a = 1 (i = 2I + 1)
-      d[row + par * half] = v0 + old[(2 * kk + jj) * 2];
-      d[row + (1 - par) * half] = v1 + old[(2 * kk + jj) * 2 + 1];
+        for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
+        const int j = 2 * J + jj, k = 2 * (K0 + z) + kk;
+        const int row = (k * n + j) * n + I, par = (j + k) & 1;   // child a has colour a ^ par
+        const float v0 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);  // a = 0 (i = 2I)
+        const float v1 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);  // a = 1 (i = 2I + 1)
+        if (!SKIP0 || par == 1) d[row + par * half] = v0 + old[z][(2 * kk + jj) * 2];
+        if (!SKIP0 || par == 0)
+          d[row + (1 - par) * half] = v1 + old[z][(2 * kk + jj) * 2 + 1];
+      }
     }
   }
+}
+
+using ProlongKernel = void (*)(int, int, const float*, const float*, const float*, float*,
+                               float*, float*);
+
+ProlongKernel prolong_kernel(bool assign, bool skip0) {
+  if (assign) return skip0 ? k_prolong_add32<true, true> : k_prolong_add32<true, false>;
+  return skip0 ? k_prolong_add32<false, true> : k_prolong_add32<false, false>;
+}
+
+// Coarse planes per block of k_prolong_add32: the most (<= kPrZ) that still
+// leave about two waves of blocks on the device (fewer planes per block for
+// the smaller levels, whose grids are short).
+int prolong_planes(int nc, int comps_members) {
+  const int64_t tiles = (int64_t)((nc + kPrTI - 1) / kPrTI) * ((nc + kPrTJ - 1) / kPrTJ) *
+                        comps_members;
+  for (int zc = kPrZ; zc > 1; zc >>= 1)
+    if (tiles * ((nc + zc - 1) / zc) >= 2 * 4 * 152) return zc;
+  return 1;
+}
+
+dim3 prolong_grid(int nc, int zc, int comps_members) {
+  return dim3((nc + kPrTI - 1) / kPrTI, (nc + kPrTJ - 1) / kPrTJ,
+              ((nc + zc - 1) / zc) * comps_members);
 }
 
 // Coarsest level of the linear problem when it is not part of a tail launch:
@@ -2687,12 +2739,14 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
   if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
-  const dim3 gp((nc + kPrTI - 1) / kPrTI, (nc + kPrTJ - 1) / kPrTJ, nc * c.nb * 3);
+  const int pz = prolong_planes(nc, 3 * c.nb);
+  // a red-black post-smoothing pass of colour 0 comes next: it recomputes
+  // the colour-0 cells without reading them
+  const bool skip0 = c.kind[l] != PFC_SWEEP_JACOBI && c.p->nu2 > 0;
   prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
-  e = launch_k(c.pr == nullptr, dzero ? k_prolong_add32<true> : k_prolong_add32<false>,
-               gp, dim3(kPrTI * kPrTJ), 0, c.st, L.n,
-               mx.d[l + 1][0], mx.d[l + 1][1], mx.d[l + 1][2], mx.d[l][0], mx.d[l][1],
-               mx.d[l][2]);
+  e = launch_k(c.pr == nullptr, prolong_kernel(dzero, skip0), prolong_grid(nc, pz, 3 * c.nb),
+               dim3(kPrTI * kPrTJ), 0, c.st, L.n, pz, mx.d[l + 1][0], mx.d[l + 1][1],
+               mx.d[l + 1][2], mx.d[l][0], mx.d[l][1], mx.d[l][2]);
   prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
   if (e != cudaSuccess) return e;
   return smooth32(c, l, c.p->nu2, false);
@@ -2924,12 +2978,11 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
                   g.grid, g.block, 0, st, to_f32(L), d1, d2, d3, r1, r2, r3, q, c1, c2, c3);
 }
 
-cudaError_t launch_prolong32(int n, bool assign, const float* e1, const float* e2,
+cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, const float* e2,
                              const float* e3, float* d1, float* d2, float* d3, cudaStream_t st) {
-  const int nc = n / 2;
-  const dim3 g((nc + kPrTI - 1) / kPrTI, (nc + kPrTJ - 1) / kPrTJ, nc * 3);
-  return launch_k(true, assign ? k_prolong_add32<true> : k_prolong_add32<false>, g,
-                  dim3(kPrTI * kPrTJ), 0, st, n, e1, e2, e3, d1, d2, d3);
+  const int nc = n / 2, pz = prolong_planes(nc, 3);
+  return launch_k(true, prolong_kernel(assign, skip0), prolong_grid(nc, pz, 3),
+                  dim3(kPrTI * kPrTJ), 0, st, n, pz, e1, e2, e3, d1, d2, d3);
 }
 
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,

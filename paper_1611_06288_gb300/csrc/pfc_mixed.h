@@ -161,7 +161,9 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
                                           const float* d2, const float* d3, const float* r1,
                                           const float* r2, const float* r3, const float* q,
                                           float* c1, float* c2, float* c3, cudaStream_t st);
-cudaError_t launch_prolong32(int n, bool assign, const float* e1, const float* e2,
+// skip0: the colour-0 cells of d are left untouched (a red-black pass of
+// colour 0 recomputes them next).
+cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, const float* e2,
                              const float* e3, float* d1, float* d2, float* d3, cudaStream_t st);
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
                                 float* d2, float* d3, const float* r1, const float* r2,

@@ -430,11 +430,14 @@ def test_linear_residual_restrict_fp32(n, zero):
         assert_close_field(from_split(host(g)), x, 2e-6, "rho")
 
 
-@pytest.mark.parametrize("n", [4, 12, 32])
+@pytest.mark.parametrize("n", [4, 12, 32, 72])
 @pytest.mark.parametrize("assign", [False, True])
-def test_linear_prolong_fp32(n, assign):
+@pytest.mark.parametrize("skip0", [False, True])
+def test_linear_prolong_fp32(n, assign, skip0):
     """d += P e (or d = P e) in FP32, three one-dimensional passes, against
-    the oracle's trilinear prolongation in FP64 (colour-split layouts)."""
+    the oracle's trilinear prolongation in FP64 (colour-split layouts).  With
+    PFC_PROLONG_SKIP_COLOUR0 the colour-1 cells are the same and the colour-0
+    cells keep their input bits (NaN where d = P e: they are not read)."""
     rng = np.random.default_rng(31 + n)
     nc = n // 2
     e = [rng.standard_normal((nc,) * 3).astype(np.float32) for _ in range(3)]
@@ -443,10 +446,54 @@ def test_linear_prolong_fp32(n, assign):
     if assign:
         for t in dd:
             t.fill_(float("nan"))            # must not be read
-    B.pfc_op_lin_prolong(n, assign, *[dev(to_split(x), torch.float32) for x in e], *dd)
-    for g, x, y in zip(dd, d0, e):
+    before = [host(t).copy() for t in dd]
+    flags = (B.PFC_PROLONG_ASSIGN if assign else 0) | (B.PFC_PROLONG_SKIP_COLOUR0 if skip0 else 0)
+    B.pfc_op_lin_prolong(n, flags, *[dev(to_split(x), torch.float32) for x in e], *dd)
+    i, j, k = np.meshgrid(*(np.arange(n),) * 3, indexing="ij")
+    colour1 = ((i + j + k) & 1) == 1                     # natural-order mask
+    for g, x, y, b0 in zip(dd, d0, e, before):
         ref = O.prolong(y.astype(np.float64)) + (0.0 if assign else x.astype(np.float64))
-        assert_close_field(from_split(host(g)), ref, 1e-6, "d+Pe")
+        got = from_split(host(g))
+        if not skip0:
+            assert_close_field(got, ref, 1e-6, "d+Pe")
+            continue
+        assert_close_field(np.where(colour1, got, 0.0), np.where(colour1, ref, 0.0), 1e-6,
+                           "colour 1 of d+Pe")
+        # colour 0 untouched: the first half of every colour-split row
+        half = n // 2
+        gs = host(g).reshape(n * n, n)
+        assert np.array_equal(gs[:, :half], b0.reshape(n * n, n)[:, :half], equal_nan=True)
+
+
+@pytest.mark.parametrize("skip0", [False, True])
+def test_linear_prolong_fp32_multiplane(skip0):
+    """At 204^3 the kernel's blocks take four coarse planes each (102 coarse
+    planes: 25 full chunks and a ragged one of two) and the grid has four
+    x tiles, the last one ragged: d += P e against the oracle."""
+    n, nc = 204, 102
+    rng = np.random.default_rng(5)
+    e = [rng.standard_normal((nc,) * 3).astype(np.float32) for _ in range(3)]
+    d0 = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    dd = [dev(to_split(x), torch.float32) for x in d0]
+    B.pfc_op_lin_prolong(n, B.PFC_PROLONG_SKIP_COLOUR0 if skip0 else 0,
+                         *[dev(to_split(x), torch.float32) for x in e], *dd)
+    i, j, k = np.indices((n,) * 3)
+    colour1 = ((i + j + k) & 1) == 1
+    for g, x, y in zip(dd, d0, e):
+        ref = O.prolong(y.astype(np.float64)) + x.astype(np.float64)
+        got = from_split(host(g))
+        if skip0:
+            assert_close_field(np.where(colour1, got, 0.0), np.where(colour1, ref, 0.0), 1e-6,
+                               "colour 1 of d+Pe")
+            assert np.array_equal(np.where(colour1, 0.0, got), np.where(colour1, 0.0, x))
+        else:
+            assert_close_field(got, ref, 1e-6, "d+Pe")
+
+
+def test_linear_prolong_rejects_unknown_flags():
+    z = torch.zeros(8 ** 3, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.PFCError):
+        B.pfc_op_lin_prolong(8, 4, z[:64], z[:64], z[:64], z, z, z)
 
 
 @pytest.mark.parametrize("n", [4, 12, 32])
