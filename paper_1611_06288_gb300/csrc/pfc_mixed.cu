@@ -1269,8 +1269,12 @@ __device__ __forceinline__ void block_sums(const float* __restrict__ v, const in
 // the averaged Laplacians taken from the block sums above and q d_phi summed
 // cell by cell.  One thread per coarse cell and row: the grid's z extent
 // covers planes x 3 rows x members, so a thread loads the children of at most
-// four fields and the block of one.  ZERO: d = 0 on entry (no pre-smoothing
-// from a zero start), so rho = r and d is not read.
+// four fields and the block of one.  The row is the fastest index of z
+// (z = (member * nc + K) * 3 + row), so the three rows of a plane, which
+// read the same fields (d_phi by all three), run close together and share
+// their reads in L2; with the row slowest each field went through DRAM up to
+// three times at 256^3.  ZERO: d = 0 on entry (no pre-smoothing from a zero
+// start), so rho = r and d is not read.
 template <bool ZERO>
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
@@ -1285,9 +1289,9 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   pdl_trigger();
   const int n = L.n, nc = n >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-  int K = blockIdx.z;
-  const int mf = member_of(K, nc);           // member * 3 + row
-  const int m = mf / 3, f = mf - 3 * m;
+  const int f = blockIdx.z % 3;              // row
+  int K = blockIdx.z / 3;
+  const int m = member_of(K, nc);
   if (I >= nc || J >= nc) return;
   const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
   // row f: own residual r_f and correction d_f, the field under the Laplacian
@@ -1348,7 +1352,7 @@ __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
     float* __restrict__ d3) {
   pdl_wait();
   pdl_trigger();
-  constexpr int kW = kPrTI + 2, kPlane = (kPrTJ + 2) * kW;
+  constexpr int kW = kPrTI + 2;
   __shared__ float sh[kPrZ + 2][kPrTJ + 2][kW];
   const int nc = n >> 1, half = n >> 1, hc = nc >> 1;
   const int chunks = (nc + zc - 1) / zc;
@@ -1377,28 +1381,58 @@ __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
 #pragma unroll
           for (int jj = 0; jj < 2; ++jj) {
             const int j = 2 * J + jj, k = 2 * (K0 + z) + kk;
-            const int row = (k * n + j) * n + I, par = (j + k) & 1;
+            const int row = (k * n + j) * n + I, par = (jj + kk) & 1;   // (j + k) & 1
             if (!SKIP0 || par == 1) old[z][(2 * kk + jj) * 2] = d[row + par * half];
             if (!SKIP0 || par == 0) old[z][(2 * kk + jj) * 2 + 1] = d[row + (1 - par) * half];
           }
       }
     }
   }
-  for (int t = threadIdx.x; t < (nz + 2) * kPlane; t += blockDim.x) {
-    const int z = t / kPlane, rem = t - z * kPlane, y = rem / kW, x = rem - y * kW;
-    // periodic wraps without a division (the tile may exceed the grid when
-    // nc < kPrTI: then more than one wrap)
-    int Ig = I0 + x - 1, Jg = J0 + y - 1, Kg = K0 + z - 1;
-    if (Ig < 0) Ig += nc;
-    while (Ig >= nc) Ig -= nc;
-    if (Jg < 0) Jg += nc;
-    while (Jg >= nc) Jg -= nc;
-    if (Kg < 0) Kg += nc;
-    while (Kg >= nc) Kg -= nc;
-    sh[z][y][x] = __ldg(e + (Kg * nc + Jg) * nc + ((Ig + Jg + Kg) & 1) * hc + (Ig >> 1));
+  // staging: every thread's loads are issued before any of them is stored
+  // (a fixed, unrolled count), so a block waits for one L2 round trip here
+  // instead of one per load
+  {
+    constexpr int kPlane = (kPrTJ + 2) * kW;
+    constexpr int kPer = ((kPrZ + 2) * kPlane + kPrTI * kPrTJ - 1) / (kPrTI * kPrTJ);
+    const int total = (nz + 2) * kPlane;
+    float v[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int t = threadIdx.x + i * (kPrTI * kPrTJ);
+      v[i] = 0.f;
+      if (t < total) {
+        const int z = t / kPlane, rem = t - z * kPlane, y = rem / kW, x = rem - y * kW;
+        // periodic wraps without a division (the tile may exceed the grid
+        // when nc < kPrTI: then more than one wrap)
+        int Ig = I0 + x - 1, Jg = J0 + y - 1, Kg = K0 + z - 1;
+        if (Ig < 0) Ig += nc;
+        while (Ig >= nc) Ig -= nc;
+        if (Jg < 0) Jg += nc;
+        while (Jg >= nc) Jg -= nc;
+        if (Kg < 0) Kg += nc;
+        while (Kg >= nc) Kg -= nc;
+        v[i] = __ldg(e + (Kg * nc + Jg) * nc + ((Ig + Jg + Kg) & 1) * hc + (Ig >> 1));
+      }
+    }
+    float* const flat = &sh[0][0][0];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+      const int t = threadIdx.x + i * (kPrTI * kPrTJ);
+      if (t < total) flat[t] = v[i];
+    }
   }
   __syncthreads();
   if (!own) return;
+  // the 3x3 columns of planes z+1 and z+2 carry over to the next plane
+  float pa[3][3], pb[3][3];
+#pragma unroll
+  for (int y = 0; y < 3; ++y)
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      pa[y][x] = sh[0][ty + y][tx + x];
+      pb[y][x] = sh[1][ty + y][tx + x];
+    }
+  const int base = ((2 * K0) * n + 2 * J) * n + I;
 #pragma unroll
   for (int z = 0; z < kPrZ; ++z) {
     if (z >= nz) break;
@@ -1407,10 +1441,11 @@ __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
     for (int y = 0; y < 3; ++y) {
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
-        const float v0 = sh[z][ty + y][tx + x], v1 = sh[z + 1][ty + y][tx + x];
         const float v2 = sh[z + 2][ty + y][tx + x];
-        zx[y][x][0] = fmaf(3.f, v1, v0);
-        zx[y][x][1] = fmaf(3.f, v1, v2);
+        zx[y][x][0] = fmaf(3.f, pb[y][x], pa[y][x]);
+        zx[y][x][1] = fmaf(3.f, pb[y][x], v2);
+        pa[y][x] = pb[y][x];
+        pb[y][x] = v2;
       }
     }
 #pragma unroll
@@ -1420,8 +1455,8 @@ __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
         float yx[3];
 #pragma unroll
         for (int x = 0; x < 3; ++x) yx[x] = fmaf(3.f, zx[1][x][kk], zx[2 * jj][x][kk]);
-        const int j = 2 * J + jj, k = 2 * (K0 + z) + kk;
-        const int row = (k * n + j) * n + I, par = (j + k) & 1;   // child a has colour a ^ par
+        // fine row (2J + jj, 2(K0 + z) + kk); child a has colour a ^ par
+        const int row = base + ((2 * z + kk) * n + jj) * n, par = (jj + kk) & 1;
         const float v0 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[0]);  // a = 0 (i = 2I)
         const float v1 = (1.f / 64.f) * fmaf(3.f, yx[1], yx[2]);  // a = 1 (i = 2I + 1)
         if (!SKIP0 || par == 1) d[row + par * half] = v0 + old[z][(2 * kk + jj) * 2];
