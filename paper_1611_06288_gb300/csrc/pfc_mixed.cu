@@ -1247,34 +1247,22 @@ __device__ __forceinline__ void block_indices(int I, int J, int K, int n, int (&
   }
 }
 
-// Sums of a field over the eight children (s_in) and over the 24 outside
-// face neighbours (s_out).  Summed over the children, the 7-point Laplacian's
-// interior faces cancel: sum_children Lap v = s_out - 3 s_in (unscaled).
-__device__ __forceinline__ void block_sums(const float* __restrict__ v, const int (&in)[8],
-                                           const int (&out)[24], float& s_in, float& s_out) {
-  float a = 0.f, b = 0.f;
-#pragma unroll
-  for (int c = 0; c < 8; ++c) a += __ldg(v + in[c]);
-#pragma unroll
-  for (int c = 0; c < 24; ++c) b += __ldg(v + out[c]);
-  s_in = a;
-  s_out = b;
-}
-
 // Restricted residual of the linear system: the average over the eight
 // children of r - J d, with
 //   (J d)1 = d_phi - tau/h^2 Lap d_mu
 //   (J d)2 = d_mu - q d_phi - 1/h^2 Lap d_om
 //   (J d)3 = d_om - 1/(2h^2) Lap d_phi,
-// the averaged Laplacians taken from the block sums above and q d_phi summed
-// cell by cell.  One thread per coarse cell and row: the grid's z extent
-// covers planes x 3 rows x members, so a thread loads the children of at most
-// four fields and the block of one.  The row is the fastest index of z
-// (z = (member * nc + K) * 3 + row), so the three rows of a plane, which
-// read the same fields (d_phi by all three), run close together and share
-// their reads in L2; with the row slowest each field went through DRAM up to
-// three times at 256^3.  ZERO: d = 0 on entry (no pre-smoothing from a zero
-// start), so rho = r and d is not read.
+// the averaged Laplacians taken from block sums (summed over the children,
+// the 7-point Laplacian's interior faces cancel: sum_children Lap v = s_out -
+// 3 s_in, unscaled, with s_in the sum over the eight children and s_out over
+// the 24 outside face neighbours) and q d_phi summed cell by cell.  One thread per coarse cell forms all three rows: each of
+// d_phi, d_mu, d_om enters one row through its children and another through
+// its block sum, so its eight children are loaded once for both (and those
+// of d_phi a third time for q d_phi), 128 loads per coarse cell where one
+// thread per row needed 160, and every field of a plane is read by the same
+// threads.  The sums are formed in the same order as one thread per row did.
+// ZERO: d = 0 on entry (no pre-smoothing from a zero start), so rho = r and d
+// and q are not read.
 template <bool ZERO>
 __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
                                           const float* __restrict__ d2,
@@ -1289,39 +1277,50 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   pdl_trigger();
   const int n = L.n, nc = n >> 1;
   const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y * blockDim.y + threadIdx.y;
-  const int f = blockIdx.z % 3;              // row
-  int K = blockIdx.z / 3;
+  int K = blockIdx.z;
   const int m = member_of(K, nc);
   if (I >= nc || J >= nc) return;
   const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
-  // row f: own residual r_f and correction d_f, the field under the Laplacian
-  // (d_mu, d_om, d_phi) and its coefficient
-  const float* __restrict__ r = (f == 0 ? r1 : f == 1 ? r2 : r3) + off;
-  const float* __restrict__ dv = (f == 0 ? d1 : f == 1 ? d2 : d3) + off;
-  const float* __restrict__ dl = (f == 0 ? d2 : f == 1 ? d3 : d1) + off;
-  const float g = f == 0 ? L.tg : f == 1 ? L.g : L.gh;
-  float* __restrict__ cf = (f == 0 ? c1 : f == 1 ? c2 : c3) + offc;
   int in[8], out[24];
   block_indices(I, J, K, n, in, out);
-  float a = 0.f;
+  const float* const rr[3] = {r1 + off, r2 + off, r3 + off};
+  float a[3];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) a += __ldg(r + in[c]);
-  if (!ZERO) {
-    float sv = 0.f, lin, lout;
+  for (int f = 0; f < 3; ++f) {
+    float s = 0.f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) sv += __ldg(dv + in[c]);
-    block_sums(dl, in, out, lin, lout);
-    a = fmaf(g, fmaf(-3.f, lin, lout), a - sv);
-    if (f == 1) {
-      const float* __restrict__ qm = q + off;
-      const float* __restrict__ p1 = d1 + off;
-      float qp = 0.f;
-#pragma unroll
-      for (int c = 0; c < 8; ++c) qp = fmaf(__ldg(qm + in[c]), __ldg(p1 + in[c]), qp);
-      a += qp;
-    }
+    for (int c = 0; c < 8; ++c) s += __ldg(rr[f] + in[c]);
+    a[f] = s;
   }
-  cf[split_index(I, J, K, nc)] = 0.125f * a;
+  if (!ZERO) {
+    const float* const dd[3] = {d1 + off, d2 + off, d3 + off};
+    float sin[3], sout[3], p1[8];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      float si = 0.f, so = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float v = __ldg(dd[f] + in[c]);
+        if (f == 0) p1[c] = v;
+        si += v;
+      }
+#pragma unroll
+      for (int c = 0; c < 24; ++c) so += __ldg(dd[f] + out[c]);
+      sin[f] = si;
+      sout[f] = so;
+    }
+    float qp = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) qp = fmaf(__ldg(q + off + in[c]), p1[c], qp);
+    // row f: own d_f, the field under the Laplacian (d_mu, d_om, d_phi)
+    a[0] = fmaf(L.tg, fmaf(-3.f, sin[1], sout[1]), a[0] - sin[0]);
+    a[1] = fmaf(L.g, fmaf(-3.f, sin[2], sout[2]), a[1] - sin[1]) + qp;
+    a[2] = fmaf(L.gh, fmaf(-3.f, sin[0], sout[0]), a[2] - sin[2]);
+  }
+  const int ci = split_index(I, J, K, nc);
+  (c1 + offc)[ci] = 0.125f * a[0];
+  (c2 + offc)[ci] = 0.125f * a[1];
+  (c3 + offc)[ci] = 0.125f * a[2];
 }
 
 // d += P e (ASSIGN: d = P e; d was zero and is not read), trilinear
@@ -2764,7 +2763,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   if (c.p->nu1 > 0) e = smooth32(c, l, c.p->nu1, zero_init);
   if (e != cudaSuccess) return e;
   const int nc = L.n / 2;
-  const Launch3 gr = launch3(nc, nc, nc * c.nb * 3);
+  const Launch3 gr = launch3(nc, nc, nc * c.nb);
   prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
   e = launch_k(c.pr == nullptr,
                dzero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
@@ -3007,7 +3006,7 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
                                           const float* r2, const float* r3, const float* q,
                                           float* c1, float* c2, float* c3, cudaStream_t st) {
   const int nc = L.n / 2;
-  const Launch3 g = launch3(nc, nc, nc * 3);
+  const Launch3 g = launch3(nc, nc, nc);
   return launch_k(true,
                   zero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
                   g.grid, g.block, 0, st, to_f32(L), d1, d2, d3, r1, r2, r3, q, c1, c2, c3);
