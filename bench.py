@@ -65,7 +65,8 @@ KERNEL_BYTES = {
 # capture of the current kernel exists.
 # The defect class of the mixed path averages a step's launches: two full
 # defects (150.2 MB each) and one pointwise first defect (158.7 MB).
-NCU_TRAFFIC = {("mixed", "defect"): 153.0e6}   # profiles/k_defect64_fx_128.md, k_defect64_point_128.md
+# Keyed by the finest level's size the capture ran at (other sizes: null).
+NCU_TRAFFIC = {("mixed", "defect", 128): 153.0e6}   # profiles/k_defect64_fx_128.md, k_defect64_point_128.md
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
 # counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
@@ -429,7 +430,7 @@ def run_ours(args):
         achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
         bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
         peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
-    traffic = NCU_TRAFFIC.get((args.precision, dom_cls))
+    traffic = NCU_TRAFFIC.get((args.precision, dom_cls, m))
     roofline = {"bound": bound, "achieved": achieved, "peak": peak,
                 "unit": unit, "frac": achieved / peak,
                 "traffic": traffic / 1e9 if traffic is not None else None,
