@@ -572,6 +572,21 @@ int pfc_op_lin_residual_restrict(int n, double h, double eps, double tau,
                                  float* d_c1, float* d_c2, float* d_c3,
                                  void* stream);
 
+/* The restriction of pfc_op_lin_residual_restrict to d_c1..3 ((n/2)^3)
+ * followed, in the same launch, by `levels` - 1 (1 or 2) plain 8-cell
+ * averages: d_e1..3 ((n/4)^3) = I c, and with levels = 3 d_g1..3 ((n/8)^3)
+ * = I e, all colour-split.  This is the V-cycle's descent without
+ * pre-smoothing, where every coarser level starts from d = 0; the results
+ * equal those of the separate restrictions bit for bit.  n a multiple of
+ * 32; d_g1..3 may be NULL when levels = 2; zero_init as for
+ * pfc_op_lin_residual_restrict. */
+int pfc_op_lin_restrict_chain(int n, double h, double eps, double tau, int zero_init,
+                              int levels, const float* d_d1, const float* d_d2,
+                              const float* d_d3, const float* d_r1, const float* d_r2,
+                              const float* d_r3, const float* d_q, float* d_c1, float* d_c2,
+                              float* d_c3, float* d_e1, float* d_e2, float* d_e3,
+                              float* d_g1, float* d_g2, float* d_g3, void* stream);
+
 /* d += P e, P the trilinear cell-centred prolongation (weights 27, 9, 3, 1
  * over 64) from the colour-split (n/2)^3 fields d_e1..3 to the colour-split
  * n^3 fields d_d1..3; n divisible by 4.  `assign` holds flags:

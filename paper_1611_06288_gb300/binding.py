@@ -110,6 +110,7 @@ _SIGS = {
     "pfc_batch_diagnostics": (_I, [_P, ctypes.POINTER(_D)]),
     "pfc_batch_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
+    "pfc_op_lin_restrict_chain": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 16 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
     "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_guess_df": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
@@ -448,6 +449,14 @@ def pfc_op_lin_residual_restrict(n, h, eps, tau, zero_init, d1, d2, d3, r1, r2, 
                                              ptr(d2), ptr(d3), ptr(r1), ptr(r2), ptr(r3),
                                              ptr(q), ptr(c1), ptr(c2), ptr(c3), stream),
           "pfc_op_lin_residual_restrict")
+
+
+def pfc_op_lin_restrict_chain(n, h, eps, tau, zero_init, levels, d1, d2, d3, r1, r2, r3, q,
+                              c1, c2, c3, e1, e2, e3, g1=None, g2=None, g3=None, stream=None):
+    check(lib().pfc_op_lin_restrict_chain(n, h, eps, tau, int(bool(zero_init)), levels,
+                                          *[ptr(x) for x in (d1, d2, d3, r1, r2, r3, q, c1, c2,
+                                                             c3, e1, e2, e3, g1, g2, g3)],
+                                          stream), "pfc_op_lin_restrict_chain")
 
 
 def pfc_op_lin_prolong(n, assign, e1, e2, e3, d1, d2, d3, stream=None):

@@ -1368,6 +1368,24 @@ int pfc_op_lin_residual_restrict(int n, double h, double eps, double tau, int ze
   return PFC_OK;
 }
 
+int pfc_op_lin_restrict_chain(int n, double h, double eps, double tau, int zero_init,
+                              int levels, const float* d1, const float* d2, const float* d3,
+                              const float* r1, const float* r2, const float* r3,
+                              const float* q, float* c1, float* c2, float* c3, float* e1,
+                              float* e2, float* e3, float* g1, float* g2, float* g3,
+                              void* stream) {
+  if (n < 32 || (n % 32) != 0 || !(h > 0) || levels < 2 || levels > 3 || !r1 || !r2 || !r3 ||
+      !c1 || !c2 || !c3 || !e1 || !e2 || !e3 ||
+      (levels == 3 && (!g1 || !g2 || !g3)) || (!zero_init && (!d1 || !d2 || !d3 || !q)))
+    return PFC_EINVAL;
+  float* const c[3] = {c1, c2, c3};
+  float* const e[3] = {e1, e2, e3};
+  float* const g[3] = {g1, g2, g3};
+  PFC_CUDA(launch_lin_restrict_chain32(make_lvl(n, h, eps, tau), zero_init != 0, levels - 1, d1,
+                                       d2, d3, r1, r2, r3, q, c, e, g, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
 int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, const float* e3,
                        float* d1, float* d2, float* d3, void* stream) {
   if (n < 2 || (n & 3) || !e1 || !e2 || !e3 || !d1 || !d2 || !d3) return PFC_EINVAL;

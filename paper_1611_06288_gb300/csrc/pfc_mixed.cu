@@ -1323,6 +1323,133 @@ __global__ void k_lin_residual_restrict32(LvlF L, const float* __restrict__ d1,
   (c3 + offc)[ci] = 0.125f * a[2];
 }
 
+// The restriction of k_lin_residual_restrict32 followed by EXTRA more
+// levels of plain 8-cell averages, in one launch.  Without pre-smoothing
+// (nu1 = 0) every coarser level starts its V-cycle from d = 0, so its own
+// restriction is the average of its r alone; a block of kChTX x kChTY x kChTZ
+// coarse cells keeps its results in shared memory and averages them down to
+// (kChTX/2 x kChTY/2 x kChTZ/2) and (kChTX/4 x kChTY/4 x kChTZ/4) cells, in
+// the children order of the separate kernel (bit-identical results), and
+// each coarser level's separate launch goes.  Coarse size nc a multiple of
+// kChTX and kChTZ.
+constexpr int kChTX = 16, kChTY = 4, kChTZ = 4;
+
+template <bool ZERO, int EXTRA>
+__global__ void __launch_bounds__(kChTX * kChTY * kChTZ) k_lin_restrict_chain32(
+    LvlF L, const float* __restrict__ d1, const float* __restrict__ d2,
+    const float* __restrict__ d3, const float* __restrict__ r1, const float* __restrict__ r2,
+    const float* __restrict__ r3, const float* __restrict__ q, float* __restrict__ c1,
+    float* __restrict__ c2, float* __restrict__ c3, float* __restrict__ e1,
+    float* __restrict__ e2, float* __restrict__ e3, float* __restrict__ g1,
+    float* __restrict__ g2, float* __restrict__ g3) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float s1[3][kChTZ][kChTY][kChTX];
+  __shared__ float s2[3][kChTZ / 2][kChTY / 2][kChTX / 2];
+  const int n = L.n, nc = n >> 1;
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int I = blockIdx.x * kChTX + tx, J = blockIdx.y * kChTY + ty;
+  int K = blockIdx.z * kChTZ + tz;
+  const int m = member_of(K, nc);
+  const size_t off = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
+  int in[8], out[24];
+  block_indices(I, J, K, n, in, out);
+  const float* const rr[3] = {r1 + off, r2 + off, r3 + off};
+  float a[3];
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += __ldg(rr[f] + in[c]);
+    a[f] = s;
+  }
+  if (!ZERO) {
+    const float* const dd[3] = {d1 + off, d2 + off, d3 + off};
+    float sin[3], sout[3], p1[8];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      float si = 0.f, so = 0.f;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const float v = __ldg(dd[f] + in[c]);
+        if (f == 0) p1[c] = v;
+        si += v;
+      }
+#pragma unroll
+      for (int c = 0; c < 24; ++c) so += __ldg(dd[f] + out[c]);
+      sin[f] = si;
+      sout[f] = so;
+    }
+    float qp = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) qp = fmaf(__ldg(q + off + in[c]), p1[c], qp);
+    a[0] = fmaf(L.tg, fmaf(-3.f, sin[1], sout[1]), a[0] - sin[0]);
+    a[1] = fmaf(L.g, fmaf(-3.f, sin[2], sout[2]), a[1] - sin[1]) + qp;
+    a[2] = fmaf(L.gh, fmaf(-3.f, sin[0], sout[0]), a[2] - sin[2]);
+  }
+  float* const cc[3] = {c1 + offc, c2 + offc, c3 + offc};
+  const int ci = split_index(I, J, K, nc);
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    const float v = 0.125f * a[f];
+    cc[f][ci] = v;
+    if (EXTRA > 0) s1[f][tz][ty][tx] = v;
+  }
+  if (EXTRA == 0) return;
+  // averages of the block's cells: children in the order of block_indices
+  // (for each child row, the cell of colour half 0 first)
+  const int tid = (tz * kChTY + ty) * kChTX + tx;
+  const int n2 = nc >> 1;
+  const size_t off2 = (size_t)m * n2 * n2 * n2;
+  __syncthreads();
+  if (tid < (kChTX / 2) * (kChTY / 2) * (kChTZ / 2)) {
+    const int x = tid % (kChTX / 2), y = (tid / (kChTX / 2)) % (kChTY / 2),
+              z = tid / ((kChTX / 2) * (kChTY / 2));
+    float* const ee[3] = {e1 + off2, e2 + off2, e3 + off2};
+    const int I2 = blockIdx.x * (kChTX / 2) + x, J2 = blockIdx.y * (kChTY / 2) + y;
+    const int K2g = (K - tz) / 2 + z;            // plane within this member's level
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      float sum = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int par = (jj + kk) & 1;
+          sum += s1[f][2 * z + kk][2 * y + jj][2 * x + par];
+          sum += s1[f][2 * z + kk][2 * y + jj][2 * x + 1 - par];
+        }
+      const float v = 0.125f * sum;
+      ee[f][split_index(I2, J2, K2g, n2)] = v;
+      if (EXTRA > 1) s2[f][z][y][x] = v;
+    }
+  }
+  if (EXTRA < 2) return;
+  __syncthreads();
+  const int n3 = n2 >> 1;
+  const size_t off3 = (size_t)m * n3 * n3 * n3;
+  if (tid < (kChTX / 4) * (kChTY / 4) * (kChTZ / 4)) {
+    const int x = tid % (kChTX / 4), y = (tid / (kChTX / 4)) % (kChTY / 4),
+              z = tid / ((kChTX / 4) * (kChTY / 4));
+    float* const gg[3] = {g1 + off3, g2 + off3, g3 + off3};
+    const int I3 = blockIdx.x * (kChTX / 4) + x, J3 = blockIdx.y * (kChTY / 4) + y;
+    const int K3g = (K - tz) / 4 + z;
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      float sum = 0.f;
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int par = (jj + kk) & 1;
+          sum += s2[f][2 * z + kk][2 * y + jj][2 * x + par];
+          sum += s2[f][2 * z + kk][2 * y + jj][2 * x + 1 - par];
+        }
+      gg[f][split_index(I3, J3, K3g, n3)] = 0.125f * sum;
+    }
+  }
+}
+
 // d += P e (ASSIGN: d = P e; d was zero and is not read), trilinear
 // cell-centred prolongation with the weights 27, 9, 3, 1 over 64 as three
 // one-dimensional passes: the child on the low side of an axis takes
@@ -2731,7 +2858,37 @@ cudaError_t ctail32(const Ctx32& c, int l0, bool zero_init, int nd, size_t smem,
   return e;
 }
 
-cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
+// Whether vcycle32 at level l restricts to l + 1 with a launch of its own
+// (not the cluster tail, the shared-memory tail or the coarsest solve).
+bool restricts_alone(const Ctx32& c, int l) {
+  if (c.p->cluster_tail || l >= c.nl - 1) return false;
+  if (c.L[l].n <= kTailMaxN && c.nl - l <= kTailMaxLevels) {
+    int sizes[kMaxLevelsMixed];
+    for (int q = 0; q < c.nl; ++q) sizes[q] = c.L[q].n;
+    if (tail_smem_bytes(sizes, l, c.nl) <= kTailMaxSmem) return false;
+  }
+  return true;
+}
+
+// Levels below l + 1 whose restriction one k_lin_restrict_chain32 launch at
+// level l can take over (0..2): they start from d = 0 (no pre-smoothing) and
+// would each restrict in a launch of their own.  Only for coarse levels of
+// at most kChainMaxNc^3 cells: there a launch costs more than the traffic,
+// while the chain's 16 x 4 x 4 blocks read a large level's rows in 64-byte
+// pieces (256^3 -> 128^3 took 107 us against 94 us for the row-wide blocks).
+constexpr int kChainMaxNc = 64;
+
+int chain_extra(const Ctx32& c, int l) {
+  const int nc = c.L[l].n / 2;
+  if (c.p->nu1 > 0 || nc > kChainMaxNc || nc % kChTX != 0 || nc % kChTZ != 0) return 0;
+  int extra = 0;
+  while (extra < 2 && l + 2 + extra < c.nl && restricts_alone(c, l + 1 + extra)) ++extra;
+  return extra;
+}
+
+// have: the restrictions of this many levels below l were done by a chain
+// launch above (r of levels l+1 .. l+have is in place; d = 0 there).
+cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init, int have = 0) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
   if (c.p->cluster_tail) {
@@ -2763,16 +2920,37 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init) {
   if (c.p->nu1 > 0) e = smooth32(c, l, c.p->nu1, zero_init);
   if (e != cudaSuccess) return e;
   const int nc = L.n / 2;
-  const Launch3 gr = launch3(nc, nc, nc * c.nb);
-  prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
-  e = launch_k(c.pr == nullptr,
-               dzero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
-               gr.grid, gr.block, 0, c.st, L,
-               mx.d[l][0], mx.d[l][1], mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l],
-               mx.r[l + 1][0], mx.r[l + 1][1], mx.r[l + 1][2]);
-  prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
+  int below = 0;
+  if (have > 0) {
+    below = have - 1;
+  } else {
+    const int extra = chain_extra(c, l);
+    prof_begin(c.pr, PFC_K_LIN_RESTRICT, c.st);
+    if (extra > 0) {
+      float* const* r2 = mx.r[l + 2];
+      float* const* r3 = extra > 1 ? mx.r[l + 3] : mx.r[l + 2];
+      const dim3 grid(nc / kChTX, nc / kChTY, (nc / kChTZ) * c.nb);
+      const dim3 block(kChTX, kChTY, kChTZ);
+      auto kern = dzero ? (extra > 1 ? k_lin_restrict_chain32<true, 2>
+                                     : k_lin_restrict_chain32<true, 1>)
+                        : (extra > 1 ? k_lin_restrict_chain32<false, 2>
+                                     : k_lin_restrict_chain32<false, 1>);
+      e = launch_k(c.pr == nullptr, kern, grid, block, 0, c.st, L, mx.d[l][0], mx.d[l][1],
+                   mx.d[l][2], mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l], mx.r[l + 1][0],
+                   mx.r[l + 1][1], mx.r[l + 1][2], r2[0], r2[1], r2[2], r3[0], r3[1], r3[2]);
+      below = extra;
+    } else {
+      const Launch3 gr = launch3(nc, nc, nc * c.nb);
+      e = launch_k(c.pr == nullptr,
+                   dzero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
+                   gr.grid, gr.block, 0, c.st, L, mx.d[l][0], mx.d[l][1], mx.d[l][2],
+                   mx.r[l][0], mx.r[l][1], mx.r[l][2], mx.q[l], mx.r[l + 1][0], mx.r[l + 1][1],
+                   mx.r[l + 1][2]);
+    }
+    prof_end(c.pr, PFC_K_LIN_RESTRICT, l, 1, c.st);
+  }
   if (e != cudaSuccess) return e;
-  if ((e = vcycle32(c, l + 1, true)) != cudaSuccess) return e;
+  if ((e = vcycle32(c, l + 1, true, below)) != cudaSuccess) return e;
   const int pz = prolong_planes(nc, 3 * c.nb);
   // a red-black post-smoothing pass of colour 0 comes next: it recomputes
   // the colour-0 cells without reading them
@@ -3010,6 +3188,21 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
   return launch_k(true,
                   zero ? k_lin_residual_restrict32<true> : k_lin_residual_restrict32<false>,
                   g.grid, g.block, 0, st, to_f32(L), d1, d2, d3, r1, r2, r3, q, c1, c2, c3);
+}
+
+cudaError_t launch_lin_restrict_chain32(const Lvl& L, bool zero, int extra, const float* d1,
+                                       const float* d2, const float* d3, const float* r1,
+                                       const float* r2, const float* r3, const float* q,
+                                       float* const c[3], float* const e[3], float* const g[3],
+                                       cudaStream_t st) {
+  const int nc = L.n / 2;
+  const dim3 grid(nc / kChTX, nc / kChTY, nc / kChTZ), block(kChTX, kChTY, kChTZ);
+  float* const* g2 = extra > 1 ? g : e;
+  auto kern = zero ? (extra > 1 ? k_lin_restrict_chain32<true, 2> : k_lin_restrict_chain32<true, 1>)
+                   : (extra > 1 ? k_lin_restrict_chain32<false, 2>
+                                : k_lin_restrict_chain32<false, 1>);
+  return launch_k(true, kern, grid, block, 0, st, to_f32(L), d1, d2, d3, r1, r2, r3, q, c[0],
+                  c[1], c[2], e[0], e[1], e[2], g2[0], g2[1], g2[2]);
 }
 
 cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, const float* e2,

@@ -161,6 +161,14 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
                                           const float* d2, const float* d3, const float* r1,
                                           const float* r2, const float* r3, const float* q,
                                           float* c1, float* c2, float* c3, cudaStream_t st);
+// The restriction of launch_lin_residual_restrict32 to c and, in the same
+// launch, `extra` (1 or 2) further 8-cell averages to e and g (n/2 a
+// multiple of 16).
+cudaError_t launch_lin_restrict_chain32(const Lvl& L, bool zero, int extra, const float* d1,
+                                       const float* d2, const float* d3, const float* r1,
+                                       const float* r2, const float* r3, const float* q,
+                                       float* const c[3], float* const e[3], float* const g[3],
+                                       cudaStream_t st);
 // skip0: the colour-0 cells of d are left untouched (a red-black pass of
 // colour 0 recomputes them next).
 cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, const float* e2,

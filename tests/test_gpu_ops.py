@@ -551,3 +551,55 @@ def test_split_layout_is_a_permutation(n):
     assert sorted(perm.tolist()) == list(range(n ** 3))
     x = np.arange(n ** 3, dtype=np.float64).reshape((n,) * 3)
     np.testing.assert_array_equal(from_split(to_split(x)), x)
+
+
+@pytest.mark.parametrize("n,levels", [(32, 2), (64, 3), (96, 3)])
+@pytest.mark.parametrize("zero", [False, True])
+def test_restrict_chain_equals_separate_restrictions(n, levels, zero):
+    """The V-cycle's descent without pre-smoothing in one launch: the first
+    restriction I (r - J d) and one or two further 8-cell averages, bit for
+    bit the separate restrictions (each coarser level from d = 0), and the
+    first level against the oracle as in the single restriction's test."""
+    h, b, c, u = case(n)
+    p = prm()
+    rng = np.random.default_rng(41 + n)
+    q = O.jacobian_coefficient(u[0], b, p).astype(np.float32)
+    r = [rng.standard_normal((n,) * 3).astype(np.float32) for _ in range(3)]
+    d = [np.zeros((n,) * 3, np.float32) if zero else
+         (0.1 * rng.standard_normal((n,) * 3)).astype(np.float32) for _ in range(3)]
+    dd = [dev(to_split(x), torch.float32) for x in d]
+    rd = [dev(to_split(x), torch.float32) for x in r]
+    qd = dev(to_split(q), torch.float32)
+    sizes = [n // 2, n // 4, n // 8][:levels]
+    chain = [[empty(m, torch.float32) for _ in range(3)] for m in sizes]
+    B.pfc_op_lin_restrict_chain(n, h, EPS, TAU, zero, levels, *(None, None, None) if zero else dd,
+                                *rd, None if zero else qd, *chain[0], *chain[1],
+                                *(chain[2] if levels == 3 else (None, None, None)))
+    # separate launches: the first restriction, then zero-start restrictions
+    sep = [[empty(m, torch.float32) for _ in range(3)] for m in sizes]
+    B.pfc_op_lin_residual_restrict(n, h, EPS, TAU, zero, *(None, None, None) if zero else dd,
+                                   *rd, None if zero else qd, *sep[0])
+    for lv in range(1, levels):
+        m = n >> lv
+        B.pfc_op_lin_residual_restrict(m, 2.0 ** lv * h, EPS, TAU, True, None, None, None,
+                                       *sep[lv - 1], None, *sep[lv])
+    for lv in range(levels):
+        for x, y in zip(chain[lv], sep[lv]):
+            assert torch.equal(x, y), (lv, n)
+    # the last level is the average of the first one's cells over blocks
+    first = [from_split(host(x)).astype(np.float64) for x in sep[0]]
+    k = 2 ** (levels - 1)
+    for x, y in zip(first, sep[levels - 1]):
+        m = x.shape[0] // k
+        avg = x.reshape(m, k, m, k, m, k).mean(axis=(1, 3, 5))
+        assert_close_field(from_split(host(y)), avg, 1e-6, "chained average")
+
+
+def test_restrict_chain_rejects_bad_sizes():
+    z = torch.zeros(48 ** 3, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.PFCError):           # n / 2 not a multiple of 16
+        B.pfc_op_lin_restrict_chain(48, 0.5, EPS, TAU, True, 2, None, None, None, z, z, z, None,
+                                    z, z, z, z, z, z)
+    with pytest.raises(B.PFCError):           # levels out of range
+        B.pfc_op_lin_restrict_chain(64, 0.5, EPS, TAU, True, 4, None, None, None, z, z, z, None,
+                                    z, z, z, z, z, z, z, z, z)
