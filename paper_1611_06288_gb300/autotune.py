@@ -28,7 +28,7 @@ from .solver import PFCBatch, PFCSolver
 
 # (nu1, nu2) x inner cycles x Jacobi factor; two coarsest sweeps.  Then the
 # defect's planes per block (0: the SM-count heuristic's choice).
-DEFAULT_SPACE = {"nu": [(0, 1), (1, 1), (1, 2), (2, 2)], "inner_cycles": [2, 3],
+DEFAULT_SPACE = {"nu": [(0, 1), (1, 1), (1, 2), (2, 2)], "inner_cycles": [2, 3, 5],
                  "jacobi_factor": [3, 4], "coarse_sweeps": [2],
                  "defect_planes": [0, 4, 8, 16, 32]}
 

@@ -154,13 +154,18 @@ def smooth_sweep(n: int, dt: float = 0.0125, tol: float = 1e-9):
     """Smooth mode on L = 32, eps = 0.025, to T = 1 (steps = 1/dt).
 
     Mixed-path settings: at n >= 64 the finest level is stiff (red-black) and
-    V(0,1) cycles with 4 Jacobi sweeps per requested sweep on the
-    intermediate levels are fastest: two per correction at 64^3 and 128^3 (2
-    corrections per step), three at 256^3 (3 corrections per step instead of
-    4 with two: 131 against 126 steps/s); at 32^3 V(1,2)."""
-    if n >= 64:
-        kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 3 if n >= 256 else 2),
-              ("jacobi_factor", 4), ("coarse_sweeps", 2))
+    V(0,1) cycles are fastest: at 64^3 and 128^3 two per correction with 4
+    Jacobi sweeps per requested sweep on the intermediate levels (2
+    corrections per step; 3 with a factor of 3, and 2 still with up to 8
+    cycles); at 256^3 five per correction with a factor of 3 (2 corrections
+    per step: 165 steps/s, against 153 for three cycles and 3 corrections,
+    143 for two and 4); at 32^3 V(1,2)."""
+    if n >= 256:
+        kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 5), ("jacobi_factor", 3),
+              ("coarse_sweeps", 2))
+    elif n >= 64:
+        kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 2), ("jacobi_factor", 4),
+              ("coarse_sweeps", 2))
     else:
         kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 2), ("jacobi_factor", 3),
               ("coarse_sweeps", 2))
