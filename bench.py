@@ -200,17 +200,38 @@ class ClockSampler:
 # shared memory.
 # ---------------------------------------------------------------------------
 
+def chained_levels(params, levels):
+    """Levels whose zero-start restriction the one-launch descent takes over
+    (k_lin_restrict_chain32: from the first level restricting to at most 64^3
+    cells, n/2 a multiple of 16, up to two more levels above the tail): their
+    r is averaged in shared memory and not read back."""
+    if params.nu1 > 0:
+        return set()
+    for l, (m, _) in enumerate(levels):
+        nc = m // 2
+        if m > 16 and l + 1 < len(levels) and nc <= 64 and nc % 16 == 0:
+            out = set()
+            for j in range(l + 1, min(l + 3, len(levels) - 1)):
+                if levels[j][0] <= 16:
+                    break
+                out.add(j)
+            return out
+    return set()
+
+
 def vcycle_bytes(params, levels):
     """levels: [(n, kind)] of the mixed hierarchy, finest first."""
     from paper_1611_06288_gb300 import binding as B
     total = 0.0
+    chained = chained_levels(params, levels)
     for l, (m, kind) in enumerate(levels):
         cells = float(m) ** 3
         if m <= 16:
             total += 28.0 * cells
             break
         first = l == 0
-        total += cells * ((28.0 + 1.5) if first else (12.0 + 1.5))          # restriction
+        rbytes = 28.0 if first else (0.0 if l in chained else 12.0)
+        total += cells * (rbytes + 1.5)                                      # restriction
         # prolongation: d read and written (first level: the measured V-cycle
         # starts from d != 0) or written; before a red-black pass of colour 0
         # only the colour-1 half of d is touched

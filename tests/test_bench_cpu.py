@@ -28,3 +28,38 @@ def test_oracle_step_timer():
     import bench
     t, cycles = bench.oracle_step_time(8)
     assert t > 0 and cycles >= 1
+
+
+def test_vcycle_byte_model_matches_the_kernel_counts():
+    """The V-cycle byte model of bench.py against the per-kernel algorithmic
+    bytes of opbench at 128^3 with the smooth-mode settings (V(0,1), red-black
+    finest level, Jacobi factor 4 below): finest level = restriction (d != 0)
+    + prolongation with the colour-0 half skipped + one red-black sweep."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1611_06288_gb300 import binding as B
+    from paper_1611_06288_gb300 import opbench as OB
+    p = B.pfc_default_params()
+    p.nu1, p.nu2, p.jacobi_factor, p.jacobi_factor0 = 0, 1, 4, 4
+    n = 128
+    finest = bench.vcycle_bytes(p, [(n, B.PFC_SWEEP_RB)])
+    assert finest == OB.algorithmic_bytes("lin_restrict", n) + \
+        OB.algorithmic_bytes("lin_prolong_skip0", n) + OB.algorithmic_bytes("lin_smooth", n)
+    # a Jacobi level: zero-start restriction, assigning prolongation of both
+    # colours, four sweeps of 40 B per cell
+    jac = [(n, B.PFC_SWEEP_RB), (64, B.PFC_SWEEP_JACOBI), (32, B.PFC_SWEEP_JACOBI),
+           (16, B.PFC_SWEEP_JACOBI)]
+    assert bench.vcycle_bytes(p, jac[:2]) - finest == \
+        OB.algorithmic_bytes("lin_restrict_zero", 64) + \
+        OB.algorithmic_bytes("lin_prolong_assign", 64) + 4 * 40.0 * 64 ** 3
+    # without pre-smoothing the 64^3 and 32^3 levels' averages come from the
+    # first restriction's launch: only their 1.5 B per cell of output count
+    assert bench.chained_levels(p, jac) == {1, 2}
+    full = bench.vcycle_bytes(p, jac)
+    p.nu1 = 1
+    assert bench.chained_levels(p, jac) == set()
+    assert bench.vcycle_bytes(p, jac) - full == 12.0 * (64 ** 3 + 32 ** 3)
+    # 256^3: the descent starts one level lower (128^3 -> 64^3, 32^3, 16^3)
+    p.nu1 = 0
+    big = [(256, B.PFC_SWEEP_RB)] + jac
+    assert bench.chained_levels(p, big) == {2, 3}
