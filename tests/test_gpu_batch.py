@@ -71,6 +71,32 @@ def test_batch_matches_single_runs(n):
         s.close()
 
 
+@pytest.mark.parametrize("n", [64, 128])
+def test_batch_without_presmoothing_matches_single_runs(n):
+    """Two members on the V(0,1) settings of the smooth-mode workload, where
+    the V-cycle's descent runs in one launch (64^3: 32^3 and 16^3 from the
+    first restriction; 128^3: 64^3, 32^3, 16^3) and the prolongation skips
+    the colour-0 children: the batch equals the members run alone."""
+    L, dt = 32.0, 0.05
+    eps, phi0 = members(n, 2, n + 1)
+    kw = dict(tol=1e-11, max_cycles=80, nu1=0, nu2=1, inner_cycles=2, jacobi_factor=4,
+              coarse_sweeps=2)
+    b = PFCBatch(n, L, eps, dt, phi0, **kw)
+    singles = [PFCSolver(n, L, eps[m], dt, phi0[m], precision="mixed", **kw) for m in range(2)]
+    for _ in range(3):
+        b.step(1)
+        for s in singles:
+            s.step(1)
+        got = host(b.phi())
+        for m, s in enumerate(singles):
+            assert rel_l2(got[m], host(s.phi())) <= PARITY_RTOL, m
+    _, res, _ = b.status()
+    assert max(res) <= 1e-11
+    b.close()
+    for s in singles:
+        s.close()
+
+
 def test_batch_validation():
     eps, phi0 = members(16, 2, 1)
     with pytest.raises(B.PFCError):
