@@ -100,3 +100,31 @@ def test_wrong_laplacian_neighbour_is_caught(monkeypatch):
     monkeypatch.setattr(O, "op_d", lambda w, axis, h: (
         (np.roll(w, -1, axis) - w) / h if axis == O.AX_Z else (w - np.roll(w, 1, axis)) / h))
     _fails(P.test_laplacian_fourier_symbol, 8, 32.0)
+
+
+def test_cell_corner_sampling_is_caught(monkeypatch):
+    # fields sampled at i h (cell corners) instead of the cell centres (i + 1/2) h
+    from paper_1611_06288_gb300 import workloads as W
+
+    def corners(n, L):
+        c = np.arange(n) * (L / n)
+        return c[:, None, None], c[None, :, None], c[None, None, :]
+    monkeypatch.setattr(W, "cell_centres", corners)
+    _fails(P.test_second_order_in_space, P_golden())
+
+
+def test_wrong_spacing_on_one_level_is_caught(monkeypatch):
+    # the 16^3 grid of the refinement run with twice its spacing
+    orig = O.run
+
+    def bad_run(phi0, nsteps, h, prm, *a, **kw):
+        if phi0.shape[0] == 16:
+            h = 2.0 * h
+        return orig(phi0, nsteps, h, prm, *a, **kw)
+    monkeypatch.setattr(O, "run", bad_run)
+    _fails(P.test_second_order_in_space, P_golden())
+
+
+def P_golden():
+    import os
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
