@@ -362,7 +362,8 @@ int pfc_op_diagnostics_df(int n, double h, double eps, const float* d_a,
                           const float* d_b, void* d_scratch, double* out,
                           void* stream);
 
-/* RMS residual sqrt(sum_c sum r_c^2 / (3 n^3)) of u (blocking). */
+/* RMS residual sqrt(sum_c sum r_c^2 / (3 n^3)) of u (blocking).  n >= 2,
+ * h > 0 and non-null pointers, else PFC_EINVAL. */
 int pfc_op_residual_norm(int n, double h, double eps, double tau,
                          const double* d_phi, const double* d_mu,
                          const double* d_om, const double* d_S1,
@@ -380,12 +381,14 @@ int pfc_op_residual_norm(int n, double h, double eps, double tau,
  * afford the device-wide synchronisation of cudaMalloc/cudaFree.
  * Limit: n^3 <= 256^3 cells; larger grids return PFC_ESIZE (with a message in
  * pfc_last_error) and must use pfc_op_residual_norm.
- * The first call on each device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every tile slot is rewritten by each call, so no state
- * carries over that needs clearing; all calls on a device share the array, so
- * calls that overlap on the GPU (concurrent streams, threads) race and must
- * be serialised by the caller.  Blocking, like pfc_op_residual_norm. */
+ * Every call looks up the array's device address with the caller's device
+ * current (cudaGetSymbolAddress).  Every tile slot a call reads is rewritten
+ * by that call, so no state carries over that needs clearing; all calls on a
+ * device share the array, so calls that overlap on the GPU (concurrent
+ * streams, threads) race and must be serialised by the caller.  The call is
+ * blocking (it reads the sum back and synchronises `stream`), so it cannot be
+ * made on a stream that is being captured.  Arguments are checked as in
+ * pfc_op_residual_norm: n >= 2, h > 0, non-null pointers, else PFC_EINVAL. */
 int pfc_op_residual_norm_static(int n, double h, double eps, double tau,
                                 const double* d_phi, const double* d_mu,
                                 const double* d_om, const double* d_S1,

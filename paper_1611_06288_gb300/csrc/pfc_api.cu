@@ -1239,7 +1239,7 @@ int pfc_op_residual_norm(int n, double h, double eps, double tau, const double* 
                          const double* mu, const double* om, const double* S1,
                          const double* S2, const double* S3, const double* b,
                          void* scratch, double* out, void* stream) {
-  if (n < 2 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !scratch || !out)
+  if (n < 2 || !(h > 0) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !scratch || !out)
     return PFC_EINVAL;
   double* partials = (double*)scratch;
   double* dout = partials + (size_t)kReduceBlocks * kReduceComps;

@@ -7,8 +7,6 @@
 #include <math.h>
 #include <stdio.h>
 
-#include <mutex>
-
 #include "pfc_internal.h"
 
 namespace pfc {
@@ -17,31 +15,23 @@ namespace {
 constexpr int kTile = 256;                       // cells per partial sum
 constexpr int kMaxPartials = 65536;              // => at most 256^3 cells
 constexpr int64_t kMaxCells = (int64_t)kMaxPartials * kTile;
-constexpr int kMaxDevices = 64;
 
 // One partial sum per 256-cell tile, then the final sum in the last slot.
 // Loaded with the library, held by every GPU that loads it until exit
 // (512 KiB + 64 B).  All calls on a device share it.
 static __device__ __align__(256) double g_scratch[kMaxPartials + 8];
 
-std::mutex g_mu;
-double* g_addr[kMaxDevices] = {nullptr};
-
-// Device address of g_scratch on the current device; looked up once per
-// device with that device current.
+// Device address of g_scratch in the current context.  In host code the name
+// g_scratch denotes a host-side stand-in, not device memory, so the address
+// is asked of the runtime with the caller's device current.  It is looked up
+// on every call rather than cached: after a cudaDeviceReset, or in another
+// context of the same device, the module is loaded again and the array may
+// sit elsewhere.  The lookup is a host-side table query.
 cudaError_t scratch_address(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double*>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -90,7 +80,8 @@ extern "C" int pfc_op_residual_norm_static(int n, double h, double eps, double t
                                            const double* om, const double* S1,
                                            const double* S2, const double* S3,
                                            const double* b, double* out, void* stream) {
-  if (n < 1 || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !out || !(h > 0))
+  // the same argument checks as pfc_op_residual_norm
+  if (n < 2 || !(h > 0) || !phi || !mu || !om || !S1 || !S2 || !S3 || !b || !out)
     return PFC_EINVAL;
   const int64_t cells = (int64_t)n * n * n;
   if (cells > kMaxCells) {
@@ -110,11 +101,21 @@ extern "C" int pfc_op_residual_norm_static(int n, double h, double eps, double t
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int ntiles = (int)((cells + kTile - 1) / kTile);
-  k_residual_norm2_tiles<<<ntiles, kTile, 0, st>>>(make_lvl(n, h, eps, tau), phi, mu, om, S1,
-                                                   S2, S3, b, scratch);
-  k_sum_tiles<<<1, 1024, 0, st>>>(scratch, ntiles);
+  // cudaLaunchKernelEx returns the status of this launch alone, so an
+  // earlier, unrelated launch error of the caller's thread is neither
+  // reported as this call's nor cleared.
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ntiles);
+  cfg.blockDim = dim3(kTile);
+  cfg.stream = st;
+  const Lvl lv = make_lvl(n, h, eps, tau);
+  e = cudaLaunchKernelEx(&cfg, k_residual_norm2_tiles, lv, phi, mu, om, S1, S2, S3, b, scratch);
+  if (e == cudaSuccess) {
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(1024);
+    e = cudaLaunchKernelEx(&cfg, k_sum_tiles, scratch, ntiles);
+  }
   double sum = 0.0;
-  e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(&sum, scratch + kMaxPartials, sizeof(double), cudaMemcpyDeviceToHost,
                         st);
