@@ -77,6 +77,11 @@ NCU_TRAFFIC = {("mixed", "defect", 128): 153.0e6}   # profiles/k_defect64_fx_128
 # defects and one pointwise per step (two corrections): 16 per launch.
 KERNEL_FLOPS = {("mixed", "defect"): (16.0, 2)}
 
+# Algorithmic bytes per cell of the FP64 defect (the ALU-bound class above),
+# reported beside its FP64 roofline: phi, mu, om, b, S2, S3 read, r(3) and q
+# FP32 and the three Laplacians FP64 written.
+DEFECT_BYTES = 88.0
+
 # FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
 # sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
 # x 2 flops x 152 SMs x 2.07 GHz.
@@ -97,6 +102,8 @@ def parse():
     ap.add_argument("--nu2", type=int, default=None)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-n256", dest="n256", action="store_false",
+                    help="skip the 256^3 legs (the n256 object)")
     # the headline path: FP64 defect correction around FP32 multigrid; the
     # double-float form is timed beside it
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df"])
@@ -251,45 +258,80 @@ def vcycle_bytes(params, levels):
 # CPU oracle timing (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step_time(n: int):
-    """Time one full oracle time step of the workload (start rule, tol 1e-9)."""
-    from oracle import pfc_oracle as O
-    from paper_1611_06288_gb300 import workloads as W
-    wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
-    phi0 = wl.phi0()
-    prm = O.Params(eps=wl.eps, tau=wl.dt)
-    t0 = time.perf_counter()
-    res = O.solve_step(phi0, phi0, [phi0, 0 * phi0, 0 * phi0], wl.h, prm, wl.tol)
-    O.energy(res.u[0], wl.h, wl.eps)
-    O.mass(res.u[0], wl.h)
-    return time.perf_counter() - t0, res.cycles
-
-
-def cpu_threads() -> int:
+def host_cpu() -> dict:
+    """Logical cores and CPU model of the host the oracle runs on."""
+    model = None
     try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        return max([i.get("num_threads", 1) for i in info] or [1])
-    except Exception:
-        return 1
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    import platform
+    # Arm cores report a part number only
+    parts = {"0xd4f": "Arm Neoverse V2 (part 0xd4f)", "0xd40": "Arm Neoverse V1 (part 0xd40)",
+             "0xd0c": "Arm Neoverse N1 (part 0xd0c)", "0xd49": "Arm Neoverse N2 (part 0xd49)"}
+    model = parts.get(model, model)
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+class OracleSteps:
+    """The oracle (numpy FP64) on the bench workload: a first step by the
+    start rule (phi^{-1} := phi^0), then warm steps from the previous step's
+    solution, as the GPU's timed steps are.  numpy's elementwise kernels run
+    on one thread, so the oracle uses one core."""
+
+    def __init__(self, n: int):
+        from oracle import pfc_oracle as O
+        from paper_1611_06288_gb300 import workloads as W
+        self.O = O
+        self.wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
+        self.prm = O.Params(eps=self.wl.eps, tau=self.wl.dt)
+        phi0 = self.wl.phi0()
+        self.b, self.c = phi0, phi0
+        self.mu, self.om = 0 * phi0, 0 * phi0
+        self.k = 0
+
+    def step(self):
+        """One time step with the energy/mass diagnostics; returns (s, cycles)."""
+        O, wl = self.O, self.wl
+        t0 = time.perf_counter()
+        res = O.solve_step(self.b, self.c, [self.b, self.mu, self.om], wl.h, self.prm, wl.tol)
+        a, self.mu, self.om = res.u
+        O.energy(a, wl.h, wl.eps)
+        O.modified_energy(a, self.b, wl.h, wl.eps)
+        O.mass(a, wl.h)
+        dt = time.perf_counter() - t0
+        self.c, self.b = self.b, a
+        self.k += 1
+        return dt, res.cycles
 
 
 def run_reference(args):
-    """The oracle (numpy FP64, host cores) on the same workload and metric."""
+    """The oracle (numpy FP64, host cores) on the same workload and metric:
+    one untimed start step, then warm steps timed one by one."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     n = args.n
-    # One full step is ~15-20 s at 128^3: the bounded sample of each bench
-    # step is one oracle time step; steps/warmup are capped to keep the run
-    # within a few minutes.
-    warm = min(args.warmup, 1)
-    steps = min(args.steps, 3)
+    # One oracle step is ~10 s at 128^3 on the GPU hosts: the bounded sample
+    # of each bench step is one warm oracle time step.  As on the GPU, the
+    # first `warmup` steps (the first by the start rule) are untimed and the
+    # next ones timed; both counts are capped so the run ends within a few
+    # minutes.
+    warm = max(1, min(args.warmup, 5))
+    steps = max(1, min(args.steps, 5))
+    orc = OracleSteps(n)
     for _ in range(warm):
-        oracle_step_time(n)
+        orc.step()
     times, cycles = [], []
     for _ in range(steps):
-        t, c = oracle_step_time(n)
+        t, c = orc.step()
         times.append(t)
         cycles.append(c)
     tot = sum(times)
@@ -300,9 +342,13 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": dict(WORKLOAD, workload=f"smooth-mode {n}^3", n=n,
                                             l2="inputs > L2 not applicable (CPU)"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-                         "sample": f"{steps} full oracle time steps at {n}^3 from phi0 "
-                                   f"(start rule), V-cycles {cycles}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "host": host_cpu(),
+                         "sample": f"oracle time steps {warm + 1}..{warm + steps} at {n}^3 "
+                                   f"after {warm} untimed (warm: each from "
+                                   f"the previous step's solution, as the GPU's timed steps), "
+                                   f"FAS V(2,2) cycles {cycles}, energy/mass each step; numpy "
+                                   f"elementwise on one thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -311,6 +357,44 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
+
+# FP64 FAS smoother: FP64 flops per updated cell of one launch (a red-black
+# colour pass updates n^3/2 cells, a Jacobi sweep n^3): three neighbour sums
+# (15 DADD), the source terms, the Newton coefficient and its cubic, and the
+# 3x3 solve by elimination with one division (k_smooth_colour, Section 5).
+FP64_SMOOTH_FLOPS = 66.0
+
+
+def fp64_roofline(s, n, B, prof_steps=1):
+    """Roofline of the dominant kernel class of the plain FP64 FAS path: one
+    host-driven step with every class timed by CUDA events picks the class,
+    then `prof_steps` steps time that class alone."""
+    s.profile(None)
+    s.step(1)
+    prof = s.profile_read()
+    (cls, lvl), _ = max(prof.items(), key=lambda kv: kv[1][1])
+    s.profile([cls])
+    for _ in range(prof_steps):
+        s.step(1)
+    launches, ms = B.pfc_profile_read(s.ctx, B.KERNEL_CLASSES.index(cls), lvl)
+    s.profile([])
+    m, _, kind = B.pfc_level_info(s.params, lvl)
+    out = {"kernel": f"{cls} (level {lvl}, {m}^3)", "ms_per_launch": ms / max(launches, 1),
+           "timing": f"CUDA events around each launch, {prof_steps} host-driven step(s)"}
+    if cls == "smooth":
+        units = m ** 3 / (2 if kind == B.PFC_SWEEP_RB else 1)
+        achieved = FP64_SMOOTH_FLOPS * units * launches / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                    "flops_per_updated_cell": FP64_SMOOTH_FLOPS,
+                    "peak_source": "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz "
+                                   "(derived)"})
+    else:
+        out.update({"bound": None, "note": "dominant class without a flop model"})
+    out["kernel_profile_ms"] = {f"{k[0]}@{n >> k[1]}": round(v[1], 4)
+                                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
+    return out
+
 
 def run_ours(args):
     import numpy as np
@@ -329,15 +413,6 @@ def run_ours(args):
     if ws > 1:
         tdist.init_process_group("nccl", device_id=dev)
     B.lib()  # fails loudly if libpfc.so is missing
-
-    n = args.n
-    wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
-    phi0 = wl.phi0()
-    mixed_kw = wl.mixed()
-    for k in ("inner_cycles", "jacobi_factor", "nu1", "nu2"):
-        if getattr(args, k) is not None:
-            mixed_kw[k] = getattr(args, k)
-    cells = n ** 3
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def barrier():
@@ -345,7 +420,7 @@ def run_ours(args):
             tdist.barrier()
         torch.cuda.synchronize(dev)
 
-    def time_steps(s, k, profile_classes=None, diag=True):
+    def time_steps(s, k, diag=True):
         """k timed steps, L2 flushed (untimed) before each; returns total ms."""
         st = s.stream
         total = 0.0
@@ -364,129 +439,163 @@ def run_ours(args):
             cycles.append(stats.cycles_last)
         return total, cycles
 
-    # ---- mixed path (headline) --------------------------------------------
-    # every leg forms the energy/mass diagnostics of each new state inside the
-    # step (step_diagnostics): the timed step includes them, with no extra
-    # host round trip
-    s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, step_diagnostics=True,
-                  precision=args.precision, **mixed_kw)
-    for _ in range(args.warmup):
-        s.step(1)
-        s.diagnostics()
-    barrier()
-    # timed region: each step is one CUDA graph launch (device-side loop)
-    clocks = ClockSampler(local)
-    clocks.start()
-    launches0 = s.launches
-    ms_total, cycles = time_steps(s, args.steps)
-    launches = s.launches - launches0
-    barrier()
-    clk = clocks.stop()
-    # kernel timing: the same steps driven from the host with every launch of
-    # the dominant kernel class bracketed by CUDA events on the solver stream
-    s.profile(None)
-    time_steps(s, 2)
-    prof = s.profile_read()
-    (dom_cls, dom_lvl), _ = max(prof.items(), key=lambda kv: kv[1][1])
-    s.profile([dom_cls])
-    prof_steps = max(2, min(args.steps, 10))
-    ms_instr, _ = time_steps(s, prof_steps)
-    dom_launches, dom_time = B.pfc_profile_read(s.ctx, B.KERNEL_CLASSES.index(dom_cls), dom_lvl)
-    s.profile([])
+    def measure(n, steps, warmup, fp64_steps, mixed_over=None, precision="mixed",
+                other_leg=True):
+        """Every GPU leg of one grid size; returns a dict of results."""
+        wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
+        phi0 = wl.phi0()
+        mixed_kw = wl.mixed()
+        mixed_kw.update(mixed_over or {})
+        cells = n ** 3
+        # ---- mixed path (headline) ----------------------------------------
+        # every leg forms the energy/mass diagnostics of each new state inside
+        # the step (step_diagnostics): the timed step includes them, with no
+        # extra host round trip
+        s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                      step_diagnostics=True, precision=precision, **mixed_kw)
+        for _ in range(warmup):
+            s.step(1)
+            s.diagnostics()
+        barrier()
+        # timed region: each step is one CUDA graph launch (device-side loop)
+        clocks = ClockSampler(local)
+        clocks.start()
+        launches0 = s.launches
+        ms_total, cycles = time_steps(s, steps)
+        launches = s.launches - launches0
+        barrier()
+        clk = clocks.stop()
+        # kernel timing: the same steps driven from the host with every launch
+        # of the dominant kernel class bracketed by CUDA events on the solver
+        # stream
+        s.profile(None)
+        time_steps(s, 2)
+        prof = s.profile_read()
+        (dom_cls, dom_lvl), _ = max(prof.items(), key=lambda kv: kv[1][1])
+        s.profile([dom_cls])
+        prof_steps = max(2, min(steps, 10))
+        ms_instr, _ = time_steps(s, prof_steps)
+        dom_launches, dom_time = B.pfc_profile_read(s.ctx, B.KERNEL_CLASSES.index(dom_cls),
+                                                    dom_lvl)
+        s.profile([])
+        s.close()
+        t_max, value = aggregate_replicas(ms_total / 1e3, steps, ws, dev)
 
-    t_max, value = aggregate_replicas(ms_total / 1e3, args.steps, ws, dev)
+        # one FP32 V-cycle, graph-launched: the step time with one more
+        # V-cycle per correction, at the same corrections per step, minus the
+        # step time as configured, per correction (no events inside the graph)
+        vcyc = None
+        if precision == "mixed" and mixed_kw.get("nu1", 0) == 0:
+            vk = max(10, min(steps, 40))
+            res = {}
+            for extra in (0, 1):
+                kw = dict(mixed_kw, inner_cycles=mixed_kw.get("inner_cycles", 1) + extra)
+                sv = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                               step_diagnostics=True, precision="mixed", **kw)
+                for _ in range(warmup):
+                    sv.step(1)
+                res[extra] = time_steps(sv, vk, diag=False)
+                if extra == 0:
+                    levels = []
+                    for lv in range(24):
+                        try:
+                            m, _, kind = B.pfc_level_info(sv.params, lv)
+                        except B.PFCError:
+                            break
+                        levels.append((m, kind))
+                    vbytes = vcycle_bytes(sv.params, levels)
+                sv.close()
+            (t0_ms, c0), (t1_ms, c1) = res[0], res[1]
+            if c0 == c1 and sum(c0) > 0:
+                v_ms = (t1_ms - t0_ms) / sum(c0)
+                peaks_v, src_v = measured_peaks()
+                gbs = vbytes / (v_ms / 1e3) / 1e9
+                vcyc = {"ms": v_ms, "algorithmic_bytes": vbytes, "achieved": gbs,
+                        "unit": "GB/s", "peak": peaks_v["hbm_gbs"],
+                        "frac": gbs / peaks_v["hbm_gbs"],
+                        "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src_v})",
+                        "levels": [m for m, _ in levels],
+                        "method": f"({vk} steps at inner_cycles+1 - {vk} steps as configured) / "
+                                  f"{sum(c0)} corrections, graph-launched, L2 flushed per "
+                                  f"step; a V-cycle that does not start from d = 0"}
+            else:
+                vcyc = {"ms": None, "reason": f"corrections differ: {c0} vs {c1}"}
 
-    # one FP32 V-cycle, graph-launched: the step time with one more V-cycle
-    # per correction, at the same corrections per step, minus the step time
-    # as configured, per correction (no events inside the graph)
-    vcyc = None
-    if args.precision == "mixed" and mixed_kw.get("nu1", 0) == 0:
-        vk = max(10, min(args.steps, 40))
-        res = {}
-        for extra in (0, 1):
-            kw = dict(mixed_kw, inner_cycles=mixed_kw.get("inner_cycles", 1) + extra)
-            sv = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
-                           step_diagnostics=True,
-                           precision="mixed", **kw)
-            for _ in range(args.warmup):
-                sv.step(1)
-            res[extra] = time_steps(sv, vk, diag=False)
-            if extra == 0:
-                levels = []
-                for lv in range(24):
-                    try:
-                        m, _, kind = B.pfc_level_info(sv.params, lv)
-                    except B.PFCError:
-                        break
-                    levels.append((m, kind))
-                vbytes = vcycle_bytes(sv.params, levels)
-            sv.close()
-        (t0_ms, c0), (t1_ms, c1) = res[0], res[1]
-        if c0 == c1 and sum(c0) > 0:
-            v_ms = (t1_ms - t0_ms) / sum(c0)
-            peaks_v, src_v = measured_peaks()
-            gbs = vbytes / (v_ms / 1e3) / 1e9
-            vcyc = {"ms": v_ms, "algorithmic_bytes": vbytes, "achieved": gbs, "unit": "GB/s",
-                    "peak": peaks_v["hbm_gbs"], "frac": gbs / peaks_v["hbm_gbs"],
-                    "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({src_v})",
-                    "levels": [m for m, _ in levels],
-                    "method": f"({vk} steps at inner_cycles+1 - {vk} steps as configured) / "
-                              f"{sum(c0)} corrections, graph-launched, L2 flushed per step; "
-                              f"a V-cycle that does not start from d = 0"}
+        # roofline of the dominant kernel
+        peaks, peak_src = measured_peaks()
+        m = n >> dom_lvl
+        if (precision, dom_cls) in KERNEL_FLOPS:
+            per_cell, per_group = KERNEL_FLOPS[(precision, dom_cls)]
+            groups = dom_launches / per_group
+            achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e12 \
+                if dom_time > 0 else 0.0
+            bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
+            peak_src = "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz (derived)"
         else:
-            vcyc = {"ms": None, "reason": f"corrections differ: {c0} vs {c1}"}
+            per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
+            groups = dom_launches / per_group
+            achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 \
+                if dom_time > 0 else 0.0
+            bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
+            peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
+        traffic = NCU_TRAFFIC.get((precision, dom_cls, m))
+        bytes_cell = KERNEL_BYTES.get(dom_cls, (None, 1))[0]
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak,
+                    "unit": unit, "frac": achieved / peak,
+                    "traffic": traffic / 1e9 if traffic is not None else None,
+                    "traffic_unit": "GB per launch (ncu dram__bytes_read + write)",
+                    "kernel": f"{dom_cls} (level {dom_lvl}, {m}^3)",
+                    "ms_per_launch": dom_time / max(groups, 1),
+                    "timing": f"CUDA events around each launch, {prof_steps} host-driven steps "
+                              f"after the timed region ({1e3 * prof_steps / ms_instr:.1f} "
+                              f"steps/s with the events)",
+                    "peak_source": peak_src}
+        if bound == "alu" and bytes_cell and dom_time > 0:
+            gbs = DEFECT_BYTES * m ** 3 * groups / (dom_time / 1e3) / 1e9
+            roofline["hbm"] = {"algorithmic_bytes_per_cell": DEFECT_BYTES, "achieved": gbs,
+                               "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]}
 
-    # roofline of the dominant kernel
-    peaks, peak_src = measured_peaks()
-    m = n >> dom_lvl
-    if (args.precision, dom_cls) in KERNEL_FLOPS:
-        per_cell, per_group = KERNEL_FLOPS[(args.precision, dom_cls)]
-        groups = dom_launches / per_group
-        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e12 if dom_time > 0 else 0.0
-        bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
-        peak_src = "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz (derived)"
-    else:
-        per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
-        groups = dom_launches / per_group
-        achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 if dom_time > 0 else 0.0
-        bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
-        peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
-    traffic = NCU_TRAFFIC.get((args.precision, dom_cls, m))
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak,
-                "unit": unit, "frac": achieved / peak,
-                "traffic": traffic / 1e9 if traffic is not None else None,
-                "traffic_unit": "GB per launch (ncu dram__bytes_read + write)",
-                "kernel": f"{dom_cls} (level {dom_lvl}, {m}^3)",
-                "ms_per_launch": dom_time / max(groups, 1),
-                "timing": f"CUDA events around each launch, {prof_steps} host-driven steps "
-                          f"after the timed region ({1e3 * prof_steps / ms_instr:.1f} steps/s "
-                          f"with the events)",
-                "peak_source": peak_src}
+        # ---- plain FP64 FAS path, same workload and tolerance -------------
+        s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                        precision="fp64", step_diagnostics=True)
+        for _ in range(min(warmup, 2)):
+            s64.step(1)
+            s64.diagnostics()
+        ms64, cyc64 = time_steps(s64, fp64_steps)
+        fp64 = {"value": fp64_steps / (ms64 / 1e3), "unit": UNIT, "steps": fp64_steps,
+                "cycles_per_step": cyc64,
+                "solver": "FAS V(2,2) (library defaults), Newton pointwise smoother, full "
+                          "coarsening to 2^3"}
+        fp64["roofline"] = fp64_roofline(s64, n, B)
+        s64.close()
 
-    # ---- plain FP64 FAS path, same workload and tolerance -----------------
-    s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision="fp64",
-                    step_diagnostics=True)
-    for _ in range(min(args.warmup, 2)):
-        s64.step(1)
-        s64.diagnostics()
-    ms64, cyc64 = time_steps(s64, args.fp64_steps)
-    fp64 = {"value": args.fp64_steps / (ms64 / 1e3), "unit": UNIT, "steps": args.fp64_steps,
-            "cycles_per_step": cyc64}
-    s64.close()
+        out = {"n": n, "wl": wl, "phi0": phi0, "mixed_kw": mixed_kw, "value": value,
+               "t_max": t_max, "cycles": cycles, "launches": launches, "clocks": clk,
+               "roofline": roofline, "vcycle": vcyc, "fp64": fp64,
+               "kernel_profile_ms": {f"{k[0]}@{n >> k[1]}": round(v[1], 4)
+                                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
 
-    # ---- the other mixed form, same workload, tolerance and settings -------
-    other = "mixed_df" if args.precision == "mixed" else "mixed"
-    so = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol, precision=other,
-                   step_diagnostics=True,
-                   **mixed_kw)
-    for _ in range(args.warmup):
-        so.step(1)
-        so.diagnostics()
-    ms_o, cyc_o = time_steps(so, args.steps)
-    alt = {"precision": other, "dtype": DTYPES[other], "value": args.steps / (ms_o / 1e3),
-           "unit": UNIT, "steps": args.steps, "ms_per_step": ms_o / args.steps,
-           "cycles_per_step": cyc_o}
-    so.close()
+        # ---- the other mixed form, same workload, tolerance and settings ---
+        if other_leg:
+            other = "mixed_df" if precision == "mixed" else "mixed"
+            so = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                           precision=other, step_diagnostics=True, **mixed_kw)
+            for _ in range(warmup):
+                so.step(1)
+                so.diagnostics()
+            ms_o, cyc_o = time_steps(so, steps)
+            out["alt"] = {"precision": other, "dtype": DTYPES[other],
+                          "value": steps / (ms_o / 1e3), "unit": UNIT, "steps": steps,
+                          "ms_per_step": ms_o / steps, "cycles_per_step": cyc_o}
+            so.close()
+        return out
+
+    overrides = {k: getattr(args, k) for k in ("inner_cycles", "jacobi_factor", "nu1", "nu2")
+                 if getattr(args, k) is not None}
+    n = args.n
+    r = measure(n, args.steps, args.warmup, args.fp64_steps, overrides, args.precision)
+    wl, phi0, mixed_kw, value = r["wl"], r["phi0"], r["mixed_kw"], r["value"]
+    cells = n ** 3
 
     # ---- end to end through the C ABI with host buffers -------------------
     pin_a = torch.from_numpy(phi0.copy()).pin_memory()
@@ -516,18 +625,37 @@ def run_ours(args):
            "d2h_bytes_per_step": cells * 8 + 6 * 8}
     se.close()
 
+    # ---- 256^3: the second size of the target, its own legs and clocks ----
+    n256 = None
+    if args.n256 and n != 256:
+        r2 = measure(256, max(3, min(args.steps, 10)), args.warmup, 2, None, args.precision,
+                     other_leg=False)
+        n256 = {"workload": "smooth-mode 256^3", "value": r2["value"], "unit": UNIT,
+                "steps": max(3, min(args.steps, 10)), "ms_per_step": r2["t_max"] * 1e3 /
+                max(3, min(args.steps, 10)), "solver": r2["mixed_kw"],
+                "cycles_per_step": r2["cycles"], "dof_updates_per_s": r2["value"] * 256 ** 3,
+                "fp64": r2["fp64"], "mixed_over_fp64": r2["value"] / ws / r2["fp64"]["value"],
+                "roofline": r2["roofline"], "vcycle": r2["vcycle"],
+                "gpu_launches": r2["launches"], "clocks": r2["clocks"],
+                "kernel_profile_ms": r2["kernel_profile_ms"]}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_cpu, cyc_cpu = oracle_step_time(n)
-        cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"1 full oracle time step at {n}^3 from phi0 (start rule), "
-                         f"{cyc_cpu} V-cycles"}
+        orc = OracleSteps(n)
+        _, cyc_start = orc.step()                  # start step: untimed
+        t_cpu, cyc_cpu = orc.step()
+        cpu = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "host": host_cpu(),
+               "sample": f"oracle time step 2 at {n}^3 (warm: from step 1's solution, as the "
+                         f"GPU's timed steps are), {cyc_cpu} FAS V(2,2) cycles to the same "
+                         f"tolerance, energy/mass included (the untimed step 1, start rule, "
+                         f"took {cyc_start}); numpy elementwise on one thread"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "ms_per_step": r["t_max"] * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPES[args.precision],
             "data": "synthetic",
             "config": {"workload": f"smooth-mode {n}^3", "n": n, "L": wl.L, "eps": wl.eps,
@@ -535,23 +663,23 @@ def run_ours(args):
                        "solver": mixed_kw, "step_execution": "CUDA graph",
                        "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MiB write) before every timed step"},
-            "cycles_per_step": cycles,
+            "cycles_per_step": r["cycles"],
             "dof_updates_per_s": value * cells,
-            "fp64": fp64,
-            "mixed_over_fp64": value / ws / fp64["value"],
-            ("mixed_df" if args.precision == "mixed" else "mixed_fp64_outer"): alt,
-            "roofline": roofline,
-            "vcycle": vcyc,
+            "fp64": r["fp64"],
+            "mixed_over_fp64": value / ws / r["fp64"]["value"],
+            ("mixed_df" if args.precision == "mixed" else "mixed_fp64_outer"): r.get("alt"),
+            "roofline": r["roofline"],
+            "vcycle": r["vcycle"],
             "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
-            "kernel_profile_ms": {f"{k[0]}@{n >> k[1]}": round(v[1], 4)
-                                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
+            "kernel_profile_ms": r["kernel_profile_ms"],
         }
+        if n256 is not None:
+            line["n256"] = n256
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
-    s.close()
     if ws > 1:
         tdist.destroy_process_group()
 

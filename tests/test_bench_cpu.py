@@ -20,14 +20,21 @@ def test_reference_arm_prints_one_json_line():
     assert line["value"] > 0 and line["unit"] == "steps/s"
     assert line["config"]["workload"] == "smooth-mode 8^3"
     assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == 1 and "warm" in line["cpu_baseline"]["sample"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0
 
 
 def test_oracle_step_timer():
+    """The cpu_baseline leg: a start step, then a warm step from its solution
+    (the work of the GPU's timed steps), each converged to the tolerance."""
     sys.path.insert(0, ROOT)
     import bench
-    t, cycles = bench.oracle_step_time(8)
-    assert t > 0 and cycles >= 1
+    orc = bench.OracleSteps(8)
+    t0, c0 = orc.step()
+    t1, c1 = orc.step()
+    assert t0 > 0 and t1 > 0 and c0 >= 1 and c1 >= 1 and orc.k == 2
+    host = bench.host_cpu()
+    assert host["nproc"] >= 1 and host["model"]
 
 
 def test_vcycle_byte_model_matches_the_kernel_counts():
