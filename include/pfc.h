@@ -433,6 +433,50 @@ int pfc_batch_diagnostics(pfc_ctx* c, double* out);
 int pfc_batch_status(const pfc_ctx* c, int* iters, double* residual, double* residual0);
 
 /* ------------------------------------------------------------------------
+ * Groups of ensembles of different grid sizes.  The paper runs one grid at a
+ * time and has no counterpart; this serves ensembles whose runs have uneven
+ * grid sizes (and eps).  A group holds 1 .. PFC_MAX_GROUP contexts made by
+ * pfc_init or pfc_batch_init (typically one ensemble per grid size) and
+ * advances them together: one CUDA graph per time step forks into every
+ * context's pre-loop work (source, initial iterate, first residual), then
+ * one device-side WHILE loop runs, per iteration, the loop body (a V-cycle
+ * or a defect correction with its residual) of every context that still has
+ * a running member, side by side under one conditional (IF) node per
+ * context, until every member of every context has converged or one has
+ * failed.  A context whose members have all converged takes no further
+ * loop body, so each context ends the step exactly (bit for bit) as when
+ * stepped alone with pfc_step.  The group owns
+ * no device memory (the contexts' workspaces hold all state; its loop
+ * decision takes the contexts' state addresses as a kernel argument) and
+ * does not own the contexts: destroy the group before them.  Contexts must
+ * be on the current device; a context may belong to one group at a time.
+ * --------------------------------------------------------------------- */
+#define PFC_MAX_GROUP 16
+
+typedef struct pfc_group pfc_group;
+
+/* Make a group of `count` distinct contexts (host array ctxs) launching on
+ * `stream` (cudaStream_t, may be NULL).  PFC_EINVAL for count outside
+ * 1..PFC_MAX_GROUP, a NULL or repeated context. */
+int pfc_group_init(pfc_group** out, pfc_ctx* const* ctxs, int count, void* stream);
+
+/* Advance every context `nsteps` steps, one graph launch per step (the
+ * step graphs are built on first use for each combination of the contexts'
+ * ring positions).  Waits for work already enqueued on the contexts' own
+ * streams first; blocking.  stats (may be NULL): host array of `count`
+ * entries, as pfc_step's for each context.  If a context sets
+ * pfc_use_graphs(c, 0) or kernel timing, the contexts are stepped one after
+ * another instead (same results).  On PFC_ENOCONV or PFC_ENAN the step is
+ * kept for the contexts that converged and repeated by none: the contexts
+ * may then stand at different step indices (pfc_step_index). */
+int pfc_group_step(pfc_group* g, int nsteps, pfc_step_stats* stats);
+
+/* Graph launches made by pfc_group_step so far (one per group step). */
+long long pfc_group_graph_launches(const pfc_group* g);
+
+void pfc_group_destroy(pfc_group* g);
+
+/* ------------------------------------------------------------------------
  * Discrete adjoint of one time step (gradients through the scheme).  Step k
  * solves F(u; b, c, eps) = N(u; b) - S(b, c) = 0 for u = (phi^{k+1}, mu,
  * omega) (Eqs. 5.4-5.10); given dL/dphi^{k+1} = d_gnext, the implicit

@@ -108,6 +108,10 @@ _SIGS = {
     "pfc_adjoint_step": (_I, [_P, _P, _P, _P, _P, _P, _P, _D, _I, ctypes.POINTER(_D),
                               ctypes.POINTER(_I)]),
     "pfc_batch_diagnostics": (_I, [_P, ctypes.POINTER(_D)]),
+    "pfc_group_init": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P]),
+    "pfc_group_step": (_I, [_P, _I, ctypes.POINTER(pfc_step_stats)]),
+    "pfc_group_graph_launches": (ctypes.c_longlong, [_P]),
+    "pfc_group_destroy": (None, [_P]),
     "pfc_batch_status": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)]),
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_restrict_chain": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 16 + [_P]),
@@ -211,6 +215,32 @@ def pfc_batch_init(p: pfc_params, eps, workspace, phi0, stream=None) -> ctypes.c
                               workspace.numel() * workspace.element_size(), ptr(phi0), stream)
     check(rc, "pfc_batch_init")
     return ctx
+
+
+PFC_MAX_GROUP = 16
+
+
+def pfc_group_init(ctxs, stream=None) -> ctypes.c_void_p:
+    """A group of contexts advanced together (one graph launch per step)."""
+    arr = (_P * len(ctxs))(*[c.value if isinstance(c, ctypes.c_void_p) else c for c in ctxs])
+    g = ctypes.c_void_p()
+    check(lib().pfc_group_init(ctypes.byref(g), arr, len(ctxs), stream), "pfc_group_init")
+    return g
+
+
+def pfc_group_step(g, count: int, nsteps: int = 1) -> list:
+    """Advance the group; returns one pfc_step_stats per context."""
+    st = (pfc_step_stats * count)()
+    check(lib().pfc_group_step(g, nsteps, st), "pfc_group_step")
+    return list(st)
+
+
+def pfc_group_graph_launches(g) -> int:
+    return int(lib().pfc_group_graph_launches(g))
+
+
+def pfc_group_destroy(g) -> None:
+    lib().pfc_group_destroy(g)
 
 
 def pfc_adjoint_step(ctx, phi_next, phi_k, gnext, gk, gkm1, z, rtol=1e-10, max_cycles=50):

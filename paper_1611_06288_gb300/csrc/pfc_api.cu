@@ -7,6 +7,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "pfc_internal.h"
 #include "pfc_mixed.h"
 
@@ -159,6 +161,7 @@ struct pfc_ctx {
   pfc::StepState* dstate;  // device convergence state of the current step
   pfc::StepState* hstate;  // pinned host copy
   int use_graphs;    // run each step as one graph launch (default on)
+  int graph_gen;     // bumped whenever the step graphs are rebuilt (groups key on it)
   cudaStream_t cap_st;  // private stream the step graphs are captured on
   struct Graph {
     cudaGraphExec_t exec;
@@ -561,16 +564,52 @@ StepState combined_state(const pfc_ctx* c) {
   return s;
 }
 
-int step_once(pfc_ctx* c, pfc_step_stats* stats) {
-  Level64 lv;
-  level0(c, &lv);
-  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
-  int rc = PFC_OK;
-  // pointwise first defect: the state is the last step's solution (guess
-  // phi^{k+1} := phi^k) and lmu, lom hold its Laplacians
+// Start of a step: level-0 views of the current ring position; returns
+// whether the first defect is pointwise (the state is the last step's
+// solution, guess phi^{k+1} := phi^k, and lmu, lom hold its Laplacians).
+bool step_prepare(pfc_ctx* c, Level64* lv) {
+  level0(c, lv);
   const bool warm = c->warm && c->lmu && c->p.guess == PFC_GUESS_PREVIOUS;
   c->warm = 0;                       // until this step has converged
   c->diag_valid = 0;
+  return warm;
+}
+
+// End of a step whose device state (hstate) has been read back: the step's
+// outcome, stats, and on success the ring rotation.
+int step_finish(pfc_ctx* c, pfc_step_stats* stats) {
+  const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
+  int rc = PFC_OK;
+  const StepState s = combined_state(c);
+  if (s.status == kStepNaN) rc = PFC_ENAN;
+  else if (s.status == kStepNoConv) rc = PFC_ENOCONV;
+  else if (s.status != kStepConverged) rc = PFC_ECUDA;
+  if (stats) {
+    stats->cycles_last = s.iters;
+    stats->cycles_total += s.iters;
+    stats->residual = s.rms;
+    stats->residual0 = s.rms0;
+  }
+  if (rc == PFC_ENAN) {
+    cudaMemsetAsync(c->mu, 0, n3 * sizeof(double), c->st);
+    cudaMemsetAsync(c->om, 0, n3 * sizeof(double), c->st);
+  }
+  if (rc) return rc;
+  const int old_c = c->ic;
+  c->ic = c->ib;
+  c->ib = c->ia;
+  c->ia = old_c;
+  c->step += 1;
+  c->warm = c->lmu != nullptr;
+  c->diag_valid = c->p.step_diagnostics;
+  if (stats) stats->steps += 1;
+  return PFC_OK;
+}
+
+int step_once(pfc_ctx* c, pfc_step_stats* stats) {
+  Level64 lv;
+  const bool warm = step_prepare(c, &lv);
+  int rc = PFC_OK;
   if (c->use_graphs && c->prof.mask == 0) {
     pfc_ctx::Graph* g = &c->graph[warm ? 1 : 0][c->ia];
     if (!g->exec) {
@@ -597,30 +636,7 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
     }
     if (rc) return rc;
   }
-  const StepState s = combined_state(c);
-  if (s.status == kStepNaN) rc = PFC_ENAN;
-  else if (s.status == kStepNoConv) rc = PFC_ENOCONV;
-  else if (s.status != kStepConverged) rc = PFC_ECUDA;
-  if (stats) {
-    stats->cycles_last = s.iters;
-    stats->cycles_total += s.iters;
-    stats->residual = s.rms;
-    stats->residual0 = s.rms0;
-  }
-  if (rc == PFC_ENAN) {
-    cudaMemsetAsync(c->mu, 0, n3 * sizeof(double), c->st);
-    cudaMemsetAsync(c->om, 0, n3 * sizeof(double), c->st);
-  }
-  if (rc) return rc;
-  const int old_c = c->ic;
-  c->ic = c->ib;
-  c->ib = c->ia;
-  c->ia = old_c;
-  c->step += 1;
-  c->warm = c->lmu != nullptr;
-  c->diag_valid = c->p.step_diagnostics;
-  if (stats) stats->steps += 1;
-  return PFC_OK;
+  return step_finish(c, stats);
 }
 
 }  // namespace
@@ -862,6 +878,7 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
     const double scale = c->p.mobility_m0 + c->p.mobility_m2 * c->hout[1] / (double)n3;
     if (scale != c->tau_scale) {
       // the step graphs hold the FP32 level constants: rebuild them
+      c->graph_gen += 1;
       for (int v = 0; v < 2; ++v)
         for (int r = 0; r < 3; ++r)
           if (c->graph[v][r].exec) {
@@ -1076,6 +1093,310 @@ void pfc_destroy(pfc_ctx* c) {
   if (c->prof.created)
     for (int i = 0; i < 2 * Prof::kPool; ++i) cudaEventDestroy(c->prof.ev[i]);
   free(c);
+}
+
+// ---------------------------------------------------------------------------
+// Groups of contexts (ensembles of different grid sizes): one graph per step
+// ---------------------------------------------------------------------------
+
+struct pfc_group {
+  int count;
+  pfc_ctx* ctx[pfc::kMaxGroup];
+  cudaStream_t st;       // launch stream (the caller's)
+  cudaStream_t cap_st;   // private stream the step graphs are captured on
+  cudaEvent_t fork;
+  cudaEvent_t join[pfc::kMaxGroup];
+  cudaEvent_t ready[pfc::kMaxGroup];
+  struct Graph {
+    // (first defect pointwise, ring position, graph generation) per context
+    int key[3 * pfc::kMaxGroup];
+    cudaGraphExec_t exec;
+    long long pre[pfc::kMaxGroup], body[pfc::kMaxGroup];
+  };
+  std::vector<Graph> graphs;
+  long long graph_launches;
+};
+
+namespace pfc {
+namespace {
+
+// Fork: every context's capture stream takes the group capture stream's
+// current dependencies.  Join: the group stream waits for all of them.
+cudaError_t group_fork(pfc_group* g) {
+  cudaError_t e = cudaEventRecord(g->fork, g->cap_st);
+  for (int i = 0; i < g->count && e == cudaSuccess; ++i)
+    e = cudaStreamWaitEvent(g->ctx[i]->cap_st, g->fork, 0);
+  return e;
+}
+
+cudaError_t group_join(pfc_group* g) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < g->count && e == cudaSuccess; ++i) {
+    e = cudaEventRecord(g->join[i], g->ctx[i]->cap_st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(g->cap_st, g->join[i], 0);
+  }
+  return e;
+}
+
+// The graph of one group step: every context's pre-loop work side by side,
+// the group decision, a WHILE node whose body sets one IF condition per
+// context (it still has a running member), runs each context's loop body
+// under its IF node side by side and then the group decision, and after the
+// loop every context's state readback (and diagnostics).  Each context's own
+// decision keeps its members' states; only the group kernels set
+// conditions.  A converged context takes no further correction, so every
+// context ends the step exactly as if it had been stepped alone.
+int group_build(pfc_group* g, const bool* warm, const Level64* lv, pfc_group::Graph* gr) {
+  cudaGraph_t G = nullptr;
+  PFC_CUDA(cudaGraphCreate(&G, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, G, 0, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess)
+    e = cudaStreamBeginCaptureToGraph(g->cap_st, G, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(G);
+    return cuda_fail(e, "group graph setup");
+  }
+  GroupStates gs = {};
+  gs.count = g->count;
+  cudaStream_t saved[kMaxGroup];
+  for (int i = 0; i < g->count; ++i) {
+    gs.s[i] = g->ctx[i]->dstate;
+    gs.members[i] = g->ctx[i]->nb;
+    saved[i] = g->ctx[i]->st;
+    g->ctx[i]->st = g->ctx[i]->cap_st;
+  }
+  int rc = PFC_OK;
+  e = group_fork(g);
+  for (int i = 0; i < g->count && rc == PFC_OK && e == cudaSuccess; ++i) {
+    pfc_ctx* c = g->ctx[i];
+    const long long l0 = c->prof.launches;
+    rc = enqueue_pre(c, lv[i], h, 0, warm[i]);
+    gr->pre[i] = c->prof.launches - l0;
+  }
+  if (rc == PFC_OK && e == cudaSuccess) e = group_join(g);
+  if (rc == PFC_OK && e == cudaSuccess) e = launch_group_decide(h, gs, g->cap_st);
+  cudaGraphNodeParams cp = {};
+  if (rc == PFC_OK && e == cudaSuccess) {
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraphNode_t cnode;
+    e = cudaStreamGetCaptureInfo(g->cap_st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = h;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cnode, G, deps, nullptr, ndeps, &cp);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(g->cap_st, &cnode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) e = group_fork(g);
+    for (int i = 0; i < g->count && e == cudaSuccess; ++i) {
+      pfc_ctx* c = g->ctx[i];
+      e = cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState) * c->nb,
+                          cudaMemcpyDeviceToHost, c->st);
+      if (e == cudaSuccess && c->p.step_diagnostics) {
+        e = enqueue_diagnostics(c->p.n, c->nb, c->ring[c->ia], c->ring[c->ib], c->lap[c->ia],
+                                c->lap[c->ib], df_state(&c->p), c->partials, c->dout,
+                                c->hdiag, c->st, c->prof.mask == 0);
+        gr->pre[i] += 2;
+      }
+    }
+    if (e == cudaSuccess) e = group_join(g);
+  }
+  cudaGraph_t cap = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(g->cap_st, &cap);
+  if (rc == PFC_OK && e == cudaSuccess) e = e2;
+  if (rc == PFC_OK && e == cudaSuccess) {
+    // loop body: the IF conditions, then per context an IF node holding its
+    // loop body (captured on the context's stream into the node's graph),
+    // then the group decision after all of them
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    GroupHandles hs = {};
+    for (int i = 0; i < g->count && e == cudaSuccess; ++i)
+      e = cudaGraphConditionalHandleCreate(&hs.h[i], body, 0, 0);
+    cudaGraphNode_t sel = nullptr;
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(g->cap_st, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = launch_group_select(hs, gs, g->cap_st);
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t ndeps = 0;
+      if (e == cudaSuccess)
+        e = cudaStreamGetCaptureInfo(g->cap_st, &cs, nullptr, nullptr, &deps, nullptr, &ndeps);
+      if (e == cudaSuccess && ndeps == 1) sel = deps[0];
+      cudaGraph_t scap = nullptr;
+      e2 = cudaStreamEndCapture(g->cap_st, &scap);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess && !sel) e = cudaErrorStreamCaptureInvalidated;
+    }
+    cudaGraphNode_t ifs[kMaxGroup];
+    for (int i = 0; i < g->count && rc == PFC_OK && e == cudaSuccess; ++i) {
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = hs.h[i];
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      e = cudaGraphAddNode(&ifs[i], body, &sel, nullptr, 1, &ip);
+      pfc_ctx* c = g->ctx[i];
+      if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(c->st, ip.conditional.phGraph_out[0], nullptr,
+                                          nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const long long l0 = c->prof.launches;
+        rc = enqueue_body(c, lv[i], h, 0);
+        gr->body[i] = c->prof.launches - l0;
+        cudaGraph_t icap = nullptr;
+        e2 = cudaStreamEndCapture(c->st, &icap);
+        if (e == cudaSuccess) e = e2;
+      }
+    }
+    if (rc == PFC_OK && e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(g->cap_st, body, ifs, nullptr, g->count,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (rc == PFC_OK && e == cudaSuccess) {
+      e = launch_group_decide(h, gs, g->cap_st);
+      cudaGraph_t dcap = nullptr;
+      e2 = cudaStreamEndCapture(g->cap_st, &dcap);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  for (int i = 0; i < g->count; ++i) g->ctx[i]->st = saved[i];
+  if (rc == PFC_OK && e == cudaSuccess) e = cudaGraphInstantiate(&gr->exec, G, 0);
+  cudaGraphDestroy(G);
+  if (rc) return rc;
+  if (e != cudaSuccess) {
+    gr->exec = nullptr;
+    return cuda_fail(e, "group graph build");
+  }
+  return PFC_OK;
+}
+
+int group_step_once(pfc_group* g, pfc_step_stats* stats) {
+  bool graphs = true;
+  for (int i = 0; i < g->count; ++i)
+    if (!g->ctx[i]->use_graphs || g->ctx[i]->prof.mask != 0) graphs = false;
+  if (!graphs) {
+    // host-driven or timed contexts: one after another
+    int first = PFC_OK;
+    for (int i = 0; i < g->count; ++i) {
+      const int rc = step_once(g->ctx[i], stats ? &stats[i] : nullptr);
+      if (rc && first == PFC_OK) first = rc;
+    }
+    return first;
+  }
+  Level64 lv[kMaxGroup];
+  bool warm[kMaxGroup];
+  int key[3 * kMaxGroup] = {0};
+  for (int i = 0; i < g->count; ++i) {
+    warm[i] = step_prepare(g->ctx[i], &lv[i]);
+    key[3 * i] = warm[i] ? 1 : 0;
+    key[3 * i + 1] = g->ctx[i]->ia;
+    key[3 * i + 2] = g->ctx[i]->graph_gen;
+  }
+  pfc_group::Graph* gr = nullptr;
+  for (auto& x : g->graphs)
+    if (memcmp(x.key, key, sizeof(key)) == 0) gr = &x;
+  if (!gr) {
+    pfc_group::Graph ng = {};
+    memcpy(ng.key, key, sizeof(key));
+    const int rc = group_build(g, warm, lv, &ng);
+    if (rc) return rc;
+    g->graphs.push_back(ng);
+    gr = &g->graphs.back();
+  }
+  // after the work already enqueued on the contexts' own streams
+  for (int i = 0; i < g->count; ++i) {
+    PFC_CUDA(cudaEventRecord(g->ready[i], g->ctx[i]->st));
+    PFC_CUDA(cudaStreamWaitEvent(g->st, g->ready[i], 0));
+  }
+  PFC_CUDA(cudaGraphLaunch(gr->exec, g->st));
+  g->graph_launches += 1;
+  PFC_CUDA(cudaStreamSynchronize(g->st));
+  // the loop ran as many iterations as the slowest context needed
+  int loop = 0;
+  bool failed = false;
+  for (int i = 0; i < g->count; ++i) {
+    const StepState s = combined_state(g->ctx[i]);
+    if (s.iters > loop) loop = s.iters;
+    failed = failed || s.status == kStepNaN || s.status == kStepNoConv;
+  }
+  g->ctx[0]->prof.launches += 1 + 2 * loop;  // the group decisions and IF selections
+  int first = PFC_OK;
+  for (int i = 0; i < g->count; ++i) {
+    pfc_ctx* c = g->ctx[i];
+    // a context's body ran while it had a running member
+    c->prof.launches += gr->pre[i] + gr->body[i] * (long long)combined_state(c).iters;
+    // a context still running when another failed takes no step
+    if (failed && combined_state(c).status == kStepRunning) continue;
+    const int rc = step_finish(c, stats ? &stats[i] : nullptr);
+    if (rc && first == PFC_OK) first = rc;
+  }
+  return first;
+}
+
+}  // namespace
+}  // namespace pfc
+
+int pfc_group_init(pfc_group** out, pfc_ctx* const* ctxs, int count, void* stream) {
+  if (!out || !ctxs || count < 1 || count > kMaxGroup) return PFC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return PFC_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return PFC_EINVAL;
+  }
+  pfc_group* g = new pfc_group();
+  g->count = count;
+  g->st = (cudaStream_t)stream;
+  g->graph_launches = 0;
+  for (int i = 0; i < count; ++i) g->ctx[i] = ctxs[i];
+  cudaError_t e = cudaStreamCreateWithFlags(&g->cap_st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming);
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    e = cudaEventCreateWithFlags(&g->join[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g->ready[i], cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctxs[i]->cap_st)
+      e = cudaStreamCreateWithFlags(&ctxs[i]->cap_st, cudaStreamNonBlocking);
+  }
+  if (e != cudaSuccess) {
+    pfc_group_destroy(g);
+    return cuda_fail(e, "pfc_group_init");
+  }
+  *out = g;
+  return PFC_OK;
+}
+
+int pfc_group_step(pfc_group* g, int nsteps, pfc_step_stats* stats) {
+  if (!g || nsteps < 0) return PFC_EINVAL;
+  if (stats) memset(stats, 0, sizeof(*stats) * g->count);
+  for (int s = 0; s < nsteps; ++s) {
+    const int rc = group_step_once(g, stats);
+    if (rc) return rc;
+  }
+  return PFC_OK;
+}
+
+long long pfc_group_graph_launches(const pfc_group* g) { return g ? g->graph_launches : -1; }
+
+void pfc_group_destroy(pfc_group* g) {
+  if (!g) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  for (auto& x : g->graphs)
+    if (x.exec) cudaGraphExecDestroy(x.exec);
+  if (g->cap_st) cudaStreamDestroy(g->cap_st);
+  if (g->fork) cudaEventDestroy(g->fork);
+  for (int i = 0; i < g->count; ++i) {
+    if (g->join[i]) cudaEventDestroy(g->join[i]);
+    if (g->ready[i]) cudaEventDestroy(g->ready[i]);
+  }
+  delete g;
 }
 
 const char* pfc_strerror(int code) {

@@ -568,6 +568,32 @@ __global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
     cudaGraphSetConditional(handle, (running && !failed) ? 1u : 0u);
 }
 
+// The loop condition of a group of contexts: every member of every context
+// (states written by the contexts' own k_decide) is read once.
+__global__ void k_group_decide(cudaGraphConditionalHandle handle, GroupStates g) {
+  int running = 0, failed = 0;
+  for (int c = 0; c < g.count; ++c)
+    for (int m = threadIdx.x; m < g.members[c]; m += blockDim.x) {
+      const int status = g.s[c][m].status;
+      running |= status == kStepRunning;
+      failed |= status == kStepNaN || status == kStepNoConv;
+    }
+  running = __syncthreads_or(running);
+  failed = __syncthreads_or(failed);
+  if (threadIdx.x == 0) cudaGraphSetConditional(handle, (running && !failed) ? 1u : 0u);
+}
+
+// The loop body of each context of a group runs only while that context
+// has a running member: one warp per context sets its IF condition.
+__global__ void k_group_select(GroupHandles hs, GroupStates g) {
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c >= g.count) return;
+  int running = 0;
+  for (int m = lane; m < g.members[c]; m += 32) running |= g.s[c][m].status == kStepRunning;
+  running = __any_sync(0xffffffffu, running);
+  if (lane == 0) cudaGraphSetConditional(hs.h[c], running ? 1u : 0u);
+}
+
 inline int reduce_blocks(int64_t cells) {
   const int64_t nb = (cells + kReduceThreads - 1) / kReduceThreads;
   return (int)(nb < kReduceBlocks ? nb : kReduceBlocks);
@@ -749,6 +775,18 @@ cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
   const int threads = ((members + 31) / 32) * 32;
   return launch_ex(pdl, k_decide, dim3(1), dim3(threads), 0, st, handle, use_handle, sum, state,
                    members, inv_3n3, tol, max_iter, first);
+}
+
+cudaError_t launch_group_select(const GroupHandles& hs, const GroupStates& g,
+                                cudaStream_t st) {
+  k_group_select<<<1, 32 * kMaxGroup, 0, st>>>(hs, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_group_decide(cudaGraphConditionalHandle handle, const GroupStates& g,
+                                cudaStream_t st) {
+  k_group_decide<<<1, 256, 0, st>>>(handle, g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,

@@ -46,6 +46,29 @@ cudaError_t launch_decide(cudaGraphConditionalHandle handle, int use_handle,
                           int max_iter, int first, cudaStream_t st, int members = 1,
                           bool pdl = false);
 
+// Convergence states of the contexts of a group (pfc_group_*), passed to the
+// group decision by value: no device memory beyond the contexts' own.
+constexpr int kMaxGroup = PFC_MAX_GROUP;
+struct GroupStates {
+  const StepState* s[kMaxGroup];
+  int members[kMaxGroup];
+  int count;
+};
+
+// Set, per context of a group, the IF condition of its loop body: the
+// context still has a running member (and no member of any context failed).
+struct GroupHandles {
+  cudaGraphConditionalHandle h[kMaxGroup];
+};
+cudaError_t launch_group_select(const GroupHandles& hs, const GroupStates& g,
+                                cudaStream_t st);
+
+// Set the WHILE condition of a group's step graph: "keep going" while some
+// member of some context runs and no member of any context has failed (the
+// per-context states are those the contexts' own decisions wrote).
+cudaError_t launch_group_decide(cudaGraphConditionalHandle handle, const GroupStates& g,
+                                cudaStream_t st);
+
 // Detail string returned by pfc_last_error() on this host thread.
 void set_last_error(const char* msg);
 

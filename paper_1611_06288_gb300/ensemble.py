@@ -1,7 +1,8 @@
 """Batched ensemble run (the ensemble workload: independent runs with grids
 drawn from {32^3, 48^3, 64^3}, their own eps and initial fields, dt = 0.05,
-100 steps each), advanced one PFCBatch per grid size, against the same runs
-made one after another through single contexts.
+100 steps each): one PFCBatch per grid size, all of them advanced together by
+one PFCGroup (one CUDA graph launch per time step for every run), against the
+same runs made one after another through single contexts.
 
     python -m paper_1611_06288_gb300.ensemble [--count 96] [--steps 100] [--sequential]
                                               [--autotune] [--cluster-tail]
@@ -18,7 +19,8 @@ import json
 import torch
 
 from . import workloads as W
-from .solver import PFCBatch, PFCSolver
+from . import binding as B
+from .solver import PFCBatch, PFCGroup, PFCSolver
 
 
 def _timed(fn):
@@ -44,29 +46,47 @@ def run(count=96, steps=100, sequential=False, L=32.0, dt=0.05, tol=1e-9, warmup
     out = {"count": count, "steps": steps, "L": L, "dt": dt, "tol": tol,
            "cluster_tail": bool(cluster_tail),
            "groups": {n: len(e) for n, (e, _) in groups.items()}, "settings": W.ENSEMBLE_SETTINGS}
-    total = 0.0
-    per_group = {}
+    batches = {}
     for n, (eps, phi0) in groups.items():
         gkw = dict(kw, **tuned.get(n, {}))
-        b = PFCBatch(n, L, eps, dt, phi0, **gkw)
-        b.step(warmup)                      # builds the step graphs
-        b.close()
-        b = PFCBatch(n, L, eps, dt, phi0, **gkw)
+        batches[n] = (PFCBatch(n, L, eps, dt, phi0, **gkw),
+                      torch.as_tensor(phi0, dtype=torch.float64, device="cuda").contiguous())
+    grp = PFCGroup([b for b, _ in batches.values()])
 
-        def go():
-            cyc = 0
-            for _ in range(steps):
-                cyc += b.step(1).cycles_last
-            return cyc
+    def restart():
+        for b, p0 in batches.values():
+            B.pfc_set_state(b.ctx, p0)
+        torch.cuda.synchronize()
 
-        t, cyc = _timed(go)
+    # warm-up: every step graph the timed run meets (a first step at each of
+    # the three ring positions, then warm steps at each) is built here
+    for _ in range(3):
+        grp.step(1)
+        restart()
+    grp.step(max(3, warmup))
+    restart()
+    launches0 = grp.graph_launches
+
+    def go():
+        cyc = [0] * len(batches)
+        for _ in range(steps):
+            for i, st in enumerate(grp.step(1)):
+                cyc[i] += st.cycles_last
+        return cyc
+
+    total, cyc = _timed(go)
+    per_group = {}
+    for (n, (b, _)), c in zip(batches.items(), cyc):
         _, res, _ = b.status()
-        per_group[n] = {"members": len(eps), "seconds": t, "corrections_per_step": cyc / steps,
-                        "max_final_residual": max(res), "settings": tuned.get(n, W.ENSEMBLE_SETTINGS)}
-        total += t
-        b.close()
+        per_group[n] = {"members": b.members, "corrections_per_step": c / steps,
+                        "max_final_residual": max(res),
+                        "settings": tuned.get(n, W.ENSEMBLE_SETTINGS)}
     out["batched"] = {"member_steps_per_s": count * steps / total, "seconds": total,
+                      "graph_launches_per_step": (grp.graph_launches - launches0) / steps,
                       "per_group": per_group}
+    grp.close()
+    for b, _ in batches.values():
+        b.close()
     if sequential:
         tot = 0.0
         for n, (eps, phi0) in groups.items():

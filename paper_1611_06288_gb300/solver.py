@@ -234,3 +234,37 @@ class PFCBatch:
             self.close()
         except Exception:
             pass
+
+
+class PFCGroup:
+    """Ensembles of different grid sizes (PFCBatch or PFCSolver objects)
+    advanced together: one CUDA graph launch per time step runs every
+    context's step side by side under one device-side convergence loop.
+    The group does not own the contexts; close it before them."""
+
+    def __init__(self, contexts, stream=None):
+        self.contexts = list(contexts)
+        if not self.contexts:
+            raise ValueError("a group needs at least one context")
+        dev = self.contexts[0].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self.g = B.pfc_group_init([c.ctx for c in self.contexts], self.stream.cuda_stream)
+
+    def step(self, nsteps: int = 1) -> list:
+        """One pfc_step_stats per context."""
+        return B.pfc_group_step(self.g, len(self.contexts), nsteps)
+
+    @property
+    def graph_launches(self) -> int:
+        return B.pfc_group_graph_launches(self.g)
+
+    def close(self) -> None:
+        if getattr(self, "g", None) is not None:
+            B.pfc_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -190,3 +190,22 @@ def test_defect_planes_param(libpfc):
         assert B.pfc_workspace_bytes(p) == base > 0
     p.defect_planes = -1
     assert B.pfc_workspace_bytes(p) == 0
+
+
+def test_group_init_checks_its_arguments(libpfc):
+    """pfc_group_init refuses a count outside 1..PFC_MAX_GROUP, a NULL
+    context and a repeated context before it touches the device."""
+    out = ctypes.c_void_p()
+    fake = [ctypes.c_void_p(4096), ctypes.c_void_p(8192)]
+
+    def init(ptrs, count):
+        arr = (ctypes.c_void_p * max(1, len(ptrs)))(*ptrs)
+        return libpfc.pfc_group_init(ctypes.byref(out), arr, count, None)
+
+    assert init([], 0) == B.PFC_EINVAL
+    assert init(fake, B.PFC_MAX_GROUP + 1) == B.PFC_EINVAL
+    assert init([fake[0], None], 2) == B.PFC_EINVAL
+    assert init([fake[0], fake[0]], 2) == B.PFC_EINVAL
+    assert libpfc.pfc_group_step(None, 1, None) == B.PFC_EINVAL
+    assert libpfc.pfc_group_graph_launches(None) == -1
+    libpfc.pfc_group_destroy(None)
