@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-n256", dest="n256", action="store_false",
                     help="skip the 256^3 legs (the n256 object)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false",
+                    help="skip the ensemble and gradient workloads")
     # the headline path: FP64 defect correction around FP32 multigrid; the
     # double-float form is timed beside it
     ap.add_argument("--precision", default="mixed", choices=["mixed", "mixed_df"])
@@ -639,6 +641,28 @@ def run_ours(args):
                 "gpu_launches": r2["launches"], "clocks": r2["clocks"],
                 "kernel_profile_ms": r2["kernel_profile_ms"]}
 
+    # ---- the ensemble and gradient workloads (secondary lines) -------------
+    extras = {}
+    if args.extras:
+        from paper_1611_06288_gb300 import ensemble as EN
+        from paper_1611_06288_gb300 import gradcheck as GC
+        ens = EN.run()
+        extras["ensemble"] = {
+            "workload": "96 independent runs, grids drawn from {32,48,64}^3, eps ~ U[0.02,0.3], "
+                        "mean phi ~ U[-0.3,0.1] + 0.05 U(-1,1), dt = 0.05, 100 steps each, "
+                        "tol 1e-9, one PFCGroup of three ensembles",
+            "member_steps_per_s": ens["batched"]["member_steps_per_s"],
+            "seconds": ens["batched"]["seconds"],
+            "graph_launches_per_step": ens["batched"]["graph_launches_per_step"],
+            "groups": ens["groups"],
+            "corrections_per_step": {k: v["corrections_per_step"]
+                                     for k, v in ens["batched"]["per_group"].items()},
+            "max_final_residual": max(v["max_final_residual"]
+                                      for v in ens["batched"]["per_group"].values())}
+        extras["gradient"] = dict(GC.run(), workload="64^3, L = 32, dt = 0.05, 200 steps, "
+                                  "checkpoints every 20, target from eps = 0.1, gradient at "
+                                  "eps = 0.15, central differences with step 1e-6")
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         orc = OracleSteps(n)
@@ -677,6 +701,7 @@ def run_ours(args):
         }
         if n256 is not None:
             line["n256"] = n256
+        line.update(extras)
         if cpu is not None:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
