@@ -100,6 +100,9 @@ def parse():
     ap.add_argument("--jacobi-factor", type=int, default=None)
     ap.add_argument("--nu1", type=int, default=None)
     ap.add_argument("--nu2", type=int, default=None)
+    ap.add_argument("--coarse-sweeps", type=int, default=None)
+    ap.add_argument("--guess", default=None, choices=["previous", "extrapolate"],
+                    help="initial iterate of a step (default: the previous step's solution)")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-n256", dest="n256", action="store_false",
@@ -592,7 +595,8 @@ def run_ours(args):
             so.close()
         return out
 
-    overrides = {k: getattr(args, k) for k in ("inner_cycles", "jacobi_factor", "nu1", "nu2")
+    overrides = {k: getattr(args, k) for k in ("inner_cycles", "jacobi_factor", "nu1", "nu2",
+                                                "coarse_sweeps", "guess")
                  if getattr(args, k) is not None}
     n = args.n
     r = measure(n, args.steps, args.warmup, args.fp64_steps, overrides, args.precision)

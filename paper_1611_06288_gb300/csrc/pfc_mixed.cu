@@ -1784,6 +1784,43 @@ struct Walk {
   }
 };
 
+// Colour walker of a red-black pass (n even, n^2/2 <= blockDim): thread ->
+// (p, j, k0) over the n/2 cells of one colour in each x-row; k advances by
+// kstep and the cell's x index i = 2p + ((j + k + colour) & 1) follows the
+// colour, so every thread has cells of the colour in every pass (a column
+// walker leaves idle the half of the threads whose column has the other
+// parity, since its k-walk keeps one parity).
+struct CWalk {
+  int n, p, j, k0, kstep, jm, jp;
+  __device__ __forceinline__ CWalk(int n_) : n(n_) {
+    const int half = n >> 1, hplane = half * n;
+    kstep = blockDim.x / hplane;
+    if (kstep > n) kstep = n;
+    const int tid = threadIdx.x;
+    k0 = tid / hplane;
+    const int rem = tid - k0 * hplane;
+    j = rem / half;
+    p = rem - j * half;
+    if (k0 >= kstep) k0 = n;                     // no cell for this thread
+    jm = (j == 0) ? n - 1 : j - 1;
+    jp = (j + 1 == n) ? 0 : j + 1;
+  }
+  __device__ __forceinline__ void at(int k, int colour, int& c, int& xm, int& xp, int& ym,
+                                     int& yp, int& zm, int& zp) const {
+    const int i = 2 * p + ((j + k + colour) & 1);
+    const int im = (i == 0) ? n - 1 : i - 1, ip = (i + 1 == n) ? 0 : i + 1;
+    const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+    const int row = n * (j + n * k);
+    c = row + i;
+    xm = row + im;
+    xp = row + ip;
+    ym = n * (jm + n * k) + i;
+    yp = n * (jp + n * k) + i;
+    zm = n * (j + n * km) + i;
+    zp = n * (j + n * kp) + i;
+  }
+};
+
 __device__ __forceinline__ float nb6(const float* v, int xm, int xp, int ym, int yp, int zm,
                                      int zp) {
   return ((v[xm] + v[xp]) + (v[ym] + v[yp])) + (v[zm] + v[zp]);
@@ -1837,25 +1874,23 @@ __device__ void tail_smooth(const LvlF& L, int kind, SLev S, int sweeps, int jfa
     }
     return;
   }
+  const CWalk CW(L.n);
   for (int s = 0; s < sweeps; ++s) {
     for (int colour = 0; colour < 2; ++colour) {
       const bool z = zero && s == 0 && colour == 0;
-      if (W.active) {
-        for (int k = W.k0; k < L.n; k += W.kstep) {
-          if (((W.i + W.j + k) & 1) != colour) continue;
-          W.at(k, c, xm, xp, ym, yp, zm, zp);
-          float sp = 0.f, sm_ = 0.f, sw = 0.f;
-          if (!z) {
-            sp = nb6(S.d0, xm, xp, ym, yp, zm, zp);
-            sm_ = nb6(S.d1, xm, xp, ym, yp, zm, zp);
-            sw = nb6(S.d2, xm, xp, ym, yp, zm, zp);
-          }
-          float dp, dm, dw;
-          lin_point(L, sp, sm_, sw, S.q[c], S.r0[c], S.r1[c], S.r2[c], dp, dm, dw);
-          S.d0[c] = dp;
-          S.d1[c] = dm;
-          S.d2[c] = dw;
+      for (int k = CW.k0; k < L.n; k += CW.kstep) {
+        CW.at(k, colour, c, xm, xp, ym, yp, zm, zp);
+        float sp = 0.f, sm_ = 0.f, sw = 0.f;
+        if (!z) {
+          sp = nb6(S.d0, xm, xp, ym, yp, zm, zp);
+          sm_ = nb6(S.d1, xm, xp, ym, yp, zm, zp);
+          sw = nb6(S.d2, xm, xp, ym, yp, zm, zp);
         }
+        float dp, dm, dw;
+        lin_point(L, sp, sm_, sw, S.q[c], S.r0[c], S.r1[c], S.r2[c], dp, dm, dw);
+        S.d0[c] = dp;
+        S.d1[c] = dm;
+        S.d2[c] = dw;
       }
       __syncthreads();
     }
@@ -1935,6 +1970,7 @@ __device__ void tail_coarse(const LvlF& L, int kind, SLev S, float w, int max_sw
   }
   __syncthreads();
   const Walk W(n);
+  const CWalk CW(n);
   int c, xm, xp, ym, yp, zm, zp;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     float change = 0.f, size = 0.f;
@@ -1963,21 +1999,18 @@ __device__ void tail_coarse(const LvlF& L, int kind, SLev S, float w, int max_sw
       __syncthreads();
     } else {
       for (int colour = 0; colour < 2; ++colour) {
-        if (W.active) {
-          for (int k = W.k0; k < n; k += W.kstep) {
-            if (((W.i + W.j + k) & 1) != colour) continue;
-            W.at(k, c, xm, xp, ym, yp, zm, zp);
-            float dp, dm, dw;
-            lin_point(L, nb6(S.d0, xm, xp, ym, yp, zm, zp), nb6(S.d1, xm, xp, ym, yp, zm, zp),
-                      nb6(S.d2, xm, xp, ym, yp, zm, zp), S.q[c], S.r0[c], S.r1[c], S.r2[c],
-                      dp, dm, dw);
-            change = fmaxf(change, fmaxf(fabsf(dp - S.d0[c]),
-                                         fmaxf(fabsf(dm - S.d1[c]), fabsf(dw - S.d2[c]))));
-            size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
-            S.d0[c] = dp;
-            S.d1[c] = dm;
-            S.d2[c] = dw;
-          }
+        for (int k = CW.k0; k < n; k += CW.kstep) {
+          CW.at(k, colour, c, xm, xp, ym, yp, zm, zp);
+          float dp, dm, dw;
+          lin_point(L, nb6(S.d0, xm, xp, ym, yp, zm, zp), nb6(S.d1, xm, xp, ym, yp, zm, zp),
+                    nb6(S.d2, xm, xp, ym, yp, zm, zp), S.q[c], S.r0[c], S.r1[c], S.r2[c],
+                    dp, dm, dw);
+          change = fmaxf(change, fmaxf(fabsf(dp - S.d0[c]),
+                                       fmaxf(fabsf(dm - S.d1[c]), fabsf(dw - S.d2[c]))));
+          size = fmaxf(size, fmaxf(fabsf(dp), fmaxf(fabsf(dm), fabsf(dw))));
+          S.d0[c] = dp;
+          S.d1[c] = dm;
+          S.d2[c] = dw;
         }
         __syncthreads();
       }
@@ -2076,18 +2109,43 @@ __global__ void __launch_bounds__(kTailThreads) k_lin_tail32(TailParams P) {
     const SLev S0 = slev(smem, P, 0);
     const int n0 = P.L[0].n;
     const int cells = n0 * n0 * n0;
-    for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-      int p, j, k, colour;
-      split_cell(t, n0, p, j, k, colour);
-      const int o = (2 * p + ((j + k + colour) & 1)) + n0 * (j + n0 * k);   // natural index
-      S0.r0[o] = gr0[t];
-      S0.r1[o] = gr1[t];
-      S0.r2[o] = gr2[t];
-      S0.q[o] = gq[t];
-      if (!zero_top) {
-        S0.d0[o] = gd0[t];
-        S0.d1[o] = gd1[t];
-        S0.d2[o] = gd2[t];
+    // all of a thread's global loads of a batch before any shared-memory
+    // store: one memory round trip per batch instead of one per value
+    constexpr int kB = 4;
+    for (int t0 = threadIdx.x; t0 < cells; t0 += kB * blockDim.x) {
+      float v[7][kB];
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < cells) {
+          v[0][u] = gr0[t];
+          v[1][u] = gr1[t];
+          v[2][u] = gr2[t];
+          v[3][u] = gq[t];
+          if (!zero_top) {
+            v[4][u] = gd0[t];
+            v[5][u] = gd1[t];
+            v[6][u] = gd2[t];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kB; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < cells) {
+          int p, j, k, colour;
+          split_cell(t, n0, p, j, k, colour);
+          const int o = (2 * p + ((j + k + colour) & 1)) + n0 * (j + n0 * k);   // natural index
+          S0.r0[o] = v[0][u];
+          S0.r1[o] = v[1][u];
+          S0.r2[o] = v[2][u];
+          S0.q[o] = v[3][u];
+          if (!zero_top) {
+            S0.d0[o] = v[4][u];
+            S0.d1[o] = v[5][u];
+            S0.d2[o] = v[6][u];
+          }
+        }
       }
     }
     __syncthreads();
