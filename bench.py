@@ -64,9 +64,9 @@ KERNEL_BYTES = {
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
 # The defect class of the mixed path averages a step's launches: two full
-# defects (150.2 MB each) and one pointwise first defect (158.7 MB).
+# defects (150.0 MB each) and one pointwise first defect (158.1 MB).
 # Keyed by the finest level's size the capture ran at (other sizes: null).
-NCU_TRAFFIC = {("mixed", "defect", 128): 153.0e6}   # profiles/k_defect64_fx_128.md, k_defect64_point_128.md
+NCU_TRAFFIC = {("mixed", "defect", 128): 152.7e6}   # profiles/k_defect64_fx_128.md, k_defect64_point_128.md
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
 # counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
