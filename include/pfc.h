@@ -634,6 +634,17 @@ int pfc_op_lin_restrict_chain(int n, double h, double eps, double tau, int zero_
                               float* d_c3, float* d_e1, float* d_e2, float* d_e3,
                               float* d_g1, float* d_g2, float* d_g3, void* stream);
 
+/* The FP32 Newton coefficient q (colour-split, n^3) averaged over 8 children
+ * (the coarse-level operators of the correction solve, Section 5 transfers
+ * of the FAS reading) down `levels` (1..3) levels in one launch: d_c =
+ * (n/2)^3, d_e = (n/4)^3, d_g = (n/8)^3, colour-split; each average sums the
+ * children in the order (x, then y, then z fastest-first) of the single-level
+ * restriction, so every level equals the separate restrictions bit for bit.
+ * n a multiple of 32 for levels >= 2 (n even for levels = 1); d_e, d_g may be
+ * NULL when not produced. */
+int pfc_op_restrict_q(int n, int levels, const float* d_q, float* d_c, float* d_e,
+                      float* d_g, void* stream);
+
 /* d += P e, P the trilinear cell-centred prolongation (weights 27, 9, 3, 1
  * over 64) from the colour-split (n/2)^3 fields d_e1..3 to the colour-split
  * n^3 fields d_d1..3; n divisible by 4.  `assign` holds flags:

@@ -116,6 +116,7 @@ _SIGS = {
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_restrict_chain": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 16 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
+    "pfc_op_restrict_q": (_I, [_I, _I] + [_P] * 4 + [_P]),
     "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_guess_df": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_round_f32": (_I, [ctypes.c_longlong, _P, _P, _P]),
@@ -479,6 +480,11 @@ def pfc_op_lin_residual_restrict(n, h, eps, tau, zero_init, d1, d2, d3, r1, r2, 
                                              ptr(d2), ptr(d3), ptr(r1), ptr(r2), ptr(r3),
                                              ptr(q), ptr(c1), ptr(c2), ptr(c3), stream),
           "pfc_op_lin_residual_restrict")
+
+
+def pfc_op_restrict_q(n, levels, q, c, e=None, g=None, stream=None):
+    check(lib().pfc_op_restrict_q(n, levels, ptr(q), ptr(c), ptr(e), ptr(g), stream),
+          "pfc_op_restrict_q")
 
 
 def pfc_op_lin_restrict_chain(n, h, eps, tau, zero_init, levels, d1, d2, d3, r1, r2, r3, q,

@@ -1707,6 +1707,15 @@ int pfc_op_lin_restrict_chain(int n, double h, double eps, double tau, int zero_
   return PFC_OK;
 }
 
+int pfc_op_restrict_q(int n, int levels, const float* q, float* c, float* e, float* g,
+                      void* stream) {
+  if (n < 2 || (n & 1) || levels < 1 || levels > 3 || !q || !c || (levels >= 2 && !e) ||
+      (levels == 3 && !g) || (levels >= 2 && (n % 32) != 0))
+    return PFC_EINVAL;
+  PFC_CUDA(launch_restrict_q(n, levels - 1, q, c, e, g, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
 int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, const float* e3,
                        float* d1, float* d2, float* d3, void* stream) {
   if (n < 2 || (n & 3) || !e1 || !e2 || !e3 || !d1 || !d2 || !d3) return PFC_EINVAL;

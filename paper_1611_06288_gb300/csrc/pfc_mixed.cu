@@ -1450,6 +1450,65 @@ __global__ void __launch_bounds__(kChTX * kChTY * kChTZ) k_lin_restrict_chain32(
   }
 }
 
+// q restricted down up to EXTRA + 1 levels in one launch: a block of kChTX x
+// kChTY x kChTZ cells of the first coarse level averages their 8 children
+// (the children order of k_restrict32), keeps its averages in shared memory
+// and averages them down to (kChTX/2 x kChTY/2 x kChTZ/2) and then
+// (kChTX/4 x kChTY/4 x kChTZ/4) cells in the same order: bit-identical to
+// EXTRA + 1 launches of k_restrict32.  First coarse size a multiple of kChTX
+// and kChTZ.
+template <int EXTRA>
+__global__ void __launch_bounds__(kChTX * kChTY * kChTZ) k_restrict_chain32(
+    int n, const float* __restrict__ f, float* __restrict__ c, float* __restrict__ e,
+    float* __restrict__ g) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float s1[kChTZ][kChTY][kChTX];
+  __shared__ float s2[kChTZ / 2][kChTY / 2][kChTX / 2];
+  const int nc = n >> 1;
+  const int tx = threadIdx.x, ty = threadIdx.y, tz = threadIdx.z;
+  const int I = blockIdx.x * kChTX + tx, J = blockIdx.y * kChTY + ty;
+  int K = blockIdx.z * kChTZ + tz;
+  const int m = member_of(K, nc);
+  f += (size_t)m * n * n * n;
+  float acc = 0.f;
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    acc += __ldg(f + split_index(2 * I + (s & 1), 2 * J + ((s >> 1) & 1), 2 * K + (s >> 2), n));
+  const float v = 0.125f * acc;
+  c[(size_t)m * nc * nc * nc + split_index(I, J, K, nc)] = v;
+  if (EXTRA == 0) return;
+  s1[tz][ty][tx] = v;
+  __syncthreads();
+  const int tid = (tz * kChTY + ty) * kChTX + tx;
+  const int n2 = nc >> 1;
+  if (tid < (kChTX / 2) * (kChTY / 2) * (kChTZ / 2)) {
+    const int x = tid % (kChTX / 2), y = (tid / (kChTX / 2)) % (kChTY / 2),
+              z = tid / ((kChTX / 2) * (kChTY / 2));
+    float a2 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) a2 += s1[2 * z + (s >> 2)][2 * y + ((s >> 1) & 1)][2 * x + (s & 1)];
+    const float v2 = 0.125f * a2;
+    const int I2 = blockIdx.x * (kChTX / 2) + x, J2 = blockIdx.y * (kChTY / 2) + y;
+    const int K2 = (K - tz) / 2 + z;
+    e[(size_t)m * n2 * n2 * n2 + split_index(I2, J2, K2, n2)] = v2;
+    if (EXTRA > 1) s2[z][y][x] = v2;
+  }
+  if (EXTRA < 2) return;
+  __syncthreads();
+  const int n3 = n2 >> 1;
+  if (tid < (kChTX / 4) * (kChTY / 4) * (kChTZ / 4)) {
+    const int x = tid % (kChTX / 4), y = (tid / (kChTX / 4)) % (kChTY / 4),
+              z = tid / ((kChTX / 4) * (kChTY / 4));
+    float a3 = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) a3 += s2[2 * z + (s >> 2)][2 * y + ((s >> 1) & 1)][2 * x + (s & 1)];
+    const int I3 = blockIdx.x * (kChTX / 4) + x, J3 = blockIdx.y * (kChTY / 4) + y;
+    const int K3 = (K - tz) / 4 + z;
+    g[(size_t)m * n3 * n3 * n3 + split_index(I3, J3, K3, n3)] = 0.125f * a3;
+  }
+}
+
 // d += P e (ASSIGN: d = P e; d was zero and is not read), trilinear
 // cell-centred prolongation with the weights 27, 9, 3, 1 over 64 as three
 // one-dimensional passes: the child on the low side of an axis takes
@@ -3263,6 +3322,18 @@ cudaError_t launch_lin_restrict_chain32(const Lvl& L, bool zero, int extra, cons
                   c[1], c[2], e[0], e[1], e[2], g2[0], g2[1], g2[2]);
 }
 
+cudaError_t launch_restrict_q(int n, int extra, const float* q, float* c, float* e, float* g,
+                              cudaStream_t st) {
+  const int nc = n / 2;
+  if (extra == 0) {
+    const Launch3 l = launch3(nc, nc, nc);
+    return launch_k(true, k_restrict32, l.grid, l.block, 0, st, n, q, c);
+  }
+  const dim3 grid(nc / kChTX, nc / kChTY, nc / kChTZ), block(kChTX, kChTY, kChTZ);
+  return launch_k(true, extra > 1 ? k_restrict_chain32<2> : k_restrict_chain32<1>, grid, block, 0,
+                  st, n, q, c, e, extra > 1 ? g : e);
+}
+
 cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, const float* e2,
                              const float* e3, float* d1, float* d2, float* d3, cudaStream_t st) {
   const int nc = n / 2, pz = prolong_planes(nc, 3);
@@ -3374,12 +3445,27 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
     h *= 2.0;
   }
   cudaError_t e = cudaSuccess;
-  for (int l = 1; l < nl && e == cudaSuccess; ++l) {
-    const Launch3 g = launch3(sizes[l], sizes[l], sizes[l] * members);
+  for (int l = 1; l < nl && e == cudaSuccess;) {
+    const int nc = sizes[l];
+    // up to two more levels in the same launch where the block tiles the level
+    int extra = nl - 1 - l;
+    if (extra > 2) extra = 2;
+    if (nc % kChTX != 0 || nc % kChTZ != 0 || nc % kChTY != 0) extra = 0;
     prof_begin(pr, PFC_K_RESTRICT, st);
-    e = launch_k(pr == nullptr, k_restrict32, g.grid, g.block, 0, st, sizes[l - 1],
-                 mx.q[l - 1], mx.q[l]);
+    if (extra > 0) {
+      const dim3 grid(nc / kChTX, nc / kChTY, (nc / kChTZ) * members),
+          block(kChTX, kChTY, kChTZ);
+      float* const g2 = extra > 1 ? mx.q[l + 2] : mx.q[l + 1];
+      e = launch_k(pr == nullptr, extra > 1 ? k_restrict_chain32<2> : k_restrict_chain32<1>,
+                   grid, block, 0, st, sizes[l - 1], (const float*)mx.q[l - 1], mx.q[l],
+                   mx.q[l + 1], g2);
+    } else {
+      const Launch3 g = launch3(nc, nc, nc * members);
+      e = launch_k(pr == nullptr, k_restrict32, g.grid, g.block, 0, st, sizes[l - 1],
+                   (const float*)mx.q[l - 1], mx.q[l]);
+    }
     prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
+    l += 1 + extra;
   }
   for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic) e = vcycle32(c, 0, ic == 0);
   return e;

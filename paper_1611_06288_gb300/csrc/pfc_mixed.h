@@ -164,6 +164,10 @@ cudaError_t launch_lin_residual_restrict32(const Lvl& L, bool zero, const float*
 // The restriction of launch_lin_residual_restrict32 to c and, in the same
 // launch, `extra` (1 or 2) further 8-cell averages to e and g (n/2 a
 // multiple of 16).
+// q (colour-split, n^3) averaged down 1 + extra levels (extra 0..2; extra > 0
+// needs n/2 a multiple of 16); c, e, g the levels produced.
+cudaError_t launch_restrict_q(int n, int extra, const float* q, float* c, float* e, float* g,
+                              cudaStream_t st);
 cudaError_t launch_lin_restrict_chain32(const Lvl& L, bool zero, int extra, const float* d1,
                                        const float* d2, const float* d3, const float* r1,
                                        const float* r2, const float* r3, const float* q,

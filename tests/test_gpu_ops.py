@@ -603,3 +603,30 @@ def test_restrict_chain_rejects_bad_sizes():
     with pytest.raises(B.PFCError):           # levels out of range
         B.pfc_op_lin_restrict_chain(64, 0.5, EPS, TAU, True, 4, None, None, None, z, z, z, None,
                                     z, z, z, z, z, z, z, z, z)
+
+
+def _restrict_f32(x):
+    """8-cell average in float32, children summed in the kernels' order
+    (x fastest, then y, then z), natural layout [k, j, i]."""
+    acc = np.zeros(tuple(s // 2 for s in x.shape), np.float32)
+    for s in range(8):
+        acc = (acc + x[(s >> 2)::2, ((s >> 1) & 1)::2, (s & 1)::2]).astype(np.float32)
+    return (np.float32(0.125) * acc).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,levels", [(12, 1), (32, 2), (64, 3), (128, 3)])
+def test_restrict_q_chain_is_bit_exact(n, levels):
+    """pfc_op_restrict_q (the one-launch restriction of the Newton coefficient
+    q to the coarse levels of the FP32 correction solve) equals the chain of
+    single-level float32 8-cell averages bit for bit."""
+    rng = np.random.default_rng(40 + n)
+    q = (0.2 + rng.random((n, n, n))).astype(np.float32)
+    outs = [torch.empty((n >> (l + 1)) ** 3, dtype=torch.float32, device="cuda")
+            for l in range(levels)]
+    B.pfc_op_restrict_q(n, levels, dev(to_split(q), torch.float32).reshape(-1), *outs)
+    torch.cuda.synchronize()
+    want = q
+    for l in range(levels):
+        want = _restrict_f32(want)
+        got = from_split(outs[l].cpu().numpy().reshape((n >> (l + 1),) * 3))
+        assert np.array_equal(got.view(np.uint32), want.view(np.uint32)), l
