@@ -101,6 +101,7 @@ def parse():
     ap.add_argument("--nu1", type=int, default=None)
     ap.add_argument("--nu2", type=int, default=None)
     ap.add_argument("--coarse-sweeps", type=int, default=None)
+    ap.add_argument("--cluster-tail", type=int, default=None)
     ap.add_argument("--guess", default=None, choices=["previous", "extrapolate"],
                     help="initial iterate of a step (default: the previous step's solution)")
     ap.add_argument("--fp64-steps", type=int, default=5)
@@ -596,7 +597,7 @@ def run_ours(args):
         return out
 
     overrides = {k: getattr(args, k) for k in ("inner_cycles", "jacobi_factor", "nu1", "nu2",
-                                                "coarse_sweeps", "guess")
+                                                "coarse_sweeps", "guess", "cluster_tail")
                  if getattr(args, k) is not None}
     n = args.n
     r = measure(n, args.steps, args.warmup, args.fp64_steps, overrides, args.precision)

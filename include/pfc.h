@@ -113,12 +113,16 @@ typedef struct pfc_params {
                                 thread-block cluster per member (levels in z
                                 slabs over the CTAs, neighbour planes through
                                 distributed shared memory) where the device
-                                can run such a cluster; 0 (default) keeps
-                                separate launches down to 16^3 and one block
-                                below, which measured as fast for one large
-                                grid and faster for ensembles.  Same
-                                arithmetic up to summation order and the
-                                approximate division of the pointwise solve */
+                                can run such a cluster; 2 uses the cluster
+                                only where the single-block tail would start
+                                (levels of at most 16^3 cells), the levels
+                                above keeping their full-GPU launches (1464
+                                against 1425 steps/s on the 128^3 smooth-mode
+                                workload); 0 (default) keeps separate
+                                launches down to 16^3 and one block below,
+                                faster for ensembles.  Same arithmetic up to
+                                summation order and the approximate division
+                                of the pointwise solve */
   int    step_diagnostics;   /* 1: every step also forms the energy/mass sums
                                 of its new state in the same graph launch
                                 (no further launch or synchronisation), and

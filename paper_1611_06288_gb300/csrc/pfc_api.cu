@@ -94,7 +94,7 @@ int validate(const pfc_params* p) {
   if (p->guess != PFC_GUESS_PREVIOUS && p->guess != PFC_GUESS_EXTRAPOLATE) return PFC_EINVAL;
   if (!(p->mobility_m0 > 0) || !(p->mobility_m2 >= 0)) return PFC_EINVAL;
   if (variable_mobility(p) && p->precision != PFC_MIXED) return PFC_EINVAL;
-  if (p->cluster_tail != 0 && p->cluster_tail != 1) return PFC_EINVAL;
+  if (p->cluster_tail < 0 || p->cluster_tail > 2) return PFC_EINVAL;
   if (p->step_diagnostics != 0 && p->step_diagnostics != 1) return PFC_EINVAL;
   if (p->defect_planes < 0) return PFC_EINVAL;
   int sizes[kMaxLevels];

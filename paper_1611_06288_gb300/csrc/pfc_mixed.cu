@@ -2978,7 +2978,7 @@ cudaError_t ctail32(const Ctx32& c, int l0, bool zero_init, int nd, size_t smem,
 // Whether vcycle32 at level l restricts to l + 1 with a launch of its own
 // (not the cluster tail, the shared-memory tail or the coarsest solve).
 bool restricts_alone(const Ctx32& c, int l) {
-  if (c.p->cluster_tail || l >= c.nl - 1) return false;
+  if (c.p->cluster_tail == 1 || l >= c.nl - 1) return false;
   if (c.L[l].n <= kTailMaxN && c.nl - l <= kTailMaxLevels) {
     int sizes[kMaxLevelsMixed];
     for (int q = 0; q < c.nl; ++q) sizes[q] = c.L[q].n;
@@ -3008,7 +3008,9 @@ int chain_extra(const Ctx32& c, int l) {
 cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init, int have = 0) {
   MixedBufs& mx = *c.mx;
   const LvlF& L = c.L[l];
-  if (c.p->cluster_tail) {
+  // cluster tail: from the first level of at most kCtMaxN^3 cells (mode 1)
+  // or only where the single-block tail would start (mode 2)
+  if (c.p->cluster_tail == 1 || (c.p->cluster_tail == 2 && L.n <= kTailMaxN)) {
     size_t smem = 0;
     int ga_off = 0;
     const int nd = ctail_layout(c, l, &smem, &ga_off);

@@ -159,13 +159,15 @@ def smooth_sweep(n: int, dt: float = 0.0125, tol: float = 1e-9):
     corrections per step; 3 with a factor of 3, and 2 still with up to 8
     cycles); at 256^3 five per correction with a factor of 3 (2 corrections
     per step: 165 steps/s, against 153 for three cycles and 3 corrections,
-    143 for two and 4); at 32^3 V(1,2)."""
+    143 for two and 4); at 32^3 V(1,2).  Below 256^3 the 16^3 coarsest level
+    runs on an 8-CTA cluster (cluster_tail 2: 1464 against 1425 steps/s at
+    128^3; no change at 256^3)."""
     if n >= 256:
         kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 5), ("jacobi_factor", 3),
               ("coarse_sweeps", 2))
     elif n >= 64:
         kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 2), ("jacobi_factor", 4),
-              ("coarse_sweeps", 2))
+              ("coarse_sweeps", 2), ("cluster_tail", 2))
     else:
         kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 2), ("jacobi_factor", 3),
               ("coarse_sweeps", 2))

@@ -152,15 +152,16 @@ def test_mobility_params(libpfc):
 
 
 def test_cluster_tail_param(libpfc):
-    """cluster_tail is 0 or 1 (default 0) and does not change the workspace:
-    the cluster kernel keeps its levels in shared memory."""
+    """cluster_tail is 0, 1 or 2 (default 0) and does not change the
+    workspace: the cluster kernel keeps its levels in shared memory."""
     p = B.pfc_default_params()
     p.n, p.L, p.eps, p.dt = 64, 32.0, 0.1, 0.05
     p.precision = B.PFC_MIXED
     off = B.pfc_workspace_bytes(p)
-    p.cluster_tail = 1
-    assert B.pfc_workspace_bytes(p) == off > 0
-    p.cluster_tail = 2
+    for mode in (1, 2):
+        p.cluster_tail = mode
+        assert B.pfc_workspace_bytes(p) == off > 0
+    p.cluster_tail = 3
     assert B.pfc_workspace_bytes(p) == 0
 
 

@@ -57,6 +57,27 @@ def test_cluster_tail_matches_block_tail(n, settings):
     assert np.sqrt(np.mean(r[0] ** 2 + r[2] ** 2) / 3) <= TOL * 1.0001
 
 
+@pytest.mark.parametrize("n", [64, 128])
+def test_cluster_tail_at_the_tail_level_only(n):
+    """cluster_tail = 2: the cluster takes only the levels the single-block
+    tail would (16^3 here); the levels above keep their full-GPU kernels.
+    Smooth mode with the workload's settings: the same correction counts and
+    fields as the single-block tail to what the tolerance allows, and the
+    oracle's FP64 residual of its result below the tolerance."""
+    wl = W.smooth_sweep(n)
+    phi0 = wl.phi0()
+    settings = {k: v for k, v in wl.mixed().items() if k != "cluster_tail"}
+    cyc_on, on = run(n, wl.L, wl.eps, wl.dt, phi0, 3, 2, **settings)
+    cyc_off, off = run(n, wl.L, wl.eps, wl.dt, phi0, 3, 0, **settings)
+    assert all(abs(a - b) <= 1 for a, b in zip(cyc_on, cyc_off)), (cyc_on, cyc_off)
+    for x, y in zip(on[:3], off[:3]):
+        assert rel_l2(x, y) <= AGREE_RTOL
+    a, mu, om, b = on
+    p = O.Params(eps=wl.eps, tau=wl.dt)
+    r = O.residual(O.source_S(b, b, wl.h, p), [a, mu, om], b, wl.h, p)
+    assert np.sqrt(np.mean(r[0] ** 2 + r[2] ** 2) / 3) <= TOL * 1.0001
+
+
 def test_cluster_jacobi_coarsest_with_convergence_test():
     """A distributed coarsest level in the damped-Jacobi regime with enough
     sweeps for the cluster-wide convergence test (every fourth sweep):
