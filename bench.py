@@ -64,23 +64,27 @@ KERNEL_BYTES = {
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
 # The defect class of the mixed path averages a step's launches: two full
-# defects (150.0 MB each) and one pointwise first defect (158.1 MB).
+# defects and the start of the step (k_start64_point).
 # Keyed by the finest level's size the capture ran at (other sizes: null).
-NCU_TRAFFIC = {("mixed", "defect", 128): 152.7e6}   # profiles/k_defect64_fx_128.md, k_defect64_point_128.md
+NCU_TRAFFIC = {}
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
 # counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
 # the three Laplacians' neighbour sums in exact int64 fixed point (no FP64
 # flops) and its rows in 6 DFMA + 4 DADD + 2 DMUL per cell (ncu: DFMA, DADD
-# and DMUL thread-instruction rates 3:2:1): 18 flops; the pointwise first
-# defect of a step 4 DFMA + 2 DADD + 2 DMUL (2:1:1): 12 flops.  With two full
-# defects and one pointwise per step (two corrections): 16 per launch.
-KERNEL_FLOPS = {("mixed", "defect"): (16.0, 2)}
+# and DMUL thread-instruction rates 3:2:1): 18 flops.  The start of a warm
+# step (k_start64_point) forms S2, S3 (2 DFMA + 3 DMUL) and the pointwise
+# first defect (4 DFMA + 2 DADD + 2 DMUL): 19 flops.  With two full defects
+# and one start per step (two corrections): 55/3 per launch.
+KERNEL_FLOPS = {("mixed", "defect"): (55.0 / 3.0, 2)}
 
-# Algorithmic bytes per cell of the FP64 defect (the ALU-bound class above),
-# reported beside its FP64 roofline: phi, mu, om, b, S2, S3 read, r(3) and q
-# FP32 and the three Laplacians FP64 written.
-DEFECT_BYTES = 88.0
+# Algorithmic bytes per cell of the FP64 defect class (the ALU-bound class
+# above), reported beside its FP64 roofline: a full defect reads phi, mu, om,
+# b, S2, S3 and writes r(3), q FP32 and three Laplacians FP64 (88 B); the
+# start of a step reads b, mu, om and four Laplacians and writes S2, S3,
+# phi^{k+1}, one Laplacian and r(3), q (104 B).  Averaged over a step's
+# launches (two full defects, one start).
+DEFECT_BYTES = (2 * 88.0 + 104.0) / 3.0
 
 # FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
 # sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)

@@ -350,6 +350,15 @@ cudaError_t enqueue_diagnostics(int n, int members, const double* a, const doubl
                          cudaMemcpyDeviceToHost, st);
 }
 
+// The convergence decision from the sum of squared residuals in dout.
+int enqueue_decide(pfc_ctx* c, cudaGraphConditionalHandle h, int use_handle, int first) {
+  const double n3 = (double)c->p.n * c->p.n * c->p.n;
+  PFC_CUDA(launch_decide(h, use_handle, c->dout, c->dstate, 1.0 / (3.0 * n3), c->p.tol,
+                         c->p.max_cycles, first, c->st, c->nb, c->prof.mask == 0));
+  c->prof.launches += 1;
+  return PFC_OK;
+}
+
 // Sum of squared residuals of the level-0 iterate (to dout[0]) and the
 // convergence decision into dstate.
 int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
@@ -379,11 +388,7 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
                                     lv.S[2], lv.b, c->partials, c->dout, st,
                                     c->lap[c->ia]));
   }
-  const double n3 = (double)c->p.n * c->p.n * c->p.n;
-  PFC_CUDA(launch_decide(h, use_handle, c->dout, c->dstate, 1.0 / (3.0 * n3), c->p.tol,
-                         c->p.max_cycles, first, st, c->nb, c->prof.mask == 0));
-  c->prof.launches += 1;
-  return PFC_OK;
+  return enqueue_decide(c, h, use_handle, first);
 }
 
 // Work of a step before its convergence loop: S2, S3 (Eqs. 5.9-5.10), phi^k on
@@ -396,6 +401,15 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   Prof* pr = &c->prof;
   const bool extrapolate = c->p.guess == PFC_GUESS_EXTRAPOLATE;
+  if (warm) {
+    // the last step's solution is the initial iterate and its Laplacians are
+    // stored (PFC_MIXED, M == 1): S2, S3, the iterate and the first defect
+    // in one pass
+    PFC_CUDA(mixed_enqueue_start_point(c->mx, lv.L, lv.u, lv.S, lv.b, c->lap[c->ib],
+                                       c->lap[c->ic], c->lmu, c->lom, c->lap[c->ia],
+                                       c->partials, c->dout, c->st, pr, c->nb, c->c1m));
+    return enqueue_decide(c, h, use_handle, 1);
+  }
   if (extrapolate && df_state(&c->p)) {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 2, c->st,
               launch_guess_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),

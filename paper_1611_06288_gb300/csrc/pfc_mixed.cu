@@ -504,6 +504,62 @@ __global__ void __launch_bounds__(256) k_defect64_point(
   if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
 }
 
+// Start of a warm step in one pass: S2, S3 of Eqs. 5.9-5.10 from the stored
+// unscaled Laplacians of phi^k (lapb) and phi^{k-1} (lapc), with the
+// operations of k_source_cached; the initial iterate phi^{k+1} := phi^k
+// (phi_next); and the pointwise first defect of k_defect64_point from those
+// S2, S3 (the same values it would read back).  Bit-identical to the three
+// separate steps; one read of b and lapb for all of them.
+__global__ void __launch_bounds__(256) k_start64_point(
+    Lvl L, const double* __restrict__ b, const double* __restrict__ mu,
+    const double* __restrict__ om, const double* __restrict__ lapb,
+    const double* __restrict__ lapc, const double* __restrict__ lapmu,
+    const double* __restrict__ lapom, double* __restrict__ S2, double* __restrict__ S3,
+    double* __restrict__ phi_next, float* __restrict__ r1, float* __restrict__ r2,
+    float* __restrict__ r3, float* __restrict__ q, double* partials, double* __restrict__ lap,
+    const double* __restrict__ c1m) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  const int m = blockIdx.y;
+  const size_t off = (size_t)m * cells;
+  b += off, mu += off, om += off, lapb += off, lapc += off, lapmu += off, lapom += off;
+  S2 += off, S3 += off, phi_next += off, lap += off;
+  r1 += off, r2 += off, r3 += off, q += off;
+  partials += (size_t)m * gridDim.x;
+  const double c1 = c1m ? c1m[m] : L.c1;
+  const float c1f = d2f_rn(c1);
+  float acc = 0.f;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const double p = __ldg(b + t), lbr = __ldg(lapb + t);
+    const double lb = L.g * lbr;
+    const double lc = L.g * __ldg(lapc + t);
+    const double s2 = fma(3.0, lb, fma(c1, p, -lc));
+    const double s3 = 0.5 * lb;
+    S2[t] = s2;
+    S3[t] = s3;
+    phi_next[t] = p;
+    const double x = L.tg * __ldg(lapmu + t);
+    const double y = fma(L.g, __ldg(lapom + t), fma(c1, p, fma(p * p, p, s2 - __ldg(mu + t))));
+    const double z = fma(L.gh, lbr, s3 - __ldg(om + t));
+    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
+    const float pf = d2f_rn(p);
+    const float qf = fmaf(1.5f * pf, pf, c1f);
+    acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
+    const int o = split_index(i, j, k, n);
+    r1[o] = xf;
+    r2[o] = yf;
+    r3[o] = zf;
+    q[o] = qf;
+    lap[t] = lbr;
+  }
+  acc = block_sum_f(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
 // Face mobilities of a step: M(A phi_*) on the faces i+1/2 of each axis for
 // M(phi) = m0 + m2 phi^2, phi_* = 3/2 b - 1/2 c (b = phi^k, c = phi^{k-1});
 // the face i+1/2 of an axis is stored at cell i.
@@ -3178,6 +3234,26 @@ cudaError_t launch_defect64_point(const Lvl& L, const double* b, const double* m
   return e;
 }
 
+cudaError_t launch_start64_point(const Lvl& L, const double* b, const double* mu,
+                                 const double* om, const double* lapb, const double* lapc,
+                                 const double* lapmu, const double* lapom, double* S2,
+                                 double* S3, double* phi_next, float* r1, float* r2, float* r3,
+                                 float* q, double* partials, double* out, double* lap,
+                                 cudaStream_t st, int members, const double* c1m, bool pdl) {
+  const int wave = wave_blocks(k_start64_point, (int64_t)L.n * L.n * L.n * members);
+  int nbx = wave / members;
+  const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
+  if (nbx > need) nbx = (int)need;
+  if (nbx < 1) nbx = 1;
+  cudaError_t e = launch_ex(pdl, k_start64_point, dim3(nbx, members), dim3(kReduceThreads), 0,
+                            st, L, b, mu, om, lapb, lapc, lapmu, lapom, S2, S3, phi_next, r1, r2,
+                            r3, q, partials, lap, c1m);
+  if (e == cudaSuccess)
+    e = launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st,
+                  (const double*)partials, nbx, out);
+  return e;
+}
+
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
                                  double* Mx, double* My, double* Mz, cudaStream_t st) {
   const Launch3 g = launch3(n, n, n);
@@ -3409,6 +3485,21 @@ cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* con
   cudaError_t e = launch_defect64_point(L0, b, u[1], u[2], S[1], S[2], lapb, lapmu, lapom,
                                         mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0], partials,
                                         dout, lap, st, members, c1m, !pr || pr->mask == 0);
+  prof_end(pr, PFC_K_DEFECT, 0, 2, st);
+  return e;
+}
+
+cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                      double* const S[3], const double* b,
+                                      const double* lapb, const double* lapc,
+                                      const double* lapmu, const double* lapom, double* lap,
+                                      double* partials, double* dout, cudaStream_t st, Prof* pr,
+                                      int members, const double* c1m) {
+  prof_begin(pr, PFC_K_DEFECT, st);
+  cudaError_t e = launch_start64_point(L0, b, u[1], u[2], lapb, lapc, lapmu, lapom, S[1], S[2],
+                                       u[0], mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0],
+                                       partials, dout, lap, st, members, c1m,
+                                       !pr || pr->mask == 0);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }

@@ -65,6 +65,16 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
 // The first defect of a step that starts from the previous step's solution
 // (phi := b, mu and omega kept), pointwise from the Laplacians of b, mu and
 // omega that the previous step's last defect stored; writes lapb to lap.
+// Start of a warm PFC_MIXED step in one launch (plus its reduction): S2, S3
+// into S[1], S[2], phi^{k+1} := b into u[0], and the pointwise first defect
+// (as mixed_enqueue_defect_point with those S2, S3); lapc is the stored
+// Laplacian of phi^{k-1}.
+cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                      double* const S[3], const double* b,
+                                      const double* lapb, const double* lapc,
+                                      const double* lapmu, const double* lapom, double* lap,
+                                      double* partials, double* dout, cudaStream_t st, Prof* pr,
+                                      int members, const double* c1m);
 cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                        double* const S[3], const double* b,
                                        const double* lapb, const double* lapmu,
