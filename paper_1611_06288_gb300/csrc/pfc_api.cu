@@ -359,11 +359,29 @@ int enqueue_decide(pfc_ctx* c, cudaGraphConditionalHandle h, int use_handle, int
   return PFC_OK;
 }
 
+// The arguments of the step's convergence decision, for residual kernels
+// that take it in their final reduction (single-member contexts).
+DecideArgs decide_args(const pfc_ctx* c, cudaGraphConditionalHandle h, int use_handle,
+                       int first) {
+  const double n3 = (double)c->p.n * c->p.n * c->p.n;
+  DecideArgs a;
+  a.handle = h;
+  a.use_handle = use_handle;
+  a.state = c->dstate;
+  a.inv_3n3 = 1.0 / (3.0 * n3);
+  a.tol = c->p.tol;
+  a.max_iter = c->p.max_cycles;
+  a.first = first;
+  return a;
+}
+
 // Sum of squared residuals of the level-0 iterate (to dout[0]) and the
 // convergence decision into dstate.
 int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h,
                             int use_handle, int first, bool point = false) {
   cudaStream_t st = c->st;
+  const DecideArgs da = decide_args(c, h, use_handle, first);
+  bool decided = false;
   if (df_state(&c->p)) {
     float2* u[3];
     float2* S[3];
@@ -376,19 +394,20 @@ int enqueue_residual_decide(pfc_ctx* c, const Level64& lv, cudaGraphConditionalH
   } else if (point) {
     PFC_CUDA(mixed_enqueue_defect_point(c->mx, lv.L, lv.u, lv.S, lv.b, c->lap[c->ib], c->lmu,
                                         c->lom, c->lap[c->ia], c->partials, c->dout, st,
-                                        &c->prof, c->nb, c->c1m));
+                                        &c->prof, c->nb, c->c1m, &da, &decided));
   } else if (is_mixed(&c->p)) {
     PFC_CUDA(mixed_enqueue_defect(c->mx, lv.L, lv.u, lv.S, lv.b, c->partials, c->dout, st,
                                   &c->prof, c->lap[c->ia], c->nb, c->c1m,
                                   c->M[0] ? c->M : nullptr, c->lmu, c->lom,
-                                  c->p.defect_planes));
+                                  c->p.defect_planes, &da, &decided));
   } else {
     PFC_TIMED(&c->prof, PFC_K_RESIDUAL_NORM, 0, 2, st,
               launch_residual_norm2(lv.L, lv.u[0], lv.u[1], lv.u[2], lv.S[0], lv.S[1],
                                     lv.S[2], lv.b, c->partials, c->dout, st,
                                     c->lap[c->ia]));
   }
-  return enqueue_decide(c, h, use_handle, first);
+  // a residual that took the decision in its reduction needs no launch of it
+  return decided ? PFC_OK : enqueue_decide(c, h, use_handle, first);
 }
 
 // Work of a step before its convergence loop: S2, S3 (Eqs. 5.9-5.10), phi^k on
@@ -405,10 +424,13 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
     // the last step's solution is the initial iterate and its Laplacians are
     // stored (PFC_MIXED, M == 1): S2, S3, the iterate and the first defect
     // in one pass
+    const DecideArgs da = decide_args(c, h, use_handle, 1);
+    bool decided = false;
     PFC_CUDA(mixed_enqueue_start_point(c->mx, lv.L, lv.u, lv.S, lv.b, c->lap[c->ib],
                                        c->lap[c->ic], c->lmu, c->lom, c->lap[c->ia],
-                                       c->partials, c->dout, c->st, pr, c->nb, c->c1m));
-    return enqueue_decide(c, h, use_handle, 1);
+                                       c->partials, c->dout, c->st, pr, c->nb, c->c1m, &da,
+                                       &decided));
+    return decided ? PFC_OK : enqueue_decide(c, h, use_handle, 1);
   }
   if (extrapolate && df_state(&c->p)) {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 2, c->st,

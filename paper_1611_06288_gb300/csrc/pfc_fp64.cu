@@ -535,33 +535,8 @@ __global__ void k_decide(cudaGraphConditionalHandle handle, int use_handle,
   // some member is still running and none has failed
   const int m = threadIdx.x;
   int running = 0, failed = 0;
-  if (m < members) {
-    StepState& st = s[m];
-    const double rms = sqrt(sum[m] * inv_3n3);
-    if (first) {
-      st.iters = 0;
-      st.rms0 = rms;
-      st.status = kStepRunning;
-    }
-    if (first || st.status == kStepRunning) {
-      if (!first) st.iters += 1;
-      st.rms = rms;
-      int status;
-      if (rms <= tol)
-        status = kStepConverged;
-      else if (!isfinite(rms))
-        status = kStepNaN;
-      else if (st.iters >= max_iter)
-        status = kStepNoConv;
-      else
-        status = kStepRunning;
-      st.status = status;
-    } else if (st.status == kStepConverged) {
-      st.rms = rms;
-    }
-    running = st.status == kStepRunning;
-    failed = st.status == kStepNaN || st.status == kStepNoConv;
-  }
+  if (m < members)
+    decide_member(s[m], sum[m], inv_3n3, tol, max_iter, first, running, failed);
   running = __syncthreads_or(running);
   failed = __syncthreads_or(failed);
   if (use_handle && threadIdx.x == 0)

@@ -37,6 +37,48 @@ struct StepState {
 };
 constexpr int kStepRunning = 0, kStepConverged = 1, kStepNaN = 2, kStepNoConv = 3;
 
+// One member's convergence decision from its sum of squared residuals: the
+// RMS residual against the tolerance, NaN, the cycle budget; a member that
+// has converged stays converged.  running / failed report the new status.
+__device__ __forceinline__ void decide_member(StepState& st, double sum, double inv_3n3,
+                                              double tol, int max_iter, int first, int& running,
+                                              int& failed) {
+  const double rms = sqrt(sum * inv_3n3);
+  if (first) {
+    st.iters = 0;
+    st.rms0 = rms;
+    st.status = kStepRunning;
+  }
+  if (first || st.status == kStepRunning) {
+    if (!first) st.iters += 1;
+    st.rms = rms;
+    int status;
+    if (rms <= tol)
+      status = kStepConverged;
+    else if (!isfinite(rms))
+      status = kStepNaN;
+    else if (st.iters >= max_iter)
+      status = kStepNoConv;
+    else
+      status = kStepRunning;
+    st.status = status;
+  } else if (st.status == kStepConverged) {
+    st.rms = rms;
+  }
+  running = st.status == kStepRunning;
+  failed = st.status == kStepNaN || st.status == kStepNoConv;
+}
+
+// The decision of a single-member step taken by the kernel that reduces its
+// residual (one launch instead of two): the arguments of launch_decide.
+struct DecideArgs {
+  cudaGraphConditionalHandle handle;
+  int use_handle;
+  StepState* state;
+  double inv_3n3, tol;
+  int max_iter, first;
+};
+
 // From the reduced sums of squared residuals sum[m] of `members` ensemble
 // members (1 for a single problem): update state[m] (a converged member stays
 // converged) and, if use_handle, set the WHILE condition of the step graph to

@@ -1003,6 +1003,39 @@ __global__ void k_reduce1(const double* __restrict__ partials, int nparts, doubl
   if (threadIdx.x == 0) out[m] = acc[0];
 }
 
+// k_reduce1 for a single member followed by its convergence decision (the
+// work of k_decide) in the same block: the sum in the same order, one launch
+// fewer per residual.
+__global__ void k_reduce1_decide(const double* __restrict__ partials, int nparts, double* out,
+                                 DecideArgs a) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double sm[32];
+  double acc[1] = {0.0};
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) acc[0] += partials[p];
+  block_sum<1>(acc, sm);
+  if (threadIdx.x == 0) {
+    out[0] = acc[0];
+    int running = 0, failed = 0;
+    decide_member(a.state[0], acc[0], a.inv_3n3, a.tol, a.max_iter, a.first, running, failed);
+    if (a.use_handle) cudaGraphSetConditional(a.handle, (running && !failed) ? 1u : 0u);
+  }
+}
+
+// The final reduction of a residual's block sums: with a decision to take
+// (single member) the fused kernel, else k_reduce1.
+cudaError_t launch_reduce1(bool pdl, const double* partials, int nparts, double* out,
+                           int members, cudaStream_t st, const DecideArgs* da, bool* decided) {
+  if (da && members == 1) {
+    if (decided) *decided = true;
+    return launch_ex(pdl, k_reduce1_decide, dim3(1), dim3(kReduceThreads), 0, st, partials,
+                     nparts, out, *da);
+  }
+  if (decided) *decided = false;
+  return launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st, partials, nparts,
+                   out);
+}
+
 // 8-cell average of a split-layout field onto the (split-layout) level n/2.
 __global__ void k_restrict32(int n, const float* __restrict__ f, float* __restrict__ c) {
   pdl_wait();
@@ -3176,7 +3209,9 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             float* q, double* partials, double* out, cudaStream_t st,
                             double* lap, int members, const double* c1m, const double* Mx,
                             const double* My, const double* Mz, double* lapmu,
-                            double* lapom, bool pdl, int planes) {
+                            double* lapom, bool pdl, int planes, const DecideArgs* da,
+                            bool* decided) {
+  if (decided) *decided = false;
   if (!Mx) {
     const int64_t cap = (int64_t)kReduceBlocks * kReduceComps;
     int zc = fx_planes(L.n, members, cap);
@@ -3194,8 +3229,8 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                                 mu, om, S1, S2, S3, b, r1, r2, r3, q, partials, lap, c1m, lapmu,
                                 lapom);
       if (e == cudaSuccess)
-        e = launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st,
-                      (const double*)partials, (int)(grid.x * grid.y * chunks), out);
+        e = launch_reduce1(pdl, partials, (int)(grid.x * grid.y * chunks), out, members, st, da,
+                           decided);
       return e;
     }
   }
@@ -3219,7 +3254,8 @@ cudaError_t launch_defect64_point(const Lvl& L, const double* b, const double* m
                                   const double* om, const double* S2, const double* S3, const double* lapb, const double* lapmu,
                                   const double* lapom, float* r1, float* r2, float* r3, float* q,
                                   double* partials, double* out, double* lap, cudaStream_t st,
-                                  int members, const double* c1m, bool pdl) {
+                                  int members, const double* c1m, bool pdl,
+                                  const DecideArgs* da, bool* decided) {
   const int wave = wave_blocks(k_defect64_point, (int64_t)L.n * L.n * L.n * members);
   int nbx = wave / members;
   const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
@@ -3228,9 +3264,7 @@ cudaError_t launch_defect64_point(const Lvl& L, const double* b, const double* m
   cudaError_t e = launch_ex(pdl, k_defect64_point, dim3(nbx, members), dim3(kReduceThreads), 0,
                             st, L, b, mu, om, S2, S3, lapb, lapmu, lapom, r1, r2, r3, q, partials,
                             lap, c1m);
-  if (e == cudaSuccess)
-    e = launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st,
-                  (const double*)partials, nbx, out);
+  if (e == cudaSuccess) e = launch_reduce1(pdl, partials, nbx, out, members, st, da, decided);
   return e;
 }
 
@@ -3239,7 +3273,8 @@ cudaError_t launch_start64_point(const Lvl& L, const double* b, const double* mu
                                  const double* lapmu, const double* lapom, double* S2,
                                  double* S3, double* phi_next, float* r1, float* r2, float* r3,
                                  float* q, double* partials, double* out, double* lap,
-                                 cudaStream_t st, int members, const double* c1m, bool pdl) {
+                                 cudaStream_t st, int members, const double* c1m, bool pdl,
+                                 const DecideArgs* da, bool* decided) {
   const int wave = wave_blocks(k_start64_point, (int64_t)L.n * L.n * L.n * members);
   int nbx = wave / members;
   const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
@@ -3248,9 +3283,7 @@ cudaError_t launch_start64_point(const Lvl& L, const double* b, const double* mu
   cudaError_t e = launch_ex(pdl, k_start64_point, dim3(nbx, members), dim3(kReduceThreads), 0,
                             st, L, b, mu, om, lapb, lapc, lapmu, lapom, S2, S3, phi_next, r1, r2,
                             r3, q, partials, lap, c1m);
-  if (e == cudaSuccess)
-    e = launch_ex(pdl, k_reduce1, dim3(members), dim3(kReduceThreads), 0, st,
-                  (const double*)partials, nbx, out);
+  if (e == cudaSuccess) e = launch_reduce1(pdl, partials, nbx, out, members, st, da, decided);
   return e;
 }
 
@@ -3464,13 +3497,14 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
                                  double* const S[3], const double* b, double* partials,
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
                                  int members, const double* c1m, double* const M[3],
-                                 double* lapmu, double* lapom, int planes) {
+                                 double* lapmu, double* lapom, int planes,
+                                 const DecideArgs* da, bool* decided) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64(L0, u[0], u[1], u[2], S[0], S[1], S[2], b, mx.r[0][0],
                                   mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, st, lap,
                                   members, c1m, M ? M[0] : nullptr, M ? M[1] : nullptr,
                                   M ? M[2] : nullptr, lapmu, lapom, !pr || pr->mask == 0,
-                                  planes);
+                                  planes, da, decided);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
@@ -3480,11 +3514,13 @@ cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* con
                                        const double* lapb, const double* lapmu,
                                        const double* lapom, double* lap, double* partials,
                                        double* dout, cudaStream_t st, Prof* pr, int members,
-                                       const double* c1m) {
+                                       const double* c1m, const DecideArgs* da,
+                                       bool* decided) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_defect64_point(L0, b, u[1], u[2], S[1], S[2], lapb, lapmu, lapom,
                                         mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0], partials,
-                                        dout, lap, st, members, c1m, !pr || pr->mask == 0);
+                                        dout, lap, st, members, c1m, !pr || pr->mask == 0, da,
+                                        decided);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }
@@ -3494,12 +3530,13 @@ cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* cons
                                       const double* lapb, const double* lapc,
                                       const double* lapmu, const double* lapom, double* lap,
                                       double* partials, double* dout, cudaStream_t st, Prof* pr,
-                                      int members, const double* c1m) {
+                                      int members, const double* c1m, const DecideArgs* da,
+                                      bool* decided) {
   prof_begin(pr, PFC_K_DEFECT, st);
   cudaError_t e = launch_start64_point(L0, b, u[1], u[2], lapb, lapc, lapmu, lapom, S[1], S[2],
                                        u[0], mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0],
                                        partials, dout, lap, st, members, c1m,
-                                       !pr || pr->mask == 0);
+                                       !pr || pr->mask == 0, da, decided);
   prof_end(pr, PFC_K_DEFECT, 0, 2, st);
   return e;
 }

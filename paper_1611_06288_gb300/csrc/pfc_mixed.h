@@ -60,27 +60,36 @@ cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, double* const u[3
                                  double* dout, cudaStream_t st, Prof* pr, double* lap,
                                  int members = 1, const double* c1m = nullptr,
                                  double* const M[3] = nullptr, double* lapmu = nullptr,
-                                 double* lapom = nullptr, int planes = 0);
+                                 double* lapom = nullptr, int planes = 0,
+                                 const DecideArgs* da = nullptr, bool* decided = nullptr);
 
 // The first defect of a step that starts from the previous step's solution
 // (phi := b, mu and omega kept), pointwise from the Laplacians of b, mu and
 // omega that the previous step's last defect stored; writes lapb to lap.
-// Start of a warm PFC_MIXED step in one launch (plus its reduction): S2, S3
-// into S[1], S[2], phi^{k+1} := b into u[0], and the pointwise first defect
-// (as mixed_enqueue_defect_point with those S2, S3); lapc is the stored
-// Laplacian of phi^{k-1}.
-cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
-                                      double* const S[3], const double* b,
-                                      const double* lapb, const double* lapc,
-                                      const double* lapmu, const double* lapom, double* lap,
-                                      double* partials, double* dout, cudaStream_t st, Prof* pr,
-                                      int members, const double* c1m);
 cudaError_t mixed_enqueue_defect_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
                                        double* const S[3], const double* b,
                                        const double* lapb, const double* lapmu,
                                        const double* lapom, double* lap, double* partials,
                                        double* dout, cudaStream_t st, Prof* pr, int members,
-                                       const double* c1m);
+                                       const double* c1m, const DecideArgs* da = nullptr,
+                                       bool* decided = nullptr);
+
+// Start of a warm PFC_MIXED step in one launch (plus its reduction): S2, S3
+// into S[1], S[2], phi^{k+1} := b into u[0], and the pointwise first defect
+// (as mixed_enqueue_defect_point with those S2, S3); lapc is the stored
+// Laplacian of phi^{k-1}.
+//
+// With da (the step's decision arguments) and a single member, each of
+// these three takes the convergence decision in its final reduction kernel
+// and sets *decided; otherwise *decided is false and the caller launches the
+// decision.
+cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                      double* const S[3], const double* b,
+                                      const double* lapb, const double* lapc,
+                                      const double* lapmu, const double* lapom, double* lap,
+                                      double* partials, double* dout, cudaStream_t st, Prof* pr,
+                                      int members, const double* c1m,
+                                      const DecideArgs* da = nullptr, bool* decided = nullptr);
 
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
@@ -154,7 +163,8 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             const double* c1m = nullptr, const double* Mx = nullptr,
                             const double* My = nullptr, const double* Mz = nullptr,
                             double* lapmu = nullptr, double* lapom = nullptr,
-                            bool pdl = false, int planes = 0);
+                            bool pdl = false, int planes = 0, const DecideArgs* da = nullptr,
+                            bool* decided = nullptr);
 // Face mobilities M(A phi_*), phi_* = 3/2 b - 1/2 c, M(phi) = m0 + m2 phi^2,
 // face i+1/2 of each axis stored at cell i (FP64).
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
