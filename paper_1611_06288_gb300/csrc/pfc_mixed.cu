@@ -293,6 +293,11 @@ __global__ void __launch_bounds__(256) k_defect64(Lvl L, const double* __restric
 // whose own value in the plane above is out of range does so alone.  Same
 // outputs either way.  Per-block partial sums of |r|^2 as k_defect64.
 constexpr int kFxTX = 32, kFxTY = 8;
+// Shared-memory ring of the fixed-point images of planes k-1, k, k+1 (own
+// cells, and the halo of plane k): four slots, so one barrier per plane
+// orders every write after the reads of the slot's previous plane.
+constexpr int kFxRing = 4;
+constexpr size_t kFxSmem = (size_t)kFxRing * 3 * (kFxTY + 2) * (kFxTX + 2) * sizeof(int64_t);
 
 // The three rows at one cell from the unscaled Laplacians, in 12 FP64
 // operations: x = S1 - phi + tau/h^2 Lap mu, y = S2 - mu + f + c1 phi +
@@ -317,7 +322,7 @@ __device__ __forceinline__ void defect_rows(const Lvl& L, double c1, float c1f, 
   qf = fmaf(0.75f * pf, pf, fmaf(0.5f * pf, bf, fmaf(0.25f * bf, bf, c1f)));
 }
 
-__global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
+__global__ void __launch_bounds__(kFxTX * kFxTY, 4) k_defect64_fx(
     Lvl L, int zc, const double* __restrict__ phi, const double* __restrict__ mu,
     const double* __restrict__ om, const double* __restrict__ S1, const double* __restrict__ S2,
     const double* __restrict__ S3, const double* __restrict__ b, float* __restrict__ r1,
@@ -326,18 +331,17 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
     double* __restrict__ lapom) {
   pdl_wait();
   pdl_trigger();
-  __shared__ int64_t tile[3][kFxTY + 2][kFxTX + 2];
+  extern __shared__ int64_t ring[];   // [kFxRing][3][kFxTY + 2][kFxTX + 2]
   __shared__ float sm[32];
+  constexpr int TW = kFxTX + 2, TP = (kFxTY + 2) * TW, TS = 3 * TP;
   const int n = L.n, nn = n * n;
   const int chunks = (n + zc - 1) / zc;
   int zb = blockIdx.z;
   const int m = member_of(zb, chunks);
-  const size_t off = (size_t)m * nn * n;
-  const bool s1_is_b = S1 == b;              // S1 = phi^k at the finest level
-  phi += off, mu += off, om += off, S1 += off, S2 += off, S3 += off, b += off;
-  r1 += off, r2 += off, r3 += off, q += off;
-  if (lap) lap += off;
-  if (lapmu) lapmu += off, lapom += off;
+  // the member's offset rides in the indices: the field pointers stay
+  // kernel parameters instead of occupying registers
+  const int64_t off = (int64_t)m * nn * n;
+  const bool s1_is_b = S1 == b;
   const double c1 = c1m ? c1m[m] : L.c1;
   const float c1f = d2f_rn(c1);
   const int tid = threadIdx.x, tx = tid % kFxTX, ty = tid / kFxTX;   // 1-D block
@@ -346,38 +350,38 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
   const bool active = i0 + tx < n && j0 + ty < n;
   const int iw = (i0 + tx) % n, jw = (j0 + ty) % n;     // wrapped own column
   const int own = jw * n + iw;
+  const int ocell = (ty + 1) * TW + tx + 1;              // own cell in a tile plane
   // halo cell of this thread (tid < 2 kFxTY + 2 kFxTX): in-plane index and
   // tile position
-  int hidx = -1, hy = 0, hx = 0;
+  int hidx = -1, hcell = 0;
   if (tid < 2 * kFxTY) {
     const int r = tid % kFxTY, side = tid / kFxTY;        // x = i0 - 1 or i0 + kFxTX
-    hy = r + 1;
-    hx = side ? kFxTX + 1 : 0;
+    hcell = (r + 1) * TW + (side ? kFxTX + 1 : 0);
     hidx = ((j0 + r) % n) * n + (side ? (i0 + kFxTX) % n : (i0 - 1 + n) % n);
   } else if (tid < 2 * kFxTY + 2 * kFxTX) {
     const int h = tid - 2 * kFxTY, c = h % kFxTX, side = h / kFxTX;   // y = j0 - 1 or j0 + kFxTY
-    hx = c + 1;
-    hy = side ? kFxTY + 1 : 0;
+    hcell = (side ? kFxTY + 1 : 0) * TW + c + 1;
     hidx = (side ? (j0 + kFxTY) % n : (j0 - 1 + n) % n) * n + (i0 + c) % n;
   }
-  const double* const fld[3] = {phi, mu, om};
-  // Software pipeline over the planes: at plane k the raw values of plane
-  // k+1 (own cell) and the halo of plane k arrived during plane k-1; the
-  // loads of plane k+2 and of the halo of plane k+1 are issued now.
-  // okc: the images this thread put in the tile so far are valid (block
-  // vote per plane); the own image of plane k+1 is checked per cell.
-  bool okc = true;
-  int64_t xm[3], xc[3];
-  double dc[3], dn[3], hraw[3];
+#define PFC_FX_FLD(f) ((f) == 0 ? phi : (f) == 1 ? mu : om)
+  // Software pipeline over the planes: the images of plane k+1 (own cells)
+  // are formed from raw values loaded during plane k-1 and stored in the
+  // ring slot of plane k+1; the halo of plane k arrives during plane k-1.
+  // ok: the own images this thread formed so far are in range (they enter
+  // the block vote of the next plane); okn: the own image of plane k+1,
+  // checked per cell.
+  bool ok = true;
+  double dn[3], hraw[3];
   {
     const int km = (k0 - 1 + n) % n, kp = (k0 + 1) % n;
 #pragma unroll
     for (int f = 0; f < 3; ++f) {
-      xm[f] = fix_of(__ldg(fld[f] + km * nn + own), okc);
-      dc[f] = __ldg(fld[f] + k0 * nn + own);
-      xc[f] = fix_of(dc[f], okc);
-      dn[f] = __ldg(fld[f] + kp * nn + own);
-      hraw[f] = hidx >= 0 ? __ldg(fld[f] + k0 * nn + hidx) : 0.0;
+      ring[((k0 + kFxRing - 1) % kFxRing) * TS + f * TP + ocell] =
+          fix_of(__ldg(PFC_FX_FLD(f) + off + km * nn + own), ok);
+      ring[(k0 % kFxRing) * TS + f * TP + ocell] =
+          fix_of(__ldg(PFC_FX_FLD(f) + off + k0 * nn + own), ok);
+      dn[f] = __ldg(PFC_FX_FLD(f) + off + kp * nn + own);
+      hraw[f] = hidx >= 0 ? __ldg(PFC_FX_FLD(f) + off + k0 * nn + hidx) : 0.0;
     }
   }
   bool fx_path = true;
@@ -386,65 +390,64 @@ __global__ void __launch_bounds__(kFxTX * kFxTY) k_defect64_fx(
     const int kp = (k + 1 == n) ? 0 : k + 1;
     const int kp2 = (kp + 1 == n) ? 0 : kp + 1;
     const int t = k * nn + own;
-    const double bb = __ldg(b + t), s2 = __ldg(S2 + t), s3 = __ldg(S3 + t);
-    const double s1 = s1_is_b ? bb : __ldg(S1 + t);
     const bool more = k + 1 < k1;
-    double dnn[3];
-#pragma unroll
-    for (int f = 0; f < 3; ++f) dnn[f] = more ? __ldg(fld[f] + kp2 * nn + own) : 0.0;
+    // kFxRing slots: the one written here (plane k+1) was last read two
+    // planes ago, so the barrier of the previous plane orders the accesses
+    int64_t* const cur = ring + (k % kFxRing) * TS;
+    int64_t* const nxt = ring + ((k + 1) % kFxRing) * TS;
+    const int64_t* const prv = ring + ((k + kFxRing - 1) % kFxRing) * TS;
     bool okn = true;
-    int64_t xn[3];
 #pragma unroll
-    for (int f = 0; f < 3; ++f) xn[f] = fix_of(dn[f], okn);
-    __syncthreads();                       // the previous plane's tile reads are done
-    bool okt = okc;
+    for (int f = 0; f < 3; ++f) nxt[f * TP + ocell] = fix_of(dn[f], okn);
 #pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      tile[f][ty + 1][tx + 1] = xc[f];
-      if (hidx >= 0) tile[f][hy][hx] = fix_of(hraw[f], okt);
+    for (int f = 0; f < 3; ++f)
+      dn[f] = more ? __ldg(PFC_FX_FLD(f) + off + kp2 * nn + own) : 0.0;
+    bool okt = ok;
+    if (hidx >= 0) {
+#pragma unroll
+      for (int f = 0; f < 3; ++f) cur[f * TP + hcell] = fix_of(hraw[f], okt);
     }
     fx_path = __syncthreads_and(fx_path && okt) != 0;
+    ok = okn;
     if (hidx >= 0 && more) {
 #pragma unroll
-      for (int f = 0; f < 3; ++f) hraw[f] = __ldg(fld[f] + kp * nn + hidx);
+      for (int f = 0; f < 3; ++f) hraw[f] = __ldg(PFC_FX_FLD(f) + off + kp * nn + hidx);
     }
     double lap3[3];
     if (fx_path && okn) {
 #pragma unroll
-      for (int f = 0; f < 3; ++f)
-        lap3[f] = fix_to_double(fix_lap(tile[f][ty + 1][tx], tile[f][ty + 1][tx + 2],
-                                        tile[f][ty][tx + 1], tile[f][ty + 2][tx + 1], xm[f],
-                                        xn[f], xc[f]));
+      for (int f = 0; f < 3; ++f) {
+        const int64_t* const c = cur + f * TP;
+        lap3[f] = fix_to_double(fix_lap(c[ocell - 1], c[ocell + 1], c[ocell - TW], c[ocell + TW],
+                                        prv[f * TP + ocell], nxt[f * TP + ocell], c[ocell]));
+      }
     } else {
       const Nb6 sn = nb6_at(t, iw, jw, k, n);
 #pragma unroll
-      for (int f = 0; f < 3; ++f) lap3[f] = fma(-6.0, dc[f], nbsum64(fld[f], sn));
+      for (int f = 0; f < 3; ++f)
+        lap3[f] = fma(-6.0, __ldg(PFC_FX_FLD(f) + off + t), nbsum64(PFC_FX_FLD(f) + off, sn));
     }
     if (active) {
+      const double bb = __ldg(b + off + t), s2 = __ldg(S2 + off + t), s3 = __ldg(S3 + off + t);
+      const double s1 = s1_is_b ? bb : __ldg(S1 + off + t);
       float xf, yf, zf, qf;
-      defect_rows(L, c1, c1f, dc[0], dc[1], dc[2], bb, lap3[1], lap3[2], lap3[0], s1, s2, s3,
-                  xf, yf, zf, qf);
+      // the centre values of plane k, loaded two planes ago, come from L1
+      defect_rows(L, c1, c1f, __ldg(phi + off + t), __ldg(mu + off + t), __ldg(om + off + t),
+                  bb, lap3[1], lap3[2], lap3[0], s1, s2, s3, xf, yf, zf, qf);
       acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
-      const int o = split_index(iw, jw, k, n);
+      const int64_t o = off + split_index(iw, jw, k, n);
       r1[o] = xf;
       r2[o] = yf;
       r3[o] = zf;
       q[o] = qf;
-      if (lap) lap[t] = lap3[0];
+      if (lap) lap[off + t] = lap3[0];
       if (lapmu) {
-        lapmu[t] = lap3[1];
-        lapom[t] = lap3[2];
+        lapmu[off + t] = lap3[1];
+        lapom[off + t] = lap3[2];
       }
     }
-    okc = okn;
-#pragma unroll
-    for (int f = 0; f < 3; ++f) {
-      xm[f] = xc[f];
-      xc[f] = xn[f];
-      dc[f] = dn[f];
-      dn[f] = dnn[f];
-    }
   }
+#undef PFC_FX_FLD
   acc = block_sum_f(acc, sm);
   if (tid == 0)
     partials[(size_t)m * (gridDim.x * gridDim.y * chunks) +
@@ -3175,16 +3178,25 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init, int have = 0) {
 }  // namespace
 
 // Planes per block of k_defect64_fx: the split of the n planes of a column
-// into chunks that minimises the busiest SM's load, ceil(blocks / SMs) x
-// (planes + 1/2 for the extra plane of z halo); 0 if even whole columns need
+// into chunks that minimises the waves of resident blocks times the planes
+// per block, ceil(blocks / (SMs x resident blocks per SM)) x (planes + 1/2
+// for the extra plane of z halo); 0 if even whole columns need
 // more partial-sum slots than `cap` (blocks = column tiles x chunks x
 // members).
 int fx_planes(int n, int members, int64_t cap) {
-  int dev = 0, sms = 0;
+  int dev = 0, sms = 0, occ = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       sms < 1)
     sms = 152;
+  // resident blocks per SM: the waves are counted in units of sms * occ
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_defect64_fx, kFxTX * kFxTY,
+                                                    kFxSmem) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  const int64_t slots = (int64_t)sms * occ;
   const int64_t tiles =
       (int64_t)((n + kFxTX - 1) / kFxTX) * ((n + kFxTY - 1) / kFxTY) * members;
   int best = 0;
@@ -3194,7 +3206,7 @@ int fx_planes(int n, int members, int64_t cap) {
     if ((n + zc - 1) / zc != chunks) continue;   // same split as a smaller count
     const int64_t blocks = tiles * chunks;
     if (blocks > cap || (int64_t)chunks * members > 65535) break;
-    const double cost = (double)((blocks + sms - 1) / sms) * (zc + 0.5);
+    const double cost = (double)((blocks + slots - 1) / slots) * (zc + 0.5);
     if (best == 0 || cost < best_cost) {
       best = zc;
       best_cost = cost;
@@ -3225,7 +3237,7 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
     if (zc > 0) {
       const int chunks = (L.n + zc - 1) / zc;
       const dim3 grid((L.n + kFxTX - 1) / kFxTX, (L.n + kFxTY - 1) / kFxTY, chunks * members);
-      cudaError_t e = launch_ex(pdl, k_defect64_fx, grid, dim3(kFxTX * kFxTY), 0, st, L, zc, phi,
+      cudaError_t e = launch_ex(pdl, k_defect64_fx, grid, dim3(kFxTX * kFxTY), kFxSmem, st, L, zc, phi,
                                 mu, om, S1, S2, S3, b, r1, r2, r3, q, partials, lap, c1m, lapmu,
                                 lapom);
       if (e == cudaSuccess)
