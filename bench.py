@@ -64,9 +64,10 @@ KERNEL_BYTES = {
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
 # The defect class of the mixed path averages a step's launches: two full
-# defects and the start of the step (k_start64_point).
-# Keyed by the finest level's size the capture ran at (other sizes: null).
-NCU_TRAFFIC = {}
+# defects (150.8 MB each) and the start of the step (k_start64_point,
+# 174.9 MB).  Keyed by the finest level's size the capture ran at (other
+# sizes: null).
+NCU_TRAFFIC = {("mixed", "defect", 128): 158.8e6}   # profiles/k_defect64_fx_128.md, k_start64_point_128.md
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
 # counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
