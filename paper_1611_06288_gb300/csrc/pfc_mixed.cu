@@ -1620,7 +1620,7 @@ __global__ void __launch_bounds__(kChTX * kChTY * kChTZ) k_restrict_chain32(
 // pointwise 3x3 solve does not read the cell's own value), so the values the
 // prolongation would put there are never used: the pass sees the same inputs
 // either way, and half of the fine-level traffic of the prolongation goes.
-constexpr int kPrTI = 32, kPrTJ = 8, kPrZ = 4;
+constexpr int kPrTI = 32, kPrTJ = 4, kPrZ = 8;
 
 template <bool ASSIGN, bool SKIP0>
 __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
@@ -1665,37 +1665,61 @@ __global__ void __launch_bounds__(kPrTI * kPrTJ) k_prolong_add32(
       }
     }
   }
-  // staging: every thread's loads are issued before any of them is stored
-  // (a fixed, unrolled count), so a block waits for one L2 round trip here
-  // instead of one per load
+  // staging: each thread loads its own column (x, y) = (tx + 1, ty + 1) of
+  // the tile and the first kHalo threads one cell of the halo ring each, on
+  // every plane; the periodic wraps (more than one when nc < kPrTI) and the
+  // column offsets are worked out once, so a load costs an add and a select.
+  // All loads are issued before any of them is stored, so a block waits for
+  // one L2 round trip here instead of one per load.
   {
-    constexpr int kPlane = (kPrTJ + 2) * kW;
-    constexpr int kPer = ((kPrZ + 2) * kPlane + kPrTI * kPrTJ - 1) / (kPrTI * kPrTJ);
-    const int total = (nz + 2) * kPlane;
-    float v[kPer];
+    constexpr int kHalo = 2 * kW + 2 * kPrTJ;
+    static_assert(kHalo <= kPrTI * kPrTJ, "one halo cell per thread at most");
+    const int t = threadIdx.x;
+    int hx = 0, hy = 0;
+    if (t < kW) {
+      hx = t;
+    } else if (t < 2 * kW) {
+      hx = t - kW;
+      hy = kPrTJ + 1;
+    } else if (t < kHalo) {
+      const int r = t - 2 * kW;
+      hx = r < kPrTJ ? 0 : kW - 1;
+      hy = 1 + (r < kPrTJ ? r : r - kPrTJ);
+    }
+    const bool halo = t < kHalo;
+    // (one conditional add or subtract once the grid is wider than the
+    // tile with its halo)
+    const auto wrap = [nc](int v) {
+      if (nc >= kPrTI + 2) return v < 0 ? v + nc : (v >= nc ? v - nc : v);
+      v %= nc;
+      return v < 0 ? v + nc : v;
+    };
+    // offset within a plane of the column (Ig, Jg), and its colour parity
+    const int Ia = wrap(I0 + tx), Ja = wrap(J0 + ty);
+    const int Ih = wrap(I0 + hx - 1), Jh = wrap(J0 + hy - 1);
+    const int oa = Ja * nc + (Ia >> 1), pa_ = (Ia + Ja) & 1;
+    const int oh = Jh * nc + (Ih >> 1), ph = (Ih + Jh) & 1;
+    const int plane = nc * nc;
+    float va[kPrZ + 2], vh[kPrZ + 2];
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int t = threadIdx.x + i * (kPrTI * kPrTJ);
-      v[i] = 0.f;
-      if (t < total) {
-        const int z = t / kPlane, rem = t - z * kPlane, y = rem / kW, x = rem - y * kW;
-        // periodic wraps without a division (the tile may exceed the grid
-        // when nc < kPrTI: then more than one wrap)
-        int Ig = I0 + x - 1, Jg = J0 + y - 1, Kg = K0 + z - 1;
-        if (Ig < 0) Ig += nc;
-        while (Ig >= nc) Ig -= nc;
-        if (Jg < 0) Jg += nc;
-        while (Jg >= nc) Jg -= nc;
+    for (int z = 0; z < kPrZ + 2; ++z) {
+      va[z] = 0.f;
+      vh[z] = 0.f;
+      if (z < nz + 2) {
+        int Kg = K0 + z - 1;
         if (Kg < 0) Kg += nc;
-        while (Kg >= nc) Kg -= nc;
-        v[i] = __ldg(e + (Kg * nc + Jg) * nc + ((Ig + Jg + Kg) & 1) * hc + (Ig >> 1));
+        if (Kg >= nc) Kg -= nc;
+        const float* const ep = e + Kg * plane;
+        va[z] = __ldg(ep + oa + ((pa_ ^ Kg) & 1) * hc);
+        if (halo) vh[z] = __ldg(ep + oh + ((ph ^ Kg) & 1) * hc);
       }
     }
-    float* const flat = &sh[0][0][0];
 #pragma unroll
-    for (int i = 0; i < kPer; ++i) {
-      const int t = threadIdx.x + i * (kPrTI * kPrTJ);
-      if (t < total) flat[t] = v[i];
+    for (int z = 0; z < kPrZ + 2; ++z) {
+      if (z < nz + 2) {
+        sh[z][ty + 1][tx + 1] = va[z];
+        if (halo) sh[z][hy][hx] = vh[z];
+      }
     }
   }
   __syncthreads();
@@ -1752,15 +1776,19 @@ ProlongKernel prolong_kernel(bool assign, bool skip0) {
   return skip0 ? k_prolong_add32<false, true> : k_prolong_add32<false, false>;
 }
 
-// Coarse planes per block of k_prolong_add32: the most (<= kPrZ) that still
-// leave about two waves of blocks on the device (fewer planes per block for
-// the smaller levels, whose grids are short).
+// Coarse planes per block of k_prolong_add32: the most (8, 4 or 2) that
+// still give about one wave of blocks at five resident blocks per SM, else 2.
+// Measured in-graph per launch (us; 2 / 4 / 8 planes): 256^3 add 70.6 / 53.7
+// / 42.3, 128^3 add 9.2 / 6.8 / 6.1, 128^3 assign 6.8 / 5.8 / 5.0, 64^3
+// assign 2.3 / 2.4 / 2.6, 32^3 assign 1.7 / 2.0 / 2.5 (one plane per block:
+// slower everywhere): a block amortises its setup and halo planes over more
+// planes, until the short grids of the small levels run out of blocks.
 int prolong_planes(int nc, int comps_members) {
   const int64_t tiles = (int64_t)((nc + kPrTI - 1) / kPrTI) * ((nc + kPrTJ - 1) / kPrTJ) *
                         comps_members;
-  for (int zc = kPrZ; zc > 1; zc >>= 1)
-    if (tiles * ((nc + zc - 1) / zc) >= 2 * 4 * 152) return zc;
-  return 1;
+  for (int zc = kPrZ; zc > 2; zc >>= 1)
+    if (tiles * ((nc + zc - 1) / zc) >= 5 * 152) return zc;
+  return 2;
 }
 
 dim3 prolong_grid(int nc, int zc, int comps_members) {

@@ -467,9 +467,10 @@ def test_linear_prolong_fp32(n, assign, skip0):
 
 @pytest.mark.parametrize("skip0", [False, True])
 def test_linear_prolong_fp32_multiplane(skip0):
-    """At 204^3 the kernel's blocks take four coarse planes each (102 coarse
-    planes: 25 full chunks and a ragged one of two) and the grid has four
-    x tiles, the last one ragged: d += P e against the oracle."""
+    """At 204^3 the kernel's blocks take eight coarse planes each (102 coarse
+    planes: 12 full chunks and a ragged one of six), and the grid's last x
+    tile (6 of 32 columns) and last y tile (2 of 4 rows) are ragged: d += P e
+    against the oracle."""
     n, nc = 204, 102
     rng = np.random.default_rng(5)
     e = [rng.standard_normal((nc,) * 3).astype(np.float32) for _ in range(3)]
