@@ -260,6 +260,10 @@ def vcycle_bytes(params, levels):
         if kind == B.PFC_SWEEP_JACOBI:
             sweeps = params.nu2 * (params.jacobi_factor0 if first else params.jacobi_factor)
             total += cells * (40.0 * sweeps + (24.0 if sweeps % 2 else 0.0))
+            if sweeps > 0 and m % 32 == 0:
+                # the prolongation fused into the first sweep: d + P e stays
+                # in shared memory (not written, not read back)
+                total -= cells * 24.0
         else:
             total += cells * 40.0 * params.nu2
     return total

@@ -663,6 +663,23 @@ int pfc_op_lin_prolong(int n, int assign, const float* d_e1, const float* d_e2,
                        const float* d_e3, float* d_d1, float* d_d2, float* d_d3,
                        void* stream);
 
+/* The V-cycle's way up on one level: d (+)= P e, exactly as
+ * pfc_op_lin_prolong (PFC_PROLONG_ASSIGN in `assign`: d = P e, d not read),
+ * followed by one post-smoothing sweep of `kind` on J d = r (q frozen):
+ * PFC_SWEEP_RB, one red-black sweep as pfc_op_lin_smooth with sweeps = 1;
+ * PFC_SWEEP_JACOBI, one damped collective Jacobi sweep of `weight` as
+ * pfc_op_lin_jacobi with sweeps = 1 (d_t1..3 scratch).  The prolongation is
+ * fused into the first pass (the colour-0 pass, or the Jacobi sweep), which
+ * forms d_old + P e in shared memory instead of memory; the result in
+ * d_d1..3 equals the separate entry points bit for bit.  n a multiple of 32
+ * (PFC_EINVAL otherwise); d_e1..3 colour-split of (n/2)^3 cells. */
+int pfc_op_lin_prolong_smooth(int n, double h, double eps, double tau, int kind,
+                              int assign, double weight, const float* d_e1,
+                              const float* d_e2, const float* d_e3, float* d_d1,
+                              float* d_d2, float* d_d3, float* d_t1, float* d_t2,
+                              float* d_t3, const float* d_r1, const float* d_r2,
+                              const float* d_r3, const float* d_q, void* stream);
+
 /* u += d for the three components: df fields d_u1..3 plus the colour-split
  * FP32 corrections d_d1..3, in double-float.  n even. */
 int pfc_op_correct_df(int n, float* d_u1, float* d_u2, float* d_u3,

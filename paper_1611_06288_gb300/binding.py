@@ -116,6 +116,7 @@ _SIGS = {
     "pfc_op_lin_residual_restrict": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_lin_restrict_chain": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 16 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
+    "pfc_op_lin_prolong_smooth": (_I, [_I, _D, _D, _D, _I, _I, _D] + [_P] * 13 + [_P]),
     "pfc_op_restrict_q": (_I, [_I, _I] + [_P] * 4 + [_P]),
     "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_guess_df": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
@@ -499,6 +500,17 @@ def pfc_op_lin_prolong(n, assign, e1, e2, e3, d1, d2, d3, stream=None):
     """assign: a bool, or the flags PFC_PROLONG_ASSIGN | PFC_PROLONG_SKIP_COLOUR0."""
     check(lib().pfc_op_lin_prolong(n, int(assign), ptr(e1), ptr(e2), ptr(e3), ptr(d1),
                                    ptr(d2), ptr(d3), stream), "pfc_op_lin_prolong")
+
+
+def pfc_op_lin_prolong_smooth(n, h, eps, tau, kind, assign, weight, e1, e2, e3, d1, d2, d3,
+                              t1, t2, t3, r1, r2, r3, q, stream=None):
+    """d (+)= P e and one post-smoothing sweep of `kind` (PFC_SWEEP_RB or
+    PFC_SWEEP_JACOBI), the prolongation fused into the first pass."""
+    check(lib().pfc_op_lin_prolong_smooth(n, h, eps, tau, kind,
+                                          PFC_PROLONG_ASSIGN if assign else 0, weight,
+                                          *[ptr(x) for x in (e1, e2, e3, d1, d2, d3, t1, t2, t3,
+                                                             r1, r2, r3, q)], stream),
+          "pfc_op_lin_prolong_smooth")
 
 
 def pfc_op_guess(n, h, eps, b, c, S2, S3, phi, mu, om, stream=None):

@@ -1762,6 +1762,22 @@ int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, cons
   return PFC_OK;
 }
 
+int pfc_op_lin_prolong_smooth(int n, double h, double eps, double tau, int kind, int assign,
+                              double weight, const float* e1, const float* e2, const float* e3,
+                              float* d1, float* d2, float* d3, float* t1, float* t2, float* t3,
+                              const float* r1, const float* r2, const float* r3, const float* q,
+                              void* stream) {
+  if (n < 32 || n % 32 != 0 || !(h > 0) || (kind != PFC_SWEEP_RB && kind != PFC_SWEEP_JACOBI) ||
+      (assign != 0 && assign != PFC_PROLONG_ASSIGN) || !e1 || !e2 || !e3 || !d1 || !d2 || !d3 ||
+      !t1 || !t2 || !t3 || !r1 || !r2 || !r3 || !q ||
+      (kind == PFC_SWEEP_JACOBI && !(weight > 0 && weight <= 1)))
+    return PFC_EINVAL;
+  PFC_CUDA(launch_lin_prolong_smooth32(make_lvl(n, h, eps, tau), kind, assign != 0, (float)weight,
+                                       e1, e2, e3, d1, d2, d3, t1, t2, t3, r1, r2, r3, q,
+                                       (cudaStream_t)stream));
+  return PFC_OK;
+}
+
 int pfc_op_correct(int n, double* u1, double* u2, double* u3, const float* d1,
                    const float* d2, const float* d3, void* stream) {
   if (n < 2 || (n & 1) || !u1 || !u2 || !u3 || !d1 || !d2 || !d3) return PFC_EINVAL;

@@ -1796,6 +1796,236 @@ dim3 prolong_grid(int nc, int zc, int comps_members) {
               ((nc + zc - 1) / zc) * comps_members);
 }
 
+// ---------------------------------------------------------------------------
+// Prolongation fused into the smoothing pass that follows it.  Inside the
+// V-cycle the corrected d = d_old + P e of a level is read next by one pass
+// only: the first damped Jacobi sweep (d -> t) on a Jacobi level, the
+// colour-0 pass on a red-black level (which reads colour-1 cells alone, as
+// neighbours; the colour-1 pass after it overwrites them without reading
+// them).  So one launch forms d_old + P e on its tile and the tile's one-cell
+// halo in shared memory and runs that pass from there: the prolonged values
+// never go to global memory, and a launch goes.  Every value is formed with
+// the operations of k_prolong_add32 in its order (z, then y, then x, the
+// 1/64 scale, then the old value) and of k_lin_jacobi32x2 /
+// k_lin_smooth32x2 (sums ((xm + xp) + (ym + yp)) + (zm + zp), lin_point),
+// so the result equals the two launches bit for bit.
+//
+// A block owns a tile of kPsTX x TY x TZ fine cells in natural order (n a
+// multiple of kPsTX, TY and TZ) of one ensemble member:
+//   1. the coarse values under the tile and its halo, (kPsTX/2 + 2) x
+//      (TY/2 + 2) x (TZ/2 + 2) cells of each component;
+//   2. their z interpolation onto each of the TZ + 2 fine planes;
+//   3. the fine values d_old + P e (P e alone for ASSIGN) on the tile and its
+//      halo (the colour-1 cells alone for the red-black pass);
+//   4. the pass on the tile's cells, r and q loaded at the start.
+// RB0 (red-black): d's colour-0 cells are written, its colour-1 cells keep
+// d_old; JACOBI: t = d + w (solve - d), d is not written.
+// ---------------------------------------------------------------------------
+constexpr int kPsTX = 32;
+
+template <int TY, int TZ>
+struct PsTile {
+  static constexpr int TX = kPsTX, NT = TX * TY;
+  static constexpr int FX = TX + 2, FY = TY + 2, FZ = TZ + 2;             // fine + halo
+  static constexpr int CX = TX / 2 + 2, CY = TY / 2 + 2, CZ = TZ / 2 + 2;  // coarse under it
+  static constexpr int kF = FZ * FY * FX;          // per component
+  static constexpr int kC = CZ * CY * CX;
+  static constexpr int kZ = FZ * CY * CX;
+  // the coarse values are dead once the fine ones are formed: one buffer
+  static constexpr int kFC = 3 * (kF > kC ? kF : kC);
+  static constexpr int kSmem = kFC + 3 * kZ;       // floats
+  static constexpr int kCols = (FX * FY + NT - 1) / NT;   // halo-tile columns per thread
+};
+
+template <int TY, int TZ, bool JACOBI, bool ASSIGN>
+__global__ void __launch_bounds__(kPsTX * TY) k_lin_prolong_sweep32(
+    LvlF L, float w, const float* __restrict__ e1, const float* __restrict__ e2,
+    const float* __restrict__ e3, float* d1, float* d2, float* d3, float* __restrict__ t1,
+    float* __restrict__ t2, float* __restrict__ t3, const float* __restrict__ r1,
+    const float* __restrict__ r2, const float* __restrict__ r3, const float* __restrict__ q) {
+  pdl_wait();
+  pdl_trigger();
+  using T = PsTile<TY, TZ>;
+  constexpr int TX = T::TX, NT = T::NT, FX = T::FX, FY = T::FY, FZ = T::FZ;
+  constexpr int CX = T::CX, CY = T::CY;
+  // cells of the pass per thread: Jacobi every cell of its column over TZ
+  // planes; red-black the colour-0 cells, two threads per column position
+  constexpr int kCells = JACOBI ? TZ : TZ / 2;
+  static_assert(JACOBI || (TZ % 2 == 0 && NT == 2 * (TX / 2) * TY), "tile");
+  __shared__ float sm[T::kSmem];
+  float* const sFC = sm;
+  float* const sZ = sm + T::kFC;
+  const int n = L.n, half = n >> 1, nc = n >> 1, hc = nc >> 1;
+  int kz = blockIdx.z;
+  const int m = member_of(kz, n / TZ);
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = kz * TZ;
+  const size_t offf = (size_t)m * n * n * n, offc = (size_t)m * nc * nc * nc;
+  const int tid = threadIdx.x;
+
+  // 0. the pass's cells: split indices, r and q (independent of the rest)
+  int px, py, pz0, pstep;
+  if (JACOBI) {
+    px = tid % TX;
+    py = tid / TX;
+    pz0 = 0;
+    pstep = 1;
+  } else {
+    const int p = tid % (TX / 2);
+    py = (tid / (TX / 2)) % TY;
+    pz0 = tid / ((TX / 2) * TY);
+    pstep = 2;
+    px = 2 * p;                     // + the row's colour-0 offset below
+  }
+  int sc[kCells], fx[kCells];
+  float rq[kCells][4];
+#pragma unroll
+  for (int s = 0; s < kCells; ++s) {
+    const int z = pz0 + s * pstep, j = j0 + py, k = k0 + z;
+    const int x = JACOBI ? px : px + ((j + k) & 1);
+    const int i = i0 + x, colour = (i + j + k) & 1;
+    fx[s] = x;
+    sc[s] = (k * n + j) * n + colour * half + (i >> 1);
+    rq[s][0] = __ldg(r1 + offf + sc[s]);
+    rq[s][1] = __ldg(r2 + offf + sc[s]);
+    rq[s][2] = __ldg(r3 + offf + sc[s]);
+    rq[s][3] = __ldg(q + offf + sc[s]);
+  }
+
+  // 1. coarse values: (I, J, K) = (i0/2 - 1 + cx, j0/2 - 1 + cy, k0/2 - 1 + cz)
+  {
+    constexpr int kPer = (T::kC + NT - 1) / NT;
+    float v[kPer][3];
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      const int idx = tid + s * NT;
+      v[s][0] = v[s][1] = v[s][2] = 0.f;
+      if (idx < T::kC) {
+        const int cz = idx / (CY * CX), rem = idx - cz * (CY * CX);
+        const int cy = rem / CX, cx = rem - cy * CX;
+        int I = (i0 >> 1) - 1 + cx, J = (j0 >> 1) - 1 + cy, K = (k0 >> 1) - 1 + cz;
+        I = I < 0 ? I + nc : (I >= nc ? I - nc : I);
+        J = J < 0 ? J + nc : (J >= nc ? J - nc : J);
+        K = K < 0 ? K + nc : (K >= nc ? K - nc : K);
+        const int g = (K * nc + J) * nc + ((I + J + K) & 1) * hc + (I >> 1);
+        v[s][0] = __ldg(e1 + offc + g);
+        v[s][1] = __ldg(e2 + offc + g);
+        v[s][2] = __ldg(e3 + offc + g);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kPer; ++s) {
+      const int idx = tid + s * NT;
+      if (idx < T::kC) {
+        sFC[idx] = v[s][0];
+        sFC[T::kC + idx] = v[s][1];
+        sFC[2 * T::kC + idx] = v[s][2];
+      }
+    }
+  }
+  __syncthreads();
+
+  // 2. z interpolation onto fine plane k0 - 1 + zf: coarse plane index (in
+  // the tile) kr = ((zf - 1) >> 1) + 1, the other one below for an even
+  // fine plane, above for an odd one
+  for (int idx = tid; idx < FZ * CY * CX; idx += NT) {
+    const int zf = idx / (CY * CX), col = idx - zf * (CY * CX);
+    const int kr = ((zf - 1) >> 1) + 1, k2r = ((zf + 1) & 1) ? kr + 1 : kr - 1;
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+      sZ[f * T::kZ + idx] = fmaf(3.f, sFC[f * T::kC + kr * (CY * CX) + col],
+                                 sFC[f * T::kC + k2r * (CY * CX) + col]);
+  }
+  __syncthreads();
+
+  // 3. fine values on the tile with its halo: column (xf, yf) = fine (i0 -
+  // 1 + xf, j0 - 1 + yf), planes k0 - 1 .. k0 + TZ
+  {
+    float old[T::kCols][FZ][3];
+#pragma unroll
+    for (int s = 0; s < T::kCols; ++s)
+#pragma unroll
+      for (int zf = 0; zf < FZ; ++zf) old[s][zf][0] = old[s][zf][1] = old[s][zf][2] = 0.f;
+    if (!ASSIGN) {
+#pragma unroll
+      for (int s = 0; s < T::kCols; ++s) {
+        const int col = tid + s * NT;
+        if (col < FX * FY) {
+          const int yf = col / FX, xf = col - yf * FX;
+          int i = i0 - 1 + xf, j = j0 - 1 + yf;
+          const int par = (i + j) & 1;
+          i = i < 0 ? i + n : (i >= n ? i - n : i);
+          j = j < 0 ? j + n : (j >= n ? j - n : j);
+#pragma unroll
+          for (int zf = 0; zf < FZ; ++zf) {
+            const int colour = (par + k0 - 1 + zf) & 1;
+            if (!JACOBI && colour == 0) continue;
+            int k = k0 - 1 + zf;
+            k = k < 0 ? k + n : (k >= n ? k - n : k);
+            const int g = (k * n + j) * n + colour * half + (i >> 1);
+            old[s][zf][0] = __ldg(d1 + offf + g);
+            old[s][zf][1] = __ldg(d2 + offf + g);
+            old[s][zf][2] = __ldg(d3 + offf + g);
+          }
+        }
+      }
+    }
+    // (the coarse values are dead since the barrier above: their buffer
+    // takes the fine values)
+#pragma unroll
+    for (int s = 0; s < T::kCols; ++s) {
+      const int col = tid + s * NT;
+      if (col < FX * FY) {
+        const int yf = col / FX, xf = col - yf * FX;
+        const int par = (i0 - 1 + xf + j0 - 1 + yf) & 1;
+        // coarse columns (in the tile) under this fine column: the own one and
+        // the other one on the child's side, in x and in y
+        const int ir = ((xf - 1) >> 1) + 1, i2r = ((xf + 1) & 1) ? ir + 1 : ir - 1;
+        const int jr = ((yf - 1) >> 1) + 1, j2r = ((yf + 1) & 1) ? jr + 1 : jr - 1;
+#pragma unroll
+        for (int zf = 0; zf < FZ; ++zf) {
+          const int colour = (par + k0 - 1 + zf) & 1;
+          if (!JACOBI && colour == 0) continue;
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            const float* const Z = sZ + f * T::kZ + zf * (CY * CX);
+            const float ya = fmaf(3.f, Z[jr * CX + ir], Z[j2r * CX + ir]);
+            const float yb = fmaf(3.f, Z[jr * CX + i2r], Z[j2r * CX + i2r]);
+            const float v = (1.f / 64.f) * fmaf(3.f, ya, yb);
+            sFC[f * T::kF + (zf * FY + yf) * FX + xf] = v + old[s][zf][f];
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // 4. the pass
+#pragma unroll
+  for (int s = 0; s < kCells; ++s) {
+    const int z = pz0 + s * pstep;
+    const int c = ((z + 1) * FY + (py + 1)) * FX + (fx[s] + 1);
+    float sum[3], own[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      const float* const F = sFC + f * T::kF;
+      sum[f] = ((F[c - 1] + F[c + 1]) + (F[c - FX] + F[c + FX])) +
+               (F[c - FY * FX] + F[c + FY * FX]);
+      own[f] = F[c];
+    }
+    float dp, dm, dw;
+    lin_point(L, sum[0], sum[1], sum[2], rq[s][3], rq[s][0], rq[s][1], rq[s][2], dp, dm, dw);
+    if (JACOBI) {
+      t1[offf + sc[s]] = fmaf(w, dp - own[0], own[0]);
+      t2[offf + sc[s]] = fmaf(w, dm - own[1], own[1]);
+      t3[offf + sc[s]] = fmaf(w, dw - own[2], own[2]);
+    } else {
+      d1[offf + sc[s]] = dp;
+      d2[offf + sc[s]] = dm;
+      d3[offf + sc[s]] = dw;
+    }
+  }
+}
+
 // Coarsest level of the linear problem when it is not part of a tail launch:
 // start from zero, sweeps in one block (red-black, kind 0, or damped Jacobi
 // through t, kind 1) until the largest change is below 1e-6 of the largest
@@ -2883,15 +3113,21 @@ struct Ctx32 {
 };
 
 // `sweeps` damped Jacobi sweeps d -> t -> d ...; the result ends in d.
+// in_t: the current iterate is in t (the sweeps run t -> d -> t ...).
 cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* const* d,
                      float* const* t, float* const* r, const float* q, cudaStream_t st,
-                     bool pdl, int nb = 1) {
+                     bool pdl, int nb = 1, bool in_t = false) {
   const int n = L.n;
   const int64_t cells = (int64_t)n * n * n * nb;
   const bool pairs = n % 4 == 0;                // two cells per thread, float2 moves
   const Launch3 g = launch3(pairs ? n / 2 : n, n, n * nb);
   float* src[3] = {d[0], d[1], d[2]};
   float* dst[3] = {t[0], t[1], t[2]};
+  if (in_t)
+    for (int c = 0; c < 3; ++c) {
+      src[c] = t[c];
+      dst[c] = d[c];
+    }
   int done = 0;
   cudaError_t e = cudaSuccess;
   while (done < sweeps && e == cudaSuccess) {
@@ -2915,6 +3151,21 @@ cudaError_t jacobi32(const LvlF& L, int sweeps, float w, bool zero_init, float* 
   return e;
 }
 
+// One colour pass of a red-black sweep on level l.
+cudaError_t rb_pass32(const Ctx32& c, int l, int colour, bool zero) {
+  const LvlF& L = c.L[l];
+  float* const* d = c.mx->d[l];
+  float* const* r = c.mx->r[l];
+  const float* q = c.mx->q[l];
+  const bool pairs = L.n % 4 == 0;              // two cells per thread, float2 moves
+  const Launch3 g = launch3(pairs ? L.n / 4 : L.n / 2, L.n, L.n * c.nb);
+  if (pairs)
+    return launch_k(c.pr == nullptr, zero ? k_lin_smooth32x2<true> : k_lin_smooth32x2<false>,
+                    g.grid, g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
+  return launch_k(c.pr == nullptr, zero ? k_lin_smooth32<true> : k_lin_smooth32<false>, g.grid,
+                  g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
+}
+
 cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   const LvlF& L = c.L[l];
   float* const* d = c.mx->d[l];
@@ -2929,21 +3180,56 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
     prof_end(c.pr, PFC_K_LIN_SMOOTH, l, js, c.st);
     return e;
   }
-  const bool pairs = L.n % 4 == 0;              // two cells per thread, float2 moves
-  const Launch3 g = launch3(pairs ? L.n / 4 : L.n / 2, L.n, L.n * c.nb);
   cudaError_t e = cudaSuccess;
-  for (int s = 0; s < sweeps && e == cudaSuccess; ++s) {
-    for (int colour = 0; colour < 2 && e == cudaSuccess; ++colour) {
-      const bool z = zero_init && s == 0 && colour == 0;
-      if (pairs)
-        e = launch_k(c.pr == nullptr, z ? k_lin_smooth32x2<true> : k_lin_smooth32x2<false>,
-                     g.grid, g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
-      else
-        e = launch_k(c.pr == nullptr, z ? k_lin_smooth32<true> : k_lin_smooth32<false>,
-                     g.grid, g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
-    }
-  }
+  for (int s = 0; s < sweeps && e == cudaSuccess; ++s)
+    for (int colour = 0; colour < 2 && e == cudaSuccess; ++colour)
+      e = rb_pass32(c, l, colour, zero_init && s == 0 && colour == 0);
   prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps, c.st);
+  return e;
+}
+
+// Whether the prolongation into a level of n^3 cells fuses with the first
+// of `sweeps` post-smoothing sweeps (k_lin_prolong_sweep32's tiles).
+bool prolong_fuses(int n, int sweeps) { return sweeps > 0 && n >= kPsTX && n % kPsTX == 0; }
+
+template <int TY, int TZ>
+cudaError_t launch_prolong_sweep(const Ctx32& c, int l, bool jacobi, bool assign) {
+  MixedBufs& mx = *c.mx;
+  const int n = c.L[l].n;
+  const dim3 grid(n / kPsTX, n / TY, (n / TZ) * c.nb), block(kPsTX * TY);
+  auto k = jacobi ? (assign ? k_lin_prolong_sweep32<TY, TZ, true, true>
+                            : k_lin_prolong_sweep32<TY, TZ, true, false>)
+                  : (assign ? k_lin_prolong_sweep32<TY, TZ, false, true>
+                            : k_lin_prolong_sweep32<TY, TZ, false, false>);
+  float* const* e = mx.d[l + 1];
+  return launch_k(c.pr == nullptr, k, grid, block, 0, c.st, c.L[l], c.w, (const float*)e[0],
+                  (const float*)e[1], (const float*)e[2], mx.d[l][0], mx.d[l][1], mx.d[l][2],
+                  mx.t[l][0], mx.t[l][1], mx.t[l][2], (const float*)mx.r[l][0],
+                  (const float*)mx.r[l][1], (const float*)mx.r[l][2], (const float*)mx.q[l]);
+}
+
+// d (+)= P e from level l + 1, then `sweeps` post-smoothing sweeps on level
+// l (damped Jacobi sweeps, or red-black sweeps), the prolongation fused into
+// the first pass (prolong_fuses must hold).  The result is in d.
+cudaError_t prolong_smooth32(const Ctx32& c, int l, bool assign, int sweeps) {
+  const bool jacobi = c.kind[l] == PFC_SWEEP_JACOBI;
+  prof_begin(c.pr, PFC_K_LIN_PROLONG, c.st);
+  cudaError_t e = c.L[l].n >= 64 ? launch_prolong_sweep<8, 4>(c, l, jacobi, assign)
+                                 : launch_prolong_sweep<4, 2>(c, l, jacobi, assign);
+  prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
+  if (e != cudaSuccess) return e;
+  if (jacobi) {
+    // the first sweep left its result in t
+    prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
+    e = jacobi32(c.L[l], sweeps - 1, c.w, false, c.mx->d[l], c.mx->t[l], c.mx->r[l], c.mx->q[l],
+                 c.st, c.pr == nullptr, c.nb, true);
+    prof_end(c.pr, PFC_K_LIN_SMOOTH, l, sweeps - 1, c.st);
+    return e;
+  }
+  prof_begin(c.pr, PFC_K_LIN_SMOOTH, c.st);
+  e = rb_pass32(c, l, 1, false);
+  prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 1, c.st);
+  if (e == cudaSuccess && sweeps > 1) e = smooth32(c, l, sweeps - 1, false);
   return e;
 }
 
@@ -3190,6 +3476,15 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init, int have = 0) {
   }
   if (e != cudaSuccess) return e;
   if ((e = vcycle32(c, l + 1, true, below)) != cudaSuccess) return e;
+  const int post = c.kind[l] == PFC_SWEEP_JACOBI
+                       ? c.p->nu2 * (l == 0 ? c.jfactor0 : c.jfactor)
+                       : c.p->nu2;
+  // fused on Jacobi levels only: on a red-black level the fused colour-0
+  // pass formed every colour-1 value of its tile and halo per cell (25 us
+  // per launch at 128^3 against 6.1 + 6.5 us for the prolongation's
+  // coarse-column carry and the plain pass)
+  if (c.kind[l] == PFC_SWEEP_JACOBI && prolong_fuses(L.n, post))
+    return prolong_smooth32(c, l, dzero, post);
   const int pz = prolong_planes(nc, 3 * c.nb);
   // a red-black post-smoothing pass of colour 0 comes next: it recomputes
   // the colour-0 cells without reading them
@@ -3515,6 +3810,40 @@ cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float*
   c.st = st;
   c.pr = nullptr;
   return smooth32(c, 0, sweeps, zero_init);
+}
+
+cudaError_t launch_lin_prolong_smooth32(const Lvl& L, int kind, bool assign, float w,
+                                       const float* e1, const float* e2, const float* e3,
+                                       float* d1, float* d2, float* d3, float* t1, float* t2,
+                                       float* t3, const float* r1, const float* r2,
+                                       const float* r3, const float* q, cudaStream_t st) {
+  if (!prolong_fuses(L.n, 1)) return cudaErrorInvalidValue;
+  MixedBufs mx;
+  mx.d[0][0] = d1;
+  mx.d[0][1] = d2;
+  mx.d[0][2] = d3;
+  mx.t[0][0] = t1;
+  mx.t[0][1] = t2;
+  mx.t[0][2] = t3;
+  mx.r[0][0] = (float*)r1;
+  mx.r[0][1] = (float*)r2;
+  mx.r[0][2] = (float*)r3;
+  mx.q[0] = (float*)q;
+  mx.d[1][0] = (float*)e1;
+  mx.d[1][1] = (float*)e2;
+  mx.d[1][2] = (float*)e3;
+  Ctx32 c;
+  c.mx = &mx;
+  c.p = nullptr;
+  c.nl = 2;
+  c.L[0] = to_f32(L);
+  c.kind[0] = kind;
+  c.w = w;
+  c.jfactor = 1;
+  c.jfactor0 = 1;
+  c.st = st;
+  c.pr = nullptr;
+  return prolong_smooth32(c, 0, assign, 1);
 }
 
 cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_init,

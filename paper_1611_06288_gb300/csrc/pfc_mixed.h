@@ -200,6 +200,14 @@ cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, co
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
                                 float* d2, float* d3, const float* r1, const float* r2,
                                 const float* r3, const float* q, cudaStream_t st);
+// d (+)= P e (e of (n/2)^3 cells) and one post-smoothing sweep of `kind`
+// (PFC_SWEEP_RB or PFC_SWEEP_JACOBI, weight w; t is Jacobi scratch) in one
+// fused launch plus the rest of the sweep; n a multiple of 32.
+cudaError_t launch_lin_prolong_smooth32(const Lvl& L, int kind, bool assign, float w,
+                                       const float* e1, const float* e2, const float* e3,
+                                       float* d1, float* d2, float* d3, float* t1, float* t2,
+                                       float* t3, const float* r1, const float* r2,
+                                       const float* r3, const float* q, cudaStream_t st);
 cudaError_t launch_lin_jacobi32(const Lvl& L, int sweeps, float w, bool zero_init,
                                 float* d1, float* d2, float* d3, float* t1, float* t2,
                                 float* t3, const float* r1, const float* r2, const float* r3,

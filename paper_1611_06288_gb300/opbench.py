@@ -17,6 +17,12 @@ op's algorithmic bytes (each field read or written once per call):
   lin_prolong        d += P e: d read and written: 24 B per fine cell (+ the
                      coarse e); the _skip0 forms touch the colour-1 half only
                      (12 B), the _assign forms write d only (12 B, 6 B)
+  lin_jacobi         one damped Jacobi sweep d -> t: reads d, r (3 fields
+                     each) and q, writes t: 40 B per cell
+  lin_prolong_jacobi the prolongation fused into the first Jacobi sweep
+                     (pfc_op_lin_prolong_smooth): reads d_old, r and q and the
+                     coarse e, writes t (d + P e stays in shared memory):
+                     40 B per fine cell (+ e); _assign: d_old not read, 28 B
 
 A tool for measuring kernels in isolation (and for capturing one of them
 under a profiler); the solver itself never calls it.
@@ -44,7 +50,9 @@ def algorithmic_bytes(op: str, n: int) -> float:
     per_cell = {"lin_restrict": 28.0 + coarse, "lin_restrict_zero": 12.0 + coarse,
                 "lin_smooth": 40.0, "lin_prolong": 24.0 + coarse,
                 "lin_prolong_skip0": 12.0 + coarse, "lin_prolong_assign": 12.0 + coarse,
-                "lin_prolong_assign_skip0": 6.0 + coarse}[op]
+                "lin_prolong_assign_skip0": 6.0 + coarse, "lin_jacobi": 40.0,
+                "lin_prolong_jacobi": 40.0 + coarse,
+                "lin_prolong_jacobi_assign": 28.0 + coarse}[op]
     return per_cell * cells
 
 

@@ -210,3 +210,17 @@ def test_group_init_checks_its_arguments(libpfc):
     assert libpfc.pfc_group_step(None, 1, None) == B.PFC_EINVAL
     assert libpfc.pfc_group_graph_launches(None) == -1
     libpfc.pfc_group_destroy(None)
+
+
+def test_fused_prolong_smooth_checks_arguments(libpfc):
+    """pfc_op_lin_prolong_smooth refuses sizes its tiles do not cover (n not
+    a multiple of 32), an unknown sweep kind or flag and NULL fields before
+    any CUDA call."""
+    f = libpfc.pfc_op_lin_prolong_smooth
+    fake = [ctypes.c_void_p(4096)] * 13
+    assert f(48, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 0, 0.7, *fake, None) == B.PFC_EINVAL
+    assert f(16, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 0, 0.7, *fake, None) == B.PFC_EINVAL
+    assert f(64, 1.0, 0.1, 0.05, 7, 0, 0.7, *fake, None) == B.PFC_EINVAL
+    assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 2, 0.7, *fake, None) == B.PFC_EINVAL
+    assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_JACOBI, 0, 0.0, *fake, None) == B.PFC_EINVAL
+    assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 0, 0.7, *([None] * 13), None) == B.PFC_EINVAL

@@ -52,13 +52,19 @@ def test_vcycle_byte_model_matches_the_kernel_counts():
     finest = bench.vcycle_bytes(p, [(n, B.PFC_SWEEP_RB)])
     assert finest == OB.algorithmic_bytes("lin_restrict", n) + \
         OB.algorithmic_bytes("lin_prolong_skip0", n) + OB.algorithmic_bytes("lin_smooth", n)
-    # a Jacobi level: zero-start restriction, assigning prolongation of both
-    # colours, four sweeps of 40 B per cell
+    # a Jacobi level: zero-start restriction, the assigning prolongation
+    # fused into the first of four sweeps, three plain sweeps
     jac = [(n, B.PFC_SWEEP_RB), (64, B.PFC_SWEEP_JACOBI), (32, B.PFC_SWEEP_JACOBI),
            (16, B.PFC_SWEEP_JACOBI)]
     assert bench.vcycle_bytes(p, jac[:2]) - finest == \
         OB.algorithmic_bytes("lin_restrict_zero", 64) + \
-        OB.algorithmic_bytes("lin_prolong_assign", 64) + 4 * 40.0 * 64 ** 3
+        OB.algorithmic_bytes("lin_prolong_jacobi_assign", 64) + \
+        3 * OB.algorithmic_bytes("lin_jacobi", 64)
+    # a level the fused kernel's tiles do not cover (48^3): separate launches
+    odd = [(96, B.PFC_SWEEP_RB), (48, B.PFC_SWEEP_JACOBI), (24, B.PFC_SWEEP_JACOBI)]
+    assert bench.vcycle_bytes(p, odd[:2]) - bench.vcycle_bytes(p, odd[:1]) == \
+        OB.algorithmic_bytes("lin_restrict_zero", 48) + \
+        OB.algorithmic_bytes("lin_prolong_assign", 48) + 4 * OB.algorithmic_bytes("lin_jacobi", 48)
     # without pre-smoothing the 64^3 and 32^3 levels' averages come from the
     # first restriction's launch: only their 1.5 B per cell of output count
     assert bench.chained_levels(p, jac) == {1, 2}

@@ -491,6 +491,52 @@ def test_linear_prolong_fp32_multiplane(skip0):
             assert_close_field(got, ref, 1e-6, "d+Pe")
 
 
+@pytest.mark.parametrize("n", [32, 64, 96, 128])
+@pytest.mark.parametrize("kind", ["rb", "jacobi"])
+@pytest.mark.parametrize("assign", [False, True])
+def test_prolong_smooth_fused_equals_separate(n, kind, assign):
+    """The fused way up (d (+)= P e formed in shared memory inside the first
+    post-smoothing pass) against pfc_op_lin_prolong followed by one sweep of
+    pfc_op_lin_smooth / pfc_op_lin_jacobi: equal bit for bit, including the
+    periodic halo of every tile (32^3: 128-thread tiles of 32 x 4 x 2 cells;
+    larger: 32 x 8 x 4; 96^3 has three tiles across)."""
+    rng = np.random.default_rng(n + (7 if assign else 0) + (3 if kind == "rb" else 0))
+    nc, h, w = n // 2, 32.0 / n, 0.7
+    f32 = lambda a: dev(a.astype(np.float32).ravel(), torch.float32)
+    e = [f32(rng.standard_normal(nc ** 3)) for _ in range(3)]
+    d0 = [rng.standard_normal(n ** 3) for _ in range(3)]
+    r = [f32(rng.standard_normal(n ** 3)) for _ in range(3)]
+    q = f32(0.3 + 0.1 * rng.standard_normal(n ** 3))
+    code = B.PFC_SWEEP_RB if kind == "rb" else B.PFC_SWEEP_JACOBI
+    # separate entry points
+    ds = [f32(x) for x in d0]
+    ts = [torch.empty_like(x) for x in ds]
+    B.pfc_op_lin_prolong(n, B.PFC_PROLONG_ASSIGN if assign else 0, *e, *ds)
+    if kind == "rb":
+        B.pfc_op_lin_smooth(n, h, EPS, TAU, 1, False, *ds, *r, q)
+    else:
+        B.pfc_op_lin_jacobi(n, h, EPS, TAU, 1, w, False, *ds, *ts, *r, q)
+    # fused
+    df = [f32(x) for x in d0]
+    if assign:
+        for t in df:
+            t.fill_(float("nan"))             # d = P e: the old values are not read
+    tf = [torch.empty_like(x) for x in df]
+    B.pfc_op_lin_prolong_smooth(n, h, EPS, TAU, code, assign, w, *e, *df, *tf, *r, q)
+    torch.cuda.synchronize()
+    for a, b in zip(ds, df):
+        assert torch.equal(a, b)
+        assert torch.isfinite(a).all()
+
+
+def test_prolong_smooth_fused_checks_its_size():
+    z = torch.zeros(48 ** 3, dtype=torch.float32, device="cuda")
+    with pytest.raises(B.PFCError) as exc:
+        B.pfc_op_lin_prolong_smooth(48, 1.0, EPS, TAU, B.PFC_SWEEP_RB, False, 0.7,
+                                    *([z] * 13))
+    assert exc.value.code == B.PFC_EINVAL
+
+
 def test_linear_prolong_rejects_unknown_flags():
     z = torch.zeros(8 ** 3, dtype=torch.float32, device="cuda")
     with pytest.raises(B.PFCError):
