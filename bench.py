@@ -46,7 +46,7 @@ KERNEL_BYTES = {
     "lin_smooth": (20.0, 1),      # per colour pass: half of read d (12) + r,q (16) + write d (12)
     "lin_restrict": (29.5, 1),    # read d,r,q (28) + write coarse r (12/8)
     "lin_prolong": (25.5, 1),     # read+write d (24) + coarse d (12/8)
-    "correct": (60.0, 1),         # read df u (24) d (12) write df u (24)
+    "correct": (60.0, 1),         # read df u (24) d (12) write df u (24); the mixed form below
     "smooth": (40.0, 1),          # per colour pass: half of (u 24 + S2,S3 16 + b 8 + phi 8 + write u 24)
     "residual_norm": (48.0, 2),   # read u, b, S2, S3
     "residual_restrict": (57.0, 1),
@@ -58,6 +58,12 @@ KERNEL_BYTES = {
     "lin_coarse": (0.0, 1),
 }
 
+
+
+# Classes whose kernel differs by precision: on the mixed path the correction
+# u += d is folded into the last colour-1 pass of the correction's last
+# V-cycle (reads colour-0 d 6, colour-1 r and q 8, u 24; writes u 24).
+KERNEL_BYTES_BY_PRECISION = {("mixed", "correct"): (62.0, 1)}
 
 
 # DRAM bytes (read + write) of one launch of a kernel class of a precision,
@@ -547,7 +553,8 @@ def run_ours(args):
             bound, peak, unit = "alu", FP64_PEAK_TFLOPS, "TFLOP/s"
             peak_src = "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz (derived)"
         else:
-            per_cell, per_group = KERNEL_BYTES.get(dom_cls, (0.0, 1))
+            per_cell, per_group = KERNEL_BYTES_BY_PRECISION.get(
+                (precision, dom_cls), KERNEL_BYTES.get(dom_cls, (0.0, 1)))
             groups = dom_launches / per_group
             achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 \
                 if dom_time > 0 else 0.0

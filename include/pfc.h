@@ -663,6 +663,18 @@ int pfc_op_lin_prolong(int n, int assign, const float* d_e1, const float* d_e2,
                        const float* d_e3, float* d_d1, float* d_d2, float* d_d3,
                        void* stream);
 
+/* `sweeps` (>= 1) FP32 red-black sweeps on J d = r as pfc_op_lin_smooth
+ * (d != 0 on entry) with the defect correction folded into the last
+ * colour-1 pass: instead of storing its colour-1 values that pass adds them,
+ * and the colour-0 values, to the FP64 state (natural layout): u += d, as
+ * pfc_op_correct after pfc_op_lin_smooth, bit for bit.  d's colour-1 cells
+ * keep the values of the sweep before.  n a multiple of 4, d_u1..3 16-byte
+ * aligned (PFC_EINVAL otherwise). */
+int pfc_op_lin_smooth_correct(int n, double h, double eps, double tau, int sweeps,
+                              float* d_d1, float* d_d2, float* d_d3, const float* d_r1,
+                              const float* d_r2, const float* d_r3, const float* d_q,
+                              double* d_u1, double* d_u2, double* d_u3, void* stream);
+
 /* The V-cycle's way up on one level: d (+)= P e, exactly as
  * pfc_op_lin_prolong (PFC_PROLONG_ASSIGN in `assign`: d = P e, d not read),
  * followed by one post-smoothing sweep of `kind` on J d = r (q frozen):

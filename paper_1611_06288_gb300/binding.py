@@ -117,6 +117,7 @@ _SIGS = {
     "pfc_op_lin_restrict_chain": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 16 + [_P]),
     "pfc_op_lin_prolong": (_I, [_I, _I] + [_P] * 6 + [_P]),
     "pfc_op_lin_prolong_smooth": (_I, [_I, _D, _D, _D, _I, _I, _D] + [_P] * 13 + [_P]),
+    "pfc_op_lin_smooth_correct": (_I, [_I, _D, _D, _D, _I] + [_P] * 10 + [_P]),
     "pfc_op_restrict_q": (_I, [_I, _I] + [_P] * 4 + [_P]),
     "pfc_op_guess": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
     "pfc_op_guess_df": (_I, [_I, _D, _D] + [_P] * 7 + [_P]),
@@ -500,6 +501,15 @@ def pfc_op_lin_prolong(n, assign, e1, e2, e3, d1, d2, d3, stream=None):
     """assign: a bool, or the flags PFC_PROLONG_ASSIGN | PFC_PROLONG_SKIP_COLOUR0."""
     check(lib().pfc_op_lin_prolong(n, int(assign), ptr(e1), ptr(e2), ptr(e3), ptr(d1),
                                    ptr(d2), ptr(d3), stream), "pfc_op_lin_prolong")
+
+
+def pfc_op_lin_smooth_correct(n, h, eps, tau, sweeps, d1, d2, d3, r1, r2, r3, q, u1, u2, u3,
+                              stream=None):
+    """Red-black sweeps whose last colour-1 pass adds d to the FP64 state u."""
+    check(lib().pfc_op_lin_smooth_correct(n, h, eps, tau, sweeps,
+                                          *[ptr(x) for x in (d1, d2, d3, r1, r2, r3, q, u1, u2,
+                                                             u3)], stream),
+          "pfc_op_lin_smooth_correct")
 
 
 def pfc_op_lin_prolong_smooth(n, h, eps, tau, kind, assign, weight, e1, e2, e3, d1, d2, d3,

@@ -1762,6 +1762,18 @@ int pfc_op_lin_prolong(int n, int assign, const float* e1, const float* e2, cons
   return PFC_OK;
 }
 
+int pfc_op_lin_smooth_correct(int n, double h, double eps, double tau, int sweeps, float* d1,
+                              float* d2, float* d3, const float* r1, const float* r2,
+                              const float* r3, const float* q, double* u1, double* u2,
+                              double* u3, void* stream) {
+  if (n < 4 || n % 4 != 0 || !(h > 0) || sweeps < 1 || !d1 || !d2 || !d3 || !r1 || !r2 || !r3 ||
+      !q || !u1 || !u2 || !u3 || ((uintptr_t)u1 | (uintptr_t)u2 | (uintptr_t)u3) % 16 != 0)
+    return PFC_EINVAL;
+  PFC_CUDA(launch_lin_smooth_correct32(make_lvl(n, h, eps, tau), sweeps, d1, d2, d3, r1, r2, r3,
+                                       q, u1, u2, u3, (cudaStream_t)stream));
+  return PFC_OK;
+}
+
 int pfc_op_lin_prolong_smooth(int n, double h, double eps, double tau, int kind, int assign,
                               double weight, const float* e1, const float* e2, const float* e3,
                               float* d1, float* d2, float* d3, float* t1, float* t2, float* t3,

@@ -1282,6 +1282,88 @@ __global__ void k_lin_jacobi32x2(LvlF L, float w, const float* __restrict__ d1,
       make_float2(fmaf(w, dw.x - o2.x, o2.x), fmaf(w, dw.y - o2.y, o2.y));
 }
 
+// The colour-1 pass of k_lin_smooth32x2 with the defect correction u += d
+// folded in, for the last pass of a correction's last V-cycle on the finest
+// level: d is not needed after it, so the pass adds its new colour-1 values
+// and the colour-0 values it reads as x neighbours to the FP64 state instead
+// of storing them.  A thread's pair of colour-1 cells and the two colour-0
+// cells at the same positions of the other half are the four consecutive
+// natural cells 2 p0 .. 2 p0 + 3 of the row (which of each pair comes first
+// depends on the row's colour offset), so u moves as two 16-byte vectors per
+// component.  Same sums and solve as the pass, same u + f2d(d) as
+// k_correct64: u equals the two launches bit for bit.  d's colour-1 cells
+// are left as they were.
+__global__ void k_lin_smooth32x2_correct(LvlF L, const float* __restrict__ d1,
+                                         const float* __restrict__ d2,
+                                         const float* __restrict__ d3,
+                                         const float* __restrict__ r1,
+                                         const float* __restrict__ r2,
+                                         const float* __restrict__ r3,
+                                         const float* __restrict__ q, double* __restrict__ u1,
+                                         double* __restrict__ u2, double* __restrict__ u3) {
+  pdl_wait();
+  pdl_trigger();
+  const int n = L.n, half = n >> 1;
+  const int p0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  int k = blockIdx.z;
+  const size_t off = (size_t)member_of(k, n) * n * n * n;
+  if (p0 >= half || j >= n) return;
+  d1 += off, d2 += off, d3 += off, r1 += off, r2 += off, r3 += off, q += off;
+  u1 += off, u2 += off, u3 += off;
+  const int sigma = (j + k + 1) & 1;                     // colour 1
+  const int jm = (j == 0) ? n - 1 : j - 1, jp = (j + 1 == n) ? 0 : j + 1;
+  const int km = (k == 0) ? n - 1 : k - 1, kp = (k + 1 == n) ? 0 : k + 1;
+  const int row = (k * n + j) * n;
+  const int c = row + half + p0;                         // own pair
+  const int xo = row + p0;                               // colour 0, same positions
+  int xe = sigma ? p0 + 2 : p0 - 1;
+  if (xe < 0) xe += half;
+  if (xe >= half) xe -= half;
+  xe += row;
+  const int ym = (k * n + jm) * n + p0, yp = (k * n + jp) * n + p0;
+  const int zm = (km * n + j) * n + p0, zp = (kp * n + j) * n + p0;
+  float s[3][2];
+  float2 a[3];
+  const float* const f[3] = {d1, d2, d3};
+#pragma unroll
+  for (int q3 = 0; q3 < 3; ++q3) {
+    const float* v = f[q3];
+    a[q3] = __ldg(reinterpret_cast<const float2*>(v + xo));
+    const float e = __ldg(v + xe);
+    const float2 y0 = __ldg(reinterpret_cast<const float2*>(v + ym));
+    const float2 y1 = __ldg(reinterpret_cast<const float2*>(v + yp));
+    const float2 z0 = __ldg(reinterpret_cast<const float2*>(v + zm));
+    const float2 z1 = __ldg(reinterpret_cast<const float2*>(v + zp));
+    const float xm0 = sigma ? a[q3].x : e, xp0 = sigma ? a[q3].y : a[q3].x;
+    const float xm1 = sigma ? a[q3].y : a[q3].x, xp1 = sigma ? e : a[q3].y;
+    s[q3][0] = ((xm0 + xp0) + (y0.x + y1.x)) + (z0.x + z1.x);
+    s[q3][1] = ((xm1 + xp1) + (y0.y + y1.y)) + (z0.y + z1.y);
+  }
+  const float2 qq = __ldg(reinterpret_cast<const float2*>(q + c));
+  const float2 ra = __ldg(reinterpret_cast<const float2*>(r1 + c));
+  const float2 rb = __ldg(reinterpret_cast<const float2*>(r2 + c));
+  const float2 rc = __ldg(reinterpret_cast<const float2*>(r3 + c));
+  float2 nd[3];
+  lin_point(L, s[0][0], s[1][0], s[2][0], qq.x, ra.x, rb.x, rc.x, nd[0].x, nd[1].x, nd[2].x);
+  lin_point(L, s[0][1], s[1][1], s[2][1], qq.y, ra.y, rb.y, rc.y, nd[0].y, nd[1].y, nd[2].y);
+  double* const u[3] = {u1, u2, u3};
+#pragma unroll
+  for (int q3 = 0; q3 < 3; ++q3) {
+    // natural order 2 p0 .. 2 p0 + 3: colour 1 first when sigma = 0
+    const float v0 = sigma ? a[q3].x : nd[q3].x, v1 = sigma ? nd[q3].x : a[q3].x;
+    const float v2 = sigma ? a[q3].y : nd[q3].y, v3 = sigma ? nd[q3].y : a[q3].y;
+    double2* const up = reinterpret_cast<double2*>(u[q3] + row + 2 * p0);
+    double2 lo = up[0], hi = up[1];
+    lo.x += f2d(v0);
+    lo.y += f2d(v1);
+    hi.x += f2d(v2);
+    hi.y += f2d(v3);
+    up[0] = lo;
+    up[1] = hi;
+  }
+}
+
 __global__ void k_copy3(int cells, const float* __restrict__ a1, const float* __restrict__ a2,
                         const float* __restrict__ a3, float* __restrict__ b1,
                         float* __restrict__ b2, float* __restrict__ b3) {
@@ -3110,6 +3192,7 @@ struct Ctx32 {
   cudaStream_t st;
   Prof* pr;
   int nb = 1;                  // members of a batched ensemble (fields member after member)
+  double* const* fold_u = nullptr;   // FP64 state the finest level's last pass adds d to
 };
 
 // `sweeps` damped Jacobi sweeps d -> t -> d ...; the result ends in d.
@@ -3166,7 +3249,30 @@ cudaError_t rb_pass32(const Ctx32& c, int l, int colour, bool zero) {
                   g.block, 0, c.st, L, colour, d[0], d[1], d[2], r[0], r[1], r[2], q);
 }
 
-cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
+// The last colour-1 pass of level l with u += d folded in (c.fold_u).
+cudaError_t rb_pass32_correct(const Ctx32& c, int l) {
+  const LvlF& L = c.L[l];
+  float* const* d = c.mx->d[l];
+  float* const* r = c.mx->r[l];
+  const Launch3 g = launch3(L.n / 4, L.n, L.n * c.nb);
+  return launch_k(c.pr == nullptr, k_lin_smooth32x2_correct, g.grid, g.block, 0, c.st, L,
+                  (const float*)d[0], (const float*)d[1], (const float*)d[2], (const float*)r[0],
+                  (const float*)r[1], (const float*)r[2], (const float*)c.mx->q[l], c.fold_u[0],
+                  c.fold_u[1], c.fold_u[2]);
+}
+
+// Whether a correction's u += d can fold into the finest level's last
+// post-smoothing pass: a red-black finest level with post-smoothing, wide
+// enough that no tail launch takes it (more than 32 cells), its rows a
+// multiple of four cells (the paired pass).
+bool correction_folds(const Ctx32& c) {
+  return c.nl >= 2 && c.kind[0] == PFC_SWEEP_RB && c.p->nu2 > 0 && c.L[0].n > kCtMaxN &&
+         c.L[0].n % 4 == 0;
+}
+
+// `sweeps` post- (or pre-) smoothing sweeps on level l; fold: the last
+// colour-1 pass adds the result to c.fold_u (red-black, n % 4 == 0).
+cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init, bool fold = false) {
   const LvlF& L = c.L[l];
   float* const* d = c.mx->d[l];
   float* const* r = c.mx->r[l];
@@ -3183,8 +3289,15 @@ cudaError_t smooth32(const Ctx32& c, int l, int sweeps, bool zero_init) {
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < sweeps && e == cudaSuccess; ++s)
     for (int colour = 0; colour < 2 && e == cudaSuccess; ++colour)
-      e = rb_pass32(c, l, colour, zero_init && s == 0 && colour == 0);
-  prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps, c.st);
+      if (!(fold && s == sweeps - 1 && colour == 1))
+        e = rb_pass32(c, l, colour, zero_init && s == 0 && colour == 0);
+  prof_end(c.pr, PFC_K_LIN_SMOOTH, l, 2 * sweeps - (fold ? 1 : 0), c.st);
+  if (e == cudaSuccess && fold) {
+    // timed as the correction it replaces
+    prof_begin(c.pr, PFC_K_CORRECT, c.st);
+    e = rb_pass32_correct(c, l);
+    prof_end(c.pr, PFC_K_CORRECT, l, 1, c.st);
+  }
   return e;
 }
 
@@ -3495,7 +3608,7 @@ cudaError_t vcycle32(const Ctx32& c, int l, bool zero_init, int have = 0) {
                mx.d[l + 1][2], mx.d[l][0], mx.d[l][1], mx.d[l][2]);
   prof_end(c.pr, PFC_K_LIN_PROLONG, l, 1, c.st);
   if (e != cudaSuccess) return e;
-  return smooth32(c, l, c.p->nu2, false);
+  return smooth32(c, l, c.p->nu2, false, l == 0 && c.fold_u != nullptr);
 }
 
 }  // namespace
@@ -3812,6 +3925,34 @@ cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float*
   return smooth32(c, 0, sweeps, zero_init);
 }
 
+cudaError_t launch_lin_smooth_correct32(const Lvl& L, int sweeps, float* d1, float* d2,
+                                       float* d3, const float* r1, const float* r2,
+                                       const float* r3, const float* q, double* u1, double* u2,
+                                       double* u3, cudaStream_t st) {
+  MixedBufs mx;
+  mx.d[0][0] = d1;
+  mx.d[0][1] = d2;
+  mx.d[0][2] = d3;
+  mx.r[0][0] = (float*)r1;
+  mx.r[0][1] = (float*)r2;
+  mx.r[0][2] = (float*)r3;
+  mx.q[0] = (float*)q;
+  double* const u[3] = {u1, u2, u3};
+  Ctx32 c;
+  c.mx = &mx;
+  c.p = nullptr;
+  c.nl = 1;
+  c.L[0] = to_f32(L);
+  c.kind[0] = PFC_SWEEP_RB;
+  c.w = 1.f;
+  c.jfactor = 1;
+  c.jfactor0 = 1;
+  c.st = st;
+  c.pr = nullptr;
+  c.fold_u = u;
+  return smooth32(c, 0, sweeps, false, true);
+}
+
 cudaError_t launch_lin_prolong_smooth32(const Lvl& L, int kind, bool assign, float w,
                                        const float* e1, const float* e2, const float* e3,
                                        float* d1, float* d2, float* d3, float* t1, float* t2,
@@ -3924,8 +4065,13 @@ namespace {
 
 // q restricted to every level, then p.inner_cycles FP32 V-cycles on J d = r
 // from d = 0 (the part of a correction shared by both outer precisions).
+// The FP32 correction solve of one defect correction: the q restrictions,
+// then p.inner_cycles V-cycles from d = 0.  u (FP64 state, or nullptr): where
+// correction_folds holds, the last V-cycle's last pass adds d to u (*folded
+// set), and the caller's u += d launch goes.
 cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int* sizes,
-                          cudaStream_t st, Prof* pr, int members, double tau_scale) {
+                          cudaStream_t st, Prof* pr, int members, double tau_scale,
+                          double* const* u, bool* folded) {
   Ctx32 c;
   c.nb = members;
   c.mx = &mx;
@@ -3966,7 +4112,11 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
     prof_end(pr, PFC_K_RESTRICT, l - 1, 1, st);
     l += 1 + extra;
   }
-  for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic) e = vcycle32(c, 0, ic == 0);
+  *folded = u != nullptr && p.inner_cycles > 0 && correction_folds(c);
+  for (int ic = 0; ic < p.inner_cycles && e == cudaSuccess; ++ic) {
+    c.fold_u = (*folded && ic + 1 == p.inner_cycles) ? u : nullptr;
+    e = vcycle32(c, 0, ic == 0);
+  }
   return e;
 }
 
@@ -3975,8 +4125,9 @@ cudaError_t mixed_vcycles(MixedBufs& mx, const pfc_params& p, int nl, const int*
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, double* const u[3], cudaStream_t st,
                                      Prof* pr, int members, double tau_scale) {
-  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, members, tau_scale);
-  if (e == cudaSuccess) {
+  bool folded = false;
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, members, tau_scale, u, &folded);
+  if (e == cudaSuccess && !folded) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct64(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,
                          pr == nullptr, members);
@@ -3988,7 +4139,8 @@ cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
 cudaError_t mixed_enqueue_correction(MixedBufs& mx, const pfc_params& p, int nl,
                                      const int* sizes, float2* const u[3], cudaStream_t st,
                                      Prof* pr) {
-  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, 1, 1.0);
+  bool folded = false;
+  cudaError_t e = mixed_vcycles(mx, p, nl, sizes, st, pr, 1, 1.0, nullptr, &folded);
   if (e == cudaSuccess) {
     prof_begin(pr, PFC_K_CORRECT, st);
     e = launch_correct_df(p.n, u[0], u[1], u[2], mx.d[0][0], mx.d[0][1], mx.d[0][2], st,

@@ -200,6 +200,13 @@ cudaError_t launch_prolong32(int n, bool assign, bool skip0, const float* e1, co
 cudaError_t launch_lin_smooth32(const Lvl& L, int sweeps, bool zero_init, float* d1,
                                 float* d2, float* d3, const float* r1, const float* r2,
                                 const float* r3, const float* q, cudaStream_t st);
+// `sweeps` (>= 1) FP32 red-black sweeps whose last colour-1 pass adds d to
+// the FP64 state u instead of storing d's colour-1 cells; n % 4 == 0.
+cudaError_t launch_lin_smooth_correct32(const Lvl& L, int sweeps, float* d1, float* d2,
+                                       float* d3, const float* r1, const float* r2,
+                                       const float* r3, const float* q, double* u1, double* u2,
+                                       double* u3, cudaStream_t st);
+
 // d (+)= P e (e of (n/2)^3 cells) and one post-smoothing sweep of `kind`
 // (PFC_SWEEP_RB or PFC_SWEEP_JACOBI, weight w; t is Jacobi scratch) in one
 // fused launch plus the rest of the sweep; n a multiple of 32.

@@ -224,3 +224,15 @@ def test_fused_prolong_smooth_checks_arguments(libpfc):
     assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 2, 0.7, *fake, None) == B.PFC_EINVAL
     assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_JACOBI, 0, 0.0, *fake, None) == B.PFC_EINVAL
     assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 0, 0.7, *([None] * 13), None) == B.PFC_EINVAL
+
+
+def test_folded_correction_checks_arguments(libpfc):
+    """pfc_op_lin_smooth_correct refuses n not a multiple of 4, no sweep,
+    NULL fields and an FP64 state not 16-byte aligned before any CUDA call."""
+    f = libpfc.pfc_op_lin_smooth_correct
+    fake = [ctypes.c_void_p(4096)] * 10
+    assert f(6, 1.0, 0.1, 0.05, 1, *fake, None) == B.PFC_EINVAL
+    assert f(8, 1.0, 0.1, 0.05, 0, *fake, None) == B.PFC_EINVAL
+    assert f(8, 1.0, 0.1, 0.05, 1, *([None] * 10), None) == B.PFC_EINVAL
+    assert f(8, 1.0, 0.1, 0.05, 1, *fake[:7], ctypes.c_void_p(4104), *fake[8:], None) == \
+        B.PFC_EINVAL

@@ -529,6 +529,32 @@ def test_prolong_smooth_fused_equals_separate(n, kind, assign):
         assert torch.isfinite(a).all()
 
 
+@pytest.mark.parametrize("n,sweeps", [(4, 1), (12, 1), (64, 2), (128, 1)])
+def test_smooth_with_folded_correction_equals_separate(n, sweeps):
+    """Red-black sweeps whose last colour-1 pass adds d to the FP64 state u
+    (the last pass of a correction's last V-cycle) against pfc_op_lin_smooth
+    followed by pfc_op_correct: u equal bit for bit, d's colour-0 cells
+    equal (its colour-1 cells are not written by the folded pass)."""
+    rng = np.random.default_rng(100 + n + sweeps)
+    h = 32.0 / n
+    f32 = lambda a: dev(a.astype(np.float32).ravel(), torch.float32)
+    d0 = [rng.standard_normal(n ** 3) for _ in range(3)]
+    r = [f32(rng.standard_normal(n ** 3)) for _ in range(3)]
+    q = f32(0.3 + 0.1 * rng.standard_normal(n ** 3))
+    u0 = [rng.standard_normal(n ** 3) for _ in range(3)]
+    ds, us = [f32(x) for x in d0], [dev(x) for x in u0]
+    B.pfc_op_lin_smooth(n, h, EPS, TAU, sweeps, False, *ds, *r, q)
+    B.pfc_op_correct(n, *us, *ds)
+    df, uf = [f32(x) for x in d0], [dev(x) for x in u0]
+    B.pfc_op_lin_smooth_correct(n, h, EPS, TAU, sweeps, *df, *r, q, *uf)
+    torch.cuda.synchronize()
+    for a, b in zip(us, uf):
+        assert torch.equal(a, b)
+    half = n // 2
+    for a, b in zip(ds, df):
+        assert torch.equal(a.view(n * n, n)[:, :half], b.view(n * n, n)[:, :half])
+
+
 def test_prolong_smooth_fused_checks_its_size():
     z = torch.zeros(48 ** 3, dtype=torch.float32, device="cuda")
     with pytest.raises(B.PFCError) as exc:
