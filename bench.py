@@ -167,7 +167,9 @@ class ClockSampler:
         self.proc = None
         self.lines = []
 
-    def start(self):
+    def start(self, busy=None):
+        """busy: called repeatedly (untimed GPU work) while nvidia-smi starts,
+        so the GPU stays under load until its first sample."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
@@ -177,6 +179,16 @@ class ClockSampler:
             self.thread.start()
         except OSError:
             self.proc = None
+            return
+        # nvidia-smi's start-up (driver and NVML initialisation) can hold the
+        # driver for tens of milliseconds: let it finish before the timed
+        # region begins (the first sample marks it), at most a few seconds
+        t0 = time.time()
+        while not self.lines and self.proc.poll() is None and time.time() - t0 < 5.0:
+            if busy is not None:
+                busy()
+            else:
+                time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -477,10 +489,12 @@ def run_ours(args):
         for _ in range(warmup):
             s.step(1)
             s.diagnostics()
+        # the clock sampler starts under load (more untimed steps until its
+        # first sample), then every rank enters the timed region together
+        clocks = ClockSampler(local)
+        clocks.start(busy=lambda: (s.step(1), s.diagnostics()))
         barrier()
         # timed region: each step is one CUDA graph launch (device-side loop)
-        clocks = ClockSampler(local)
-        clocks.start()
         launches0 = s.launches
         ms_total, cycles = time_steps(s, steps)
         launches = s.launches - launches0

@@ -160,6 +160,8 @@ struct pfc_ctx {
   pfc::Prof prof;    // optional event timing of launches
   pfc::StepState* dstate;  // device convergence state of the current step
   pfc::StepState* hstate;  // pinned host copy
+  pfc::StepState* hstate_dev;  // its device address (mapped): written by a step graph's last kernel
+  double* hdiag_dev;       // device address of hdiag (mapped)
   int use_graphs;    // run each step as one graph launch (default on)
   int graph_gen;     // bumped whenever the step graphs are rebuilt (groups key on it)
   cudaStream_t cap_st;  // private stream the step graphs are captured on
@@ -331,10 +333,18 @@ void diagnostics_finish(int n, double h, const double* eps, int members,
 
 // Diagnostics kernels of the state (a, b) and their raw sums copied to hout
 // (asynchronous).
+// direct (FP64 fields with stored Laplacians only): the final reduction
+// writes the sums to direct_out (hout's device mapping) and copies the step
+// states state -> state_out itself, so no copy follows.
 cudaError_t enqueue_diagnostics(int n, int members, const double* a, const double* b,
                                 const double* lapa, const double* lapb, bool df_fields,
                                 double* partials, double* dout, double* hout, cudaStream_t st,
-                                bool pdl = false) {
+                                bool pdl = false, double* direct_out = nullptr,
+                                const StepState* state = nullptr,
+                                StepState* state_out = nullptr) {
+  if (direct_out && !df_fields && lapa)
+    return launch_diagnostics_cached(n, a, b, lapa, lapb, partials, direct_out, st, members, pdl,
+                                     state, state_out);
   cudaError_t e;
   if (df_fields && lapa)
     e = launch_diagnostics_cached_df(n, as_df(a), as_df(b), as_df(lapa), as_df(lapb), partials,
@@ -544,14 +554,18 @@ int build_graph_on(pfc_ctx* c, const Level64& lv, pfc_ctx::Graph* g, bool warm) 
     if (e == cudaSuccess)
       e = cudaStreamUpdateCaptureDependencies(c->st, &cnode, nullptr, 1,
                                               cudaStreamSetCaptureDependencies);
-    if (e == cudaSuccess)
+    // the new state's energy/mass sums in the same graph launch; with FP64
+    // fields their final reduction also copies the step state to the mapped
+    // host copy (a copy node costs a few microseconds of the step)
+    const bool direct = c->p.step_diagnostics && !df_state(&c->p) && c->lap[c->ia] != nullptr;
+    if (e == cudaSuccess && !direct)
       e = cudaMemcpyAsync(c->hstate, c->dstate, sizeof(StepState) * c->nb,
                           cudaMemcpyDeviceToHost, c->st);
     if (e == cudaSuccess && c->p.step_diagnostics) {
-      // the new state's energy/mass sums in the same graph launch
       e = enqueue_diagnostics(c->p.n, c->nb, c->ring[c->ia], c->ring[c->ib], c->lap[c->ia],
                               c->lap[c->ib], df_state(&c->p), c->partials, c->dout, c->hdiag,
-                              c->st, c->prof.mask == 0);
+                              c->st, c->prof.mask == 0, direct ? c->hdiag_dev : nullptr,
+                              c->dstate, c->hstate_dev);
       g->launches_pre += 2;
     }
   }
@@ -822,14 +836,19 @@ static int init_members(pfc_ctx** out, const pfc_params* p, int members, const d
   memcpy(c->eps_host, eps, sizeof(double) * members);
   e = cudaHostAlloc((void**)&c->hout, kReduceComps * sizeof(double) * members,
                     cudaHostAllocDefault);
+  // the step state and the diagnostics sums are mapped: a step graph's last
+  // kernel writes them, with no copy node
   if (e == cudaSuccess)
-    e = cudaHostAlloc((void**)&c->hstate, sizeof(StepState) * members, cudaHostAllocDefault);
+    e = cudaHostAlloc((void**)&c->hstate, sizeof(StepState) * members, cudaHostAllocMapped);
   if (e == cudaSuccess)
     e = cudaHostAlloc((void**)&c->hdiag, kReduceComps * sizeof(double) * members,
-                      cudaHostAllocDefault);
+                      cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->hstate_dev, c->hstate, 0);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->hdiag_dev, c->hdiag, 0);
   if (e != cudaSuccess) {
     if (c->hout) cudaFreeHost(c->hout);
     if (c->hstate) cudaFreeHost(c->hstate);
+    if (c->hdiag) cudaFreeHost(c->hdiag);
     free(c->eps_host);
     free(c);
     return cuda_fail(e, "cudaHostAlloc");

@@ -597,14 +597,45 @@ cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* la
                    dim3(kThreads), 0, st, L, members, c1m, b, lapb, lapc, S2, S3);
 }
 
+// k_reduce_final<6> that also copies each member's step state (the step's
+// end inside a step graph: out and state_out may be mapped host memory, so
+// the graph needs no copy nodes).
+__global__ void k_reduce_final_state(const double* __restrict__ partials, int nparts,
+                                     double* out, const StepState* __restrict__ state,
+                                     StepState* state_out) {
+  pdl_wait();
+  pdl_trigger();
+  constexpr int NV = 6;
+  __shared__ double sm[32 * NV];
+  partials += (size_t)blockIdx.x * nparts * NV;
+  out += (size_t)blockIdx.x * kReduceComps;
+  double acc[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) acc[c] = 0.0;
+  for (int p = threadIdx.x; p < nparts; p += blockDim.x) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) acc[c] += partials[(int64_t)p * NV + c];
+  }
+  block_sum<NV>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < NV; ++c) out[c] = acc[c];
+    state_out[blockIdx.x] = state[blockIdx.x];
+  }
+}
+
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
-                                      double* out, cudaStream_t st, int members, bool pdl) {
+                                      double* out, cudaStream_t st, int members, bool pdl,
+                                      const StepState* state, StepState* state_out) {
   int nb = reduce_blocks((int64_t)n * n * n * members) / members;
   if (nb < 1) nb = 1;
   cudaError_t e = launch_ex(pdl, k_diagnostics_cached, dim3(nb, members), dim3(kReduceThreads), 0,
                             st, n, a, b, lapa, lapb, partials);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && state_out)
+    e = launch_ex(pdl, k_reduce_final_state, dim3(members), dim3(kReduceThreads), 0, st,
+                  (const double*)partials, nb, out, state, state_out);
+  else if (e == cudaSuccess)
     e = launch_ex(pdl, k_reduce_final<6>, dim3(members), dim3(kReduceThreads), 0, st,
                   (const double*)partials, nb, out);
   return e;

@@ -184,10 +184,13 @@ cudaError_t launch_source_cached(const Lvl& L, const double* b, const double* la
                                  const double* lapc, double* S2, double* S3, cudaStream_t st,
                                  int members = 1, const double* c1m = nullptr, bool pdl = false);
 // launch_diagnostics from the stored unscaled Laplacians of a and b.
+// state_out (optional, with state): the final reduction also copies the
+// members' step states there; out and state_out may be mapped host memory.
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
                                       double* out, cudaStream_t st, int members = 1,
-                                      bool pdl = false);
+                                      bool pdl = false, const StepState* state = nullptr,
+                                      StepState* state_out = nullptr);
 // out[0..5] = sum a^4, sum a^2, sum |D a|^2 (faces), sum (Lap a)^2 (times h^4
 // removed: raw stencil sums), sum |D(a-b)|^2, sum a.  Raw sums; the host scales.
 cudaError_t launch_diagnostics(int n, const double* a, const double* b, double* partials,
