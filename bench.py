@@ -117,6 +117,8 @@ def parse():
                     help="initial iterate of a step (default: the previous step's solution)")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cpu-all-cores", action="store_true",
+                    help="skip the all-cores oracle timing (one replica per host core)")
     ap.add_argument("--no-n256", dest="n256", action="store_false",
                     help="skip the 256^3 legs (the n256 object)")
     ap.add_argument("--no-extras", dest="extras", action="store_false",
@@ -343,6 +345,37 @@ class OracleSteps:
         self.c, self.b = self.b, a
         self.k += 1
         return dt, res.cycles
+
+
+def _oracle_replica(n: int, barrier, results) -> None:
+    """One oracle replica of the all-cores timing: its start step, then (all
+    replicas together) one timed warm step."""
+    orc = OracleSteps(n)
+    orc.step()
+    barrier.wait()
+    t, cycles = orc.step()
+    results.put((t, cycles))
+
+
+def oracle_all_cores(n: int, procs: int):
+    """The oracle on every host core: `procs` independent replicas of the
+    bench workload in spawned processes (one numpy thread each), their warm
+    steps started together; returns (aggregate steps/s, slowest step s,
+    cycles).  numpy has no parallel elementwise kernels, so independent
+    replicas are how the plain oracle uses all cores."""
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_replica, args=(n, barrier, results)) for _ in range(procs)]
+    for p in ps:
+        p.start()
+    out = [results.get(timeout=900) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    slowest = max(t for t, _ in out)
+    return procs / slowest, slowest, [c for _, c in out]
 
 
 def run_reference(args):
@@ -709,6 +742,15 @@ def run_ours(args):
                          f"GPU's timed steps are), {cyc_cpu} FAS V(2,2) cycles to the same "
                          f"tolerance, energy/mass included (the untimed step 1, start rule, "
                          f"took {cyc_start}); numpy elementwise on one thread"}
+        if not args.no_cpu_all_cores:
+            procs = os.cpu_count() or 1
+            agg, slowest, cyc_all = oracle_all_cores(n, procs)
+            cpu["all_cores"] = {
+                "value": agg, "unit": UNIT, "cores": procs, "kind": "oracle",
+                "sample": f"{procs} independent replicas of the same workload, one per host "
+                          f"core (spawned processes, one numpy thread each): each an untimed "
+                          f"start step, then one warm step started together; value = replicas "
+                          f"/ slowest warm step ({slowest:.2f} s, cycles {sorted(set(cyc_all))})"}
 
     if rank == 0:
         line = {

@@ -7,6 +7,8 @@ import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -76,3 +78,13 @@ def test_vcycle_byte_model_matches_the_kernel_counts():
     p.nu1 = 0
     big = [(256, B.PFC_SWEEP_RB)] + jac
     assert bench.chained_levels(p, big) == {2, 3}
+
+
+def test_oracle_all_cores_timing_runs_spawned_replicas():
+    """The all-cores CPU baseline: independent oracle replicas in spawned
+    processes, warm steps started together (two replicas at 8^3 here)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    agg, slowest, cycles = bench.oracle_all_cores(8, 2)
+    assert slowest > 0 and agg == pytest.approx(2 / slowest)
+    assert len(cycles) == 2 and all(c >= 1 for c in cycles)
