@@ -3,6 +3,7 @@
 //
 // Layout: every field is n^3 doubles, x fastest (cell (i,j,k) at i + n(j + nk)),
 // one array per component (phi, mu, omega), so warps load contiguous x-runs.
+#include "pfc_fixed.cuh"
 #include "pfc_internal.h"
 
 namespace pfc {
@@ -494,6 +495,11 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
 // The raw sums of k_diagnostics from the stored unscaled Laplacians of a and
 // b: -(a, Lap a) and (Lap a)^2 directly, and the forward-face sum of
 // |D(a-b)|^2 by summation by parts as -(a-b, Lap a - Lap b) (Lemma 2.1).
+// The kernel is bound by GB300's FP64 pipe, so the two plain sums, sum a^2
+// and sum a, run on the integer pipe: each value of magnitude below 1 enters
+// as its fixed-point image (2^-54 quantum, pfc_fixed.cuh) into an exact int64
+// sum, which is rounded to FP64 and added every 256 cells (at most 2^8 values
+// below 2^54 each: no overflow); larger values take the FP64 adds.
 __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
                                      const double* __restrict__ b,
                                      const double* __restrict__ lapa,
@@ -506,17 +512,33 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
   a += off, b += off, lapa += off, lapb += off;
   partials += (size_t)blockIdx.y * gridDim.x * 6;
   double acc[6] = {0, 0, 0, 0, 0, 0};
+  int64_t s1 = 0, s2 = 0;       // fixed-point sums of a and a^2 since the last flush
+  int count = 0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
     const double x = __ldg(a + t), la = __ldg(lapa + t);
     const double y = x - __ldg(b + t);
     const double x2 = x * x;
     acc[0] = fma(x2, x2, acc[0]);
-    acc[1] += x2;
     acc[2] = fma(-x, la, acc[2]);
     acc[3] = fma(la, la, acc[3]);
     acc[4] = fma(-y, la - __ldg(lapb + t), acc[4]);
-    acc[5] += x;
+    if (((fix_bits_of(x) >> 52) & 0x7FFu) <= 1022u) {     // |x| < 1, so x^2 < 1
+      bool ok = true;
+      s1 += fix_of(x, ok);
+      s2 += fix_of(x2, ok);
+    } else {
+      acc[5] += x;
+      acc[1] += x2;
+    }
+    if (++count == 256) {
+      acc[5] += fix_to_double(s1);
+      acc[1] += fix_to_double(s2);
+      s1 = s2 = 0;
+      count = 0;
+    }
   }
+  acc[5] += fix_to_double(s1);
+  acc[1] += fix_to_double(s2);
   block_sum<6>(acc, sm);
   if (threadIdx.x == 0) {
     for (int c = 0; c < 6; ++c) partials[(int64_t)blockIdx.x * 6 + c] = acc[c];
