@@ -117,6 +117,8 @@ def parse():
                     help="initial iterate of a step (default: the previous step's solution)")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-soak", action="store_true",
+                    help="skip the 10^4-step growth soak of the extras (about 25 s)")
     ap.add_argument("--no-cpu-all-cores", action="store_true",
                     help="skip the all-cores oracle timing (one replica per host core)")
     ap.add_argument("--no-n256", dest="n256", action="store_false",
@@ -730,6 +732,13 @@ def run_ours(args):
         extras["gradient"] = dict(GC.run(), workload="64^3, L = 32, dt = 0.05, 200 steps, "
                                   "checkpoints every 20, target from eps = 0.1, gradient at "
                                   "eps = 0.15, central differences with step 1e-6")
+        if not args.no_soak:
+            from paper_1611_06288_gb300 import soak as SK
+            extras["soak"] = dict(
+                SK.soak(n=128, steps=10000, workload="growth"),
+                description="Section 6.2 polycrystal growth, Omega = [0,64]^3, eps = 0.25, "
+                            "dt = 0.01, 10^4 steps (t = 100), diagnostics after every step: "
+                            "largest relative mass drift and largest rise of the modified energy")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
