@@ -56,6 +56,9 @@ KERNEL_BYTES = {
     "coarse_source": (80.0, 1),
     "coarse_solve": (0.0, 1),
     "lin_coarse": (0.0, 1),
+    # pointwise start of a step from stored Laplacians, by initial iterate:
+    "start": (104.0, 2),          # phi^k: read b, mu, om, 4 Laplacians (56) write S2, S3,
+                                  # phi, a Laplacian (32), r32 x3, q32 (16)
 }
 
 
@@ -65,33 +68,31 @@ KERNEL_BYTES = {
 # V-cycle (reads colour-0 d 6, colour-1 r and q 8, u 24; writes u 24).
 KERNEL_BYTES_BY_PRECISION = {("mixed", "correct"): (62.0, 1)}
 
+# The start from u^{k+1} := 2 u^k - u^{k-1} (k_start64_extrap): reads b, c,
+# mu^k, om^k, mu^{k-1}, om^{k-1} and six Laplacians (96); writes S2, S3, phi,
+# mu, om and three Laplacians (64) and r32 x3, q32 (16).
+START_BYTES = {"previous": 104.0, "extrapolate_all": 176.0}
+
 
 # DRAM bytes (read + write) of one launch of a kernel class of a precision,
 # from the ncu capture summarised in profiles/ (cold L2); absent where no
 # capture of the current kernel exists.
-# The defect class of the mixed path averages a step's launches: two full
-# defects (150.8 MB each) and the start of the step (k_start64_point,
-# 174.9 MB).  Keyed by the finest level's size the capture ran at (other
-# sizes: null).
-NCU_TRAFFIC = {("mixed", "defect", 128): 158.8e6}   # profiles/k_defect64_fx_128.md, k_start64_point_128.md
+# The defect class of the mixed path is the full defect (150.8 MB a launch);
+# the start of a step has a class of its own.  Keyed by the finest level's
+# size the capture ran at (other sizes: null).
+NCU_TRAFFIC = {("mixed", "defect", 128): 150.8e6}   # profiles/k_defect64_fx_128.md
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
 # counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
 # the three Laplacians' neighbour sums in exact int64 fixed point (no FP64
 # flops) and its rows in 6 DFMA + 4 DADD + 2 DMUL per cell (ncu: DFMA, DADD
-# and DMUL thread-instruction rates 3:2:1): 18 flops.  The start of a warm
-# step (k_start64_point) forms S2, S3 (2 DFMA + 3 DMUL) and the pointwise
-# first defect (4 DFMA + 2 DADD + 2 DMUL): 19 flops.  With two full defects
-# and one start per step (two corrections): 55/3 per launch.
-KERNEL_FLOPS = {("mixed", "defect"): (55.0 / 3.0, 2)}
+# and DMUL thread-instruction rates 3:2:1): 18 flops.
+KERNEL_FLOPS = {("mixed", "defect"): (18.0, 2)}
 
 # Algorithmic bytes per cell of the FP64 defect class (the ALU-bound class
 # above), reported beside its FP64 roofline: a full defect reads phi, mu, om,
-# b, S2, S3 and writes r(3), q FP32 and three Laplacians FP64 (88 B); the
-# start of a step reads b, mu, om and four Laplacians and writes S2, S3,
-# phi^{k+1}, one Laplacian and r(3), q (104 B).  Averaged over a step's
-# launches (two full defects, one start).
-DEFECT_BYTES = (2 * 88.0 + 104.0) / 3.0
+# b, S2, S3 and writes r(3), q FP32 and three Laplacians FP64 (88 B).
+DEFECT_BYTES = 88.0
 
 # FP64 peak of GB300: 2 FP64 FMA lanes per SM per clock (the peak of
 # sm__sass_thread_inst_executed_op_dfma_pred_on is 304 per cycle for 152 SMs)
@@ -113,8 +114,10 @@ def parse():
     ap.add_argument("--nu2", type=int, default=None)
     ap.add_argument("--coarse-sweeps", type=int, default=None)
     ap.add_argument("--cluster-tail", type=int, default=None)
-    ap.add_argument("--guess", default=None, choices=["previous", "extrapolate"],
-                    help="initial iterate of a step (default: the previous step's solution)")
+    ap.add_argument("--guess", default=None,
+                    choices=["previous", "extrapolate", "extrapolate_all"],
+                    help="initial iterate of a step (default: the workload's, 2 u^k - u^{k-1} "
+                         "in all three fields)")
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-soak", action="store_true",
@@ -512,7 +515,7 @@ def run_ours(args):
         """Every GPU leg of one grid size; returns a dict of results."""
         wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
         phi0 = wl.phi0()
-        mixed_kw = wl.mixed()
+        mixed_kw = wl.settings(precision)
         mixed_kw.update(mixed_over or {})
         cells = n ** 3
         # ---- mixed path (headline) ----------------------------------------
@@ -604,12 +607,15 @@ def run_ours(args):
         else:
             per_cell, per_group = KERNEL_BYTES_BY_PRECISION.get(
                 (precision, dom_cls), KERNEL_BYTES.get(dom_cls, (0.0, 1)))
+            if dom_cls == "start":
+                per_cell = START_BYTES[mixed_kw.get("guess", "previous")]
             groups = dom_launches / per_group
             achieved = per_cell * m ** 3 * groups / (dom_time / 1e3) / 1e9 \
                 if dom_time > 0 else 0.0
             bound, peak, unit = "hbm", peaks["hbm_gbs"], "GB/s"
             peak_src = f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"
-        traffic = NCU_TRAFFIC.get((precision, dom_cls, m))
+        traffic = NCU_TRAFFIC.get((precision, dom_cls, m, mixed_kw.get("guess", "previous")),
+                                  NCU_TRAFFIC.get((precision, dom_cls, m)))
         bytes_cell = KERNEL_BYTES.get(dom_cls, (None, 1))[0]
         roofline = {"bound": bound, "achieved": achieved, "peak": peak,
                     "unit": unit, "frac": achieved / peak,
@@ -626,36 +632,63 @@ def run_ours(args):
             roofline["hbm"] = {"algorithmic_bytes_per_cell": DEFECT_BYTES, "achieved": gbs,
                                "unit": "GB/s", "frac": gbs / peaks["hbm_gbs"]}
 
-        # ---- plain FP64 FAS path, same workload and tolerance -------------
-        s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
-                        precision="fp64", step_diagnostics=True)
-        for _ in range(min(warmup, 2)):
-            s64.step(1)
-            s64.diagnostics()
-        ms64, cyc64 = time_steps(s64, fp64_steps)
-        fp64 = {"value": fp64_steps / (ms64 / 1e3), "unit": UNIT, "steps": fp64_steps,
-                "cycles_per_step": cyc64,
-                "solver": "FAS V(2,2) (library defaults), Newton pointwise smoother, full "
-                          "coarsening to 2^3"}
-        fp64["roofline"] = fp64_roofline(s64, n, B)
-        s64.close()
+        # ---- plain FP64 FAS path, same workload, tolerance and initial
+        # iterate (and from phi^k alone, for comparison) ---------------------
+        guess = mixed_kw.get("guess", "previous")
+        guess64 = guess
+        fp64 = None
+        for g in dict.fromkeys((guess64, "previous")):
+            s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                            precision="fp64", step_diagnostics=True, guess=g)
+            # two steps in a row before the extrapolated start applies
+            for _ in range(max(min(warmup, 3), 3 if g == "extrapolate_all" else 1)):
+                s64.step(1)
+                s64.diagnostics()
+            ms64, cyc64 = time_steps(s64, fp64_steps)
+            if fp64 is None:
+                fp64 = {"value": fp64_steps / (ms64 / 1e3), "unit": UNIT, "steps": fp64_steps,
+                        "cycles_per_step": cyc64, "guess": g,
+                        "solver": "FAS V(2,2) (library defaults), Newton pointwise smoother, "
+                                  "full coarsening to 2^3"}
+                fp64["roofline"] = fp64_roofline(s64, n, B)
+            else:
+                fp64["guess_previous"] = {"value": fp64_steps / (ms64 / 1e3), "unit": UNIT,
+                                          "cycles_per_step": cyc64}
+            s64.close()
+
+        # ---- the headline path started from phi^k (mu, omega of step k) ----
+        prev = None
+        if guess != "previous":
+            sp = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
+                           step_diagnostics=True, precision=precision,
+                           **dict(mixed_kw, guess="previous"))
+            for _ in range(warmup):
+                sp.step(1)
+                sp.diagnostics()
+            ms_p, cyc_p = time_steps(sp, steps)
+            prev = {"value": steps / (ms_p / 1e3), "unit": UNIT, "steps": steps,
+                    "ms_per_step": ms_p / steps, "cycles_per_step": cyc_p}
+            sp.close()
 
         out = {"n": n, "wl": wl, "phi0": phi0, "mixed_kw": mixed_kw, "value": value,
                "t_max": t_max, "cycles": cycles, "launches": launches, "clocks": clk,
-               "roofline": roofline, "vcycle": vcyc, "fp64": fp64,
+               "roofline": roofline, "vcycle": vcyc, "fp64": fp64, "guess_previous": prev,
                "kernel_profile_ms": {f"{k[0]}@{n >> k[1]}": round(v[1], 4)
                                      for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
 
         # ---- the other mixed form, same workload, tolerance and settings ---
         if other_leg:
             other = "mixed_df" if precision == "mixed" else "mixed"
+            kw_o = dict(mixed_kw)
+            if other == "mixed_df" and kw_o.get("guess") == "extrapolate_all":
+                kw_o["guess"] = "previous"       # no three-field extrapolation there
             so = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
-                           precision=other, step_diagnostics=True, **mixed_kw)
+                           precision=other, step_diagnostics=True, **kw_o)
             for _ in range(warmup):
                 so.step(1)
                 so.diagnostics()
             ms_o, cyc_o = time_steps(so, steps)
-            out["alt"] = {"precision": other, "dtype": DTYPES[other],
+            out["alt"] = {"precision": other, "dtype": DTYPES[other], "guess": kw_o["guess"],
                           "value": steps / (ms_o / 1e3), "unit": UNIT, "steps": steps,
                           "ms_per_step": ms_o / steps, "cycles_per_step": cyc_o}
             so.close()
@@ -706,7 +739,8 @@ def run_ours(args):
                 "steps": max(3, min(args.steps, 10)), "ms_per_step": r2["t_max"] * 1e3 /
                 max(3, min(args.steps, 10)), "solver": r2["mixed_kw"],
                 "cycles_per_step": r2["cycles"], "dof_updates_per_s": r2["value"] * 256 ** 3,
-                "fp64": r2["fp64"], "mixed_over_fp64": r2["value"] / ws / r2["fp64"]["value"],
+                "fp64": r2["fp64"], "guess_previous": r2["guess_previous"],
+                "mixed_over_fp64": r2["value"] / ws / r2["fp64"]["value"],
                 "roofline": r2["roofline"], "vcycle": r2["vcycle"],
                 "gpu_launches": r2["launches"], "clocks": r2["clocks"],
                 "kernel_profile_ms": r2["kernel_profile_ms"]}
@@ -776,6 +810,7 @@ def run_ours(args):
             "cycles_per_step": r["cycles"],
             "dof_updates_per_s": value * cells,
             "fp64": r["fp64"],
+            "guess_previous": r["guess_previous"],
             "mixed_over_fp64": value / ws / r["fp64"]["value"],
             ("mixed_df" if args.precision == "mixed" else "mixed_fp64_outer"): r.get("alt"),
             "roofline": r["roofline"],

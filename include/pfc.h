@@ -92,8 +92,9 @@ typedef struct pfc_params {
   int    coarse_sweeps;      /* mixed paths: most FP32 sweeps on the coarsest
                                 level (stopping earlier once the largest change
                                 is below 1e-6 of the largest value) */
-  int    guess;              /* initial iterate of a step: PFC_GUESS_PREVIOUS
-                                or PFC_GUESS_EXTRAPOLATE */
+  int    guess;              /* initial iterate of a step: PFC_GUESS_PREVIOUS,
+                                PFC_GUESS_EXTRAPOLATE or
+                                PFC_GUESS_EXTRAPOLATE_ALL */
   double mobility_m0, mobility_m2;
                              /* mobility M(phi) = m0 + m2 phi^2 (m0 > 0,
                                 m2 >= 0), evaluated on every face at
@@ -148,6 +149,19 @@ typedef struct pfc_params {
                                     The step converges to the same solution
                                     (Prop. 3.1) from a residual O(tau^2) in
                                     the first row only. */
+#define PFC_GUESS_EXTRAPOLATE_ALL 2  /* phi, mu and omega of step k+1 :=
+                                    2 u^k - u^{k-1} from the two last
+                                    converged steps (u^k alone after a start,
+                                    pfc_set_state or a failed step); the
+                                    first defect is O(tau^2) in all three rows
+                                    and a smooth step converges in one
+                                    correction.  Holds a second mu and omega
+                                    (16 n^3 bytes per member more; 32 n^3 on
+                                    PFC_MIXED with M == 1, which also keeps
+                                    their Laplacians and then forms the
+                                    iterate and its first defect pointwise
+                                    from them); not with PFC_MIXED_DF
+                                    (EINVAL). */
 
 typedef struct pfc_step_stats {
   int    steps;        /* steps completed by the call */
@@ -261,7 +275,10 @@ const char* pfc_last_error(void);
 #define PFC_K_LIN_PROLONG      11   /* mixed: FP32 d += P d_c */
 #define PFC_K_LIN_COARSE       12   /* mixed: FP32 coarsest-level solve */
 #define PFC_K_CORRECT          13   /* mixed: u += d in FP64 or double-float */
-#define PFC_K_COUNT            14
+#define PFC_K_START            14   /* mixed: pointwise start of a step (S2, S3,
+                                       the iterate and its first defect from
+                                       stored Laplacians) */
+#define PFC_K_COUNT            15
 #define PFC_PROFILE_LEVELS     24
 
 /* Enable timing for the classes whose bit (1 << PFC_K_*) is set in mask

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(PKG, "libpfc.so")
 
 PFC_OK, PFC_EINVAL, PFC_ESIZE, PFC_ENOCONV, PFC_ENAN, PFC_ECUDA = 0, -1, -2, -3, -4, -5
 PFC_FP64, PFC_MIXED, PFC_MIXED_DF = 0, 1, 2
-PFC_GUESS_PREVIOUS, PFC_GUESS_EXTRAPOLATE = 0, 1
+PFC_GUESS_PREVIOUS, PFC_GUESS_EXTRAPOLATE, PFC_GUESS_EXTRAPOLATE_ALL = 0, 1, 2
 PFC_NEWTON, PFC_PICARD = 0, 1
 PFC_POLICY_HYBRID, PFC_POLICY_RB = 0, 1
 PFC_SWEEP_RB, PFC_SWEEP_JACOBI = 0, 1
@@ -134,7 +134,7 @@ _SIGS = {
 # kernel classes of pfc_profile_enable / pfc_profile_read
 KERNEL_CLASSES = ["source", "restrict", "smooth", "residual_restrict", "coarse_source",
                   "prolong", "coarse_solve", "residual_norm", "defect", "lin_smooth",
-                  "lin_restrict", "lin_prolong", "lin_coarse", "correct"]
+                  "lin_restrict", "lin_prolong", "lin_coarse", "correct", "start"]
 PROFILE_LEVELS = 24
 
 _lib = None

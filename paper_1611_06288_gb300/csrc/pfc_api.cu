@@ -39,6 +39,7 @@ int cuda_fail(cudaError_t e, const char* what) {
 constexpr int kMaxLevels = 24;
 constexpr int kMaxMembers = 1024;   // ensemble members of one context (one decide block)
 constexpr size_t kAlign = 256;
+constexpr int kVariants = 6;        // step graphs per ring position (pfc_ctx::variant)
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -91,7 +92,10 @@ int validate(const pfc_params* p) {
     return PFC_EINVAL;
   if (!(p->stiff_lo >= 0) || !(p->stiff_hi >= p->stiff_lo)) return PFC_EINVAL;
   if (!(p->coarse_stiffness >= 0) || p->coarse_sweeps < 1) return PFC_EINVAL;
-  if (p->guess != PFC_GUESS_PREVIOUS && p->guess != PFC_GUESS_EXTRAPOLATE) return PFC_EINVAL;
+  if (p->guess != PFC_GUESS_PREVIOUS && p->guess != PFC_GUESS_EXTRAPOLATE &&
+      p->guess != PFC_GUESS_EXTRAPOLATE_ALL)
+    return PFC_EINVAL;
+  if (p->guess == PFC_GUESS_EXTRAPOLATE_ALL && p->precision == PFC_MIXED_DF) return PFC_EINVAL;
   if (!(p->mobility_m0 > 0) || !(p->mobility_m2 >= 0)) return PFC_EINVAL;
   if (variable_mobility(p) && p->precision != PFC_MIXED) return PFC_EINVAL;
   if (p->cluster_tail < 0 || p->cluster_tail > 2) return PFC_EINVAL;
@@ -168,7 +172,15 @@ struct pfc_ctx {
   struct Graph {
     cudaGraphExec_t exec;
     long long launches_pre, launches_body;
-  } graph[2][3];     // [first defect full / pointwise][position of the phi ring]
+  } graph[pfc::kVariants][3];  // [step variant][position of the phi ring]
+  int variant;       // of the step in flight: 0 full first defect, 1 pointwise,
+                     // 2 + 2 slot + extrap for PFC_GUESS_EXTRAPOLATE_ALL
+  double* mslot[2];  // PFC_GUESS_EXTRAPOLATE_ALL: mu of the last two converged
+  double* oslot[2];  // steps (and omega); mu, om point at the current one
+  double* lmslot[2]; // their Laplacians (lmu, lom point at the current step's;
+  double* loslot[2]; // null without lmu, lom)
+  int mcur;          // slot of the last converged step's mu, omega
+  int nconv;         // converged steps in a row whose mu, omega the slots hold (<= 2)
 };
 
 namespace pfc {
@@ -193,15 +205,25 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base, int members) {
   }
   {
     const bool keep = p->precision == PFC_MIXED && !variable_mobility(p);
+    const bool two = keep && p->guess == PFC_GUESS_EXTRAPOLATE_ALL;
     double* a = keep ? cv.take<double>(n3) : nullptr;
     double* b = keep ? cv.take<double>(n3) : nullptr;
+    double* a2 = two ? cv.take<double>(n3) : nullptr;
+    double* b2 = two ? cv.take<double>(n3) : nullptr;
     if (c) {
       c->lmu = a;
       c->lom = b;
+      c->lmslot[0] = a;
+      c->lmslot[1] = a2;
+      c->loslot[0] = b;
+      c->loslot[1] = b2;
     }
   }
   double* mu = cv.take<double>(n3);
   double* om = cv.take<double>(n3);
+  const bool all = p->guess == PFC_GUESS_EXTRAPOLATE_ALL;
+  double* mu2 = all ? cv.take<double>(n3) : nullptr;
+  double* om2 = all ? cv.take<double>(n3) : nullptr;
   double* S2 = cv.take<double>(n3);
   double* S3 = cv.take<double>(n3);
   const bool fp64 = p->precision == PFC_FP64;
@@ -212,6 +234,12 @@ size_t carve(pfc_ctx* c, const pfc_params* p, char* base, int members) {
   if (c) {
     c->mu = mu;
     c->om = om;
+    c->mslot[0] = mu;
+    c->mslot[1] = mu2;
+    c->oslot[0] = om;
+    c->oslot[1] = om2;
+    c->mcur = 0;
+    c->nconv = 0;
     c->S2 = S2;
     c->S3 = S3;
     c->nl = nl;
@@ -442,6 +470,19 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
                                        &decided));
     return decided ? PFC_OK : enqueue_decide(c, h, use_handle, 1);
   }
+  if (c->p.guess == PFC_GUESS_EXTRAPOLATE_ALL && c->nconv >= 2 && c->lmu) {
+    // the two last steps' mu, omega and all their Laplacians are stored:
+    // S2, S3, the extrapolated iterate and the first defect in one pass
+    const int x = c->mcur;
+    const DecideArgs da = decide_args(c, h, use_handle, 1);
+    bool decided = false;
+    PFC_CUDA(mixed_enqueue_start_extrap(c->mx, lv.L, lv.u, lv.S, lv.b, cprev, c->lap[c->ib],
+                                        c->lap[c->ic], c->mslot[x], c->oslot[x],
+                                        c->lmslot[x], c->loslot[x], c->lmu, c->lom,
+                                        c->lap[c->ia], c->partials, c->dout, c->st, pr, c->nb,
+                                        c->c1m, &da, &decided));
+    return decided ? PFC_OK : enqueue_decide(c, h, use_handle, 1);
+  }
   if (extrapolate && df_state(&c->p)) {
     PFC_TIMED(pr, PFC_K_SOURCE, 0, 2, c->st,
               launch_guess_df(lv.L, as_df(lv.b), as_df(cprev), as_df(c->S2), as_df(c->S3),
@@ -468,9 +509,16 @@ int enqueue_pre(pfc_ctx* c, const Level64& lv, cudaGraphConditionalHandle h, int
       fine = c->lev[l].b;
     }
   }
-  if (!extrapolate)
+  if (c->p.guess == PFC_GUESS_EXTRAPOLATE_ALL) {
+    // the new iterate goes to the slots of mu^{k-1}, omega^{k-1} (lv.u[1], lv.u[2])
+    PFC_TIMED(pr, PFC_K_SOURCE, 0, 1, c->st,
+              launch_guess_all(n3, c->nconv >= 2, lv.b, cprev, c->mslot[c->mcur],
+                               c->oslot[c->mcur], lv.u[1], lv.u[2], lv.u[0], c->st,
+                               c->prof.mask == 0));
+  } else if (!extrapolate) {
     PFC_CUDA(cudaMemcpyAsync(lv.u[0], lv.b, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
                              c->st));
+  }
   if (c->M[0]) {
     // M(A phi_*) of this step (Section 5: phi_* = 3/2 phi^k - 1/2 phi^{k-1})
     PFC_CUDA(launch_face_mobility(c->p.n, c->p.mobility_m0, c->p.mobility_m2, lv.b, cprev,
@@ -618,11 +666,32 @@ StepState combined_state(const pfc_ctx* c) {
 // whether the first defect is pointwise (the state is the last step's
 // solution, guess phi^{k+1} := phi^k, and lmu, lom hold its Laplacians).
 bool step_prepare(pfc_ctx* c, Level64* lv) {
-  level0(c, lv);
   const bool warm = c->warm && c->lmu && c->p.guess == PFC_GUESS_PREVIOUS;
+  c->variant = warm ? 1 : 0;
+  if (c->p.guess == PFC_GUESS_EXTRAPOLATE_ALL) {
+    // the step's iterate takes the other slot; mcur keeps the last solution's
+    const int y = 1 - c->mcur;
+    c->mu = c->mslot[y];
+    c->om = c->oslot[y];
+    c->lmu = c->lmslot[y];
+    c->lom = c->loslot[y];
+    c->variant = 2 + 2 * y + (c->nconv >= 2 ? 1 : 0);
+  }
+  level0(c, lv);
   c->warm = 0;                       // until this step has converged
   c->diag_valid = 0;
   return warm;
+}
+
+// A step stopped before its end (another member of its group failed): the
+// state stays the last solution.
+void step_abandon(pfc_ctx* c) {
+  if (c->p.guess != PFC_GUESS_EXTRAPOLATE_ALL) return;
+  c->mu = c->mslot[c->mcur];
+  c->om = c->oslot[c->mcur];
+  c->lmu = c->lmslot[c->mcur];
+  c->lom = c->loslot[c->mcur];
+  c->nconv = 0;
 }
 
 // End of a step whose device state (hstate) has been read back: the step's
@@ -640,7 +709,21 @@ int step_finish(pfc_ctx* c, pfc_step_stats* stats) {
     stats->residual = s.rms;
     stats->residual0 = s.rms0;
   }
-  if (rc == PFC_ENAN) {
+  if (c->p.guess == PFC_GUESS_EXTRAPOLATE_ALL) {
+    if (rc) {
+      // back to the last solution's mu, omega (the failed iterate's slot held
+      // mu^{k-1}, which is gone)
+      c->mu = c->mslot[c->mcur];
+      c->om = c->oslot[c->mcur];
+      c->lmu = c->lmslot[c->mcur];
+      c->lom = c->loslot[c->mcur];
+      c->nconv = 0;
+    } else {
+      c->mcur = 1 - c->mcur;
+      if (c->nconv < 2) c->nconv += 1;
+    }
+  }
+  if (rc == PFC_ENAN && c->p.guess != PFC_GUESS_EXTRAPOLATE_ALL) {
     cudaMemsetAsync(c->mu, 0, n3 * sizeof(double), c->st);
     cudaMemsetAsync(c->om, 0, n3 * sizeof(double), c->st);
   }
@@ -661,7 +744,7 @@ int step_once(pfc_ctx* c, pfc_step_stats* stats) {
   const bool warm = step_prepare(c, &lv);
   int rc = PFC_OK;
   if (c->use_graphs && c->prof.mask == 0) {
-    pfc_ctx::Graph* g = &c->graph[warm ? 1 : 0][c->ia];
+    pfc_ctx::Graph* g = &c->graph[c->variant][c->ia];
     if (!g->exec) {
       rc = build_graph(c, lv, g, warm);
       if (rc) return rc;
@@ -903,6 +986,7 @@ int pfc_batch_init(pfc_ctx** out, const pfc_params* p, int members, const double
 int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev) {
   if (!c || !any_phi) return PFC_EINVAL;
   c->warm = 0;                       // mu, omega are no longer the state's own
+  c->nconv = 0;
   c->diag_valid = 0;
   const int64_t n3 = (int64_t)c->p.n * c->p.n * c->p.n * c->nb;
   const size_t bytes = (size_t)n3 * sizeof(double);
@@ -934,7 +1018,7 @@ int pfc_set_state(pfc_ctx* c, const double* any_phi, const double* any_phi_prev)
     if (scale != c->tau_scale) {
       // the step graphs hold the FP32 level constants: rebuild them
       c->graph_gen += 1;
-      for (int v = 0; v < 2; ++v)
+      for (int v = 0; v < kVariants; ++v)
         for (int r = 0; r < 3; ++r)
           if (c->graph[v][r].exec) {
             cudaGraphExecDestroy(c->graph[v][r].exec);
@@ -1137,7 +1221,7 @@ int pfc_profile_read(pfc_ctx* c, int kclass, int level, long long* launches, dou
 void pfc_destroy(pfc_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
-  for (int v = 0; v < 2; ++v)
+  for (int v = 0; v < kVariants; ++v)
     for (int r = 0; r < 3; ++r)
       if (c->graph[v][r].exec) cudaGraphExecDestroy(c->graph[v][r].exec);
   if (c->cap_st) cudaStreamDestroy(c->cap_st);
@@ -1351,7 +1435,7 @@ int group_step_once(pfc_group* g, pfc_step_stats* stats) {
   int key[3 * kMaxGroup] = {0};
   for (int i = 0; i < g->count; ++i) {
     warm[i] = step_prepare(g->ctx[i], &lv[i]);
-    key[3 * i] = warm[i] ? 1 : 0;
+    key[3 * i] = g->ctx[i]->variant;
     key[3 * i + 1] = g->ctx[i]->ia;
     key[3 * i + 2] = g->ctx[i]->graph_gen;
   }
@@ -1389,7 +1473,10 @@ int group_step_once(pfc_group* g, pfc_step_stats* stats) {
     // a context's body ran while it had a running member
     c->prof.launches += gr->pre[i] + gr->body[i] * (long long)combined_state(c).iters;
     // a context still running when another failed takes no step
-    if (failed && combined_state(c).status == kStepRunning) continue;
+    if (failed && combined_state(c).status == kStepRunning) {
+      step_abandon(c);
+      continue;
+    }
     const int rc = step_finish(c, stats ? &stats[i] : nullptr);
     if (rc && first == PFC_OK) first = rc;
   }

@@ -62,6 +62,33 @@ __global__ void k_source_guess(Lvl L, const double* __restrict__ b,
   omg[s.c] = 0.5 * fma(3.0, lb, -lc);
 }
 
+// Initial iterate of PFC_GUESS_EXTRAPOLATE_ALL: every unknown extrapolated
+// linearly from the two last converged steps, phi = 2 b - c (b = phi^k,
+// c = phi^{k-1}), mu = 2 mu^k - mu^{k-1}, omega = 2 omega^k - omega^{k-1}
+// (extrap), or the last step's values (phi = b; mu, omega copied) while
+// fewer than two converged steps are at hand.  mu^{k-1}, omega^{k-1} live in
+// the slots that receive the new iterate (m1, o1, in place).
+__global__ void k_guess_all(int64_t cells, int extrap, const double* __restrict__ b,
+                            const double* __restrict__ c, const double* __restrict__ m0,
+                            const double* __restrict__ o0, double* m1, double* o1,
+                            double* __restrict__ phi) {
+  pdl_wait();
+  pdl_trigger();
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < cells;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const double bb = __ldg(b + t), mm = __ldg(m0 + t), oo = __ldg(o0 + t);
+    if (extrap) {
+      phi[t] = fma(2.0, bb, -__ldg(c + t));
+      m1[t] = fma(2.0, mm, -m1[t]);
+      o1[t] = fma(2.0, oo, -o1[t]);
+    } else {
+      phi[t] = bb;
+      m1[t] = mm;
+      o1[t] = oo;
+    }
+  }
+}
+
 // mu_g = S2 + f(phi_g, b) + (1-eps)/2 phi_g + Lap omega_g: row 2 of
 // N(u) = S (Eq. 5.5) solved for mu at the extrapolated phi_g, omega_g.
 __global__ void k_mu_guess(Lvl L, const double* __restrict__ phig,
@@ -597,6 +624,13 @@ inline int reduce_blocks(int64_t cells) {
 }
 
 }  // namespace
+
+cudaError_t launch_guess_all(int64_t cells, bool extrap, const double* b, const double* c,
+                             const double* m0, const double* o0, double* m1, double* o1,
+                             double* phi, cudaStream_t st, bool pdl) {
+  return launch_ex(pdl, k_guess_all, dim3(grid_for(cells)), dim3(kThreads), 0, st, cells,
+                   extrap ? 1 : 0, b, c, m0, o0, m1, o1, phi);
+}
 
 cudaError_t launch_guess(const Lvl& L, const double* b, const double* c, double* S2,
                          double* S3, double* phig, double* mug, double* omg, cudaStream_t st) {

@@ -123,6 +123,11 @@ void prof_harvest(Prof* pr);
 // FP64 kernels (pfc_fp64.cu).  All enqueue on `st` and return the launch error.
 // S2, S3 and the extrapolated initial iterate (phi_g, mu_g, omega_g) of a
 // step from b = phi^k, c = phi^{k-1} (two launches).
+// PFC_GUESS_EXTRAPOLATE_ALL's initial iterate (k_guess_all): phi = 2b - c,
+// m1 = 2 m0 - m1, o1 = 2 o0 - o1 (extrap), else phi = b, m1 = m0, o1 = o0.
+cudaError_t launch_guess_all(int64_t cells, bool extrap, const double* b, const double* c,
+                             const double* m0, const double* o0, double* m1, double* o1,
+                             double* phi, cudaStream_t st, bool pdl);
 cudaError_t launch_guess(const Lvl& L, const double* b, const double* c, double* S2,
                          double* S3, double* phig, double* mug, double* omg, cudaStream_t st);
 cudaError_t launch_source(const Lvl& L, const double* b, const double* c, double* S2,

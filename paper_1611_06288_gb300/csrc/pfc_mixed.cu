@@ -563,6 +563,73 @@ __global__ void __launch_bounds__(256) k_start64_point(
   if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
 }
 
+// Start of a step from the extrapolated iterate u^{k+1} := 2 u^k - u^{k-1}
+// of all three fields, in one pass with no stencil: the Laplacian is linear,
+// so the iterate's Laplacians are 2 Lap u^k - Lap u^{k-1} of the ones the two
+// last steps' final defects stored (lapb, lapc of phi^k = b, phi^{k-1} = c;
+// lapmu0, lapom0 of mu^k, omega^k; lapmu1, lapom1 of mu^{k-1}, omega^{k-1}).
+// S2, S3 (Eqs. 5.9-5.10) with the operations of k_start64_point, the iterate
+// phi with those of k_guess_all, the first defect with defect_rows (S1 = b).
+// mu1, om1, lapmu1, lapom1 hold step k-1's fields on entry and the iterate's
+// on exit: each cell is read, then written, by the same thread (plain loads).
+// lap receives the iterate's Laplacian of phi.  Grid: blockIdx.y the member,
+// a grid-stride loop over its cells; per-block sums of |r|^2.
+__global__ void __launch_bounds__(256) k_start64_extrap(
+    Lvl L, const double* __restrict__ b, const double* __restrict__ c,
+    const double* __restrict__ lapb, const double* __restrict__ lapc,
+    const double* __restrict__ mu0, const double* __restrict__ om0,
+    const double* __restrict__ lapmu0, const double* __restrict__ lapom0, double* mu1,
+    double* om1, double* lapmu1, double* lapom1, double* __restrict__ S2,
+    double* __restrict__ S3, double* __restrict__ phi, float* __restrict__ r1,
+    float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
+    double* __restrict__ lap, const double* __restrict__ c1m) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ float sm[32];
+  const int n = L.n;
+  const int cells = n * n * n;
+  const int m = blockIdx.y;
+  const size_t off = (size_t)m * cells;
+  b += off, c += off, lapb += off, lapc += off, mu0 += off, om0 += off;
+  lapmu0 += off, lapom0 += off, mu1 += off, om1 += off, lapmu1 += off, lapom1 += off;
+  S2 += off, S3 += off, phi += off, lap += off;
+  r1 += off, r2 += off, r3 += off, q += off;
+  partials += (size_t)m * gridDim.x;
+  const double c1 = c1m ? c1m[m] : L.c1;
+  const float c1f = d2f_rn(c1);
+  float acc = 0.f;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
+    const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
+    const double pb = __ldg(b + t), lbr = __ldg(lapb + t), lcr = __ldg(lapc + t);
+    const double s2 = fma(3.0, L.g * lbr, fma(c1, pb, -(L.g * lcr)));
+    const double s3 = 0.5 * (L.g * lbr);
+    const double p = fma(2.0, pb, -__ldg(c + t));
+    const double mm = fma(2.0, __ldg(mu0 + t), -mu1[t]);
+    const double w = fma(2.0, __ldg(om0 + t), -om1[t]);
+    const double lp = fma(2.0, lbr, -lcr);
+    const double lm = fma(2.0, __ldg(lapmu0 + t), -lapmu1[t]);
+    const double lo = fma(2.0, __ldg(lapom0 + t), -lapom1[t]);
+    S2[t] = s2;
+    S3[t] = s3;
+    phi[t] = p;
+    mu1[t] = mm;
+    om1[t] = w;
+    lap[t] = lp;
+    lapmu1[t] = lm;
+    lapom1[t] = lo;
+    float xf, yf, zf, qf;
+    defect_rows(L, c1, c1f, p, mm, w, pb, lm, lo, lp, pb, s2, s3, xf, yf, zf, qf);
+    acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
+    const int o = split_index(i, j, k, n);
+    r1[o] = xf;
+    r2[o] = yf;
+    r3[o] = zf;
+    q[o] = qf;
+  }
+  acc = block_sum_f(acc, sm);
+  if (threadIdx.x == 0) partials[blockIdx.x] = (double)acc;
+}
+
 // Face mobilities of a step: M(A phi_*) on the faces i+1/2 of each axis for
 // M(phi) = m0 + m2 phi^2, phi_* = 3/2 b - 1/2 c (b = phi^k, c = phi^{k-1});
 // the face i+1/2 of an axis is stored at cell i.
@@ -3735,6 +3802,27 @@ cudaError_t launch_start64_point(const Lvl& L, const double* b, const double* mu
   return e;
 }
 
+cudaError_t launch_start64_extrap(const Lvl& L, const double* b, const double* c,
+                                  const double* lapb, const double* lapc, const double* mu0,
+                                  const double* om0, const double* lapmu0,
+                                  const double* lapom0, double* mu1, double* om1,
+                                  double* lapmu1, double* lapom1, double* S2, double* S3,
+                                  double* phi, float* r1, float* r2, float* r3, float* q,
+                                  double* partials, double* out, double* lap, cudaStream_t st,
+                                  int members, const double* c1m, bool pdl,
+                                  const DecideArgs* da, bool* decided) {
+  const int wave = wave_blocks(k_start64_extrap, (int64_t)L.n * L.n * L.n * members);
+  int nbx = wave / members;
+  const int64_t need = ((int64_t)L.n * L.n * L.n + kReduceThreads - 1) / kReduceThreads;
+  if (nbx > need) nbx = (int)need;
+  if (nbx < 1) nbx = 1;
+  cudaError_t e = launch_ex(pdl, k_start64_extrap, dim3(nbx, members), dim3(kReduceThreads), 0,
+                            st, L, b, c, lapb, lapc, mu0, om0, lapmu0, lapom0, mu1, om1, lapmu1,
+                            lapom1, S2, S3, phi, r1, r2, r3, q, partials, lap, c1m);
+  if (e == cudaSuccess) e = launch_reduce1(pdl, partials, nbx, out, members, st, da, decided);
+  return e;
+}
+
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,
                                  double* Mx, double* My, double* Mz, cudaStream_t st) {
   const Launch3 g = launch3(n, n, n);
@@ -4042,12 +4130,30 @@ cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* cons
                                       double* partials, double* dout, cudaStream_t st, Prof* pr,
                                       int members, const double* c1m, const DecideArgs* da,
                                       bool* decided) {
-  prof_begin(pr, PFC_K_DEFECT, st);
+  prof_begin(pr, PFC_K_START, st);
   cudaError_t e = launch_start64_point(L0, b, u[1], u[2], lapb, lapc, lapmu, lapom, S[1], S[2],
                                        u[0], mx.r[0][0], mx.r[0][1], mx.r[0][2], mx.q[0],
                                        partials, dout, lap, st, members, c1m,
                                        !pr || pr->mask == 0, da, decided);
-  prof_end(pr, PFC_K_DEFECT, 0, 2, st);
+  prof_end(pr, PFC_K_START, 0, 2, st);
+  return e;
+}
+
+cudaError_t mixed_enqueue_start_extrap(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                       double* const S[3], const double* b, const double* c,
+                                       const double* lapb, const double* lapc,
+                                       const double* mu0, const double* om0,
+                                       const double* lapmu0, const double* lapom0,
+                                       double* lapmu1, double* lapom1, double* lap,
+                                       double* partials, double* dout, cudaStream_t st,
+                                       Prof* pr, int members, const double* c1m,
+                                       const DecideArgs* da, bool* decided) {
+  prof_begin(pr, PFC_K_START, st);
+  cudaError_t e = launch_start64_extrap(L0, b, c, lapb, lapc, mu0, om0, lapmu0, lapom0, u[1],
+                                        u[2], lapmu1, lapom1, S[1], S[2], u[0], mx.r[0][0],
+                                        mx.r[0][1], mx.r[0][2], mx.q[0], partials, dout, lap,
+                                        st, members, c1m, !pr || pr->mask == 0, da, decided);
+  prof_end(pr, PFC_K_START, 0, 2, st);
   return e;
 }
 

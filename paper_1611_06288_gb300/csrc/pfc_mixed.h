@@ -91,6 +91,21 @@ cudaError_t mixed_enqueue_start_point(MixedBufs& mx, const Lvl& L0, double* cons
                                       int members, const double* c1m,
                                       const DecideArgs* da = nullptr, bool* decided = nullptr);
 
+// Start of a step from u^{k+1} := 2 u^k - u^{k-1} in all three fields
+// (u[1], u[2] and lapmu1, lapom1 hold step k-1's mu, omega and their
+// Laplacians on entry, the iterate's on exit; u[0] receives phi): S2, S3,
+// the iterate, its Laplacians and the first defect in one pointwise pass
+// from the stored Laplacians, then the reduction (and decision, as above).
+cudaError_t mixed_enqueue_start_extrap(MixedBufs& mx, const Lvl& L0, double* const u[3],
+                                       double* const S[3], const double* b, const double* c,
+                                       const double* lapb, const double* lapc,
+                                       const double* mu0, const double* om0,
+                                       const double* lapmu0, const double* lapom0,
+                                       double* lapmu1, double* lapom1, double* lap,
+                                       double* partials, double* dout, cudaStream_t st,
+                                       Prof* pr, int members, const double* c1m,
+                                       const DecideArgs* da = nullptr, bool* decided = nullptr);
+
 // Defect r = S - N(u) of the df state -> FP32 r and q on level 0, and the
 // sum of |r|^2 at dout[0] (two launches).  S[0] is S1 (= b in a time step).
 cudaError_t mixed_enqueue_defect(MixedBufs& mx, const Lvl& L0, float2* const u[3],

@@ -36,7 +36,8 @@ def make_params(n, L, eps, dt, tol=1e-9, nu1=2, nu2=2, max_cycles=50,
     p.stiff_hi, p.stiff_lo = float(stiff_hi), float(stiff_lo)
     p.coarse_stiffness = float(coarse_stiffness)
     p.coarse_sweeps = int(coarse_sweeps)
-    p.guess = {"previous": B.PFC_GUESS_PREVIOUS, "extrapolate": B.PFC_GUESS_EXTRAPOLATE}[guess]
+    p.guess = {"previous": B.PFC_GUESS_PREVIOUS, "extrapolate": B.PFC_GUESS_EXTRAPOLATE,
+               "extrapolate_all": B.PFC_GUESS_EXTRAPOLATE_ALL}[guess]
     p.mobility_m0, p.mobility_m2 = float(mobility[0]), float(mobility[1])
     p.cluster_tail = int(cluster_tail)
     p.step_diagnostics = 1 if step_diagnostics else 0

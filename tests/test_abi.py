@@ -151,6 +151,24 @@ def test_mobility_params(libpfc):
     assert B.pfc_batch_workspace_bytes(p, 2) > 0     # size only; pfc_batch_init refuses
 
 
+def test_guess_param(libpfc):
+    """guess 0..2; extrapolating all three fields holds a second mu and omega
+    (and, on the mixed path, a second pair of their Laplacians) and is
+    refused with the double-float state."""
+    p = B.pfc_default_params()
+    p.n, p.L, p.eps, p.dt = 32, 32.0, 0.1, 0.05
+    for prec, fields in ((B.PFC_FP64, 2), (B.PFC_MIXED, 4)):
+        p.precision, p.guess = prec, B.PFC_GUESS_PREVIOUS
+        base = B.pfc_workspace_bytes(p)
+        p.guess = B.PFC_GUESS_EXTRAPOLATE_ALL
+        extra = fields * 8 * 32 ** 3
+        assert base + extra <= B.pfc_workspace_bytes(p) <= base + extra + 4096
+        p.guess = 3
+        assert B.pfc_workspace_bytes(p) == 0
+    p.precision, p.guess = B.PFC_MIXED_DF, B.PFC_GUESS_EXTRAPOLATE_ALL
+    assert B.pfc_workspace_bytes(p) == 0
+
+
 def test_cluster_tail_param(libpfc):
     """cluster_tail is 0, 1 or 2 (default 0) and does not change the
     workspace: the cluster kernel keeps its levels in shared memory."""

@@ -88,3 +88,16 @@ def test_oracle_all_cores_timing_runs_spawned_replicas():
     agg, slowest, cycles = bench.oracle_all_cores(8, 2)
     assert slowest > 0 and agg == pytest.approx(2 / slowest)
     assert len(cycles) == 2 and all(c >= 1 for c in cycles)
+
+
+def test_workload_settings_by_precision():
+    """The timed runs of the smooth sweep start from the three-field
+    extrapolation on the FP64 and mixed paths; the double-float state, which
+    has none, starts from phi^k; the FP64 path takes no mixed settings."""
+    from paper_1611_06288_gb300 import workloads as W
+    wl = W.smooth_sweep(128)
+    assert wl.settings("mixed") == dict(wl.mixed(), guess="extrapolate_all")
+    assert wl.settings("fp64") == {"guess": "extrapolate_all"}
+    assert wl.settings("mixed_df")["guess"] == "previous"
+    assert "guess" not in wl.mixed()
+    assert W.growth(32).settings("mixed")["guess"] == "previous"

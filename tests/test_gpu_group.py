@@ -82,6 +82,32 @@ def test_group_matches_its_ensembles_alone():
         b.close()
 
 
+def test_group_with_extrapolated_guesses_matches_alone():
+    """Ensembles whose steps start from 2 u^k - u^{k-1} (guess
+    extrapolate_all; the graph of a step depends on which mu, omega slot it
+    writes): 5 group steps equal 5 steps of each ensemble alone, bit for
+    bit, and the members match the oracle."""
+    kw = dict(tol=1e-12, max_cycles=80, guess="extrapolate_all", **W.ENSEMBLE_SETTINGS)
+    spec = {16: members(16, 2, 5), 24: members(24, 2, 6)}
+    grouped = [PFCBatch(n, L, eps, DT, phi0, **kw) for n, (eps, phi0) in spec.items()]
+    alone = [PFCBatch(n, L, eps, DT, phi0, **kw) for n, (eps, phi0) in spec.items()]
+    g = PFCGroup(grouped)
+    for _ in range(5):
+        gst = g.step(1)
+        for b, st in zip(alone, gst):
+            assert b.step(1).cycles_last == st.cycles_last
+    for a, b, (n, (eps, phi0)) in zip(grouped, alone, spec.items()):
+        assert np.array_equal(host(a.phi()), host(b.phi()))
+        assert np.array_equal(host(a.mu()), host(b.mu()))
+        phi = host(a.phi())
+        for m in range(len(eps)):
+            ref = O.run(phi0[m], 5, L / n, O.Params(eps=eps[m], tau=DT), tol=1e-12)
+            assert rel_l2(phi[m], ref[0]) <= PARITY_RTOL, (n, m)
+    g.close()
+    for b in grouped + alone:
+        b.close()
+
+
 def test_group_of_a_single_run_and_an_ensemble():
     """A pfc_init context (16^3, random start) grouped with a 24^3 ensemble:
     the single run equals its oracle run."""

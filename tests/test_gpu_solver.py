@@ -112,6 +112,52 @@ def test_extrapolated_guess(precision, graphs):
     assert cyc["extrapolate"] < cyc["previous"], cyc
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("graphs", [True, False])
+def test_extrapolate_all_guess(precision, graphs):
+    """guess = extrapolate_all starts a step from 2 u^k - u^{k-1} in phi, mu
+    and omega once two steps in a row have converged: the same converged
+    trajectory as the oracle (which starts from phi^k); pfc_set_state drops
+    back to u^k for two steps and keeps the trajectory; on a smooth
+    trajectory the mixed path then takes one correction per step."""
+    wl = W.random16()
+    phi0 = wl.phi0()
+    ref = oracle_run(phi0, 7, wl.h, wl.eps, wl.dt, "newton")
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=1e-12, precision=precision,
+                  guess="extrapolate_all", max_cycles=60)
+    s.use_graphs(graphs)
+    for k in range(7):
+        if k == 4:
+            s.set_state(ref[3][0], ref[2][0])
+        st = s.step(1)
+        assert st.residual <= 1e-12
+        assert rel_l2(host(s.phi()), ref[k][0]) <= PARITY_RTOL, k
+        assert rel_l2(host(s.mu()), ref[k][1]) <= PARITY_RTOL, k
+    s.close()
+    wl = W.smooth_sweep(32)
+    kw = wl.mixed() if precision != "fp64" else {}
+    cyc = {}
+    for guess in ("previous", "extrapolate_all"):
+        s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), tol=wl.tol, precision=precision,
+                      guess=guess, **kw)
+        s.use_graphs(graphs)
+        s.step(3)
+        cyc[guess] = s.step(4).cycles_total
+        s.close()
+    assert cyc["extrapolate_all"] < cyc["previous"], cyc
+    if precision == "mixed":
+        assert cyc["extrapolate_all"] == 4, cyc
+
+
+def test_extrapolate_all_guess_is_refused_with_df_state():
+    """The double-float state path has no extrapolated mu, omega: the
+    parameters are refused (no workspace size) before any allocation."""
+    wl = W.random16()
+    with pytest.raises(B.PFCError):
+        PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), precision="mixed_df",
+                  guess="extrapolate_all")
+
+
 @pytest.mark.parametrize("n,coarsest", [(4, 2), (12, 6), (20, 10), (24, 6)])
 def test_uneven_sizes_and_level_counts(n, coarsest):
     """Grids that are not powers of two and the smallest grid, against the

@@ -521,3 +521,39 @@ def test_unit_mobility_is_the_constant_scheme():
     a2 = O.run(wl.phi0(), 2, wl.h, O.Params(eps=wl.eps, tau=wl.dt, mobility=(1.0, 0.0)),
                tol=1e-13)[0]
     np.testing.assert_allclose(a2, a1, atol=1e-13)
+
+
+def test_three_field_extrapolation_misses_by_tau_squared():
+    """The iterate u^{k+1} := 2 u^k - u^{k-1} in phi, mu and omega, from two
+    converged steps of a smooth mode, leaves a first residual of order
+    tau^2 (u^{k+1} - 2 u^k + u^{k-1} = tau^2 u_tt + O(tau^3)), the start
+    from u^k one of order tau: at the same time t = 0.4, halving tau
+    divides the first by four and the second by two.  This is why the
+    extrapolated start needs one correction where u^k needs two."""
+    n, L, eps = 16, 32.0, 0.025
+    h = L / n
+    x = np.arange(n) * h
+    X, Y, Z = np.meshgrid(x, x, x, indexing="ij")
+    phi0 = (0.1 * np.sin(2 * np.pi * X / L) * np.cos(2 * np.pi * Y / L)
+            * np.sin(2 * np.pi * Z / L))
+
+    def first_residuals(tau, steps):
+        prm = O.Params(eps=eps, tau=tau)
+        c = b = phi0
+        mu = om = 0 * phi0
+        hist = []
+        for _ in range(steps):
+            a, mu, om = O.solve_step(b, c, [b, mu, om], h, prm, 1e-12).u
+            hist.append((a, mu, om))
+            c, b = b, a
+        (p1, m1, o1), (p2, m2, o2) = hist[-1], hist[-2]
+        S = O.source_S(b, c, h, prm)
+        ext = O.rms(O.residual(S, [2 * p1 - p2, 2 * m1 - m2, 2 * o1 - o2], b, h, prm))
+        prev = O.rms(O.residual(S, [p1, m1, o1], b, h, prm))
+        return ext, prev
+
+    r = [first_residuals(tau, steps) for tau, steps in ((0.1, 4), (0.05, 8), (0.025, 16))]
+    for (e1, p1), (e2, p2) in zip(r, r[1:]):
+        assert 3.6 <= e1 / e2 <= 4.4, (e1, e2)
+        assert 1.8 <= p1 / p2 <= 2.2, (p1, p2)
+        assert e2 < 0.01 * p2
