@@ -559,6 +559,33 @@ int pfc_op_defect(int n, double h, double eps, double tau, const double* d_phi,
                   float* d_r1, float* d_r2, float* d_r3, float* d_q,
                   void* d_scratch, double* out, double* d_lap, void* stream);
 
+/* The start of a time step from u^{k+1} := 2 u^k - u^{k-1} in phi, mu and
+ * omega (PFC_GUESS_EXTRAPOLATE_ALL on PFC_MIXED) in one pointwise pass.
+ * Inputs: phi^k = d_b, phi^{k-1} = d_c, mu^k = d_mu0, omega^k = d_om0 and
+ * the unscaled 7-point Laplacians (neighbour sum - 6 centre) d_lapb,
+ * d_lapc, d_lapmu0, d_lapom0 of those four fields; d_mu1, d_om1 hold
+ * mu^{k-1}, omega^{k-1} and d_lapmu1, d_lapom1 their Laplacians on entry,
+ * and receive the iterate's mu, omega and Laplacians.  Outputs: S2, S3 of
+ * Eqs. 5.9-5.10, the iterate phi = 2 phi^k - phi^{k-1} (d_phi) and its
+ * Laplacian (d_lap), formed as 2 Lap u^k - Lap u^{k-1} (the Laplacian is
+ * linear); the residual r = S - N(u) of the iterate (Eqs. 5.4-5.6, with
+ * S1 = phi^k) rounded to FP32 into d_r1..3 and q as in pfc_op_defect
+ * (colour-split); *out = RMS of r (blocking).  The combinations of phi^k,
+ * phi^{k-1} and their Laplacians are exact in 64-bit fixed point (inputs
+ * quantised to 2^-54, |v| < 32; larger values take FP64), those of mu and
+ * omega FP64, so results differ from FP64 arithmetic by about 1e-16
+ * absolute.  d_scratch: pfc_reduce_scratch_bytes(n) bytes.  Device
+ * pointers, caller-owned, n^3 doubles (floats for r, q) each; n even;
+ * PFC_EINVAL on a null pointer or a bad size. */
+int pfc_op_start_extrap(int n, double h, double eps, double tau, const double* d_b,
+                        const double* d_c, const double* d_lapb, const double* d_lapc,
+                        const double* d_mu0, const double* d_om0, const double* d_lapmu0,
+                        const double* d_lapom0, double* d_mu1, double* d_om1,
+                        double* d_lapmu1, double* d_lapom1, double* d_S2, double* d_S3,
+                        double* d_phi, double* d_lap, float* d_r1, float* d_r2,
+                        float* d_r3, float* d_q, void* d_scratch, double* out,
+                        void* stream);
+
 /* u += d (FP64 += FP32) for the three components; d colour-split.  n even. */
 int pfc_op_correct(int n, double* d_u1, double* d_u2, double* d_u3,
                    const float* d_d1, const float* d_d2, const float* d_d3,

@@ -97,6 +97,7 @@ _SIGS = {
     "pfc_op_residual_norm_static": (_I, [_I, _D, _D, _D] + [_P] * 7 +
                                     [ctypes.POINTER(_D), _P]),
     "pfc_op_defect": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P, _P]),
+    "pfc_op_start_extrap": (_I, [_I, _D, _D, _D] + [_P] * 21 + [ctypes.POINTER(_D), _P]),
     "pfc_op_lin_smooth": (_I, [_I, _D, _D, _D, _I, _I] + [_P] * 7 + [_P]),
     "pfc_op_correct": (_I, [_I] + [_P] * 6 + [_P]),
     "pfc_op_defect_df": (_I, [_I, _D, _D, _D] + [_P] * 12 + [ctypes.POINTER(_D), _P, _P]),
@@ -448,6 +449,17 @@ def pfc_op_residual_norm_static(n, h, eps, tau, phi, mu, om, S1, S2, S3, b, stre
                                             ptr(S1), ptr(S2), ptr(S3), ptr(b),
                                             ctypes.byref(out), stream),
           "pfc_op_residual_norm_static")
+    return out.value
+
+
+def pfc_op_start_extrap(n, h, eps, tau, b, c, lapb, lapc, mu0, om0, lapmu0, lapom0, mu1, om1,
+                        lapmu1, lapom1, S2, S3, phi, lap, r1, r2, r3, q, scratch,
+                        stream=None):
+    out = ctypes.c_double()
+    args = [b, c, lapb, lapc, mu0, om0, lapmu0, lapom0, mu1, om1, lapmu1, lapom1, S2, S3, phi,
+            lap, r1, r2, r3, q, scratch]
+    check(lib().pfc_op_start_extrap(n, h, eps, tau, *[ptr(a) for a in args], ctypes.byref(out),
+                                    stream), "pfc_op_start_extrap")
     return out.value
 
 

@@ -1787,6 +1787,30 @@ int pfc_op_defect(int n, double h, double eps, double tau, const double* phi,
   return PFC_OK;
 }
 
+int pfc_op_start_extrap(int n, double h, double eps, double tau, const double* b,
+                        const double* c, const double* lapb, const double* lapc,
+                        const double* mu0, const double* om0, const double* lapmu0,
+                        const double* lapom0, double* mu1, double* om1, double* lapmu1,
+                        double* lapom1, double* S2, double* S3, double* phi, double* lap,
+                        float* r1, float* r2, float* r3, float* q, void* scratch, double* out,
+                        void* stream) {
+  if (n < 2 || (n & 1) || !(h > 0) || !b || !c || !lapb || !lapc || !mu0 || !om0 || !lapmu0 ||
+      !lapom0 || !mu1 || !om1 || !lapmu1 || !lapom1 || !S2 || !S3 || !phi || !lap || !r1 ||
+      !r2 || !r3 || !q || !scratch || !out)
+    return PFC_EINVAL;
+  double* partials = (double*)scratch;
+  double* dout = partials + (size_t)kReduceBlocks * kReduceComps;
+  double hv = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  PFC_CUDA(launch_start64_extrap(make_lvl(n, h, eps, tau), b, c, lapb, lapc, mu0, om0, lapmu0,
+                                 lapom0, mu1, om1, lapmu1, lapom1, S2, S3, phi, r1, r2, r3, q,
+                                 partials, dout, lap, st));
+  PFC_CUDA(cudaMemcpyAsync(&hv, dout, sizeof(double), cudaMemcpyDeviceToHost, st));
+  PFC_CUDA(cudaStreamSynchronize(st));
+  *out = sqrt(hv / (3.0 * (double)n * n * n));
+  return PFC_OK;
+}
+
 int pfc_op_defect_df(int n, double h, double eps, double tau, const float* phi, const float* mu,
                   const float* om, const float* S1, const float* S2, const float* S3,
                   const float* b, float* r1, float* r2, float* r3, float* q, void* scratch,

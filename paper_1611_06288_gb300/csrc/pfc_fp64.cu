@@ -680,11 +680,20 @@ __global__ void k_reduce_final_state(const double* __restrict__ partials, int np
   }
 }
 
+// Blocks of k_diagnostics_cached over all members: two per SM.  Its six
+// FP64 block sums cost 5 lanes of FP64 adds per thread in the warp
+// shuffles, as much as its per-cell work when a thread has only 7 cells
+// (1216 blocks at 128^3), so each thread takes about 27.
+constexpr int kDiagBlocks = 2 * 152;
+
 cudaError_t launch_diagnostics_cached(int n, const double* a, const double* b,
                                       const double* lapa, const double* lapb, double* partials,
                                       double* out, cudaStream_t st, int members, bool pdl,
                                       const StepState* state, StepState* state_out) {
-  int nb = reduce_blocks((int64_t)n * n * n * members) / members;
+  const int64_t cells = (int64_t)n * n * n;
+  int nb = kDiagBlocks / members;
+  if (nb > (cells + kReduceThreads - 1) / kReduceThreads)
+    nb = (int)((cells + kReduceThreads - 1) / kReduceThreads);
   if (nb < 1) nb = 1;
   cudaError_t e = launch_ex(pdl, k_diagnostics_cached, dim3(nb, members), dim3(kReduceThreads), 0,
                             st, n, a, b, lapa, lapb, partials);

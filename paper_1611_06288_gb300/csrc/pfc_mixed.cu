@@ -568,20 +568,36 @@ __global__ void __launch_bounds__(256) k_start64_point(
 // so the iterate's Laplacians are 2 Lap u^k - Lap u^{k-1} of the ones the two
 // last steps' final defects stored (lapb, lapc of phi^k = b, phi^{k-1} = c;
 // lapmu0, lapom0 of mu^k, omega^k; lapmu1, lapom1 of mu^{k-1}, omega^{k-1}).
-// S2, S3 (Eqs. 5.9-5.10) with the operations of k_start64_point, the iterate
-// phi with those of k_guess_all, the first defect with defect_rows (S1 = b).
+// The rows of the first defect are then linear combinations of the twelve
+// stored values with small integer weights plus the cubic f (Eq. 5.2):
+//   x = (c - b) + tau/h^2 Lap mu,
+//   z = (3 Lap b - Lap c)/(2h^2) - omega,
+//   y = (3 Lap b - Lap c + Lap omega)/h^2 + c1 (3b - c) + f(phi, b) - mu,
+// with S2 = (3 Lap b - Lap c)/h^2 + c1 b and S3 = Lap b/(2h^2) (Eqs. 5.9-5.10)
+// and phi = 2b - c, mu, omega the iterate.  GB300's FP64 pipe is the limit of
+// this pass (23 FP64 operations per cell in plain FP64), so the five
+// combinations of b, c and their Laplacians (2b - c, c - b, 3b - c,
+// 2 Lap b - Lap c, 3 Lap b - Lap c) are formed exactly on the integer pipe
+// from the fixed-point images of pfc_fixed.cuh (each rounded once to
+// binary64), leaving 16 FP64 operations and about as much integer work:
+// converting every input instead moves the limit to the integer pipe (a
+// conversion costs about 30 instructions).  A cell with b, c or a Laplacian
+// outside the fixed-point range (|v| >= 32, Inf, NaN) takes the same
+// formulas in FP64.  The results differ from FP64 arithmetic by the 2^-55
+// quantisation of the inputs, far below the FP32 rounding of the rows.
 // mu1, om1, lapmu1, lapom1 hold step k-1's fields on entry and the iterate's
-// on exit: each cell is read, then written, by the same thread (plain loads).
-// lap receives the iterate's Laplacian of phi.  Grid: blockIdx.y the member,
-// a grid-stride loop over its cells; per-block sums of |r|^2.
-__global__ void __launch_bounds__(256) k_start64_extrap(
+// on exit: each cell is read, then written, by the same thread.  lap receives
+// the iterate's Laplacian of phi.  Grid: blockIdx.y the member, a grid-stride
+// loop over its cells; per-block sums of |r|^2.
+__global__ void __launch_bounds__(256, 4) k_start64_extrap(
     Lvl L, const double* __restrict__ b, const double* __restrict__ c,
     const double* __restrict__ lapb, const double* __restrict__ lapc,
     const double* __restrict__ mu0, const double* __restrict__ om0,
-    const double* __restrict__ lapmu0, const double* __restrict__ lapom0, double* mu1,
-    double* om1, double* lapmu1, double* lapom1, double* __restrict__ S2,
-    double* __restrict__ S3, double* __restrict__ phi, float* __restrict__ r1,
-    float* __restrict__ r2, float* __restrict__ r3, float* __restrict__ q, double* partials,
+    const double* __restrict__ lapmu0, const double* __restrict__ lapom0,
+    double* __restrict__ mu1, double* __restrict__ om1, double* __restrict__ lapmu1,
+    double* __restrict__ lapom1, double* __restrict__ S2, double* __restrict__ S3,
+    double* __restrict__ phi, float* __restrict__ r1, float* __restrict__ r2,
+    float* __restrict__ r3, float* __restrict__ q, double* partials,
     double* __restrict__ lap, const double* __restrict__ c1m) {
   pdl_wait();
   pdl_trigger();
@@ -600,15 +616,39 @@ __global__ void __launch_bounds__(256) k_start64_extrap(
   float acc = 0.f;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
     const int i = t % n, rr = t / n, j = rr % n, k = rr / n;
-    const double pb = __ldg(b + t), lbr = __ldg(lapb + t), lcr = __ldg(lapc + t);
-    const double s2 = fma(3.0, L.g * lbr, fma(c1, pb, -(L.g * lcr)));
-    const double s3 = 0.5 * (L.g * lbr);
-    const double p = fma(2.0, pb, -__ldg(c + t));
-    const double mm = fma(2.0, __ldg(mu0 + t), -mu1[t]);
-    const double w = fma(2.0, __ldg(om0 + t), -om1[t]);
-    const double lp = fma(2.0, lbr, -lcr);
-    const double lm = fma(2.0, __ldg(lapmu0 + t), -lapmu1[t]);
-    const double lo = fma(2.0, __ldg(lapom0 + t), -lapom1[t]);
+    const double vb = __ldg(b + t), vc = __ldg(c + t);
+    const double vlb = __ldg(lapb + t), vlc = __ldg(lapc + t);
+    const double vm0 = __ldg(mu0 + t), vm1 = mu1[t];
+    const double vo0 = __ldg(om0 + t), vo1 = om1[t];
+    const double vlm0 = __ldg(lapmu0 + t), vlm1 = lapmu1[t];
+    const double vlo0 = __ldg(lapom0 + t), vlo1 = lapom1[t];
+    // the iterate, its Laplacians and the linear parts of the rows: the
+    // combinations of phi^k, phi^{k-1} and their Laplacians in fixed point,
+    // those of mu, omega in FP64 (the split that balances the two pipes)
+    const double mm = fma(2.0, vm0, -vm1);
+    const double w = fma(2.0, vo0, -vo1);
+    const double lm = fma(2.0, vlm0, -vlm1);
+    const double lo = fma(2.0, vlo0, -vlo1);
+    double p, lp, cmb, k3, bs;
+    bool ok = true;
+    const int64_t B = fix_of(vb, ok), C = fix_of(vc, ok);
+    const int64_t LB = fix_of(vlb, ok), LC = fix_of(vlc, ok);
+    if (ok) {                       // |images| < 2^59: no overflow
+      p = fix_to_double(2 * B - C);
+      cmb = fix_to_double(C - B);
+      bs = fix_to_double(3 * B - C);
+      lp = fix_to_double(2 * LB - LC);
+      k3 = fix_to_double(3 * LB - LC);
+    } else {
+      p = fma(2.0, vb, -vc);
+      cmb = vc - vb;
+      bs = vb + p;
+      lp = fma(2.0, vlb, -vlc);
+      k3 = fma(3.0, vlb, -vlc);
+    }
+    const double a = k3 + lo;
+    const double s2 = fma(L.g, k3, c1 * vb);
+    const double s3 = L.gh * vlb;
     S2[t] = s2;
     S3[t] = s3;
     phi[t] = p;
@@ -617,8 +657,13 @@ __global__ void __launch_bounds__(256) k_start64_extrap(
     lap[t] = lp;
     lapmu1[t] = lm;
     lapom1[t] = lo;
-    float xf, yf, zf, qf;
-    defect_rows(L, c1, c1f, p, mm, w, pb, lm, lo, lp, pb, s2, s3, xf, yf, zf, qf);
+    const double sq = fma(p, p, vb * vb);
+    const double x = fma(L.tg, lm, cmb);
+    const double y = fma(L.g, a, fma(c1, bs, fma(0.25 * bs, sq, -mm)));
+    const double z = fma(L.gh, k3, -w);
+    const float xf = d2f_rn(x), yf = d2f_rn(y), zf = d2f_rn(z);
+    const float pf = d2f_rn(p), bf = d2f_rn(vb);
+    const float qf = fmaf(0.75f * pf, pf, fmaf(0.5f * pf, bf, fmaf(0.25f * bf, bf, c1f)));
     acc = fmaf(xf, xf, fmaf(yf, yf, fmaf(zf, zf, acc)));
     const int o = split_index(i, j, k, n);
     r1[o] = xf;

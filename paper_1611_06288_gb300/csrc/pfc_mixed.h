@@ -180,6 +180,18 @@ cudaError_t launch_defect64(const Lvl& L, const double* phi, const double* mu,
                             double* lapmu = nullptr, double* lapom = nullptr,
                             bool pdl = false, int planes = 0, const DecideArgs* da = nullptr,
                             bool* decided = nullptr);
+// The pointwise start from u^{k+1} := 2 u^k - u^{k-1} (k_start64_extrap) and
+// its reduction to out[member] (for the C ABI checks and the step).
+cudaError_t launch_start64_extrap(const Lvl& L, const double* b, const double* c,
+                                  const double* lapb, const double* lapc, const double* mu0,
+                                  const double* om0, const double* lapmu0,
+                                  const double* lapom0, double* mu1, double* om1,
+                                  double* lapmu1, double* lapom1, double* S2, double* S3,
+                                  double* phi, float* r1, float* r2, float* r3, float* q,
+                                  double* partials, double* out, double* lap, cudaStream_t st,
+                                  int members = 1, const double* c1m = nullptr,
+                                  bool pdl = false, const DecideArgs* da = nullptr,
+                                  bool* decided = nullptr);
 // Face mobilities M(A phi_*), phi_* = 3/2 b - 1/2 c, M(phi) = m0 + m2 phi^2,
 // face i+1/2 of each axis stored at cell i (FP64).
 cudaError_t launch_face_mobility(int n, double m0, double m2, const double* b, const double* c,

@@ -244,6 +244,18 @@ def test_fused_prolong_smooth_checks_arguments(libpfc):
     assert f(64, 1.0, 0.1, 0.05, B.PFC_SWEEP_RB, 0, 0.7, *([None] * 13), None) == B.PFC_EINVAL
 
 
+def test_start_extrap_checks_arguments(libpfc):
+    """pfc_op_start_extrap: an even n >= 2, h > 0 and every pointer (checked
+    before any launch)."""
+    f = libpfc.pfc_op_start_extrap
+    fake = [ctypes.c_void_p(4096 * (i + 1)) for i in range(21)]
+    out = ctypes.c_double()
+    assert f(7, 1.0, 0.1, 0.05, *fake, ctypes.byref(out), None) == B.PFC_EINVAL
+    assert f(8, 0.0, 0.1, 0.05, *fake, ctypes.byref(out), None) == B.PFC_EINVAL
+    assert f(8, 1.0, 0.1, 0.05, *([None] * 21), ctypes.byref(out), None) == B.PFC_EINVAL
+    assert f(8, 1.0, 0.1, 0.05, *fake, None, None) == B.PFC_EINVAL
+
+
 def test_folded_correction_checks_arguments(libpfc):
     """pfc_op_lin_smooth_correct refuses n not a multiple of 4, no sweep,
     NULL fields and an FP64 state not 16-byte aligned before any CUDA call."""

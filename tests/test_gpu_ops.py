@@ -323,6 +323,58 @@ def check_defect(n, h, b, c, u):
                        "q32")
 
 
+def check_start_extrap(n, h, b, c, u0, u1):
+    """pfc_op_start_extrap against the oracle: the iterate 2 u^k - u^{k-1},
+    S2, S3 (Eqs. 5.9-5.10), the residual of the iterate (Eqs. 5.4-5.6) and
+    q rounded to FP32, and the iterate's Laplacians."""
+    L = lambda x: h * h * O.lap(x, h)                     # unscaled Laplacian
+    scratch = torch.empty(B.pfc_reduce_scratch_bytes(n), dtype=torch.uint8, device="cuda")
+    r = [empty(n, torch.float32) for _ in range(3)]
+    q = empty(n, torch.float32)
+    S2, S3, phi, lap = empty(n), empty(n), empty(n), empty(n)
+    mu1, om1, lmu1, lom1 = dev(u1[1]), dev(u1[2]), dev(L(u1[1])), dev(L(u1[2]))
+    rms = B.pfc_op_start_extrap(n, h, EPS, TAU, dev(b), dev(c), dev(L(b)), dev(L(c)),
+                                dev(u0[1]), dev(u0[2]), dev(L(u0[1])), dev(L(u0[2])),
+                                mu1, om1, lmu1, lom1, S2, S3, phi, lap, *r, q, scratch)
+    ug = [2 * b - c, 2 * u0[1] - u1[1], 2 * u0[2] - u1[2]]
+    S = O.source_S(b, c, h, prm())
+    ref = O.residual(S, ug, b, h, prm())
+    assert rms == pytest.approx(O.rms(ref), rel=1e-5)
+    assert_close_field(host(S2), S[1], FP64_RTOL, "S2")
+    assert_close_field(host(S3), S[2], FP64_RTOL, "S3")
+    for got, x, what in ((phi, ug[0], "phi"), (mu1, ug[1], "mu"), (om1, ug[2], "omega")):
+        assert_close_field(host(got), x, FP64_RTOL, what)
+    for got, x, what in ((lap, ug[0], "lap phi"), (lmu1, ug[1], "lap mu"),
+                         (lom1, ug[2], "lap omega")):
+        assert_close_field(host(got), L(x), FP64_RTOL, what)
+    for g, x in zip(r, ref):
+        assert_close_field(from_split(host(g)), x, 2 ** -23, "r32")
+    assert_close_field(from_split(host(q)), O.jacobian_coefficient(ug[0], b, prm()), 2 ** -20,
+                       "q32")
+
+
+@pytest.mark.parametrize("n", SIZES + [48])
+def test_start_extrap(n):
+    """The pointwise start from the three-field extrapolation (the Laplacians
+    of the iterate as combinations of the stored ones)."""
+    h, b, c, u0 = case(n)
+    _, _, _, u1 = case(n, seed=1)
+    check_start_extrap(n, h, b, c, u0, u1)
+
+
+def test_start_extrap_values_beyond_fixed_point_range():
+    """A cell with phi^{k-1} = 33 (and so a Laplacian of phi^{k-1} beyond 32)
+    takes the FP64 form of the fixed-point combinations; large mu^{k-1}
+    (40) and Lap omega^k (48) enter FP64 arithmetic as always."""
+    n = 12
+    h, b, c, u0 = case(n, seed=4)
+    _, _, _, u1 = case(n, seed=5)
+    u1[1][3, 4:7, 5] = 40.0
+    u0[2][7, 7, 7] = -8.0          # its unscaled Laplacian's centre term: -6 * -8 = 48
+    c[1, 2, 3] = 33.0
+    check_start_extrap(n, h, b, c, u0, u1)
+
+
 def test_defect_values_beyond_fixed_point_range():
     """The defect's neighbour sums run in 64-bit fixed point for |v| < 32; a
     block that meets larger values (here mu = 40 in a few cells of one plane,
