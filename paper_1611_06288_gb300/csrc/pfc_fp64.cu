@@ -526,7 +526,9 @@ __global__ void k_diagnostics(int n, const double* __restrict__ a,
 // and sum a, run on the integer pipe: each value of magnitude below 1 enters
 // as its fixed-point image (2^-54 quantum, pfc_fixed.cuh) into an exact int64
 // sum, which is rounded to FP64 and added every 256 cells (at most 2^8 values
-// below 2^54 each: no overflow); larger values take the FP64 adds.
+// below 2^54 each: no overflow); larger values take the FP64 adds.  The two
+// differences a - b and Lap a - Lap b are formed from the same images (exact,
+// one rounding each), which leaves 5 FP64 operations per cell.
 __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
                                      const double* __restrict__ b,
                                      const double* __restrict__ lapa,
@@ -541,19 +543,21 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
   double acc[6] = {0, 0, 0, 0, 0, 0};
   int64_t s1 = 0, s2 = 0;       // fixed-point sums of a and a^2 since the last flush
   int count = 0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cells; t += gridDim.x * blockDim.x) {
-    const double x = __ldg(a + t), la = __ldg(lapa + t);
-    const double y = x - __ldg(b + t);
+  auto cell = [&](double x, double la, double vb, double lb) {
     const double x2 = x * x;
     acc[0] = fma(x2, x2, acc[0]);
     acc[2] = fma(-x, la, acc[2]);
     acc[3] = fma(la, la, acc[3]);
-    acc[4] = fma(-y, la - __ldg(lapb + t), acc[4]);
-    if (((fix_bits_of(x) >> 52) & 0x7FFu) <= 1022u) {     // |x| < 1, so x^2 < 1
-      bool ok = true;
-      s1 += fix_of(x, ok);
+    bool ok = ((fix_bits_of(x) >> 52) & 0x7FFu) <= 1022u;   // |x| < 1, so x^2 < 1
+    const int64_t X = fix_of(x, ok), B = fix_of(vb, ok);
+    const int64_t LA = fix_of(la, ok), LB = fix_of(lb, ok);
+    if (ok) {
+      // a - b and Lap a - Lap b exact in fixed point, each rounded once
+      acc[4] = fma(-fix_to_double(X - B), fix_to_double(LA - LB), acc[4]);
+      s1 += X;
       s2 += fix_of(x2, ok);
     } else {
+      acc[4] = fma(-(x - vb), la - lb, acc[4]);
       acc[5] += x;
       acc[1] += x2;
     }
@@ -563,7 +567,24 @@ __global__ void k_diagnostics_cached(int n, const double* __restrict__ a,
       s1 = s2 = 0;
       count = 0;
     }
+  };
+  // four cells a thread in flight: their 16 loads are issued before the
+  // arithmetic of the first (the kernel is latency bound with one)
+  const int stride = gridDim.x * blockDim.x;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; t + 3 * stride < cells; t += 4 * stride) {
+    double x[4], la[4], vb[4], lb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[u] = __ldg(a + t + u * stride);
+      la[u] = __ldg(lapa + t + u * stride);
+      vb[u] = __ldg(b + t + u * stride);
+      lb[u] = __ldg(lapb + t + u * stride);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) cell(x[u], la[u], vb[u], lb[u]);
   }
+  for (; t < cells; t += stride) cell(__ldg(a + t), __ldg(lapa + t), __ldg(b + t), __ldg(lapb + t));
   acc[5] += fix_to_double(s1);
   acc[1] += fix_to_double(s2);
   block_sum<6>(acc, sm);
