@@ -168,25 +168,23 @@ def smooth_sweep(n: int, dt: float = 0.0125, tol: float = 1e-9):
     """Smooth mode on L = 32, eps = 0.025, to T = 1 (steps = 1/dt).
 
     Mixed-path settings: at n >= 64 the finest level is stiff (red-black) and
-    V(0,1) cycles are fastest: at 64^3 and 128^3 two per correction with 4
-    Jacobi sweeps per requested sweep on the intermediate levels (2
-    corrections per step; 3 with a factor of 3, and 2 still with up to 8
-    cycles); at 256^3 five per correction with a factor of 3 (2 corrections
-    per step: 165 steps/s, against 153 for three cycles and 3 corrections,
-    143 for two and 4); at 32^3 V(1,2).  Below 256^3 the 16^3 coarsest level
-    runs on an 8-CTA cluster (cluster_tail 2: 1464 against 1425 steps/s at
-    128^3; no change at 256^3).
+    V(0,1) cycles are fastest, two per correction with 4 Jacobi sweeps per
+    requested sweep on the intermediate levels; at 32^3 V(1,2).  Below 256^3
+    the 16^3 coarsest level runs on an 8-CTA cluster (cluster_tail 2: 1464
+    against 1425 steps/s at 128^3 when a step took two corrections; no
+    change at 256^3).
 
     Timed runs start each step from u^{k+1} := 2 u^k - u^{k-1} in phi, mu and
     omega (guess extrapolate_all): the first defect falls from 2.3e-5 to
-    2.6e-8 and a step takes one correction instead of two (128^3: 2438
-    against 1694 steps/s; 256^3: 313 against 200)."""
-    if n >= 256:
-        kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 5), ("jacobi_factor", 3),
-              ("coarse_sweeps", 2))
-    elif n >= 64:
+    2.6e-8 and a step takes one correction instead of two.  Whole runs to
+    T = 1 (steps/s, corrections): 128^3 2510 at a Jacobi factor of 4 (2485 at
+    2, 2390 at 5, and 1626 at 3, where every step takes two corrections);
+    256^3 455 with two cycles per correction and a factor of 4 (461 at 2, 342
+    at 3), against 321 with the five cycles and factor 3 that three
+    corrections per step needed from phi^k."""
+    if n >= 64:
         kw = (("nu1", 0), ("nu2", 1), ("inner_cycles", 2), ("jacobi_factor", 4),
-              ("coarse_sweeps", 2), ("cluster_tail", 2))
+              ("coarse_sweeps", 2)) + ((("cluster_tail", 2),) if n < 256 else ())
     else:
         kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 2), ("jacobi_factor", 3),
               ("coarse_sweeps", 2))
