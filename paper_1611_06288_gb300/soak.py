@@ -30,7 +30,7 @@ from .solver import PFCSolver
 
 def soak(n=128, steps=10000, precision="mixed", every=1, device="cuda", workload="growth"):
     wl = W.growth(n, steps) if workload == "growth" else W.polycrystal(n, steps)
-    kw = wl.mixed() if precision != "fp64" else {}
+    kw = wl.settings(precision)
     s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, wl.phi0(), device=device, tol=wl.tol,
                   step_diagnostics=every == 1,
                   precision=precision, max_cycles=100, **kw)

@@ -100,4 +100,5 @@ def test_workload_settings_by_precision():
     assert wl.settings("fp64") == {"guess": "extrapolate_all"}
     assert wl.settings("mixed_df")["guess"] == "previous"
     assert "guess" not in wl.mixed()
-    assert W.growth(32).settings("mixed")["guess"] == "previous"
+    assert W.growth(32).settings("mixed")["guess"] == "extrapolate_all"
+    assert W.cosine_table(16).settings("mixed")["guess"] == "previous"
