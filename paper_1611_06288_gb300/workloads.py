@@ -211,11 +211,12 @@ def growth(n: int = 128, steps: int = 10000, tol: float = 1e-9):
     gives h = 0.5).  Long runs of it are the energy/mass soak test.
 
     Mixed-path settings: the finest level is in the damped-Jacobi regime
-    (108 tau/h^6 = 69 at h = 0.5), so V(1,2) cycles; timed runs start from
-    the three-field extrapolation with two cycles per correction (128^3, 600
-    steps: 1.22 corrections per step, 1415 steps/s; three cycles 1.00 and
-    1266; from phi^k 2.09 and 685 with three cycles)."""
-    kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 2), ("jacobi_factor", 3),
+    (108 tau/h^6 = 69 at h = 0.5), so V(1,2) with three cycles per
+    correction; timed runs start from the three-field extrapolation (128^3,
+    10^4 steps: 1.24 corrections per step and 1063 steps/s; two cycles 1.89
+    and 978, though faster over the first 600 steps; from phi^k 2.6 and
+    549)."""
+    kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 3), ("jacobi_factor", 3),
           ("coarse_sweeps", 2))
     return Workload(f"growth{n}", n, 64.0, 0.25, 0.01, steps, tol, kw, "extrapolate_all")
 
