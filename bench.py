@@ -80,7 +80,9 @@ START_BYTES = {"previous": 104.0, "extrapolate_all": 176.0}
 # The defect class of the mixed path is the full defect (150.8 MB a launch);
 # the start of a step has a class of its own.  Keyed by the finest level's
 # size the capture ran at (other sizes: null).
-NCU_TRAFFIC = {("mixed", "defect", 128): 150.8e6}   # profiles/k_defect64_fx_128.md
+NCU_TRAFFIC = {("mixed", "defect", 128): 150.8e6,   # profiles/k_defect64_fx_128.md
+               # the start from the three-field extrapolation:
+               ("mixed", "start", 128, "extrapolate_all"): 319.0e6}  # k_start64_extrap_128.md
 
 # FP64-ALU-bound kernel classes of a precision: FP64 flops per cell of one
 # counted launch (FMA = 2) and launches per group.  The full FP64 defect forms
