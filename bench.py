@@ -515,6 +515,12 @@ def run_ours(args):
     def measure(n, steps, warmup, fp64_steps, mixed_over=None, precision="mixed",
                 other_leg=True):
         """Every GPU leg of one grid size; returns a dict of results."""
+        # untimed steps before the secondary legs' timed ones: a context caches
+        # one step graph per ring position (3) and, with the three-field
+        # extrapolated start, per mu/omega slot (2); eight steps build them all
+        # outside the timed region (the headline leg's clock sampler runs many
+        # more untimed steps before its timed region)
+        prime = max(warmup, 8)
         wl = W.smooth_sweep(n, dt=WORKLOAD["dt"], tol=WORKLOAD["tol"])
         phi0 = wl.phi0()
         mixed_kw = wl.settings(precision)
@@ -567,7 +573,7 @@ def run_ours(args):
                 kw = dict(mixed_kw, inner_cycles=mixed_kw.get("inner_cycles", 1) + extra)
                 sv = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
                                step_diagnostics=True, precision="mixed", **kw)
-                for _ in range(warmup):
+                for _ in range(prime):
                     sv.step(1)
                 res[extra] = time_steps(sv, vk, diag=False)
                 if extra == 0:
@@ -642,8 +648,7 @@ def run_ours(args):
         for g in dict.fromkeys((guess64, "previous")):
             s64 = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
                             precision="fp64", step_diagnostics=True, guess=g)
-            # two steps in a row before the extrapolated start applies
-            for _ in range(max(min(warmup, 3), 3 if g == "extrapolate_all" else 1)):
+            for _ in range(prime):
                 s64.step(1)
                 s64.diagnostics()
             ms64, cyc64 = time_steps(s64, fp64_steps)
@@ -664,7 +669,7 @@ def run_ours(args):
             sp = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
                            step_diagnostics=True, precision=precision,
                            **dict(mixed_kw, guess="previous"))
-            for _ in range(warmup):
+            for _ in range(prime):
                 sp.step(1)
                 sp.diagnostics()
             ms_p, cyc_p = time_steps(sp, steps)
@@ -686,7 +691,7 @@ def run_ours(args):
                 kw_o["guess"] = "previous"       # no three-field extrapolation there
             so = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
                            precision=other, step_diagnostics=True, **kw_o)
-            for _ in range(warmup):
+            for _ in range(prime):
                 so.step(1)
                 so.diagnostics()
             ms_o, cyc_o = time_steps(so, steps)
@@ -722,6 +727,9 @@ def run_ours(args):
         B.pfc_diagnostics(se.ctx)                 # D2H of the diagnostics (blocking)
         bufs[:] = [out, a, b]
 
+    # two untimed steps: pfc_set_state restarts the ring, and the two mu/omega
+    # slots of the extrapolated start alternate, so two step graphs are used
+    host_step()
     host_step()
     barrier()
     t0 = time.perf_counter()
