@@ -532,7 +532,9 @@ def run_ours(args):
         # extra host round trip
         s = PFCSolver(n, wl.L, wl.eps, wl.dt, phi0, device=dev, tol=wl.tol,
                       step_diagnostics=True, precision=precision, **mixed_kw)
-        for _ in range(warmup):
+        # the W warm-up steps, and more until every step graph the timed
+        # steps meet is built (see prime above)
+        for _ in range(prime):
             s.step(1)
             s.diagnostics()
         # the clock sampler starts under load (more untimed steps until its
