@@ -122,6 +122,7 @@ class Workload:
     tol: float
     mixed_settings: tuple = ()
     guess: str = "previous"
+    fp64_settings: tuple = ()
 
     @property
     def h(self) -> float:
@@ -134,10 +135,10 @@ class Workload:
 
     def settings(self, precision: str = "mixed") -> dict:
         """Keyword arguments of PFCSolver for this workload's timed runs at a
-        precision: the mixed settings (not on the FP64 FAS path) and the
-        initial iterate of a step.  The double-float state has no
-        three-field extrapolation and starts from phi^k."""
-        kw = self.mixed() if precision != "fp64" else {}
+        precision: the mixed settings, or on the FP64 FAS path its own
+        measured ones, and the initial iterate of a step.  The double-float
+        state has no three-field extrapolation and starts from phi^k."""
+        kw = self.mixed() if precision != "fp64" else dict(self.fp64_settings)
         guess = self.guess
         if guess == "extrapolate_all" and precision == "mixed_df":
             guess = "previous"
@@ -188,8 +189,13 @@ def smooth_sweep(n: int, dt: float = 0.0125, tol: float = 1e-9):
     else:
         kw = (("nu1", 1), ("nu2", 2), ("inner_cycles", 2), ("jacobi_factor", 3),
               ("coarse_sweeps", 2))
+    # FP64 FAS: V(0,1) with a Jacobi factor of 2, the fastest of a measured
+    # sweep of cycle shapes and factors from the extrapolated start (128^3 /
+    # 256^3 steps/s: 514 / 81.8 with 2 cycles a step; V(1,1) factor 2 402 /
+    # 64.0; the library's V(2,2) 165 / 29.8 with 3)
+    fp64 = (("nu1", 0), ("nu2", 1), ("jacobi_factor", 2))
     return Workload(f"smooth{n}", n, 32.0, 0.025, dt, int(round(1.0 / dt)), tol, kw,
-                    "extrapolate_all")
+                    "extrapolate_all", fp64)
 
 
 def polycrystal(n: int = 256, steps: int = 2000, tol: float = 1e-9):

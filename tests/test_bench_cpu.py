@@ -93,11 +93,13 @@ def test_oracle_all_cores_timing_runs_spawned_replicas():
 def test_workload_settings_by_precision():
     """The timed runs of the smooth sweep start from the three-field
     extrapolation on the FP64 and mixed paths; the double-float state, which
-    has none, starts from phi^k; the FP64 path takes no mixed settings."""
+    has none, starts from phi^k; the FP64 path takes its own cycle settings,
+    not the mixed ones."""
     from paper_1611_06288_gb300 import workloads as W
     wl = W.smooth_sweep(128)
     assert wl.settings("mixed") == dict(wl.mixed(), guess="extrapolate_all")
-    assert wl.settings("fp64") == {"guess": "extrapolate_all"}
+    assert wl.settings("fp64") == {"nu1": 0, "nu2": 1, "jacobi_factor": 2,
+                                   "guess": "extrapolate_all"}
     assert wl.settings("mixed_df")["guess"] == "previous"
     assert "guess" not in wl.mixed()
     assert W.growth(32).settings("mixed")["guess"] == "extrapolate_all"
