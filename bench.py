@@ -48,7 +48,7 @@ KERNEL_BYTES = {
     "lin_prolong": (25.5, 1),     # read+write d (24) + coarse d (12/8)
     "correct": (60.0, 1),         # read df u (24) d (12) write df u (24); the mixed form below
     "smooth": (40.0, 1),          # per colour pass: half of (u 24 + S2,S3 16 + b 8 + phi 8 + write u 24)
-    "residual_norm": (48.0, 2),   # read u, b, S2, S3
+    "residual_norm": (56.0, 2),   # read u, b, S2, S3 (48), write the Laplacian of phi (8)
     "residual_restrict": (57.0, 1),
     "prolong": (57.0, 2),
     "source": (32.0, 1),
@@ -438,6 +438,30 @@ def run_reference(args):
 FP64_SMOOTH_FLOPS = 66.0
 
 
+def fp64_class_roofline(cls, m, red_black, launches, ms, hbm_gbs, hbm_source):
+    """Roofline of an FP64 FAS kernel class from its event-timed launches at a
+    level of m^3 cells (ms in total over `launches`): the red-black or Jacobi
+    smoother in FP64 flops against the FP64 pipe, a class with a byte model
+    in algorithmic bytes against the measured HBM peak, else no fraction."""
+    if cls == "smooth":
+        units = m ** 3 / (2 if red_black else 1)
+        achieved = FP64_SMOOTH_FLOPS * units * launches / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "flops_per_updated_cell": FP64_SMOOTH_FLOPS,
+                "peak_source": "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz "
+                               "(derived)"}
+    per_cell, per_group = KERNEL_BYTES.get(cls, (0.0, 1))
+    if per_cell > 0:
+        groups = launches / per_group
+        gbs = per_cell * m ** 3 * groups / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": gbs / hbm_gbs, "algorithmic_bytes_per_cell": per_cell,
+                "launches_per_pass": per_group, "ms_per_pass": ms / max(groups, 1e-30),
+                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({hbm_source})"}
+    return {"bound": None, "note": "dominant class without a flop or byte model"}
+
+
 def fp64_roofline(s, n, B, prof_steps=1):
     """Roofline of the dominant kernel class of the plain FP64 FAS path: one
     host-driven step with every class timed by CUDA events picks the class,
@@ -454,16 +478,9 @@ def fp64_roofline(s, n, B, prof_steps=1):
     m, _, kind = B.pfc_level_info(s.params, lvl)
     out = {"kernel": f"{cls} (level {lvl}, {m}^3)", "ms_per_launch": ms / max(launches, 1),
            "timing": f"CUDA events around each launch, {prof_steps} host-driven step(s)"}
-    if cls == "smooth":
-        units = m ** 3 / (2 if kind == B.PFC_SWEEP_RB else 1)
-        achieved = FP64_SMOOTH_FLOPS * units * launches / (ms / 1e3) / 1e12 if ms > 0 else 0.0
-        out.update({"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                    "flops_per_updated_cell": FP64_SMOOTH_FLOPS,
-                    "peak_source": "FP64: 2 FMA lanes/SM/clock x 2 flops x 152 SMs x 2.07 GHz "
-                                   "(derived)"})
-    else:
-        out.update({"bound": None, "note": "dominant class without a flop model"})
+    peaks, src = measured_peaks()
+    out.update(fp64_class_roofline(cls, m, kind == B.PFC_SWEEP_RB, launches, ms,
+                                   peaks["hbm_gbs"], src))
     out["kernel_profile_ms"] = {f"{k[0]}@{n >> k[1]}": round(v[1], 4)
                                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])[:8]}
     return out

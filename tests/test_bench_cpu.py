@@ -104,3 +104,20 @@ def test_workload_settings_by_precision():
     assert "guess" not in wl.mixed()
     assert W.growth(32).settings("mixed")["guess"] == "extrapolate_all"
     assert W.cosine_table(16).settings("mixed")["guess"] == "previous"
+
+
+def test_fp64_class_roofline():
+    """The FP64 arm's kernel-class fractions: the smoother in flops against the
+    FP64 pipe (half the cells per red-black pass), the residual norm (kernel
+    and reduction: two launches a pass) in bytes against HBM."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.fp64_class_roofline("smooth", 128, True, 4, 1.0, 6781.8, "measured")
+    flops = bench.FP64_SMOOTH_FLOPS * 128 ** 3 / 2 * 4 / 1e-3 / 1e12
+    assert r["bound"] == "alu" and r["achieved"] == pytest.approx(flops)
+    assert r["frac"] == pytest.approx(flops / bench.FP64_PEAK_TFLOPS)
+    r = bench.fp64_class_roofline("residual_norm", 128, True, 2, 0.072, 6781.8, "measured")
+    gbs = 56.0 * 128 ** 3 / 0.072e-3 / 1e9
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(gbs)
+    assert r["frac"] == pytest.approx(gbs / 6781.8) and r["ms_per_pass"] == pytest.approx(0.072)
+    assert bench.fp64_class_roofline("coarse_solve", 2, False, 1, 0.01, 1.0, "")["bound"] is None
