@@ -219,25 +219,37 @@ def test_energy_law_and_mass_on_gpu_trajectory():
         c, b = b, a
 
 
-@pytest.mark.parametrize("precision", ["mixed", "mixed_df", "fp64"])
-def test_full_size_128_residual_by_oracle(precision):
-    """128^3 smooth-mode workload (L = 32, eps = 0.025, dt = 0.0125, tol 1e-9)
-    in the benchmark's configuration (the workload's mixed-path settings): after two steps the oracle evaluates
-    S - N(u) of the GPU result on the CPU in FP64 and finds it below the
-    tolerance; mass is conserved."""
-    wl = W.smooth_sweep(128)
+@pytest.mark.parametrize("n,precision", [(128, "mixed"), (128, "mixed_df"), (128, "fp64"),
+                                         (256, "mixed")])
+def test_full_size_residual_by_oracle(n, precision):
+    """Smooth-mode workload (L = 32, eps = 0.025, dt = 0.0125, tol 1e-9) at
+    128^3 and 256^3 in the benchmark's configuration (the workload's timed
+    settings for the precision, the step diagnostics inside the step; on the
+    mixed and FP64 paths the fourth step starts from the three-field
+    extrapolation): the oracle evaluates S - N(u) of the GPU's fourth step on
+    the CPU in FP64 and finds it below the tolerance, the energy the step
+    formed equals the oracle's F_h of the same field, and mass is
+    conserved."""
+    wl = W.smooth_sweep(n)
     phi0 = wl.phi0()
-    kw = wl.mixed() if precision != "fp64" else {}
-    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision, **kw)
-    s.step(1)
-    b = phi0
-    a1 = host(s.phi())
-    s.step(1)
+    s = PFCSolver(wl.n, wl.L, wl.eps, wl.dt, phi0, tol=wl.tol, precision=precision,
+                  step_diagnostics=True, **wl.settings(precision))
+    hist = [phi0]
+    for _ in range(3):
+        s.step(1)
+        hist.append(host(s.phi()))
+    st = s.step(1)
+    assert st.residual <= wl.tol
     a, mu, om = host(s.phi()), host(s.mu()), host(s.omega())
+    b, c = hist[-1], hist[-2]
     p = O.Params(eps=wl.eps, tau=wl.dt)
-    r = O.residual(O.source_S(a1, b, wl.h, p), [a, mu, om], a1, wl.h, p)
+    r = O.residual(O.source_S(b, c, wl.h, p), [a, mu, om], b, wl.h, p)
     assert O.rms(r) <= wl.tol * 1.0001
-    assert O.mass(a, wl.h) == pytest.approx(O.mass(phi0, wl.h), abs=1e-9 * wl.L ** 3)
+    F, _ = s.energy()
+    assert F == pytest.approx(O.energy(a, wl.h, wl.eps), rel=1e-10)
+    # a converged step moves the mass by at most sqrt(3) tol L^3
+    assert O.mass(a, wl.h) == pytest.approx(O.mass(phi0, wl.h),
+                                            abs=4 * 3 ** 0.5 * wl.tol * wl.L ** 3)
 
 
 @pytest.mark.parametrize("precision", ["mixed", "mixed_df"])
