@@ -169,6 +169,20 @@ def test_guess_param(libpfc):
     assert B.pfc_workspace_bytes(p) == 0
 
 
+def test_guess_param_batch_workspace(libpfc):
+    """An ensemble with the three-field extrapolated start holds the second
+    mu, omega slot and its Laplacians for every member."""
+    p = B.pfc_default_params()
+    p.n, p.L, p.eps, p.dt = 16, 32.0, 0.1, 0.05
+    p.precision, p.guess = B.PFC_MIXED, B.PFC_GUESS_PREVIOUS
+    for members in (1, 3, 7):
+        base = B.pfc_batch_workspace_bytes(p, members)
+        p.guess = B.PFC_GUESS_EXTRAPOLATE_ALL
+        extra = 4 * 8 * 16 ** 3 * members
+        assert base + extra <= B.pfc_batch_workspace_bytes(p, members) <= base + extra + 4096
+        p.guess = B.PFC_GUESS_PREVIOUS
+
+
 def test_cluster_tail_param(libpfc):
     """cluster_tail is 0, 1 or 2 (default 0) and does not change the
     workspace: the cluster kernel keeps its levels in shared memory."""
